@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs shaped like the beamline data of the paper.
+
+This module holds only input generation (random shapes, noise, detector
+defects); none of the method's arithmetic lives here.  Both the CUDA path's
+tests/benchmarks and the CPU oracle take their inputs from it.
+
+The paper's data (60 micron glass spheres at 1.8 micron voxels, section
+"Introduction") are not available; piecewise-constant disk and ellipse
+phantoms stand in for them:
+
+* disks:    radii 8-20 px, values U[0.5, 1], non-overlapping, inside the
+            inscribed circle, pixel value = covered area fraction (4x4
+            super-sampling);
+* ellipses: semi-axes U[20, 200] px (scaled with N), orientation U[0, pi),
+            values U[0.5, 1], overlaps summed, inside the inscribed circle;
+* phase-contrast image: 5-point discrete Laplacian of such a phantom (the
+            measured quantity is the Laplacian of the phase, section
+            "Introduction"), which is sparse;
+* sinogram defects: Gaussian noise of standard deviation 1% of the clean
+            sinogram's maximum plus 8 "stuck" detector columns carrying a
+            constant offset U[-0.2, 0.2] x max over all angles (ring artifacts).
+
+Seeds: configuration c uses seed 1009 + c; slice i of a batch uses
+(1009 + c) * 10007 + i.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED_BASE = 1009
+
+
+def seed_for(config_index: int, slice_index: int | None = None) -> int:
+    s = SEED_BASE + config_index
+    return s if slice_index is None else s * 10007 + slice_index
+
+
+def rng_for(config_index: int, slice_index: int | None = None) -> np.random.Generator:
+    return np.random.default_rng(seed_for(config_index, slice_index))
+
+
+# named workloads (sizes of the five benchmark configurations)
+CONFIGS = {
+    "c1_128": dict(index=0, n=128, n_det=128, n_views=180, kind="disks", n_shapes=5),
+    "c2_2048": dict(index=1, n=2048, n_det=2048, n_views=1024, kind="ellipses", n_shapes=40),
+    "c3_batch1024": dict(index=2, n=1024, n_det=1024, views_choices=(64, 128, 256, 512),
+                         batch=256, kind="ellipses", n_shapes=20),
+    "c4_spgl1_1024": dict(index=3, n=1024, n_det=1024, n_views=128, batch=64,
+                          kind="laplacian", n_shapes=20, iterations=300),
+    "c5_warm512": dict(index=4, n=512, n_det=512, n_views=90, kind="laplacian", n_shapes=12),
+}
+
+
+def _coverage(n, inside_fn, ss=4):
+    """Fraction of each pixel covered by a shape (ss x ss sub-samples)."""
+    off = (np.arange(ss) + 0.5) / ss - 0.5
+    X = np.arange(n, dtype=np.float64) - n // 2
+    img = np.zeros((n, n))
+    for dy in off:
+        for dx in off:
+            img += inside_fn(X[None, :] + dx, X[:, None] + dy)
+    return img / (ss * ss)
+
+
+def disk_phantom(n: int, n_disks: int, rng: np.random.Generator,
+                 r_range=(8.0, 20.0), v_range=(0.5, 1.0), max_tries=10000):
+    """Non-overlapping disks; returns (image float64, [(cx, cy, r, v), ...])."""
+    R_in = n / 2 - 2.0
+    disks = []
+    tries = 0
+    while len(disks) < n_disks and tries < max_tries:
+        tries += 1
+        r = rng.uniform(*r_range)
+        rho = (R_in - r) * math.sqrt(rng.uniform())
+        phi = rng.uniform(0, 2 * math.pi)
+        cx, cy = rho * math.cos(phi), rho * math.sin(phi)
+        if all((cx - d[0]) ** 2 + (cy - d[1]) ** 2 > (r + d[2] + 1.0) ** 2 for d in disks):
+            disks.append((cx, cy, r, rng.uniform(*v_range)))
+    img = np.zeros((n, n))
+    for (cx, cy, r, v) in disks:
+        box = _coverage(n, lambda X, Y, cx=cx, cy=cy, r=r: ((X - cx) ** 2 + (Y - cy) ** 2 < r * r))
+        img += v * box
+    return img, disks
+
+
+def ellipse_phantom(n: int, n_shapes: int, rng: np.random.Generator,
+                    axes_range=(20.0, 200.0), v_range=(0.5, 1.0), ss=2):
+    """Random ellipses (overlaps summed) inside the inscribed circle.
+
+    Semi-axes are drawn from ``axes_range`` scaled by n / 2048.
+    """
+    scale = n / 2048.0
+    R_in = n / 2 - 2.0
+    img = np.zeros((n, n))
+    shapes = []
+    for _ in range(n_shapes):
+        a = max(2.0, rng.uniform(*axes_range) * scale)
+        b = max(2.0, rng.uniform(*axes_range) * scale)
+        a, b = min(a, 0.45 * R_in), min(b, 0.45 * R_in)
+        ang = rng.uniform(0, math.pi)
+        rho = (R_in - max(a, b)) * math.sqrt(rng.uniform())
+        phi = rng.uniform(0, 2 * math.pi)
+        cx, cy = rho * math.cos(phi), rho * math.sin(phi)
+        v = rng.uniform(*v_range)
+        ca, sa = math.cos(ang), math.sin(ang)
+
+        def inside(X, Y, cx=cx, cy=cy, a=a, b=b, ca=ca, sa=sa):
+            xr = (X - cx) * ca + (Y - cy) * sa
+            yr = -(X - cx) * sa + (Y - cy) * ca
+            return (xr / a) ** 2 + (yr / b) ** 2 < 1.0
+
+        img += v * _coverage(n, inside, ss)
+        shapes.append((cx, cy, a, b, ang, v))
+    return img, shapes
+
+
+def laplacian5(u: np.ndarray) -> np.ndarray:
+    """5-point discrete Laplacian with zero outside the image."""
+    p = np.pad(u, 1)
+    return p[:-2, 1:-1] + p[2:, 1:-1] + p[1:-1, :-2] + p[1:-1, 2:] - 4.0 * u
+
+
+def phantom(config: str, slice_index: int | None = None, dtype=np.float32):
+    """Image of a named configuration (one slice)."""
+    c = CONFIGS[config]
+    rng = rng_for(c["index"], slice_index)
+    n = c["n"]
+    if c["kind"] == "disks":
+        img, _ = disk_phantom(n, c["n_shapes"], rng)
+    elif c["kind"] == "ellipses":
+        img, _ = ellipse_phantom(n, c["n_shapes"], rng)
+    else:
+        u, _ = ellipse_phantom(n, c["n_shapes"], rng)
+        img = laplacian5(u)
+    return img.astype(dtype)
+
+
+def views_for_batch(config: str = "c3_batch1024") -> np.ndarray:
+    """Per-slice view counts, uniform over the configuration's choices."""
+    c = CONFIGS[config]
+    rng = rng_for(c["index"])
+    return rng.choice(np.asarray(c["views_choices"]), size=c["batch"])
+
+
+def corrupt_sinogram(y_clean: np.ndarray, rng: np.random.Generator,
+                     noise_frac=0.01, n_stuck=8, stuck_frac=0.2):
+    """Add Gaussian noise (std = noise_frac * max) and stuck-column offsets.
+
+    Returns (y_noisy, noise_std, stuck_columns).
+    """
+    y = np.asarray(y_clean, dtype=np.float64)
+    ymax = float(np.abs(y).max())
+    std = noise_frac * ymax
+    out = y + rng.normal(0.0, std, size=y.shape)
+    cols = rng.choice(y.shape[1], size=n_stuck, replace=False)
+    offs = rng.uniform(-stuck_frac, stuck_frac, size=n_stuck) * ymax
+    out[:, cols] += offs[None, :]
+    return out, std, np.sort(cols)
+
+
+def random_sinogram(n_views: int, n_det: int, rng: np.random.Generator, dtype=np.float32):
+    """Dense random test vector in sinogram space (for adjoint tests)."""
+    return rng.standard_normal((n_views, n_det)).astype(dtype)
