@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the Radon forward + adjoint pair (gridding NUFFT) on GB300.
+
+Workload (default): one 2048 x 2048 float32 slice of 40 random ellipses,
+1024 views x 2048 detector bins (S = 2,097,152 polar samples), Kaiser-Bessel
+width 6, oversampling 2.  A step is one radon_fwd followed by one radon_adj
+of its output (the operator pair an SPGL1 iteration applies).
+
+value      = samples of all ranks / max-over-ranks device time   [Msamples/s]
+             (S samples per pair; inputs resident in HBM; L2 flushed with a
+             256 MB write before every timed step, outside the timed events)
+e2e        = the same pair through the host-buffer C ABI entry points
+             (radon_fwd_host / radon_adj_host, pinned host memory, copies
+             inside the timed region)
+roofline   = dominant kernel's algorithmic bytes / its CUDA-event time
+cpu_baseline = the FP64 oracle on the host cores, bounded sample
+
+--impl reference times the FP64 oracle (the only reference this paper has) on
+the same workload, metric and unit.  Multi-GPU: slices are independent, so N
+ranks run N replicas (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (N, Ns, M, synth config)
+    "c2_2048": (2048, 2048, 1024, "c2_2048"),
+    "c1_128": (128, 128, 180, "c1_128"),
+}
+KERNELS = ["k_fwd_col", "k_fwd_row", "k_fwd_interp", "k_fwd_ray", "k_adj_ray", "k_adj_spread",
+           "k_adj_reduce", "k_adj_row", "k_adj_col"]
+METRIC = "Radon fwd+adj Msamples/s"
+
+
+def alg_bytes(kname, n, ns, m):
+    """Compulsory DRAM bytes of one launch: what the kernel must read + write."""
+    G, K = 2 * n, ns // 2
+    half = (n + 1) * G * 8          # half spectrum b = 0..N, complex64
+    h1 = (n + 1) * n * 8            # column/row intermediate, complex64
+    img = n * n * 4
+    q = m * (K + 1) * 8             # polar samples k = 0..Ns/2, complex64
+    sino = m * ns * 4
+    return {
+        "k_fwd_col": img + h1, "k_fwd_row": h1 + half, "k_fwd_interp": half + q, "k_fwd_ray": q + sino,
+        "k_adj_ray": sino + q, "k_adj_spread": q + half, "k_adj_reduce": 0, "k_adj_row": half + h1,
+        "k_adj_col": h1 + img,
+    }[kname]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(kname, workload):
+    """DRAM bytes per launch of `kname` from the committed ncu summary, if the
+    summary's source hash matches the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kname}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    want = None
+    traffic = None
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("source_sha256:"):
+                want = line.split(":", 1)[1].strip()
+            if line.startswith("traffic_bytes_per_launch:"):
+                traffic = float(line.split(":", 1)[1].strip())
+    if want is None or traffic is None:
+        return None
+    from paper_1009_1380_gb300 import build as b
+    return traffic if b.source_digest() == want else None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.tmp.read().splitlines() if ln.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+class OracleTimer:
+    """Times the FP64 oracle's fwd + adj on the workload.
+
+    The 2D FFT and inverse FFT of the oversampled grid are timed once; a step
+    grids a block of rays forward and back (interpolation, ray inverse DFT,
+    ray DFT, spread) and is charged its share rays/M of the measured FFT time,
+    so that a cycle over all M rays costs exactly one full oracle pair.
+    """
+
+    def __init__(self, workload):
+        from oracle import nufft
+        from paper_1009_1380_gb300 import synth
+        self.nufft = nufft
+        n, ns, m, cfg = WORKLOADS[workload]
+        self.n, self.ns, self.m = n, ns, m
+        self.img = synth.phantom(cfg).astype(np.float64)
+        self.geo = nufft.GridGeometry(n, ns, nufft.default_angles(m))
+        t0 = time.perf_counter()
+        self.F = np.fft.fft2(nufft.grid_deapod_pad(self.img, self.geo))
+        t1 = time.perf_counter()
+        G = self.geo.grid
+        z = np.fft.ifft2(self.F) * (G * G)
+        nufft.grid_crop_deapod(z, self.geo)
+        t2 = time.perf_counter()
+        self.t_fft = (t1 - t0) + (t2 - t1)
+        self.cursor = 0
+
+    def step(self, rays_per_step):
+        nf = self.nufft
+        r0 = self.cursor
+        rays = (np.arange(rays_per_step) + r0) % self.m
+        self.cursor = (r0 + rays_per_step) % self.m
+        t0 = time.perf_counter()
+        P = nf.grid_interp(self.F, self.geo, rays)
+        y = nf.ray_idft(P).real
+        nf.grid_spread(nf.ray_idft_adj(y), self.geo, rays)
+        t = time.perf_counter() - t0
+        return t + self.t_fft * rays_per_step / self.m, rays_per_step * self.ns
+
+    def time_per_ray(self):
+        t, _ = self.step(4)
+        return (t - self.t_fft * 4 / self.m) / 4
+
+
+def cpu_baseline(workload, budget_s=20.0):
+    ot = OracleTimer(workload)
+    per_ray = ot.time_per_ray()
+    rays = int(max(1, min(ot.m, budget_s / max(per_ray, 1e-6))))
+    t, samples = ot.step(rays)
+    return {"value": samples / t / 1e6, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle (NumPy, single-threaded): fwd+adj gridding of {rays} of {ot.m} rays of "
+                       f"the {ot.n}x{ot.n} workload, plus {rays}/{ot.m} of the measured oversampled 2D FFT + "
+                       f"inverse FFT time ({ot.t_fft:.2f} s per full pair)"),
+            "seconds": t}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ot = OracleTimer(args.workload)
+    per_ray = ot.time_per_ray()
+    total_steps = args.steps + args.warmup
+    budget = 150.0 / max(1, total_steps)
+    rays = int(max(1, min(ot.m, budget / max(per_ray, 1e-6))))
+    for _ in range(args.warmup):
+        ot.step(rays)
+    tot_t, tot_s = 0.0, 0
+    for _ in range(args.steps):
+        t, s = ot.step(rays)
+        tot_t += t
+        tot_s += s
+    value = tot_s / tot_t / 1e6
+    sample = (f"per step: FP64 oracle fwd+adj gridding of {rays} of {ot.m} rays of the {ot.n}x{ot.n} workload "
+              f"plus {rays}/{ot.m} of the measured 2D FFT + inverse FFT time")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_dict(args),
+           "cpu_baseline": {"value": value, "unit": "Msamples/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "Msamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_dict(args):
+    n, ns, m, _ = WORKLOADS[args.workload]
+    return {"workload": f"{args.workload}: {n}x{n} float32 phantom, {m} views x {ns} bins, KB W=6 sigma=2",
+            "n": n, "n_views": m, "n_det": ns, "samples_per_op": m * ns,
+            "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1009_1380_gb300 import build as b
+    b.build()
+    from paper_1009_1380_gb300 import cpct, synth
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n, ns, m, cfg = WORKLOADS[args.workload]
+    S = m * ns
+    plan = cpct.Plan(n, ns, m)
+    img = torch.from_numpy(synth.phantom(cfg, slice_index=rank if world > 1 else None)).cuda()
+    y = torch.empty((m, ns), device="cuda")
+    z = torch.empty((n, n), device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def pair():
+        plan.fwd(img, y)
+        plan.adj(y, z)
+
+    # untimed pass: per-kernel breakdown (all kernels bracketed by events)
+    for _ in range(3):
+        pair()
+    plan.profile_enable(0x1FF)
+    for _ in range(5):
+        flush.zero_()
+        pair()
+    torch.cuda.synchronize()
+    breakdown = plan.profile_read()
+    dominant = max(breakdown, key=lambda k: breakdown[k][0])
+    plan.profile_enable(1 << KERNELS.index(dominant))
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        pair()
+    plan.profile_read()  # drop warm-up records
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    plan.launch_count(reset=True)
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        pair()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = plan.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    plan.sync()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    dom_ms, dom_cnt = plan.profile_read().get(dominant, (0.0, 0))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    plan.profile_enable(0)
+    value = world * args.steps * S / (total_ms / 1000.0) / 1e6
+
+    # end to end through the host-buffer C ABI (pinned host memory)
+    img_h = torch.from_numpy(synth.phantom(cfg)).pin_memory().numpy()
+    sino_h = torch.empty((m, ns), dtype=torch.float32).pin_memory().numpy()
+    out_h = torch.empty((n, n), dtype=torch.float32).pin_memory().numpy()
+    for _ in range(3):
+        plan.fwd_host(img_h, sino_h)
+        plan.adj_host(sino_h, out_h)
+    e2e_steps = max(5, min(50, args.steps))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.fwd_host(img_h, sino_h)
+        plan.adj_host(sino_h, out_h)
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    dom_avg_s = dom_ms / max(1, dom_cnt) / 1000.0
+    ab = alg_bytes(dominant, n, ns, m)
+    achieved = ab / dom_avg_s / 1e9 if dom_avg_s > 0 else 0.0
+    out = {
+        "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(args),
+        "e2e": {"value": S / t_e2e / 1e6, "unit": "Msamples/s",
+                "h2d_bytes_per_step": 4 * n * n + 4 * m * ns, "d2h_bytes_per_step": 4 * m * ns + 4 * n * n},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                     "alg_bytes_per_launch": ab, "avg_launch_us": dom_avg_s * 1e6,
+                     "traffic": profile_traffic(dominant, args.workload)},
+        "kernels_us": {k: round(v[0] / max(1, v[1]) * 1000.0, 2) for k, v in breakdown.items()},
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2_2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

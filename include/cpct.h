@@ -1,0 +1,176 @@
+/*
+ * cpct.h -- C ABI of the GB300-native compressive phase-contrast tomography
+ * library: the Fourier-slice Radon transform by gridding (non-uniform FFT),
+ * its adjoint, the cubic ring-artifact filter and the SPGL1 basis-pursuit
+ * solver that calls them.
+ *
+ * Paper: Maia et al., "Compressive Phase Contrast Tomography" (arXiv 1009.1380).
+ *  - Section "fast radon transform": Radon{x} = 2D FFT of x on a regular grid,
+ *    gridding interpolation onto a polar grid, 1D inverse FFT along each
+ *    radial line; the adjoint runs the steps in reverse (gridding).
+ *  - Section "Introduction", the L1 problem: min ||x||_1 subject to
+ *    ||filter(Radon{x} - data)||_2 < eps, solved by SPGL1, which needs the
+ *    operator y = Radon{x} and its adjoint.
+ *
+ * Conventions shared by every entry point (the paper fixes none of them):
+ *  - image x: N x N float32, row-major, x[p*N + q]; row p is the y axis,
+ *    column q the x axis; pixel centre at (p, q) = (N/2, N/2);
+ *  - sinogram y: M x Ns float32, row-major, y[j*Ns + s]; angle theta_j,
+ *    detector bin s with the rotation axis at s = Ns/2, pitch = pixel pitch;
+ *  - default angles theta_j = pi j / M (from +x towards +y);
+ *  - the real operator is R x = Re(A x) with A the complex Fourier-slice
+ *    transform (unnormalised 2D DFT, centred ray inverse DFT scaled by 1/Ns);
+ *    radon_adj computes R^T w = Re(A^H w), the exact adjoint up to rounding;
+ *  - Kaiser-Bessel kernel, width 6, grid oversampling 2 (G = 2N).
+ *
+ * Ownership: every pointer argument named d_* is DEVICE memory owned by the
+ * caller (CUDA runtime allocations, e.g. from PyTorch); h_* arguments are host
+ * memory owned by the caller.  A plan owns its own device workspaces (the
+ * oversampled spectrum, tables and bin lists) and frees them in
+ * cpct_plan_destroy.  Device pointers to float data must be 16-byte aligned.
+ *
+ * Streams: every call is stream-ordered on the given stream (NULL = legacy
+ * default stream) and asynchronous unless stated otherwise.  A plan holds
+ * per-call workspaces and must not be used by two streams concurrently.
+ *
+ * Errors: every function returns CPCT_OK (0) or a negative cpct_status; an
+ * argument error is detected on the host before anything is enqueued.
+ * Asynchronous device-side failures (a bounded wait that expired) are
+ * recorded in the plan and returned by the next cpct_plan_sync().
+ */
+#ifndef CPCT_H_
+#define CPCT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cpct_status {
+  CPCT_OK = 0,
+  CPCT_EINVAL = -1,       /* null pointer, bad size, unsupported geometry      */
+  CPCT_ENOMEM = -2,       /* a device or host allocation failed                */
+  CPCT_ECUDA = -3,        /* a CUDA runtime/driver call failed                 */
+  CPCT_ETIMEOUT = -4,     /* a bounded device wait expired (kernel returned)   */
+  CPCT_ENONFINITE = -5,   /* the solver met a NaN/Inf                          */
+  CPCT_ENOTCONV = -6,     /* the solver hit its iteration cap                  */
+  CPCT_EUNSUPPORTED = -7  /* feature not available (e.g. no sm_103a device)    */
+} cpct_status;
+
+/* Geometry of one slice.  Section "fast radon transform".
+ *   n        image side N; power of two, 32 <= N <= 2048
+ *   n_det    detector bins Ns; power of two, N <= Ns <= 4096
+ *   n_views  number of projection angles M, 1 <= M <= 32768
+ *   angles   host array of M angles in [0, pi) radians, or NULL for pi j / M
+ *   kb_width kernel width W; only 6 is supported (0 selects 6)
+ *   oversamp grid oversampling sigma; only 2.0 is supported (0 selects 2)
+ *   flags    CPCT_PLAN_* bits                                               */
+typedef struct cpct_geom {
+  int n;
+  int n_det;
+  int n_views;
+  const double* angles;
+  int kb_width;
+  double oversamp;
+  int flags;
+} cpct_geom;
+
+/* plan flags */
+#define CPCT_PLAN_FAIL_ALLOC 0x1000 /* testing: make the first device allocation fail */
+
+typedef struct cpct_plan cpct_plan;
+
+/* Create a plan: builds, on the device and in FP64, the Kaiser-Bessel kernel
+ * approximation and deapodization vector and the FFT twiddle tables; builds
+ * the tile bin lists of the polar samples (gridding, section "fast radon
+ * transform": the sample plane is divided into bins with one thread block per
+ * bin) and uploads them.  Synchronous on `stream`.  *out is NULL on failure. */
+int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_t stream);
+
+/* Free a plan and every workspace it owns.  NULL is accepted. */
+int cpct_plan_destroy(cpct_plan* plan);
+
+/* Wait for the plan's work on `stream` and report the first asynchronous
+ * device-side error recorded since the previous call (CPCT_ETIMEOUT ...). */
+int cpct_plan_sync(cpct_plan* plan, cudaStream_t stream);
+
+/* Query plan sizes: image side, detector bins, views, oversampled grid G,
+ * bytes of plan-owned device memory. Any output pointer may be NULL. */
+int cpct_plan_info(const cpct_plan* plan, int* n, int* n_det, int* n_views,
+                   int* grid, size_t* device_bytes);
+
+/* Forward operator  y = Re(A x).  Section "fast radon transform": deapodize
+ * and zero-pad, oversampled 2D FFT, Kaiser-Bessel interpolation onto the
+ * polar grid, inverse FFT along each ray.
+ *   d_img   device, N*N float32 (read)
+ *   d_sino  device, M*Ns float32 (written)                                  */
+int radon_fwd(cpct_plan* plan, const float* d_img, float* d_sino, cudaStream_t stream);
+
+/* Adjoint operator  x = Re(A^H w) (the transpose of radon_fwd): FFT along each
+ * ray, gridding (polar -> Cartesian convolution) as a deterministic
+ * tile-binned gather, inverse 2D FFT, crop and deapodize.
+ *   d_sino  device, M*Ns float32 (read)
+ *   d_img   device, N*N float32 (written)                                   */
+int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream);
+
+/* Host-buffer variants: copy h_in (pinned or pageable host memory) to a
+ * plan-owned device staging buffer, run the operator, copy the result back
+ * to h_out and synchronize `stream`.  For end-to-end timing and for callers
+ * without device memory. */
+int radon_fwd_host(cpct_plan* plan, const float* h_img, float* h_sino, cudaStream_t stream);
+int radon_adj_host(cpct_plan* plan, const float* h_sino, float* h_img, cudaStream_t stream);
+
+/* Human-readable name of a cpct_status (static string). */
+const char* cpct_strerror(int status);
+
+/* ---- introspection for tests (host-only unless stated) ------------------ */
+
+/* Bin lists of a geometry, built on the host exactly as cpct_plan_create
+ * builds them (no GPU needed).  which = 0: forward bins (each polar sample
+ * k = 0..Ns/2 in the 32x32 tile of its footprint's first grid point);
+ * which = 1: adjoint bins (every tile of the extended half spectrum that the
+ * 6x6 footprint touches).  Reports the tile count, the entry count and
+ * checksum = sum_i id_i * (i mod 1000003 + 1). */
+int cpct_debug_bins(const cpct_geom* g, int which, int* n_tiles, int* n_entries, int64_t* checksum);
+
+/* Copy the sample ids (j << 16 | k) of one tile's bin into ids (capacity
+ * cap).  Returns the bin length (may exceed cap) or a negative status. */
+int cpct_debug_bin_tile(const cpct_geom* g, int which, int tile, uint32_t* ids, int cap);
+
+/* The split of a sample coordinate u = k (hi + lo) into floor and fraction,
+ * with the same float32 operations as the kernels. */
+int cpct_debug_split(float k, float hi, float lo, int* fl, float* z);
+
+/* Copy a plan's FP64 kernel-approximation coefficients (6 taps x 10
+ * monomial coefficients in s = 2 frac(u) - 1) and its float32 deapodization
+ * vector (N) to host buffers; either pointer may be NULL.  Synchronous. */
+int cpct_debug_tables(cpct_plan* plan, double* h_poly64, float* h_deapod);
+
+/* ---- profiling ---------------------------------------------------------- */
+
+/* Kernel ids: 0 k_fwd_col, 1 k_fwd_row, 2 k_fwd_interp, 3 k_fwd_ray,
+ * 4 k_adj_ray, 5 k_adj_spread, 6 k_adj_reduce, 7 k_adj_row, 8 k_adj_col. */
+#define CPCT_NUM_KERNELS 9
+
+/* Bracket every later launch of the kernels whose bit (1 << id) is set in
+ * `mask` with a CUDA event pair on its launch stream (0 disables). */
+int cpct_profile_enable(cpct_plan* plan, unsigned mask);
+
+/* Synchronize on the recorded events and return, per kernel id, the summed
+ * device milliseconds and the launch count since the previous read
+ * (arrays of CPCT_NUM_KERNELS entries). */
+int cpct_profile_read(cpct_plan* plan, double* total_ms, long long* launches);
+
+/* Name of kernel id `kid` (static string). */
+const char* cpct_kernel_name(int kid);
+
+/* Number of kernels the plan's operators have launched (optionally reset). */
+long long cpct_launch_count(cpct_plan* plan, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPCT_H_ */

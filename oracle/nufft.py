@@ -285,11 +285,14 @@ def grid_interp(F: np.ndarray, geo: GridGeometry, rays=None) -> np.ndarray:
     return out
 
 
-def grid_spread(Pt: np.ndarray, geo: GridGeometry) -> np.ndarray:
-    """Adjoint of step 3: Yh[b mod G, a mod G] += g(u - a) g(v - b) Pt[j,k]."""
+def grid_spread(Pt: np.ndarray, geo: GridGeometry, rays=None) -> np.ndarray:
+    """Adjoint of step 3: Yh[b mod G, a mod G] += g(u - a) g(v - b) Pt[j,k].
+
+    With ``rays`` only those rays' samples are spread (Pt holds just them).
+    """
     G = geo.grid
-    a, wa = geo.taps(geo.u)
-    b, wb = geo.taps(geo.v)
+    a, wa = geo.taps(geo.u if rays is None else geo.u[rays])
+    b, wb = geo.taps(geo.v if rays is None else geo.v[rays])
     acc_re = np.zeros(G * G)
     acc_im = np.zeros(G * G)
     for ib in range(b.shape[-1]):

@@ -1,0 +1,234 @@
+"""Thin ctypes binding of libcpct (include/cpct.h).
+
+Argument marshalling only: every step of the operators and of the solver runs
+in the CUDA library.  PyTorch provides device memory and the current stream.
+There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+LIB_PATH = os.path.join(_PKG, "_lib", "libcpct.so")
+HEADER = os.path.join(_ROOT, "include", "cpct.h")
+
+_lib = None
+
+STATUS = {
+    0: "CPCT_OK", -1: "CPCT_EINVAL", -2: "CPCT_ENOMEM", -3: "CPCT_ECUDA", -4: "CPCT_ETIMEOUT",
+    -5: "CPCT_ENONFINITE", -6: "CPCT_ENOTCONV", -7: "CPCT_EUNSUPPORTED",
+}
+
+PLAN_FAIL_ALLOC = 0x1000
+NUM_KERNELS = 9
+
+
+def kernel_name(kid):
+    return lib().cpct_kernel_name(int(kid)).decode()
+
+
+class CpctError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int), ("n_det", ctypes.c_int), ("n_views", ctypes.c_int),
+        ("angles", ctypes.POINTER(ctypes.c_double)), ("kb_width", ctypes.c_int),
+        ("oversamp", ctypes.c_double), ("flags", ctypes.c_int),
+    ]
+
+
+def lib():
+    """Load libcpct.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, f = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        L.cpct_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Geom), vp]
+        L.cpct_plan_destroy.argtypes = [vp]
+        L.cpct_plan_sync.argtypes = [vp, vp]
+        L.cpct_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                     ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t)]
+        for name in ("radon_fwd", "radon_adj", "radon_fwd_host", "radon_adj_host"):
+            getattr(L, name).argtypes = [vp, vp, vp, vp]
+        L.cpct_strerror.restype = ctypes.c_char_p
+        L.cpct_strerror.argtypes = [i]
+        L.cpct_debug_bins.argtypes = [ctypes.POINTER(Geom), i, ctypes.POINTER(i), ctypes.POINTER(i),
+                                      ctypes.POINTER(ctypes.c_int64)]
+        L.cpct_debug_bin_tile.argtypes = [ctypes.POINTER(Geom), i, i, vp, i]
+        L.cpct_debug_split.argtypes = [f, f, f, ctypes.POINTER(i), ctypes.POINTER(f)]
+        L.cpct_debug_tables.argtypes = [vp, vp, vp]
+        L.cpct_profile_enable.argtypes = [vp, ctypes.c_uint]
+        L.cpct_profile_read.argtypes = [vp, vp, vp]
+        L.cpct_kernel_name.restype = ctypes.c_char_p
+        L.cpct_kernel_name.argtypes = [i]
+        L.cpct_launch_count.restype = ctypes.c_longlong
+        L.cpct_launch_count.argtypes = [vp, i]
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions declared in include/cpct.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)))
+
+
+def check(status, what):
+    if status != 0:
+        raise CpctError(status, what)
+
+
+def make_geom(n, n_det, n_views, angles=None, flags=0):
+    g = Geom()
+    g.n, g.n_det, g.n_views = int(n), int(n_det), int(n_views)
+    g.kb_width, g.oversamp, g.flags = 6, 2.0, int(flags)
+    keep = None
+    if angles is not None:
+        keep = np.ascontiguousarray(angles, dtype=np.float64)
+        g.angles = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return g, keep
+
+
+def _stream(torch, stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, shape, torch):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Geometry plan of one slice: N x N image, M views x Ns detector bins."""
+
+    def __init__(self, n, n_det=None, n_views=180, angles=None, flags=0, stream=None):
+        import torch
+        self._torch = torch
+        n_det = n if n_det is None else n_det
+        g, self._angles = make_geom(n, n_det, n_views, angles, flags)
+        h = ctypes.c_void_p()
+        check(lib().cpct_plan_create(ctypes.byref(h), ctypes.byref(g), _stream(torch, stream)), "cpct_plan_create")
+        self._h = h
+        self.n, self.n_det, self.n_views = n, n_det, n_views
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().cpct_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n, ns, m, G = (ctypes.c_int() for _ in range(4))
+        b = ctypes.c_size_t()
+        check(lib().cpct_plan_info(self._h, ctypes.byref(n), ctypes.byref(ns), ctypes.byref(m), ctypes.byref(G),
+                                   ctypes.byref(b)), "cpct_plan_info")
+        return dict(n=n.value, n_det=ns.value, n_views=m.value, grid=G.value, device_bytes=b.value)
+
+    def sync(self, stream=None):
+        check(lib().cpct_plan_sync(self._h, _stream(self._torch, stream)), "cpct_plan_sync")
+
+    def fwd(self, img, out=None, stream=None):
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.n_views, self.n_det), device=img.device, dtype=torch.float32)
+        check(lib().radon_fwd(self._h, _dev_ptr(img, (self.n, self.n), torch),
+                              _dev_ptr(out, (self.n_views, self.n_det), torch), _stream(torch, stream)), "radon_fwd")
+        return out
+
+    def adj(self, sino, out=None, stream=None):
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.n, self.n), device=sino.device, dtype=torch.float32)
+        check(lib().radon_adj(self._h, _dev_ptr(sino, (self.n_views, self.n_det), torch),
+                              _dev_ptr(out, (self.n, self.n), torch), _stream(torch, stream)), "radon_adj")
+        return out
+
+    def fwd_host(self, img: np.ndarray, out: np.ndarray | None = None, stream=None):
+        img = np.ascontiguousarray(img, dtype=np.float32)
+        if out is None:
+            out = np.empty((self.n_views, self.n_det), dtype=np.float32)
+        check(lib().radon_fwd_host(self._h, img.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                                   _stream(self._torch, stream)), "radon_fwd_host")
+        return out
+
+    def adj_host(self, sino: np.ndarray, out: np.ndarray | None = None, stream=None):
+        sino = np.ascontiguousarray(sino, dtype=np.float32)
+        if out is None:
+            out = np.empty((self.n, self.n), dtype=np.float32)
+        check(lib().radon_adj_host(self._h, sino.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                                   _stream(self._torch, stream)), "radon_adj_host")
+        return out
+
+    def profile_enable(self, mask=0x1FF):
+        check(lib().cpct_profile_enable(self._h, ctypes.c_uint(mask)), "cpct_profile_enable")
+
+    def profile_read(self):
+        ms = np.zeros(NUM_KERNELS, dtype=np.float64)
+        cnt = np.zeros(NUM_KERNELS, dtype=np.int64)
+        check(lib().cpct_profile_read(self._h, ms.ctypes.data_as(ctypes.c_void_p), cnt.ctypes.data_as(ctypes.c_void_p)),
+              "cpct_profile_read")
+        return {kernel_name(k): (float(ms[k]), int(cnt[k])) for k in range(NUM_KERNELS) if cnt[k] > 0}
+
+    def launch_count(self, reset=False):
+        return int(lib().cpct_launch_count(self._h, 1 if reset else 0))
+
+    def debug_tables(self):
+        poly = np.zeros((6, 10), dtype=np.float64)
+        dp = np.zeros(self.n, dtype=np.float32)
+        check(lib().cpct_debug_tables(self._h, poly.ctypes.data_as(ctypes.c_void_p), dp.ctypes.data_as(ctypes.c_void_p)),
+              "cpct_debug_tables")
+        return poly, dp
+
+
+def debug_bins(n, n_det, n_views, which, angles=None):
+    """Host-side bin statistics (no GPU needed): (tiles, entries, checksum)."""
+    g, _keep = make_geom(n, n_det, n_views, angles)
+    t, e, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    check(lib().cpct_debug_bins(ctypes.byref(g), int(which), ctypes.byref(t), ctypes.byref(e), ctypes.byref(c)),
+          "cpct_debug_bins")
+    return t.value, e.value, c.value
+
+
+def debug_bin_tile(n, n_det, n_views, which, tile, cap=1 << 20, angles=None):
+    g, _keep = make_geom(n, n_det, n_views, angles)
+    buf = np.zeros(cap, dtype=np.uint32)
+    cnt = lib().cpct_debug_bin_tile(ctypes.byref(g), int(which), int(tile), buf.ctypes.data_as(ctypes.c_void_p), cap)
+    if cnt < 0:
+        raise CpctError(cnt, "cpct_debug_bin_tile")
+    return buf[:min(cnt, cap)].copy()
+
+
+def debug_split(k, hi, lo):
+    fl, z = ctypes.c_int(), ctypes.c_float()
+    lib().cpct_debug_split(ctypes.c_float(k), ctypes.c_float(hi), ctypes.c_float(lo), ctypes.byref(fl), ctypes.byref(z))
+    return fl.value, z.value

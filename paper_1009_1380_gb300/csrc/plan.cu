@@ -1,0 +1,500 @@
+// Plan construction: geometry, Kaiser-Bessel kernel approximation and
+// deapodization (built on the device in FP64), FFT twiddle tables, and the
+// tile bin lists of the polar samples.
+//
+// Gridding (section "fast radon transform") convolves the irregular polar
+// samples with a kernel on the regular grid.  The paper divides the sample
+// plane into bins (one thread block per bin) chosen by a quadtree on the cost
+// samples x grid points; here the bins are fixed 32x32 grid tiles and every
+// bin whose sample list is longer than a cap is split into several work items
+// (ordered longest first), which balances the load around the origin where all
+// rays meet.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kPolyDeg = 9;            // Chebyshev interpolation degree per tap
+constexpr int kFwdItemMax = 1024;      // samples per forward gather work item
+constexpr int kAdjItemMax = 512;       // entries per adjoint spread work item
+
+// ---------------------------------------------------------------------------
+// FP64 device builders (kernel table, deapodization, twiddles)
+// ---------------------------------------------------------------------------
+// I0(x) = sum_m (x^2/4)^m / (m!)^2  (all terms positive: no cancellation)
+__device__ double i0_series(double x) {
+  const double q = 0.25 * x * x;
+  double term = 1.0, sum = 1.0;
+  for (int m = 1; m < 400; ++m) {
+    term *= q / ((double)m * (double)m);
+    sum += term;
+    if (term < 1e-18 * sum) break;
+  }
+  return sum;
+}
+
+// g(t) = I0(beta sqrt(1 - (2t/W)^2)) / I0(beta), |t| < W/2
+__device__ double kb_g(double t, double beta, double W) {
+  const double a = 2.0 * t / W;
+  const double w = 1.0 - a * a;
+  if (w <= 0.0) return 0.0;
+  return i0_series(beta * sqrt(w)) / i0_series(beta);
+}
+
+// One thread per tap i: Chebyshev interpolation of w_i(s) = g(z + 2 - i),
+// z = (s+1)/2, at the kPolyDeg+1 Chebyshev nodes, converted to monomials in s.
+__global__ void k_build_poly(double* __restrict__ out, double beta, double W) {
+  const int i = threadIdx.x;
+  if (i >= CPCT_W) return;
+  constexpr int n = kPolyDeg + 1;
+  double f[n], c[n];
+  for (int mm = 0; mm < n; ++mm) {
+    const double s = cospi((mm + 0.5) / n);
+    f[mm] = kb_g(0.5 * (s + 1.0) + 2.0 - i, beta, W);
+  }
+  for (int k = 0; k < n; ++k) {
+    double acc = 0.0;
+    for (int mm = 0; mm < n; ++mm) acc += f[mm] * cospi(k * (mm + 0.5) / n);
+    c[k] = (k == 0 ? 1.0 : 2.0) * acc / n;
+  }
+  // T_0 = 1, T_1 = s, T_{k+1} = 2 s T_k - T_{k-1}
+  double Tm[n], T0[n], T1[n], mono[n];
+  for (int d = 0; d < n; ++d) { T0[d] = 0.0; T1[d] = 0.0; mono[d] = 0.0; Tm[d] = 0.0; }
+  T0[0] = 1.0;
+  T1[1] = 1.0;
+  mono[0] += c[0];
+  for (int d = 0; d < n; ++d) mono[d] += c[1] * T1[d];
+  for (int k = 2; k < n; ++k) {
+    for (int d = 0; d < n; ++d) Tm[d] = (d > 0 ? 2.0 * T1[d - 1] : 0.0) - T0[d];
+    for (int d = 0; d < n; ++d) { T0[d] = T1[d]; T1[d] = Tm[d]; mono[d] += c[k] * Tm[d]; }
+  }
+  for (int d = 0; d < n; ++d) out[i * n + d] = mono[d];
+}
+
+// c[q] = 1 / ghat((q - N/2)/G),  ghat(xi) = (W/I0(beta)) sinh(z)/z,
+// z = sqrt(beta^2 - (pi W xi)^2)
+__global__ void k_build_deapod(float* __restrict__ out, int n, int G, double beta, double W) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double xi = (double)(q - n / 2) / (double)G;
+  const double pw = 3.14159265358979323846 * W * xi;
+  const double z = sqrt(beta * beta - pw * pw);
+  const double ghat = W / i0_series(beta) * sinh(z) / z;
+  out[q] = (float)(1.0 / ghat);
+}
+
+// twiddles of pass (offset, L, R): entry (m-1)*L + j = exp(-2 pi i m j / (L R))
+__global__ void k_build_twiddles(float2* __restrict__ tw, int offset, int L, int R) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (R - 1) * L) return;
+  const int m = idx / L + 1, j = idx % L;
+  double s, c;
+  sincospi(-2.0 * (double)m * (double)j / ((double)L * R), &s, &c);
+  tw[offset + idx] = make_float2((float)c, (float)s);
+}
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// host mirror of split_coord (identical IEEE single-precision operations)
+void host_split(float k, float hi, float lo, int* fl_out, float* z) {
+  float p = k * hi;
+  float e = std::fmaf(k, hi, -p);
+  float corr = std::fmaf(k, lo, e);
+  float fl = std::floor(p);
+  float zz = (p - fl) + corr;
+  if (zz < 0.f) {
+    float t = zz + 1.f;
+    if (t < 1.f) { zz = t; fl = fl - 1.f; } else { zz = 0.f; }
+  } else if (zz >= 1.f) {
+    zz = zz - 1.f;
+    fl = fl + 1.f;
+  }
+  *fl_out = (int)fl;
+  *z = zz;
+}
+
+struct Alloc {
+  cpct_plan* p;
+  bool fail_next;
+  int operator()(void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (fail_next) { fail_next = false; return CPCT_ENOMEM; }
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) { *ptr = nullptr; return CPCT_ENOMEM; }
+    p->device_bytes += bytes;
+    return CPCT_OK;
+  }
+};
+
+template <class T>
+int upload(Alloc& al, T** dst, const std::vector<T>& src, cudaStream_t s) {
+  int rc = al((void**)dst, src.size() * sizeof(T));
+  if (rc) return rc;
+  if (!src.empty())
+    CPCT_CUDA_TRY(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return CPCT_OK;
+}
+
+void free_plan(cpct_plan* p) {
+  if (!p) return;
+  cpct_prof_free(p);
+  void* ptrs[] = {p->d_poly64, p->d_ray, p->d_deapod, p->d_twG, p->d_twNs, p->d_Hx, p->d_Ax, p->d_H1,
+                  p->d_Q, p->d_fwd_items, p->d_fwd_ids, p->d_adj_items, p->d_adj_ids, p->d_partials,
+                  p->d_split, p->d_stage_img, p->d_stage_sino, p->d_err};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// bin lists (exported for host-side tests: no GPU needed)
+// ---------------------------------------------------------------------------
+extern "C" int cpct_debug_bins(const cpct_geom* g, int which, int* n_tiles, int* n_entries, int64_t* checksum);
+
+namespace cpct_detail {
+
+struct Bins {
+  int tiles_x, tiles_y;
+  std::vector<int> ptr;          // tiles + 1
+  std::vector<uint32_t> ids;     // grouped by tile, increasing id inside a tile
+};
+
+struct RayTab {
+  std::vector<float4> ray;
+};
+
+void make_rays(int n, int ns, int m, const double* angles, double scale, std::vector<float4>& ray) {
+  ray.resize(m);
+  for (int j = 0; j < m; ++j) {
+    const double th = angles ? angles[j] : M_PI * (double)j / (double)m;
+    const double c = scale * std::cos(th), s = scale * std::sin(th);
+    const float ch = (float)c, sh = (float)s;
+    ray[j] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
+  }
+}
+
+// forward bins: every sample (j, k >= 0) lands in the tile of its footprint's
+// first grid point (a0 = floor(u)-2 mod G, buffer row floor(v)); adjoint bins:
+// every tile of the extended spectrum that its 6x6 footprint touches.
+void build_bins(int n, int ns, int m, int G, const std::vector<float4>& ray, Bins& fwd, Bins& adj) {
+  const int K = ns / 2;
+  const int T = CPCT_TILE;
+  fwd.tiles_x = G / T;
+  fwd.tiles_y = n / T + 1;
+  adj.tiles_x = G / T + 1;
+  adj.tiles_y = (n + 5) / T + 1;
+  const int nf = fwd.tiles_x * fwd.tiles_y, na = adj.tiles_x * adj.tiles_y;
+  std::vector<int> cf(nf + 1, 0), ca(na + 1, 0);
+  std::vector<int> fa0((size_t)m * (K + 1)), frb((size_t)m * (K + 1));
+  for (int j = 0; j < m; ++j) {
+    for (int k = 0; k <= K; ++k) {
+      int fu, fv;
+      float zu, zv;
+      host_split((float)k, ray[j].x, ray[j].y, &fu, &zu);
+      host_split((float)k, ray[j].z, ray[j].w, &fv, &zv);
+      const int a0 = (fu - 2) & (G - 1);
+      const int rb0 = fv;  // buffer row of the first tap: (floor(v) - 2) + 2
+      const size_t sidx = (size_t)j * (K + 1) + k;
+      fa0[sidx] = a0;
+      frb[sidx] = rb0;
+      cf[(rb0 / T) * fwd.tiles_x + a0 / T + 1]++;
+      for (int ty = rb0 / T; ty <= (rb0 + CPCT_HALO) / T; ++ty)
+        for (int tx = a0 / T; tx <= (a0 + CPCT_HALO) / T; ++tx) ca[ty * adj.tiles_x + tx + 1]++;
+    }
+  }
+  for (int i = 0; i < nf; ++i) cf[i + 1] += cf[i];
+  for (int i = 0; i < na; ++i) ca[i + 1] += ca[i];
+  fwd.ptr = cf;
+  adj.ptr = ca;
+  fwd.ids.resize(cf[nf]);
+  adj.ids.resize(ca[na]);
+  std::vector<int> pf(cf.begin(), cf.end() - 1), pa(ca.begin(), ca.end() - 1);
+  for (int j = 0; j < m; ++j) {
+    for (int k = 0; k <= K; ++k) {
+      const size_t sidx = (size_t)j * (K + 1) + k;
+      const int a0 = fa0[sidx], rb0 = frb[sidx];
+      const uint32_t id = ((uint32_t)j << 16) | (uint32_t)k;
+      fwd.ids[pf[(rb0 / T) * fwd.tiles_x + a0 / T]++] = id;
+      for (int ty = rb0 / T; ty <= (rb0 + CPCT_HALO) / T; ++ty)
+        for (int tx = a0 / T; tx <= (a0 + CPCT_HALO) / T; ++tx) adj.ids[pa[ty * adj.tiles_x + tx]++] = id;
+    }
+  }
+}
+
+// split bins into work items of at most `cap` entries, longest first
+void make_items(const Bins& b, int cap, bool slots, std::vector<int4>& items, std::vector<int4>& split,
+                int* n_slots) {
+  const int nt = (int)b.ptr.size() - 1;
+  items.clear();
+  split.clear();
+  int slot = 0;
+  for (int t = 0; t < nt; ++t) {
+    const int beg = b.ptr[t], end = b.ptr[t + 1];
+    if (end == beg) continue;
+    const int pieces = (end - beg + cap - 1) / cap;
+    if (pieces == 1 || !slots) {
+      for (int q = 0; q < pieces; ++q)
+        items.push_back(make_int4(t, beg + q * cap, std::min(end, beg + (q + 1) * cap), -1));
+    } else {
+      split.push_back(make_int4(t, slot, pieces, 0));
+      for (int q = 0; q < pieces; ++q)
+        items.push_back(make_int4(t, beg + q * cap, std::min(end, beg + (q + 1) * cap), slot + q));
+      slot += pieces;
+    }
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const int4& a, const int4& c) { return (a.z - a.y) > (c.z - c.y); });
+  if (n_slots) *n_slots = slot;
+}
+
+}  // namespace cpct_detail
+
+// which = 0: forward bins, 1: adjoint bins.  Reports the number of tiles, the
+// number of entries and a checksum sum(id * (position + 1)) of the id list.
+extern "C" int cpct_debug_bins(const cpct_geom* g, int which, int* n_tiles, int* n_entries, int64_t* checksum) {
+  if (!g || g->n < 32 || !is_pow2(g->n) || !is_pow2(g->n_det) || g->n_det < g->n || g->n_views < 1)
+    return CPCT_EINVAL;
+  const int G = 2 * g->n;
+  std::vector<float4> ray;
+  cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
+  cpct_detail::Bins f, a;
+  cpct_detail::build_bins(g->n, g->n_det, g->n_views, G, ray, f, a);
+  const cpct_detail::Bins& b = which ? a : f;
+  if (n_tiles) *n_tiles = (int)b.ptr.size() - 1;
+  if (n_entries) *n_entries = (int)b.ids.size();
+  if (checksum) {
+    int64_t cs = 0;
+    for (size_t i = 0; i < b.ids.size(); ++i) cs += (int64_t)b.ids[i] * (int64_t)(i % 1000003 + 1);
+    *checksum = cs;
+  }
+  return CPCT_OK;
+}
+
+// Copy the bin list of tile `tile` (which = 0 forward, 1 adjoint) into ids
+// (capacity cap); returns the number of entries or a negative status.
+extern "C" int cpct_debug_bin_tile(const cpct_geom* g, int which, int tile, uint32_t* ids, int cap) {
+  if (!g || g->n < 32 || !is_pow2(g->n) || !is_pow2(g->n_det) || g->n_det < g->n || g->n_views < 1)
+    return CPCT_EINVAL;
+  const int G = 2 * g->n;
+  std::vector<float4> ray;
+  cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
+  cpct_detail::Bins f, a;
+  cpct_detail::build_bins(g->n, g->n_det, g->n_views, G, ray, f, a);
+  const cpct_detail::Bins& b = which ? a : f;
+  if (tile < 0 || tile >= (int)b.ptr.size() - 1) return CPCT_EINVAL;
+  const int cnt = b.ptr[tile + 1] - b.ptr[tile];
+  for (int i = 0; i < cnt && i < cap; ++i) ids[i] = b.ids[b.ptr[tile] + i];
+  return cnt;
+}
+
+// Sample coordinate split exactly as the kernels do it (host mirror).
+extern "C" int cpct_debug_split(float k, float hi, float lo, int* fl, float* z) {
+  host_split(k, hi, lo, fl, z);
+  return CPCT_OK;
+}
+
+extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_t stream) {
+  if (!out) return CPCT_EINVAL;
+  *out = nullptr;
+  if (!g) return CPCT_EINVAL;
+  const int n = g->n, ns = g->n_det, m = g->n_views;
+  const int W = g->kb_width ? g->kb_width : 6;
+  const double sigma = g->oversamp != 0.0 ? g->oversamp : 2.0;
+  if (W != 6 || sigma != 2.0) return CPCT_EINVAL;
+  if (!is_pow2(n) || n < 32 || n > 2048) return CPCT_EINVAL;
+  if (!is_pow2(ns) || ns < n || ns > 4096) return CPCT_EINVAL;
+  if (m < 1 || m > 32768) return CPCT_EINVAL;
+  if (g->angles) {
+    for (int j = 0; j < m; ++j)
+      if (!(g->angles[j] >= 0.0 && g->angles[j] < M_PI)) return CPCT_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CPCT_ECUDA;
+
+  cpct_plan* p = new (std::nothrow) cpct_plan;
+  if (!p) return CPCT_ENOMEM;
+  std::memset(p, 0, sizeof(*p));
+  p->n = n;
+  p->ns = ns;
+  p->m = m;
+  p->G = 2 * n;
+  p->K = ns / 2;
+  p->logn = ilog2(n);
+  p->logG = ilog2(p->G);
+  p->logNs = ilog2(ns);
+  p->ldh = p->G + 8;
+  p->ext_rows = n + 8;
+  p->ldq = p->K + 2;
+  p->flags = g->flags;
+  p->scale = (double)p->G / (double)ns;
+  Alloc al{p, (g->flags & CPCT_PLAN_FAIL_ALLOC) != 0};
+  int rc = CPCT_OK;
+#define TRY(x)                         \
+  do {                                 \
+    rc = (x);                          \
+    if (rc != CPCT_OK) goto fail;      \
+  } while (0)
+#define TRYC(x)                                      \
+  do {                                               \
+    if ((x) != cudaSuccess) { rc = CPCT_ECUDA; goto fail; } \
+  } while (0)
+
+  {
+    int rca = cpct_radon_setup_attributes(p->logG, p->logNs);
+    if (rca != CPCT_OK) { rc = rca; goto fail; }
+    // geometry
+    std::vector<float4> ray;
+    cpct_detail::make_rays(n, ns, m, g->angles, p->scale, ray);
+    TRY(upload(al, &p->d_ray, ray, stream));
+    // kernel approximation, deapodization, twiddles (FP64 on the device)
+    const double beta = M_PI * std::sqrt((W / sigma) * (W / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8);
+    TRY(al((void**)&p->d_poly64, sizeof(double) * CPCT_W * (kPolyDeg + 1)));
+    k_build_poly<<<1, 32, 0, stream>>>(p->d_poly64, beta, (double)W);
+    TRY(al((void**)&p->d_deapod, sizeof(float) * n));
+    k_build_deapod<<<(n + 127) / 128, 128, 0, stream>>>(p->d_deapod, n, p->G, beta, (double)W);
+    TRY(al((void**)&p->d_twG, sizeof(float2) * std::max(1, fft_tw_size(p->logG))));
+    TRY(al((void**)&p->d_twNs, sizeof(float2) * std::max(1, fft_tw_size(p->logNs))));
+    for (int which = 0; which < 2; ++which) {
+      const int lg = which ? p->logNs : p->logG;
+      float2* tw = which ? p->d_twNs : p->d_twG;
+      for (int pp = 1; pp < fft_npass(lg); ++pp) {
+        const int L = 1 << fft_ll(pp), R = 1 << fft_lr(lg, pp);
+        const int cnt = (R - 1) * L;
+        k_build_twiddles<<<(cnt + 255) / 256, 256, 0, stream>>>(tw, fft_tw_offset(lg, pp), L, R);
+      }
+    }
+    TRYC(cudaGetLastError());
+    // workspaces
+    const size_t hx_bytes = sizeof(float2) * (size_t)p->ext_rows * p->ldh;
+    TRY(al((void**)&p->d_Hx, hx_bytes));
+    TRY(al((void**)&p->d_Ax, hx_bytes));
+    TRY(al((void**)&p->d_H1, sizeof(float2) * (size_t)(n + 1) * n));
+    TRY(al((void**)&p->d_Q, sizeof(float2) * (size_t)m * p->ldq));
+    TRY(al((void**)&p->d_err, sizeof(int)));
+    TRYC(cudaMemsetAsync(p->d_Hx, 0, hx_bytes, stream));
+    TRYC(cudaMemsetAsync(p->d_Ax, 0, hx_bytes, stream));
+    TRYC(cudaMemsetAsync(p->d_Q, 0, sizeof(float2) * (size_t)m * p->ldq, stream));
+    TRYC(cudaMemsetAsync(p->d_err, 0, sizeof(int), stream));
+    // bins
+    cpct_detail::Bins fb, ab;
+    cpct_detail::build_bins(n, ns, m, p->G, ray, fb, ab);
+    p->tiles_x_fwd = fb.tiles_x;
+    p->tiles_y_fwd = fb.tiles_y;
+    p->tiles_x_adj = ab.tiles_x;
+    p->tiles_y_adj = ab.tiles_y;
+    std::vector<int4> fitems, aitems, fsplit, asplit;
+    cpct_detail::make_items(fb, kFwdItemMax, false, fitems, fsplit, nullptr);
+    cpct_detail::make_items(ab, kAdjItemMax, true, aitems, asplit, &p->n_slots);
+    p->n_fwd_items = (int)fitems.size();
+    p->n_adj_items = (int)aitems.size();
+    p->n_split = (int)asplit.size();
+    TRY(upload(al, &p->d_fwd_items, fitems, stream));
+    TRY(upload(al, &p->d_fwd_ids, fb.ids, stream));
+    TRY(upload(al, &p->d_adj_items, aitems, stream));
+    TRY(upload(al, &p->d_adj_ids, ab.ids, stream));
+    TRY(upload(al, &p->d_split, asplit, stream));
+    TRY(al((void**)&p->d_partials, sizeof(float2) * (size_t)std::max(1, p->n_slots) * CPCT_TILE * CPCT_TILE));
+    // TMA descriptor of the forward extended spectrum (viewed as float32 pairs)
+    {
+      EncodeTiledFn enc = get_encode_fn();
+      if (!enc) { rc = CPCT_EUNSUPPORTED; goto fail; }
+      cuuint64_t dims[2] = {(cuuint64_t)2 * p->ldh, (cuuint64_t)p->ext_rows};
+      cuuint64_t strides[1] = {(cuuint64_t)p->ldh * sizeof(float2)};
+      cuuint32_t box[2] = {2 * (CPCT_TILE + CPCT_HALO + 1), CPCT_TILE + CPCT_HALO};
+      cuuint32_t estr[2] = {1, 1};
+      CUresult cr = enc(&p->tmap_Hx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->d_Hx, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (cr != CUDA_SUCCESS) { rc = CPCT_ECUDA; goto fail; }
+    }
+    // FP32 copy of the even/odd polynomial parts
+    double poly[CPCT_W * (kPolyDeg + 1)];
+    TRYC(cudaMemcpyAsync(poly, p->d_poly64, sizeof(poly), cudaMemcpyDeviceToHost, stream));
+    TRYC(cudaStreamSynchronize(stream));
+    for (int i = 0; i < 3; ++i)
+      for (int d = 0; d < CPCT_NPOLY; ++d) {
+        p->poly.e[i][d] = (float)poly[i * (kPolyDeg + 1) + 2 * d];
+        p->poly.o[i][d] = (float)poly[i * (kPolyDeg + 1) + 2 * d + 1];
+      }
+    TRYC(cudaGetLastError());
+  }
+#undef TRY
+#undef TRYC
+  *out = p;
+  return CPCT_OK;
+fail:
+  cudaStreamSynchronize(stream);
+  free_plan(p);
+  return rc;
+}
+
+extern "C" int cpct_plan_destroy(cpct_plan* plan) {
+  if (!plan) return CPCT_OK;
+  cudaDeviceSynchronize();
+  free_plan(plan);
+  return CPCT_OK;
+}
+
+extern "C" int cpct_plan_info(const cpct_plan* p, int* n, int* n_det, int* n_views, int* grid, size_t* bytes) {
+  if (!p) return CPCT_EINVAL;
+  if (n) *n = p->n;
+  if (n_det) *n_det = p->ns;
+  if (n_views) *n_views = p->m;
+  if (grid) *grid = p->G;
+  if (bytes) *bytes = p->device_bytes;
+  return CPCT_OK;
+}
+
+extern "C" int cpct_plan_sync(cpct_plan* p, cudaStream_t stream) {
+  if (!p) return CPCT_EINVAL;
+  int err = 0;
+  CPCT_CUDA_TRY(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  CPCT_CUDA_TRY(cudaStreamSynchronize(stream));
+  if (err) {
+    CPCT_CUDA_TRY(cudaMemsetAsync(p->d_err, 0, sizeof(int), stream));
+    CPCT_CUDA_TRY(cudaStreamSynchronize(stream));
+    return (err & CPCT_ERR_TIMEOUT) ? CPCT_ETIMEOUT : CPCT_ECUDA;
+  }
+  return CPCT_OK;
+}
+
+// FP64 polynomial coefficients [6][10] (monomials in s = 2z-1 per tap) and
+// the FP32 deapodization vector [N], copied to host buffers (either may be NULL).
+extern "C" int cpct_debug_tables(cpct_plan* p, double* h_poly64, float* h_deapod) {
+  if (!p) return CPCT_EINVAL;
+  if (h_poly64)
+    CPCT_CUDA_TRY(cudaMemcpy(h_poly64, p->d_poly64, sizeof(double) * CPCT_W * (kPolyDeg + 1), cudaMemcpyDeviceToHost));
+  if (h_deapod) CPCT_CUDA_TRY(cudaMemcpy(h_deapod, p->d_deapod, sizeof(float) * p->n, cudaMemcpyDeviceToHost));
+  return CPCT_OK;
+}

@@ -1,0 +1,619 @@
+// Fourier-slice Radon transform by gridding, and its exact adjoint
+// (section "fast radon transform").
+//
+// Forward  y = Re(A x)   (real image x -> real sinogram y):
+//   1. k_fwd_col   deapodize x[p,q] c(Y) c(X), place at (Y mod G), G-point FFT
+//                  of two real columns packed into one complex FFT, keep the
+//                  non-negative frequency rows b = 0..N        -> H1 (N+1) x N
+//   2. k_fwd_row   G-point FFT along x of every row b = 0..N, write the
+//                  extended half spectrum (Hermitian mirror rows, wrapped
+//                  columns)                                     -> Hx
+//   3. k_fwd_interp  polar samples k = 0..Ns/2 of every ray: 6x6 Kaiser-Bessel
+//                  interpolation; the 37x38 grid window of each 32x32 bin is
+//                  staged in shared memory by one TMA tensor copy -> Q
+//   4. k_fwd_ray   Hermitian completion + (-1)^k centring, Ns-point inverse
+//                  FFT of two rays packed into one complex FFT, 1/Ns -> y
+// Adjoint  x = Re(A^H w) is the transpose of these four real-linear maps,
+// applied in reverse order:
+//   5. k_adj_ray   Ns-point FFT of two packed sinogram rows, weights
+//                  (1, 2, ..., 2, 1) (-1)^k / Ns               -> Q~
+//   6. k_adj_spread  gridding as a deterministic gather: each 32x32 tile of
+//                  the extended spectrum owns its output; one warp walks the
+//                  tile's sample list in a fixed order and adds each sample's
+//                  36 taps (one tap per lane) into shared memory; no atomics
+//   7. k_adj_reduce  heavy tiles were split into several work items with
+//                  partial tiles; summed here in a fixed order  -> Ax
+//   8. k_adj_row   fold the extension (mirror rows, wrapped columns), G-point
+//                  inverse FFT along x, keep X = -N/2..N/2-1    -> H1
+//   9. k_adj_col   Hermitian-symmetrise the rows b = 0..N of two columns,
+//                  pack, G-point inverse FFT, crop Y, deapodize  -> x
+#include <algorithm>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+using cpct::fpad;
+using cpct::SmemFFT;
+
+namespace {
+
+constexpr int kE = 32;                 // FFT values per thread
+constexpr int kColFFTs = 4;            // packed column FFTs per CTA (8 columns)
+constexpr int kThreads = 256;          // threads of the row / ray FFT kernels
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+
+template <int LOG>
+constexpr int fft_threads() { return (1 << LOG) / kE; }
+template <int LOG>
+constexpr int rows_per_cta() { return kThreads / fft_threads<LOG>() > 0 ? kThreads / fft_threads<LOG>() : 1; }
+template <int LOG>
+constexpr size_t fft_smem(int nfft) { return (size_t)nfft * SmemFFT<LOG, kE, -1>::PADN * sizeof(float2); }
+
+// ---------------------------------------------------------------------------
+// 1. forward column transform
+// ---------------------------------------------------------------------------
+template <int LOGG>
+__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
+    k_fwd_col(const float* __restrict__ img, const float* __restrict__ dp, float2* __restrict__ H1,
+              const float2* __restrict__ tw, int N) {
+  using FFT = SmemFFT<LOGG, kE, -1>;
+  constexpr int G = 1 << LOGG;
+  extern __shared__ float2 sm[];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int q0 = blockIdx.x * (2 * kColFFTs);
+  // zero the padding half [N/2, G - N/2) of every FFT
+  for (int idx = tid; idx < kColFFTs * N; idx += nthr) {
+    const int f = idx / N, q = N / 2 + idx % N;
+    sm[f * FFT::PADN + fpad(q)] = make_float2(0.f, 0.f);
+  }
+  // deapodized columns: FFT f packs columns q0+2f (real part), q0+2f+1 (imag)
+  for (int idx = tid; idx < 2 * N; idx += nthr) {
+    const int p = idx >> 1, h = idx & 1;
+    const float4 v = *reinterpret_cast<const float4*>(img + (size_t)p * N + q0 + 4 * h);
+    const float4 d = *reinterpret_cast<const float4*>(dp + q0 + 4 * h);
+    const float cp = dp[p];
+    const int pos = (p - N / 2) & (G - 1);
+    sm[(2 * h) * FFT::PADN + fpad(pos)] = make_float2(v.x * cp * d.x, v.y * cp * d.y);
+    sm[(2 * h + 1) * FFT::PADN + fpad(pos)] = make_float2(v.z * cp * d.z, v.w * cp * d.w);
+  }
+  __syncthreads();
+  FFT::run(sm + (tid / FFT::T) * FFT::PADN, tw, tid % FFT::T);
+  // unpack the two real columns: C1 = (Z[b] + conj Z[G-b])/2, C2 = (Z[b] - conj Z[G-b])/(2i)
+  for (int idx = tid; idx < (N + 1) * kColFFTs; idx += nthr) {
+    const int b = idx / kColFFTs, f = idx % kColFFTs;
+    const float2 Z = sm[f * FFT::PADN + fpad(b)];
+    const float2 Zm = sm[f * FFT::PADN + fpad((G - b) & (G - 1))];
+    const float4 o = make_float4(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y), 0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
+    *reinterpret_cast<float4*>(H1 + (size_t)b * N + q0 + 2 * f) = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. forward row transform + extension
+// ---------------------------------------------------------------------------
+template <int LOGG>
+__global__ void __launch_bounds__(kThreads)
+    k_fwd_row(const float2* __restrict__ H1, float2* __restrict__ Hx, const float2* __restrict__ tw, int N, int ldh) {
+  using FFT = SmemFFT<LOGG, kE, -1>;
+  constexpr int G = 1 << LOGG, T = FFT::T, RPC = rows_per_cta<LOGG>();
+  extern __shared__ float2 sm[];
+  const int f = threadIdx.x / T, t = threadIdx.x % T;
+  float2* buf = sm + f * FFT::PADN;
+  const int b = blockIdx.x * RPC + f;
+  const bool valid = b <= N;
+  for (int q = t; q < N; q += T) {
+    buf[fpad(N / 2 + q)] = make_float2(0.f, 0.f);
+    const int pos = (q - N / 2) & (G - 1);
+    buf[fpad(pos)] = valid ? H1[(size_t)b * N + q] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  FFT::run(buf, tw, t);
+  if (!valid) return;
+  float2* dst = Hx + (size_t)(b + 2) * ldh;
+  for (int a = t; a < G + 6; a += T) dst[a] = buf[fpad(a & (G - 1))];
+  // Hermitian mirrors: ext row -b (b = 1, 2) and ext row G-b (b = N-3..N-1)
+  int mrow = -1;
+  if (b == 1 || b == 2) mrow = 2 - b;
+  else if (b >= N - 3 && b <= N - 1) mrow = (2 * N - b) + 2;
+  if (mrow >= 0) {
+    float2* md = Hx + (size_t)mrow * ldh;
+    for (int a = t; a < G + 6; a += T) md[a] = cconj(buf[fpad((-a) & (G - 1))]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. forward interpolation onto the polar grid (TMA-staged bins)
+// ---------------------------------------------------------------------------
+struct FwdInterpArgs {
+  const int4* items;
+  const uint32_t* ids;
+  const float4* ray;
+  const float2* Hx;
+  float2* Q;
+  int* err;
+  int G, ldq, ldh, tiles_x;
+  KBPoly poly;
+};
+
+constexpr int kWinR = CPCT_TILE + CPCT_HALO;      // 37 rows
+constexpr int kWinC = CPCT_TILE + CPCT_HALO + 1;  // 38 complex columns (304 B rows)
+
+__global__ void __launch_bounds__(256)
+    k_fwd_interp(const __grid_constant__ CUtensorMap tmap, const FwdInterpArgs a) {
+  __shared__ __align__(128) float2 win[kWinR * kWinC];
+  __shared__ __align__(8) uint64_t bar;
+  const int4 it = a.items[blockIdx.x];
+  const int C0 = (it.x % a.tiles_x) * CPCT_TILE, R0 = (it.x / a.tiles_x) * CPCT_TILE;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, (uint32_t)(kWinR * kWinC * sizeof(float2)));
+    tma_load_2d(win, &tmap, 2 * C0, R0, &bar);
+  }
+  if (!mbar_wait_bounded(&bar, 0, kWaitCycles)) {
+    if (threadIdx.x == 0) atomicOr(a.err, CPCT_ERR_TIMEOUT);
+    mbar_wait_bounded(&bar, 0, kWaitCycles / 4);  // let an in-flight copy land before exiting
+    return;
+  }
+  for (int idx = it.y + threadIdx.x; idx < it.z; idx += blockDim.x) {
+    const uint32_t id = a.ids[idx];
+    const int j = (int)(id >> 16), k = (int)(id & 0xffffu);
+    const float4 r = a.ray[j];
+    int fu, fv;
+    float zu, zv;
+    split_coord((float)k, r.x, r.y, fu, zu);
+    split_coord((float)k, r.z, r.w, fv, zv);
+    const int a0 = (fu - 2) & (a.G - 1);
+    float wu[CPCT_W], wv[CPCT_W];
+    kb_weights(a.poly, zu, wu);
+    kb_weights(a.poly, zv, wv);
+    const int ar = a0 - C0, br = fv - R0;
+    float2 acc = make_float2(0.f, 0.f);
+    if ((unsigned)ar < (unsigned)CPCT_TILE && (unsigned)br < (unsigned)CPCT_TILE) {
+#pragma unroll
+      for (int rr = 0; rr < CPCT_W; ++rr) {
+        const float2* row = win + (br + rr) * kWinC + ar;
+        float2 rs = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < CPCT_W; ++c) {
+          const float2 h = row[c];
+          rs.x = fmaf(wu[c], h.x, rs.x);
+          rs.y = fmaf(wu[c], h.y, rs.y);
+        }
+        acc.x = fmaf(wv[rr], rs.x, acc.x);
+        acc.y = fmaf(wv[rr], rs.y, acc.y);
+      }
+    } else {
+      // the sample is not in this bin (host/device coordinate mismatch):
+      // record it and read the footprint from global memory instead
+      atomicOr(a.err, CPCT_ERR_BIN);
+      for (int rr = 0; rr < CPCT_W; ++rr) {
+        const float2* row = a.Hx + (size_t)(fv + rr) * a.ldh + a0;
+        float2 rs = make_float2(0.f, 0.f);
+        for (int c = 0; c < CPCT_W; ++c) {
+          rs.x = fmaf(wu[c], row[c].x, rs.x);
+          rs.y = fmaf(wu[c], row[c].y, rs.y);
+        }
+        acc.x = fmaf(wv[rr], rs.x, acc.x);
+        acc.y = fmaf(wv[rr], rs.y, acc.y);
+      }
+    }
+    a.Q[(size_t)j * a.ldq + k] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. forward ray transform (c2r of the Hermitian-completed rays)
+// ---------------------------------------------------------------------------
+template <int LOGNS>
+__global__ void __launch_bounds__(kThreads)
+    k_fwd_ray(const float2* __restrict__ Q, float* __restrict__ sino, const float2* __restrict__ tw, int M, int ldq) {
+  using FFT = SmemFFT<LOGNS, kE, +1>;
+  constexpr int NS = 1 << LOGNS, T = FFT::T, PPC = rows_per_cta<LOGNS>(), K = NS / 2;
+  extern __shared__ float2 sm[];
+  const int f = threadIdx.x / T, t = threadIdx.x % T;
+  float2* buf = sm + f * FFT::PADN;
+  const int j1 = 2 * (blockIdx.x * PPC + f), j2 = j1 + 1;
+  const bool v1 = j1 < M, v2 = j2 < M;
+  for (int k = t; k < NS; k += T) {
+    const int kk = k <= K ? k : NS - k;
+    const float sg = (kk & 1) ? -1.f : 1.f;
+    float2 q1 = v1 ? Q[(size_t)j1 * ldq + kk] : make_float2(0.f, 0.f);
+    float2 q2 = v2 ? Q[(size_t)j2 * ldq + kk] : make_float2(0.f, 0.f);
+    q1 = cscale(q1, sg);
+    q2 = cscale(q2, sg);
+    if (kk == 0 || kk == K) { q1.y = 0.f; q2.y = 0.f; }
+    if (k > K) { q1.y = -q1.y; q2.y = -q2.y; }
+    buf[fpad(k)] = make_float2(q1.x - q2.y, q1.y + q2.x);
+  }
+  __syncthreads();
+  FFT::run(buf, tw, t);
+  const float inv = 1.f / (float)NS;
+  for (int s = t; s < NS; s += T) {
+    const float2 w = buf[fpad(s)];
+    if (v1) sino[(size_t)j1 * NS + s] = w.x * inv;
+    if (v2) sino[(size_t)j2 * NS + s] = w.y * inv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5. adjoint ray transform (transpose of step 4)
+// ---------------------------------------------------------------------------
+template <int LOGNS>
+__global__ void __launch_bounds__(kThreads)
+    k_adj_ray(const float* __restrict__ sino, float2* __restrict__ Q, const float2* __restrict__ tw, int M, int ldq) {
+  using FFT = SmemFFT<LOGNS, kE, -1>;
+  constexpr int NS = 1 << LOGNS, T = FFT::T, PPC = rows_per_cta<LOGNS>(), K = NS / 2;
+  extern __shared__ float2 sm[];
+  const int f = threadIdx.x / T, t = threadIdx.x % T;
+  float2* buf = sm + f * FFT::PADN;
+  const int j1 = 2 * (blockIdx.x * PPC + f), j2 = j1 + 1;
+  const bool v1 = j1 < M, v2 = j2 < M;
+  for (int s = t; s < NS; s += T)
+    buf[fpad(s)] = make_float2(v1 ? sino[(size_t)j1 * NS + s] : 0.f, v2 ? sino[(size_t)j2 * NS + s] : 0.f);
+  __syncthreads();
+  FFT::run(buf, tw, t);
+  const float inv = 1.f / (float)NS;
+  for (int k = t; k <= K; k += T) {
+    const float2 W = buf[fpad(k)];
+    const float2 Wm = buf[fpad((NS - k) & (NS - 1))];
+    float2 d1 = make_float2(0.5f * (W.x + Wm.x), 0.5f * (W.y - Wm.y));
+    float2 d2 = make_float2(0.5f * (W.y + Wm.y), -0.5f * (W.x - Wm.x));
+    float sc = ((k & 1) ? -inv : inv);
+    if (k == 0 || k == K) { d1.y = 0.f; d2.y = 0.f; } else { sc *= 2.f; }
+    if (v1) Q[(size_t)j1 * ldq + k] = cscale(d1, sc);
+    if (v2) Q[(size_t)j2 * ldq + k] = cscale(d2, sc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 6. adjoint spread: deterministic tile-owned gather (one warp per work item)
+// ---------------------------------------------------------------------------
+struct AdjSpreadArgs {
+  const int4* items;
+  const uint32_t* ids;
+  const float4* ray;
+  const float2* Qt;
+  float2* Ax;
+  float2* partials;
+  int G, ldq, ldh, tiles_x, ext_rows;
+  KBPoly poly;
+};
+
+constexpr int kAccLd = CPCT_TILE + 6;  // 38: taps of rows 0..4 hit 30 distinct banks
+constexpr int kStg = 20;               // staged words per sample
+
+__global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
+  __shared__ float acc_re[CPCT_TILE * kAccLd];
+  __shared__ float acc_im[CPCT_TILE * kAccLd];
+  __shared__ float stg[32 * kStg];
+  const int lane = threadIdx.x;
+  const int4 it = a.items[blockIdx.x];
+  const int TC = (it.x % a.tiles_x) * CPCT_TILE, TR = (it.x / a.tiles_x) * CPCT_TILE;
+  for (int i = lane; i < CPCT_TILE * kAccLd; i += 32) {
+    acc_re[i] = 0.f;
+    acc_im[i] = 0.f;
+  }
+  const int r1 = lane / 6, c1 = lane % 6;  // tap of lanes 0..29 (rows 0..4)
+  __syncwarp();
+  for (int base = it.y; base < it.z; base += 32) {
+    const int idx = base + lane;
+    if (idx < it.z) {
+      const uint32_t id = a.ids[idx];
+      const int j = (int)(id >> 16), k = (int)(id & 0xffffu);
+      const float4 r = a.ray[j];
+      int fu, fv;
+      float zu, zv;
+      split_coord((float)k, r.x, r.y, fu, zu);
+      split_coord((float)k, r.z, r.w, fv, zv);
+      const int a0 = (fu - 2) & (a.G - 1);
+      float wu[CPCT_W], wv[CPCT_W];
+      kb_weights(a.poly, zu, wu);
+      kb_weights(a.poly, zv, wv);
+      const float2 val = a.Qt[(size_t)j * a.ldq + k];
+      float* S = stg + lane * kStg;
+      S[0] = __int_as_float(a0 - TC);
+      S[1] = __int_as_float(fv - TR);
+#pragma unroll
+      for (int c = 0; c < CPCT_W; ++c) S[2 + c] = wu[c];
+#pragma unroll
+      for (int rr = 0; rr < CPCT_W; ++rr) {
+        S[8 + 2 * rr] = wv[rr] * val.x;
+        S[9 + 2 * rr] = wv[rr] * val.y;
+      }
+    }
+    __syncwarp();
+    const int cnt = min(32, it.z - base);
+    for (int e = 0; e < cnt; ++e) {
+      const float* S = stg + e * kStg;
+      const int ar = __float_as_int(S[0]), br = __float_as_int(S[1]);
+      if (lane < 30) {
+        const int rr = br + r1, cc = ar + c1;
+        if ((unsigned)rr < (unsigned)CPCT_TILE && (unsigned)cc < (unsigned)CPCT_TILE) {
+          const float w = S[2 + c1];
+          acc_re[rr * kAccLd + cc] = fmaf(w, S[8 + 2 * r1], acc_re[rr * kAccLd + cc]);
+          acc_im[rr * kAccLd + cc] = fmaf(w, S[9 + 2 * r1], acc_im[rr * kAccLd + cc]);
+        }
+      } else {
+        // lanes 30, 31: taps (5, 0), (5, 1)
+        const int c = lane - 30, rr = br + 5, cc = ar + c;
+        if ((unsigned)rr < (unsigned)CPCT_TILE && (unsigned)cc < (unsigned)CPCT_TILE) {
+          const float w = S[2 + c];
+          acc_re[rr * kAccLd + cc] = fmaf(w, S[18], acc_re[rr * kAccLd + cc]);
+          acc_im[rr * kAccLd + cc] = fmaf(w, S[19], acc_im[rr * kAccLd + cc]);
+        }
+      }
+      if (lane < 4) {
+        // taps (5, 2..5)
+        const int c = lane + 2, rr = br + 5, cc = ar + c;
+        if ((unsigned)rr < (unsigned)CPCT_TILE && (unsigned)cc < (unsigned)CPCT_TILE) {
+          const float w = S[2 + c];
+          acc_re[rr * kAccLd + cc] = fmaf(w, S[18], acc_re[rr * kAccLd + cc]);
+          acc_im[rr * kAccLd + cc] = fmaf(w, S[19], acc_im[rr * kAccLd + cc]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  if (it.w < 0) {
+    for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32) {
+      const int rr = i / CPCT_TILE, cc = i % CPCT_TILE;
+      const int gr = TR + rr, gc = TC + cc;
+      if (gr < a.ext_rows && gc < a.ldh)
+        a.Ax[(size_t)gr * a.ldh + gc] = make_float2(acc_re[rr * kAccLd + cc], acc_im[rr * kAccLd + cc]);
+    }
+  } else {
+    float2* dst = a.partials + (size_t)it.w * CPCT_TILE * CPCT_TILE;
+    for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32) {
+      const int rr = i / CPCT_TILE, cc = i % CPCT_TILE;
+      dst[i] = make_float2(acc_re[rr * kAccLd + cc], acc_im[rr * kAccLd + cc]);
+    }
+  }
+}
+
+// 7. fixed-order sum of the partial tiles of split bins
+__global__ void __launch_bounds__(256) k_adj_reduce(const int4* __restrict__ split, const float2* __restrict__ partials,
+                                                   float2* __restrict__ Ax, int tiles_x, int ldh, int ext_rows) {
+  const int4 s = split[blockIdx.x];
+  const int TC = (s.x % tiles_x) * CPCT_TILE, TR = (s.x / tiles_x) * CPCT_TILE;
+  for (int i = threadIdx.x; i < CPCT_TILE * CPCT_TILE; i += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < s.z; ++q) acc = cadd(acc, partials[(size_t)(s.y + q) * CPCT_TILE * CPCT_TILE + i]);
+    const int gr = TR + i / CPCT_TILE, gc = TC + i % CPCT_TILE;
+    if (gr < ext_rows && gc < ldh) Ax[(size_t)gr * ldh + gc] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 8. adjoint row transform with the fold of the extension
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 wrapped(const float2* __restrict__ row, int a, int G) {
+  float2 v = row[a];
+  if (a < 6) v = cadd(v, row[a + G]);
+  return v;
+}
+
+template <int LOGG>
+__global__ void __launch_bounds__(kThreads)
+    k_adj_row(const float2* __restrict__ Ax, float2* __restrict__ H1, const float2* __restrict__ tw, int N, int ldh) {
+  using FFT = SmemFFT<LOGG, kE, +1>;
+  constexpr int G = 1 << LOGG, T = FFT::T, RPC = rows_per_cta<LOGG>();
+  extern __shared__ float2 sm[];
+  const int f = threadIdx.x / T, t = threadIdx.x % T;
+  float2* buf = sm + f * FFT::PADN;
+  const int b = blockIdx.x * RPC + f;
+  const bool valid = b <= N;
+  int mrow = -1;
+  if (b == 1 || b == 2) mrow = 2 - b;
+  else if (b >= N - 3 && b <= N - 1) mrow = (2 * N - b) + 2;
+  const float2* row = Ax + (size_t)(b + 2) * ldh;
+  const float2* mr = Ax + (size_t)(mrow < 0 ? 0 : mrow) * ldh;
+  for (int a = t; a < G; a += T) {
+    float2 v = make_float2(0.f, 0.f);
+    if (valid) {
+      v = wrapped(row, a, G);
+      if (mrow >= 0) v = cadd(v, cconj(wrapped(mr, (-a) & (G - 1), G)));
+    }
+    buf[fpad(a)] = v;
+  }
+  __syncthreads();
+  FFT::run(buf, tw, t);
+  if (!valid) return;
+  for (int q = t; q < N; q += T) H1[(size_t)b * N + q] = buf[fpad((q - N / 2) & (G - 1))];
+}
+
+// ---------------------------------------------------------------------------
+// 9. adjoint column transform: Re of the inverse transform over b = 0..N
+// ---------------------------------------------------------------------------
+template <int LOGG>
+__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
+    k_adj_col(const float2* __restrict__ H1, const float* __restrict__ dp, float* __restrict__ img,
+              const float2* __restrict__ tw, int N) {
+  using FFT = SmemFFT<LOGG, kE, +1>;
+  constexpr int G = 1 << LOGG;
+  extern __shared__ float2 sm[];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int q0 = blockIdx.x * (2 * kColFFTs);
+  for (int idx = tid; idx < (N + 1) * kColFFTs; idx += nthr) {
+    const int b = idx / kColFFTs, f = idx % kColFFTs;
+    const float4 z = *reinterpret_cast<const float4*>(H1 + (size_t)b * N + q0 + 2 * f);  // z1 = (x,y), z2 = (z,w)
+    float2* buf = sm + f * FFT::PADN;
+    if (b == 0 || b == N) {
+      buf[fpad(b)] = make_float2(z.x, z.z);
+    } else {
+      buf[fpad(b)] = make_float2(0.5f * (z.x - z.w), 0.5f * (z.y + z.z));
+      buf[fpad(G - b)] = make_float2(0.5f * (z.x + z.w), 0.5f * (z.z - z.y));
+    }
+  }
+  __syncthreads();
+  FFT::run(sm + (tid / FFT::T) * FFT::PADN, tw, tid % FFT::T);
+  for (int idx = tid; idx < 2 * N; idx += nthr) {
+    const int p = idx >> 1, h = idx & 1;
+    const int pos = (p - N / 2) & (G - 1);
+    const float2 w0 = sm[(2 * h) * FFT::PADN + fpad(pos)];
+    const float2 w1 = sm[(2 * h + 1) * FFT::PADN + fpad(pos)];
+    const float4 d = *reinterpret_cast<const float4*>(dp + q0 + 4 * h);
+    const float cp = dp[p];
+    *reinterpret_cast<float4*>(img + (size_t)p * N + q0 + 4 * h) =
+        make_float4(w0.x * cp * d.x, w0.y * cp * d.y, w1.x * cp * d.z, w1.y * cp * d.w);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// size dispatch
+// ---------------------------------------------------------------------------
+template <int LOGG>
+int set_attr_G() {
+  if (cudaFuncSetAttribute(k_fwd_col<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(kColFFTs)) != cudaSuccess) return CPCT_ECUDA;
+  if (cudaFuncSetAttribute(k_adj_col<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(kColFFTs)) != cudaSuccess) return CPCT_ECUDA;
+  if (cudaFuncSetAttribute(k_fwd_row<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(rows_per_cta<LOGG>())) != cudaSuccess) return CPCT_ECUDA;
+  if (cudaFuncSetAttribute(k_adj_row<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(rows_per_cta<LOGG>())) != cudaSuccess) return CPCT_ECUDA;
+  return CPCT_OK;
+}
+template <int LOGNS>
+int set_attr_Ns() {
+  if (cudaFuncSetAttribute(k_fwd_ray<LOGNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGNS>(rows_per_cta<LOGNS>())) != cudaSuccess) return CPCT_ECUDA;
+  if (cudaFuncSetAttribute(k_adj_ray<LOGNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGNS>(rows_per_cta<LOGNS>())) != cudaSuccess) return CPCT_ECUDA;
+  return CPCT_OK;
+}
+
+template <int LOGG>
+void launch_fwd_G(cpct_plan* p, const float* img, cudaStream_t s) {
+  constexpr int G = 1 << LOGG;
+  cpct_prof_begin(p, KID_FWD_COL, s);
+  k_fwd_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kE, fft_smem<LOGG>(kColFFTs), s>>>(img, p->d_deapod, p->d_H1, p->d_twG, p->n);
+  cpct_prof_end(p, KID_FWD_COL, s);
+  constexpr int RPC = rows_per_cta<LOGG>();
+  cpct_prof_begin(p, KID_FWD_ROW, s);
+  k_fwd_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kE), fft_smem<LOGG>(RPC), s>>>(p->d_H1, p->d_Hx, p->d_twG, p->n, p->ldh);
+  cpct_prof_end(p, KID_FWD_ROW, s);
+}
+template <int LOGNS>
+void launch_fwd_Ns(cpct_plan* p, float* sino, cudaStream_t s) {
+  constexpr int NS = 1 << LOGNS, PPC = rows_per_cta<LOGNS>();
+  const int pairs = (p->m + 1) / 2;
+  cpct_prof_begin(p, KID_FWD_RAY, s);
+  k_fwd_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kE), fft_smem<LOGNS>(PPC), s>>>(p->d_Q, sino, p->d_twNs, p->m, p->ldq);
+  cpct_prof_end(p, KID_FWD_RAY, s);
+}
+template <int LOGNS>
+void launch_adj_Ns(cpct_plan* p, const float* sino, cudaStream_t s) {
+  constexpr int NS = 1 << LOGNS, PPC = rows_per_cta<LOGNS>();
+  const int pairs = (p->m + 1) / 2;
+  cpct_prof_begin(p, KID_ADJ_RAY, s);
+  k_adj_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kE), fft_smem<LOGNS>(PPC), s>>>(sino, p->d_Q, p->d_twNs, p->m, p->ldq);
+  cpct_prof_end(p, KID_ADJ_RAY, s);
+}
+template <int LOGG>
+void launch_adj_G(cpct_plan* p, float* img, cudaStream_t s) {
+  constexpr int G = 1 << LOGG;
+  constexpr int RPC = rows_per_cta<LOGG>();
+  cpct_prof_begin(p, KID_ADJ_ROW, s);
+  k_adj_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kE), fft_smem<LOGG>(RPC), s>>>(p->d_Ax, p->d_H1, p->d_twG, p->n, p->ldh);
+  cpct_prof_end(p, KID_ADJ_ROW, s);
+  cpct_prof_begin(p, KID_ADJ_COL, s);
+  k_adj_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kE, fft_smem<LOGG>(kColFFTs), s>>>(p->d_H1, p->d_deapod, img, p->d_twG, p->n);
+  cpct_prof_end(p, KID_ADJ_COL, s);
+}
+
+#define CPCT_DISPATCH_G(lg, CALL)   \
+  switch (lg) {                     \
+    case 6: CALL(6); break;         \
+    case 7: CALL(7); break;         \
+    case 8: CALL(8); break;         \
+    case 9: CALL(9); break;         \
+    case 10: CALL(10); break;       \
+    case 11: CALL(11); break;       \
+    case 12: CALL(12); break;       \
+    default: return CPCT_EINVAL;    \
+  }
+#define CPCT_DISPATCH_NS(lg, CALL)  \
+  switch (lg) {                     \
+    case 5: CALL(5); break;         \
+    case 6: CALL(6); break;         \
+    case 7: CALL(7); break;         \
+    case 8: CALL(8); break;         \
+    case 9: CALL(9); break;         \
+    case 10: CALL(10); break;       \
+    case 11: CALL(11); break;       \
+    case 12: CALL(12); break;       \
+    default: return CPCT_EINVAL;    \
+  }
+
+}  // namespace
+
+int cpct_radon_setup_attributes(int logG, int logNs) {
+  int rc = CPCT_OK;
+#define SETG(L) rc = set_attr_G<L>()
+#define SETN(L) rc = set_attr_Ns<L>()
+  CPCT_DISPATCH_G(logG, SETG);
+  if (rc) return rc;
+  CPCT_DISPATCH_NS(logNs, SETN);
+#undef SETG
+#undef SETN
+  return rc;
+}
+
+int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_t s) {
+#define FG(L) launch_fwd_G<L>(p, d_img, s)
+  CPCT_DISPATCH_G(p->logG, FG);
+#undef FG
+  FwdInterpArgs a;
+  a.items = p->d_fwd_items;
+  a.ids = p->d_fwd_ids;
+  a.ray = p->d_ray;
+  a.Hx = p->d_Hx;
+  a.Q = p->d_Q;
+  a.err = p->d_err;
+  a.G = p->G;
+  a.ldq = p->ldq;
+  a.ldh = p->ldh;
+  a.tiles_x = p->tiles_x_fwd;
+  a.poly = p->poly;
+  if (p->n_fwd_items > 0) {
+    cpct_prof_begin(p, KID_FWD_INTERP, s);
+    k_fwd_interp<<<p->n_fwd_items, 256, 0, s>>>(p->tmap_Hx, a);
+    cpct_prof_end(p, KID_FWD_INTERP, s);
+  }
+#define FN(L) launch_fwd_Ns<L>(p, d_sino, s)
+  CPCT_DISPATCH_NS(p->logNs, FN);
+#undef FN
+  return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}
+
+int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_t s) {
+#define AN(L) launch_adj_Ns<L>(p, d_sino, s)
+  CPCT_DISPATCH_NS(p->logNs, AN);
+#undef AN
+  AdjSpreadArgs a;
+  a.items = p->d_adj_items;
+  a.ids = p->d_adj_ids;
+  a.ray = p->d_ray;
+  a.Qt = p->d_Q;
+  a.Ax = p->d_Ax;
+  a.partials = p->d_partials;
+  a.G = p->G;
+  a.ldq = p->ldq;
+  a.ldh = p->ldh;
+  a.tiles_x = p->tiles_x_adj;
+  a.ext_rows = p->ext_rows;
+  a.poly = p->poly;
+  if (p->n_adj_items > 0) {
+    cpct_prof_begin(p, KID_ADJ_SPREAD, s);
+    k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
+    cpct_prof_end(p, KID_ADJ_SPREAD, s);
+  }
+  if (p->n_split > 0) {
+    cpct_prof_begin(p, KID_ADJ_REDUCE, s);
+    k_adj_reduce<<<p->n_split, 256, 0, s>>>(p->d_split, p->d_partials, p->d_Ax, p->tiles_x_adj, p->ldh, p->ext_rows);
+    cpct_prof_end(p, KID_ADJ_REDUCE, s);
+  }
+#define AG(L) launch_adj_G<L>(p, d_img, s)
+  CPCT_DISPATCH_G(p->logG, AG);
+#undef AG
+  return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}

@@ -53,15 +53,28 @@ CONFIGS = {
 }
 
 
-def _coverage(n, inside_fn, ss=4):
-    """Fraction of each pixel covered by a shape (ss x ss sub-samples)."""
+def _coverage(n, inside_fn, ss=4, bbox=None):
+    """Fraction of each pixel covered by a shape (ss x ss sub-samples).
+
+    ``bbox`` = (xmin, xmax, ymin, ymax) in pixel coordinates limits the work
+    to the pixels that can be covered.
+    """
     off = (np.arange(ss) + 0.5) / ss - 0.5
-    X = np.arange(n, dtype=np.float64) - n // 2
     img = np.zeros((n, n))
+    q0, q1, p0, p1 = 0, n, 0, n
+    if bbox is not None:
+        q0 = max(0, int(math.floor(bbox[0])) + n // 2 - 1)
+        q1 = min(n, int(math.ceil(bbox[1])) + n // 2 + 2)
+        p0 = max(0, int(math.floor(bbox[2])) + n // 2 - 1)
+        p1 = min(n, int(math.ceil(bbox[3])) + n // 2 + 2)
+    Xq = np.arange(q0, q1, dtype=np.float64) - n // 2
+    Yp = np.arange(p0, p1, dtype=np.float64) - n // 2
+    acc = np.zeros((p1 - p0, q1 - q0))
     for dy in off:
         for dx in off:
-            img += inside_fn(X[None, :] + dx, X[:, None] + dy)
-    return img / (ss * ss)
+            acc += inside_fn(Xq[None, :] + dx, Yp[:, None] + dy)
+    img[p0:p1, q0:q1] = acc / (ss * ss)
+    return img
 
 
 def disk_phantom(n: int, n_disks: int, rng: np.random.Generator,
@@ -80,7 +93,8 @@ def disk_phantom(n: int, n_disks: int, rng: np.random.Generator,
             disks.append((cx, cy, r, rng.uniform(*v_range)))
     img = np.zeros((n, n))
     for (cx, cy, r, v) in disks:
-        box = _coverage(n, lambda X, Y, cx=cx, cy=cy, r=r: ((X - cx) ** 2 + (Y - cy) ** 2 < r * r))
+        box = _coverage(n, lambda X, Y, cx=cx, cy=cy, r=r: ((X - cx) ** 2 + (Y - cy) ** 2 < r * r),
+                        bbox=(cx - r, cx + r, cy - r, cy + r))
         img += v * box
     return img, disks
 
@@ -111,7 +125,8 @@ def ellipse_phantom(n: int, n_shapes: int, rng: np.random.Generator,
             yr = -(X - cx) * sa + (Y - cy) * ca
             return (xr / a) ** 2 + (yr / b) ** 2 < 1.0
 
-        img += v * _coverage(n, inside, ss)
+        ext = max(a, b)
+        img += v * _coverage(n, inside, ss, bbox=(cx - ext, cx + ext, cy - ext, cy + ext))
         shapes.append((cx, cy, a, b, ang, v))
     return img, shapes
 

@@ -1,0 +1,203 @@
+"""GPU parity of the Radon operator pair (C ABI) against the FP64 oracle.
+
+Tolerance: relative L2 <= 1e-5 for the FP32 operators against the FP64
+gridding oracle (same Kaiser-Bessel approximation), the bar of the
+operators' specification; the exact NUDFT is matched within the kernel's own
+aliasing error (1e-4).  Every comparison prints its measured error.
+"""
+import numpy as np
+import pytest
+
+from oracle import nufft
+from paper_1009_1380_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_1380_gb300 import build
+    build.build()
+    return torch
+
+
+def _plan(n, ns, m, angles=None):
+    from paper_1009_1380_gb300.cpct import Plan
+    return Plan(n, ns, m, angles=angles)
+
+
+def _run(torch, plan, img, sino):
+    x = torch.from_numpy(np.ascontiguousarray(img, np.float32)).cuda()
+    w = torch.from_numpy(np.ascontiguousarray(sino, np.float32)).cuda()
+    y = plan.fwd(x)
+    z = plan.adj(w)
+    torch.cuda.synchronize()
+    plan.sync()
+    return y.cpu().numpy().astype(np.float64), z.cpu().numpy().astype(np.float64)
+
+
+def test_kernel_tables_fp64(torch_cuda):
+    from scipy import special
+    p = _plan(128, 128, 8)
+    poly, dp = p.debug_tables()
+    beta = nufft.kb_beta(6, 2.0)
+    s = np.linspace(-1, 1, 4001)
+    z = (s + 1) / 2
+    worst = 0.0
+    for i in range(6):
+        t = z + 2 - i
+        ok = np.abs(t) < 3
+        exact = special.i0(beta * np.sqrt(np.maximum(1 - (t / 3) ** 2, 0))) / special.i0(beta)
+        approx = np.polyval(poly[i][::-1], s)
+        worst = max(worst, float(np.abs(approx - exact)[ok].max()))
+    print("kb polynomial max error", worst)
+    assert worst < 2e-9
+    ref = nufft.deapod(128, 256)
+    print("deapod rel error", _rel(dp, ref))
+    assert _rel(dp, ref) < 1e-6
+
+
+@pytest.mark.parametrize("n,ns,m", [(128, 128, 180), (32, 32, 7), (64, 128, 33), (256, 256, 64), (32, 64, 1)])
+def test_parity_vs_gridding_oracle(torch_cuda, n, ns, m):
+    rng = np.random.default_rng(100 + n + m)
+    if n == 128:
+        img = synth.phantom("c1_128").astype(np.float64)
+    else:
+        img = rng.standard_normal((n, n))
+    sino = rng.standard_normal((m, ns))
+    geo = nufft.GridGeometry(n, ns, nufft.default_angles(m))
+    y_ref = nufft.radon_grid(img, geo)
+    z_ref = nufft.radon_grid_adj(sino, geo)
+    p = _plan(n, ns, m)
+    y, z = _run(torch_cuda, p, img, sino)
+    ef, ea = _rel(y, y_ref), _rel(z, z_ref)
+    print(f"n={n} ns={ns} m={m}: fwd rel {ef:.2e}  adj rel {ea:.2e}")
+    assert ef < TOL and ea < TOL
+
+
+def test_parity_vs_exact_nudft(torch_cuda):
+    n, m = 128, 180
+    img = synth.phantom("c1_128").astype(np.float64)
+    th = nufft.default_angles(m)
+    y_ex = nufft.radon_exact(img, n, th)
+    w = np.random.default_rng(3).standard_normal((m, n))
+    z_ex = nufft.radon_exact_adj(w, n, th)
+    y, z = _run(torch_cuda, _plan(n, n, m), img, w)
+    print("vs exact NUDFT: fwd", _rel(y, y_ex), "adj", _rel(z, z_ex))
+    assert _rel(y, y_ex) < 1e-4 and _rel(z, z_ex) < 1e-4
+
+
+def test_custom_angles(torch_cuda):
+    n, m = 64, 20
+    th = np.sort(np.random.default_rng(4).uniform(0, np.pi, m))
+    th[0] = 0.0
+    img = np.random.default_rng(5).standard_normal((n, n))
+    w = np.random.default_rng(6).standard_normal((m, n))
+    geo = nufft.GridGeometry(n, n, th)
+    y, z = _run(torch_cuda, _plan(n, n, m, angles=th), img, w)
+    assert _rel(y, nufft.radon_grid(img, geo)) < TOL
+    assert _rel(z, nufft.radon_grid_adj(w, geo)) < TOL
+
+
+@pytest.mark.parametrize("n,m", [(128, 180), (512, 90), (1024, 128)])
+def test_adjoint_identity_and_determinism(torch_cuda, n, m):
+    torch = torch_cuda
+    p = _plan(n, n, m)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn((n, n), device="cuda", generator=g)
+    w = torch.randn((m, n), device="cuda", generator=g)
+    y = p.fwd(x)
+    z1 = p.adj(w)
+    z2 = p.adj(w)
+    torch.cuda.synchronize()
+    lhs = float((y.double() * w.double()).sum())
+    rhs = float((x.double() * z1.double()).sum())
+    rel = abs(lhs - rhs) / (float(y.double().norm()) * float(w.double().norm()))
+    print(f"n={n}: adjoint identity rel {rel:.2e}")
+    assert rel < 1e-6
+    assert torch.equal(z1, z2), "adjoint is not bitwise deterministic"
+    y2 = p.fwd(x)
+    assert torch.equal(y, y2)
+    p.sync()
+
+
+def test_edge_cases(torch_cuda):
+    torch = torch_cuda
+    p = _plan(64, 64, 10)
+    zero = torch.zeros((64, 64), device="cuda")
+    assert float(p.fwd(zero).abs().max()) == 0.0
+    assert float(p.adj(torch.zeros((10, 64), device="cuda")).abs().max()) == 0.0
+    # a single pixel at the centre projects to (nearly) a delta at s = Ns/2 for every angle
+    e = torch.zeros((64, 64), device="cuda")
+    e[32, 32] = 1.0
+    y = p.fwd(e).cpu().numpy()
+    assert np.all(np.argmax(y, axis=1) == 32)
+    np.testing.assert_allclose(y.sum(axis=1), 1.0, rtol=1e-5)
+    p.sync()
+
+
+def test_host_variants_match_device(torch_cuda):
+    torch = torch_cuda
+    n, m = 128, 180
+    p = _plan(n, n, m)
+    img = synth.phantom("c1_128")
+    w = np.random.default_rng(9).standard_normal((m, n)).astype(np.float32)
+    y_h = p.fwd_host(img)
+    z_h = p.adj_host(w)
+    y_d, z_d = _run(torch, p, img, w)
+    np.testing.assert_array_equal(y_h, y_d.astype(np.float32))
+    np.testing.assert_array_equal(z_h, z_d.astype(np.float32))
+
+
+def test_errors(torch_cuda):
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    with pytest.raises(cpct.CpctError) as ei:
+        cpct.Plan(100, 100, 10)
+    assert ei.value.status == -1
+    with pytest.raises(cpct.CpctError) as ei:
+        cpct.Plan(64, 32, 10)
+    assert ei.value.status == -1
+    with pytest.raises(cpct.CpctError) as ei:
+        cpct.Plan(64, 64, 10, angles=np.linspace(0, 4, 10))
+    assert ei.value.status == -1
+    with pytest.raises(cpct.CpctError) as ei:
+        cpct.Plan(64, 64, 10, flags=cpct.PLAN_FAIL_ALLOC)
+    assert ei.value.status == -2
+    p = cpct.Plan(64, 64, 10)
+    with pytest.raises(ValueError):
+        p.fwd(torch.zeros((32, 32), device="cuda"))
+
+
+def test_full_size_2048_sampled_rays(torch_cuda):
+    """2048^2, 1024 views x 2048 bins (the benchmark workload): sampled rays of
+    the forward against the FP64 oracle, the adjoint by the adjoint identity."""
+    torch = torch_cuda
+    n, m = 2048, 1024
+    img = synth.phantom("c2_2048")
+    p = _plan(n, n, m)
+    x = torch.from_numpy(img).cuda()
+    y = p.fwd(x).cpu().numpy().astype(np.float64)
+    geo = nufft.GridGeometry(n, n, nufft.default_angles(m))
+    rays = np.array([0, 1, 255, 256, 511, 512, 700, 1023])
+    y_ref = nufft.radon_grid(img.astype(np.float64), geo, rays)
+    e = _rel(y[rays], y_ref)
+    print("2048 sampled rays fwd rel", e)
+    assert e < TOL
+    w = torch.randn((m, n), device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    z = p.adj(w)
+    lhs = float((torch.from_numpy(y).cuda() * w.double()).sum())
+    rhs = float((x.double() * z.double()).sum())
+    rel = abs(lhs - rhs) / (np.linalg.norm(y) * float(w.double().norm()))
+    print("2048 adjoint identity rel", rel)
+    assert rel < 1e-6
+    p.sync()
