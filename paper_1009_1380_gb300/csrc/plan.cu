@@ -22,7 +22,7 @@ namespace {
 
 constexpr int kPolyDeg = 9;            // Chebyshev interpolation degree per tap
 constexpr int kFwdItemMax = 1024;      // samples per forward gather work item
-constexpr int kAdjItemMax = 512;       // entries per adjoint spread work item
+constexpr int kAdjItemMax = 1024;      // entries per adjoint spread work item
 
 // ---------------------------------------------------------------------------
 // FP64 device builders (kernel table, deapodization, twiddles)

@@ -18,9 +18,10 @@
 //   5. k_adj_ray   Ns-point FFT of two packed sinogram rows, weights
 //                  (1, 2, ..., 2, 1) (-1)^k / Ns               -> Q~
 //   6. k_adj_spread  gridding as a deterministic gather: each 32x32 tile of
-//                  the extended spectrum owns its output; one warp walks the
-//                  tile's sample list in a fixed order and adds each sample's
-//                  36 taps (one tap per lane) into shared memory; no atomics
+//                  the extended spectrum owns its output; 8 warps own 4-row
+//                  strips, and each walks the tile's sample list in a fixed
+//                  order, adding the taps of every sample that touches its
+//                  strip (one tap per lane) into shared memory; no atomics
 //   7. k_adj_reduce  heavy tiles were split into several work items with
 //                  partial tiles; summed here in a fixed order  -> Ax
 //   8. k_adj_row   fold the extension (mirror rows, wrapped columns), G-point
@@ -55,11 +56,11 @@ constexpr size_t fft_smem(int nfft) { return (size_t)nfft * SmemFFT<LOG, kE, -1>
 template <int LOGG>
 __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
     k_fwd_col(const float* __restrict__ img, const float* __restrict__ dp, float2* __restrict__ H1,
-              const float2* __restrict__ tw, int N) {
+              const float2* __restrict__ tw) {
   using FFT = SmemFFT<LOGG, kE, -1>;
-  constexpr int G = 1 << LOGG;
+  constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kE;
   extern __shared__ float2 sm[];
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   const int q0 = blockIdx.x * (2 * kColFFTs);
   // zero the padding half [N/2, G - N/2) of every FFT
   for (int idx = tid; idx < kColFFTs * N; idx += nthr) {
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
     sm[f * FFT::PADN + fpad(q)] = make_float2(0.f, 0.f);
   }
   // deapodized columns: FFT f packs columns q0+2f (real part), q0+2f+1 (imag)
+#pragma unroll
   for (int idx = tid; idx < 2 * N; idx += nthr) {
     const int p = idx >> 1, h = idx & 1;
     const float4 v = *reinterpret_cast<const float4*>(img + (size_t)p * N + q0 + 4 * h);
@@ -93,14 +95,15 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
 // ---------------------------------------------------------------------------
 template <int LOGG>
 __global__ void __launch_bounds__(kThreads)
-    k_fwd_row(const float2* __restrict__ H1, float2* __restrict__ Hx, const float2* __restrict__ tw, int N, int ldh) {
+    k_fwd_row(const float2* __restrict__ H1, float2* __restrict__ Hx, const float2* __restrict__ tw, int ldh) {
   using FFT = SmemFFT<LOGG, kE, -1>;
-  constexpr int G = 1 << LOGG, T = FFT::T, RPC = rows_per_cta<LOGG>();
+  constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = rows_per_cta<LOGG>();
   extern __shared__ float2 sm[];
   const int f = threadIdx.x / T, t = threadIdx.x % T;
   float2* buf = sm + f * FFT::PADN;
   const int b = blockIdx.x * RPC + f;
   const bool valid = b <= N;
+#pragma unroll
   for (int q = t; q < N; q += T) {
     buf[fpad(N / 2 + q)] = make_float2(0.f, 0.f);
     const int pos = (q - N / 2) & (G - 1);
@@ -218,6 +221,7 @@ __global__ void __launch_bounds__(kThreads)
   float2* buf = sm + f * FFT::PADN;
   const int j1 = 2 * (blockIdx.x * PPC + f), j2 = j1 + 1;
   const bool v1 = j1 < M, v2 = j2 < M;
+#pragma unroll
   for (int k = t; k < NS; k += T) {
     const int kk = k <= K ? k : NS - k;
     const float sg = (kk & 1) ? -1.f : 1.f;
@@ -252,6 +256,7 @@ __global__ void __launch_bounds__(kThreads)
   float2* buf = sm + f * FFT::PADN;
   const int j1 = 2 * (blockIdx.x * PPC + f), j2 = j1 + 1;
   const bool v1 = j1 < M, v2 = j2 < M;
+#pragma unroll
   for (int s = t; s < NS; s += T)
     buf[fpad(s)] = make_float2(v1 ? sino[(size_t)j1 * NS + s] : 0.f, v2 ? sino[(size_t)j2 * NS + s] : 0.f);
   __syncthreads();
@@ -283,109 +288,108 @@ struct AdjSpreadArgs {
   KBPoly poly;
 };
 
-constexpr int kAccLd = CPCT_TILE + 6;  // 38: taps of rows 0..4 hit 30 distinct banks
-constexpr int kStg = 20;               // staged words per sample
+constexpr int kAccLd = CPCT_TILE + 6;  // 38 complex: 64-bit taps of a 4-row strip are bank-conflict free
+constexpr int kStg = 20;               // staged words per sample: ar, br, wa[6], wv[6] (complex)
+constexpr int kSpreadWarps = 8;        // warps per tile; warp w owns rows 4w..4w+3
+constexpr int kSpreadChunk = 32 * kSpreadWarps;
 
-__global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
-  __shared__ float acc_re[CPCT_TILE * kAccLd];
-  __shared__ float acc_im[CPCT_TILE * kAccLd];
-  __shared__ float stg[32 * kStg];
-  const int lane = threadIdx.x;
+__global__ void __launch_bounds__(32 * kSpreadWarps) k_adj_spread(const AdjSpreadArgs a) {
+  __shared__ __align__(16) float2 acc[CPCT_TILE * kAccLd];
+  __shared__ __align__(16) float stg[kSpreadChunk * kStg];
+  __shared__ unsigned masks[kSpreadWarps][kSpreadWarps];  // [entry group][strip]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int4 it = a.items[blockIdx.x];
   const int TC = (it.x % a.tiles_x) * CPCT_TILE, TR = (it.x / a.tiles_x) * CPCT_TILE;
-  for (int i = lane; i < CPCT_TILE * kAccLd; i += 32) {
-    acc_re[i] = 0.f;
-    acc_im[i] = 0.f;
-  }
-  const int r1 = lane / 6, c1 = lane % 6;  // tap of lanes 0..29 (rows 0..4)
-  __syncwarp();
-  for (int base = it.y; base < it.z; base += 32) {
-    const int idx = base + lane;
+  for (int i = tid; i < CPCT_TILE * kAccLd; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
+  // tap of this lane inside the warp's strip: row 4w + tr, column offset tc
+  const int tr = lane / 6, tc = lane % 6;
+  const int row = 4 * warp + tr;
+  for (int base = it.y; base < it.z; base += kSpreadChunk) {
+    const int idx = base + tid;
+    int br = -1000;
     if (idx < it.z) {
       const uint32_t id = a.ids[idx];
       const int j = (int)(id >> 16), k = (int)(id & 0xffffu);
       const float4 r = a.ray[j];
+      const float2 val = a.Qt[(size_t)j * a.ldq + k];
       int fu, fv;
       float zu, zv;
       split_coord((float)k, r.x, r.y, fu, zu);
       split_coord((float)k, r.z, r.w, fv, zv);
-      const int a0 = (fu - 2) & (a.G - 1);
       float wu[CPCT_W], wv[CPCT_W];
       kb_weights(a.poly, zu, wu);
       kb_weights(a.poly, zv, wv);
-      const float2 val = a.Qt[(size_t)j * a.ldq + k];
-      float* S = stg + lane * kStg;
-      S[0] = __int_as_float(a0 - TC);
-      S[1] = __int_as_float(fv - TR);
+      br = fv - TR;
+      float* S = stg + tid * kStg;
+      reinterpret_cast<int2*>(S)[0] = make_int2(((fu - 2) & (a.G - 1)) - TC, br);
 #pragma unroll
       for (int c = 0; c < CPCT_W; ++c) S[2 + c] = wu[c];
 #pragma unroll
-      for (int rr = 0; rr < CPCT_W; ++rr) {
-        S[8 + 2 * rr] = wv[rr] * val.x;
-        S[9 + 2 * rr] = wv[rr] * val.y;
+      for (int rr = 0; rr < CPCT_W; ++rr) reinterpret_cast<float2*>(S + 8)[rr] = cscale(val, wv[rr]);
+    }
+    // strip s (rows 4s..4s+3) is touched when 4s <= br+5 and 4s+3 >= br
+#pragma unroll
+    for (int st = 0; st < kSpreadWarps; ++st) {
+      const unsigned m = __ballot_sync(0xffffffffu, 4 * st <= br + 5 && 4 * st + 3 >= br);
+      if (lane == 0) masks[warp][st] = m;
+    }
+    __syncthreads();
+    // warp `warp` adds, in bin order, every staged sample touching its strip
+#pragma unroll 1
+    for (int g = 0; g < kSpreadWarps; ++g) {
+      unsigned m = masks[g][warp];
+      while (m) {
+        const int e = g * 32 + __ffs(m) - 1;
+        m &= m - 1;
+        const float* S = stg + e * kStg;
+        const int2 ab = reinterpret_cast<const int2*>(S)[0];
+        const int dr = row - ab.y, cc = ab.x + tc;
+        if (lane < 24 && (unsigned)dr < (unsigned)CPCT_W && (unsigned)cc < (unsigned)CPCT_TILE) {
+          const float w = S[2 + tc];
+          const float2 v = reinterpret_cast<const float2*>(S + 8)[dr];
+          float2* dst = acc + row * kAccLd + cc;
+          float2 t = *dst;
+          t.x = fmaf(w, v.x, t.x);
+          t.y = fmaf(w, v.y, t.y);
+          *dst = t;
+        }
+        __syncwarp();
       }
     }
-    __syncwarp();
-    const int cnt = min(32, it.z - base);
-    for (int e = 0; e < cnt; ++e) {
-      const float* S = stg + e * kStg;
-      const int ar = __float_as_int(S[0]), br = __float_as_int(S[1]);
-      if (lane < 30) {
-        const int rr = br + r1, cc = ar + c1;
-        if ((unsigned)rr < (unsigned)CPCT_TILE && (unsigned)cc < (unsigned)CPCT_TILE) {
-          const float w = S[2 + c1];
-          acc_re[rr * kAccLd + cc] = fmaf(w, S[8 + 2 * r1], acc_re[rr * kAccLd + cc]);
-          acc_im[rr * kAccLd + cc] = fmaf(w, S[9 + 2 * r1], acc_im[rr * kAccLd + cc]);
-        }
-      } else {
-        // lanes 30, 31: taps (5, 0), (5, 1)
-        const int c = lane - 30, rr = br + 5, cc = ar + c;
-        if ((unsigned)rr < (unsigned)CPCT_TILE && (unsigned)cc < (unsigned)CPCT_TILE) {
-          const float w = S[2 + c];
-          acc_re[rr * kAccLd + cc] = fmaf(w, S[18], acc_re[rr * kAccLd + cc]);
-          acc_im[rr * kAccLd + cc] = fmaf(w, S[19], acc_im[rr * kAccLd + cc]);
-        }
-      }
-      if (lane < 4) {
-        // taps (5, 2..5)
-        const int c = lane + 2, rr = br + 5, cc = ar + c;
-        if ((unsigned)rr < (unsigned)CPCT_TILE && (unsigned)cc < (unsigned)CPCT_TILE) {
-          const float w = S[2 + c];
-          acc_re[rr * kAccLd + cc] = fmaf(w, S[18], acc_re[rr * kAccLd + cc]);
-          acc_im[rr * kAccLd + cc] = fmaf(w, S[19], acc_im[rr * kAccLd + cc]);
-        }
-      }
-      __syncwarp();
-    }
+    __syncthreads();
   }
-  __syncwarp();
   if (it.w < 0) {
-    for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32) {
+    for (int i = tid; i < CPCT_TILE * CPCT_TILE; i += blockDim.x) {
       const int rr = i / CPCT_TILE, cc = i % CPCT_TILE;
       const int gr = TR + rr, gc = TC + cc;
-      if (gr < a.ext_rows && gc < a.ldh)
-        a.Ax[(size_t)gr * a.ldh + gc] = make_float2(acc_re[rr * kAccLd + cc], acc_im[rr * kAccLd + cc]);
+      if (gr < a.ext_rows && gc < a.ldh) a.Ax[(size_t)gr * a.ldh + gc] = acc[rr * kAccLd + cc];
     }
   } else {
     float2* dst = a.partials + (size_t)it.w * CPCT_TILE * CPCT_TILE;
-    for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32) {
-      const int rr = i / CPCT_TILE, cc = i % CPCT_TILE;
-      dst[i] = make_float2(acc_re[rr * kAccLd + cc], acc_im[rr * kAccLd + cc]);
-    }
+    for (int i = tid; i < CPCT_TILE * CPCT_TILE; i += blockDim.x)
+      dst[i] = acc[(i / CPCT_TILE) * kAccLd + i % CPCT_TILE];
   }
 }
 
-// 7. fixed-order sum of the partial tiles of split bins
-__global__ void __launch_bounds__(256) k_adj_reduce(const int4* __restrict__ split, const float2* __restrict__ partials,
-                                                   float2* __restrict__ Ax, int tiles_x, int ldh, int ext_rows) {
+// 7. fixed-order sum of the partial tiles of split bins (slot order q = 0, 1, ...)
+__global__ void __launch_bounds__(1024) k_adj_reduce(const int4* __restrict__ split, const float2* __restrict__ partials,
+                                                    float2* __restrict__ Ax, int tiles_x, int ldh, int ext_rows) {
   const int4 s = split[blockIdx.x];
   const int TC = (s.x % tiles_x) * CPCT_TILE, TR = (s.x / tiles_x) * CPCT_TILE;
-  for (int i = threadIdx.x; i < CPCT_TILE * CPCT_TILE; i += blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int q = 0; q < s.z; ++q) acc = cadd(acc, partials[(size_t)(s.y + q) * CPCT_TILE * CPCT_TILE + i]);
-    const int gr = TR + i / CPCT_TILE, gc = TC + i % CPCT_TILE;
-    if (gr < ext_rows && gc < ldh) Ax[(size_t)gr * ldh + gc] = acc;
+  const int i = threadIdx.x;
+  const float2* src = partials + (size_t)s.y * CPCT_TILE * CPCT_TILE + i;
+  float2 acc = make_float2(0.f, 0.f);
+  int q = 0;
+  for (; q + 4 <= s.z; q += 4) {
+    const float2 v0 = src[(size_t)(q + 0) * CPCT_TILE * CPCT_TILE];
+    const float2 v1 = src[(size_t)(q + 1) * CPCT_TILE * CPCT_TILE];
+    const float2 v2 = src[(size_t)(q + 2) * CPCT_TILE * CPCT_TILE];
+    const float2 v3 = src[(size_t)(q + 3) * CPCT_TILE * CPCT_TILE];
+    acc = cadd(cadd(cadd(cadd(acc, v0), v1), v2), v3);
   }
+  for (; q < s.z; ++q) acc = cadd(acc, src[(size_t)q * CPCT_TILE * CPCT_TILE]);
+  const int gr = TR + i / CPCT_TILE, gc = TC + i % CPCT_TILE;
+  if (gr < ext_rows && gc < ldh) Ax[(size_t)gr * ldh + gc] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -399,9 +403,9 @@ __device__ __forceinline__ float2 wrapped(const float2* __restrict__ row, int a,
 
 template <int LOGG>
 __global__ void __launch_bounds__(kThreads)
-    k_adj_row(const float2* __restrict__ Ax, float2* __restrict__ H1, const float2* __restrict__ tw, int N, int ldh) {
+    k_adj_row(const float2* __restrict__ Ax, float2* __restrict__ H1, const float2* __restrict__ tw, int ldh) {
   using FFT = SmemFFT<LOGG, kE, +1>;
-  constexpr int G = 1 << LOGG, T = FFT::T, RPC = rows_per_cta<LOGG>();
+  constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = rows_per_cta<LOGG>();
   extern __shared__ float2 sm[];
   const int f = threadIdx.x / T, t = threadIdx.x % T;
   float2* buf = sm + f * FFT::PADN;
@@ -412,13 +416,13 @@ __global__ void __launch_bounds__(kThreads)
   else if (b >= N - 3 && b <= N - 1) mrow = (2 * N - b) + 2;
   const float2* row = Ax + (size_t)(b + 2) * ldh;
   const float2* mr = Ax + (size_t)(mrow < 0 ? 0 : mrow) * ldh;
-  for (int a = t; a < G; a += T) {
-    float2 v = make_float2(0.f, 0.f);
-    if (valid) {
-      v = wrapped(row, a, G);
-      if (mrow >= 0) v = cadd(v, cconj(wrapped(mr, (-a) & (G - 1), G)));
-    }
-    buf[fpad(a)] = v;
+#pragma unroll
+  for (int a = t; a < G; a += T) buf[fpad(a)] = valid ? row[a] : make_float2(0.f, 0.f);
+  // fold the extension: wrapped columns G..G+5 and, for rows 1, 2, N-3..N-1,
+  // the conjugated mirror row (each thread only touches its own elements)
+  if (valid && t < 6) buf[fpad(t)] = cadd(buf[fpad(t)], row[t + G]);
+  if (valid && mrow >= 0) {
+    for (int a = t; a < G; a += T) buf[fpad(a)] = cadd(buf[fpad(a)], cconj(wrapped(mr, (-a) & (G - 1), G)));
   }
   __syncthreads();
   FFT::run(buf, tw, t);
@@ -432,12 +436,13 @@ __global__ void __launch_bounds__(kThreads)
 template <int LOGG>
 __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
     k_adj_col(const float2* __restrict__ H1, const float* __restrict__ dp, float* __restrict__ img,
-              const float2* __restrict__ tw, int N) {
+              const float2* __restrict__ tw) {
   using FFT = SmemFFT<LOGG, kE, +1>;
-  constexpr int G = 1 << LOGG;
+  constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kE;
   extern __shared__ float2 sm[];
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   const int q0 = blockIdx.x * (2 * kColFFTs);
+#pragma unroll
   for (int idx = tid; idx < (N + 1) * kColFFTs; idx += nthr) {
     const int b = idx / kColFFTs, f = idx % kColFFTs;
     const float4 z = *reinterpret_cast<const float4*>(H1 + (size_t)b * N + q0 + 2 * f);  // z1 = (x,y), z2 = (z,w)
@@ -485,11 +490,11 @@ template <int LOGG>
 void launch_fwd_G(cpct_plan* p, const float* img, cudaStream_t s) {
   constexpr int G = 1 << LOGG;
   cpct_prof_begin(p, KID_FWD_COL, s);
-  k_fwd_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kE, fft_smem<LOGG>(kColFFTs), s>>>(img, p->d_deapod, p->d_H1, p->d_twG, p->n);
+  k_fwd_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kE, fft_smem<LOGG>(kColFFTs), s>>>(img, p->d_deapod, p->d_H1, p->d_twG);
   cpct_prof_end(p, KID_FWD_COL, s);
   constexpr int RPC = rows_per_cta<LOGG>();
   cpct_prof_begin(p, KID_FWD_ROW, s);
-  k_fwd_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kE), fft_smem<LOGG>(RPC), s>>>(p->d_H1, p->d_Hx, p->d_twG, p->n, p->ldh);
+  k_fwd_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kE), fft_smem<LOGG>(RPC), s>>>(p->d_H1, p->d_Hx, p->d_twG, p->ldh);
   cpct_prof_end(p, KID_FWD_ROW, s);
 }
 template <int LOGNS>
@@ -513,10 +518,10 @@ void launch_adj_G(cpct_plan* p, float* img, cudaStream_t s) {
   constexpr int G = 1 << LOGG;
   constexpr int RPC = rows_per_cta<LOGG>();
   cpct_prof_begin(p, KID_ADJ_ROW, s);
-  k_adj_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kE), fft_smem<LOGG>(RPC), s>>>(p->d_Ax, p->d_H1, p->d_twG, p->n, p->ldh);
+  k_adj_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kE), fft_smem<LOGG>(RPC), s>>>(p->d_Ax, p->d_H1, p->d_twG, p->ldh);
   cpct_prof_end(p, KID_ADJ_ROW, s);
   cpct_prof_begin(p, KID_ADJ_COL, s);
-  k_adj_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kE, fft_smem<LOGG>(kColFFTs), s>>>(p->d_H1, p->d_deapod, img, p->d_twG, p->n);
+  k_adj_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kE, fft_smem<LOGG>(kColFFTs), s>>>(p->d_H1, p->d_deapod, img, p->d_twG);
   cpct_prof_end(p, KID_ADJ_COL, s);
 }
 
@@ -604,12 +609,12 @@ int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_
   a.poly = p->poly;
   if (p->n_adj_items > 0) {
     cpct_prof_begin(p, KID_ADJ_SPREAD, s);
-    k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
+    k_adj_spread<<<p->n_adj_items, 32 * kSpreadWarps, 0, s>>>(a);
     cpct_prof_end(p, KID_ADJ_SPREAD, s);
   }
   if (p->n_split > 0) {
     cpct_prof_begin(p, KID_ADJ_REDUCE, s);
-    k_adj_reduce<<<p->n_split, 256, 0, s>>>(p->d_split, p->d_partials, p->d_Ax, p->tiles_x_adj, p->ldh, p->ext_rows);
+    k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, p->d_partials, p->d_Ax, p->tiles_x_adj, p->ldh, p->ext_rows);
     cpct_prof_end(p, KID_ADJ_REDUCE, s);
   }
 #define AG(L) launch_adj_G<L>(p, d_img, s)
