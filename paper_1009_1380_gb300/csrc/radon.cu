@@ -420,7 +420,8 @@ __global__ void __launch_bounds__(kThreads)
   for (int a = t; a < G; a += T) buf[fpad(a)] = valid ? row[a] : make_float2(0.f, 0.f);
   // fold the extension: wrapped columns G..G+5 and, for rows 1, 2, N-3..N-1,
   // the conjugated mirror row (each thread only touches its own elements)
-  if (valid && t < 6) buf[fpad(t)] = cadd(buf[fpad(t)], row[t + G]);
+  if (valid)
+    for (int a = t; a < 6; a += T) buf[fpad(a)] = cadd(buf[fpad(a)], row[a + G]);
   if (valid && mrow >= 0) {
     for (int a = t; a < G; a += T) buf[fpad(a)] = cadd(buf[fpad(a)], cconj(wrapped(mr, (-a) & (G - 1), G)));
   }
