@@ -140,6 +140,14 @@ int cpct_debug_bins(const cpct_geom* g, int which, int* n_tiles, int* n_entries,
  * cap).  Returns the bin length (may exceed cap) or a negative status. */
 int cpct_debug_bin_tile(const cpct_geom* g, int which, int tile, uint32_t* ids, int cap);
 
+/* Round packing of the adjoint bins (host only): the samples of every tile
+ * are packed into rounds of <= 32 samples with pairwise disjoint footprints,
+ * one lane each, lanes chosen so that their shared-memory accesses are
+ * bank-conflict free.  Reports the round count, the packed sample count and
+ * valid = 1 if every invariant holds (each bin entry exactly once, no two
+ * footprints of a round overlap, lane = bank class). */
+int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packed, int* valid);
+
 /* The split of a sample coordinate u = k (hi + lo) into floor and fraction,
  * with the same float32 operations as the kernels. */
 int cpct_debug_split(float k, float hi, float lo, int* fl, float* z);

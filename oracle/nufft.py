@@ -29,10 +29,12 @@ Conventions (the paper states none; these are the readings this build uses):
 * polar spectrum ``P[j,k] = sum_{p,q} x[p,q] exp(-2 pi i (k/Ns)(X cos + Y sin))``;
 * ray inverse DFT ``y[j,s] = (1/Ns) sum_k P[j,k] exp(+2 pi i k (s - Ns/2)/Ns)``;
 * the real Radon transform is ``Re y``; its adjoint is ``Re(A^H w)``;
-* Kaiser-Bessel kernel of width ``W`` (open support ``|t| < W/2``) on a grid
-  oversampled by ``sigma``: ``g(t) = I0(beta sqrt(1-(2t/W)^2)) / I0(beta)``
-  with ``beta = pi sqrt((W/sigma)^2 (sigma-1/2)^2 - 0.8)`` (Beatty, Nishimura
-  and Pauly 2005); deapodization divides by its continuous Fourier transform
+* Kaiser-Bessel kernel of width ``W`` (support ``|t| < W/2``) on a grid
+  oversampled by ``sigma``, with its edge pedestal removed so that it is
+  continuous at the support edge:
+  ``g(t) = (I0(beta sqrt(1-(2t/W)^2)) - 1) / (I0(beta) - 1)``,
+  ``beta = pi sqrt((W/sigma)^2 (sigma-1/2)^2 - 0.8)`` (Beatty, Nishimura and
+  Pauly 2005); deapodization divides by its continuous Fourier transform
   ``ghat(X/G)``; the kernel footprint wraps periodically on the ``G x G`` grid
   (``G = sigma N``).
 
@@ -191,18 +193,24 @@ def kb_beta(width: int = 6, oversamp: float = 2.0) -> float:
 
 
 def kb_kernel(t, width: int = 6, beta: float | None = None):
-    """g(t) = I0(beta sqrt(1 - (2t/W)^2)) / I0(beta) on |t| < W/2, else 0."""
+    """g(t) = (I0(beta sqrt(1 - (2t/W)^2)) - 1) / (I0(beta) - 1) on |t| < W/2, else 0.
+
+    The Kaiser-Bessel window with its edge pedestal I0(0) = 1 removed, so that
+    g vanishes continuously at |t| = W/2 (reading: the paper names no kernel).
+    """
     if beta is None:
         beta = kb_beta(width)
     t = np.asarray(t, dtype=np.float64)
     inside = np.abs(t) < width / 2.0
     arg = np.where(inside, 1.0 - (2.0 * t / width) ** 2, 0.0)
-    return np.where(inside, special.i0(beta * np.sqrt(arg)) / special.i0(beta), 0.0)
+    return np.where(inside, (special.i0(beta * np.sqrt(arg)) - 1.0) / (special.i0(beta) - 1.0), 0.0)
 
 
 def kb_ft(xi, width: int = 6, beta: float | None = None):
     """Continuous Fourier transform of ``kb_kernel``:
-    ghat(xi) = (W / I0(beta)) sinh(sqrt(beta^2 - (pi W xi)^2)) / sqrt(beta^2 - (pi W xi)^2)."""
+    ghat(xi) = W [sinh(z)/z - sin(pi W xi)/(pi W xi)] / (I0(beta) - 1),
+    z = sqrt(beta^2 - (pi W xi)^2) (sin(|z|)/|z| when z^2 < 0); the first term
+    transforms the Kaiser-Bessel window, the second the removed pedestal."""
     if beta is None:
         beta = kb_beta(width)
     xi = np.asarray(xi, dtype=np.float64)
@@ -214,7 +222,7 @@ def kb_ft(xi, width: int = 6, beta: float | None = None):
     neg = z2 < 0
     out[neg] = np.sin(z[neg]) / z[neg]
     out[z2 == 0] = 1.0
-    return width / special.i0(beta) * out
+    return width * (out - np.sinc(width * xi)) / (special.i0(beta) - 1.0)
 
 
 def deapod(n: int, grid: int, width: int = 6, beta: float | None = None) -> np.ndarray:

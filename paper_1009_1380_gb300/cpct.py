@@ -232,3 +232,14 @@ def debug_split(k, hi, lo):
     fl, z = ctypes.c_int(), ctypes.c_float()
     lib().cpct_debug_split(ctypes.c_float(k), ctypes.c_float(hi), ctypes.c_float(lo), ctypes.byref(fl), ctypes.byref(z))
     return fl.value, z.value
+
+
+def debug_rounds(n, n_det, n_views, angles=None):
+    """Host-side round packing of the adjoint bins: (rounds, packed samples, valid)."""
+    g, _keep = make_geom(n, n_det, n_views, angles)
+    r, pk, ok = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    L = lib()
+    L.cpct_debug_rounds.argtypes = [ctypes.POINTER(Geom), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    check(L.cpct_debug_rounds(ctypes.byref(g), ctypes.byref(r), ctypes.byref(pk), ctypes.byref(ok)),
+          "cpct_debug_rounds")
+    return r.value, pk.value, bool(ok.value)

@@ -10,6 +10,7 @@
 // (ordered longest first), which balances the load around the origin where all
 // rays meet.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -22,7 +23,7 @@ namespace {
 
 constexpr int kPolyDeg = 9;            // Chebyshev interpolation degree per tap
 constexpr int kFwdItemMax = 1024;      // samples per forward gather work item
-constexpr int kAdjItemMax = 1024;      // entries per adjoint spread work item
+constexpr int kAdjItemRounds = 16;     // conflict-free rounds per adjoint spread work item
 
 // ---------------------------------------------------------------------------
 // FP64 device builders (kernel table, deapodization, twiddles)
@@ -39,12 +40,13 @@ __device__ double i0_series(double x) {
   return sum;
 }
 
-// g(t) = I0(beta sqrt(1 - (2t/W)^2)) / I0(beta), |t| < W/2
+// g(t) = (I0(beta sqrt(1 - (2t/W)^2)) - 1) / (I0(beta) - 1), |t| < W/2: the
+// Kaiser-Bessel window minus its edge pedestal (continuous at |t| = W/2)
 __device__ double kb_g(double t, double beta, double W) {
   const double a = 2.0 * t / W;
   const double w = 1.0 - a * a;
   if (w <= 0.0) return 0.0;
-  return i0_series(beta * sqrt(w)) / i0_series(beta);
+  return (i0_series(beta * sqrt(w)) - 1.0) / (i0_series(beta) - 1.0);
 }
 
 // One thread per tap i: Chebyshev interpolation of w_i(s) = g(z + 2 - i),
@@ -77,15 +79,17 @@ __global__ void k_build_poly(double* __restrict__ out, double beta, double W) {
   for (int d = 0; d < n; ++d) out[i * n + d] = mono[d];
 }
 
-// c[q] = 1 / ghat((q - N/2)/G),  ghat(xi) = (W/I0(beta)) sinh(z)/z,
-// z = sqrt(beta^2 - (pi W xi)^2)
+// c[q] = 1 / ghat((q - N/2)/G) with the continuous Fourier transform of g:
+// ghat(xi) = W (sinh(z)/z - sin(pi W xi)/(pi W xi)) / (I0(beta) - 1),
+// z = sqrt(beta^2 - (pi W xi)^2) > 0 for |xi| <= 1/4
 __global__ void k_build_deapod(float* __restrict__ out, int n, int G, double beta, double W) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const double xi = (double)(q - n / 2) / (double)G;
   const double pw = 3.14159265358979323846 * W * xi;
   const double z = sqrt(beta * beta - pw * pw);
-  const double ghat = W / i0_series(beta) * sinh(z) / z;
+  const double pedestal = (q == n / 2) ? 1.0 : sinpi(W * xi) / pw;
+  const double ghat = W * (sinh(z) / z - pedestal) / (i0_series(beta) - 1.0);
   out[q] = (float)(1.0 / ghat);
 }
 
@@ -106,6 +110,21 @@ int ilog2(int v) {
 }
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// geometry limits shared by plan creation and the host-side introspection
+bool geom_ok(const cpct_geom* g) {
+  if (!g) return false;
+  const int W = g->kb_width ? g->kb_width : 6;
+  const double sigma = g->oversamp != 0.0 ? g->oversamp : 2.0;
+  if (W != 6 || sigma != 2.0) return false;
+  if (!is_pow2(g->n) || g->n < 32 || g->n > 2048) return false;
+  if (!is_pow2(g->n_det) || g->n_det < g->n || g->n_det > 4096) return false;
+  if (g->n_views < 1 || g->n_views > 32768) return false;
+  if (g->angles)
+    for (int j = 0; j < g->n_views; ++j)
+      if (!(g->angles[j] >= 0.0 && g->angles[j] < M_PI)) return false;
+  return true;
+}
 
 // host mirror of split_coord (identical IEEE single-precision operations)
 void host_split(float k, float hi, float lo, int* fl_out, float* z) {
@@ -207,7 +226,8 @@ void make_rays(int n, int ns, int m, const double* angles, double scale, std::ve
 // forward bins: every sample (j, k >= 0) lands in the tile of its footprint's
 // first grid point (a0 = floor(u)-2 mod G, buffer row floor(v)); adjoint bins:
 // every tile of the extended spectrum that its 6x6 footprint touches.
-void build_bins(int n, int ns, int m, int G, const std::vector<float4>& ray, Bins& fwd, Bins& adj) {
+void build_bins(int n, int ns, int m, int G, const std::vector<float4>& ray, Bins& fwd, Bins& adj,
+                std::vector<int>* a0_out = nullptr, std::vector<int>* rb0_out = nullptr) {
   const int K = ns / 2;
   const int T = CPCT_TILE;
   fwd.tiles_x = G / T;
@@ -250,6 +270,73 @@ void build_bins(int n, int ns, int m, int G, const std::vector<float4>& ray, Bin
         for (int tx = a0 / T; tx <= (a0 + CPCT_HALO) / T; ++tx) adj.ids[pa[ty * adj.tiles_x + tx]++] = id;
     }
   }
+  if (a0_out) a0_out->swap(fa0);
+  if (rb0_out) rb0_out->swap(frb);
+}
+
+// Pack the samples of every adjoint tile into rounds of at most 32 samples
+// whose 6x6 footprints (clipped to the tile plus a 5-cell halo) are pairwise
+// disjoint, so that one warp can add a whole round with one lane per sample
+// and no two lanes touching the same accumulator.  The lane of a sample is
+// fixed by the 64-bit shared-memory bank pair of its footprint's first cell
+// (lanes c and c+16 for bank pair c), which makes every accumulator access of
+// a round bank-conflict free.  Greedy first fit in bin order (deterministic).
+struct Rounds {
+  std::vector<int> tile_ptr;      // tiles + 1, in rounds
+  std::vector<uint32_t> ids;      // 32 per round, 0xffffffff = empty lane
+};
+
+constexpr int kRoundLd = CPCT_TILE + 2 * CPCT_HALO + 2;  // 44 complex per accumulator row
+
+void pack_rounds(const Bins& adj, int G, const std::vector<int>& fa0, const std::vector<int>& frb, int K,
+                 Rounds& out) {
+  const int nt = (int)adj.ptr.size() - 1;
+  out.tile_ptr.assign(nt + 1, 0);
+  out.ids.clear();
+  struct R {
+    uint64_t occ[CPCT_TILE + 2 * CPCT_HALO];
+    uint32_t lanes;
+    int count;
+  };
+  std::vector<R> rounds;
+  for (int t = 0; t < nt; ++t) {
+    const int TC = (t % adj.tiles_x) * CPCT_TILE, TR = (t / adj.tiles_x) * CPCT_TILE;
+    rounds.clear();
+    size_t first_open = 0;
+    std::vector<std::array<uint32_t, 32>> lanes_of;
+    for (int e = adj.ptr[t]; e < adj.ptr[t + 1]; ++e) {
+      const uint32_t id = adj.ids[e];
+      const size_t sidx = (size_t)(id >> 16) * (K + 1) + (id & 0xffffu);
+      const int ar = fa0[sidx] - TC + CPCT_HALO, br = frb[sidx] - TR + CPCT_HALO;  // 0..36
+      const int cls = ((br * kRoundLd + ar) & 15);
+      const uint64_t fm = 0x3Full << ar;
+      size_t r = first_open;
+      for (; r < rounds.size(); ++r) {
+        R& rd = rounds[r];
+        if (rd.count == 32) continue;
+        if ((rd.lanes >> cls) & (rd.lanes >> (cls + 16)) & 1u) continue;
+        bool clash = false;
+        for (int q = 0; q < CPCT_W && !clash; ++q) clash = (rd.occ[br + q] & fm) != 0;
+        if (!clash) break;
+      }
+      if (r == rounds.size()) {
+        rounds.push_back(R{});
+        std::memset(&rounds.back(), 0, sizeof(R));
+        std::array<uint32_t, 32> empty;
+        empty.fill(0xffffffffu);
+        lanes_of.push_back(empty);
+      }
+      R& rd = rounds[r];
+      const int lane = ((rd.lanes >> cls) & 1u) ? cls + 16 : cls;
+      rd.lanes |= 1u << lane;
+      rd.count++;
+      for (int q = 0; q < CPCT_W; ++q) rd.occ[br + q] |= fm;
+      lanes_of[r][lane] = id;
+      while (first_open < rounds.size() && rounds[first_open].count == 32) ++first_open;
+    }
+    for (auto& l : lanes_of) out.ids.insert(out.ids.end(), l.begin(), l.end());
+    out.tile_ptr[t + 1] = out.tile_ptr[t] + (int)rounds.size();
+  }
 }
 
 // split bins into work items of at most `cap` entries, longest first
@@ -278,13 +365,83 @@ void make_items(const Bins& b, int cap, bool slots, std::vector<int4>& items, st
   if (n_slots) *n_slots = slot;
 }
 
+// work items over rounds: at most `cap` rounds per item, longest first; tiles
+// split over several items accumulate into partial-tile slots
+void make_round_items(const Rounds& rd, int cap, std::vector<int4>& items, std::vector<int4>& split, int* n_slots) {
+  const int nt = (int)rd.tile_ptr.size() - 1;
+  items.clear();
+  split.clear();
+  int slot = 0;
+  for (int t = 0; t < nt; ++t) {
+    const int beg = rd.tile_ptr[t], end = rd.tile_ptr[t + 1];
+    if (end == beg) continue;
+    const int pieces = (end - beg + cap - 1) / cap;
+    if (pieces == 1) {
+      items.push_back(make_int4(t, beg, end, -1));
+    } else {
+      split.push_back(make_int4(t, slot, pieces, 0));
+      for (int q = 0; q < pieces; ++q)
+        items.push_back(make_int4(t, beg + q * cap, std::min(end, beg + (q + 1) * cap), slot + q));
+      slot += pieces;
+    }
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const int4& a, const int4& c) { return (a.z - a.y) > (c.z - c.y); });
+  *n_slots = slot;
+}
+
 }  // namespace cpct_detail
+
+// Round packing of the adjoint bins of a geometry (host only): number of
+// rounds, number of packed samples, and 1 if every round is footprint- and
+// bank-conflict free and every bin entry appears exactly once, else 0.
+extern "C" int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packed, int* valid) {
+  if (!geom_ok(g)) return CPCT_EINVAL;
+  const int G = 2 * g->n, K = g->n_det / 2;
+  std::vector<float4> ray;
+  cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
+  cpct_detail::Bins f, a;
+  std::vector<int> fa0, frb;
+  cpct_detail::build_bins(g->n, g->n_det, g->n_views, G, ray, f, a, &fa0, &frb);
+  cpct_detail::Rounds rd;
+  cpct_detail::pack_rounds(a, G, fa0, frb, K, rd);
+  const int nt = (int)a.ptr.size() - 1;
+  int ok = 1, packed = 0;
+  for (int t = 0; t < nt && ok; ++t) {
+    const int TC = (t % a.tiles_x) * CPCT_TILE, TR = (t / a.tiles_x) * CPCT_TILE;
+    std::vector<uint32_t> seen;
+    for (int r = rd.tile_ptr[t]; r < rd.tile_ptr[t + 1] && ok; ++r) {
+      std::vector<int> cells;
+      for (int l = 0; l < 32; ++l) {
+        const uint32_t id = rd.ids[(size_t)r * 32 + l];
+        if (id == 0xffffffffu) continue;
+        seen.push_back(id);
+        const size_t sidx = (size_t)(id >> 16) * (K + 1) + (id & 0xffffu);
+        const int ar = fa0[sidx] - TC + CPCT_HALO, br = frb[sidx] - TR + CPCT_HALO;
+        if (ar < 0 || br < 0 || ar > CPCT_TILE + CPCT_HALO - 1 || br > CPCT_TILE + CPCT_HALO - 1) ok = 0;
+        if (((br * cpct_detail::kRoundLd + ar) & 15) != (l & 15)) ok = 0;
+        for (int q = 0; q < CPCT_W; ++q)
+          for (int c = 0; c < CPCT_W; ++c) cells.push_back((br + q) * cpct_detail::kRoundLd + ar + c);
+      }
+      std::sort(cells.begin(), cells.end());
+      if (std::adjacent_find(cells.begin(), cells.end()) != cells.end()) ok = 0;
+    }
+    std::vector<uint32_t> want(a.ids.begin() + a.ptr[t], a.ids.begin() + a.ptr[t + 1]);
+    std::sort(seen.begin(), seen.end());
+    std::sort(want.begin(), want.end());
+    if (seen != want) ok = 0;
+    packed += (int)seen.size();
+  }
+  if (n_rounds) *n_rounds = (int)(rd.ids.size() / 32);
+  if (n_packed) *n_packed = packed;
+  if (valid) *valid = ok;
+  return CPCT_OK;
+}
 
 // which = 0: forward bins, 1: adjoint bins.  Reports the number of tiles, the
 // number of entries and a checksum sum(id * (position + 1)) of the id list.
 extern "C" int cpct_debug_bins(const cpct_geom* g, int which, int* n_tiles, int* n_entries, int64_t* checksum) {
-  if (!g || g->n < 32 || !is_pow2(g->n) || !is_pow2(g->n_det) || g->n_det < g->n || g->n_views < 1)
-    return CPCT_EINVAL;
+  if (!geom_ok(g)) return CPCT_EINVAL;
   const int G = 2 * g->n;
   std::vector<float4> ray;
   cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
@@ -304,8 +461,7 @@ extern "C" int cpct_debug_bins(const cpct_geom* g, int which, int* n_tiles, int*
 // Copy the bin list of tile `tile` (which = 0 forward, 1 adjoint) into ids
 // (capacity cap); returns the number of entries or a negative status.
 extern "C" int cpct_debug_bin_tile(const cpct_geom* g, int which, int tile, uint32_t* ids, int cap) {
-  if (!g || g->n < 32 || !is_pow2(g->n) || !is_pow2(g->n_det) || g->n_det < g->n || g->n_views < 1)
-    return CPCT_EINVAL;
+  if (!geom_ok(g)) return CPCT_EINVAL;
   const int G = 2 * g->n;
   std::vector<float4> ray;
   cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
@@ -328,17 +484,10 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
   if (!out) return CPCT_EINVAL;
   *out = nullptr;
   if (!g) return CPCT_EINVAL;
+  if (!geom_ok(g)) return CPCT_EINVAL;
   const int n = g->n, ns = g->n_det, m = g->n_views;
-  const int W = g->kb_width ? g->kb_width : 6;
-  const double sigma = g->oversamp != 0.0 ? g->oversamp : 2.0;
-  if (W != 6 || sigma != 2.0) return CPCT_EINVAL;
-  if (!is_pow2(n) || n < 32 || n > 2048) return CPCT_EINVAL;
-  if (!is_pow2(ns) || ns < n || ns > 4096) return CPCT_EINVAL;
-  if (m < 1 || m > 32768) return CPCT_EINVAL;
-  if (g->angles) {
-    for (int j = 0; j < m; ++j)
-      if (!(g->angles[j] >= 0.0 && g->angles[j] < M_PI)) return CPCT_EINVAL;
-  }
+  const int W = 6;
+  const double sigma = 2.0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CPCT_ECUDA;
 
@@ -408,21 +557,24 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
     TRYC(cudaMemsetAsync(p->d_err, 0, sizeof(int), stream));
     // bins
     cpct_detail::Bins fb, ab;
-    cpct_detail::build_bins(n, ns, m, p->G, ray, fb, ab);
+    std::vector<int> fa0, frb;
+    cpct_detail::build_bins(n, ns, m, p->G, ray, fb, ab, &fa0, &frb);
+    cpct_detail::Rounds rounds;
+    cpct_detail::pack_rounds(ab, p->G, fa0, frb, p->K, rounds);
     p->tiles_x_fwd = fb.tiles_x;
     p->tiles_y_fwd = fb.tiles_y;
     p->tiles_x_adj = ab.tiles_x;
     p->tiles_y_adj = ab.tiles_y;
     std::vector<int4> fitems, aitems, fsplit, asplit;
     cpct_detail::make_items(fb, kFwdItemMax, false, fitems, fsplit, nullptr);
-    cpct_detail::make_items(ab, kAdjItemMax, true, aitems, asplit, &p->n_slots);
+    cpct_detail::make_round_items(rounds, kAdjItemRounds, aitems, asplit, &p->n_slots);
     p->n_fwd_items = (int)fitems.size();
     p->n_adj_items = (int)aitems.size();
     p->n_split = (int)asplit.size();
     TRY(upload(al, &p->d_fwd_items, fitems, stream));
     TRY(upload(al, &p->d_fwd_ids, fb.ids, stream));
     TRY(upload(al, &p->d_adj_items, aitems, stream));
-    TRY(upload(al, &p->d_adj_ids, ab.ids, stream));
+    TRY(upload(al, &p->d_adj_ids, rounds.ids, stream));
     TRY(upload(al, &p->d_split, asplit, stream));
     TRY(al((void**)&p->d_partials, sizeof(float2) * (size_t)std::max(1, p->n_slots) * CPCT_TILE * CPCT_TILE));
     // TMA descriptor of the forward extended spectrum (viewed as float32 pairs)

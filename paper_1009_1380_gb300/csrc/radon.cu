@@ -18,10 +18,10 @@
 //   5. k_adj_ray   Ns-point FFT of two packed sinogram rows, weights
 //                  (1, 2, ..., 2, 1) (-1)^k / Ns               -> Q~
 //   6. k_adj_spread  gridding as a deterministic gather: each 32x32 tile of
-//                  the extended spectrum owns its output; 8 warps own 4-row
-//                  strips, and each walks the tile's sample list in a fixed
-//                  order, adding the taps of every sample that touches its
-//                  strip (one tap per lane) into shared memory; no atomics
+//                  the extended spectrum owns its output; its samples were
+//                  packed at plan time into rounds of <= 32 samples with
+//                  disjoint footprints; one warp applies the rounds in order,
+//                  one sample per lane, into a shared-memory tile; no atomics
 //   7. k_adj_reduce  heavy tiles were split into several work items with
 //                  partial tiles; summed here in a fixed order  -> Ax
 //   8. k_adj_row   fold the extension (mirror rows, wrapped columns), G-point
@@ -284,90 +284,97 @@ struct AdjSpreadArgs {
   const float2* Qt;
   float2* Ax;
   float2* partials;
+  int* err;
   int G, ldq, ldh, tiles_x, ext_rows;
   KBPoly poly;
 };
 
-constexpr int kAccLd = CPCT_TILE + 6;  // 38 complex: 64-bit taps of a 4-row strip are bank-conflict free
-constexpr int kStg = 20;               // staged words per sample: ar, br, wa[6], wv[6] (complex)
-constexpr int kSpreadWarps = 8;        // warps per tile; warp w owns rows 4w..4w+3
-constexpr int kSpreadChunk = 32 * kSpreadWarps;
+constexpr int kRRows = CPCT_TILE + 2 * CPCT_HALO;  // 42: tile rows plus a 5-cell halo on both sides
+constexpr int kRLd = kRRows + 2;                    // 44 complex per row (bank classes use this stride)
 
-__global__ void __launch_bounds__(32 * kSpreadWarps) k_adj_spread(const AdjSpreadArgs a) {
-  __shared__ __align__(16) float2 acc[CPCT_TILE * kAccLd];
-  __shared__ __align__(16) float stg[kSpreadChunk * kStg];
-  __shared__ unsigned masks[kSpreadWarps][kSpreadWarps];  // [entry group][strip]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// One warp per work item (a run of conflict-free rounds of one tile).  In a
+// round, lane l holds one sample (or none); the 6x6 footprints of the round's
+// samples are pairwise disjoint and their first cells fall in distinct 64-bit
+// bank pairs within each half-warp, so every lane updates its 36 accumulator
+// cells with plain shared-memory loads and stores: no atomics, no conflicts.
+// Rounds are applied in their fixed plan order, hence every output element
+// receives its contributions in the same order on every run.
+__global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
+  __shared__ __align__(16) float2 acc[kRRows * kRLd];
+  const int lane = threadIdx.x;
   const int4 it = a.items[blockIdx.x];
   const int TC = (it.x % a.tiles_x) * CPCT_TILE, TR = (it.x / a.tiles_x) * CPCT_TILE;
-  for (int i = tid; i < CPCT_TILE * kAccLd; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
-  // tap of this lane inside the warp's strip: row 4w + tr, column offset tc
-  const int tr = lane / 6, tc = lane % 6;
-  const int row = 4 * warp + tr;
-  for (int base = it.y; base < it.z; base += kSpreadChunk) {
-    const int idx = base + tid;
-    int br = -1000;
-    if (idx < it.z) {
-      const uint32_t id = a.ids[idx];
-      const int j = (int)(id >> 16), k = (int)(id & 0xffffu);
-      const float4 r = a.ray[j];
-      const float2 val = a.Qt[(size_t)j * a.ldq + k];
+  for (int i = lane; i < kRRows * kRLd; i += 32) acc[i] = make_float2(0.f, 0.f);
+  // software pipeline: ids two rounds ahead, sample data one round ahead
+  uint32_t id0 = it.y < it.z ? a.ids[(size_t)it.y * 32 + lane] : 0xffffffffu;
+  uint32_t id1 = it.y + 1 < it.z ? a.ids[(size_t)(it.y + 1) * 32 + lane] : 0xffffffffu;
+  float4 ray0 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 val0 = make_float2(0.f, 0.f);
+  if (id0 != 0xffffffffu) {
+    ray0 = a.ray[id0 >> 16];
+    val0 = a.Qt[(size_t)(id0 >> 16) * a.ldq + (id0 & 0xffffu)];
+  }
+  __syncwarp();
+  for (int r = it.y; r < it.z; ++r) {
+    const uint32_t id2 = r + 2 < it.z ? a.ids[(size_t)(r + 2) * 32 + lane] : 0xffffffffu;
+    float4 ray1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 val1 = make_float2(0.f, 0.f);
+    if (id1 != 0xffffffffu) {
+      ray1 = a.ray[id1 >> 16];
+      val1 = a.Qt[(size_t)(id1 >> 16) * a.ldq + (id1 & 0xffffu)];
+    }
+    if (id0 != 0xffffffffu) {
+      const float k = (float)(id0 & 0xffffu);
       int fu, fv;
       float zu, zv;
-      split_coord((float)k, r.x, r.y, fu, zu);
-      split_coord((float)k, r.z, r.w, fv, zv);
-      float wu[CPCT_W], wv[CPCT_W];
-      kb_weights(a.poly, zu, wu);
-      kb_weights(a.poly, zv, wv);
-      br = fv - TR;
-      float* S = stg + tid * kStg;
-      reinterpret_cast<int2*>(S)[0] = make_int2(((fu - 2) & (a.G - 1)) - TC, br);
+      split_coord(k, ray0.x, ray0.y, fu, zu);
+      split_coord(k, ray0.z, ray0.w, fv, zv);
+      const int ar = ((fu - 2) & (a.G - 1)) - TC + CPCT_HALO, br = fv - TR + CPCT_HALO;
+      if ((unsigned)ar <= (unsigned)(CPCT_TILE + CPCT_HALO - 1) && (unsigned)br <= (unsigned)(CPCT_TILE + CPCT_HALO - 1)) {
+        float wu[CPCT_W], wv[CPCT_W];
+        kb_weights(a.poly, zu, wu);
+        kb_weights(a.poly, zv, wv);
+        float2* base = acc + br * kRLd + ar;
+        float2 t[CPCT_W * CPCT_W];
 #pragma unroll
-      for (int c = 0; c < CPCT_W; ++c) S[2 + c] = wu[c];
+        for (int q = 0; q < CPCT_W; ++q)
 #pragma unroll
-      for (int rr = 0; rr < CPCT_W; ++rr) reinterpret_cast<float2*>(S + 8)[rr] = cscale(val, wv[rr]);
-    }
-    // strip s (rows 4s..4s+3) is touched when 4s <= br+5 and 4s+3 >= br
+          for (int c = 0; c < CPCT_W; ++c) t[q * CPCT_W + c] = base[q * kRLd + c];
 #pragma unroll
-    for (int st = 0; st < kSpreadWarps; ++st) {
-      const unsigned m = __ballot_sync(0xffffffffu, 4 * st <= br + 5 && 4 * st + 3 >= br);
-      if (lane == 0) masks[warp][st] = m;
-    }
-    __syncthreads();
-    // warp `warp` adds, in bin order, every staged sample touching its strip
-#pragma unroll 1
-    for (int g = 0; g < kSpreadWarps; ++g) {
-      unsigned m = masks[g][warp];
-      while (m) {
-        const int e = g * 32 + __ffs(m) - 1;
-        m &= m - 1;
-        const float* S = stg + e * kStg;
-        const int2 ab = reinterpret_cast<const int2*>(S)[0];
-        const int dr = row - ab.y, cc = ab.x + tc;
-        if (lane < 24 && (unsigned)dr < (unsigned)CPCT_W && (unsigned)cc < (unsigned)CPCT_TILE) {
-          const float w = S[2 + tc];
-          const float2 v = reinterpret_cast<const float2*>(S + 8)[dr];
-          float2* dst = acc + row * kAccLd + cc;
-          float2 t = *dst;
-          t.x = fmaf(w, v.x, t.x);
-          t.y = fmaf(w, v.y, t.y);
-          *dst = t;
+        for (int q = 0; q < CPCT_W; ++q) {
+          const float2 vq = cscale(val0, wv[q]);
+#pragma unroll
+          for (int c = 0; c < CPCT_W; ++c) {
+            t[q * CPCT_W + c].x = fmaf(wu[c], vq.x, t[q * CPCT_W + c].x);
+            t[q * CPCT_W + c].y = fmaf(wu[c], vq.y, t[q * CPCT_W + c].y);
+          }
         }
-        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < CPCT_W; ++q)
+#pragma unroll
+          for (int c = 0; c < CPCT_W; ++c) base[q * kRLd + c] = t[q * CPCT_W + c];
+      } else {
+        atomicOr(a.err, CPCT_ERR_BIN);
       }
     }
-    __syncthreads();
+    __syncwarp();
+    id0 = id1;
+    ray0 = ray1;
+    val0 = val1;
+    id1 = id2;
   }
+  __syncwarp();
   if (it.w < 0) {
-    for (int i = tid; i < CPCT_TILE * CPCT_TILE; i += blockDim.x) {
+    for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32) {
       const int rr = i / CPCT_TILE, cc = i % CPCT_TILE;
       const int gr = TR + rr, gc = TC + cc;
-      if (gr < a.ext_rows && gc < a.ldh) a.Ax[(size_t)gr * a.ldh + gc] = acc[rr * kAccLd + cc];
+      if (gr < a.ext_rows && gc < a.ldh)
+        a.Ax[(size_t)gr * a.ldh + gc] = acc[(rr + CPCT_HALO) * kRLd + cc + CPCT_HALO];
     }
   } else {
     float2* dst = a.partials + (size_t)it.w * CPCT_TILE * CPCT_TILE;
-    for (int i = tid; i < CPCT_TILE * CPCT_TILE; i += blockDim.x)
-      dst[i] = acc[(i / CPCT_TILE) * kAccLd + i % CPCT_TILE];
+    for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32)
+      dst[i] = acc[(i / CPCT_TILE + CPCT_HALO) * kRLd + i % CPCT_TILE + CPCT_HALO];
   }
 }
 
@@ -602,6 +609,7 @@ int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_
   a.Qt = p->d_Q;
   a.Ax = p->d_Ax;
   a.partials = p->d_partials;
+  a.err = p->d_err;
   a.G = p->G;
   a.ldq = p->ldq;
   a.ldh = p->ldh;
@@ -610,7 +618,7 @@ int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_
   a.poly = p->poly;
   if (p->n_adj_items > 0) {
     cpct_prof_begin(p, KID_ADJ_SPREAD, s);
-    k_adj_spread<<<p->n_adj_items, 32 * kSpreadWarps, 0, s>>>(a);
+    k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
     cpct_prof_end(p, KID_ADJ_SPREAD, s);
   }
   if (p->n_split > 0) {

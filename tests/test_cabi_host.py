@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI library (no GPU): exports, bins, rounds."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import nufft
+
+
+@pytest.fixture(scope="module")
+def cpct():
+    from paper_1009_1380_gb300 import build
+    build.build()
+    from paper_1009_1380_gb300 import cpct as c
+    return c
+
+
+def test_library_exports_every_header_symbol(cpct):
+    L = cpct.lib()
+    names = cpct.header_functions()
+    assert {"radon_fwd", "radon_adj", "cpct_plan_create", "cpct_plan_destroy"} <= set(names)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_strerror(cpct):
+    L = cpct.lib()
+    assert L.cpct_strerror(0) == b"ok"
+    assert L.cpct_strerror(-1) == b"invalid argument"
+
+
+def test_split_matches_fp64_floor(cpct):
+    """The float32 split of u = k (G/Ns) cos(theta) agrees with the FP64 floor
+    except within float32 rounding of an integer, and its fraction is accurate."""
+    rng = np.random.default_rng(0)
+    worst = 0.0
+    for _ in range(2000):
+        th = rng.uniform(0, math.pi)
+        c = 2.0 * math.cos(th)
+        hi = np.float32(c)
+        lo = np.float32(c - float(hi))
+        k = float(rng.integers(0, 2049))
+        fl, z = cpct.debug_split(k, float(hi), float(lo))
+        u = k * c
+        err = abs((fl + z) - u)
+        worst = max(worst, err)
+        assert 0.0 <= z < 1.0
+    assert worst < 2e-7, worst
+
+
+@pytest.mark.parametrize("n,ns,m", [(128, 128, 180), (64, 128, 33), (256, 256, 7)])
+def test_bins_cover_every_footprint(cpct, n, ns, m):
+    """Forward bins hold each sample k = 0..Ns/2 exactly once; adjoint bins hold
+    it once per tile its 6x6 footprint touches."""
+    K = ns // 2
+    G = 2 * n
+    nt_f, ne_f, _ = cpct.debug_bins(n, ns, m, 0)
+    assert ne_f == m * (K + 1)
+    nt_a, ne_a, _ = cpct.debug_bins(n, ns, m, 1)
+    geo = nufft.GridGeometry(n, ns, nufft.default_angles(m))
+    tiles_x = G // 32 + 1
+    expect = {}
+    for j in range(m):
+        th = geo.angles[j]
+        c, s_ = (G / ns) * math.cos(th), (G / ns) * math.sin(th)
+        ch, sh = float(np.float32(c)), float(np.float32(s_))
+        cl, sl = float(np.float32(c - ch)), float(np.float32(s_ - sh))
+        for k in range(K + 1):
+            u, v = k * c, k * s_
+            fu, _ = cpct.debug_split(k, ch, cl)
+            fv, _ = cpct.debug_split(k, sh, sl)
+            # the float32 window decision equals the FP64 floor away from integers
+            if abs(u - round(u)) > 1e-6:
+                assert fu == math.floor(u)
+            if abs(v - round(v)) > 1e-6:
+                assert fv == math.floor(v)
+            a0 = (fu - 2) % G
+            rb0 = fv
+            for ty in range(rb0 // 32, (rb0 + 5) // 32 + 1):
+                for tx in range(a0 // 32, (a0 + 5) // 32 + 1):
+                    expect.setdefault(ty * tiles_x + tx, []).append((j << 16) | k)
+    assert ne_a == sum(len(v) for v in expect.values())
+    for t in list(expect)[:: max(1, len(expect) // 25)]:
+        got = cpct.debug_bin_tile(n, ns, m, 1, t)
+        assert list(got) == expect[t], t
+
+
+@pytest.mark.parametrize("n,ns,m", [(128, 128, 180), (256, 256, 64), (512, 512, 90)])
+def test_rounds_conflict_free(cpct, n, ns, m):
+    rounds, packed, ok = cpct.debug_rounds(n, ns, m)
+    _, ne, _ = cpct.debug_bins(n, ns, m, 1)
+    assert ok and packed == ne
+    assert rounds * 32 >= packed
+
+
+def test_invalid_geometry_rejected_on_host(cpct):
+    for n, ns, m in [(100, 100, 10), (64, 32, 10), (64, 64, 0), (4096, 4096, 10)]:
+        with pytest.raises(cpct.CpctError):
+            cpct.debug_bins(n, ns, m, 0)

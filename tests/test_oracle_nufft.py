@@ -131,7 +131,8 @@ def test_kb_fourier_transform_by_quadrature():
     W = 6
     beta = nufft.kb_beta(W, 2.0)
     assert nufft.kb_kernel(0.0, W, beta) == pytest.approx(1.0)
-    assert nufft.kb_kernel(3.0, W, beta) == 0.0  # open support
+    assert nufft.kb_kernel(3.0, W, beta) == 0.0  # support edge
+    assert nufft.kb_kernel(3.0 - 1e-9, W, beta) < 1e-11  # continuous there (no pedestal)
     for xi in [0.0, 0.05, 0.125, 0.2, 0.25, 0.4]:
         val, _ = integrate.quad(lambda t: float(nufft.kb_kernel(t, W, beta)) * math.cos(2 * math.pi * xi * t),
                                 -3, 3, limit=200, epsabs=1e-14, epsrel=1e-13)
