@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kPolyDeg = 9;            // Chebyshev interpolation degree per tap
 constexpr int kFwdItemMax = 1024;      // samples per forward gather work item
-constexpr int kAdjItemRounds = 16;     // conflict-free rounds per adjoint spread work item
+constexpr int kAdjItemRounds = 32;     // conflict-free rounds per adjoint spread work item
 
 // ---------------------------------------------------------------------------
 // FP64 device builders (kernel table, deapodization, twiddles)
@@ -171,7 +171,8 @@ void free_plan(cpct_plan* p) {
   cpct_prof_free(p);
   void* ptrs[] = {p->d_poly64, p->d_ray, p->d_deapod, p->d_twG, p->d_twNs, p->d_Hx, p->d_Ax, p->d_H1,
                   p->d_Q, p->d_fwd_items, p->d_fwd_ids, p->d_adj_items, p->d_adj_ids, p->d_partials,
-                  p->d_split, p->d_stage_img, p->d_stage_sino, p->d_err};
+                  p->d_split, p->d_stage_img, p->d_stage_sino, p->d_err, p->d_adj_item_split,
+                  p->d_split_count};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -339,6 +340,32 @@ void pack_rounds(const Bins& adj, int G, const std::vector<int>& fa0, const std:
   }
 }
 
+// Order the samples of every forward bin so that within each group of 16
+// consecutive samples (one half-warp) the first cells of their 6x6 windows
+// fall in distinct 64-bit bank pairs of the staged 37 x 38 window: every tap
+// load of the gather is then bank-conflict free.  Round-robin over the bank
+// classes, each class in bin order (deterministic).
+void order_fwd_bins(Bins& fwd, int K, const std::vector<int>& fa0, const std::vector<int>& frb, int win_ld) {
+  const int nt = (int)fwd.ptr.size() - 1;
+  std::vector<uint32_t> cls[16];
+  for (int t = 0; t < nt; ++t) {
+    const int C0 = (t % fwd.tiles_x) * CPCT_TILE, R0 = (t / fwd.tiles_x) * CPCT_TILE;
+    for (auto& c : cls) c.clear();
+    for (int e = fwd.ptr[t]; e < fwd.ptr[t + 1]; ++e) {
+      const uint32_t id = fwd.ids[e];
+      const size_t sidx = (size_t)(id >> 16) * (K + 1) + (id & 0xffffu);
+      const int ar = fa0[sidx] - C0, br = frb[sidx] - R0;
+      cls[(br * win_ld + ar) & 15].push_back(id);
+    }
+    size_t pos[16] = {0};
+    int e = fwd.ptr[t];
+    while (e < fwd.ptr[t + 1]) {
+      for (int c = 0; c < 16; ++c)
+        if (pos[c] < cls[c].size()) fwd.ids[e++] = cls[c][pos[c]++];
+    }
+  }
+}
+
 // split bins into work items of at most `cap` entries, longest first
 void make_items(const Bins& b, int cap, bool slots, std::vector<int4>& items, std::vector<int4>& split,
                 int* n_slots) {
@@ -367,7 +394,8 @@ void make_items(const Bins& b, int cap, bool slots, std::vector<int4>& items, st
 
 // work items over rounds: at most `cap` rounds per item, longest first; tiles
 // split over several items accumulate into partial-tile slots
-void make_round_items(const Rounds& rd, int cap, std::vector<int4>& items, std::vector<int4>& split, int* n_slots) {
+void make_round_items(const Rounds& rd, int cap, std::vector<int4>& items, std::vector<int4>& split, int* n_slots,
+                      std::vector<int>& item_split) {
   const int nt = (int)rd.tile_ptr.size() - 1;
   items.clear();
   split.clear();
@@ -388,6 +416,17 @@ void make_round_items(const Rounds& rd, int cap, std::vector<int4>& items, std::
   std::stable_sort(items.begin(), items.end(),
                    [](const int4& a, const int4& c) { return (a.z - a.y) > (c.z - c.y); });
   *n_slots = slot;
+  // split index of every item (slots of split k are contiguous from split[k].y)
+  item_split.assign(items.size(), -1);
+  for (size_t i = 0; i < items.size(); ++i) {
+    if (items[i].w < 0) continue;
+    int lo = 0, hi = (int)split.size() - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (split[mid].y <= items[i].w) lo = mid; else hi = mid - 1;
+    }
+    item_split[i] = lo;
+  }
 }
 
 }  // namespace cpct_detail
@@ -561,13 +600,15 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
     cpct_detail::build_bins(n, ns, m, p->G, ray, fb, ab, &fa0, &frb);
     cpct_detail::Rounds rounds;
     cpct_detail::pack_rounds(ab, p->G, fa0, frb, p->K, rounds);
+    cpct_detail::order_fwd_bins(fb, p->K, fa0, frb, CPCT_TILE + CPCT_HALO + 1);
     p->tiles_x_fwd = fb.tiles_x;
     p->tiles_y_fwd = fb.tiles_y;
     p->tiles_x_adj = ab.tiles_x;
     p->tiles_y_adj = ab.tiles_y;
     std::vector<int4> fitems, aitems, fsplit, asplit;
     cpct_detail::make_items(fb, kFwdItemMax, false, fitems, fsplit, nullptr);
-    cpct_detail::make_round_items(rounds, kAdjItemRounds, aitems, asplit, &p->n_slots);
+    std::vector<int> item_split;
+    cpct_detail::make_round_items(rounds, kAdjItemRounds, aitems, asplit, &p->n_slots, item_split);
     p->n_fwd_items = (int)fitems.size();
     p->n_adj_items = (int)aitems.size();
     p->n_split = (int)asplit.size();
@@ -576,6 +617,9 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
     TRY(upload(al, &p->d_adj_items, aitems, stream));
     TRY(upload(al, &p->d_adj_ids, rounds.ids, stream));
     TRY(upload(al, &p->d_split, asplit, stream));
+    TRY(upload(al, &p->d_adj_item_split, item_split, stream));
+    TRY(al((void**)&p->d_split_count, sizeof(int) * std::max<size_t>(1, asplit.size())));
+    TRYC(cudaMemsetAsync(p->d_split_count, 0, sizeof(int) * std::max<size_t>(1, asplit.size()), stream));
     TRY(al((void**)&p->d_partials, sizeof(float2) * (size_t)std::max(1, p->n_slots) * CPCT_TILE * CPCT_TILE));
     // TMA descriptor of the forward extended spectrum (viewed as float32 pairs)
     {

@@ -22,8 +22,9 @@
 //                  packed at plan time into rounds of <= 32 samples with
 //                  disjoint footprints; one warp applies the rounds in order,
 //                  one sample per lane, into a shared-memory tile; no atomics
-//   7. k_adj_reduce  heavy tiles were split into several work items with
-//                  partial tiles; summed here in a fixed order  -> Ax
+//                  heavy tiles are split into several work items that
+//                  write partial tiles; the last one to finish sums them in
+//                  slot order                                   -> Ax
 //   8. k_adj_row   fold the extension (mirror rows, wrapped columns), G-point
 //                  inverse FFT along x, keep X = -N/2..N/2-1    -> H1
 //   9. k_adj_col   Hermitian-symmetrise the rows b = 0..N of two columns,
@@ -38,27 +39,29 @@ using cpct::SmemFFT;
 
 namespace {
 
-constexpr int kE = 32;                 // FFT values per thread
-constexpr int kColFFTs = 4;            // packed column FFTs per CTA (8 columns)
+constexpr int kEcol = 16;              // FFT values per thread, column kernels
+constexpr int kErow = 16;              // FFT values per thread, row and ray kernels
+constexpr int kColFFTs = 2;            // packed column FFTs per CTA (4 columns)
+constexpr int kColHalf = kColFFTs / 2; // float4 loads of 4 real columns per image row
 constexpr int kThreads = 256;          // threads of the row / ray FFT kernels
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
 template <int LOG>
-constexpr int fft_threads() { return (1 << LOG) / kE; }
+constexpr int fft_threads() { return (1 << LOG) / kErow; }
 template <int LOG>
 constexpr int rows_per_cta() { return kThreads / fft_threads<LOG>() > 0 ? kThreads / fft_threads<LOG>() : 1; }
 template <int LOG>
-constexpr size_t fft_smem(int nfft) { return (size_t)nfft * SmemFFT<LOG, kE, -1>::PADN * sizeof(float2); }
+constexpr size_t fft_smem(int nfft) { return (size_t)nfft * SmemFFT<LOG, kErow, -1>::PADN * sizeof(float2); }
 
 // ---------------------------------------------------------------------------
 // 1. forward column transform
 // ---------------------------------------------------------------------------
 template <int LOGG>
-__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
+__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol, 2)
     k_fwd_col(const float* __restrict__ img, const float* __restrict__ dp, float2* __restrict__ H1,
               const float2* __restrict__ tw) {
-  using FFT = SmemFFT<LOGG, kE, -1>;
-  constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kE;
+  using FFT = SmemFFT<LOGG, kEcol, -1>;
+  constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kEcol;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * (2 * kColFFTs);
@@ -69,8 +72,8 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
   }
   // deapodized columns: FFT f packs columns q0+2f (real part), q0+2f+1 (imag)
 #pragma unroll
-  for (int idx = tid; idx < 2 * N; idx += nthr) {
-    const int p = idx >> 1, h = idx & 1;
+  for (int idx = tid; idx < kColHalf * N; idx += nthr) {
+    const int p = idx / kColHalf, h = idx % kColHalf;
     const float4 v = *reinterpret_cast<const float4*>(img + (size_t)p * N + q0 + 4 * h);
     const float4 d = *reinterpret_cast<const float4*>(dp + q0 + 4 * h);
     const float cp = dp[p];
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
 template <int LOGG>
 __global__ void __launch_bounds__(kThreads)
     k_fwd_row(const float2* __restrict__ H1, float2* __restrict__ Hx, const float2* __restrict__ tw, int ldh) {
-  using FFT = SmemFFT<LOGG, kE, -1>;
+  using FFT = SmemFFT<LOGG, kErow, -1>;
   constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = rows_per_cta<LOGG>();
   extern __shared__ float2 sm[];
   const int f = threadIdx.x / T, t = threadIdx.x % T;
@@ -141,70 +144,121 @@ struct FwdInterpArgs {
 constexpr int kWinR = CPCT_TILE + CPCT_HALO;      // 37 rows
 constexpr int kWinC = CPCT_TILE + CPCT_HALO + 1;  // 38 complex columns (304 B rows)
 
+// interpolate one polar sample from the staged window (or, if the bin does not
+// hold it -- never expected -- from global memory, recording the mismatch)
+__device__ __forceinline__ void interp_sample(const FwdInterpArgs& a, const float2* win, int C0, int R0, uint32_t id,
+                                              float4 r) {
+  const int j = (int)(id >> 16), k = (int)(id & 0xffffu);
+  int fu, fv;
+  float zu, zv;
+  split_coord((float)k, r.x, r.y, fu, zu);
+  split_coord((float)k, r.z, r.w, fv, zv);
+  const int a0 = (fu - 2) & (a.G - 1);
+  float wu[CPCT_W], wv[CPCT_W];
+  kb_weights(a.poly, zu, wu);
+  kb_weights(a.poly, zv, wv);
+  const int ar = a0 - C0, br = fv - R0;
+  float2 acc = make_float2(0.f, 0.f);
+  if ((unsigned)ar < (unsigned)CPCT_TILE && (unsigned)br < (unsigned)CPCT_TILE) {
+#pragma unroll
+    for (int rr = 0; rr < CPCT_W; ++rr) {
+      const float2* row = win + (br + rr) * kWinC + ar;
+      float2 rs = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < CPCT_W; ++c) {
+        const float2 h = row[c];
+        rs.x = fmaf(wu[c], h.x, rs.x);
+        rs.y = fmaf(wu[c], h.y, rs.y);
+      }
+      acc.x = fmaf(wv[rr], rs.x, acc.x);
+      acc.y = fmaf(wv[rr], rs.y, acc.y);
+    }
+  } else {
+    atomicOr(a.err, CPCT_ERR_BIN);
+    for (int rr = 0; rr < CPCT_W; ++rr) {
+      const float2* row = a.Hx + (size_t)(fv + rr) * a.ldh + a0;
+      float2 rs = make_float2(0.f, 0.f);
+      for (int c = 0; c < CPCT_W; ++c) {
+        rs.x = fmaf(wu[c], row[c].x, rs.x);
+        rs.y = fmaf(wu[c], row[c].y, rs.y);
+      }
+      acc.x = fmaf(wv[rr], rs.x, acc.x);
+      acc.y = fmaf(wv[rr], rs.y, acc.y);
+    }
+  }
+  a.Q[(size_t)j * a.ldq + k] = acc;
+}
+
+// Persistent CTAs walk the work items (tile, sample range) round robin; the
+// 37x38 grid window of the next item is copied by TMA into the second buffer
+// while the current one is interpolated, and the next item's first sample id
+// and ray are prefetched into registers.
 __global__ void __launch_bounds__(256)
-    k_fwd_interp(const __grid_constant__ CUtensorMap tmap, const FwdInterpArgs a) {
-  __shared__ __align__(128) float2 win[kWinR * kWinC];
-  __shared__ __align__(8) uint64_t bar;
-  const int4 it = a.items[blockIdx.x];
-  const int C0 = (it.x % a.tiles_x) * CPCT_TILE, R0 = (it.x / a.tiles_x) * CPCT_TILE;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+    k_fwd_interp(const __grid_constant__ CUtensorMap tmap, const FwdInterpArgs a, int n_items) {
+  __shared__ __align__(128) float2 win[2][kWinR * kWinC];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar, (uint32_t)(kWinR * kWinC * sizeof(float2)));
-    tma_load_2d(win, &tmap, 2 * C0, R0, &bar);
+  auto issue = [&](int item, int buf) {
+    const int4 itn = a.items[item];
+    const int c0 = (itn.x % a.tiles_x) * CPCT_TILE, r0 = (itn.x / a.tiles_x) * CPCT_TILE;
+    mbar_arrive_expect_tx(&bar[buf], (uint32_t)(kWinR * kWinC * sizeof(float2)));
+    tma_load_2d(win[buf], &tmap, 2 * c0, r0, &bar[buf]);
+  };
+  int item = blockIdx.x;
+  if (tid == 0 && item < n_items) issue(item, 0);
+  uint32_t phase0 = 0, phase1 = 0;
+  // prefetched first sample of the current item
+  uint32_t pid = 0xffffffffu;
+  float4 pray = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (item < n_items) {
+    const int4 it0 = a.items[item];
+    if (it0.y + tid < it0.z) {
+      pid = a.ids[it0.y + tid];
+      pray = a.ray[pid >> 16];
+    }
   }
-  if (!mbar_wait_bounded(&bar, 0, kWaitCycles)) {
-    if (threadIdx.x == 0) atomicOr(a.err, CPCT_ERR_TIMEOUT);
-    mbar_wait_bounded(&bar, 0, kWaitCycles / 4);  // let an in-flight copy land before exiting
-    return;
-  }
-  for (int idx = it.y + threadIdx.x; idx < it.z; idx += blockDim.x) {
-    const uint32_t id = a.ids[idx];
-    const int j = (int)(id >> 16), k = (int)(id & 0xffffu);
-    const float4 r = a.ray[j];
-    int fu, fv;
-    float zu, zv;
-    split_coord((float)k, r.x, r.y, fu, zu);
-    split_coord((float)k, r.z, r.w, fv, zv);
-    const int a0 = (fu - 2) & (a.G - 1);
-    float wu[CPCT_W], wv[CPCT_W];
-    kb_weights(a.poly, zu, wu);
-    kb_weights(a.poly, zv, wv);
-    const int ar = a0 - C0, br = fv - R0;
-    float2 acc = make_float2(0.f, 0.f);
-    if ((unsigned)ar < (unsigned)CPCT_TILE && (unsigned)br < (unsigned)CPCT_TILE) {
-#pragma unroll
-      for (int rr = 0; rr < CPCT_W; ++rr) {
-        const float2* row = win + (br + rr) * kWinC + ar;
-        float2 rs = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int c = 0; c < CPCT_W; ++c) {
-          const float2 h = row[c];
-          rs.x = fmaf(wu[c], h.x, rs.x);
-          rs.y = fmaf(wu[c], h.y, rs.y);
-        }
-        acc.x = fmaf(wv[rr], rs.x, acc.x);
-        acc.y = fmaf(wv[rr], rs.y, acc.y);
-      }
-    } else {
-      // the sample is not in this bin (host/device coordinate mismatch):
-      // record it and read the footprint from global memory instead
-      atomicOr(a.err, CPCT_ERR_BIN);
-      for (int rr = 0; rr < CPCT_W; ++rr) {
-        const float2* row = a.Hx + (size_t)(fv + rr) * a.ldh + a0;
-        float2 rs = make_float2(0.f, 0.f);
-        for (int c = 0; c < CPCT_W; ++c) {
-          rs.x = fmaf(wu[c], row[c].x, rs.x);
-          rs.y = fmaf(wu[c], row[c].y, rs.y);
-        }
-        acc.x = fmaf(wv[rr], rs.x, acc.x);
-        acc.y = fmaf(wv[rr], rs.y, acc.y);
+  for (int iter = 0; item < n_items; ++iter, item += gridDim.x) {
+    const int cur = iter & 1;
+    const int next = item + gridDim.x;
+    if (tid == 0 && next < n_items) issue(next, cur ^ 1);
+    const int4 it = a.items[item];
+    // prefetch the next item's first sample before waiting
+    uint32_t nid = 0xffffffffu;
+    float4 nray = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (next < n_items) {
+      const int4 itn = a.items[next];
+      if (itn.y + tid < itn.z) {
+        nid = a.ids[itn.y + tid];
+        nray = a.ray[nid >> 16];
       }
     }
-    a.Q[(size_t)j * a.ldq + k] = acc;
+    const uint32_t ph = cur ? phase1 : phase0;
+    const bool ok = mbar_wait_bounded(&bar[cur], ph, kWaitCycles);
+    if (cur) phase1 ^= 1u; else phase0 ^= 1u;
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) {
+        atomicOr(a.err, CPCT_ERR_TIMEOUT);
+        // let copies in flight land before the CTA exits
+        mbar_wait_bounded(&bar[cur], ph, kWaitCycles / 4);
+        if (next < n_items) mbar_wait_bounded(&bar[cur ^ 1], cur ? phase0 : phase1, kWaitCycles / 4);
+      }
+      return;
+    }
+    const int C0 = (it.x % a.tiles_x) * CPCT_TILE, R0 = (it.x / a.tiles_x) * CPCT_TILE;
+    if (pid != 0xffffffffu) interp_sample(a, win[cur], C0, R0, pid, pray);
+    for (int idx = it.y + tid + (int)blockDim.x; idx < it.z; idx += blockDim.x) {
+      const uint32_t id = a.ids[idx];
+      interp_sample(a, win[cur], C0, R0, id, a.ray[id >> 16]);
+    }
+    pid = nid;
+    pray = nray;
+    __syncthreads();  // buffer `cur` is free for the copy issued next iteration
   }
 }
 
@@ -214,7 +268,7 @@ __global__ void __launch_bounds__(256)
 template <int LOGNS>
 __global__ void __launch_bounds__(kThreads)
     k_fwd_ray(const float2* __restrict__ Q, float* __restrict__ sino, const float2* __restrict__ tw, int M, int ldq) {
-  using FFT = SmemFFT<LOGNS, kE, +1>;
+  using FFT = SmemFFT<LOGNS, kErow, +1>;
   constexpr int NS = 1 << LOGNS, T = FFT::T, PPC = rows_per_cta<LOGNS>(), K = NS / 2;
   extern __shared__ float2 sm[];
   const int f = threadIdx.x / T, t = threadIdx.x % T;
@@ -249,7 +303,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int LOGNS>
 __global__ void __launch_bounds__(kThreads)
     k_adj_ray(const float* __restrict__ sino, float2* __restrict__ Q, const float2* __restrict__ tw, int M, int ldq) {
-  using FFT = SmemFFT<LOGNS, kE, -1>;
+  using FFT = SmemFFT<LOGNS, kErow, -1>;
   constexpr int NS = 1 << LOGNS, T = FFT::T, PPC = rows_per_cta<LOGNS>(), K = NS / 2;
   extern __shared__ float2 sm[];
   const int f = threadIdx.x / T, t = threadIdx.x % T;
@@ -284,6 +338,9 @@ struct AdjSpreadArgs {
   const float2* Qt;
   float2* Ax;
   float2* partials;
+  const int* item_split;   // per item: index into split[] or -1
+  const int4* split;       // (tile, first slot, n slots, 0)
+  int* split_count;        // per split tile: finished items (reset by the last)
   int* err;
   int G, ldq, ldh, tiles_x, ext_rows;
   KBPoly poly;
@@ -375,28 +432,28 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
     float2* dst = a.partials + (size_t)it.w * CPCT_TILE * CPCT_TILE;
     for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32)
       dst[i] = acc[(i / CPCT_TILE + CPCT_HALO) * kRLd + i % CPCT_TILE + CPCT_HALO];
+    // the last item of a split tile to finish sums all its partial tiles in
+    // slot order (the same order whichever item finishes last) and resets
+    // the tile's counter for the next call
+    const int si = a.item_split[blockIdx.x];
+    const int4 sp = a.split[si];
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(a.split_count + si, 1) == sp.z - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence();
+      const float2* src = a.partials + (size_t)sp.y * CPCT_TILE * CPCT_TILE;
+      for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32) {
+        float2 sum = make_float2(0.f, 0.f);
+        for (int q = 0; q < sp.z; ++q) sum = cadd(sum, __ldcg(src + (size_t)q * CPCT_TILE * CPCT_TILE + i));
+        const int gr = TR + i / CPCT_TILE, gc = TC + i % CPCT_TILE;
+        if (gr < a.ext_rows && gc < a.ldh) a.Ax[(size_t)gr * a.ldh + gc] = sum;
+      }
+      if (lane == 0) a.split_count[si] = 0;
+    }
   }
-}
-
-// 7. fixed-order sum of the partial tiles of split bins (slot order q = 0, 1, ...)
-__global__ void __launch_bounds__(1024) k_adj_reduce(const int4* __restrict__ split, const float2* __restrict__ partials,
-                                                    float2* __restrict__ Ax, int tiles_x, int ldh, int ext_rows) {
-  const int4 s = split[blockIdx.x];
-  const int TC = (s.x % tiles_x) * CPCT_TILE, TR = (s.x / tiles_x) * CPCT_TILE;
-  const int i = threadIdx.x;
-  const float2* src = partials + (size_t)s.y * CPCT_TILE * CPCT_TILE + i;
-  float2 acc = make_float2(0.f, 0.f);
-  int q = 0;
-  for (; q + 4 <= s.z; q += 4) {
-    const float2 v0 = src[(size_t)(q + 0) * CPCT_TILE * CPCT_TILE];
-    const float2 v1 = src[(size_t)(q + 1) * CPCT_TILE * CPCT_TILE];
-    const float2 v2 = src[(size_t)(q + 2) * CPCT_TILE * CPCT_TILE];
-    const float2 v3 = src[(size_t)(q + 3) * CPCT_TILE * CPCT_TILE];
-    acc = cadd(cadd(cadd(cadd(acc, v0), v1), v2), v3);
-  }
-  for (; q < s.z; ++q) acc = cadd(acc, src[(size_t)q * CPCT_TILE * CPCT_TILE]);
-  const int gr = TR + i / CPCT_TILE, gc = TC + i % CPCT_TILE;
-  if (gr < ext_rows && gc < ldh) Ax[(size_t)gr * ldh + gc] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -411,7 +468,7 @@ __device__ __forceinline__ float2 wrapped(const float2* __restrict__ row, int a,
 template <int LOGG>
 __global__ void __launch_bounds__(kThreads)
     k_adj_row(const float2* __restrict__ Ax, float2* __restrict__ H1, const float2* __restrict__ tw, int ldh) {
-  using FFT = SmemFFT<LOGG, kE, +1>;
+  using FFT = SmemFFT<LOGG, kErow, +1>;
   constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = rows_per_cta<LOGG>();
   extern __shared__ float2 sm[];
   const int f = threadIdx.x / T, t = threadIdx.x % T;
@@ -442,11 +499,11 @@ __global__ void __launch_bounds__(kThreads)
 // 9. adjoint column transform: Re of the inverse transform over b = 0..N
 // ---------------------------------------------------------------------------
 template <int LOGG>
-__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
+__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol, 2)
     k_adj_col(const float2* __restrict__ H1, const float* __restrict__ dp, float* __restrict__ img,
               const float2* __restrict__ tw) {
-  using FFT = SmemFFT<LOGG, kE, +1>;
-  constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kE;
+  using FFT = SmemFFT<LOGG, kEcol, +1>;
+  constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kEcol;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * (2 * kColFFTs);
@@ -464,8 +521,8 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
   }
   __syncthreads();
   FFT::run(sm + (tid / FFT::T) * FFT::PADN, tw, tid % FFT::T);
-  for (int idx = tid; idx < 2 * N; idx += nthr) {
-    const int p = idx >> 1, h = idx & 1;
+  for (int idx = tid; idx < kColHalf * N; idx += nthr) {
+    const int p = idx / kColHalf, h = idx % kColHalf;
     const int pos = (p - N / 2) & (G - 1);
     const float2 w0 = sm[(2 * h) * FFT::PADN + fpad(pos)];
     const float2 w1 = sm[(2 * h + 1) * FFT::PADN + fpad(pos)];
@@ -479,8 +536,17 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kE)
 // ---------------------------------------------------------------------------
 // size dispatch
 // ---------------------------------------------------------------------------
+template <class F>
+void max_carveout(F f) {
+  cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
 template <int LOGG>
 int set_attr_G() {
+  max_carveout(k_fwd_col<LOGG>);
+  max_carveout(k_adj_col<LOGG>);
+  max_carveout(k_fwd_row<LOGG>);
+  max_carveout(k_adj_row<LOGG>);
   if (cudaFuncSetAttribute(k_fwd_col<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(kColFFTs)) != cudaSuccess) return CPCT_ECUDA;
   if (cudaFuncSetAttribute(k_adj_col<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(kColFFTs)) != cudaSuccess) return CPCT_ECUDA;
   if (cudaFuncSetAttribute(k_fwd_row<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(rows_per_cta<LOGG>())) != cudaSuccess) return CPCT_ECUDA;
@@ -489,6 +555,8 @@ int set_attr_G() {
 }
 template <int LOGNS>
 int set_attr_Ns() {
+  max_carveout(k_fwd_ray<LOGNS>);
+  max_carveout(k_adj_ray<LOGNS>);
   if (cudaFuncSetAttribute(k_fwd_ray<LOGNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGNS>(rows_per_cta<LOGNS>())) != cudaSuccess) return CPCT_ECUDA;
   if (cudaFuncSetAttribute(k_adj_ray<LOGNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGNS>(rows_per_cta<LOGNS>())) != cudaSuccess) return CPCT_ECUDA;
   return CPCT_OK;
@@ -498,11 +566,11 @@ template <int LOGG>
 void launch_fwd_G(cpct_plan* p, const float* img, cudaStream_t s) {
   constexpr int G = 1 << LOGG;
   cpct_prof_begin(p, KID_FWD_COL, s);
-  k_fwd_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kE, fft_smem<LOGG>(kColFFTs), s>>>(img, p->d_deapod, p->d_H1, p->d_twG);
+  k_fwd_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kEcol, fft_smem<LOGG>(kColFFTs), s>>>(img, p->d_deapod, p->d_H1, p->d_twG);
   cpct_prof_end(p, KID_FWD_COL, s);
   constexpr int RPC = rows_per_cta<LOGG>();
   cpct_prof_begin(p, KID_FWD_ROW, s);
-  k_fwd_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kE), fft_smem<LOGG>(RPC), s>>>(p->d_H1, p->d_Hx, p->d_twG, p->ldh);
+  k_fwd_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kErow), fft_smem<LOGG>(RPC), s>>>(p->d_H1, p->d_Hx, p->d_twG, p->ldh);
   cpct_prof_end(p, KID_FWD_ROW, s);
 }
 template <int LOGNS>
@@ -510,7 +578,7 @@ void launch_fwd_Ns(cpct_plan* p, float* sino, cudaStream_t s) {
   constexpr int NS = 1 << LOGNS, PPC = rows_per_cta<LOGNS>();
   const int pairs = (p->m + 1) / 2;
   cpct_prof_begin(p, KID_FWD_RAY, s);
-  k_fwd_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kE), fft_smem<LOGNS>(PPC), s>>>(p->d_Q, sino, p->d_twNs, p->m, p->ldq);
+  k_fwd_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kErow), fft_smem<LOGNS>(PPC), s>>>(p->d_Q, sino, p->d_twNs, p->m, p->ldq);
   cpct_prof_end(p, KID_FWD_RAY, s);
 }
 template <int LOGNS>
@@ -518,7 +586,7 @@ void launch_adj_Ns(cpct_plan* p, const float* sino, cudaStream_t s) {
   constexpr int NS = 1 << LOGNS, PPC = rows_per_cta<LOGNS>();
   const int pairs = (p->m + 1) / 2;
   cpct_prof_begin(p, KID_ADJ_RAY, s);
-  k_adj_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kE), fft_smem<LOGNS>(PPC), s>>>(sino, p->d_Q, p->d_twNs, p->m, p->ldq);
+  k_adj_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kErow), fft_smem<LOGNS>(PPC), s>>>(sino, p->d_Q, p->d_twNs, p->m, p->ldq);
   cpct_prof_end(p, KID_ADJ_RAY, s);
 }
 template <int LOGG>
@@ -526,10 +594,10 @@ void launch_adj_G(cpct_plan* p, float* img, cudaStream_t s) {
   constexpr int G = 1 << LOGG;
   constexpr int RPC = rows_per_cta<LOGG>();
   cpct_prof_begin(p, KID_ADJ_ROW, s);
-  k_adj_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kE), fft_smem<LOGG>(RPC), s>>>(p->d_Ax, p->d_H1, p->d_twG, p->ldh);
+  k_adj_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kErow), fft_smem<LOGG>(RPC), s>>>(p->d_Ax, p->d_H1, p->d_twG, p->ldh);
   cpct_prof_end(p, KID_ADJ_ROW, s);
   cpct_prof_begin(p, KID_ADJ_COL, s);
-  k_adj_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kE, fft_smem<LOGG>(kColFFTs), s>>>(p->d_H1, p->d_deapod, img, p->d_twG);
+  k_adj_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kEcol, fft_smem<LOGG>(kColFFTs), s>>>(p->d_H1, p->d_deapod, img, p->d_twG);
   cpct_prof_end(p, KID_ADJ_COL, s);
 }
 
@@ -589,7 +657,16 @@ int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_
   a.poly = p->poly;
   if (p->n_fwd_items > 0) {
     cpct_prof_begin(p, KID_FWD_INTERP, s);
-    k_fwd_interp<<<p->n_fwd_items, 256, 0, s>>>(p->tmap_Hx, a);
+    if (p->fwd_interp_grid <= 0) {
+      // persistent grid: every CTA resident at once
+      int dev = 0, sms = 1, per_sm = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_interp, 256, 0);
+      p->fwd_interp_grid = std::max(1, sms * std::max(1, per_sm));
+    }
+    const int grid = std::min(p->n_fwd_items, p->fwd_interp_grid);
+    k_fwd_interp<<<grid, 256, 0, s>>>(p->tmap_Hx, a, p->n_fwd_items);
     cpct_prof_end(p, KID_FWD_INTERP, s);
   }
 #define FN(L) launch_fwd_Ns<L>(p, d_sino, s)
@@ -609,6 +686,9 @@ int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_
   a.Qt = p->d_Q;
   a.Ax = p->d_Ax;
   a.partials = p->d_partials;
+  a.item_split = p->d_adj_item_split;
+  a.split = p->d_split;
+  a.split_count = p->d_split_count;
   a.err = p->d_err;
   a.G = p->G;
   a.ldq = p->ldq;
@@ -621,11 +701,7 @@ int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_
     k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
     cpct_prof_end(p, KID_ADJ_SPREAD, s);
   }
-  if (p->n_split > 0) {
-    cpct_prof_begin(p, KID_ADJ_REDUCE, s);
-    k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, p->d_partials, p->d_Ax, p->tiles_x_adj, p->ldh, p->ext_rows);
-    cpct_prof_end(p, KID_ADJ_REDUCE, s);
-  }
+
 #define AG(L) launch_adj_G<L>(p, d_img, s)
   CPCT_DISPATCH_G(p->logG, AG);
 #undef AG
