@@ -143,6 +143,10 @@ struct FwdInterpArgs {
 
 constexpr int kWinR = CPCT_TILE + CPCT_HALO;      // 37 rows
 constexpr int kWinC = CPCT_TILE + CPCT_HALO + 1;  // 38 complex columns (304 B rows)
+// buffer stride: a TMA tensor copy into shared memory must start on a 128-byte
+// boundary, so each window buffer is padded to a multiple of 128 bytes
+constexpr int kWinStride = ((kWinR * kWinC * (int)sizeof(float2) + 127) / 128) * 128 / (int)sizeof(float2);
+static_assert((kWinStride * sizeof(float2)) % 128 == 0, "window buffers must be 128-byte aligned");
 
 // interpolate one polar sample from the staged window (or, if the bin does not
 // hold it -- never expected -- from global memory, recording the mismatch)
@@ -195,7 +199,7 @@ __device__ __forceinline__ void interp_sample(const FwdInterpArgs& a, const floa
 // and ray are prefetched into registers.
 __global__ void __launch_bounds__(256)
     k_fwd_interp(const __grid_constant__ CUtensorMap tmap, const FwdInterpArgs a, int n_items) {
-  __shared__ __align__(128) float2 win[2][kWinR * kWinC];
+  __shared__ __align__(128) float2 win[2][kWinStride];
   __shared__ __align__(8) uint64_t bar[2];
   const int tid = threadIdx.x;
   if (tid == 0) {
