@@ -84,8 +84,6 @@ struct cpct_plan {
   float2* d_partials;       // n_slots x 32 x 32 partial tiles (split heavy tiles)
   int n_split;
   int4* d_split;            // (tile, first slot, n slots, 0)
-  int* d_adj_item_split;    // per adjoint item: index into d_split or -1
-  int* d_split_count;       // per split tile: finished items of the running call
   // staging for the host-buffer entry points
   float* d_stage_img;
   float* d_stage_sino;

@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kPolyDeg = 9;            // Chebyshev interpolation degree per tap
 constexpr int kFwdItemMax = 1024;      // samples per forward gather work item
-constexpr int kAdjItemRounds = 32;     // conflict-free rounds per adjoint spread work item
+constexpr int kAdjItemRounds = 64;     // conflict-free rounds per adjoint spread work item
 
 // ---------------------------------------------------------------------------
 // FP64 device builders (kernel table, deapodization, twiddles)
@@ -171,8 +171,7 @@ void free_plan(cpct_plan* p) {
   cpct_prof_free(p);
   void* ptrs[] = {p->d_poly64, p->d_ray, p->d_deapod, p->d_twG, p->d_twNs, p->d_Hx, p->d_Ax, p->d_H1,
                   p->d_Q, p->d_fwd_items, p->d_fwd_ids, p->d_adj_items, p->d_adj_ids, p->d_partials,
-                  p->d_split, p->d_stage_img, p->d_stage_sino, p->d_err, p->d_adj_item_split,
-                  p->d_split_count};
+                  p->d_split, p->d_stage_img, p->d_stage_sino, p->d_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -617,9 +616,6 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
     TRY(upload(al, &p->d_adj_items, aitems, stream));
     TRY(upload(al, &p->d_adj_ids, rounds.ids, stream));
     TRY(upload(al, &p->d_split, asplit, stream));
-    TRY(upload(al, &p->d_adj_item_split, item_split, stream));
-    TRY(al((void**)&p->d_split_count, sizeof(int) * std::max<size_t>(1, asplit.size())));
-    TRYC(cudaMemsetAsync(p->d_split_count, 0, sizeof(int) * std::max<size_t>(1, asplit.size()), stream));
     TRY(al((void**)&p->d_partials, sizeof(float2) * (size_t)std::max(1, p->n_slots) * CPCT_TILE * CPCT_TILE));
     // TMA descriptor of the forward extended spectrum (viewed as float32 pairs)
     {

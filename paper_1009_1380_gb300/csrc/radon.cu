@@ -22,9 +22,9 @@
 //                  packed at plan time into rounds of <= 32 samples with
 //                  disjoint footprints; one warp applies the rounds in order,
 //                  one sample per lane, into a shared-memory tile; no atomics
-//                  heavy tiles are split into several work items that
-//                  write partial tiles; the last one to finish sums them in
-//                  slot order                                   -> Ax
+//   7. k_adj_reduce  the few heavy tiles (near the origin, where all rays
+//                  meet) are split into several work items writing partial
+//                  tiles, summed here in a fixed order           -> Ax
 //   8. k_adj_row   fold the extension (mirror rows, wrapped columns), G-point
 //                  inverse FFT along x, keep X = -N/2..N/2-1    -> H1
 //   9. k_adj_col   Hermitian-symmetrise the rows b = 0..N of two columns,
@@ -39,9 +39,9 @@ using cpct::SmemFFT;
 
 namespace {
 
-constexpr int kEcol = 16;              // FFT values per thread, column kernels
+constexpr int kEcol = 32;              // FFT values per thread, column kernels
 constexpr int kErow = 16;              // FFT values per thread, row and ray kernels
-constexpr int kColFFTs = 2;            // packed column FFTs per CTA (4 columns)
+constexpr int kColFFTs = 4;            // packed column FFTs per CTA (8 columns)
 constexpr int kColHalf = kColFFTs / 2; // float4 loads of 4 real columns per image row
 constexpr int kThreads = 256;          // threads of the row / ray FFT kernels
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
@@ -57,7 +57,7 @@ constexpr size_t fft_smem(int nfft) { return (size_t)nfft * SmemFFT<LOG, kErow, 
 // 1. forward column transform
 // ---------------------------------------------------------------------------
 template <int LOGG>
-__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol, 2)
+__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
     k_fwd_col(const float* __restrict__ img, const float* __restrict__ dp, float2* __restrict__ H1,
               const float2* __restrict__ tw) {
   using FFT = SmemFFT<LOGG, kEcol, -1>;
@@ -342,9 +342,6 @@ struct AdjSpreadArgs {
   const float2* Qt;
   float2* Ax;
   float2* partials;
-  const int* item_split;   // per item: index into split[] or -1
-  const int4* split;       // (tile, first slot, n slots, 0)
-  int* split_count;        // per split tile: finished items (reset by the last)
   int* err;
   int G, ldq, ldh, tiles_x, ext_rows;
   KBPoly poly;
@@ -436,28 +433,27 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
     float2* dst = a.partials + (size_t)it.w * CPCT_TILE * CPCT_TILE;
     for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32)
       dst[i] = acc[(i / CPCT_TILE + CPCT_HALO) * kRLd + i % CPCT_TILE + CPCT_HALO];
-    // the last item of a split tile to finish sums all its partial tiles in
-    // slot order (the same order whichever item finishes last) and resets
-    // the tile's counter for the next call
-    const int si = a.item_split[blockIdx.x];
-    const int4 sp = a.split[si];
-    __threadfence();
-    __syncwarp();
-    int last = 0;
-    if (lane == 0) last = atomicAdd(a.split_count + si, 1) == sp.z - 1;
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last) {
-      __threadfence();
-      const float2* src = a.partials + (size_t)sp.y * CPCT_TILE * CPCT_TILE;
-      for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32) {
-        float2 sum = make_float2(0.f, 0.f);
-        for (int q = 0; q < sp.z; ++q) sum = cadd(sum, __ldcg(src + (size_t)q * CPCT_TILE * CPCT_TILE + i));
-        const int gr = TR + i / CPCT_TILE, gc = TC + i % CPCT_TILE;
-        if (gr < a.ext_rows && gc < a.ldh) a.Ax[(size_t)gr * a.ldh + gc] = sum;
-      }
-      if (lane == 0) a.split_count[si] = 0;
-    }
   }
+}
+
+// 7. fixed-order sum of the partial tiles of split tiles (slot order q = 0, 1, ...)
+__global__ void __launch_bounds__(CPCT_TILE * CPCT_TILE)
+    k_adj_reduce(const int4* __restrict__ split, const float2* __restrict__ partials, float2* __restrict__ Ax,
+                 int tiles_x, int ldh, int ext_rows) {
+  const int4 sp = split[blockIdx.x];
+  const int TC = (sp.x % tiles_x) * CPCT_TILE, TR = (sp.x / tiles_x) * CPCT_TILE;
+  const int i = threadIdx.x;
+  const float2* src = partials + (size_t)sp.y * CPCT_TILE * CPCT_TILE + i;
+  constexpr size_t S = CPCT_TILE * CPCT_TILE;
+  float2 sum = make_float2(0.f, 0.f);
+  int q = 0;
+  for (; q + 4 <= sp.z; q += 4) {
+    const float2 v0 = src[(q + 0) * S], v1 = src[(q + 1) * S], v2 = src[(q + 2) * S], v3 = src[(q + 3) * S];
+    sum = cadd(cadd(cadd(cadd(sum, v0), v1), v2), v3);
+  }
+  for (; q < sp.z; ++q) sum = cadd(sum, src[q * S]);
+  const int gr = TR + i / CPCT_TILE, gc = TC + i % CPCT_TILE;
+  if (gr < ext_rows && gc < ldh) Ax[(size_t)gr * ldh + gc] = sum;
 }
 
 // ---------------------------------------------------------------------------
@@ -503,7 +499,7 @@ __global__ void __launch_bounds__(kThreads)
 // 9. adjoint column transform: Re of the inverse transform over b = 0..N
 // ---------------------------------------------------------------------------
 template <int LOGG>
-__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol, 2)
+__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
     k_adj_col(const float2* __restrict__ H1, const float* __restrict__ dp, float* __restrict__ img,
               const float2* __restrict__ tw) {
   using FFT = SmemFFT<LOGG, kEcol, +1>;
@@ -690,9 +686,6 @@ int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_
   a.Qt = p->d_Q;
   a.Ax = p->d_Ax;
   a.partials = p->d_partials;
-  a.item_split = p->d_adj_item_split;
-  a.split = p->d_split;
-  a.split_count = p->d_split_count;
   a.err = p->d_err;
   a.G = p->G;
   a.ldq = p->ldq;
@@ -704,6 +697,12 @@ int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_
     cpct_prof_begin(p, KID_ADJ_SPREAD, s);
     k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
     cpct_prof_end(p, KID_ADJ_SPREAD, s);
+  }
+  if (p->n_split > 0) {
+    cpct_prof_begin(p, KID_ADJ_REDUCE, s);
+    k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, p->d_partials, p->d_Ax, p->tiles_x_adj,
+                                                             p->ldh, p->ext_rows);
+    cpct_prof_end(p, KID_ADJ_REDUCE, s);
   }
 
 #define AG(L) launch_adj_G<L>(p, d_img, s)
