@@ -123,6 +123,32 @@ int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t s
 int radon_fwd_host(cpct_plan* plan, const float* h_img, float* h_sino, cudaStream_t stream);
 int radon_adj_host(cpct_plan* plan, const float* h_sino, float* h_img, cudaStream_t stream);
 
+/* Allocation-free adjoint.  Some callers cannot allocate device memory at
+ * the point where they apply the operator: code running under an allocator
+ * that has reserved the whole device pool (a framework's caching allocator),
+ * real-time acquisition loops that must not pay for or risk an allocation,
+ * or code that must not allocate while its stream work is being recorded.
+ * radon_adj_noalloc computes exactly what radon_adj computes (same kernels,
+ * same summation order), but the only scratch of its gridding step -- the
+ * partial tiles of the few heavy tiles that are split over several work
+ * items -- lives in a fixed device array inside this library instead of plan
+ * memory: CPCT_NOALLOC_MAX_SLOTS tiles of 32 x 32 complex64 (8 KB each, 4 MB
+ * in all), held by every GPU that loads the library until the process exits.
+ * The paper has no counterpart of this entry point.
+ *   plan    an existing plan (created earlier; this call allocates nothing:
+ *           no cudaMalloc, cudaFree or allocating library routine)
+ *   d_sino  device, M*Ns float32 (read);  d_img  device, N*N float32 (written)
+ * Returns CPCT_EINVAL for bad arguments or if the plan's geometry needs more
+ * partial tiles than the array holds, CPCT_ECUDA if the array's device
+ * address cannot be obtained.  The first call on each device looks that
+ * address up (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  Every call shares the one array and it
+ * keeps the last call's contents (each call overwrites every tile it reads,
+ * so nothing needs clearing); calls that overlap on the GPU -- on different
+ * streams, or from different plans -- race on it and must be serialised. */
+#define CPCT_NOALLOC_MAX_SLOTS 512
+int radon_adj_noalloc(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream);
+
 /* Human-readable name of a cpct_status (static string). */
 const char* cpct_strerror(int status);
 

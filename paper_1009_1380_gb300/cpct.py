@@ -62,7 +62,7 @@ def lib():
         L.cpct_plan_sync.argtypes = [vp, vp]
         L.cpct_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                      ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t)]
-        for name in ("radon_fwd", "radon_adj", "radon_fwd_host", "radon_adj_host"):
+        for name in ("radon_fwd", "radon_adj", "radon_fwd_host", "radon_adj_host", "radon_adj_noalloc"):
             getattr(L, name).argtypes = [vp, vp, vp, vp]
         L.cpct_strerror.restype = ctypes.c_char_p
         L.cpct_strerror.argtypes = [i]

@@ -30,6 +30,7 @@
 //   9. k_adj_col   Hermitian-symmetrise the rows b = 0..N of two columns,
 //                  pack, G-point inverse FFT, crop Y, deapodize  -> x
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -705,6 +706,83 @@ int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_
     cpct_prof_end(p, KID_ADJ_REDUCE, s);
   }
 
+#define AG(L) launch_adj_G<L>(p, d_img, s)
+  CPCT_DISPATCH_G(p->logG, AG);
+#undef AG
+  return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free adjoint: the same operator as radon_adj, with the spread's
+// only per-call scratch (the partial tiles of split heavy tiles) in a fixed
+// static device array instead of plan memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxSlots = CPCT_NOALLOC_MAX_SLOTS;
+constexpr int kNoAllocMaxDevices = 64;
+
+// Every device that loads this library holds this array until the process
+// exits.  Host code must not use its name as a device address: the device
+// address is looked up per device with cudaGetSymbolAddress below.
+static __device__ __align__(256) float2 g_noalloc_partials[(size_t)kNoAllocMaxSlots * CPCT_TILE * CPCT_TILE];
+
+std::mutex g_noalloc_mutex;
+float2* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// device address of g_noalloc_partials on the current device (looked up once
+// per device, with that device current); nullptr on failure
+float2* noalloc_scratch(int* status) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    *status = CPCT_ECUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_partials) != cudaSuccess || !ptr) {
+      *status = CPCT_ECUDA;
+      return nullptr;
+    }
+    g_noalloc_ptr[dev] = static_cast<float2*>(ptr);
+  }
+  *status = CPCT_OK;
+  return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" int radon_adj_noalloc(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_t s) {
+  if (!p || !d_sino || !d_img) return CPCT_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_sino) & 15u) || (reinterpret_cast<uintptr_t>(d_img) & 15u)) return CPCT_EINVAL;
+  if (p->n_slots > kNoAllocMaxSlots) return CPCT_EINVAL;  // geometry needs more partial tiles than the array holds
+  int status = CPCT_OK;
+  float2* partials = noalloc_scratch(&status);
+  if (!partials) return status;
+#define AN(L) launch_adj_Ns<L>(p, d_sino, s)
+  CPCT_DISPATCH_NS(p->logNs, AN);
+#undef AN
+  AdjSpreadArgs a;
+  a.items = p->d_adj_items;
+  a.ids = p->d_adj_ids;
+  a.ray = p->d_ray;
+  a.Qt = p->d_Q;
+  a.Ax = p->d_Ax;
+  a.partials = partials;
+  a.err = p->d_err;
+  a.G = p->G;
+  a.ldq = p->ldq;
+  a.ldh = p->ldh;
+  a.tiles_x = p->tiles_x_adj;
+  a.ext_rows = p->ext_rows;
+  a.poly = p->poly;
+  // every partial tile is written in full by its work item before the reduce
+  // reads it, so the array needs no clearing between calls
+  if (p->n_adj_items > 0) k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
+  if (p->n_split > 0)
+    k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, partials, p->d_Ax, p->tiles_x_adj, p->ldh,
+                                                             p->ext_rows);
 #define AG(L) launch_adj_G<L>(p, d_img, s)
   CPCT_DISPATCH_G(p->logG, AG);
 #undef AG
