@@ -32,6 +32,10 @@ point carries both halves of the optimality certificate.
 
 Constants (the paper gives none; readings): memory of 3 objective values,
 sufficient-decrease gamma = 1e-4, step lengths clamped to [1e-16, 1e5],
+a flat projection arc is detected when two consecutive trial displacements
+have the same norm to 1e-6 (the step then jumps to half the displacement's
+scale), after every Newton update of tau the step restarts from the projected
+gradient,
 opt_tol = 1e-4, bp_tol = 1e-6, at most 10 halvings per line search.
 
 Parity pins (tests/test_oracle_spgl1.py): the l1 projection is pinned by its
@@ -211,7 +215,7 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
         fmax = max(fhist[-o.memory:])
         step = alpha
         accepted = False
-        xt_prev = None
+        dn_prev = None
         gn = float(np.linalg.norm(g_old))
         for _ in range(o.max_line + 1):
             xt = project_l1(x_old - step * g_old, tau)
@@ -225,14 +229,14 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
                 accepted = True
                 break
             dn = float(np.linalg.norm(d))
-            if xt_prev is not None and np.linalg.norm(xt - xt_prev) <= 1e-6 * dn and gn > 0:
+            if dn_prev is not None and abs(dn - dn_prev) <= 1e-6 * dn and gn > 0:
                 # the arc is flat here (the projection saturates for long
                 # steps): jump to the step whose gradient move is half the
                 # current displacement
                 step = min(0.5 * step, 0.5 * dn / gn)
             else:
                 step *= 0.5
-            xt_prev = xt
+            dn_prev = dn
         if not accepted:
             if ft < f_old and gtd < 0:
                 accepted = True
