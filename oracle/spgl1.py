@@ -25,10 +25,13 @@ The published method, restated:
   projection arc against the maximum of the last few objective values;
 * P_tau is the Euclidean projection onto the l1 ball of radius tau.
 
-Termination (reading): the root is accepted when | ||r|| - sigma | <=
-opt_tol max(1, ||r||) and, at the same iterate, the relative duality gap of
-the LASSO problem is <= max(opt_tol, relative error in f); so the returned
-point carries both halves of the optimality certificate.
+Inexact Newton and termination (readings): the LASSO problem for the current
+tau counts as solved when its relative duality gap is <= max(opt_tol,
+relative error in f) or when it stagnates (relative decrease of f in the last
+step <= dec_tol = 1e-4 while ||r|| > 2 sigma, <= 0.1 |(||r|| - sigma)| /
+||r|| otherwise); the tau Newton step is then taken, and the root is accepted
+when | ||r|| - sigma | <= opt_tol max(1, ||b||) at such a point (root error
+measured relative to the data).
 
 Constants (the paper gives none; readings): memory of 3 objective values,
 sufficient-decrease gamma = 1e-4, step lengths clamped to [1e-16, 1e5],
@@ -36,7 +39,7 @@ a flat projection arc is detected when two consecutive trial displacements
 have the same norm to 1e-6 (the step then jumps to half the displacement's
 scale), after every Newton update of tau the step restarts from the projected
 gradient,
-opt_tol = 1e-4, bp_tol = 1e-6, at most 10 halvings per line search.
+opt_tol = 1e-4, bp_tol = 1e-6, at most 30 halvings per line search.
 
 Parity pins (tests/test_oracle_spgl1.py): the l1 projection is pinned by its
 optimality conditions and by an independent bisection; the solver with
@@ -115,7 +118,9 @@ class Options:
     gamma: float = 1e-4
     step_min: float = 1e-16
     step_max: float = 1e5
-    max_line: int = 10
+    max_line: int = 30
+    dec_tol: float = 1e-4
+    restart_step: bool = True
 
 
 @dataclass
@@ -175,20 +180,29 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
 
     fhist = [f]
     it = 0
+    f_old = None
     while True:
         rnorm = float(np.linalg.norm(r))
         gnorm = float(np.abs(g).max())
         # duality gap of the current LASSO problem, in the scale of f
         gap = float(r.ravel() @ (r - b).ravel()) + tau * gnorm
         rel_gap = abs(gap) / max(1.0, f)
-        err_root = abs(rnorm - sigma) / max(1.0, rnorm)
+        err_root = abs(rnorm - sigma) / max(1.0, bnorm)
         err_f = abs(f - 0.5 * sigma ** 2) / max(1.0, f)
         info.history.append((it, tau, rnorm, rel_gap))
 
         status = 0
         # the current LASSO problem is solved as accurately as the distance
-        # to the root requires
+        # to the root requires: certified by its duality gap, or stagnant
+        # (objective decrease below 1e-4 relative far from the root, below a
+        # tenth of the relative root error near it)
         solved_sub = rel_gap <= max(o.opt_tol, err_f)
+        if f_old is not None and f > 0:
+            dec = abs(f - f_old) / f
+            if rnorm > 2 * sigma:
+                solved_sub = solved_sub or dec <= o.dec_tol
+            else:
+                solved_sub = solved_sub or dec <= 0.1 * abs(rnorm - sigma) / max(rnorm, 1e-300)
         if solved_sub:
             if err_root <= o.opt_tol:
                 status = EXIT_ROOT_FOUND
@@ -204,10 +218,12 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
             tau_new = max(0.0, tau + (rnorm - sigma) * rnorm / gnorm)
             if tau_new < tau:
                 x = project_l1(x, tau_new)
+            tau_was_zero = tau == 0.0
             tau = tau_new
-            # the feasible set changed: restart the step length from the
-            # projected gradient on the new ball
-            alpha = pg_step(x, g, tau)
+            if tau_was_zero or o.restart_step:
+                # leaving tau = 0 (x = 0, no step history yet): restart the
+                # step length from the projected gradient on the new ball
+                alpha = pg_step(x, g, tau)
 
         # spectral projected gradient step, non-monotone arc search
         it += 1
