@@ -123,6 +123,75 @@ int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t s
 int radon_fwd_host(cpct_plan* plan, const float* h_img, float* h_sino, cudaStream_t stream);
 int radon_adj_host(cpct_plan* plan, const float* h_sino, float* h_img, cudaStream_t stream);
 
+/* ---- ring filter and SPGL1 (section "Introduction", the L1 problem) ---- */
+
+/* Ring-artifact filter ("polynomial subtraction" with a 3rd-order fit), read
+ * as the orthogonal projector  F y = y - 1_M (m - Pi_3 m),  m[s] the mean of
+ * detector column s over the M views, Pi_3 the least-squares cubic fit over
+ * s (FP64 column means and fit).  Per-detector-column offsets (rings) that a
+ * cubic does not explain are removed.
+ *   d_in, d_out  device, M*Ns float32 (may alias).  Allocates a small
+ *   workspace (Ns x 6 doubles) and synchronizes `stream`. */
+int cpct_ring_filter(cpct_plan* plan, const float* d_in, float* d_out, cudaStream_t stream);
+
+/* SPGL1 options (0 selects the default shown). */
+typedef struct spgl1_opts {
+  int max_iter;       /* iteration cap, 300                                     */
+  int memory;         /* non-monotone line-search memory, 3 (<= 8)            */
+  int max_line;       /* step halvings per line search, 30                      */
+  int flags;          /* CPCT_SPGL1_* bits                                      */
+  double opt_tol;     /* relative duality gap / root tolerance, 1e-4            */
+  double bp_tol;      /* basis-pursuit tolerance, 1e-6                          */
+  double gamma;       /* sufficient decrease, 1e-4                              */
+  double step_min;    /* Barzilai-Borwein step clamp, 1e-16                     */
+  double step_max;    /* 1e5                                                    */
+  double tau0;        /* initial l1 radius when CPCT_SPGL1_TAU0 is set          */
+} spgl1_opts;
+
+#define CPCT_SPGL1_TAU0 0x1       /* start from opts->tau0 instead of ||x0||_1  */
+#define CPCT_SPGL1_NO_FILTER 0x2  /* solve with A = R (no ring filter)          */
+
+/* Result record of one solve. status: 1 root found (| ||r|| - sigma | <=
+ * opt_tol max(1, ||F b||) at a solved or stagnant LASSO subproblem),
+ * 2 basis-pursuit solution, 3 iteration cap, 4 line-search failure,
+ * 5 non-finite values. */
+typedef struct spgl1_info {
+  int status;
+  int iterations;     /* SPGL1 iterations (spectral projected-gradient steps)  */
+  int ticks;          /* device ticks (line-search trials + bookkeeping)        */
+  int trials;         /* line-search trials                                     */
+  double tau;         /* final l1 radius                                        */
+  double rnorm;       /* ||F(R x) - F b||_2                                     */
+  double xnorm1;      /* ||x||_1                                                */
+  double rel_gap;     /* relative duality gap of the last LASSO subproblem      */
+} spgl1_info;
+
+/* Basis-pursuit denoising  min ||x||_1  s.t.  ||F(R x - b)||_2 <= sigma  by
+ * SPGL1 (van den Berg & Friedlander 2008): Newton root-finding on the Pareto
+ * curve tau -> ||r_tau||, each LASSO subproblem solved by spectral projected
+ * gradient with a non-monotone arc search; FP32 vectors, FP64 reductions and
+ * controller (tau-sigma Newton step, Armijo test, Barzilai-Borwein step,
+ * duality gap) on the device, one CUDA graph per iteration tick.
+ *   d_b     device, M*Ns float32 data (read)
+ *   sigma   misfit bound eps >= 0 (0: basis pursuit)
+ *   d_x     device, N*N float32: in = warm start (zeros for a cold start),
+ *           out = solution; tau starts at ||x0||_1 unless CPCT_SPGL1_TAU0
+ *   opts    NULL for defaults;  info  host record, may be NULL
+ * Returns CPCT_OK (status 1 or 2), CPCT_ENOTCONV (iteration cap or line-search
+ * failure; d_x holds the last iterate), CPCT_ENONFINITE, CPCT_EINVAL,
+ * CPCT_ENOMEM, CPCT_ECUDA.  Allocates its workspace (5 N^2 + 4 M Ns floats)
+ * for the duration of the call and synchronizes `stream`.  Kernel event
+ * profiling of the plan is switched off by this call. */
+int spgl1_solve(cpct_plan* plan, const float* d_b, double sigma, float* d_x, const spgl1_opts* opts,
+                spgl1_info* info, cudaStream_t stream);
+
+/* The same for `batch` independent slices solved together (one graph whose
+ * branches run the slices concurrently).  Each slice needs its own plan (a
+ * plan holds per-call workspaces); arrays are host arrays of `batch` entries;
+ * info is an array of `batch` records. */
+int spgl1_solve_batched(cpct_plan* const* plans, int batch, const float* const* d_b, const double* sigma,
+                        float* const* d_x, const spgl1_opts* opts, spgl1_info* info, cudaStream_t stream);
+
 /* Allocation-free adjoint.  Some callers cannot allocate device memory at
  * the point where they apply the operator: code running under an allocator
  * that has reserved the whole device pool (a framework's caching allocator),

@@ -243,3 +243,97 @@ def debug_rounds(n, n_det, n_views, angles=None):
     check(L.cpct_debug_rounds(ctypes.byref(g), ctypes.byref(r), ctypes.byref(pk), ctypes.byref(ok)),
           "cpct_debug_rounds")
     return r.value, pk.value, bool(ok.value)
+
+
+# ---------------------------------------------------------------------------
+# ring filter and SPGL1
+# ---------------------------------------------------------------------------
+SPGL1_TAU0 = 0x1
+SPGL1_NO_FILTER = 0x2
+SPGL1_STATUS = {1: "root found", 2: "basis pursuit solution", 3: "iteration cap", 4: "line search failure",
+                5: "non-finite"}
+
+
+class Spgl1Opts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("memory", ctypes.c_int), ("max_line", ctypes.c_int),
+                ("flags", ctypes.c_int), ("opt_tol", ctypes.c_double), ("bp_tol", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("step_min", ctypes.c_double), ("step_max", ctypes.c_double),
+                ("tau0", ctypes.c_double)]
+
+
+class Spgl1Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("ticks", ctypes.c_int),
+                ("trials", ctypes.c_int), ("tau", ctypes.c_double), ("rnorm", ctypes.c_double),
+                ("xnorm1", ctypes.c_double), ("rel_gap", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _spgl1_setup():
+    L = lib()
+    vp = ctypes.c_void_p
+    L.cpct_ring_filter.argtypes = [vp, vp, vp, vp]
+    L.spgl1_solve.argtypes = [vp, vp, ctypes.c_double, vp, ctypes.POINTER(Spgl1Opts), ctypes.POINTER(Spgl1Info), vp]
+    L.spgl1_solve_batched.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vp),
+                                      ctypes.POINTER(Spgl1Opts), ctypes.POINTER(Spgl1Info), vp]
+    return L
+
+
+def make_opts(max_iter=0, opt_tol=0.0, bp_tol=0.0, memory=0, max_line=0, tau0=None, ring_filter=True):
+    o = Spgl1Opts()
+    o.max_iter, o.opt_tol, o.bp_tol, o.memory, o.max_line = max_iter, opt_tol, bp_tol, memory, max_line
+    o.flags = (0 if ring_filter else SPGL1_NO_FILTER) | (SPGL1_TAU0 if tau0 is not None else 0)
+    o.tau0 = 0.0 if tau0 is None else float(tau0)
+    return o
+
+
+def ring_filter(plan, sino, out=None, stream=None):
+    """F y on the device (same shape as the sinogram)."""
+    torch = plan._torch
+    L = _spgl1_setup()
+    if out is None:
+        out = torch.empty_like(sino)
+    check(L.cpct_ring_filter(plan.handle, _dev_ptr(sino, (plan.n_views, plan.n_det), torch),
+                             _dev_ptr(out, (plan.n_views, plan.n_det), torch), _stream(torch, stream)),
+          "cpct_ring_filter")
+    return out
+
+
+def spgl1(plan, b, sigma, x0=None, opts=None, stream=None, allow_notconv=True):
+    """Solve min ||x||_1 s.t. ||F(R x - b)||_2 <= sigma on the device.
+
+    Returns (x, info dict).  ``x0`` (N x N CUDA tensor) warm-starts the solve
+    (tau starts at ||x0||_1); otherwise the solve starts cold from x = 0.
+    """
+    torch = plan._torch
+    L = _spgl1_setup()
+    x = torch.zeros((plan.n, plan.n), device=b.device, dtype=torch.float32) if x0 is None else x0.clone()
+    info = Spgl1Info()
+    o = opts if opts is not None else make_opts()
+    rc = L.spgl1_solve(plan.handle, _dev_ptr(b, (plan.n_views, plan.n_det), torch), float(sigma),
+                       _dev_ptr(x, (plan.n, plan.n), torch), ctypes.byref(o), ctypes.byref(info),
+                       _stream(torch, stream))
+    if rc != 0 and not (allow_notconv and rc == -6):
+        raise CpctError(rc, "spgl1_solve")
+    return x, info.as_dict()
+
+
+def spgl1_batched(plans, bs, sigmas, x0s=None, opts=None, stream=None, allow_notconv=True):
+    """Solve len(plans) independent slices together (one plan per slice)."""
+    torch = plans[0]._torch
+    L = _spgl1_setup()
+    B = len(plans)
+    xs = [torch.zeros((p.n, p.n), device=b.device, dtype=torch.float32) if x0s is None else x0s[i].clone()
+          for i, (p, b) in enumerate(zip(plans, bs))]
+    H = (ctypes.c_void_p * B)(*[p.handle.value for p in plans])
+    Bp = (ctypes.c_void_p * B)(*[_dev_ptr(b, (p.n_views, p.n_det), torch).value for p, b in zip(plans, bs)])
+    Xp = (ctypes.c_void_p * B)(*[_dev_ptr(x, (p.n, p.n), torch).value for p, x in zip(plans, xs)])
+    S = (ctypes.c_double * B)(*[float(s) for s in sigmas])
+    infos = (Spgl1Info * B)()
+    o = opts if opts is not None else make_opts()
+    rc = L.spgl1_solve_batched(H, B, Bp, S, Xp, ctypes.byref(o), infos, _stream(torch, stream))
+    if rc != 0 and not (allow_notconv and rc == -6):
+        raise CpctError(rc, "spgl1_solve_batched")
+    return xs, [i.as_dict() for i in infos]
