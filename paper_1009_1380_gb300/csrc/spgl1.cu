@@ -796,6 +796,15 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
     k_spg_setup<<<1, kRB, 0, stream>>>(V, tau0);
     if (!cuda(cudaGetLastError())) goto done;
   }
+  // the first tick runs eagerly: it loads every kernel of a tick (modules
+  // load lazily, which is not allowed while a stream is being captured)
+  for (int i = 0; i < batch; ++i) {
+    cpct_profile_enable(ws[i].plan, 0);
+    SliceWork w = ws[i];
+    w.stream = stream;
+    enqueue_tick(w, filter);
+  }
+  if (!cuda(cudaGetLastError())) goto done;
   if (!cuda(cudaStreamSynchronize(stream))) goto done;
   // one tick of every slice, captured once
   {
