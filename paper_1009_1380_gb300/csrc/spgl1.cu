@@ -751,6 +751,9 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> joins;
   std::vector<SpgState> h_states(batch);
+  std::vector<cudaStream_t> branch;
+  cudaStream_t cap = nullptr;
+  bool capturing = false;
   rc = CPCT_OK;
   auto cuda = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == CPCT_OK) rc = CPCT_ECUDA;
@@ -782,8 +785,11 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
     V.part = d_part + (size_t)i * P_TOTAL * kRG;
     V.st = d_states + i;
     if ((rc = ring_work(w.plan->ns, w.ring, stream)) != CPCT_OK) goto done;
-    if (batch == 1) w.stream = stream;
-    else if (!cuda(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking))) goto done;
+    w.stream = stream;
+    if (batch > 1) {
+      branch.push_back(nullptr);
+      if (!cuda(cudaStreamCreateWithFlags(&branch.back(), cudaStreamNonBlocking))) goto done;
+    }
     // state, filtered data, zero gradient and residual, ||b||, tau0
     SpgState st = proto;
     st.sigma = w.sigma;
@@ -800,31 +806,40 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
   // load lazily, which is not allowed while a stream is being captured)
   for (int i = 0; i < batch; ++i) {
     cpct_profile_enable(ws[i].plan, 0);
-    SliceWork w = ws[i];
-    w.stream = stream;
-    enqueue_tick(w, filter);
+    enqueue_tick(ws[i], filter);
   }
   if (!cuda(cudaGetLastError())) goto done;
   if (!cuda(cudaStreamSynchronize(stream))) goto done;
-  // one tick of every slice, captured once
+  // one tick of every slice, captured once on a private stream (the
+  // caller's stream may be the legacy default stream, which cannot be
+  // captured); the graph is then launched on the caller's stream
   {
     // kernel-level event profiling cannot be recorded inside a graph
     for (int i = 0; i < batch; ++i) cpct_profile_enable(ws[i].plan, 0);
+    if (!cuda(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) goto done;
     if (!cuda(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming))) goto done;
     joins.resize(batch, nullptr);
     for (int i = 0; i < batch; ++i)
       if (!cuda(cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming))) goto done;
-    if (!cuda(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal))) goto done;
-    if (batch > 1) cudaEventRecord(fork, stream);
+    if (!cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal))) goto done;
+    capturing = true;
+    if (batch > 1) cudaEventRecord(fork, cap);
     for (int i = 0; i < batch; ++i) {
-      if (batch > 1) cudaStreamWaitEvent(ws[i].stream, fork, 0);
-      enqueue_tick(ws[i], filter);
+      SliceWork w = ws[i];
       if (batch > 1) {
-        cudaEventRecord(joins[i], ws[i].stream);
-        cudaStreamWaitEvent(stream, joins[i], 0);
+        w.stream = branch[i];
+        cudaStreamWaitEvent(w.stream, fork, 0);
+      } else {
+        w.stream = cap;
+      }
+      enqueue_tick(w, filter);
+      if (batch > 1) {
+        cudaEventRecord(joins[i], w.stream);
+        cudaStreamWaitEvent(cap, joins[i], 0);
       }
     }
-    if (!cuda(cudaStreamEndCapture(stream, &graph))) goto done;
+    capturing = false;
+    if (!cuda(cudaStreamEndCapture(cap, &graph))) goto done;
     if (!cuda(cudaGraphInstantiate(&exec, graph, 0))) goto done;
   }
   {
@@ -875,6 +890,12 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
     }
   }
 done:
+  if (capturing) {
+    // end a capture that an error interrupted, so no stream stays capturing
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(cap, &g);
+    if (g) cudaGraphDestroy(g);
+  }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   cudaStreamSynchronize(stream);
@@ -884,8 +905,10 @@ done:
   for (auto& w : ws) {
     if (w.mem) cudaFree(w.mem);
     ring_free(w.ring);
-    if (w.stream && w.stream != stream) cudaStreamDestroy(w.stream);
   }
+  for (auto b : branch)
+    if (b) cudaStreamDestroy(b);
+  if (cap) cudaStreamDestroy(cap);
   if (d_states) cudaFree(d_states);
   if (d_part) cudaFree(d_part);
   return rc;
