@@ -68,9 +68,13 @@ def test_spgl1_matches_oracle(torch_cuda):
     bf = ring.ring_filter(b32.astype(np.float64))
     A = lambda v: ring.ring_filter(nufft.radon_grid(v.reshape(n, n), geo))
     At = lambda r: nufft.radon_grid_adj(ring.ring_filter(r.reshape(m, n)), geo)
-    xo, io = spgl1.spgl1(A, At, bf, sigma)
+    # a root tolerance 10x tighter than the default: both solvers stop within
+    # opt_tol ||F b|| of sigma, which moves ||x||_1 along the Pareto curve by
+    # about that relative amount
+    tol = 1e-5
+    xo, io = spgl1.spgl1(A, At, bf, sigma, opts=spgl1.Options(opt_tol=tol, max_iter=600))
     p = cpct.Plan(n, n, m)
-    xg, ig = cpct.spgl1(p, torch.from_numpy(b32).cuda(), sigma)
+    xg, ig = cpct.spgl1(p, torch.from_numpy(b32).cuda(), sigma, opts=cpct.make_opts(opt_tol=tol, max_iter=600))
     xg = xg.cpu().numpy().astype(np.float64)
     rg = np.linalg.norm(A(xg) - bf)
     print("oracle", io.status, io.iterations, io.rnorm, io.xnorm1)
@@ -78,7 +82,7 @@ def test_spgl1_matches_oracle(torch_cuda):
     print("x rel", _rel(xg, xo), "l1 rel", abs(ig["xnorm1"] - io.xnorm1) / io.xnorm1, "r (oracle op)", rg, sigma)
     assert io.status == spgl1.EXIT_ROOT_FOUND
     assert ig["status"] == 1
-    assert abs(ig["rnorm"] - sigma) <= 1e-4 * np.linalg.norm(bf) * 2
+    assert abs(ig["rnorm"] - sigma) <= 2 * tol * np.linalg.norm(bf)
     assert abs(rg - sigma) <= 1e-3 * np.linalg.norm(bf)
     assert abs(ig["xnorm1"] - io.xnorm1) <= 1e-3 * io.xnorm1
     assert _rel(xg, xo) < 5e-2
