@@ -226,6 +226,36 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def spgl1_bench(args, torch, cpct, synth):
+    """Batched SPGL1 on the 1024^2 / 128-view workload with noise (1% of max)
+    and 8 stuck detector columns: slices that reach the root
+    (| ||r|| - sigma | <= 1e-4 ||F b||) per second of wall time."""
+    c = synth.CONFIGS["c4_spgl1_1024"]
+    n, m, B = c["n"], c["n_views"], args.spgl1_batch
+    plans = [cpct.Plan(n, n, m) for _ in range(B)]
+    bs, sig = [], []
+    for i in range(B):
+        x = torch.from_numpy(synth.phantom("c4_spgl1_1024", slice_index=i)).cuda()
+        y = plans[i].fwd(x).cpu().numpy()
+        b, std, _ = synth.corrupt_sinogram(y, synth.rng_for(c["index"], i))
+        bs.append(torch.from_numpy(b.astype(np.float32)).cuda())
+        sig.append(std * np.sqrt(m * n - n + 4))
+    opts = cpct.make_opts(max_iter=c["iterations"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xs, infos = cpct.spgl1_batched(plans, bs, sig, opts=opts)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    roots = sum(1 for i in infos if i["status"] == 1)
+    its = [i["iterations"] for i in infos]
+    return {"metric": "SPGL1 slices/s to the root", "value": roots / wall, "unit": "slices/s",
+            "slices": B, "slices_at_root": roots, "wall_s": wall,
+            "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
+            "ticks_mean": float(np.mean([i["ticks"] for i in infos])),
+            "config": f"{B} slices {n}x{n} Laplacian phantoms, {m} views x {n} bins, noise 1% + 8 stuck columns, "
+                      f"<= {c['iterations']} iterations, opt_tol 1e-4, ring filter"}
+
+
 def config_dict(args):
     n, ns, m, _ = WORKLOADS[args.workload]
     return {"workload": f"{args.workload}: {n}x{n} float32 phantom, {m} views x {ns} bins, KB W=6 sigma=2",
@@ -352,6 +382,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload)
+    if world == 1 and args.spgl1_batch > 0:
+        out["spgl1"] = spgl1_bench(args, torch, cpct, synth)
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -365,6 +397,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2_2048", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spgl1-batch", type=int, default=64, help="slices of the SPGL1 workload (0: skip)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -181,6 +181,7 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
     fhist = [f]
     it = 0
     f_old = None
+    n_stationary = 0
     while True:
         rnorm = float(np.linalg.norm(r))
         gnorm = float(np.abs(g).max())
@@ -240,7 +241,7 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
             d = (xt - x_old).ravel()
             gtd = float(g_old.ravel() @ d)
             if gtd >= 0:
-                break  # no descent along the arc: projection returned x
+                break  # no descent along the arc: x is stationary for this tau
             if ft < fmax + o.gamma * gtd:
                 accepted = True
                 break
@@ -253,13 +254,23 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
             else:
                 step *= 0.5
             dn_prev = dn
+        if not accepted and gtd >= 0:
+            # x is stationary for the current LASSO problem: it is solved
+            # (f unchanged registers as stagnation at the next check); only
+            # repeated stationarity without a tau update is a failure
+            n_stationary += 1
+            if n_stationary > 3:
+                info.status = EXIT_LINE_ERROR
+                break
+            continue
         if not accepted:
-            if ft < f_old and gtd < 0:
+            if ft < f_old:
                 accepted = True
             else:
                 # stalled: the current point is kept; signal and stop
                 info.status = EXIT_LINE_ERROR
                 break
+        n_stationary = 0
         x, r, f = xt, rt, ft
         g = -Atr(r)
         s = (x - x_old).ravel()

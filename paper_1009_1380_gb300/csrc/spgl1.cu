@@ -231,7 +231,7 @@ struct SpgState {
   // mid-tick results
   double ft, gtd, dn2, dinf, rtb_t;
   // counters / status
-  int iter, n_line, status, done, ticks, n_trials, pad2, pad3;
+  int iter, n_line, status, done, ticks, n_trials, stationary, n_stationary;
 };
 
 // SPGL1 status codes (spgl1_info.status)
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(kRB) k_spg_mid(SpgVec V) {
   st->dinf = dinf;
   st->ft = 0.5 * r[0];
   st->rtb_t = r[1];
-  st->accept_x = st->accept_r = st->update_g = st->line_fail = 0;
+  st->accept_x = st->accept_r = st->update_g = st->line_fail = st->stationary = 0;
   const int type = st->type;
   if (type == T_INIT || type == T_TRIAL) {
     if (!isfinite(st->ft) || !isfinite(st->gtd)) {
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kRB) k_spg_mid(SpgVec V) {
   } else if (type == T_TRIAL) {
     st->n_trials++;
     bool acc = false;
-    if (st->gtd >= 0.0) st->line_fail = 1;                        // no descent along the arc
+    if (st->gtd >= 0.0) st->stationary = 1;                       // no descent: x is stationary
     else if (st->ft < st->fmax + st->gamma * st->gtd) acc = true;  // non-monotone Armijo
     else if (st->n_line >= st->max_line) {                         // last halving
       if (st->ft < st->f_old) acc = true;
@@ -611,7 +611,20 @@ __global__ void __launch_bounds__(kRB) k_spg_end(SpgVec V) {
         st->done = 1;
         break;
       }
+      if (st->stationary) {
+        // x is stationary for the current LASSO problem: check the root /
+        // take the Newton step (unchanged f registers as stagnation);
+        // repeated stationarity without progress is a failure
+        if (++st->n_stationary > 3) {
+          st->status = S_LINE;
+          st->done = 1;
+          break;
+        }
+        spg_check(st);
+        break;
+      }
       if (st->accept_r) {
+        st->n_stationary = 0;
         const double sts = gq[0], sty = gq[1];
         st->alpha = sty <= 0.0 ? st->step_max : fmin(st->step_max, fmax(st->step_min, sts / sty));
         if (st->f > 0.5 * st->sigma * st->sigma) spg_push_hist(st, st->f);
