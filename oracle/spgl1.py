@@ -254,22 +254,19 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
             else:
                 step *= 0.5
             dn_prev = dn
-        if not accepted and gtd >= 0:
-            # x is stationary for the current LASSO problem: it is solved
-            # (f unchanged registers as stagnation at the next check); only
-            # repeated stationarity without a tau update is a failure
+        if not accepted and gtd < 0 and ft < f_old:
+            accepted = True  # halvings exhausted, but f decreased
+        if not accepted:
+            # no descent along the arc, or no measurable decrease after every
+            # halving: x is stationary for the current LASSO problem to the
+            # working precision, which is then solved (f unchanged registers
+            # as stagnation at the next check); only repeated stationarity
+            # without progress is a failure
             n_stationary += 1
             if n_stationary > 3:
                 info.status = EXIT_LINE_ERROR
                 break
             continue
-        if not accepted:
-            if ft < f_old:
-                accepted = True
-            else:
-                # stalled: the current point is kept; signal and stop
-                info.status = EXIT_LINE_ERROR
-                break
         n_stationary = 0
         x, r, f = xt, rt, ft
         g = -Atr(r)

@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(kRB) k_spg_mid(SpgVec V) {
     else if (st->ft < st->fmax + st->gamma * st->gtd) acc = true;  // non-monotone Armijo
     else if (st->n_line >= st->max_line) {                         // last halving
       if (st->ft < st->f_old) acc = true;
-      else st->line_fail = 1;
+      else st->stationary = 1;  // no measurable decrease left at this tau
     }
     if (acc) st->accept_x = st->accept_r = st->update_g = 1;
   }
