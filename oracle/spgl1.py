@@ -218,7 +218,12 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
             # Newton step on the Pareto curve
             tau_new = max(0.0, tau + (rnorm - sigma) * rnorm / gnorm)
             if tau_new < tau:
+                # the ball shrank: project x onto it and bring the residual,
+                # objective and gradient up to date with the projected x
                 x = project_l1(x, tau_new)
+                r = b - Ax(x)
+                g = -Atr(r)
+                f = 0.5 * float(r.ravel() @ r.ravel())
             tau_was_zero = tau == 0.0
             tau = tau_new
             if tau_was_zero or o.restart_step:

@@ -552,7 +552,9 @@ __global__ void __launch_bounds__(kRB) k_spg_mid(SpgVec V) {
   if (type == T_INIT) {
     st->accept_x = st->accept_r = st->update_g = 1;
   } else if (type == T_PROJX) {
-    st->accept_x = 1;
+    // x projected onto the shrunk ball: residual, objective and gradient
+    // are brought up to date with it
+    st->accept_x = st->accept_r = st->update_g = 1;
   } else if (type == T_TRIAL) {
     st->n_trials++;
     bool acc = false;
