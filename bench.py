@@ -240,7 +240,7 @@ def spgl1_bench(args, torch, cpct, synth):
         b, std, _ = synth.corrupt_sinogram(y, synth.rng_for(c["index"], i))
         bs.append(torch.from_numpy(b.astype(np.float32)).cuda())
         sig.append(std * np.sqrt(m * n - n + 4))
-    opts = cpct.make_opts(max_iter=c["iterations"])
+    opts = cpct.make_opts(max_iter=args.spgl1_iters or c["iterations"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     xs, infos = cpct.spgl1_batched(plans, bs, sig, opts=opts)
@@ -398,12 +398,21 @@ def main():
     ap.add_argument("--workload", default="c2_2048", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spgl1-batch", type=int, default=64, help="slices of the SPGL1 workload (0: skip)")
+    ap.add_argument("--spgl1-iters", type=int, default=0, help="override the SPGL1 iteration cap (0: 300)")
+    ap.add_argument("--only", default="", choices=["", "spgl1"], help="run one secondary workload alone")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.only == "spgl1":
+        import torch
+        from paper_1009_1380_gb300 import build as b
+        b.build()
+        from paper_1009_1380_gb300 import cpct, synth
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(spgl1_bench(args, torch, cpct, synth)), flush=True)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -123,6 +123,42 @@ int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t s
 int radon_fwd_host(cpct_plan* plan, const float* h_img, float* h_sino, cudaStream_t stream);
 int radon_adj_host(cpct_plan* plan, const float* h_sino, float* h_img, cudaStream_t stream);
 
+/* ---- many slices: clones, autotuner, batches ----------------------------- */
+
+/* A new plan for the same geometry as `src` that shares src's read-only
+ * tables and bin lists (freed with the last plan using them) but owns its own
+ * workspaces, so that it can run concurrently with src on another slice.
+ * Synchronous on `stream`.  Cheap: no bin building. */
+int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream_t stream);
+
+/* Autotuner of the work-item sizes (the bins' split caps): times radon_fwd
+ * for 256..4096 samples per gather item and radon_adj for 16..256 rounds per
+ * spread item (median of `reps` launches each, CUDA events on `stream`) and
+ * keeps the fastest; reports the chosen caps.  The plan must not have clones
+ * yet.  Allocates temporary buffers; synchronous. */
+int cpct_plan_tune(cpct_plan* plan, int reps, int* fwd_cap, int* adj_cap, cudaStream_t stream);
+
+/* A batch: the operator applied to `batch` slices, each with its own plan
+ * (clones of one plan per distinct geometry; uneven view counts are fine),
+ * captured once as a CUDA graph whose `branches` concurrent branches (0: 16)
+ * take the slices longest first, round robin.  d_in/d_out are host arrays of
+ * `batch` device pointers bound into the graph (they must stay valid and keep
+ * their addresses).  mode: CPCT_BATCH_FWD (image -> sinogram),
+ * CPCT_BATCH_ADJ (sinogram -> image), CPCT_BATCH_PAIR (image -> radon_adj of
+ * radon_fwd, the sinogram kept in a plan-owned buffer).  Creation runs the
+ * batch once eagerly and synchronizes `stream`. */
+typedef struct cpct_batch cpct_batch;
+#define CPCT_BATCH_FWD 0
+#define CPCT_BATCH_ADJ 1
+#define CPCT_BATCH_PAIR 2
+int cpct_batch_create(cpct_batch** out, cpct_plan* const* plans, int batch, const float* const* d_in,
+                      float* const* d_out, int mode, int branches, cudaStream_t stream);
+/* Run the whole batch: one graph launch on `stream` (asynchronous). */
+int cpct_batch_run(cpct_batch* batch, cudaStream_t stream);
+/* Slices, polar samples per operator application over all slices, branches. */
+int cpct_batch_info(const cpct_batch* batch, int* n_slices, long long* samples, int* branches);
+int cpct_batch_destroy(cpct_batch* batch);
+
 /* ---- ring filter and SPGL1 (section "Introduction", the L1 problem) ---- */
 
 /* Ring-artifact filter ("polynomial subtraction" with a 3rd-order fit), read

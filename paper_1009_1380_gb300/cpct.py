@@ -337,3 +337,81 @@ def spgl1_batched(plans, bs, sigmas, x0s=None, opts=None, stream=None, allow_not
     if rc != 0 and not (allow_notconv and rc == -6):
         raise CpctError(rc, "spgl1_solve_batched")
     return xs, [i.as_dict() for i in infos]
+
+
+# ---------------------------------------------------------------------------
+# clones, autotuner, batches
+# ---------------------------------------------------------------------------
+BATCH_FWD, BATCH_ADJ, BATCH_PAIR = 0, 1, 2
+
+
+def _batch_setup():
+    L = lib()
+    vp = ctypes.c_void_p
+    L.cpct_plan_clone.argtypes = [vp, ctypes.POINTER(vp), vp]
+    L.cpct_plan_tune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp]
+    L.cpct_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp]
+    L.cpct_batch_run.argtypes = [vp, vp]
+    L.cpct_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(ctypes.c_int)]
+    L.cpct_batch_destroy.argtypes = [vp]
+    return L
+
+
+def clone(plan, stream=None):
+    """A plan of the same geometry sharing tables and bins, with own workspaces."""
+    L = _batch_setup()
+    h = ctypes.c_void_p()
+    check(L.cpct_plan_clone(plan.handle, ctypes.byref(h), _stream(plan._torch, stream)), "cpct_plan_clone")
+    c = Plan.__new__(Plan)
+    c._torch, c._h, c._angles = plan._torch, h, plan._angles
+    c.n, c.n_det, c.n_views = plan.n, plan.n_det, plan.n_views
+    return c
+
+
+def tune(plan, reps=5, stream=None):
+    """Time candidate work-item caps and keep the fastest: (fwd_cap, adj_cap)."""
+    L = _batch_setup()
+    f, a = ctypes.c_int(), ctypes.c_int()
+    check(L.cpct_plan_tune(plan.handle, int(reps), ctypes.byref(f), ctypes.byref(a), _stream(plan._torch, stream)),
+          "cpct_plan_tune")
+    return f.value, a.value
+
+
+class Batch:
+    """The operator over many slices as one CUDA graph (one plan per slice)."""
+
+    def __init__(self, plans, ins, outs, mode=BATCH_PAIR, branches=0, stream=None):
+        torch = plans[0]._torch
+        L = _batch_setup()
+        B = len(plans)
+        vp = ctypes.c_void_p
+        self._keep = (list(plans), list(ins), list(outs))
+        H = (vp * B)(*[p.handle.value for p in plans])
+        I = (vp * B)(*[t.data_ptr() for t in ins])
+        O = (vp * B)(*[t.data_ptr() for t in outs])
+        h = vp()
+        check(L.cpct_batch_create(ctypes.byref(h), H, B, I, O, int(mode), int(branches), _stream(torch, stream)),
+              "cpct_batch_create")
+        self._h, self._torch = h, torch
+
+    def run(self, stream=None):
+        check(_batch_setup().cpct_batch_run(self._h, _stream(self._torch, stream)), "cpct_batch_run")
+
+    def info(self):
+        n, s, b = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+        check(_batch_setup().cpct_batch_info(self._h, ctypes.byref(n), ctypes.byref(s), ctypes.byref(b)),
+              "cpct_batch_info")
+        return dict(slices=n.value, samples=s.value, branches=b.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _batch_setup().cpct_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

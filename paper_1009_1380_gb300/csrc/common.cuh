@@ -91,8 +91,21 @@ struct cpct_plan {
   CUtensorMap tmap_Hx;
   size_t device_bytes;
   int fwd_interp_grid;      // persistent grid of the forward gather (0 = not yet sized)
+  int fwd_cap, adj_cap;     // work-item caps (samples / rounds per item), tunable
+  struct PlanShared* shared;  // read-only geometry shared with clones (refcounted)
   long long launches;       // kernels launched by this plan's operators
   CpctProfiler* prof;       // NULL unless profiling is enabled
+};
+
+// Read-only data of one geometry, shared by a plan and its clones: the
+// tables and bin lists (device) and the bin pointers kept on the host so the
+// work items can be rebuilt with other caps.  Freed with the last plan.
+#include <atomic>
+#include <vector>
+struct PlanShared {
+  std::atomic<int> refs{1};
+  std::vector<int> fwd_tile_ptr;    // forward bins: tiles + 1
+  std::vector<int> round_tile_ptr;  // adjoint rounds per tile: tiles + 1
 };
 
 // bracket a kernel launch: counts it and, if its id is profiled, records a

@@ -166,17 +166,6 @@ int upload(Alloc& al, T** dst, const std::vector<T>& src, cudaStream_t s) {
   return CPCT_OK;
 }
 
-void free_plan(cpct_plan* p) {
-  if (!p) return;
-  cpct_prof_free(p);
-  void* ptrs[] = {p->d_poly64, p->d_ray, p->d_deapod, p->d_twG, p->d_twNs, p->d_Hx, p->d_Ax, p->d_H1,
-                  p->d_Q, p->d_fwd_items, p->d_fwd_ids, p->d_adj_items, p->d_adj_ids, p->d_partials,
-                  p->d_split, p->d_stage_img, p->d_stage_sino, p->d_err};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
-  delete p;
-}
-
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -192,6 +181,39 @@ EncodeTiledFn get_encode_fn() {
       fn = reinterpret_cast<EncodeTiledFn>(ptr);
   }
   return fn;
+}
+
+
+void free_plan(cpct_plan* p) {
+  if (!p) return;
+  cpct_prof_free(p);
+  // per-plan workspaces
+  void* own[] = {p->d_Hx, p->d_Ax, p->d_H1, p->d_Q, p->d_partials, p->d_stage_img, p->d_stage_sino, p->d_err};
+  for (void* q : own)
+    if (q) cudaFree(q);
+  // geometry data, shared with clones: freed with the last plan
+  const bool last = !p->shared || --p->shared->refs == 0;
+  if (last) {
+    void* geo[] = {p->d_poly64, p->d_ray, p->d_deapod, p->d_twG, p->d_twNs, p->d_fwd_items, p->d_fwd_ids,
+                   p->d_adj_items, p->d_adj_ids, p->d_split};
+    for (void* q : geo)
+      if (q) cudaFree(q);
+    delete p->shared;
+  }
+  delete p;
+}
+
+int encode_hx_map(cpct_plan* p) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) return CPCT_EUNSUPPORTED;
+  cuuint64_t dims[2] = {(cuuint64_t)2 * p->ldh, (cuuint64_t)p->ext_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)p->ldh * sizeof(float2)};
+  cuuint32_t box[2] = {2 * (CPCT_TILE + CPCT_HALO + 1), CPCT_TILE + CPCT_HALO};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult cr = enc(&p->tmap_Hx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->d_Hx, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return cr == CUDA_SUCCESS ? CPCT_OK : CPCT_ECUDA;
 }
 
 }  // namespace
@@ -607,7 +629,13 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
     std::vector<int4> fitems, aitems, fsplit, asplit;
     cpct_detail::make_items(fb, kFwdItemMax, false, fitems, fsplit, nullptr);
     std::vector<int> item_split;
+    p->fwd_cap = kFwdItemMax;
+    p->adj_cap = kAdjItemRounds;
     cpct_detail::make_round_items(rounds, kAdjItemRounds, aitems, asplit, &p->n_slots, item_split);
+    p->shared = new (std::nothrow) PlanShared;
+    if (!p->shared) { rc = CPCT_ENOMEM; goto fail; }
+    p->shared->fwd_tile_ptr = fb.ptr;
+    p->shared->round_tile_ptr = rounds.tile_ptr;
     p->n_fwd_items = (int)fitems.size();
     p->n_adj_items = (int)aitems.size();
     p->n_split = (int)asplit.size();
@@ -618,18 +646,7 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
     TRY(upload(al, &p->d_split, asplit, stream));
     TRY(al((void**)&p->d_partials, sizeof(float2) * (size_t)std::max(1, p->n_slots) * CPCT_TILE * CPCT_TILE));
     // TMA descriptor of the forward extended spectrum (viewed as float32 pairs)
-    {
-      EncodeTiledFn enc = get_encode_fn();
-      if (!enc) { rc = CPCT_EUNSUPPORTED; goto fail; }
-      cuuint64_t dims[2] = {(cuuint64_t)2 * p->ldh, (cuuint64_t)p->ext_rows};
-      cuuint64_t strides[1] = {(cuuint64_t)p->ldh * sizeof(float2)};
-      cuuint32_t box[2] = {2 * (CPCT_TILE + CPCT_HALO + 1), CPCT_TILE + CPCT_HALO};
-      cuuint32_t estr[2] = {1, 1};
-      CUresult cr = enc(&p->tmap_Hx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->d_Hx, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (cr != CUDA_SUCCESS) { rc = CPCT_ECUDA; goto fail; }
-    }
+    TRY(encode_hx_map(p));
     // FP32 copy of the even/odd polynomial parts
     double poly[CPCT_W * (kPolyDeg + 1)];
     TRYC(cudaMemcpyAsync(poly, p->d_poly64, sizeof(poly), cudaMemcpyDeviceToHost, stream));
@@ -689,4 +706,170 @@ extern "C" int cpct_debug_tables(cpct_plan* p, double* h_poly64, float* h_deapod
     CPCT_CUDA_TRY(cudaMemcpy(h_poly64, p->d_poly64, sizeof(double) * CPCT_W * (kPolyDeg + 1), cudaMemcpyDeviceToHost));
   if (h_deapod) CPCT_CUDA_TRY(cudaMemcpy(h_deapod, p->d_deapod, sizeof(float) * p->n, cudaMemcpyDeviceToHost));
   return CPCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// clones and the work-item autotuner
+// ---------------------------------------------------------------------------
+extern "C" int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream_t stream) {
+  if (!src || !out || !src->shared) return CPCT_EINVAL;
+  *out = nullptr;
+  cpct_plan* p = new (std::nothrow) cpct_plan;
+  if (!p) return CPCT_ENOMEM;
+  std::memcpy(p, src, sizeof(*p));
+  // fresh per-plan state; the geometry pointers stay shared
+  p->d_Hx = p->d_Ax = p->d_H1 = p->d_Q = p->d_partials = nullptr;
+  p->d_stage_img = p->d_stage_sino = nullptr;
+  p->d_err = nullptr;
+  p->prof = nullptr;
+  p->launches = 0;
+  p->device_bytes = 0;
+  p->shared->refs++;
+  Alloc al{p, false};
+  int rc = CPCT_OK;
+  const size_t hx_bytes = sizeof(float2) * (size_t)p->ext_rows * p->ldh;
+  if ((rc = al((void**)&p->d_Hx, hx_bytes)) || (rc = al((void**)&p->d_Ax, hx_bytes)) ||
+      (rc = al((void**)&p->d_H1, sizeof(float2) * (size_t)(p->n + 1) * p->n)) ||
+      (rc = al((void**)&p->d_Q, sizeof(float2) * (size_t)p->m * p->ldq)) || (rc = al((void**)&p->d_err, sizeof(int))) ||
+      (rc = al((void**)&p->d_partials, sizeof(float2) * (size_t)std::max(1, p->n_slots) * CPCT_TILE * CPCT_TILE))) {
+    free_plan(p);
+    return rc;
+  }
+  if (cudaMemsetAsync(p->d_Hx, 0, hx_bytes, stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_Ax, 0, hx_bytes, stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_Q, 0, sizeof(float2) * (size_t)p->m * p->ldq, stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_err, 0, sizeof(int), stream) != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) {
+    free_plan(p);
+    return CPCT_ECUDA;
+  }
+  if ((rc = encode_hx_map(p)) != CPCT_OK) {
+    free_plan(p);
+    return rc;
+  }
+  *out = p;
+  return CPCT_OK;
+}
+
+namespace {
+
+// install forward items built with `cap` samples per item
+int install_fwd_items(cpct_plan* p, int cap, cudaStream_t s) {
+  cpct_detail::Bins b;
+  b.ptr = p->shared->fwd_tile_ptr;
+  b.tiles_x = p->tiles_x_fwd;
+  b.tiles_y = p->tiles_y_fwd;
+  std::vector<int4> items, split;
+  cpct_detail::make_items(b, cap, false, items, split, nullptr);
+  int4* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int4) * std::max<size_t>(1, items.size())) != cudaSuccess) return CPCT_ENOMEM;
+  if (cudaMemcpyAsync(d, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaFree(d);
+    return CPCT_ECUDA;
+  }
+  cudaFree(p->d_fwd_items);
+  p->d_fwd_items = d;
+  p->n_fwd_items = (int)items.size();
+  p->fwd_cap = cap;
+  return CPCT_OK;
+}
+
+// install adjoint items (and split list, partial tiles) with `cap` rounds per item
+int install_adj_items(cpct_plan* p, int cap, cudaStream_t s) {
+  cpct_detail::Rounds r;
+  r.tile_ptr = p->shared->round_tile_ptr;
+  std::vector<int4> items, split;
+  std::vector<int> item_split;
+  int n_slots = 0;
+  cpct_detail::make_round_items(r, cap, items, split, &n_slots, item_split);
+  int4 *di = nullptr, *ds = nullptr;
+  float2* dp = nullptr;
+  if (cudaMalloc(&di, sizeof(int4) * std::max<size_t>(1, items.size())) != cudaSuccess ||
+      cudaMalloc(&ds, sizeof(int4) * std::max<size_t>(1, split.size())) != cudaSuccess ||
+      cudaMalloc(&dp, sizeof(float2) * (size_t)std::max(1, n_slots) * CPCT_TILE * CPCT_TILE) != cudaSuccess) {
+    if (di) cudaFree(di);
+    if (ds) cudaFree(ds);
+    return CPCT_ENOMEM;
+  }
+  cudaMemcpyAsync(di, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s);
+  if (!split.empty()) cudaMemcpyAsync(ds, split.data(), sizeof(int4) * split.size(), cudaMemcpyHostToDevice, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaFree(di);
+    cudaFree(ds);
+    cudaFree(dp);
+    return CPCT_ECUDA;
+  }
+  cudaFree(p->d_adj_items);
+  cudaFree(p->d_split);
+  cudaFree(p->d_partials);
+  p->d_adj_items = di;
+  p->d_split = ds;
+  p->d_partials = dp;
+  p->n_adj_items = (int)items.size();
+  p->n_split = (int)split.size();
+  p->n_slots = n_slots;
+  p->adj_cap = cap;
+  return CPCT_OK;
+}
+
+}  // namespace
+
+// Autotuner of the work-item caps (how many samples a forward gather item and
+// how many rounds an adjoint spread item may hold): every candidate is timed
+// (median of `reps` launches, CUDA events on `stream`) and the fastest kept.
+extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap, cudaStream_t stream) {
+  if (!p || !p->shared) return CPCT_EINVAL;
+  if (p->shared->refs != 1) return CPCT_EINVAL;  // tune before cloning
+  if (reps < 1) reps = 5;
+  float *img = nullptr, *sino = nullptr;
+  if (cudaMalloc(&img, sizeof(float) * (size_t)p->n * p->n) != cudaSuccess) return CPCT_ENOMEM;
+  if (cudaMalloc(&sino, sizeof(float) * (size_t)p->m * p->ns) != cudaSuccess) {
+    cudaFree(img);
+    return CPCT_ENOMEM;
+  }
+  cudaMemsetAsync(img, 0, sizeof(float) * (size_t)p->n * p->n, stream);
+  cudaMemsetAsync(sino, 0, sizeof(float) * (size_t)p->m * p->ns, stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_op = [&](bool fwd) {
+    std::vector<float> t;
+    for (int r = 0; r < reps + 1; ++r) {
+      cudaEventRecord(e0, stream);
+      if (fwd) cpct_launch_fwd(p, img, sino, stream);
+      else cpct_launch_adj(p, sino, img, stream);
+      cudaEventRecord(e1, stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) t.push_back(ms);  // the first launch warms up
+    }
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
+  };
+  int rc = CPCT_OK;
+  const int fcands[] = {256, 512, 1024, 2048, 4096};
+  const int acands[] = {16, 32, 64, 128, 256};
+  int best_f = p->fwd_cap, best_a = p->adj_cap;
+  float tf = 1e30f, ta = 1e30f;
+  for (int c : fcands) {
+    if ((rc = install_fwd_items(p, c, stream)) != CPCT_OK) break;
+    const float t = time_op(true);
+    if (t < tf) { tf = t; best_f = c; }
+  }
+  if (rc == CPCT_OK) rc = install_fwd_items(p, best_f, stream);
+  for (int c : acands) {
+    if (rc != CPCT_OK) break;
+    if ((rc = install_adj_items(p, c, stream)) != CPCT_OK) break;
+    const float t = time_op(false);
+    if (t < ta) { ta = t; best_a = c; }
+  }
+  if (rc == CPCT_OK) rc = install_adj_items(p, best_a, stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(img);
+  cudaFree(sino);
+  if (fwd_cap) *fwd_cap = p->fwd_cap;
+  if (adj_cap) *adj_cap = p->adj_cap;
+  return rc;
 }
