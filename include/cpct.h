@@ -205,9 +205,10 @@ typedef struct spgl1_info {
 /* Basis-pursuit denoising  min ||x||_1  s.t.  ||F(R x - b)||_2 <= sigma  by
  * SPGL1 (van den Berg & Friedlander 2008): Newton root-finding on the Pareto
  * curve tau -> ||r_tau||, each LASSO subproblem solved by spectral projected
- * gradient with a non-monotone arc search; FP32 vectors, FP64 reductions and
+ * gradient with a non-monotone arc search; FP32 per-element work, partial
+ * sums combined in FP64, exact l1-ball projection (cpct_project_l1), and the
  * controller (tau-sigma Newton step, Armijo test, Barzilai-Borwein step,
- * duality gap) on the device, one CUDA graph per iteration tick.
+ * duality gap) in FP64 on the device, one CUDA graph per iteration tick.
  *   d_b     device, M*Ns float32 data (read)
  *   sigma   misfit bound eps >= 0 (0: basis pursuit)
  *   d_x     device, N*N float32: in = warm start (zeros for a cold start),
@@ -227,6 +228,26 @@ int spgl1_solve(cpct_plan* plan, const float* d_b, double sigma, float* d_x, con
  * info is an array of `batch` records. */
 int spgl1_solve_batched(cpct_plan* const* plans, int batch, const float* const* d_b, const double* sigma,
                         float* const* d_x, const spgl1_opts* opts, spgl1_info* info, cudaStream_t stream);
+
+/* Euclidean projection onto the l1 ball {x : ||x||_1 <= tau}, the
+ * projection step of SPGL1's spectral projected gradient (van den Berg &
+ * Friedlander 2008; the L1 problem of section "Introduction"):
+ *   out_i = sign(v_i) max(|v_i| - theta, 0),  theta >= 0 the root of
+ *   sum_i max(|v_i| - theta, 0) = tau;  out = v and theta = 0 when
+ *   ||v||_1 <= tau;  out = 0 (theta reported as 0) when tau <= 0.
+ * theta is exact for the FP32 input: the set of |v_i| above it is found by a
+ * radix selection on the float bit patterns with exact integer bin sums, and
+ * theta = (sum of that set - tau) / its size is evaluated in FP64; out is
+ * rounded to FP32.  Deterministic, sort-free, three histogram passes.
+ *   d_v     device, n float32 (read; finite values)
+ *   n       1 <= n <= 2^30
+ *   tau     radius (finite)
+ *   d_out   device, n float32 (may alias d_v)
+ *   theta   host, may be NULL: the threshold (FP64)
+ * Returns CPCT_OK, CPCT_EINVAL (null pointer, n or tau out of range),
+ * CPCT_ENOMEM, CPCT_ECUDA.  Allocates a small workspace (about 30 KB) for
+ * the call and synchronizes `stream`. */
+int cpct_project_l1(const float* d_v, long long n, double tau, float* d_out, double* theta, cudaStream_t stream);
 
 /* Allocation-free adjoint.  Some callers cannot allocate device memory at
  * the point where they apply the operator: code running under an allocator

@@ -278,7 +278,24 @@ def _spgl1_setup():
     L.spgl1_solve_batched.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vp),
                                       ctypes.POINTER(Spgl1Opts), ctypes.POINTER(Spgl1Info), vp]
+    L.cpct_project_l1.argtypes = [vp, ctypes.c_longlong, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_double), vp]
     return L
+
+
+def project_l1(v, tau, out=None, stream=None):
+    """Projection of the float32 CUDA tensor ``v`` onto {||x||_1 <= tau}.
+
+    Returns (out, theta) with out_i = sign(v_i) max(|v_i| - theta, 0).
+    """
+    import torch
+    L = _spgl1_setup()
+    if out is None:
+        out = torch.empty_like(v)
+    th = ctypes.c_double()
+    check(L.cpct_project_l1(_dev_ptr(v, tuple(v.shape), torch), v.numel(), float(tau),
+                            _dev_ptr(out, tuple(v.shape), torch), ctypes.byref(th), _stream(torch, stream)),
+          "cpct_project_l1")
+    return out, th.value
 
 
 def make_opts(max_iter=0, opt_tol=0.0, bp_tol=0.0, memory=0, max_line=0, tau0=None, ring_filter=True):

@@ -209,8 +209,14 @@ namespace {
 enum TickType { T_INIT = 0, T_PG = 1, T_PROJX = 2, T_TRIAL = 3 };
 enum AfterPG { PG_THEN_CHECK = 0, PG_THEN_TRIAL = 1 };
 constexpr int kHist = 8;        // objective history capacity (memory <= 8)
-constexpr int kCand = 16;       // candidate thresholds per multi-section pass
-constexpr int kPasses = 8;      // multi-section passes per projection
+// l1-ball projection by radix selection on the FP32 bit patterns of |v|
+// (non-negative floats order like their patterns): three passes over bits
+// 30..20, 19..9 and 8..0; a bin of any pass holds values of one exponent, so
+// its sum is an exact integer sum of 24-bit significands times a power of 2
+constexpr int kRadixPasses = 3;
+constexpr int kBins = 2048;
+__host__ __device__ constexpr int radix_shift(int p) { return p == 0 ? 20 : p == 1 ? 9 : 0; }
+__host__ __device__ constexpr int radix_bits(int p) { return p == 2 ? 9 : 11; }
 constexpr double kDecTol = 1e-4;  // stagnation threshold of the inexact Newton test
 
 struct SpgState {
@@ -226,8 +232,9 @@ struct SpgState {
   int type, pg_then, accept_x, accept_r, update_g, line_fail;
   double ps;
   // projection of v = x - ps g onto the l1 ball of radius tau
-  double lo, hi, theta, c_lo, s_lo;
-  int proj_done, proj_identity, proj_zero, pad1;
+  double theta, c_above, s_above;  // threshold; count and sum of |v| above the selected prefix
+  unsigned prefix;                  // selected high bits of the pattern of theta
+  int proj_done, proj_identity, proj_zero;
   // mid-tick results
   double ft, gtd, dn2, dinf, rtb_t;
   // counters / status
@@ -241,103 +248,133 @@ struct SpgVec {
   float *x, *xt, *xold, *g, *gold, *gtmp;  // image space, n
   float *y, *rt, *r, *bf;                  // sinogram space, m
   double* part;                            // per-block partials
+  unsigned* hcnt;                          // radix histogram: counts (kBins)
+  unsigned long long* hsum;                // radix histogram: significand sums (kBins)
   SpgState* st;
   long long n, m;
 };
 
 // partial buffer regions (each kRG doubles per quantity)
-constexpr int P_VSTAT = 0;                  // 2: sum|v|, max|v|
-constexpr int P_PROJ = 2;                   // 2*(kCand+1): counts, sums
-constexpr int P_APPLY = P_PROJ + 2 * (kCand + 1);  // 3: gtd, dn2, dinf
+constexpr int P_APPLY = 0;                  // 3: gtd, dn2, dinf
 constexpr int P_RES = P_APPLY + 3;          // 2: sum rt^2, sum rt*bf
 constexpr int P_GRAD = P_RES + 2;           // 4: sts, sty, ginf, gnorm2
 constexpr int P_TOTAL = P_GRAD + 4;
 
 __device__ __forceinline__ double pget(const double* part, int q, int b) { return part[(size_t)q * kRG + b]; }
 
-// v_i = x_i - ps g_i
-__device__ __forceinline__ float vval(const SpgVec& V, double ps, long long i) {
-  return (float)((double)V.x[i] - ps * (double)V.g[i]);
-}
-
-__global__ void __launch_bounds__(kRB) k_spg_vstats(SpgVec V) {
-  const SpgState* st = V.st;
-  if (st->done) return;
-  const double ps = st->ps;
-  double s[1] = {0.0};
-  double mx = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += (long long)gridDim.x * blockDim.x) {
-    const double a = fabs((double)vval(V, ps, i));
-    s[0] += a;
-    mx = fmax(mx, a);
-  }
-  block_sum<1>(s);
-  mx = block_max(mx);
-  if (threadIdx.x == 0) {
-    V.part[(size_t)(P_VSTAT + 0) * kRG + blockIdx.x] = s[0];
-    V.part[(size_t)(P_VSTAT + 1) * kRG + blockIdx.x] = mx;
-  }
-}
-
-// one multi-section pass: counts and sums of |v| above kCand+1 thresholds
-// t_c = lo + (hi - lo) c / kCand, c = 0..kCand
-__global__ void __launch_bounds__(kRB) k_spg_proj_pass(SpgVec V) {
-  const SpgState* st = V.st;
-  if (st->done || st->proj_done) return;
-  const double ps = st->ps, lo = st->lo, w = (st->hi - st->lo) / kCand;
-  double cnt[kCand + 1], sum[kCand + 1];
+// FP64 throughput is a small fraction of FP32 on this GPU, so every
+// per-element operation and per-thread / per-warp partial is FP32 (counts are
+// integers) and FP64 only combines the 8 warp partials of a block and the 256
+// block partials of a grid, in a fixed order.
+template <int NQ>
+__device__ __forceinline__ void block_sum_f(float (&v)[NQ], double (&out)[NQ]) {
+  __shared__ float sh[NQ][kRB / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int c = 0; c <= kCand; ++c) { cnt[c] = 0.0; sum[c] = 0.0; }
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += (long long)gridDim.x * blockDim.x) {
-    const double a = fabs((double)vval(V, ps, i));
-    if (a <= lo) continue;
+  for (int q = 0; q < NQ; ++q) {
+    float t = v[q];
 #pragma unroll
-    for (int c = 0; c <= kCand; ++c) {
-      const bool above = a > lo + w * c;
-      cnt[c] += above ? 1.0 : 0.0;
-      sum[c] += above ? a : 0.0;
-    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[q][w] = t;
   }
-  block_sum<kCand + 1>(cnt);
-  block_sum<kCand + 1>(sum);
+  __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int c = 0; c <= kCand; ++c) {
-      V.part[(size_t)(P_PROJ + c) * kRG + blockIdx.x] = cnt[c];
-      V.part[(size_t)(P_PROJ + kCand + 1 + c) * kRG + blockIdx.x] = sum[c];
+    for (int q = 0; q < NQ; ++q) {
+      double t = 0.0;
+      for (int i = 0; i < kRB / 32; ++i) t += (double)sh[q][i];
+      out[q] = t;
     }
   }
+  __syncthreads();
+}
+
+__device__ __forceinline__ float block_max_f(float v) {
+  __shared__ float sh[kRB / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 1; i < kRB / 32; ++i) v = fmaxf(v, sh[i]);
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ void put(double* part, int q, double v) { part[(size_t)q * kRG + blockIdx.x] = v; }
+
+// v_i = x_i - ps g_i (FP32)
+__device__ __forceinline__ float vval(const SpgVec& V, float ps, long long i) { return fmaf(-ps, V.g[i], V.x[i]); }
+
+#define SPG_LOOP(i, len) \
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (len); i += (long long)gridDim.x * blockDim.x)
+
+// histogram of the patterns u of |v_i| that carry the prefix selected so far
+// (pass 0: all), binned by the pass's bits; zeros are skipped (they never lie
+// above a threshold >= 0).  Shared-memory integer atomics, then one global
+// integer atomic per non-empty bin: the result is independent of order.
+__global__ void __launch_bounds__(kRB) k_spg_radix_hist(SpgVec V, int pass) {
+  const SpgState* st = V.st;
+  if (st->done || (pass > 0 && st->proj_done)) return;
+  __shared__ unsigned hc[kBins];
+  __shared__ unsigned long long hs[kBins];
+  for (int b = threadIdx.x; b < kBins; b += kRB) {
+    hc[b] = 0u;
+    hs[b] = 0ull;
+  }
+  __syncthreads();
+  const float ps = (float)st->ps;
+  const int shift = radix_shift(pass), top = shift + radix_bits(pass);
+  const unsigned mask = (1u << radix_bits(pass)) - 1u;
+  const unsigned prefix = pass > 0 ? st->prefix : 0u;
+  SPG_LOOP(i, V.n) {
+    const unsigned u = __float_as_uint(fabsf(vval(V, ps, i)));
+    if (u == 0u || (u >> top) != prefix) continue;
+    const unsigned e = u >> 23;
+    const unsigned sig = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const unsigned b = (u >> shift) & mask;
+    atomicAdd(&hc[b], 1u);
+    atomicAdd(&hs[b], (unsigned long long)sig);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kBins; b += kRB)
+    if (hc[b]) {
+      atomicAdd(&V.hcnt[b], hc[b]);
+      atomicAdd(&V.hsum[b], hs[b]);
+    }
 }
 
 // xt = soft(v, theta) and the partials needed by the controllers
 __global__ void __launch_bounds__(kRB) k_spg_proj_apply(SpgVec V) {
   const SpgState* st = V.st;
   if (st->done) return;
-  const double ps = st->ps, th = st->theta;
+  const float ps = (float)st->ps, th = (float)st->theta;
   const int ident = st->proj_identity, zero = st->proj_zero;
-  double q[2] = {0.0, 0.0};  // gtd, dn2
-  double dinf = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += (long long)gridDim.x * blockDim.x) {
+  float q[2] = {0.f, 0.f};  // gtd, dn2
+  float dinf = 0.f;
+  SPG_LOOP(i, V.n) {
     const float v = vval(V, ps, i);
     float xt;
     if (zero) xt = 0.f;
     else if (ident) xt = v;
     else {
-      const double a = fabs((double)v) - th;
-      xt = a > 0.0 ? copysignf((float)a, v) : 0.f;
+      const float a = fabsf(v) - th;
+      xt = a > 0.f ? copysignf(a, v) : 0.f;
     }
     V.xt[i] = xt;
-    const double d = (double)xt - (double)V.x[i];
-    q[0] += (double)V.g[i] * d;
-    q[1] += d * d;
-    dinf = fmax(dinf, fabs(d));
+    const float d = xt - V.x[i];
+    q[0] = fmaf(V.g[i], d, q[0]);
+    q[1] = fmaf(d, d, q[1]);
+    dinf = fmaxf(dinf, fabsf(d));
   }
-  block_sum<2>(q);
-  dinf = block_max(dinf);
+  double o[2];
+  block_sum_f<2>(q, o);
+  dinf = block_max_f(dinf);
   if (threadIdx.x == 0) {
-    V.part[(size_t)(P_APPLY + 0) * kRG + blockIdx.x] = q[0];
-    V.part[(size_t)(P_APPLY + 1) * kRG + blockIdx.x] = q[1];
-    V.part[(size_t)(P_APPLY + 2) * kRG + blockIdx.x] = dinf;
+    put(V.part, P_APPLY + 0, o[0]);
+    put(V.part, P_APPLY + 1, o[1]);
+    put(V.part, P_APPLY + 2, (double)dinf);
   }
 }
 
@@ -345,18 +382,19 @@ __global__ void __launch_bounds__(kRB) k_spg_proj_apply(SpgVec V) {
 __global__ void __launch_bounds__(kRB) k_spg_resid(SpgVec V, const float* __restrict__ doff, int ns, int filter) {
   const SpgState* st = V.st;
   if (st->done) return;
-  double q[2] = {0.0, 0.0};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V.m; i += (long long)gridDim.x * blockDim.x) {
+  float q[2] = {0.f, 0.f};
+  SPG_LOOP(i, V.m) {
     const float fy = filter ? V.y[i] - doff[i % ns] : V.y[i];
     const float r = V.bf[i] - fy;
     V.rt[i] = r;
-    q[0] += (double)r * r;
-    q[1] += (double)r * V.bf[i];
+    q[0] = fmaf(r, r, q[0]);
+    q[1] = fmaf(r, V.bf[i], q[1]);
   }
-  block_sum<2>(q);
+  double o[2];
+  block_sum_f<2>(q, o);
   if (threadIdx.x == 0) {
-    V.part[(size_t)(P_RES + 0) * kRG + blockIdx.x] = q[0];
-    V.part[(size_t)(P_RES + 1) * kRG + blockIdx.x] = q[1];
+    put(V.part, P_RES + 0, o[0]);
+    put(V.part, P_RES + 1, o[1]);
   }
 }
 
@@ -364,39 +402,38 @@ __global__ void __launch_bounds__(kRB) k_spg_accept(SpgVec V) {
   const SpgState* st = V.st;
   if (st->done) return;
   const int ax = st->accept_x, ar = st->accept_r;
-  const long long stride = (long long)gridDim.x * blockDim.x, i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (ax)
-    for (long long i = i0; i < V.n; i += stride) {
+    SPG_LOOP(i, V.n) {
       V.xold[i] = V.x[i];
       V.x[i] = V.xt[i];
     }
-  if (ar)
-    for (long long i = i0; i < V.m; i += stride) V.r[i] = V.rt[i];
+  if (ar) SPG_LOOP(i, V.m) V.r[i] = V.rt[i];
 }
 
 // g = -A^T r (gtmp holds R^T r; F r = r because r lies in the range of F)
 __global__ void __launch_bounds__(kRB) k_spg_grad(SpgVec V) {
   const SpgState* st = V.st;
   if (st->done || !st->update_g) return;
-  double q[3] = {0.0, 0.0, 0.0};  // sts, sty, gnorm2
-  double ginf = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += (long long)gridDim.x * blockDim.x) {
+  float q[3] = {0.f, 0.f, 0.f};  // sts, sty, gnorm2
+  float ginf = 0.f;
+  SPG_LOOP(i, V.n) {
     const float go = V.g[i], gn = -V.gtmp[i];
     V.gold[i] = go;
     V.g[i] = gn;
-    const double s = (double)V.x[i] - (double)V.xold[i], yv = (double)gn - (double)go;
-    q[0] += s * s;
-    q[1] += s * yv;
-    q[2] += (double)gn * gn;
-    ginf = fmax(ginf, fabs((double)gn));
+    const float sv = V.x[i] - V.xold[i], yv = gn - go;
+    q[0] = fmaf(sv, sv, q[0]);
+    q[1] = fmaf(sv, yv, q[1]);
+    q[2] = fmaf(gn, gn, q[2]);
+    ginf = fmaxf(ginf, fabsf(gn));
   }
-  block_sum<3>(q);
-  ginf = block_max(ginf);
+  double o[3];
+  block_sum_f<3>(q, o);
+  ginf = block_max_f(ginf);
   if (threadIdx.x == 0) {
-    V.part[(size_t)(P_GRAD + 0) * kRG + blockIdx.x] = q[0];
-    V.part[(size_t)(P_GRAD + 1) * kRG + blockIdx.x] = q[1];
-    V.part[(size_t)(P_GRAD + 2) * kRG + blockIdx.x] = q[2];
-    V.part[(size_t)(P_GRAD + 3) * kRG + blockIdx.x] = ginf;
+    put(V.part, P_GRAD + 0, o[0]);
+    put(V.part, P_GRAD + 1, o[1]);
+    put(V.part, P_GRAD + 2, o[2]);
+    put(V.part, P_GRAD + 3, (double)ginf);
   }
 }
 
@@ -404,65 +441,138 @@ __global__ void __launch_bounds__(kRB) k_spg_grad(SpgVec V) {
 
 namespace {
 
-// block-parallel fixed-order sum of partials q0..q0+NQ-1 (thread 0 gets them)
+// fixed-order sums of the block partials of quantities q0..q0+NQ-1 (one
+// warp per quantity: strided FP64 sums, then a shuffle tree); every thread
+// gets the results
 template <int NQ>
 __device__ __forceinline__ void gather_sums(const double* part, int q0, double (&v)[NQ]) {
+  __shared__ double res[NQ];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int q = w; q < NQ; q += kRB / 32) {
+    double t = 0.0;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) v[q] = threadIdx.x < kRG ? part[(size_t)(q0 + q) * kRG + threadIdx.x] : 0.0;
-  block_sum<NQ>(v);
+    for (int b = lane; b < kRG; b += 32) t += part[(size_t)(q0 + q) * kRG + b];
+    t = warp_sum(t);
+    if (lane == 0) res[q] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = res[q];
+  __syncthreads();
 }
 __device__ __forceinline__ double gather_max(const double* part, int q) {
-  return block_max(threadIdx.x < kRG ? part[(size_t)q * kRG + threadIdx.x] : 0.0);
-}
-
-// choose the sub-interval of the bracket that holds theta (block-parallel
-// reduction of the pass partials); finish when it holds no |v_i|: the active
-// set is then fixed and theta = (sum of active |v_i| - tau) / their count
-__global__ void __launch_bounds__(kRB) k_spg_proj_pick2(SpgVec V, int last_pass) {
-  SpgState* st = V.st;
-  if (st->done || st->proj_done) return;
-  double C[kCand + 1], S[kCand + 1];
-  gather_sums<kCand + 1>(V.part, P_PROJ, C);
-  gather_sums<kCand + 1>(V.part, P_PROJ + kCand + 1, S);
-  if (threadIdx.x != 0) return;
-  const double lo = st->lo, w = (st->hi - st->lo) / kCand, tau = st->tau;
-  int c = 1;
-  for (; c < kCand; ++c)
-    if (S[c] - (lo + w * c) * C[c] - tau <= 0.0) break;
-  if (C[c - 1] == C[c] || last_pass || w <= 1e-15 * st->hi) {
-    const double t0 = lo + w * (c - 1), t1 = lo + w * c;
-    const double th = C[c] > 0.0 ? (S[c] - tau) / C[c] : t1;
-    st->theta = C[c - 1] == C[c] ? th : fmin(fmax(th, t0), t1);
-    st->proj_done = 1;
-  } else {
-    st->lo = lo + w * (c - 1);
-    st->hi = lo + w * c;
+  __shared__ double res;
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < kRG; b += 32) t = fmax(t, part[(size_t)q * kRG + b]);
+    t = warp_max(t);
+    if (threadIdx.x == 0) res = t;
   }
+  __syncthreads();
+  const double r = res;
+  __syncthreads();
+  return r;
 }
 
-// start of the projection: the threshold theta solves
-// sum_i max(|v_i| - theta, 0) = tau; it lies in [max(0, max|v| - tau), max|v|]
-__global__ void __launch_bounds__(kRB) k_spg_proj_begin2(SpgVec V) {
+// one radix-select step.  phi(t) = sum_i max(|v_i| - t, 0) - tau decreases
+// in t; at the lower edge t_b of bin b it is (S_above + S_{>=b}) - t_b
+// (C_above + C_{>=b}) - tau.  theta lies in the highest bin b* with
+// phi(t_b*) > 0.  If b* holds no value, or its values are all equal (last
+// pass), the active set is exactly the values above it and theta =
+// (S - tau) / C over that set; otherwise the next pass refines inside b*.
+// Pass 0 also decides the two trivial cases: tau <= 0 (projection is 0) and
+// ||v||_1 <= tau (projection is v).  The kernel consumes and re-zeroes the
+// histogram.
+__global__ void __launch_bounds__(kRB) k_spg_radix_select(SpgVec V, int pass) {
   SpgState* st = V.st;
-  if (st->done) return;
-  double s[1];
-  gather_sums<1>(V.part, P_VSTAT, s);
-  const double mx = gather_max(V.part, P_VSTAT + 1);
-  if (threadIdx.x != 0) return;
-  st->proj_identity = 0;
-  st->proj_zero = 0;
-  if (st->tau <= 0.0) {
-    st->proj_zero = 1;
-    st->proj_done = 1;
-    st->theta = mx;
-  } else if (s[0] <= st->tau) {
-    st->proj_identity = 1;
-    st->proj_done = 1;
+  if (st->done || (pass > 0 && st->proj_done)) return;
+  constexpr int kPer = kBins / kRB;
+  __shared__ double scan_c[kRB], scan_s[kRB];
+  __shared__ int best;
+  const int shift = radix_shift(pass), nb = radix_bits(pass), nbins = 1 << nb;
+  const unsigned prefix = pass > 0 ? st->prefix : 0u;
+  const double c_above = pass > 0 ? st->c_above : 0.0, s_above = pass > 0 ? st->s_above : 0.0;
+  const double tau = st->tau;
+  const int b0 = threadIdx.x * kPer;
+  double c[kPer], s[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int b = b0 + k;
+    c[k] = 0.0;
+    s[k] = 0.0;
+    if (b < nbins) {
+      const unsigned pat = (prefix << (shift + nb)) | ((unsigned)b << shift);
+      const int e = (int)(pat >> 23);
+      c[k] = (double)V.hcnt[b];
+      s[k] = ldexp((double)V.hsum[b], (e > 0 ? e : 1) - 150);
+      V.hcnt[b] = 0u;
+      V.hsum[b] = 0ull;
+    }
+  }
+  // inclusive suffix sums over bins: within the thread, then across threads
+  double tc = 0.0, ts = 0.0;
+#pragma unroll
+  for (int k = kPer - 1; k >= 0; --k) {
+    tc += c[k];
+    ts += s[k];
+  }
+  scan_c[threadIdx.x] = tc;
+  scan_s[threadIdx.x] = ts;
+  if (threadIdx.x == 0) best = 0;
+  __syncthreads();
+  for (int off = 1; off < kRB; off <<= 1) {
+    const double ac = threadIdx.x + off < kRB ? scan_c[threadIdx.x + off] : 0.0;
+    const double as = threadIdx.x + off < kRB ? scan_s[threadIdx.x + off] : 0.0;
+    __syncthreads();
+    scan_c[threadIdx.x] += ac;
+    scan_s[threadIdx.x] += as;
+    __syncthreads();
+  }
+  // bins above this thread's chunk
+  double xc = threadIdx.x + 1 < kRB ? scan_c[threadIdx.x + 1] : 0.0;
+  double xs = threadIdx.x + 1 < kRB ? scan_s[threadIdx.x + 1] : 0.0;
+  double cx[kPer], sx[kPer];  // counts and sums strictly above each bin
+  int mine = -1;
+#pragma unroll
+  for (int k = kPer - 1; k >= 0; --k) {
+    cx[k] = xc;
+    sx[k] = xs;
+    xc += c[k];
+    xs += s[k];
+    const int b = b0 + k;
+    if (mine < 0 && b < nbins) {
+      const double t = (double)__uint_as_float((prefix << (shift + nb)) | ((unsigned)b << shift));
+      const double phi = (s_above + xs) - t * (c_above + xc) - tau;
+      if (phi > 0.0) mine = b;
+    }
+  }
+  if (pass == 0 && threadIdx.x == 0) {
+    const double total = scan_s[0];
+    st->proj_zero = tau <= 0.0;
+    st->proj_identity = tau > 0.0 && total <= tau;
+    st->proj_done = st->proj_zero || st->proj_identity;
     st->theta = 0.0;
+  }
+  if (mine >= 0) atomicMax(&best, mine);
+  __syncthreads();
+  if (st->proj_done || threadIdx.x != best / kPer) return;
+  const int k = best - b0;
+  double ck = 0.0, cxk = 0.0, sxk = 0.0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q)
+    if (q == k) {
+      ck = c[q];
+      cxk = cx[q];
+      sxk = sx[q];
+    }
+  if (ck == 0.0 || pass == kRadixPasses - 1) {
+    const double cnt = c_above + cxk;
+    st->theta = cnt > 0.0 ? fmax((s_above + sxk - tau) / cnt, 0.0) : 0.0;
+    st->proj_done = 1;
   } else {
-    st->proj_done = 0;
-    st->lo = fmax(0.0, mx - st->tau);
-    st->hi = mx;
+    st->prefix = (prefix << nb) | (unsigned)best;
+    st->c_above = c_above + cxk;
+    st->s_above = s_above + sxk;
   }
 }
 
@@ -707,11 +817,9 @@ struct SliceWork {
 void enqueue_tick(SliceWork& w, int filter) {
   cudaStream_t s = w.stream;
   SpgVec V = w.V;
-  k_spg_vstats<<<kRG, kRB, 0, s>>>(V);
-  k_spg_proj_begin2<<<1, kRB, 0, s>>>(V);
-  for (int pass = 0; pass < kPasses; ++pass) {
-    k_spg_proj_pass<<<kRG, kRB, 0, s>>>(V);
-    k_spg_proj_pick2<<<1, kRB, 0, s>>>(V, pass == kPasses - 1);
+  for (int pass = 0; pass < kRadixPasses; ++pass) {
+    k_spg_radix_hist<<<kRG, kRB, 0, s>>>(V, pass);
+    k_spg_radix_select<<<1, kRB, 0, s>>>(V, pass);
   }
   k_spg_proj_apply<<<kRG, kRB, 0, s>>>(V);
   cpct_launch_fwd(w.plan, V.xt, V.y, s);
@@ -761,6 +869,7 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
   std::vector<SliceWork> ws(batch);
   SpgState* d_states = nullptr;
   double* d_part = nullptr;
+  unsigned char* d_hist = nullptr;  // per slice: kBins counts, then (all slices) kBins sums
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t fork = nullptr;
@@ -776,6 +885,9 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
   };
   if (!cuda(cudaMalloc(&d_states, sizeof(SpgState) * batch))) goto done;
   if (!cuda(cudaMalloc(&d_part, sizeof(double) * P_TOTAL * kRG * batch))) goto done;
+  if (!cuda(cudaMalloc(&d_hist, (sizeof(unsigned) + sizeof(unsigned long long)) * kBins * batch))) goto done;
+  if (!cuda(cudaMemsetAsync(d_hist, 0, (sizeof(unsigned) + sizeof(unsigned long long)) * kBins * batch, stream)))
+    goto done;
   for (int i = 0; i < batch; ++i) {
     SliceWork& w = ws[i];
     w.plan = plans[i];
@@ -798,6 +910,8 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
     V.r = V.rt + m;
     V.bf = V.r + m;
     V.part = d_part + (size_t)i * P_TOTAL * kRG;
+    V.hcnt = reinterpret_cast<unsigned*>(d_hist) + (size_t)i * kBins;
+    V.hsum = reinterpret_cast<unsigned long long*>(d_hist + sizeof(unsigned) * kBins * batch) + (size_t)i * kBins;
     V.st = d_states + i;
     if ((rc = ring_work(w.plan->ns, w.ring, stream)) != CPCT_OK) goto done;
     w.stream = stream;
@@ -926,10 +1040,53 @@ done:
   if (cap) cudaStreamDestroy(cap);
   if (d_states) cudaFree(d_states);
   if (d_part) cudaFree(d_part);
+  if (d_hist) cudaFree(d_hist);
   return rc;
 }
 
 extern "C" int spgl1_solve(cpct_plan* plan, const float* d_b, double sigma, float* d_x, const spgl1_opts* opts,
                            spgl1_info* info, cudaStream_t stream) {
   return spgl1_solve_batched(&plan, 1, &d_b, &sigma, &d_x, opts, info, stream);
+}
+
+extern "C" int cpct_project_l1(const float* d_v, long long n, double tau, float* d_out, double* theta,
+                               cudaStream_t stream) {
+  if (!d_v || !d_out || n < 1 || n > (1LL << 30) || !std::isfinite(tau)) return CPCT_EINVAL;
+  // workspace: state, partials of the apply kernel, histogram
+  const size_t b_state = (sizeof(SpgState) + 255) / 256 * 256;
+  const size_t b_part = sizeof(double) * P_TOTAL * kRG;
+  const size_t b_cnt = sizeof(unsigned) * kBins;
+  unsigned char* mem = nullptr;
+  if (cudaMalloc(&mem, b_state + b_part + b_cnt + sizeof(unsigned long long) * kBins) != cudaSuccess)
+    return CPCT_ENOMEM;
+  SpgState st;
+  std::memset(&st, 0, sizeof(st));
+  st.tau = tau;  // ps = 0: v = x - 0 * g = x
+  SpgVec V{};
+  V.x = const_cast<float*>(d_v);
+  V.g = const_cast<float*>(d_v);
+  V.xt = d_out;
+  V.n = n;
+  V.st = reinterpret_cast<SpgState*>(mem);
+  V.part = reinterpret_cast<double*>(mem + b_state);
+  V.hcnt = reinterpret_cast<unsigned*>(mem + b_state + b_part);
+  V.hsum = reinterpret_cast<unsigned long long*>(mem + b_state + b_part + b_cnt);
+  int rc = CPCT_OK;
+  if (cudaMemcpyAsync(V.st, &st, sizeof(st), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+      cudaMemsetAsync(V.hcnt, 0, b_cnt + sizeof(unsigned long long) * kBins, stream) != cudaSuccess)
+    rc = CPCT_ECUDA;
+  if (rc == CPCT_OK) {
+    for (int pass = 0; pass < kRadixPasses; ++pass) {
+      k_spg_radix_hist<<<kRG, kRB, 0, stream>>>(V, pass);
+      k_spg_radix_select<<<1, kRB, 0, stream>>>(V, pass);
+    }
+    k_spg_proj_apply<<<kRG, kRB, 0, stream>>>(V);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&st, V.st, sizeof(st), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      rc = CPCT_ECUDA;
+  }
+  cudaFree(mem);
+  if (rc == CPCT_OK && theta) *theta = st.proj_zero ? 0.0 : st.theta;
+  return rc;
 }

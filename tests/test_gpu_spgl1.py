@@ -117,3 +117,68 @@ def test_spgl1_warm_start_and_basis_pursuit_flag(torch_cuda):
     # without the filter the stuck columns enter the misfit: a different problem
     x3, i3 = cpct.spgl1(p, bd, sigma, opts=cpct.make_opts(ring_filter=False, max_iter=50))
     assert i3["status"] in (1, 3)
+
+
+def _proj_case(case, rng):
+    if case == "gauss":
+        v = rng.standard_normal(1 << 20)
+        return v, 0.1 * np.abs(v).sum()
+    if case == "sparse":
+        v = rng.standard_normal(1 << 18) * (rng.random(1 << 18) < 0.1)
+        return v, 0.02 * np.abs(v).sum()
+    if case == "ties":
+        v = rng.choice([-3.0, -2.0, -1.0, 1.0, 2.0, 3.0], size=100_003)
+        return v, 0.25 * np.abs(v).sum()
+    if case == "wide":
+        v = np.exp(rng.uniform(-80.0, 20.0, 300_001)) * rng.choice([-1.0, 1.0], 300_001)
+        return v, 0.3 * np.abs(v).sum()
+    if case == "ragged":
+        v = rng.laplace(size=1_000_003)
+        return v, 0.5 * np.abs(v).sum()
+    if case == "one":
+        return np.array([-2.5]), 1.0
+    if case == "identity":
+        v = rng.standard_normal(4097)
+        return v, 1.5 * np.abs(v.astype(np.float32).astype(np.float64)).sum()
+    if case == "zero_tau":
+        return rng.standard_normal(1000), 0.0
+    if case == "zero_v":
+        return np.zeros(5000), 3.0
+    raise ValueError(case)
+
+
+@pytest.mark.parametrize("case", ["gauss", "sparse", "ties", "wide", "ragged", "one", "identity", "zero_tau",
+                                  "zero_v"])
+def test_project_l1_matches_oracle(torch_cuda, case):
+    """The device threshold is exact for the FP32 input: the same active set as
+    the FP64 sort-based oracle, theta to FP64 rounding, outputs to FP32
+    rounding of |v| - theta."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    rng = np.random.default_rng(1380)
+    v, tau = _proj_case(case, rng)
+    v32 = v.astype(np.float32)
+    v64 = v32.astype(np.float64)
+    ref = spgl1.project_l1(v64, tau)
+    vd = torch.from_numpy(v32).cuda()
+    out, theta = cpct.project_l1(vd, tau)
+    out2, theta2 = cpct.project_l1(vd, tau)
+    o = out.cpu().numpy().astype(np.float64)
+    assert torch.equal(out, out2) and theta == theta2
+    act = ref != 0
+    if case in ("identity", "zero_v"):
+        assert theta == 0.0 and np.array_equal(o, v64)
+        return
+    if case == "zero_tau":
+        assert not o.any()
+        return
+    theta_ref = float(np.median(np.abs(v64[act]) - np.abs(ref[act])))
+    assert abs(theta - theta_ref) <= 1e-12 * max(theta_ref, 1e-300), (theta, theta_ref)
+    # active sets agree except for values within FP32 rounding of theta
+    near = np.abs(np.abs(v64) - theta_ref) <= 2 * np.spacing(np.float32(theta_ref))
+    assert np.array_equal((o != 0)[~near], act[~near])
+    ulp = np.spacing(np.abs(v32)).astype(np.float64)
+    assert np.all(np.abs(o - ref) <= ulp + np.spacing(np.float32(theta_ref)))
+    assert np.all(np.sign(o[o != 0]) == np.sign(v64[o != 0]))
+    # ||out||_1 = tau to FP32 rounding of the outputs
+    assert abs(np.abs(o).sum() - tau) <= 1e-6 * tau
