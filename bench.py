@@ -86,7 +86,7 @@ def profile_traffic(kname, workload):
     if want is None or traffic is None:
         return None
     from paper_1009_1380_gb300 import build as b
-    return traffic if b.source_digest() == want else None
+    return traffic if b.radon_digest() == want else None
 
 
 class ClockSampler:

@@ -40,22 +40,36 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _digest() -> str:
+def _hash_files(files) -> str:
     h = hashlib.sha256()
-    files = sources() + sorted(
-        os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))
-    ) + [os.path.join(INCLUDE, f) for f in sorted(os.listdir(INCLUDE))]
     for f in files:
-        h.update(f.encode())
+        h.update(os.path.basename(f).encode())  # names, not paths: equal on every machine
         with open(f, "rb") as fh:
             h.update(fh.read())
     h.update(" ".join(NVCC_FLAGS).encode())
     return h.hexdigest()
 
 
+def _digest() -> str:
+    return _hash_files(sources() + sorted(
+        os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))
+    ) + [os.path.join(INCLUDE, f) for f in sorted(os.listdir(INCLUDE))])
+
+
 def source_digest() -> str:
     """SHA-256 of the CUDA sources, headers and build flags (identifies a kernel version)."""
     return _digest()
+
+
+# files that define the Radon operator kernels (kernels, their headers, and
+# the plan builder whose tables and bins they read)
+RADON_FILES = ("radon.cu", "plan.cu", "common.cuh", "fft.cuh")
+
+
+def radon_digest() -> str:
+    """SHA-256 of the Radon operator's sources and build flags: identifies the
+    kernel version an ncu summary of an operator kernel was taken on."""
+    return _hash_files([os.path.join(CSRC, f) for f in RADON_FILES])
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
