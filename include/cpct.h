@@ -249,6 +249,84 @@ int spgl1_solve_batched(cpct_plan* const* plans, int batch, const float* const* 
  * the call and synchronizes `stream`. */
 int cpct_project_l1(const float* d_v, long long n, double tau, float* d_out, double* theta, cudaStream_t stream);
 
+/* ---- learned warm start: convolutional denoiser (no counterpart in the
+ * paper; the network maps a filtered back-projection to a starting point of
+ * spgl1_solve) ------------------------------------------------------------ */
+
+/* U-Net on single-channel H x W images, `levels` resolution levels, c_l =
+ * base * 2^l channels at level l:
+ *   encoder l = 0..L-1:  h = relu(conv_b(relu(conv_a(x)))), skip_l = h,
+ *                        x = 2x2 average pool of h below the last level;
+ *   decoder l = L-2..0:  u = relu(conv_up(nearest 2x upsample of h)),
+ *                        h = relu(conv_b(relu(conv_a([skip_l, u]))));
+ *   output:              out = x_in + bias + sum_c w_c h_c  (1x1 head).
+ * 3x3 convolutions are cross-correlations with zero padding 1 and a bias.
+ * Loss of a batch: L = sum (out - target)^2 / (2 P) over its P pixels.
+ * Precision: activations and gradients FP32, convolution weights rounded to
+ * BF16 and activations rounded to BF16 inside each tensor-core contraction,
+ * FP32 accumulation; FP32 master weights and Adam state.
+ * Parameter vector (host, float32): layers in the order enc0.a, enc0.b, ...,
+ * enc(L-1).b, then for l = L-2..0: dec_l.up, dec_l.a, dec_l.b, then head;
+ * per layer W as (Cout, k, k, Cin) row-major, then b (Cout).  Cin of enc0.a
+ * is 1, of dec_l.a 2 c_l (skip channels first). */
+typedef struct cpct_unet cpct_unet;
+
+/* Number of parameters of the vector above; -1 for an unsupported shape
+ * (levels 1..6, base a positive multiple of 32).  Host only. */
+long long cpct_unet_param_count(int levels, int base);
+
+/* Network with device activations for up to max_batch images of height x
+ * width (both divisible by 2^(levels-1)), parameters zero.  CPCT_EINVAL for
+ * unsupported shapes (also base * 2^(levels-1) > 1024), CPCT_ENOMEM. */
+int cpct_unet_create(cpct_unet** out, int levels, int base, int max_batch, int height, int width,
+                     cudaStream_t stream);
+int cpct_unet_destroy(cpct_unet* net);
+
+/* Host copies of the parameters / of the gradients of the last
+ * cpct_unet_backward (layout above).  set_params resets the Adam state.
+ * Synchronous. */
+int cpct_unet_set_params(cpct_unet* net, const float* h_params, cudaStream_t stream);
+int cpct_unet_get_params(cpct_unet* net, float* h_params, cudaStream_t stream);
+int cpct_unet_get_grads(cpct_unet* net, float* h_grads, cudaStream_t stream);
+
+/* out = net(in) for `batch` images; d_in, d_out device float32 batch x H x W
+ * (16-byte aligned).  Stream-ordered, asynchronous. */
+int cpct_unet_forward(cpct_unet* net, const float* d_in, float* d_out, int batch, cudaStream_t stream);
+
+/* Forward pass, loss against d_target and the gradients of every parameter
+ * (kept on the device for cpct_unet_adam_step / cpct_unet_get_grads);
+ * *loss (host, may be NULL) receives the loss and then the call synchronizes
+ * `stream`. */
+int cpct_unet_backward(cpct_unet* net, const float* d_in, const float* d_target, int batch, double* loss,
+                       cudaStream_t stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the
+ * gradients of the last backward pass; refreshes the BF16 weights. */
+int cpct_unet_adam_step(cpct_unet* net, float lr, cudaStream_t stream);
+
+/* One denoiser operation on caller tensors, for tests (B images, channels
+ * fastest, device float32; H x W is the size of a for ops 0, 1, 2, 5 and
+ * the size of y for ops 3, 4):
+ *   op 0: y = relu(conv3x3([a | b]) + bias), a: C1 channels, b: C2 (or NULL
+ *         with C2 = 0), y: Cout; h_w host float32: weights (Cout, 3, 3,
+ *         C1 + C2) then Cout biases; operands rounded as in the network
+ *   op 1: y = 2x2 average pool of a (C1 channels)
+ *   op 2: y = nearest 2x upsampling of a
+ *   op 3: y = adjoint of the pooling of an H x W image applied to the
+ *         half-size gradient a, plus b (H x W, may be NULL)
+ *   op 4: y = adjoint of the upsampling of an H x W image applied to the
+ *         double-size gradient a
+ *   op 5: y = data gradient of op 0's convolution at output gradient a
+ *         (Cout channels) with ReLU mask taken from b (Cout channels, the
+ *         op's output); y has C1 + C2 channels
+ *   op 6: weight and bias gradients of op 0's convolution at input a (C1
+ *         channels, C2 = 0) and output gradient b (Cout channels, used as
+ *         is): y = (Cout, 3, 3, C1) weights then Cout biases (flat)
+ * C1, C2 multiples of 32 (C1 > 0), Cout a multiple of 32 for ops 0, 5, 6.
+ * Synchronous; allocates a workspace for ops 0, 5 and 6. */
+int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, float* d_y, const float* h_w, int B, int H, int W,
+                       int C1, int C2, int Cout, cudaStream_t stream);
+
 /* Allocation-free adjoint.  Some callers cannot allocate device memory at
  * the point where they apply the operator: code running under an allocator
  * that has reserved the whole device pool (a framework's caching allocator),

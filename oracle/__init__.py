@@ -18,6 +18,9 @@ Modules
 ``spgl1``     the SPGL1 Pareto-root-finding basis-pursuit solver applied to
               filter(Radon) (section "Introduction", the L1 problem).
 ``analytic``  closed forms used as pins: parallel projections of disks.
+``unet``      the convolutional denoiser of the learned warm start (no
+              counterpart in the paper): forward pass and hand-written
+              backward pass in FP64.
 
 Parity status of every function is listed in its module header.
 """

@@ -29,6 +29,15 @@ fixed order with their shapes (W as (Cout, 3, 3, Cin), b as (Cout,)).
 The backward pass is written out by hand (the adjoint of every step), and is
 checked in the tests against central finite differences of the forward pass,
 and the convolution against scipy's 2D correlation.
+
+Operand rounding (``q``): the device rounds the operands of every 3x3
+contraction to bfloat16 (the activations entering a convolution, the
+masked output gradient entering the data and weight gradients, and the
+weights) and accumulates in floating point.  ``forward`` / ``backward`` take
+an optional rounding function q applied at exactly those points (the
+caller rounds the weights); with q = None the network is computed exactly.
+The ReLU masks are decisions taken on rounded values, so comparisons with
+the device use q = bf16_round, to take them in the device's precision.
 """
 from __future__ import annotations
 
@@ -122,16 +131,24 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def bf16_round(a):
+    """Round to the nearest bfloat16 value (ties to even), via float32."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 # ---------------------------------------------------------------------------
 # network
 # ---------------------------------------------------------------------------
-def forward(params, x_in: np.ndarray, levels: int, base: int):
+def forward(params, x_in: np.ndarray, levels: int, base: int, q=None):
     """x_in (B, H, W) -> (out (B, H, W), tape for backward)."""
     tape = []
     x = x_in[:, None, :, :].astype(np.float64)
+    qf = q if q is not None else (lambda a: a)
 
     def cr(name, inp):
-        z = conv(inp, params[name + ".W"], params[name + ".b"])
+        z = conv(qf(inp), params[name + ".W"], params[name + ".b"])
         y = relu(z)
         tape.append((name, inp, y))
         return y
@@ -157,9 +174,10 @@ def loss(out: np.ndarray, target: np.ndarray) -> float:
     return float(np.sum((out - target) ** 2) / (2.0 * out.size))
 
 
-def backward(params, x_in: np.ndarray, target: np.ndarray, levels: int, base: int):
+def backward(params, x_in: np.ndarray, target: np.ndarray, levels: int, base: int, q=None):
     """Loss and its gradient with respect to every parameter (dict) and to x_in."""
-    out, (tape, h_last) = forward(params, x_in, levels, base)
+    out, (tape, h_last) = forward(params, x_in, levels, base, q)
+    qf = q if q is not None else (lambda a: a)
     P = out.size
     g_out = (out - target) / P                                   # dL/d out
     grads = {}
@@ -171,7 +189,8 @@ def backward(params, x_in: np.ndarray, target: np.ndarray, levels: int, base: in
     def cr_back(name, gy):
         inp, y = rec[name]
         gz = gy * (y > 0)
-        gi, grads[name + ".W"], grads[name + ".b"] = conv_backward(inp, params[name + ".W"], gz)
+        gi, grads[name + ".W"], _ = conv_backward(qf(inp), params[name + ".W"], qf(gz))
+        grads[name + ".b"] = gz.sum(axis=(0, 2, 3))
         return gi
 
     c = channels(levels, base)

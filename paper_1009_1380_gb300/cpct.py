@@ -432,3 +432,120 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# learned warm start: the convolutional denoiser
+# ---------------------------------------------------------------------------
+def _unet_setup():
+    L = lib()
+    vp = ctypes.c_void_p
+    L.cpct_unet_param_count.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.cpct_unet_param_count.restype = ctypes.c_longlong
+    L.cpct_unet_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, vp]
+    L.cpct_unet_destroy.argtypes = [vp]
+    for name in ("cpct_unet_set_params", "cpct_unet_get_params", "cpct_unet_get_grads"):
+        getattr(L, name).argtypes = [vp, vp, vp]
+    L.cpct_unet_forward.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    L.cpct_unet_backward.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
+    L.cpct_unet_adam_step.argtypes = [vp, ctypes.c_float, vp]
+    return L
+
+
+def unet_param_count(levels, base):
+    """Length of the parameter vector of cpct_unet (-1: unsupported shape)."""
+    return int(_unet_setup().cpct_unet_param_count(int(levels), int(base)))
+
+
+class UNet:
+    """The denoiser of the learned warm start (device weights and buffers)."""
+
+    def __init__(self, levels, base, max_batch, height, width, stream=None):
+        import torch
+        self._torch = torch
+        self.levels, self.base, self.max_batch, self.height, self.width = levels, base, max_batch, height, width
+        L = _unet_setup()
+        h = ctypes.c_void_p()
+        check(L.cpct_unet_create(ctypes.byref(h), levels, base, max_batch, height, width, _stream(torch, stream)),
+              "cpct_unet_create")
+        self.handle = h
+        self.n_params = unet_param_count(levels, base)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _unet_setup().cpct_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params, stream=None):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {p.size}")
+        check(_unet_setup().cpct_unet_set_params(self.handle, p.ctypes.data_as(ctypes.c_void_p),
+                                                 _stream(self._torch, stream)), "cpct_unet_set_params")
+
+    def _host_vec(self, fn, stream):
+        import numpy as np
+        out = np.empty(self.n_params, dtype=np.float32)
+        check(getattr(_unet_setup(), fn)(self.handle, out.ctypes.data_as(ctypes.c_void_p),
+                                         _stream(self._torch, stream)), fn)
+        return out
+
+    def get_params(self, stream=None):
+        return self._host_vec("cpct_unet_get_params", stream)
+
+    def get_grads(self, stream=None):
+        return self._host_vec("cpct_unet_get_grads", stream)
+
+    def forward(self, x, out=None, stream=None):
+        torch = self._torch
+        B = x.shape[0]
+        shape = (B, self.height, self.width)
+        if out is None:
+            out = torch.empty_like(x)
+        check(_unet_setup().cpct_unet_forward(self.handle, _dev_ptr(x, shape, torch), _dev_ptr(out, shape, torch), B,
+                                              _stream(torch, stream)), "cpct_unet_forward")
+        return out
+
+    def backward(self, x, target, stream=None):
+        """Forward + loss + parameter gradients; returns the loss."""
+        torch = self._torch
+        B = x.shape[0]
+        shape = (B, self.height, self.width)
+        loss = ctypes.c_double()
+        check(_unet_setup().cpct_unet_backward(self.handle, _dev_ptr(x, shape, torch), _dev_ptr(target, shape, torch),
+                                               B, ctypes.byref(loss), _stream(torch, stream)), "cpct_unet_backward")
+        return loss.value
+
+    def adam_step(self, lr, stream=None):
+        check(_unet_setup().cpct_unet_adam_step(self.handle, float(lr), _stream(self._torch, stream)),
+              "cpct_unet_adam_step")
+
+
+def unet_debug_op(op, a, b, out_shape, w=None, C1=None, C2=0, Cout=0, stream=None):
+    """Run one denoiser operation (cpct_unet_debug_op) on NHWC CUDA tensors."""
+    import numpy as np
+    import torch
+    L = _unet_setup()
+    vp = ctypes.c_void_p
+    L.cpct_unet_debug_op.argtypes = [ctypes.c_int, vp, vp, vp, vp] + [ctypes.c_int] * 6 + [vp]
+    B, H, W = a.shape[0], a.shape[1], a.shape[2]
+    if op in (3, 4):
+        B, H, W = out_shape[0], out_shape[1], out_shape[2]
+    C1 = a.shape[3] if C1 is None else C1
+    y = torch.empty(out_shape, device=a.device, dtype=torch.float32)
+    for t in (a, b, y):
+        if t is not None and not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("expected contiguous float32 CUDA tensors")
+    hw = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+    check(L.cpct_unet_debug_op(op, vp(a.data_ptr()), vp(b.data_ptr()) if b is not None else None,
+                               vp(y.data_ptr()), hw.ctypes.data_as(vp) if hw is not None else None,
+                               B, H, W, C1, C2, Cout, _stream(torch, stream)), "cpct_unet_debug_op")
+    return y

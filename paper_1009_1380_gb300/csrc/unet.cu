@@ -1,0 +1,1218 @@
+// Learned warm start: the convolutional denoiser (U-Net) and its training.
+//
+// The paper has no learned component.  The network maps a filtered
+// back-projection of the data to a starting point of SPGL1 (the solver of the
+// paper's L1 problem, section "Introduction"); its function is fixed in the
+// C header (cpct_unet_*).  Layout and precision:
+//   * activations and their gradients: FP32, NHWC (channel fastest);
+//   * weights: FP32 master copy (Adam), BF16 copies in [Cout][3][3][Cin]
+//     (forward) and [Cin][3][3][Cout] with flipped taps (data gradient);
+//   * every 3x3 convolution is an implicit GEMM on the tensor cores
+//     (BF16 x BF16 -> FP32, mma.sync m16n8k16): activation tiles are
+//     converted to BF16 while they are staged in shared memory, and the
+//     accumulation stays FP32;
+//   * the level-0 input is stored with 32 channels (channel 0 = image), so
+//     every GEMM reduction chunk is 32 channels of one tap.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kCT = 256;     // threads of the convolution kernels
+constexpr int kBM = 128;     // pixels per forward tile
+constexpr int kBK = 32;      // reduction chunk: 32 channels of one tap
+constexpr int kEW = 256;     // threads of elementwise kernels
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+// D = A (16x16, row) * B (16x8, col) + D, BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// A tile row of 32 BF16 (64 B = four 16-byte chunks); chunk c of row r is
+// stored at chunk c ^ ((r >> 1) & 3): the eight rows an ldmatrix phase reads
+// then fall in eight distinct 16-byte bank groups
+__device__ __forceinline__ int sw64(int r, int c) { return r * 4 + (c ^ ((r >> 1) & 3)); }
+
+struct ConvArgs {
+  // input activations: channels [0, C1) from x1, [C1, C1 + C2) from x2
+  const float* x1;
+  const float* x2;
+  int C1, C2;
+  // optional ReLU mask of the input (data gradient: dZ = dY * (Y > 0))
+  const float* m1;
+  const __nv_bfloat16* W;  // [Cout][3][3][Cin] (Cin = C1 + C2)
+  const float* bias;       // [Cout] or null
+  // output: channels [0, O1) to y1 (stride O1), [O1, Cout) to y2
+  float* y1;
+  float* y2;
+  int O1, Cout;
+  int relu;                // apply max(., 0) in the epilogue
+  int B, H, Wd;            // batch, height, width
+};
+
+// Implicit-GEMM 3x3 convolution (zero padding 1): M = B*H*W pixels, N = Cout,
+// K = 9 * Cin in chunks of 32 channels of one tap.  256 threads, tile
+// 128 pixels x BN output channels, warps 4 (M) x 2 (N), double-buffered
+// shared memory (A converted from FP32 through registers, B by cp.async).
+template <int BN>
+__global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
+  constexpr int WN = BN / 2;        // warp tile N (32 or 16)
+  constexpr int NT = WN / 8;        // n8 tiles per warp
+  __shared__ __align__(128) uint32_t sA[2][kBM * kBK / 2];
+  __shared__ __align__(128) uint32_t sB[2][BN * kBK / 2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp & 3, wn = warp >> 2;
+  const int P = a.B * a.H * a.Wd;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int Cin = a.C1 + a.C2, cchunks = Cin / kBK, nk = 9 * cchunks;
+
+  // A loader: thread -> (pixel row, 16-channel half)
+  const int la_row = tid >> 1, la_half = tid & 1;
+  const int pm = m0 + la_row;
+  int py = 0, px = 0, pb = 0;
+  const bool pvalid = pm < P;
+  if (pvalid) {
+    pb = pm / (a.H * a.Wd);
+    const int r = pm - pb * a.H * a.Wd;
+    py = r / a.Wd;
+    px = r - py * a.Wd;
+  }
+  float4 ra[4];
+  auto load_a = [&](int kc) {
+    const int tap = kc / cchunks, ci0 = (kc - tap * cchunks) * kBK + la_half * 16;
+    const int sy = py + tap / 3 - 1, sx = px + tap % 3 - 1;
+    const bool ok = pvalid && sy >= 0 && sy < a.H && sx >= 0 && sx < a.Wd;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ra[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ok) {
+      const size_t pix = ((size_t)pb * a.H + sy) * a.Wd + sx;
+      const float* src = ci0 < a.C1 ? a.x1 + pix * a.C1 + ci0 : a.x2 + pix * a.C2 + (ci0 - a.C1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) ra[i] = *reinterpret_cast<const float4*>(src + 4 * i);
+      if (a.m1) {
+        const float* ms = a.m1 + pix * a.C1 + ci0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 mv = *reinterpret_cast<const float4*>(ms + 4 * i);
+          ra[i].x = mv.x > 0.f ? ra[i].x : 0.f;
+          ra[i].y = mv.y > 0.f ? ra[i].y : 0.f;
+          ra[i].z = mv.z > 0.f ? ra[i].z : 0.f;
+          ra[i].w = mv.w > 0.f ? ra[i].w : 0.f;
+        }
+      }
+    }
+  };
+  auto store_a = [&](int buf) {
+    uint32_t* dst = sA[buf];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {  // two 16-byte chunks (8 channels each)
+      const float4 u = ra[2 * c], v = ra[2 * c + 1];
+      uint4 q;
+      q.x = pack_bf16(u.x, u.y);
+      q.y = pack_bf16(u.z, u.w);
+      q.z = pack_bf16(v.x, v.y);
+      q.w = pack_bf16(v.z, v.w);
+      *reinterpret_cast<uint4*>(dst + 4 * sw64(la_row, la_half * 2 + c)) = q;
+    }
+  };
+  // B loader: BN rows x 64 B; each thread copies one 16-byte chunk (BN = 64)
+  // or threads 0..127 do (BN = 32)
+  auto load_b = [&](int kc, int buf) {
+    const int tap = kc / cchunks, ci0 = (kc - tap * cchunks) * kBK;
+    if (tid < BN * 4) {
+      const int r = tid >> 2, c = tid & 3;
+      const __nv_bfloat16* src = a.W + ((size_t)(n0 + r) * 9 + tap) * Cin + ci0 + c * 8;
+      cp_async16(smem_u32(sB[buf] + 4 * sw64(r, c)), src);
+    }
+    cp_async_commit();
+  };
+
+  float acc[2][NT][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+  load_a(0);
+  load_b(0, 0);
+  store_a(0);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int kc = 0; kc < nk; ++kc) {
+    const int cur = kc & 1;
+    if (kc + 1 < nk) {
+      load_a(kc + 1);
+      load_b(kc + 1, cur ^ 1);
+    }
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {  // two k16 steps per chunk
+      uint32_t af[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm * 32 + i * 16 + (lane & 15);
+        const int c = ks * 2 + (lane >> 4);
+        ldsm_x4(smem_u32(sA[cur] + 4 * sw64(r, c)), af[i][0], af[i][1], af[i][2], af[i][3]);
+      }
+#pragma unroll
+      for (int j = 0; j < NT; j += 2) {
+        // two n8 tiles: lanes 0-7 n 0-7 k0, 8-15 n 0-7 k8, 16-23 n 8-15 k0, 24-31 n 8-15 k8
+        const int r = wn * WN + j * 8 + (lane & 7) + ((lane >> 4) << 3);
+        const int c = ks * 2 + ((lane >> 3) & 1);
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4(smem_u32(sB[cur] + 4 * sw64(r, c)), b0, b1, b2, b3);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          mma_bf16(acc[i][j], af[i], b0, b1);
+          mma_bf16(acc[i][j + 1], af[i], b2, b3);
+        }
+      }
+    }
+    if (kc + 1 < nk) store_a(cur ^ 1);
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  // epilogue: rows lane/4 and lane/4 + 8, columns 2 (lane % 4) + {0, 1}
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = m0 + wm * 32 + i * 16 + (lane >> 2) + h * 8;
+      if (m >= P) continue;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int n = n0 + wn * WN + j * 8 + 2 * (lane & 3);
+        float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
+        if (a.bias) {
+          v0 += a.bias[n];
+          v1 += a.bias[n + 1];
+        }
+        if (a.relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        float* dst = n < a.O1 ? a.y1 + (size_t)m * a.O1 + n : a.y2 + (size_t)m * (a.Cout - a.O1) + (n - a.O1);
+        *reinterpret_cast<float2*>(dst) = make_float2(v0, v1);
+      }
+    }
+}
+
+// swizzled 16-byte chunk index of a row of CPR chunks (CPR = 4 or 8)
+template <int CPR>
+__device__ __forceinline__ int swz(int r, int c) {
+  return CPR == 8 ? r * 8 + (c ^ (r & 7)) : r * 4 + (c ^ ((r >> 1) & 3));
+}
+
+struct WgradArgs {
+  const float* dy;   // [P][Cout] gradient of the layer output
+  const float* y;    // [P][Cout] layer output (ReLU mask) or null
+  const float* x1;   // layer input channels [0, C1)
+  const float* x2;   // channels [C1, C1 + C2)
+  int C1, C2, Cout;
+  int B, H, Wd;
+  int chunks_per_split;  // 32-pixel chunks per split
+  float* part;       // [splits][Cout][9][Cin]
+};
+
+// Weight gradient dW[co][tap][ci] = sum_p dZ[p][co] X[p + tap][ci] as a GEMM
+// with M = Cout, N = 9 Cin (tiles inside one tap), K = pixels, split over
+// blockIdx.z.  Both operands are staged K-major ([pixel][channel]) and read
+// with ldmatrix.trans.  Warp tile 16 x 16, (BM / 16) x (BN / 16) warps.
+template <int BM, int BN>
+__global__ void __launch_bounds__((BM / 16) * (BN / 16) * 32) k_conv3x3_wgrad(const WgradArgs a) {
+  constexpr int NW_N = BN / 16, NTH = (BM / 16) * NW_N * 32;
+  constexpr int CA = BM / 8, CB = BN / 8;  // 16-byte chunks per staged row
+  __shared__ __align__(128) uint32_t sA[2][kBK * BM / 2];
+  __shared__ __align__(128) uint32_t sB[2][kBK * BN / 2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp / NW_N, wn = warp % NW_N;
+  const int Cin = a.C1 + a.C2, ctiles = Cin / BN;
+  const int m0 = blockIdx.x * BM;
+  const int tap = blockIdx.y / ctiles, ci0 = (blockIdx.y % ctiles) * BN;
+  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int P = a.B * a.H * a.Wd;
+  const int c_begin = blockIdx.z * a.chunks_per_split;
+  const int c_end = min(c_begin + a.chunks_per_split, (P + kBK - 1) / kBK);
+  const float* xs = ci0 < a.C1 ? a.x1 : a.x2;
+  const int xc = ci0 < a.C1 ? a.C1 : a.C2, xo = ci0 < a.C1 ? ci0 : ci0 - a.C1;
+
+  constexpr int NA4 = kBK * BM / 4, NB4 = kBK * BN / 4;  // float4 loads per tile
+  constexpr int LA = (NA4 + NTH - 1) / NTH, LB = (NB4 + NTH - 1) / NTH;
+  float4 ra[LA], rb[LB];
+  auto load = [&](int ch) {
+    const int p0 = ch * kBK;
+#pragma unroll
+    for (int t = 0; t < LA; ++t) {
+      const int idx = tid + t * NTH;
+      ra[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (idx < NA4) {
+        const int r = idx / (BM / 4), c4 = idx % (BM / 4), p = p0 + r;
+        if (p < P) {
+          float4 v = *reinterpret_cast<const float4*>(a.dy + (size_t)p * a.Cout + m0 + 4 * c4);
+          if (a.y) {
+            const float4 m = *reinterpret_cast<const float4*>(a.y + (size_t)p * a.Cout + m0 + 4 * c4);
+            v.x = m.x > 0.f ? v.x : 0.f;
+            v.y = m.y > 0.f ? v.y : 0.f;
+            v.z = m.z > 0.f ? v.z : 0.f;
+            v.w = m.w > 0.f ? v.w : 0.f;
+          }
+          ra[t] = v;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < LB; ++t) {
+      const int idx = tid + t * NTH;
+      rb[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (idx < NB4) {
+        const int r = idx / (BN / 4), c4 = idx % (BN / 4), p = p0 + r;
+        if (p < P) {
+          const int b = p / (a.H * a.Wd), rem = p - b * a.H * a.Wd;
+          const int py = rem / a.Wd + dy, px = rem % a.Wd + dx;
+          if (py >= 0 && py < a.H && px >= 0 && px < a.Wd)
+            rb[t] = *reinterpret_cast<const float4*>(xs + (((size_t)b * a.H + py) * a.Wd + px) * xc + xo + 4 * c4);
+        }
+      }
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int t = 0; t < LA; ++t) {
+      const int idx = tid + t * NTH;
+      if (idx < NA4) {
+        const int r = idx / (BM / 4), c4 = idx % (BM / 4);
+        uint2 q = make_uint2(pack_bf16(ra[t].x, ra[t].y), pack_bf16(ra[t].z, ra[t].w));
+        *reinterpret_cast<uint2*>(sA[buf] + 4 * swz<CA>(r, c4 >> 1) + 2 * (c4 & 1)) = q;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < LB; ++t) {
+      const int idx = tid + t * NTH;
+      if (idx < NB4) {
+        const int r = idx / (BN / 4), c4 = idx % (BN / 4);
+        uint2 q = make_uint2(pack_bf16(rb[t].x, rb[t].y), pack_bf16(rb[t].z, rb[t].w));
+        *reinterpret_cast<uint2*>(sB[buf] + 4 * swz<CB>(r, c4 >> 1) + 2 * (c4 & 1)) = q;
+      }
+    }
+  };
+
+  float acc[2][4];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+  if (c_begin < c_end) {
+    load(c_begin);
+    store(0);
+    __syncthreads();
+    for (int ch = c_begin; ch < c_end; ++ch) {
+      const int cur = (ch - c_begin) & 1;
+      if (ch + 1 < c_end) load(ch + 1);
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const int q = lane >> 3;
+        uint32_t af[4];
+        {
+          const int k = ks * 16 + (lane & 7) + ((q >> 1) << 3);
+          const int c = wm * 2 + (q & 1);
+          ldsm_x4_t(smem_u32(sA[cur] + 4 * swz<CA>(k, c)), af[0], af[1], af[2], af[3]);
+        }
+        uint32_t b0, b1, b2, b3;
+        {
+          const int k = ks * 16 + (lane & 7) + ((q & 1) << 3);
+          const int c = wn * 2 + (q >> 1);
+          ldsm_x4_t(smem_u32(sB[cur] + 4 * swz<CB>(k, c)), b0, b1, b2, b3);
+        }
+        mma_bf16(acc[0], af, b0, b1);
+        mma_bf16(acc[1], af, b2, b3);
+      }
+      if (ch + 1 < c_end) store(cur ^ 1);
+      __syncthreads();
+    }
+  }
+  float* dst = a.part + (size_t)blockIdx.z * a.Cout * 9 * Cin;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int co = m0 + wm * 16 + (lane >> 2) + h * 8;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int ci = ci0 + wn * 16 + j * 8 + 2 * (lane & 3);
+      *reinterpret_cast<float2*>(dst + ((size_t)co * 9 + tap) * Cin + ci) =
+          make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
+    }
+  }
+}
+
+// out[i] (+)= sum_s part[s][i], s in order (deterministic split reduction)
+__global__ void __launch_bounds__(kEW) k_split_sum(const float* __restrict__ part, int splits, long long n,
+                                                   float* __restrict__ out, int accumulate) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < splits; ++k) s += part[(size_t)k * n + i];
+    out[i] = accumulate ? out[i] + s : s;
+  }
+}
+
+// per-channel sums of dZ = dy * (y > 0) over pixel ranges: part[split][c]
+// (lane <-> channel within a 32-channel group, 8 pixel rows per block)
+__global__ void __launch_bounds__(kEW) k_colsum(const float* __restrict__ dy, const float* __restrict__ y, int P, int C,
+                                                int rows_per_split, float* __restrict__ part) {
+  __shared__ float sh[8][33];
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31), r = threadIdx.x >> 5;
+  const int p0 = blockIdx.y * rows_per_split, p1 = min(P, p0 + rows_per_split);
+  float s = 0.f;
+  if (c < C)
+    for (int p = p0 + r; p < p1; p += 8) {
+      const float v = dy[(size_t)p * C + c];
+      s += (!y || y[(size_t)p * C + c] > 0.f) ? v : 0.f;
+    }
+  sh[r][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (r == 0 && c < C) {
+    float t = 0.f;
+    for (int i = 0; i < 8; ++i) t += sh[i][threadIdx.x & 31];
+    part[(size_t)blockIdx.y * C + c] = t;
+  }
+}
+
+// level-0 input: X0[p][0] = x[p], channels 1..31 zero
+__global__ void __launch_bounds__(kEW) k_pack_input(const float* __restrict__ x, float* __restrict__ X0, int P) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    float4* d = reinterpret_cast<float4*>(X0 + (size_t)p * 32);
+    d[0] = make_float4(x[p], 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 1; i < 8; ++i) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// 2x2 average pooling: (B, H, W, C) -> (B, H/2, W/2, C), float4 over channels
+__global__ void __launch_bounds__(kEW) k_avgpool(const float* __restrict__ x, float* __restrict__ y, int B, int H, int W,
+                                                 int C) {
+  const int H2 = H / 2, W2 = W / 2, C4 = C / 4;
+  const long long n = (long long)B * H2 * W2 * C4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c4 = (int)(i % C4);
+    long long q = i / C4;
+    const int ox = (int)(q % W2);
+    q /= W2;
+    const int oy = (int)(q % H2);
+    const int b = (int)(q / H2);
+    const float4* s = reinterpret_cast<const float4*>(x);
+    const size_t r0 = (((size_t)b * H + 2 * oy) * W + 2 * ox) * C4 + c4, r1 = r0 + (size_t)W * C4;
+    const float4 a0 = s[r0], a1 = s[r0 + C4], a2 = s[r1], a3 = s[r1 + C4];
+    reinterpret_cast<float4*>(y)[i] = make_float4(0.25f * (a0.x + a1.x + a2.x + a3.x), 0.25f * (a0.y + a1.y + a2.y + a3.y),
+                                                  0.25f * (a0.z + a1.z + a2.z + a3.z), 0.25f * (a0.w + a1.w + a2.w + a3.w));
+  }
+}
+
+// adjoint of the pooling plus the skip gradient: g[p] = gp[p/2] / 4 + gs[p]
+__global__ void __launch_bounds__(kEW) k_avgpool_bwd(const float* __restrict__ gp, const float* __restrict__ gs,
+                                                     float* __restrict__ g, int B, int H, int W, int C) {
+  const int C4 = C / 4;
+  const long long n = (long long)B * H * W * C4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c4 = (int)(i % C4);
+    long long q = i / C4;
+    const int x = (int)(q % W);
+    q /= W;
+    const int yy = (int)(q % H);
+    const int b = (int)(q / H);
+    const float4 v = reinterpret_cast<const float4*>(gp)[(((size_t)b * (H / 2) + yy / 2) * (W / 2) + x / 2) * C4 + c4];
+    float4 o = make_float4(0.25f * v.x, 0.25f * v.y, 0.25f * v.z, 0.25f * v.w);
+    if (gs) {
+      const float4 s = reinterpret_cast<const float4*>(gs)[i];
+      o.x += s.x;
+      o.y += s.y;
+      o.z += s.z;
+      o.w += s.w;
+    }
+    reinterpret_cast<float4*>(g)[i] = o;
+  }
+}
+
+// nearest 2x upsampling: (B, H, W, C) -> (B, 2H, 2W, C)
+__global__ void __launch_bounds__(kEW) k_upsample(const float* __restrict__ x, float* __restrict__ y, int B, int H, int W,
+                                                  int C) {
+  const int C4 = C / 4, H2 = 2 * H, W2 = 2 * W;
+  const long long n = (long long)B * H2 * W2 * C4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c4 = (int)(i % C4);
+    long long q = i / C4;
+    const int ox = (int)(q % W2);
+    q /= W2;
+    const int oy = (int)(q % H2);
+    const int b = (int)(q / H2);
+    reinterpret_cast<float4*>(y)[i] = reinterpret_cast<const float4*>(x)[(((size_t)b * H + oy / 2) * W + ox / 2) * C4 + c4];
+  }
+}
+
+// adjoint of the upsampling: sum of the 2x2 block
+__global__ void __launch_bounds__(kEW) k_upsample_bwd(const float* __restrict__ g, float* __restrict__ gx, int B, int H,
+                                                      int W, int C) {
+  const int C4 = C / 4;
+  const long long n = (long long)B * H * W * C4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c4 = (int)(i % C4);
+    long long q = i / C4;
+    const int x = (int)(q % W);
+    q /= W;
+    const int yy = (int)(q % H);
+    const int b = (int)(q / H);
+    const float4* s = reinterpret_cast<const float4*>(g);
+    const size_t r0 = (((size_t)b * 2 * H + 2 * yy) * 2 * W + 2 * x) * C4 + c4, r1 = r0 + (size_t)2 * W * C4;
+    const float4 a0 = s[r0], a1 = s[r0 + C4], a2 = s[r1], a3 = s[r1 + C4];
+    reinterpret_cast<float4*>(gx)[i] =
+        make_float4(a0.x + a1.x + a2.x + a3.x, a0.y + a1.y + a2.y + a3.y, a0.z + a1.z + a2.z + a3.z, a0.w + a1.w + a2.w + a3.w);
+  }
+}
+
+// head: out[p] = x[p] + bh + sum_c Wh[c] h[p][c]   (one warp per pixel group)
+__global__ void __launch_bounds__(kEW) k_head(const float* __restrict__ x, const float* __restrict__ h,
+                                              const float* __restrict__ wh, const float* __restrict__ bh,
+                                              float* __restrict__ out, int P, int C) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    float s = bh[0];
+    const float4* hp = reinterpret_cast<const float4*>(h + (size_t)p * C);
+    for (int c4 = 0; c4 < C / 4; ++c4) {
+      const float4 v = hp[c4];
+      s = fmaf(wh[4 * c4], v.x, s);
+      s = fmaf(wh[4 * c4 + 1], v.y, s);
+      s = fmaf(wh[4 * c4 + 2], v.z, s);
+      s = fmaf(wh[4 * c4 + 3], v.w, s);
+    }
+    out[p] = x[p] + s;
+  }
+}
+
+// loss partials and the output gradient g = (out - t) / P
+__global__ void __launch_bounds__(kEW) k_loss(const float* __restrict__ out, const float* __restrict__ t,
+                                              float* __restrict__ g, int P, double* __restrict__ part) {
+  __shared__ double sh[kEW / 32];
+  double s = 0.0;
+  const float inv = 1.f / (float)P;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const float d = out[p] - t[p];
+    g[p] = d * inv;
+    s += (double)d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tt = 0.0;
+    for (int i = 0; i < kEW / 32; ++i) tt += sh[i];
+    part[blockIdx.x] = tt;
+  }
+}
+
+// head backward: gh[p][c] = g[p] Wh[c]
+__global__ void __launch_bounds__(kEW) k_head_bwd(const float* __restrict__ g, const float* __restrict__ wh,
+                                                  float* __restrict__ gh, int P, int C) {
+  const long long n = (long long)P * C;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    gh[i] = g[i / C] * wh[i % C];
+}
+
+// head weight gradient partials: part[s][c] = sum_p g[p] h[p][c] (c < C),
+// part[s][C] = sum_p g[p]
+__global__ void __launch_bounds__(kEW) k_head_wgrad(const float* __restrict__ g, const float* __restrict__ h, int P,
+                                                    int C, int rows_per_split, float* __restrict__ part) {
+  __shared__ float sh[8][33];
+  const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int p0 = blockIdx.x * rows_per_split, p1 = min(P, p0 + rows_per_split);
+  for (int cb = 0; cb <= C; cb += 32) {
+    const int cc = cb + c;
+    float s = 0.f;
+    if (cc <= C)
+      for (int p = p0 + r; p < p1; p += 8) s += g[p] * (cc < C ? h[(size_t)p * C + cc] : 1.f);
+    sh[r][c] = s;
+    __syncthreads();
+    if (r == 0 && cc <= C) {
+      float t = 0.f;
+      for (int i = 0; i < 8; ++i) t += sh[i][c];
+      part[(size_t)blockIdx.x * (C + 1) + cc] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// Adam on the FP32 master parameters (bias-corrected step size lr_t)
+__global__ void __launch_bounds__(kEW) k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                                              float* __restrict__ v, long long n, float lr_t, float b1, float b2,
+                                              float eps) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr_t * mi / (sqrtf(vi) + eps);
+  }
+}
+
+// BF16 weight copies of one 3x3 layer: Wf[co][tap][ci] (forward) and
+// Wt[ci][8 - tap][co] (data gradient: transposed channels, flipped taps)
+__global__ void __launch_bounds__(kEW) k_weights_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wf,
+                                                      __nv_bfloat16* __restrict__ wt, int Cout, int Cin) {
+  const long long n = (long long)Cout * 9 * Cin;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int ci = (int)(i % Cin);
+    const int tap = (int)((i / Cin) % 9);
+    const int co = (int)(i / ((long long)9 * Cin));
+    const __nv_bfloat16 b = __float2bfloat16_rn(w[i]);
+    wf[i] = b;
+    wt[((size_t)ci * 9 + (8 - tap)) * Cout + co] = b;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Layer {
+  int cout, cin, cin_pad, k;    // k = 3 (convolution) or 1 (head)
+  int c1, c2, lv;               // input channels from the first / second tensor, level
+  size_t w_off, b_off;          // into the padded FP32 parameter vector
+  size_t bf_off;                // into the BF16 weight arrays (3x3 layers)
+  size_t host_off;              // into the caller's (unpadded) parameter vector
+};
+
+struct Net {
+  int L, base, maxB, H, W;
+  std::vector<int> c;           // channels per level
+  std::vector<Layer> layers;    // enc0.a, enc0.b, ..., dec(L-2).up/a/b, ..., head
+  size_t n_param = 0, n_bf = 0;
+  long long host_count = 0;
+  std::vector<void*> allocs;
+  float *param = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  __nv_bfloat16 *wf = nullptr, *wt = nullptr;
+  int adam_t = 0;
+  // activations and gradients (indexed by level)
+  float* X0 = nullptr;
+  std::vector<float*> ea, eb, pool, upin, upout, da, db;
+  std::vector<float*> g_ea, g_eb, g_pool, g_upin, g_upout, g_da, g_db, g_skip;
+  float *out = nullptr, *g_out = nullptr, *g_in = nullptr;
+  float* part = nullptr;        // split partials
+  size_t part_floats = 0;
+  double* loss_part = nullptr;
+  int last_batch = 0;
+};
+
+int enc_a(int l) { return 2 * l; }
+int enc_b(int l) { return 2 * l + 1; }
+int dec_up(const Net& n, int l) { return 2 * n.L + 3 * (n.L - 2 - l); }
+int dec_a(const Net& n, int l) { return dec_up(n, l) + 1; }
+int dec_b(const Net& n, int l) { return dec_up(n, l) + 2; }
+int head_idx(const Net& n) { return (int)n.layers.size() - 1; }
+
+int grid_for(long long n) { return (int)std::min<long long>((n + kEW - 1) / kEW, 152LL * 16); }
+
+// pixel rows per split of the per-channel sums (at most 65535 splits: the
+// grid's y extent)
+long long colsum_rows(long long P) { return std::max<long long>(2048, (P + 65534) / 65535); }
+
+bool build_layers(Net& n) {
+  n.c.resize(n.L);
+  for (int l = 0; l < n.L; ++l) n.c[l] = n.base << l;
+  auto add = [&](int cout, int cin, int k, int lv, bool concat) {
+    Layer y;
+    y.cout = cout;
+    y.cin = cin;
+    y.cin_pad = (k == 3 && cin < 32) ? 32 : cin;
+    y.c1 = concat ? cin / 2 : y.cin_pad;
+    y.c2 = concat ? cin / 2 : 0;
+    y.lv = lv;
+    y.k = k;
+    y.w_off = n.n_param;
+    n.n_param += (size_t)cout * k * k * y.cin_pad;
+    y.b_off = n.n_param;
+    n.n_param += cout;
+    y.bf_off = n.n_bf;
+    if (k == 3) n.n_bf += (size_t)cout * 9 * y.cin_pad;
+    y.host_off = (size_t)n.host_count;
+    n.host_count += (long long)cout * k * k * cin + cout;
+    n.layers.push_back(y);
+  };
+  for (int l = 0; l < n.L; ++l) {
+    add(n.c[l], l == 0 ? 1 : n.c[l - 1], 3, l, false);
+    add(n.c[l], n.c[l], 3, l, false);
+  }
+  for (int l = n.L - 2; l >= 0; --l) {
+    add(n.c[l], n.c[l + 1], 3, l, false);
+    add(n.c[l], 2 * n.c[l], 3, l, true);
+    add(n.c[l], n.c[l], 3, l, false);
+  }
+  add(1, n.c[0], 1, 0, false);
+  return true;
+}
+
+template <class T>
+bool dalloc(Net& n, T** p, size_t count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, sizeof(T) * std::max<size_t>(count, 1)) != cudaSuccess) return false;
+  n.allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return true;
+}
+
+void free_net(Net* n) {
+  for (void* p : n->allocs) cudaFree(p);
+  delete n;
+}
+
+// the largest split-partial buffer any layer needs (floats)
+// tiles of the weight gradient (an N tile must not straddle the two input
+// tensors of a concatenation) and the split of the pixel reduction
+size_t wgrad_splits(int cout, int c1, int c2, long long P, int* bm, int* bn, int* splits, int* cps) {
+  const int cin = c1 + c2;
+  *bm = cout % 64 == 0 ? 64 : 32;
+  *bn = (c1 % 64 == 0 && c2 % 64 == 0) ? 64 : 32;
+  const long long tiles = (long long)(cout / *bm) * 9 * (cin / *bn);
+  const long long chunks = (P + kBK - 1) / kBK;
+  long long s = std::max<long long>(1, std::min<long long>((4LL * 152 + tiles - 1) / tiles, chunks));
+  const long long per = (chunks + s - 1) / s;
+  s = (chunks + per - 1) / per;
+  *splits = (int)s;
+  *cps = (int)per;
+  return (size_t)s * cout * 9 * cin;
+}
+
+void launch_conv(const Net& n, const ConvArgs& a, cudaStream_t s) {
+  const int P = a.B * a.H * a.Wd;
+  if (a.Cout % 64 == 0) {
+    dim3 grid((P + kBM - 1) / kBM, a.Cout / 64);
+    k_conv3x3<64><<<grid, kCT, 0, s>>>(a);
+  } else {
+    dim3 grid((P + kBM - 1) / kBM, a.Cout / 32);
+    k_conv3x3<32><<<grid, kCT, 0, s>>>(a);
+  }
+  (void)n;
+}
+
+void launch_wgrad(const WgradArgs& a, int bm, int bn, int splits, cudaStream_t s) {
+  const int Cin = a.C1 + a.C2;
+  dim3 grid(a.Cout / bm, 9 * (Cin / bn), splits);
+  if (bm == 64 && bn == 64) k_conv3x3_wgrad<64, 64><<<grid, 16 * 32, 0, s>>>(a);
+  else if (bm == 64) k_conv3x3_wgrad<64, 32><<<grid, 8 * 32, 0, s>>>(a);
+  else if (bn == 64) k_conv3x3_wgrad<32, 64><<<grid, 8 * 32, 0, s>>>(a);
+  else k_conv3x3_wgrad<32, 32><<<grid, 4 * 32, 0, s>>>(a);
+}
+
+// forward of one 3x3 layer: y = relu(conv(x1 | x2) + b)
+void conv_fwd(Net& n, int li, const float* x1, int C1, const float* x2, int C2, float* y, int B, int lv,
+              cudaStream_t s) {
+  const Layer& L = n.layers[li];
+  ConvArgs a{};
+  a.x1 = x1;
+  a.x2 = x2;
+  a.C1 = C1;
+  a.C2 = C2;
+  a.m1 = nullptr;
+  a.W = n.wf + L.bf_off;
+  a.bias = n.param + L.b_off;
+  a.y1 = y;
+  a.y2 = nullptr;
+  a.O1 = L.cout;
+  a.Cout = L.cout;
+  a.relu = 1;
+  a.B = B;
+  a.H = n.H >> lv;
+  a.Wd = n.W >> lv;
+  launch_conv(n, a, s);
+}
+
+// backward of one 3x3 layer with output y = relu(z): data gradient into
+// (dx1 | dx2) if dx1 is given, weight and bias gradients into n.grad
+void conv_bwd(Net& n, int li, const float* dy, const float* y, const float* x1, int C1, const float* x2, int C2,
+              float* dx1, float* dx2, int B, int lv, cudaStream_t s) {
+  const Layer& L = n.layers[li];
+  const int H = n.H >> lv, W = n.W >> lv;
+  const long long P = (long long)B * H * W;
+  if (dx1) {
+    ConvArgs a{};
+    a.x1 = dy;
+    a.x2 = nullptr;
+    a.C1 = L.cout;
+    a.C2 = 0;
+    a.m1 = y;
+    a.W = n.wt + L.bf_off;
+    a.bias = nullptr;
+    a.y1 = dx1;
+    a.y2 = dx2;
+    a.O1 = C1;
+    a.Cout = C1 + C2;
+    a.relu = 0;
+    a.B = B;
+    a.H = H;
+    a.Wd = W;
+    launch_conv(n, a, s);
+  }
+  int bm, bn, splits, cps;
+  wgrad_splits(L.cout, C1, C2, P, &bm, &bn, &splits, &cps);
+  WgradArgs w{};
+  w.dy = dy;
+  w.y = y;
+  w.x1 = x1;
+  w.x2 = x2;
+  w.C1 = C1;
+  w.C2 = C2;
+  w.Cout = L.cout;
+  w.B = B;
+  w.H = H;
+  w.Wd = W;
+  w.chunks_per_split = cps;
+  w.part = n.part;
+  launch_wgrad(w, bm, bn, splits, s);
+  const long long nw = (long long)L.cout * 9 * (C1 + C2);
+  k_split_sum<<<grid_for(nw), kEW, 0, s>>>(n.part, splits, nw, n.grad + L.w_off, 0);
+  // bias: per-channel sums of dZ over pixel ranges, then the fixed-order sum
+  const int rows = (int)colsum_rows(P), sp = (int)((P + rows - 1) / rows);
+  dim3 cg((L.cout + 31) / 32, sp);
+  k_colsum<<<cg, kEW, 0, s>>>(dy, y, (int)P, L.cout, rows, n.part);
+  k_split_sum<<<grid_for(L.cout), kEW, 0, s>>>(n.part, sp, L.cout, n.grad + L.b_off, 0);
+}
+
+void refresh_bf16(Net& n, cudaStream_t s) {
+  for (const Layer& L : n.layers)
+    if (L.k == 3) {
+      const long long cnt = (long long)L.cout * 9 * L.cin_pad;
+      k_weights_bf16<<<grid_for(cnt), kEW, 0, s>>>(n.param + L.w_off, n.wf + L.bf_off, n.wt + L.bf_off, L.cout,
+                                                   L.cin_pad);
+    }
+}
+
+void forward_pass(Net& n, const float* x, int B, cudaStream_t s) {
+  const int P0 = B * n.H * n.W;
+  k_pack_input<<<grid_for(P0), kEW, 0, s>>>(x, n.X0, P0);
+  const float* h = n.X0;
+  int hc = 32;
+  for (int l = 0; l < n.L; ++l) {
+    conv_fwd(n, enc_a(l), h, hc, nullptr, 0, n.ea[l], B, l, s);
+    conv_fwd(n, enc_b(l), n.ea[l], n.c[l], nullptr, 0, n.eb[l], B, l, s);
+    if (l < n.L - 1) {
+      const long long cnt = (long long)B * (n.H >> (l + 1)) * (n.W >> (l + 1)) * n.c[l] / 4;
+      k_avgpool<<<grid_for(cnt), kEW, 0, s>>>(n.eb[l], n.pool[l], B, n.H >> l, n.W >> l, n.c[l]);
+      h = n.pool[l];
+      hc = n.c[l];
+    }
+  }
+  h = n.eb[n.L - 1];
+  for (int l = n.L - 2; l >= 0; --l) {
+    const long long cnt = (long long)B * (n.H >> l) * (n.W >> l) * n.c[l + 1] / 4;
+    k_upsample<<<grid_for(cnt), kEW, 0, s>>>(h, n.upin[l], B, n.H >> (l + 1), n.W >> (l + 1), n.c[l + 1]);
+    conv_fwd(n, dec_up(n, l), n.upin[l], n.c[l + 1], nullptr, 0, n.upout[l], B, l, s);
+    conv_fwd(n, dec_a(n, l), n.eb[l], n.c[l], n.upout[l], n.c[l], n.da[l], B, l, s);
+    conv_fwd(n, dec_b(n, l), n.da[l], n.c[l], nullptr, 0, n.db[l], B, l, s);
+    h = n.db[l];
+  }
+  const Layer& Hd = n.layers[head_idx(n)];
+  k_head<<<grid_for(P0), kEW, 0, s>>>(x, h, n.param + Hd.w_off, n.param + Hd.b_off, n.out, P0, n.c[0]);
+}
+
+void backward_pass(Net& n, const float* x, const float* t, int B, cudaStream_t s) {
+  const int P0 = B * n.H * n.W;
+  const int lg = std::min(1024, (P0 + kEW - 1) / kEW);
+  k_loss<<<lg, kEW, 0, s>>>(n.out, t, n.g_out, P0, n.loss_part);
+  const float* h = n.L > 1 ? n.db[0] : n.eb[0];
+  float* gh = n.L > 1 ? n.g_db[0] : n.g_eb[0];
+  const Layer& Hd = n.layers[head_idx(n)];
+  k_head_bwd<<<grid_for((long long)P0 * n.c[0]), kEW, 0, s>>>(n.g_out, n.param + Hd.w_off, gh, P0, n.c[0]);
+  {
+    const int rows = 2048, sp = (P0 + rows - 1) / rows;
+    k_head_wgrad<<<sp, kEW, 0, s>>>(n.g_out, h, P0, n.c[0], rows, n.part);
+    k_split_sum<<<grid_for(n.c[0] + 1), kEW, 0, s>>>(n.part, sp, n.c[0] + 1, n.grad + Hd.w_off, 0);
+  }
+  for (int l = 0; l <= n.L - 2; ++l) {
+    conv_bwd(n, dec_b(n, l), n.g_db[l], n.db[l], n.da[l], n.c[l], nullptr, 0, n.g_da[l], nullptr, B, l, s);
+    conv_bwd(n, dec_a(n, l), n.g_da[l], n.da[l], n.eb[l], n.c[l], n.upout[l], n.c[l], n.g_skip[l], n.g_upout[l], B,
+             l, s);
+    conv_bwd(n, dec_up(n, l), n.g_upout[l], n.upout[l], n.upin[l], n.c[l + 1], nullptr, 0, n.g_upin[l], nullptr, B, l,
+             s);
+    float* gnext = l + 1 <= n.L - 2 ? n.g_db[l + 1] : n.g_eb[n.L - 1];
+    const long long cnt = (long long)B * (n.H >> (l + 1)) * (n.W >> (l + 1)) * n.c[l + 1] / 4;
+    k_upsample_bwd<<<grid_for(cnt), kEW, 0, s>>>(n.g_upin[l], gnext, B, n.H >> (l + 1), n.W >> (l + 1), n.c[l + 1]);
+  }
+  for (int l = n.L - 1; l >= 0; --l) {
+    if (l < n.L - 1) {
+      const long long cnt = (long long)B * (n.H >> l) * (n.W >> l) * n.c[l] / 4;
+      k_avgpool_bwd<<<grid_for(cnt), kEW, 0, s>>>(n.g_pool[l], n.g_skip[l], n.g_eb[l], B, n.H >> l, n.W >> l, n.c[l]);
+    }
+    conv_bwd(n, enc_b(l), n.g_eb[l], n.eb[l], n.ea[l], n.c[l], nullptr, 0, n.g_ea[l], nullptr, B, l, s);
+    if (l > 0)
+      conv_bwd(n, enc_a(l), n.g_ea[l], n.ea[l], n.pool[l - 1], n.c[l - 1], nullptr, 0, n.g_pool[l - 1], nullptr, B, l,
+               s);
+    else
+      conv_bwd(n, enc_a(0), n.g_ea[0], n.ea[0], n.X0, 32, nullptr, 0, nullptr, nullptr, B, 0, s);
+  }
+}
+
+}  // namespace
+
+struct cpct_unet {
+  Net* net;
+};
+
+extern "C" long long cpct_unet_param_count(int levels, int base) {
+  if (levels < 1 || levels > 6 || base < 32 || base % 32) return -1;
+  Net n;
+  n.L = levels;
+  n.base = base;
+  build_layers(n);
+  return n.host_count;
+}
+
+extern "C" int cpct_unet_create(cpct_unet** out, int levels, int base, int max_batch, int height, int width,
+                                cudaStream_t stream) {
+  if (!out) return CPCT_EINVAL;
+  *out = nullptr;
+  if (levels < 1 || levels > 6 || base < 32 || base % 32 || (base << (levels - 1)) > 1024 || max_batch < 1)
+    return CPCT_EINVAL;
+  const int div = 1 << (levels - 1);
+  if (height < div || width < div || height % div || width % div) return CPCT_EINVAL;
+  if ((long long)max_batch * height * width > (1LL << 30)) return CPCT_EINVAL;
+  Net* n = new (std::nothrow) Net;
+  if (!n) return CPCT_ENOMEM;
+  n->L = levels;
+  n->base = base;
+  n->maxB = max_batch;
+  n->H = height;
+  n->W = width;
+  build_layers(*n);
+  bool ok = dalloc(*n, &n->param, n->n_param) && dalloc(*n, &n->grad, n->n_param) &&
+            dalloc(*n, &n->adam_m, n->n_param) && dalloc(*n, &n->adam_v, n->n_param) &&
+            dalloc(*n, &n->wf, n->n_bf) && dalloc(*n, &n->wt, n->n_bf);
+  const int L = levels;
+  n->ea.assign(L, nullptr);
+  n->eb.assign(L, nullptr);
+  n->pool.assign(L, nullptr);
+  n->upin.assign(L, nullptr);
+  n->upout.assign(L, nullptr);
+  n->da.assign(L, nullptr);
+  n->db.assign(L, nullptr);
+  n->g_ea.assign(L, nullptr);
+  n->g_eb.assign(L, nullptr);
+  n->g_pool.assign(L, nullptr);
+  n->g_upin.assign(L, nullptr);
+  n->g_upout.assign(L, nullptr);
+  n->g_da.assign(L, nullptr);
+  n->g_db.assign(L, nullptr);
+  n->g_skip.assign(L, nullptr);
+  const size_t P0 = (size_t)max_batch * height * width;
+  ok = ok && dalloc(*n, &n->X0, P0 * 32) && dalloc(*n, &n->out, P0) && dalloc(*n, &n->g_out, P0) &&
+       dalloc(*n, &n->loss_part, 1024);
+  for (int l = 0; l < L && ok; ++l) {
+    const size_t Pl = P0 >> (2 * l), cl = n->c[l];
+    ok = dalloc(*n, &n->ea[l], Pl * cl) && dalloc(*n, &n->eb[l], Pl * cl) && dalloc(*n, &n->g_ea[l], Pl * cl) &&
+         dalloc(*n, &n->g_eb[l], Pl * cl);
+    if (ok && l < L - 1) {
+      const size_t c1 = n->c[l + 1];
+      ok = dalloc(*n, &n->pool[l], (Pl / 4) * cl) && dalloc(*n, &n->g_pool[l], (Pl / 4) * cl) &&
+           dalloc(*n, &n->upin[l], Pl * c1) && dalloc(*n, &n->g_upin[l], Pl * c1) &&
+           dalloc(*n, &n->upout[l], Pl * cl) && dalloc(*n, &n->g_upout[l], Pl * cl) &&
+           dalloc(*n, &n->da[l], Pl * cl) && dalloc(*n, &n->g_da[l], Pl * cl) && dalloc(*n, &n->db[l], Pl * cl) &&
+           dalloc(*n, &n->g_db[l], Pl * cl) && dalloc(*n, &n->g_skip[l], Pl * cl);
+    }
+  }
+  // split partials: the largest weight-gradient split of any layer, the
+  // bias and head sums
+  size_t part = 0;
+  for (int li = 0; li < (int)n->layers.size() && ok; ++li) {
+    const Layer& Ly = n->layers[li];
+    if (Ly.k != 3) continue;
+    int bm, bn, sp, cps;
+    part = std::max(part, wgrad_splits(Ly.cout, Ly.c1, Ly.c2, (long long)(P0 >> (2 * Ly.lv)), &bm, &bn, &sp, &cps));
+    const long long Pl = (long long)(P0 >> (2 * Ly.lv));
+    part = std::max(part, (size_t)((Pl + colsum_rows(Pl) - 1) / colsum_rows(Pl)) * (size_t)Ly.cout);
+  }
+  part = std::max(part, (size_t)((P0 + 2047) / 2048) * (size_t)(n->c[0] + 1));
+  ok = ok && dalloc(*n, &n->part, part);
+  n->part_floats = part;
+  if (ok) {
+    ok = cudaMemsetAsync(n->param, 0, sizeof(float) * n->n_param, stream) == cudaSuccess &&
+         cudaMemsetAsync(n->grad, 0, sizeof(float) * n->n_param, stream) == cudaSuccess &&
+         cudaMemsetAsync(n->adam_m, 0, sizeof(float) * n->n_param, stream) == cudaSuccess &&
+         cudaMemsetAsync(n->adam_v, 0, sizeof(float) * n->n_param, stream) == cudaSuccess;
+    refresh_bf16(*n, stream);
+    ok = ok && cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(stream) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    free_net(n);
+    return CPCT_ENOMEM;
+  }
+  cpct_unet* h = new (std::nothrow) cpct_unet;
+  if (!h) {
+    free_net(n);
+    return CPCT_ENOMEM;
+  }
+  h->net = n;
+  *out = h;
+  return CPCT_OK;
+}
+
+extern "C" int cpct_unet_destroy(cpct_unet* net) {
+  if (!net) return CPCT_OK;
+  cudaDeviceSynchronize();
+  free_net(net->net);
+  delete net;
+  return CPCT_OK;
+}
+
+// copy between the caller's layout (per layer: W (Cout, k, k, Cin), b) and
+// the padded device layout; to_device selects the direction
+static int params_copy(Net& n, float* h, const float* dev_src, float* dev_dst, cudaStream_t s, bool to_device) {
+  std::vector<float> pad(n.n_param, 0.f);
+  if (!to_device) {
+    if (cudaMemcpyAsync(pad.data(), dev_src, sizeof(float) * n.n_param, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return CPCT_ECUDA;
+  }
+  for (const Layer& L : n.layers) {
+    const int kk = L.k * L.k;
+    for (int co = 0; co < L.cout; ++co)
+      for (int t = 0; t < kk; ++t)
+        for (int ci = 0; ci < L.cin; ++ci) {
+          const size_t hi = L.host_off + ((size_t)co * kk + t) * L.cin + ci;
+          const size_t di = L.w_off + ((size_t)co * kk + t) * L.cin_pad + ci;
+          if (to_device) pad[di] = h[hi];
+          else h[hi] = pad[di];
+        }
+    const size_t hb = L.host_off + (size_t)L.cout * kk * L.cin;
+    for (int co = 0; co < L.cout; ++co) {
+      if (to_device) pad[L.b_off + co] = h[hb + co];
+      else h[hb + co] = pad[L.b_off + co];
+    }
+  }
+  if (to_device) {
+    if (cudaMemcpyAsync(dev_dst, pad.data(), sizeof(float) * n.n_param, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return CPCT_ECUDA;
+  }
+  return CPCT_OK;
+}
+
+extern "C" int cpct_unet_set_params(cpct_unet* net, const float* h_params, cudaStream_t stream) {
+  if (!net || !h_params) return CPCT_EINVAL;
+  Net& n = *net->net;
+  int rc = params_copy(n, const_cast<float*>(h_params), nullptr, n.param, stream, true);
+  if (rc) return rc;
+  if (cudaMemsetAsync(n.adam_m, 0, sizeof(float) * n.n_param, stream) != cudaSuccess ||
+      cudaMemsetAsync(n.adam_v, 0, sizeof(float) * n.n_param, stream) != cudaSuccess)
+    return CPCT_ECUDA;
+  n.adam_t = 0;
+  refresh_bf16(n, stream);
+  return cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(stream) == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}
+
+extern "C" int cpct_unet_get_params(cpct_unet* net, float* h_params, cudaStream_t stream) {
+  if (!net || !h_params) return CPCT_EINVAL;
+  return params_copy(*net->net, h_params, net->net->param, nullptr, stream, false);
+}
+
+extern "C" int cpct_unet_get_grads(cpct_unet* net, float* h_grads, cudaStream_t stream) {
+  if (!net || !h_grads) return CPCT_EINVAL;
+  return params_copy(*net->net, h_grads, net->net->grad, nullptr, stream, false);
+}
+
+static bool unet_ptr_ok(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+extern "C" int cpct_unet_forward(cpct_unet* net, const float* d_in, float* d_out, int batch, cudaStream_t stream) {
+  if (!net || !unet_ptr_ok(d_in) || !unet_ptr_ok(d_out)) return CPCT_EINVAL;
+  Net& n = *net->net;
+  if (batch < 1 || batch > n.maxB) return CPCT_EINVAL;
+  forward_pass(n, d_in, batch, stream);
+  const size_t P0 = (size_t)batch * n.H * n.W;
+  if (cudaMemcpyAsync(d_out, n.out, sizeof(float) * P0, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+    return CPCT_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}
+
+extern "C" int cpct_unet_backward(cpct_unet* net, const float* d_in, const float* d_target, int batch, double* loss,
+                                  cudaStream_t stream) {
+  if (!net || !unet_ptr_ok(d_in) || !unet_ptr_ok(d_target)) return CPCT_EINVAL;
+  Net& n = *net->net;
+  if (batch < 1 || batch > n.maxB) return CPCT_EINVAL;
+  forward_pass(n, d_in, batch, stream);
+  backward_pass(n, d_in, d_target, batch, stream);
+  if (cudaGetLastError() != cudaSuccess) return CPCT_ECUDA;
+  if (loss) {
+    const int P0 = batch * n.H * n.W;
+    const int lg = std::min(1024, (P0 + kEW - 1) / kEW);
+    std::vector<double> part(lg);
+    if (cudaMemcpyAsync(part.data(), n.loss_part, sizeof(double) * lg, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      return CPCT_ECUDA;
+    double s = 0.0;
+    for (double v : part) s += v;
+    *loss = s / (2.0 * P0);
+  }
+  return CPCT_OK;
+}
+
+extern "C" int cpct_unet_adam_step(cpct_unet* net, float lr, cudaStream_t stream) {
+  if (!net || !(lr > 0.f)) return CPCT_EINVAL;
+  Net& n = *net->net;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  n.adam_t++;
+  const double lr_t = lr * std::sqrt(1.0 - std::pow((double)b2, n.adam_t)) / (1.0 - std::pow((double)b1, n.adam_t));
+  k_adam<<<grid_for((long long)n.n_param), kEW, 0, stream>>>(n.param, n.grad, n.adam_m, n.adam_v, (long long)n.n_param,
+                                                             (float)lr_t, b1, b2, eps);
+  refresh_bf16(n, stream);
+  return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}
+
+// One network operation on caller tensors (NHWC, device float32), for tests:
+//   op 0: y = relu(conv3x3([a | b]) + bias), weights h_w (host float32,
+//         [Cout][3][3][C1 + C2] followed by Cout biases)
+//   op 1: y = 2x2 average pool of a (C1 channels)
+//   op 2: y = nearest 2x upsampling of a
+//   op 3: y = adjoint of the pooling applied to a (half-size), plus b
+//   op 4: y = adjoint of the upsampling applied to a (double-size)
+//   op 5: y = data gradient of op 0 at output gradient a with ReLU mask b
+//         (a, b: Cout channels; y: C1 + C2 channels, one tensor)
+//   op 6: y = weight and bias gradients of op 0's convolution (no mask) at
+//         input a (C1 channels) and output gradient b (Cout channels):
+//         [Cout][3][3][C1] weights, then Cout biases
+extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, float* d_y, const float* h_w, int B,
+                                  int H, int W, int C1, int C2, int Cout, cudaStream_t stream) {
+  if (!d_a || !d_y || B < 1 || H < 1 || W < 1 || C1 < 1 || C1 % 32 || C2 < 0 || C2 % 32) return CPCT_EINVAL;
+  if (op == 6) {
+    if (!d_b || C2 != 0 || Cout < 32 || Cout % 32) return CPCT_EINVAL;
+    const long long P = (long long)B * H * W;
+    int bm, bn, sp, cps;
+    size_t need = wgrad_splits(Cout, C1, 0, P, &bm, &bn, &sp, &cps);
+    const int rows = (int)colsum_rows(P), csp = (int)((P + rows - 1) / rows);
+    need = std::max(need, (size_t)csp * Cout);
+    float* part = nullptr;
+    if (cudaMalloc(&part, sizeof(float) * need) != cudaSuccess) return CPCT_ENOMEM;
+    WgradArgs w{};
+    w.dy = d_b;
+    w.y = nullptr;
+    w.x1 = d_a;
+    w.x2 = nullptr;
+    w.C1 = C1;
+    w.C2 = 0;
+    w.Cout = Cout;
+    w.B = B;
+    w.H = H;
+    w.Wd = W;
+    w.chunks_per_split = cps;
+    w.part = part;
+    launch_wgrad(w, bm, bn, sp, stream);
+    const long long nw = (long long)Cout * 9 * C1;
+    k_split_sum<<<grid_for(nw), kEW, 0, stream>>>(part, sp, nw, d_y, 0);
+    dim3 cg((Cout + 31) / 32, csp);
+    k_colsum<<<cg, kEW, 0, stream>>>(d_b, nullptr, (int)P, Cout, rows, part);
+    k_split_sum<<<grid_for(Cout), kEW, 0, stream>>>(part, csp, Cout, d_y + nw, 0);
+    const int rc = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(stream) == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+    cudaFree(part);
+    return rc;
+  }
+  if (op == 0 || op == 5) {
+    if (!h_w || Cout < 32 || Cout % 32 || (op == 5 && !d_b)) return CPCT_EINVAL;
+    const int Cin = C1 + C2;
+    const size_t nw = (size_t)Cout * 9 * Cin;
+    float* dw = nullptr;
+    __nv_bfloat16* bf = nullptr;
+    if (cudaMalloc(&dw, sizeof(float) * (nw + Cout)) != cudaSuccess) return CPCT_ENOMEM;
+    if (cudaMalloc(&bf, sizeof(__nv_bfloat16) * 2 * nw) != cudaSuccess) {
+      cudaFree(dw);
+      return CPCT_ENOMEM;
+    }
+    int rc = CPCT_OK;
+    if (cudaMemcpyAsync(dw, h_w, sizeof(float) * (nw + Cout), cudaMemcpyHostToDevice, stream) != cudaSuccess)
+      rc = CPCT_ECUDA;
+    if (rc == CPCT_OK) {
+      k_weights_bf16<<<grid_for((long long)nw), kEW, 0, stream>>>(dw, bf, bf + nw, Cout, Cin);
+      ConvArgs a{};
+      a.B = B;
+      a.H = H;
+      a.Wd = W;
+      if (op == 0) {
+        a.x1 = d_a;
+        a.x2 = d_b;
+        a.C1 = C1;
+        a.C2 = C2;
+        a.W = bf;
+        a.bias = dw + nw;
+        a.y1 = d_y;
+        a.O1 = Cout;
+        a.Cout = Cout;
+        a.relu = 1;
+      } else {
+        a.x1 = d_a;
+        a.C1 = Cout;
+        a.C2 = 0;
+        a.m1 = d_b;
+        a.W = bf + nw;
+        a.y1 = d_y;
+        a.O1 = Cin;
+        a.Cout = Cin;
+      }
+      launch_conv(Net(), a, stream);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
+    }
+    cudaFree(bf);
+    cudaFree(dw);
+    return rc;
+  }
+  const long long n4 = (long long)B * H * W * C1 / 4;
+  switch (op) {
+    case 1:
+      k_avgpool<<<grid_for(n4 / 4), kEW, 0, stream>>>(d_a, d_y, B, H, W, C1);
+      break;
+    case 2:
+      k_upsample<<<grid_for(n4 * 4), kEW, 0, stream>>>(d_a, d_y, B, H, W, C1);
+      break;
+    case 3:
+      k_avgpool_bwd<<<grid_for(n4), kEW, 0, stream>>>(d_a, d_b, d_y, B, H, W, C1);
+      break;
+    case 4:
+      k_upsample_bwd<<<grid_for(n4), kEW, 0, stream>>>(d_a, d_y, B, H, W, C1);
+      break;
+    default:
+      return CPCT_EINVAL;
+  }
+  return cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(stream) == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}

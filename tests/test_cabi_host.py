@@ -97,3 +97,12 @@ def test_invalid_geometry_rejected_on_host(cpct):
     for n, ns, m in [(100, 100, 10), (64, 32, 10), (64, 64, 0), (4096, 4096, 10)]:
         with pytest.raises(cpct.CpctError):
             cpct.debug_bins(n, ns, m, 0)
+
+
+def test_unet_param_count_matches_oracle(cpct):
+    from oracle import unet
+    for levels, base in [(1, 32), (3, 32), (5, 32), (4, 64)]:
+        want = sum(co * k * k * ci + co for _, co, ci, k in unet.layer_specs(levels, base))
+        assert cpct.unet_param_count(levels, base) == want
+    assert cpct.unet_param_count(0, 32) == -1
+    assert cpct.unet_param_count(3, 16) == -1

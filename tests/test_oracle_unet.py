@@ -6,7 +6,10 @@
   hand-written backward steps, and the mean / replication on constants;
 * the hand-written backward pass equals central finite differences of the
   forward pass (relative 1e-6) for every parameter tensor and the input;
-* the residual form: with a zero head the network is the identity.
+* the residual form: with a zero head the network is the identity;
+* the bfloat16 operand rounding equals torch's CPU float32 -> bfloat16
+  conversion (round to nearest even), and leaves representable operands
+  unchanged.
 """
 import numpy as np
 import pytest
@@ -127,3 +130,25 @@ def test_planted_mistake_is_caught():
         fd[i] = (f(xp) - f(xm)) / (2 * h)
     assert np.linalg.norm(good.ravel() - fd) / np.linalg.norm(fd) < 1e-6
     assert np.linalg.norm(bad.ravel() - fd) / np.linalg.norm(fd) > 1e-2
+
+
+def test_bf16_round_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    a = np.concatenate([rng.standard_normal(10000) * 10.0 ** rng.integers(-20, 20, 10000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.01171875, -3.5e-40, 65504.0]]).astype(np.float32)
+    ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(unet.bf16_round(a), ref)
+
+
+def test_rounded_mode_is_the_exact_mode_on_representable_values():
+    """With operands already bfloat16-representable and a one-level net, the
+    rounded forward equals the exact forward on its first contraction."""
+    rng = np.random.default_rng(12)
+    p = unet.init_params(1, 2, rng)
+    for k in p:
+        p[k] = unet.bf16_round(p[k])
+    x = unet.bf16_round(rng.standard_normal((1, 6, 6)))
+    z_exact = unet.conv(x[:, None], p["enc0.a.W"], p["enc0.a.b"])
+    out_q, (tape, _) = unet.forward(p, x, 1, 2, q=unet.bf16_round)
+    np.testing.assert_array_equal(tape[0][2], unet.relu(z_exact))
