@@ -116,6 +116,15 @@ int radon_fwd(cpct_plan* plan, const float* d_img, float* d_sino, cudaStream_t s
  *   d_img   device, N*N float32 (written)                                   */
 int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream);
 
+/* Filtered back-projection x = R^T(h * y): the ray spectra of the sinogram
+ * are weighted by the ramp h[k] = (pi / M) |k| / Ns (the DC bin by (pi / M)
+ * 0.25 / Ns, the mean of |k| over its width) before the adjoint, which
+ * discretises the polar Fourier inversion integral with d(theta) = pi / M
+ * (uniform angles over [0, pi)).  The paper's baseline reconstruction
+ * ("using a filter", Fig. 3); here also the input of the learned warm
+ * start.  Same arguments, layout and errors as radon_adj. */
+int radon_fbp(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream);
+
 /* Host-buffer variants: copy h_in (pinned or pageable host memory) to a
  * plan-owned device staging buffer, run the operator, copy the result back
  * to h_out and synchronize `stream`.  For end-to-end timing and for callers

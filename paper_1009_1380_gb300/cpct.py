@@ -62,7 +62,7 @@ def lib():
         L.cpct_plan_sync.argtypes = [vp, vp]
         L.cpct_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                      ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t)]
-        for name in ("radon_fwd", "radon_adj", "radon_fwd_host", "radon_adj_host", "radon_adj_noalloc"):
+        for name in ("radon_fwd", "radon_adj", "radon_fbp", "radon_fwd_host", "radon_adj_host", "radon_adj_noalloc"):
             getattr(L, name).argtypes = [vp, vp, vp, vp]
         L.cpct_strerror.restype = ctypes.c_char_p
         L.cpct_strerror.argtypes = [i]
@@ -171,6 +171,15 @@ class Plan:
             out = torch.empty((self.n, self.n), device=sino.device, dtype=torch.float32)
         check(lib().radon_adj(self._h, _dev_ptr(sino, (self.n_views, self.n_det), torch),
                               _dev_ptr(out, (self.n, self.n), torch), _stream(torch, stream)), "radon_adj")
+        return out
+
+    def fbp(self, sino, out=None, stream=None):
+        """Filtered back-projection R^T(ramp * sino)."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.n, self.n), device=sino.device, dtype=torch.float32)
+        check(lib().radon_fbp(self._h, _dev_ptr(sino, (self.n_views, self.n_det), torch),
+                              _dev_ptr(out, (self.n, self.n), torch), _stream(torch, stream)), "radon_fbp")
         return out
 
     def fwd_host(self, img: np.ndarray, out: np.ndarray | None = None, stream=None):

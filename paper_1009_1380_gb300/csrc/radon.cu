@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(kThreads)
 // ---------------------------------------------------------------------------
 template <int LOGNS>
 __global__ void __launch_bounds__(kThreads)
-    k_adj_ray(const float* __restrict__ sino, float2* __restrict__ Q, const float2* __restrict__ tw, int M, int ldq) {
+    k_adj_ray(const float* __restrict__ sino, float2* __restrict__ Q, const float2* __restrict__ tw, int M, int ldq,
+              float ramp) {
   using FFT = SmemFFT<LOGNS, kErow, -1>;
   constexpr int NS = 1 << LOGNS, T = FFT::T, PPC = rows_per_cta<LOGNS>(), K = NS / 2;
   extern __shared__ float2 sm[];
@@ -328,6 +329,9 @@ __global__ void __launch_bounds__(kThreads)
     float2 d2 = make_float2(0.5f * (W.y + Wm.y), -0.5f * (W.x - Wm.x));
     float sc = ((k & 1) ? -inv : inv);
     if (k == 0 || k == K) { d1.y = 0.f; d2.y = 0.f; } else { sc *= 2.f; }
+    // filtered back-projection: ramp weight (pi / M) |k| / Ns, the DC bin
+    // weighted by the mean of |k| over its width (1/4)
+    if (ramp > 0.f) sc *= ramp * (k == 0 ? 0.25f : (float)k);
     if (v1) Q[(size_t)j1 * ldq + k] = cscale(d1, sc);
     if (v2) Q[(size_t)j2 * ldq + k] = cscale(d2, sc);
   }
@@ -583,11 +587,12 @@ void launch_fwd_Ns(cpct_plan* p, float* sino, cudaStream_t s) {
   cpct_prof_end(p, KID_FWD_RAY, s);
 }
 template <int LOGNS>
-void launch_adj_Ns(cpct_plan* p, const float* sino, cudaStream_t s) {
+void launch_adj_Ns(cpct_plan* p, const float* sino, float ramp, cudaStream_t s) {
   constexpr int NS = 1 << LOGNS, PPC = rows_per_cta<LOGNS>();
   const int pairs = (p->m + 1) / 2;
   cpct_prof_begin(p, KID_ADJ_RAY, s);
-  k_adj_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kErow), fft_smem<LOGNS>(PPC), s>>>(sino, p->d_Q, p->d_twNs, p->m, p->ldq);
+  k_adj_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kErow), fft_smem<LOGNS>(PPC), s>>>(sino, p->d_Q, p->d_twNs, p->m,
+                                                                                           p->ldq, ramp);
   cpct_prof_end(p, KID_ADJ_RAY, s);
 }
 template <int LOGG>
@@ -677,7 +682,11 @@ int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_
 }
 
 int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_t s) {
-#define AN(L) launch_adj_Ns<L>(p, d_sino, s)
+  return cpct_launch_adj_ramp(p, d_sino, d_img, 0.f, s);
+}
+
+int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float ramp, cudaStream_t s) {
+#define AN(L) launch_adj_Ns<L>(p, d_sino, ramp, s)
   CPCT_DISPATCH_NS(p->logNs, AN);
 #undef AN
   AdjSpreadArgs a;
@@ -760,7 +769,7 @@ extern "C" int radon_adj_noalloc(cpct_plan* p, const float* d_sino, float* d_img
   int status = CPCT_OK;
   float2* partials = noalloc_scratch(&status);
   if (!partials) return status;
-#define AN(L) launch_adj_Ns<L>(p, d_sino, s)
+#define AN(L) launch_adj_Ns<L>(p, d_sino, 0.f, s)
   CPCT_DISPATCH_NS(p->logNs, AN);
 #undef AN
   AdjSpreadArgs a;

@@ -1,0 +1,275 @@
+"""Learned warm start for SPGL1 (an extension: the paper has none).
+
+The method generates its own training data: for synthetic slices it computes
+the filtered back-projection of the ring-filtered data (radon_fbp) and the
+converged cold-start SPGL1 solution of the paper's L1 problem; a U-Net
+(cpct_unet_*, trained here with the project's own forward and backward
+kernels) learns to map the first to the second.  A new slice then starts
+SPGL1 from the prediction projected onto an l1 ball, x0 = P_tau0(net(FBP))
+with tau0 = kappa ||net(FBP)||_1: prediction noise spread over all pixels
+inflates the l1 norm of a raw prediction, and the Pareto-curve Newton
+iteration of SPGL1 converges monotonically from below the root, so kappa is
+calibrated on training slices as a little less than the median of
+tau* / ||net(FBP)||_1.  The plain cold-started solver is the fallback for any
+slice whose warm solve does not reach the root, and the judge of the result
+(its residual criterion is unchanged).  The same calibrated projection of
+the FBP image itself is the non-learned warm start it is compared with.
+
+Inputs are scaled per slice by s = the standard deviation of the FBP image:
+the network sees FBP / s and predicts x / s.
+
+Command line: ``python -m paper_1009_1380_gb300.warmstart --help``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import cpct, synth
+
+CONFIG = synth.CONFIGS["c5_warm512"]
+
+
+def layer_shapes(levels, base):
+    """(Cout, Cin, k) of every layer in the parameter order of cpct_unet."""
+    c = [base << l for l in range(levels)]
+    out = []
+    for l in range(levels):
+        out += [(c[l], 1 if l == 0 else c[l - 1], 3), (c[l], c[l], 3)]
+    for l in range(levels - 2, -1, -1):
+        out += [(c[l], c[l + 1], 3), (c[l], 2 * c[l], 3), (c[l], c[l], 3)]
+    return out + [(1, c[0], 1)]
+
+
+def he_init(levels, base, seed=0):
+    """He-normal 3x3 weights, zero biases and a zero head: the network starts
+    as the identity map of its (scaled) input."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    shapes = layer_shapes(levels, base)
+    for i, (co, ci, k) in enumerate(shapes):
+        if i == len(shapes) - 1:
+            parts.append(np.zeros(co * k * k * ci))
+        else:
+            parts.append(rng.standard_normal(co * k * k * ci) * np.sqrt(2.0 / (ci * k * k)))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def make_slices(plan, count, first_index, torch, n_shapes=None, config_index=None):
+    """Synthetic slices: b (count, M, Ns) device, sigma (count,), FBP inputs
+    (count, N, N) device.  Slice i uses the seed of slice first_index + i."""
+    n, m = plan.n, plan.n_views
+    ci = CONFIG["index"] if config_index is None else config_index
+    ns = CONFIG["n_shapes"] if n_shapes is None else n_shapes
+    b = torch.empty((count, m, plan.n_det), device="cuda", dtype=torch.float32)
+    fbp = torch.empty((count, n, n), device="cuda", dtype=torch.float32)
+    sigma = np.empty(count)
+    filt = torch.empty((m, plan.n_det), device="cuda", dtype=torch.float32)
+    for i in range(count):
+        rng = synth.rng_for(ci, first_index + i)
+        u, _ = synth.ellipse_phantom(n, ns, rng)
+        x = torch.from_numpy(synth.laplacian5(u).astype(np.float32)).cuda()
+        y = plan.fwd(x).cpu().numpy()
+        bi, std, _ = synth.corrupt_sinogram(y, rng)
+        b[i].copy_(torch.from_numpy(bi.astype(np.float32)))
+        sigma[i] = std * np.sqrt(m * plan.n_det - plan.n_det + 4)
+        cpct.ring_filter(plan, b[i], out=filt)
+        plan.fbp(filt, out=fbp[i])
+    return b, sigma, fbp
+
+
+def solve(plans, b, sigma, opts, x0=None):
+    """Batched SPGL1 over all slices in groups of len(plans); returns
+    (x (count, N, N), infos, wall seconds)."""
+    torch = plans[0]._torch
+    count, P = b.shape[0], len(plans)
+    xs = torch.empty((count, plans[0].n, plans[0].n), device=b.device, dtype=torch.float32)
+    infos = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g in range(0, count, P):
+        k = min(P, count - g)
+        x0s = None if x0 is None else [x0[g + i] for i in range(k)]
+        out, inf = cpct.spgl1_batched(plans[:k], [b[g + i] for i in range(k)], list(sigma[g:g + k]), x0s=x0s,
+                                      opts=opts)
+        for i in range(k):
+            xs[g + i].copy_(out[i])
+        infos.extend(inf)
+    torch.cuda.synchronize()
+    return xs, infos, time.perf_counter() - t0
+
+
+def scales(fbp):
+    return fbp.flatten(1).std(dim=1).clamp_min(1e-12)
+
+
+def train(net, fbp, target, epochs, batch, lr, seed=0, log=None):
+    """Adam on (FBP / s, x / s) pairs; returns the per-epoch mean losses."""
+    torch = net._torch
+    s = scales(fbp)[:, None, None]
+    inp, tgt = (fbp / s).contiguous(), (target / s).contiguous()
+    rng = np.random.default_rng(seed)
+    count = fbp.shape[0]
+    losses = []
+    for ep in range(epochs):
+        perm = rng.permutation(count)
+        tot, nb = 0.0, 0
+        for g in range(0, count - batch + 1, batch):
+            idx = torch.from_numpy(perm[g:g + batch]).cuda()
+            xb, tb = inp.index_select(0, idx).contiguous(), tgt.index_select(0, idx).contiguous()
+            tot += net.backward(xb, tb)
+            net.adam_step(lr)
+            nb += 1
+        losses.append(tot / max(nb, 1))
+        if log:
+            log(f"epoch {ep}: loss {losses[-1]:.4e}")
+    return losses
+
+
+def predict(net, fbp, batch):
+    torch = net._torch
+    s = scales(fbp)[:, None, None]
+    inp = (fbp / s).contiguous()
+    out = torch.empty_like(inp)
+    for g in range(0, fbp.shape[0], batch):
+        k = min(batch, fbp.shape[0] - g)
+        net.forward(inp[g:g + k], out=out[g:g + k])
+    return out * s
+
+
+KAPPA_MARGIN = 0.97  # start a little below the calibrated root estimate
+
+
+def calibrate(x_hat, tau_star):
+    """kappa: a little less than the median ratio tau* / ||x_hat||_1."""
+    l1 = x_hat.abs().flatten(1).sum(dim=1).double().cpu().numpy()
+    ratio = np.asarray(tau_star, dtype=np.float64) / np.maximum(l1, 1e-30)
+    return float(KAPPA_MARGIN * np.median(ratio))
+
+
+def project_start(x_hat, kappa):
+    """x0 = P_tau0(x_hat), tau0 = kappa ||x_hat||_1 (exact projection, per slice)."""
+    x0 = torch_empty_like(x_hat)
+    for i in range(x_hat.shape[0]):
+        tau0 = kappa * float(x_hat[i].abs().sum().item())
+        cpct.project_l1(x_hat[i].reshape(-1), tau0, out=x0[i].reshape(-1))
+    return x0
+
+
+def torch_empty_like(t):
+    return t.new_empty(t.shape)
+
+
+def evaluate(net, plans, b, sigma, fbp, opts, batch, kappa):
+    """Cold start, FBP warm start and learned warm start on the same slices.
+
+    ``kappa`` = {"fbp": k, "learned": k} from ``calibrate``.  A warm solve
+    that does not reach the root is redone cold (the fallback); its time
+    counts against the warm start."""
+    torch = plans[0]._torch
+    res = {}
+    x_cold, inf_cold, t_cold = solve(plans, b, sigma, opts)
+    res["cold"] = _summary(inf_cold, t_cold, 0.0)
+    for name in ("fbp", "learned"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x_hat = fbp if name == "fbp" else predict(net, fbp, batch)
+        x0 = project_start(x_hat, kappa[name])
+        torch.cuda.synchronize()
+        t_net = time.perf_counter() - t0
+        x, inf, t = solve(plans, b, sigma, opts, x0=x0)
+        bad = [i for i, f in enumerate(inf) if f["status"] != 1]
+        t_fb = 0.0
+        if bad:
+            idx = torch.tensor(bad, device=b.device)
+            _, inf_fb, t_fb = solve(plans, b.index_select(0, idx).contiguous(), sigma[bad], opts)
+            for j, i in enumerate(bad):
+                inf[i] = dict(inf_fb[j], fallback=True)
+        r = _summary(inf, t + t_fb + t_net, t_net)
+        r["fallbacks"] = len(bad)
+        # the warm and the cold solution of each slice: l1 norms
+        l1w = np.array([f["xnorm1"] for f in inf])
+        l1c = np.array([f["xnorm1"] for f in inf_cold])
+        r["l1_rel_diff_vs_cold_mean"] = float(np.mean(np.abs(l1w - l1c) / l1c))
+        res[name] = r
+    return res
+
+
+def _summary(infos, wall, t_net):
+    its = np.array([f["iterations"] for f in infos])
+    roots = sum(1 for f in infos if f["status"] == 1)
+    return {"slices": len(infos), "at_root": roots, "wall_s": wall, "net_s": t_net,
+            "slices_per_s": roots / wall if wall > 0 else None, "iterations_mean": float(its.mean()),
+            "iterations_median": float(np.median(its)), "iterations_max": int(its.max())}
+
+
+def run(pairs, eval_slices, epochs, batch, lr, levels, base, plans_per_group, target_iters, eval_tol, n=None, m=None,
+        log=print):
+    import torch
+    n = CONFIG["n"] if n is None else n
+    m = CONFIG["n_views"] if m is None else m
+    out = {"config": {"n": n, "views": m, "pairs": pairs, "eval_slices": eval_slices, "epochs": epochs,
+                      "batch": batch, "lr": lr, "levels": levels, "base": base, "target_max_iter": target_iters,
+                      "eval_opt_tol": eval_tol}}
+    plan0 = cpct.Plan(n, n, m)
+    plans = [plan0] + [cpct.clone(plan0) for _ in range(plans_per_group - 1)]
+    t0 = time.perf_counter()
+    b, sigma, fbp = make_slices(plan0, pairs, 0, torch)
+    out["gen_inputs_s"] = time.perf_counter() - t0
+    x_t, inf_t, t_sol = solve(plans, b, sigma, cpct.make_opts(max_iter=target_iters))
+    out["targets"] = _summary(inf_t, t_sol, 0.0)
+    log(f"targets: {out['targets']}")
+    net = cpct.UNet(levels, base, batch, n, n)
+    net.set_params(he_init(levels, base, seed=7))
+    t0 = time.perf_counter()
+    losses = train(net, fbp, x_t, epochs, batch, lr, log=log)
+    torch.cuda.synchronize()
+    out["train_s"] = time.perf_counter() - t0
+    out["train_loss"] = losses
+    # calibration of the starting radius on (up to 256) training slices
+    k = min(pairs, 256)
+    tau_star = [f["xnorm1"] for f in inf_t[:k]]
+    kappa = {"fbp": calibrate(fbp[:k], tau_star), "learned": calibrate(predict(net, fbp[:k], batch), tau_star)}
+    out["kappa"] = kappa
+    log(f"kappa {kappa}")
+    del b, fbp, x_t
+    be, se, fe = make_slices(plan0, eval_slices, pairs, torch)
+    out["eval"] = evaluate(net, plans, be, se, fe, cpct.make_opts(opt_tol=eval_tol, max_iter=target_iters), batch,
+                           kappa)
+    c, w = out["eval"]["cold"], out["eval"]["learned"]
+    out["speedup_wall"] = c["wall_s"] / w["wall_s"] if w["wall_s"] > 0 else None
+    out["iterations_ratio"] = w["iterations_mean"] / c["iterations_mean"] if c["iterations_mean"] > 0 else None
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--pairs", type=int, default=4096)
+    ap.add_argument("--eval", type=int, default=512)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--levels", type=int, default=5)
+    ap.add_argument("--base", type=int, default=32)
+    ap.add_argument("--group", type=int, default=64, help="slices per batched SPGL1 solve")
+    ap.add_argument("--target-iters", type=int, default=500)
+    ap.add_argument("--eval-tol", type=float, default=1e-3)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--views", type=int, default=None)
+    ap.add_argument("--out", default=None, help="write the JSON summary here")
+    a = ap.parse_args(argv)
+    res = run(a.pairs, a.eval, a.epochs, a.batch, a.lr, a.levels, a.base, a.group, a.target_iters, a.eval_tol,
+              n=a.n, m=a.views)
+    line = json.dumps(res)
+    print(line)
+    if a.out:
+        with open(a.out, "w") as fh:
+            fh.write(line + "\n")
+
+
+if __name__ == "__main__":
+    main()

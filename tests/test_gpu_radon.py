@@ -84,6 +84,21 @@ def test_parity_vs_gridding_oracle(torch_cuda, n, ns, m):
     assert ef < TOL and ea < TOL
 
 
+@pytest.mark.parametrize("n,m", [(128, 180), (64, 45), (512, 90)])
+def test_fbp_parity(torch_cuda, n, m):
+    """radon_fbp = radon_adj of the ramp-filtered sinogram (oracle fbp_grid)."""
+    torch = torch_cuda
+    rng = np.random.default_rng(n + m)
+    sino = rng.standard_normal((m, n))
+    geo = nufft.GridGeometry(n, n, nufft.default_angles(m))
+    ref = nufft.fbp_grid(sino.astype(np.float32).astype(np.float64), geo)
+    p = _plan(n, n, m)
+    x = p.fbp(torch.from_numpy(sino.astype(np.float32)).cuda()).cpu().numpy()
+    e = _rel(x, ref)
+    print("fbp rel", e)
+    assert e < TOL
+
+
 def test_parity_vs_exact_nudft(torch_cuda):
     n, m = 128, 180
     img = synth.phantom("c1_128").astype(np.float64)
