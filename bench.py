@@ -256,6 +256,21 @@ def spgl1_bench(args, torch, cpct, synth):
                       f"<= {c['iterations']} iterations, opt_tol 1e-4, ring filter"}
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The maximum of a per-rank float over all ranks (x itself for one rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, units_per_rank, seconds):
+    """Whole-job rate: every rank processed units_per_rank in at most `seconds`."""
+    return world * units_per_rank / seconds
+
+
 def config_dict(args):
     n, ns, m, _ = WORKLOADS[args.workload]
     return {"workload": f"{args.workload}: {n}x{n} float32 phantom, {m} views x {ns} bins, KB W=6 sigma=2",
@@ -331,12 +346,9 @@ def run_ours(args, rank, world, local_rank):
     plan.sync()
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     dom_ms, dom_cnt = plan.profile_read().get(dominant, (0.0, 0))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     plan.profile_enable(0)
-    value = world * args.steps * S / (total_ms / 1000.0) / 1e6
+    value = aggregate_rate(world, args.steps * S, total_ms / 1000.0) / 1e6
 
     # end to end through the host-buffer C ABI (pinned host memory)
     img_h = torch.from_numpy(synth.phantom(cfg)).pin_memory().numpy()
@@ -350,11 +362,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         plan.fwd_host(img_h, sino_h)
         plan.adj_host(sino_h, out_h)
-    t_e2e = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
 
     if rank != 0:
         if dist:
@@ -369,7 +377,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(args),
-        "e2e": {"value": S / t_e2e / 1e6, "unit": "Msamples/s",
+        "e2e": {"value": aggregate_rate(world, S, t_e2e) / 1e6, "unit": "Msamples/s",
                 "h2d_bytes_per_step": 4 * n * n + 4 * m * ns, "d2h_bytes_per_step": 4 * m * ns + 4 * n * n},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -204,7 +204,9 @@ def _summary(infos, wall, t_net):
     roots = sum(1 for f in infos if f["status"] == 1)
     return {"slices": len(infos), "at_root": roots, "wall_s": wall, "net_s": t_net,
             "slices_per_s": roots / wall if wall > 0 else None, "iterations_mean": float(its.mean()),
-            "iterations_median": float(np.median(its)), "iterations_max": int(its.max())}
+            "iterations_median": float(np.median(its)), "iterations_max": int(its.max()),
+            "ticks_mean": float(np.mean([f["ticks"] for f in infos])),
+            "ticks_max": int(max(f["ticks"] for f in infos))}
 
 
 def run(pairs, eval_slices, epochs, batch, lr, levels, base, plans_per_group, target_iters, eval_tol, n=None, m=None,

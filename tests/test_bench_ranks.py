@@ -1,0 +1,58 @@
+"""Multi-rank logic of bench.py on CPU ranks (gloo, world size 2).
+
+Each rank contributes its own timing; rank 0 must see the maximum, and the
+whole-job value counts the units of every rank over that maximum (replicas,
+weak scaling).
+"""
+import importlib.util
+import os
+import socket
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    b = _bench()
+    elapsed = [1.5, 2.5][rank]
+    m = b.max_over_ranks(elapsed, dist, "cpu")
+    v = b.aggregate_rate(world, 1000.0, m)
+    q.put((rank, m, v))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_aggregate_gloo():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for rank, m, v in res:
+        assert m == 2.5
+        assert v == pytest.approx(2 * 1000.0 / 2.5)
+
+
+def test_single_rank_is_identity():
+    b = _bench()
+    assert b.max_over_ranks(3.0) == 3.0
+    assert b.aggregate_rate(1, 10.0, 2.0) == 5.0
