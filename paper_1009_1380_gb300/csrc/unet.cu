@@ -75,93 +75,103 @@ struct ConvArgs {
   const float* x1;
   const float* x2;
   int C1, C2;
-  // optional ReLU mask of the input (data gradient: dZ = dY * (Y > 0))
-  const float* m1;
   const __nv_bfloat16* W;  // [Cout][3][3][Cin] (Cin = C1 + C2)
   const float* bias;       // [Cout] or null
   // output: channels [0, O1) to y1 (stride O1), [O1, Cout) to y2
   float* y1;
   float* y2;
+  // optional ReLU masks of the outputs (same layout as y1 / y2): an output
+  // element is zeroed where its mask is not positive (data gradients land
+  // on ReLU outputs as pre-activation gradients)
+  const float* om1;
+  const float* om2;
   int O1, Cout;
   int relu;                // apply max(., 0) in the epilogue
   int B, H, Wd;            // batch, height, width
 };
 
+constexpr int kStages = 3;  // cp.async pipeline depth of the convolution GEMMs
+
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0));
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <int BN>
+constexpr size_t conv_smem() {
+  return (size_t)kStages * (kBM * kBK * 4 + BN * kBK * 2) + kBM * kBK * 2;
+}
+
 // Implicit-GEMM 3x3 convolution (zero padding 1): M = B*H*W pixels, N = Cout,
 // K = 9 * Cin in chunks of 32 channels of one tap.  256 threads, tile
-// 128 pixels x BN output channels, warps 4 (M) x 2 (N), double-buffered
-// shared memory (A converted from FP32 through registers, B by cp.async).
+// 128 pixels x BN output channels, warps 4 (M) x 2 (N).  A 3-stage cp.async
+// pipeline stages the FP32 activation chunk (zero-filled outside the image)
+// and the BF16 weight chunk; each chunk's activations are converted once to a
+// swizzled BF16 tile that ldmatrix feeds to mma.sync.
 template <int BN>
 __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
   constexpr int WN = BN / 2;        // warp tile N (32 or 16)
   constexpr int NT = WN / 8;        // n8 tiles per warp
-  __shared__ __align__(128) uint32_t sA[2][kBM * kBK / 2];
-  __shared__ __align__(128) uint32_t sB[2][BN * kBK / 2];
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* Af = reinterpret_cast<float*>(smraw);                                   // [kStages][kBM * kBK]
+  uint32_t* sB = reinterpret_cast<uint32_t*>(smraw + (size_t)kStages * kBM * kBK * 4);  // [kStages][BN * kBK / 2]
+  uint32_t* sA = sB + kStages * BN * kBK / 2;                                   // [kBM * kBK / 2]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 3, wn = warp >> 2;
-  const int P = a.B * a.H * a.Wd;
+  const int HW = a.H * a.Wd, P = a.B * HW;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
   const int Cin = a.C1 + a.C2, cchunks = Cin / kBK, nk = 9 * cchunks;
 
-  // A loader: thread -> (pixel row, 16-channel half)
-  const int la_row = tid >> 1, la_half = tid & 1;
-  const int pm = m0 + la_row;
-  int py = 0, px = 0, pb = 0;
-  const bool pvalid = pm < P;
-  if (pvalid) {
-    pb = pm / (a.H * a.Wd);
-    const int r = pm - pb * a.H * a.Wd;
-    py = r / a.Wd;
-    px = r - py * a.Wd;
+  // A copies: this thread's 16-byte chunk c16 of rows r0 + 32 i, i = 0..3
+  const int c16 = tid & 7, r0 = tid >> 3;
+  int py[4], px[4], pb[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int pm = m0 + r0 + 32 * i;
+    pb[i] = -1;
+    if (pm < P) {
+      pb[i] = pm / HW;
+      const int r = pm - pb[i] * HW;
+      py[i] = r / a.Wd;
+      px[i] = r - py[i] * a.Wd;
+    }
   }
-  float4 ra[4];
-  auto load_a = [&](int kc) {
-    const int tap = kc / cchunks, ci0 = (kc - tap * cchunks) * kBK + la_half * 16;
-    const int sy = py + tap / 3 - 1, sx = px + tap % 3 - 1;
-    const bool ok = pvalid && sy >= 0 && sy < a.H && sx >= 0 && sx < a.Wd;
+  auto load_stage = [&](int kc, int st) {
+    const int tap = kc / cchunks, ci0 = (kc - tap * cchunks) * kBK;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const float* base = ci0 < a.C1 ? a.x1 : a.x2;
+    const int cs = ci0 < a.C1 ? a.C1 : a.C2, co = (ci0 < a.C1 ? ci0 : ci0 - a.C1) + 4 * c16;
+    float* dst = Af + (size_t)st * kBM * kBK;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) ra[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ok) {
-      const size_t pix = ((size_t)pb * a.H + sy) * a.Wd + sx;
-      const float* src = ci0 < a.C1 ? a.x1 + pix * a.C1 + ci0 : a.x2 + pix * a.C2 + (ci0 - a.C1);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) ra[i] = *reinterpret_cast<const float4*>(src + 4 * i);
-      if (a.m1) {
-        const float* ms = a.m1 + pix * a.C1 + ci0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float4 mv = *reinterpret_cast<const float4*>(ms + 4 * i);
-          ra[i].x = mv.x > 0.f ? ra[i].x : 0.f;
-          ra[i].y = mv.y > 0.f ? ra[i].y : 0.f;
-          ra[i].z = mv.z > 0.f ? ra[i].z : 0.f;
-          ra[i].w = mv.w > 0.f ? ra[i].w : 0.f;
-        }
-      }
+    for (int i = 0; i < 4; ++i) {
+      const int sy = py[i] + dy, sx = px[i] + dx;
+      const bool ok = pb[i] >= 0 && sy >= 0 && sy < a.H && sx >= 0 && sx < a.Wd;
+      const float* src = ok ? base + (((size_t)pb[i] * a.H + sy) * a.Wd + sx) * cs + co : base;
+      cp_async16_zfill(smem_u32(dst + (r0 + 32 * i) * kBK + 4 * c16), src, ok);
+    }
+    if (tid < BN * 4) {
+      const int r = tid >> 2, c = tid & 3;
+      const __nv_bfloat16* src = a.W + ((size_t)(n0 + r) * 9 + tap) * Cin + ci0 + c * 8;
+      cp_async16(smem_u32(sB + (size_t)st * BN * kBK / 2 + 4 * sw64(r, c)), src);
     }
   };
-  auto store_a = [&](int buf) {
-    uint32_t* dst = sA[buf];
+  // FP32 chunk -> swizzled BF16 tile: thread -> (row, 16-channel half)
+  auto convert = [&](int st) {
+    const int row = tid >> 1, half = tid & 1;
+    const float4* src = reinterpret_cast<const float4*>(Af + (size_t)st * kBM * kBK + row * kBK + half * 16);
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {  // two 16-byte chunks (8 channels each)
-      const float4 u = ra[2 * c], v = ra[2 * c + 1];
+    for (int c = 0; c < 2; ++c) {
+      const float4 u = src[2 * c], v = src[2 * c + 1];
       uint4 q;
       q.x = pack_bf16(u.x, u.y);
       q.y = pack_bf16(u.z, u.w);
       q.z = pack_bf16(v.x, v.y);
       q.w = pack_bf16(v.z, v.w);
-      *reinterpret_cast<uint4*>(dst + 4 * sw64(la_row, la_half * 2 + c)) = q;
+      *reinterpret_cast<uint4*>(sA + 4 * sw64(row, half * 2 + c)) = q;
     }
-  };
-  // B loader: BN rows x 64 B; each thread copies one 16-byte chunk (BN = 64)
-  // or threads 0..127 do (BN = 32)
-  auto load_b = [&](int kc, int buf) {
-    const int tap = kc / cchunks, ci0 = (kc - tap * cchunks) * kBK;
-    if (tid < BN * 4) {
-      const int r = tid >> 2, c = tid & 3;
-      const __nv_bfloat16* src = a.W + ((size_t)(n0 + r) * 9 + tap) * Cin + ci0 + c * 8;
-      cp_async16(smem_u32(sB[buf] + 4 * sw64(r, c)), src);
-    }
-    cp_async_commit();
   };
 
   float acc[2][NT][4];
@@ -172,17 +182,23 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
 
-  load_a(0);
-  load_b(0, 0);
-  store_a(0);
-  cp_async_wait_all();
-  __syncthreads();
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    if (st < nk) load_stage(st, st);
+    cp_async_commit();
+  }
   for (int kc = 0; kc < nk; ++kc) {
-    const int cur = kc & 1;
-    if (kc + 1 < nk) {
-      load_a(kc + 1);
-      load_b(kc + 1, cur ^ 1);
+    const int cur = kc % kStages;
+    cp_async_wait<kStages - 2>();
+    __syncthreads();  // chunk kc landed for every thread; chunk kc-1 fully consumed
+    convert(cur);
+    {
+      const int nx = kc + kStages - 1;
+      if (nx < nk) load_stage(nx, nx % kStages);
+      cp_async_commit();
     }
+    __syncthreads();  // BF16 tile of chunk kc visible
+    const uint32_t* sBc = sB + (size_t)cur * BN * kBK / 2;
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {  // two k16 steps per chunk
       uint32_t af[2][4];
@@ -190,7 +206,7 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
       for (int i = 0; i < 2; ++i) {
         const int r = wm * 32 + i * 16 + (lane & 15);
         const int c = ks * 2 + (lane >> 4);
-        ldsm_x4(smem_u32(sA[cur] + 4 * sw64(r, c)), af[i][0], af[i][1], af[i][2], af[i][3]);
+        ldsm_x4(smem_u32(sA + 4 * sw64(r, c)), af[i][0], af[i][1], af[i][2], af[i][3]);
       }
 #pragma unroll
       for (int j = 0; j < NT; j += 2) {
@@ -198,7 +214,7 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
         const int r = wn * WN + j * 8 + (lane & 7) + ((lane >> 4) << 3);
         const int c = ks * 2 + ((lane >> 3) & 1);
         uint32_t b0, b1, b2, b3;
-        ldsm_x4(smem_u32(sB[cur] + 4 * sw64(r, c)), b0, b1, b2, b3);
+        ldsm_x4(smem_u32(sBc + 4 * sw64(r, c)), b0, b1, b2, b3);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           mma_bf16(acc[i][j], af[i], b0, b1);
@@ -206,10 +222,8 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
         }
       }
     }
-    if (kc + 1 < nk) store_a(cur ^ 1);
-    cp_async_wait_all();
-    __syncthreads();
   }
+  cp_async_wait<0>();
   // epilogue: rows lane/4 and lane/4 + 8, columns 2 (lane % 4) + {0, 1}
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -229,8 +243,15 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
           v0 = fmaxf(v0, 0.f);
           v1 = fmaxf(v1, 0.f);
         }
-        float* dst = n < a.O1 ? a.y1 + (size_t)m * a.O1 + n : a.y2 + (size_t)m * (a.Cout - a.O1) + (n - a.O1);
-        *reinterpret_cast<float2*>(dst) = make_float2(v0, v1);
+        const bool first = n < a.O1;
+        const size_t off = first ? (size_t)m * a.O1 + n : (size_t)m * (a.Cout - a.O1) + (n - a.O1);
+        const float* mk = first ? a.om1 : a.om2;
+        if (mk) {
+          const float2 mv = *reinterpret_cast<const float2*>(mk + off);
+          v0 = mv.x > 0.f ? v0 : 0.f;
+          v1 = mv.y > 0.f ? v1 : 0.f;
+        }
+        *reinterpret_cast<float2*>((first ? a.y1 : a.y2) + off) = make_float2(v0, v1);
       }
     }
 }
@@ -242,8 +263,7 @@ __device__ __forceinline__ int swz(int r, int c) {
 }
 
 struct WgradArgs {
-  const float* dy;   // [P][Cout] gradient of the layer output
-  const float* y;    // [P][Cout] layer output (ReLU mask) or null
+  const float* dz;   // [P][Cout] gradient of the layer's pre-activation
   const float* x1;   // layer input channels [0, C1)
   const float* x2;   // channels [C1, C1 + C2)
   int C1, C2, Cout;
@@ -252,85 +272,76 @@ struct WgradArgs {
   float* part;       // [splits][Cout][9][Cin]
 };
 
+template <int BM, int BN>
+constexpr size_t wgrad_smem() {
+  return (size_t)kStages * kBK * (BM + BN) * 4 + (size_t)kBK * (BM + BN) * 2;
+}
+
 // Weight gradient dW[co][tap][ci] = sum_p dZ[p][co] X[p + tap][ci] as a GEMM
 // with M = Cout, N = 9 Cin (tiles inside one tap), K = pixels, split over
-// blockIdx.z.  Both operands are staged K-major ([pixel][channel]) and read
-// with ldmatrix.trans.  Warp tile 16 x 16, (BM / 16) x (BN / 16) warps.
+// blockIdx.z.  Both FP32 operand chunks ([pixel][channel], 32 pixels) are
+// staged by a 3-stage cp.async pipeline (shifted pixels outside the image
+// zero-filled), converted to swizzled BF16 tiles and read with
+// ldmatrix.trans.  Warp tile 16 x 16, (BM / 16) x (BN / 16) warps.
 template <int BM, int BN>
 __global__ void __launch_bounds__((BM / 16) * (BN / 16) * 32) k_conv3x3_wgrad(const WgradArgs a) {
   constexpr int NW_N = BN / 16, NTH = (BM / 16) * NW_N * 32;
-  constexpr int CA = BM / 8, CB = BN / 8;  // 16-byte chunks per staged row
-  __shared__ __align__(128) uint32_t sA[2][kBK * BM / 2];
-  __shared__ __align__(128) uint32_t sB[2][kBK * BN / 2];
+  constexpr int CA = BM / 8, CB = BN / 8;  // 16-byte chunks per BF16 row
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* Af = reinterpret_cast<float*>(smraw);                 // [kStages][kBK][BM]
+  float* Bf = Af + (size_t)kStages * kBK * BM;                 // [kStages][kBK][BN]
+  uint32_t* sA = reinterpret_cast<uint32_t*>(Bf + (size_t)kStages * kBK * BN);  // [kBK][BM] bf16
+  uint32_t* sB = sA + kBK * BM / 2;                            // [kBK][BN] bf16
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp / NW_N, wn = warp % NW_N;
   const int Cin = a.C1 + a.C2, ctiles = Cin / BN;
   const int m0 = blockIdx.x * BM;
   const int tap = blockIdx.y / ctiles, ci0 = (blockIdx.y % ctiles) * BN;
   const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-  const int P = a.B * a.H * a.Wd;
+  const int HW = a.H * a.Wd, P = a.B * HW;
   const int c_begin = blockIdx.z * a.chunks_per_split;
   const int c_end = min(c_begin + a.chunks_per_split, (P + kBK - 1) / kBK);
   const float* xs = ci0 < a.C1 ? a.x1 : a.x2;
   const int xc = ci0 < a.C1 ? a.C1 : a.C2, xo = ci0 < a.C1 ? ci0 : ci0 - a.C1;
 
-  constexpr int NA4 = kBK * BM / 4, NB4 = kBK * BN / 4;  // float4 loads per tile
-  constexpr int LA = (NA4 + NTH - 1) / NTH, LB = (NB4 + NTH - 1) / NTH;
-  float4 ra[LA], rb[LB];
-  auto load = [&](int ch) {
+  constexpr int NA16 = kBK * BM / 4, NB16 = kBK * BN / 4;  // 16-byte chunks per stage
+  auto load_stage = [&](int ch, int st) {
     const int p0 = ch * kBK;
-#pragma unroll
-    for (int t = 0; t < LA; ++t) {
-      const int idx = tid + t * NTH;
-      ra[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (idx < NA4) {
-        const int r = idx / (BM / 4), c4 = idx % (BM / 4), p = p0 + r;
-        if (p < P) {
-          float4 v = *reinterpret_cast<const float4*>(a.dy + (size_t)p * a.Cout + m0 + 4 * c4);
-          if (a.y) {
-            const float4 m = *reinterpret_cast<const float4*>(a.y + (size_t)p * a.Cout + m0 + 4 * c4);
-            v.x = m.x > 0.f ? v.x : 0.f;
-            v.y = m.y > 0.f ? v.y : 0.f;
-            v.z = m.z > 0.f ? v.z : 0.f;
-            v.w = m.w > 0.f ? v.w : 0.f;
-          }
-          ra[t] = v;
-        }
-      }
+    float* da = Af + (size_t)st * kBK * BM;
+    float* db = Bf + (size_t)st * kBK * BN;
+    for (int idx = tid; idx < NA16; idx += NTH) {
+      const int r = idx / (BM / 4), c4 = idx % (BM / 4), p = p0 + r;
+      const bool ok = p < P;
+      const float* src = ok ? a.dz + (size_t)p * a.Cout + m0 + 4 * c4 : a.dz;
+      cp_async16_zfill(smem_u32(da + r * BM + 4 * c4), src, ok);
     }
-#pragma unroll
-    for (int t = 0; t < LB; ++t) {
-      const int idx = tid + t * NTH;
-      rb[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (idx < NB4) {
-        const int r = idx / (BN / 4), c4 = idx % (BN / 4), p = p0 + r;
-        if (p < P) {
-          const int b = p / (a.H * a.Wd), rem = p - b * a.H * a.Wd;
-          const int py = rem / a.Wd + dy, px = rem % a.Wd + dx;
-          if (py >= 0 && py < a.H && px >= 0 && px < a.Wd)
-            rb[t] = *reinterpret_cast<const float4*>(xs + (((size_t)b * a.H + py) * a.Wd + px) * xc + xo + 4 * c4);
-        }
+    for (int idx = tid; idx < NB16; idx += NTH) {
+      const int r = idx / (BN / 4), c4 = idx % (BN / 4), p = p0 + r;
+      bool ok = p < P;
+      const float* src = xs;
+      if (ok) {
+        const int b = p / HW, rem = p - b * HW;
+        const int py = rem / a.Wd + dy, px = rem % a.Wd + dx;
+        ok = py >= 0 && py < a.H && px >= 0 && px < a.Wd;
+        if (ok) src = xs + (((size_t)b * a.H + py) * a.Wd + px) * xc + xo + 4 * c4;
       }
+      cp_async16_zfill(smem_u32(db + r * BN + 4 * c4), src, ok);
     }
   };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int t = 0; t < LA; ++t) {
-      const int idx = tid + t * NTH;
-      if (idx < NA4) {
-        const int r = idx / (BM / 4), c4 = idx % (BM / 4);
-        uint2 q = make_uint2(pack_bf16(ra[t].x, ra[t].y), pack_bf16(ra[t].z, ra[t].w));
-        *reinterpret_cast<uint2*>(sA[buf] + 4 * swz<CA>(r, c4 >> 1) + 2 * (c4 & 1)) = q;
-      }
+  auto convert = [&](int st) {
+    const float* da = Af + (size_t)st * kBK * BM;
+    const float* db = Bf + (size_t)st * kBK * BN;
+    for (int idx = tid; idx < NA16; idx += NTH) {
+      const int r = idx / (BM / 4), c4 = idx % (BM / 4);
+      const float4 v = *reinterpret_cast<const float4*>(da + r * BM + 4 * c4);
+      *reinterpret_cast<uint2*>(sA + 4 * swz<CA>(r, c4 >> 1) + 2 * (c4 & 1)) =
+          make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
     }
-#pragma unroll
-    for (int t = 0; t < LB; ++t) {
-      const int idx = tid + t * NTH;
-      if (idx < NB4) {
-        const int r = idx / (BN / 4), c4 = idx % (BN / 4);
-        uint2 q = make_uint2(pack_bf16(rb[t].x, rb[t].y), pack_bf16(rb[t].z, rb[t].w));
-        *reinterpret_cast<uint2*>(sB[buf] + 4 * swz<CB>(r, c4 >> 1) + 2 * (c4 & 1)) = q;
-      }
+    for (int idx = tid; idx < NB16; idx += NTH) {
+      const int r = idx / (BN / 4), c4 = idx % (BN / 4);
+      const float4 v = *reinterpret_cast<const float4*>(db + r * BN + 4 * c4);
+      *reinterpret_cast<uint2*>(sB + 4 * swz<CB>(r, c4 >> 1) + 2 * (c4 & 1)) =
+          make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
     }
   };
 
@@ -339,35 +350,42 @@ __global__ void __launch_bounds__((BM / 16) * (BN / 16) * 32) k_conv3x3_wgrad(co
   for (int j = 0; j < 2; ++j)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-  if (c_begin < c_end) {
-    load(c_begin);
-    store(0);
-    __syncthreads();
-    for (int ch = c_begin; ch < c_end; ++ch) {
-      const int cur = (ch - c_begin) & 1;
-      if (ch + 1 < c_end) load(ch + 1);
+  const int nch = max(0, c_end - c_begin);
 #pragma unroll
-      for (int ks = 0; ks < 2; ++ks) {
-        const int q = lane >> 3;
-        uint32_t af[4];
-        {
-          const int k = ks * 16 + (lane & 7) + ((q >> 1) << 3);
-          const int c = wm * 2 + (q & 1);
-          ldsm_x4_t(smem_u32(sA[cur] + 4 * swz<CA>(k, c)), af[0], af[1], af[2], af[3]);
-        }
-        uint32_t b0, b1, b2, b3;
-        {
-          const int k = ks * 16 + (lane & 7) + ((q & 1) << 3);
-          const int c = wn * 2 + (q >> 1);
-          ldsm_x4_t(smem_u32(sB[cur] + 4 * swz<CB>(k, c)), b0, b1, b2, b3);
-        }
-        mma_bf16(acc[0], af, b0, b1);
-        mma_bf16(acc[1], af, b2, b3);
+  for (int st = 0; st < kStages - 1; ++st) {
+    if (st < nch) load_stage(c_begin + st, st);
+    cp_async_commit();
+  }
+  for (int k = 0; k < nch; ++k) {
+    cp_async_wait<kStages - 2>();
+    __syncthreads();
+    convert(k % kStages);
+    {
+      const int nx = k + kStages - 1;
+      if (nx < nch) load_stage(c_begin + nx, nx % kStages);
+      cp_async_commit();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int q = lane >> 3;
+      uint32_t af[4];
+      {
+        const int kk = ks * 16 + (lane & 7) + ((q >> 1) << 3);
+        const int c = wm * 2 + (q & 1);
+        ldsm_x4_t(smem_u32(sA + 4 * swz<CA>(kk, c)), af[0], af[1], af[2], af[3]);
       }
-      if (ch + 1 < c_end) store(cur ^ 1);
-      __syncthreads();
+      uint32_t b0, b1, b2, b3;
+      {
+        const int kk = ks * 16 + (lane & 7) + ((q & 1) << 3);
+        const int c = wn * 2 + (q >> 1);
+        ldsm_x4_t(smem_u32(sB + 4 * swz<CB>(kk, c)), b0, b1, b2, b3);
+      }
+      mma_bf16(acc[0], af, b0, b1);
+      mma_bf16(acc[1], af, b2, b3);
     }
   }
+  cp_async_wait<0>();
   float* dst = a.part + (size_t)blockIdx.z * a.Cout * 9 * Cin;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -443,9 +461,11 @@ __global__ void __launch_bounds__(kEW) k_avgpool(const float* __restrict__ x, fl
   }
 }
 
-// adjoint of the pooling plus the skip gradient: g[p] = gp[p/2] / 4 + gs[p]
+// adjoint of the pooling plus the skip gradient: g[p] = gp[p/2] / 4 + gs[p],
+// zeroed where the ReLU mask mk (if given) is not positive
 __global__ void __launch_bounds__(kEW) k_avgpool_bwd(const float* __restrict__ gp, const float* __restrict__ gs,
-                                                     float* __restrict__ g, int B, int H, int W, int C) {
+                                                     const float* __restrict__ mk, float* __restrict__ g, int B, int H,
+                                                     int W, int C) {
   const int C4 = C / 4;
   const long long n = (long long)B * H * W * C4;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -463,6 +483,13 @@ __global__ void __launch_bounds__(kEW) k_avgpool_bwd(const float* __restrict__ g
       o.y += s.y;
       o.z += s.z;
       o.w += s.w;
+    }
+    if (mk) {
+      const float4 m = reinterpret_cast<const float4*>(mk)[i];
+      o.x = m.x > 0.f ? o.x : 0.f;
+      o.y = m.y > 0.f ? o.y : 0.f;
+      o.z = m.z > 0.f ? o.z : 0.f;
+      o.w = m.w > 0.f ? o.w : 0.f;
     }
     reinterpret_cast<float4*>(g)[i] = o;
   }
@@ -484,9 +511,10 @@ __global__ void __launch_bounds__(kEW) k_upsample(const float* __restrict__ x, f
   }
 }
 
-// adjoint of the upsampling: sum of the 2x2 block
-__global__ void __launch_bounds__(kEW) k_upsample_bwd(const float* __restrict__ g, float* __restrict__ gx, int B, int H,
-                                                      int W, int C) {
+// adjoint of the upsampling: sum of the 2x2 block, zeroed where the ReLU
+// mask mk (if given) is not positive
+__global__ void __launch_bounds__(kEW) k_upsample_bwd(const float* __restrict__ g, const float* __restrict__ mk,
+                                                      float* __restrict__ gx, int B, int H, int W, int C) {
   const int C4 = C / 4;
   const long long n = (long long)B * H * W * C4;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -499,8 +527,16 @@ __global__ void __launch_bounds__(kEW) k_upsample_bwd(const float* __restrict__ 
     const float4* s = reinterpret_cast<const float4*>(g);
     const size_t r0 = (((size_t)b * 2 * H + 2 * yy) * 2 * W + 2 * x) * C4 + c4, r1 = r0 + (size_t)2 * W * C4;
     const float4 a0 = s[r0], a1 = s[r0 + C4], a2 = s[r1], a3 = s[r1 + C4];
-    reinterpret_cast<float4*>(gx)[i] =
-        make_float4(a0.x + a1.x + a2.x + a3.x, a0.y + a1.y + a2.y + a3.y, a0.z + a1.z + a2.z + a3.z, a0.w + a1.w + a2.w + a3.w);
+    float4 o = make_float4(a0.x + a1.x + a2.x + a3.x, a0.y + a1.y + a2.y + a3.y, a0.z + a1.z + a2.z + a3.z,
+                           a0.w + a1.w + a2.w + a3.w);
+    if (mk) {
+      const float4 m = reinterpret_cast<const float4*>(mk)[i];
+      o.x = m.x > 0.f ? o.x : 0.f;
+      o.y = m.y > 0.f ? o.y : 0.f;
+      o.z = m.z > 0.f ? o.z : 0.f;
+      o.w = m.w > 0.f ? o.w : 0.f;
+    }
+    reinterpret_cast<float4*>(gx)[i] = o;
   }
 }
 
@@ -543,12 +579,19 @@ __global__ void __launch_bounds__(kEW) k_loss(const float* __restrict__ out, con
   }
 }
 
-// head backward: gh[p][c] = g[p] Wh[c]
+// head backward: gh[p][c] = g[p] Wh[c] where h[p][c] > 0 (h is a ReLU output)
 __global__ void __launch_bounds__(kEW) k_head_bwd(const float* __restrict__ g, const float* __restrict__ wh,
-                                                  float* __restrict__ gh, int P, int C) {
+                                                  const float* __restrict__ h, float* __restrict__ gh, int P, int C) {
   const long long n = (long long)P * C;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    gh[i] = g[i / C] * wh[i % C];
+    gh[i] = h[i] > 0.f ? g[i / C] * wh[i % C] : 0.f;
+}
+
+// dz = dy where y > 0, else 0
+__global__ void __launch_bounds__(kEW) k_relu_mask(const float* __restrict__ dy, const float* __restrict__ y,
+                                                   float* __restrict__ dz, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dz[i] = y[i] > 0.f ? dy[i] : 0.f;
 }
 
 // head weight gradient partials: part[s][c] = sum_p g[p] h[p][c] (c < C),
@@ -718,25 +761,49 @@ size_t wgrad_splits(int cout, int c1, int c2, long long P, int* bm, int* bn, int
   return (size_t)s * cout * 9 * cin;
 }
 
+// the pipelined kernels need more than the default 48 KB of dynamic shared
+// memory: raise the limit once per process (per kernel)
+bool smem_attrs_set() {
+  static const bool ok = [] {
+    bool r = true;
+    r &= cudaFuncSetAttribute(k_conv3x3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<64>()) ==
+         cudaSuccess;
+    r &= cudaFuncSetAttribute(k_conv3x3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<32>()) ==
+         cudaSuccess;
+    r &= cudaFuncSetAttribute(k_conv3x3_wgrad<64, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)wgrad_smem<64, 64>()) == cudaSuccess;
+    r &= cudaFuncSetAttribute(k_conv3x3_wgrad<64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)wgrad_smem<64, 32>()) == cudaSuccess;
+    r &= cudaFuncSetAttribute(k_conv3x3_wgrad<32, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)wgrad_smem<32, 64>()) == cudaSuccess;
+    r &= cudaFuncSetAttribute(k_conv3x3_wgrad<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)wgrad_smem<32, 32>()) == cudaSuccess;
+    return r;
+  }();
+  return ok;
+}
+
 void launch_conv(const Net& n, const ConvArgs& a, cudaStream_t s) {
   const int P = a.B * a.H * a.Wd;
+  smem_attrs_set();  // if this failed, the launch below reports the error
   if (a.Cout % 64 == 0) {
     dim3 grid((P + kBM - 1) / kBM, a.Cout / 64);
-    k_conv3x3<64><<<grid, kCT, 0, s>>>(a);
+    k_conv3x3<64><<<grid, kCT, conv_smem<64>(), s>>>(a);
   } else {
     dim3 grid((P + kBM - 1) / kBM, a.Cout / 32);
-    k_conv3x3<32><<<grid, kCT, 0, s>>>(a);
+    k_conv3x3<32><<<grid, kCT, conv_smem<32>(), s>>>(a);
   }
   (void)n;
 }
 
 void launch_wgrad(const WgradArgs& a, int bm, int bn, int splits, cudaStream_t s) {
   const int Cin = a.C1 + a.C2;
+  smem_attrs_set();
   dim3 grid(a.Cout / bm, 9 * (Cin / bn), splits);
-  if (bm == 64 && bn == 64) k_conv3x3_wgrad<64, 64><<<grid, 16 * 32, 0, s>>>(a);
-  else if (bm == 64) k_conv3x3_wgrad<64, 32><<<grid, 8 * 32, 0, s>>>(a);
-  else if (bn == 64) k_conv3x3_wgrad<32, 64><<<grid, 8 * 32, 0, s>>>(a);
-  else k_conv3x3_wgrad<32, 32><<<grid, 4 * 32, 0, s>>>(a);
+  if (bm == 64 && bn == 64) k_conv3x3_wgrad<64, 64><<<grid, 16 * 32, wgrad_smem<64, 64>(), s>>>(a);
+  else if (bm == 64) k_conv3x3_wgrad<64, 32><<<grid, 8 * 32, wgrad_smem<64, 32>(), s>>>(a);
+  else if (bn == 64) k_conv3x3_wgrad<32, 64><<<grid, 8 * 32, wgrad_smem<32, 64>(), s>>>(a);
+  else k_conv3x3_wgrad<32, 32><<<grid, 4 * 32, wgrad_smem<32, 32>(), s>>>(a);
 }
 
 // forward of one 3x3 layer: y = relu(conv(x1 | x2) + b)
@@ -748,7 +815,6 @@ void conv_fwd(Net& n, int li, const float* x1, int C1, const float* x2, int C2, 
   a.x2 = x2;
   a.C1 = C1;
   a.C2 = C2;
-  a.m1 = nullptr;
   a.W = n.wf + L.bf_off;
   a.bias = n.param + L.b_off;
   a.y1 = y;
@@ -762,24 +828,28 @@ void conv_fwd(Net& n, int li, const float* x1, int C1, const float* x2, int C2, 
   launch_conv(n, a, s);
 }
 
-// backward of one 3x3 layer with output y = relu(z): data gradient into
-// (dx1 | dx2) if dx1 is given, weight and bias gradients into n.grad
-void conv_bwd(Net& n, int li, const float* dy, const float* y, const float* x1, int C1, const float* x2, int C2,
-              float* dx1, float* dx2, int B, int lv, cudaStream_t s) {
+// backward of one 3x3 layer at dz = dL/dz, z its pre-activation: data
+// gradient into (dx1 | dx2) if dx1 is given -- each part zeroed where its
+// mask (om1 / om2, the ReLU output it lands on) is not positive, so it is
+// again a pre-activation gradient -- and the weight and bias gradients into
+// n.grad
+void conv_bwd(Net& n, int li, const float* dz, const float* x1, int C1, const float* x2, int C2, float* dx1,
+              float* dx2, const float* om1, const float* om2, int B, int lv, cudaStream_t s) {
   const Layer& L = n.layers[li];
   const int H = n.H >> lv, W = n.W >> lv;
   const long long P = (long long)B * H * W;
   if (dx1) {
     ConvArgs a{};
-    a.x1 = dy;
+    a.x1 = dz;
     a.x2 = nullptr;
     a.C1 = L.cout;
     a.C2 = 0;
-    a.m1 = y;
     a.W = n.wt + L.bf_off;
     a.bias = nullptr;
     a.y1 = dx1;
     a.y2 = dx2;
+    a.om1 = om1;
+    a.om2 = om2;
     a.O1 = C1;
     a.Cout = C1 + C2;
     a.relu = 0;
@@ -791,8 +861,7 @@ void conv_bwd(Net& n, int li, const float* dy, const float* y, const float* x1, 
   int bm, bn, splits, cps;
   wgrad_splits(L.cout, C1, C2, P, &bm, &bn, &splits, &cps);
   WgradArgs w{};
-  w.dy = dy;
-  w.y = y;
+  w.dz = dz;
   w.x1 = x1;
   w.x2 = x2;
   w.C1 = C1;
@@ -806,10 +875,10 @@ void conv_bwd(Net& n, int li, const float* dy, const float* y, const float* x1, 
   launch_wgrad(w, bm, bn, splits, s);
   const long long nw = (long long)L.cout * 9 * (C1 + C2);
   k_split_sum<<<grid_for(nw), kEW, 0, s>>>(n.part, splits, nw, n.grad + L.w_off, 0);
-  // bias: per-channel sums of dZ over pixel ranges, then the fixed-order sum
+  // bias: per-channel sums of dz over pixel ranges, then the fixed-order sum
   const int rows = (int)colsum_rows(P), sp = (int)((P + rows - 1) / rows);
   dim3 cg((L.cout + 31) / 32, sp);
-  k_colsum<<<cg, kEW, 0, s>>>(dy, y, (int)P, L.cout, rows, n.part);
+  k_colsum<<<cg, kEW, 0, s>>>(dz, nullptr, (int)P, L.cout, rows, n.part);
   k_split_sum<<<grid_for(L.cout), kEW, 0, s>>>(n.part, sp, L.cout, n.grad + L.b_off, 0);
 }
 
@@ -851,39 +920,46 @@ void forward_pass(Net& n, const float* x, int B, cudaStream_t s) {
 }
 
 void backward_pass(Net& n, const float* x, const float* t, int B, cudaStream_t s) {
+  // every gradient buffer of a ReLU output holds the pre-activation gradient
+  // dL/dz of the layer that produced it (the ReLU mask is applied where the
+  // gradient is formed)
   const int P0 = B * n.H * n.W;
   const int lg = std::min(1024, (P0 + kEW - 1) / kEW);
   k_loss<<<lg, kEW, 0, s>>>(n.out, t, n.g_out, P0, n.loss_part);
   const float* h = n.L > 1 ? n.db[0] : n.eb[0];
   float* gh = n.L > 1 ? n.g_db[0] : n.g_eb[0];
   const Layer& Hd = n.layers[head_idx(n)];
-  k_head_bwd<<<grid_for((long long)P0 * n.c[0]), kEW, 0, s>>>(n.g_out, n.param + Hd.w_off, gh, P0, n.c[0]);
+  k_head_bwd<<<grid_for((long long)P0 * n.c[0]), kEW, 0, s>>>(n.g_out, n.param + Hd.w_off, h, gh, P0, n.c[0]);
   {
     const int rows = 2048, sp = (P0 + rows - 1) / rows;
     k_head_wgrad<<<sp, kEW, 0, s>>>(n.g_out, h, P0, n.c[0], rows, n.part);
     k_split_sum<<<grid_for(n.c[0] + 1), kEW, 0, s>>>(n.part, sp, n.c[0] + 1, n.grad + Hd.w_off, 0);
   }
   for (int l = 0; l <= n.L - 2; ++l) {
-    conv_bwd(n, dec_b(n, l), n.g_db[l], n.db[l], n.da[l], n.c[l], nullptr, 0, n.g_da[l], nullptr, B, l, s);
-    conv_bwd(n, dec_a(n, l), n.g_da[l], n.da[l], n.eb[l], n.c[l], n.upout[l], n.c[l], n.g_skip[l], n.g_upout[l], B,
-             l, s);
-    conv_bwd(n, dec_up(n, l), n.g_upout[l], n.upout[l], n.upin[l], n.c[l + 1], nullptr, 0, n.g_upin[l], nullptr, B, l,
-             s);
+    conv_bwd(n, dec_b(n, l), n.g_db[l], n.da[l], n.c[l], nullptr, 0, n.g_da[l], nullptr, n.da[l], nullptr, B, l, s);
+    // the skip part is summed with the pooled path before its mask applies
+    conv_bwd(n, dec_a(n, l), n.g_da[l], n.eb[l], n.c[l], n.upout[l], n.c[l], n.g_skip[l], n.g_upout[l], nullptr,
+             n.upout[l], B, l, s);
+    conv_bwd(n, dec_up(n, l), n.g_upout[l], n.upin[l], n.c[l + 1], nullptr, 0, n.g_upin[l], nullptr, nullptr, nullptr,
+             B, l, s);
     float* gnext = l + 1 <= n.L - 2 ? n.g_db[l + 1] : n.g_eb[n.L - 1];
+    const float* mnext = l + 1 <= n.L - 2 ? n.db[l + 1] : n.eb[n.L - 1];
     const long long cnt = (long long)B * (n.H >> (l + 1)) * (n.W >> (l + 1)) * n.c[l + 1] / 4;
-    k_upsample_bwd<<<grid_for(cnt), kEW, 0, s>>>(n.g_upin[l], gnext, B, n.H >> (l + 1), n.W >> (l + 1), n.c[l + 1]);
+    k_upsample_bwd<<<grid_for(cnt), kEW, 0, s>>>(n.g_upin[l], mnext, gnext, B, n.H >> (l + 1), n.W >> (l + 1),
+                                                 n.c[l + 1]);
   }
   for (int l = n.L - 1; l >= 0; --l) {
     if (l < n.L - 1) {
       const long long cnt = (long long)B * (n.H >> l) * (n.W >> l) * n.c[l] / 4;
-      k_avgpool_bwd<<<grid_for(cnt), kEW, 0, s>>>(n.g_pool[l], n.g_skip[l], n.g_eb[l], B, n.H >> l, n.W >> l, n.c[l]);
+      k_avgpool_bwd<<<grid_for(cnt), kEW, 0, s>>>(n.g_pool[l], n.g_skip[l], n.eb[l], n.g_eb[l], B, n.H >> l,
+                                                  n.W >> l, n.c[l]);
     }
-    conv_bwd(n, enc_b(l), n.g_eb[l], n.eb[l], n.ea[l], n.c[l], nullptr, 0, n.g_ea[l], nullptr, B, l, s);
+    conv_bwd(n, enc_b(l), n.g_eb[l], n.ea[l], n.c[l], nullptr, 0, n.g_ea[l], nullptr, n.ea[l], nullptr, B, l, s);
     if (l > 0)
-      conv_bwd(n, enc_a(l), n.g_ea[l], n.ea[l], n.pool[l - 1], n.c[l - 1], nullptr, 0, n.g_pool[l - 1], nullptr, B, l,
-               s);
+      conv_bwd(n, enc_a(l), n.g_ea[l], n.pool[l - 1], n.c[l - 1], nullptr, 0, n.g_pool[l - 1], nullptr, nullptr,
+               nullptr, B, l, s);
     else
-      conv_bwd(n, enc_a(0), n.g_ea[0], n.ea[0], n.X0, 32, nullptr, 0, nullptr, nullptr, B, 0, s);
+      conv_bwd(n, enc_a(0), n.g_ea[0], n.X0, 32, nullptr, 0, nullptr, nullptr, nullptr, nullptr, B, 0, s);
   }
 }
 
@@ -1127,8 +1203,7 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
     float* part = nullptr;
     if (cudaMalloc(&part, sizeof(float) * need) != cudaSuccess) return CPCT_ENOMEM;
     WgradArgs w{};
-    w.dy = d_b;
-    w.y = nullptr;
+    w.dz = d_b;
     w.x1 = d_a;
     w.x2 = nullptr;
     w.C1 = C1;
@@ -1181,16 +1256,25 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
         a.Cout = Cout;
         a.relu = 1;
       } else {
-        a.x1 = d_a;
-        a.C1 = Cout;
-        a.C2 = 0;
-        a.m1 = d_b;
-        a.W = bf + nw;
-        a.y1 = d_y;
-        a.O1 = Cin;
-        a.Cout = Cin;
+        // pre-activation gradient dz = a * (b > 0), then the data gradient
+        float* dz = nullptr;
+        const long long nz = (long long)B * H * W * Cout;
+        if (cudaMalloc(&dz, sizeof(float) * nz) != cudaSuccess) rc = CPCT_ENOMEM;
+        if (rc == CPCT_OK) {
+          k_relu_mask<<<grid_for(nz), kEW, 0, stream>>>(d_a, d_b, dz, nz);
+          a.x1 = dz;
+          a.C1 = Cout;
+          a.C2 = 0;
+          a.W = bf + nw;
+          a.y1 = d_y;
+          a.O1 = Cin;
+          a.Cout = Cin;
+          launch_conv(Net(), a, stream);
+          if (cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
+          cudaFree(dz);
+        }
       }
-      launch_conv(Net(), a, stream);
+      if (rc == CPCT_OK && op == 0) launch_conv(Net(), a, stream);
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
     }
     cudaFree(bf);
@@ -1206,10 +1290,10 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
       k_upsample<<<grid_for(n4 * 4), kEW, 0, stream>>>(d_a, d_y, B, H, W, C1);
       break;
     case 3:
-      k_avgpool_bwd<<<grid_for(n4), kEW, 0, stream>>>(d_a, d_b, d_y, B, H, W, C1);
+      k_avgpool_bwd<<<grid_for(n4), kEW, 0, stream>>>(d_a, d_b, nullptr, d_y, B, H, W, C1);
       break;
     case 4:
-      k_upsample_bwd<<<grid_for(n4), kEW, 0, stream>>>(d_a, d_y, B, H, W, C1);
+      k_upsample_bwd<<<grid_for(n4), kEW, 0, stream>>>(d_a, nullptr, d_y, B, H, W, C1);
       break;
     default:
       return CPCT_EINVAL;
