@@ -39,7 +39,12 @@ WORKLOADS = {
     # name: (N, Ns, M, synth config)
     "c2_2048": (2048, 2048, 1024, "c2_2048"),
     "c1_128": (128, 128, 180, "c1_128"),
+    "paper_1024": (1024, 1024, 180, "paper_1024"),
 }
+# the paper's only timing: FFTs 3 ms + gridding 6 ms on a Tesla C1060 for a
+# 1024 x 1024 grid with 180 angles x 1024 pixels, i.e. 184,320 samples per
+# forward + adjoint pair in 9 ms (context; another machine)
+PAPER_C1060_MSAMPLES = 184320 / 9e-3 / 1e6
 KERNELS = ["k_fwd_col", "k_fwd_row", "k_fwd_interp", "k_fwd_ray", "k_adj_ray", "k_adj_spread",
            "k_adj_reduce", "k_adj_row", "k_adj_col"]
 METRIC = "Radon fwd+adj Msamples/s"
@@ -226,6 +231,36 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def paper_workload(torch, cpct, synth, steps=200):
+    """The operator pair on the paper's timing size (1024^2, 180 x 1024), L2
+    flushed before every step, CUDA events: context next to the paper's own
+    Tesla C1060 figure."""
+    n, ns, m, cfg = WORKLOADS["paper_1024"]
+    plan = cpct.Plan(n, ns, m)
+    img = torch.from_numpy(synth.phantom(cfg)).cuda()
+    y = torch.empty((m, ns), device="cuda")
+    z = torch.empty((n, n), device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(5):
+        plan.fwd(img, y)
+        plan.adj(y, z)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        plan.fwd(img, y)
+        plan.adj(y, z)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    value = m * ns / (ms / 1000.0) / 1e6
+    return {"metric": METRIC, "value": value, "unit": "Msamples/s", "ms_per_step": ms,
+            "workload": f"paper_1024: {n}x{n} float32 phantom, {m} views x {ns} bins",
+            "paper_c1060_context": {"value": PAPER_C1060_MSAMPLES, "unit": "Msamples/s",
+                                    "note": "FFTs 3 ms + gridding 6 ms on a Tesla C1060 (another machine)"}}
+
+
 def spgl1_bench(args, torch, cpct, synth):
     """Batched SPGL1 on the 1024^2 / 128-view workload with noise (1% of max)
     and 8 stuck detector columns: slices that reach the root
@@ -390,6 +425,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload)
+    if world == 1:
+        out["paper_workload"] = paper_workload(torch, cpct, synth)
     if world == 1 and args.spgl1_batch > 0:
         out["spgl1"] = spgl1_bench(args, torch, cpct, synth)
     print(json.dumps(out), flush=True)

@@ -50,6 +50,9 @@ CONFIGS = {
     "c4_spgl1_1024": dict(index=3, n=1024, n_det=1024, n_views=128, batch=64,
                           kind="laplacian", n_shapes=20, iterations=300),
     "c5_warm512": dict(index=4, n=512, n_det=512, n_views=90, kind="laplacian", n_shapes=12),
+    # the size of the paper's own timing (1024 x 1024 grid, 180 angles x 1024
+    # pixels per angle, section "fast radon transform")
+    "paper_1024": dict(index=5, n=1024, n_det=1024, n_views=180, kind="ellipses", n_shapes=20),
 }
 
 
