@@ -69,11 +69,21 @@ __device__ __forceinline__ void dft_reg(float2* x) {
   for (int i = 0; i < R; ++i) x[i] = y[i];
 }
 
-template <int LOGN, int E, int DIR>
+// PIN: the input is zero outside the circular window [-N/4, N/4) (a signal
+// of N/2 values zero-padded to N); in the first pass (radix R >= 4) those
+// zeros are exactly the inputs m = R/4 .. 3R/4-1 of every DFT, which are
+// then neither loaded nor computed on (constant zeros fold away), and the
+// caller need not write them.  POUT: only the outputs in [-N/4, N/4) are needed; the last pass
+// stores only the outputs m < R/4 and m >= 3R/4 of every DFT, and the others
+// are left unwritten.
+template <int LOGN, int E, int DIR, bool PIN = false, bool POUT = false>
 struct SmemFFT {
   static constexpr int N = 1 << LOGN;
   static constexpr int T = N / E;  // threads per FFT
-  static constexpr int PADN = N + (N >> 4);
+  // buffers of the FFTs of one CTA start 4 complex values (two 16-byte bank
+  // groups) apart modulo 128 bytes: reads of one index from several FFTs
+  // fall in distinct banks
+  static constexpr int PADN = N + (N >> 4) + 4;
   static constexpr int NPASS = fft_npass(LOGN);
   static_assert(E >= 16 && (N % E) == 0, "E must be >= 16 and divide N");
 
@@ -89,7 +99,10 @@ struct SmemFFT {
     for (int b = 0; b < NB; ++b) {
       const int i = t + b * T;
 #pragma unroll
-      for (int m = 0; m < R; ++m) v[b * R + m] = buf[fpad(i + m * (N / R))];
+      for (int m = 0; m < R; ++m) {
+        if (PIN && R >= 4 && P == 0 && m >= R / 4 && m < 3 * R / 4) v[b * R + m] = make_float2(0.f, 0.f);
+        else v[b * R + m] = buf[fpad(i + m * (N / R))];
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -109,7 +122,12 @@ struct SmemFFT {
       dft_reg<LR, DIR>(x);
       const int base = (i - j) * R + j;
 #pragma unroll
-      for (int m = 0; m < R; ++m) buf[fpad(base + m * L)] = x[m];
+      for (int m = 0; m < R; ++m) {
+        // (for R >= 4 the outputs i + m N/R, i < N/R, outside [-N/4, N/4)
+        // are exactly m = R/4 .. 3R/4-1; a radix-2 last pass stores all)
+        if (POUT && R >= 4 && P == NPASS - 1 && m >= R / 4 && m < 3 * R / 4) continue;
+        buf[fpad(base + m * L)] = x[m];
+      }
     }
     __syncthreads();
   }

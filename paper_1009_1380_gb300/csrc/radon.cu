@@ -61,16 +61,12 @@ template <int LOGG>
 __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
     k_fwd_col(const float* __restrict__ img, const float* __restrict__ dp, float2* __restrict__ H1,
               const float2* __restrict__ tw) {
-  using FFT = SmemFFT<LOGG, kEcol, -1>;
+  // the padding half [N/2, G - N/2) is zero: the FFT skips it (PIN)
+  using FFT = SmemFFT<LOGG, kEcol, -1, true, false>;
   constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kEcol;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * (2 * kColFFTs);
-  // zero the padding half [N/2, G - N/2) of every FFT
-  for (int idx = tid; idx < kColFFTs * N; idx += nthr) {
-    const int f = idx / N, q = N / 2 + idx % N;
-    sm[f * FFT::PADN + fpad(q)] = make_float2(0.f, 0.f);
-  }
   // deapodized columns: FFT f packs columns q0+2f (real part), q0+2f+1 (imag)
 #pragma unroll
   for (int idx = tid; idx < kColHalf * N; idx += nthr) {
@@ -100,7 +96,8 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
 template <int LOGG>
 __global__ void __launch_bounds__(kThreads)
     k_fwd_row(const float2* __restrict__ H1, float2* __restrict__ Hx, const float2* __restrict__ tw, int ldh) {
-  using FFT = SmemFFT<LOGG, kErow, -1>;
+  // the padding half [N/2, G - N/2) is zero: the FFT skips it (PIN)
+  using FFT = SmemFFT<LOGG, kErow, -1, true, false>;
   constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = rows_per_cta<LOGG>();
   extern __shared__ float2 sm[];
   const int f = threadIdx.x / T, t = threadIdx.x % T;
@@ -109,7 +106,6 @@ __global__ void __launch_bounds__(kThreads)
   const bool valid = b <= N;
 #pragma unroll
   for (int q = t; q < N; q += T) {
-    buf[fpad(N / 2 + q)] = make_float2(0.f, 0.f);
     const int pos = (q - N / 2) & (G - 1);
     buf[fpad(pos)] = valid ? H1[(size_t)b * N + q] : make_float2(0.f, 0.f);
   }
@@ -473,7 +469,8 @@ __device__ __forceinline__ float2 wrapped(const float2* __restrict__ row, int a,
 template <int LOGG>
 __global__ void __launch_bounds__(kThreads)
     k_adj_row(const float2* __restrict__ Ax, float2* __restrict__ H1, const float2* __restrict__ tw, int ldh) {
-  using FFT = SmemFFT<LOGG, kErow, +1>;
+  // only X = -N/2 .. N/2-1 is kept: the FFT skips the other outputs (POUT)
+  using FFT = SmemFFT<LOGG, kErow, +1, false, true>;
   constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = rows_per_cta<LOGG>();
   extern __shared__ float2 sm[];
   const int f = threadIdx.x / T, t = threadIdx.x % T;
@@ -507,7 +504,8 @@ template <int LOGG>
 __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
     k_adj_col(const float2* __restrict__ H1, const float* __restrict__ dp, float* __restrict__ img,
               const float2* __restrict__ tw) {
-  using FFT = SmemFFT<LOGG, kEcol, +1>;
+  // only Y = -N/2 .. N/2-1 is kept: the FFT skips the other outputs (POUT)
+  using FFT = SmemFFT<LOGG, kEcol, +1, false, true>;
   constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kEcol;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
