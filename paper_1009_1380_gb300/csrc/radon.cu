@@ -194,7 +194,11 @@ __device__ __forceinline__ void interp_sample(const FwdInterpArgs& a, const floa
 // 37x38 grid window of the next item is copied by TMA into the second buffer
 // while the current one is interpolated, and the next item's first sample id
 // and ray are prefetched into registers.
-__global__ void __launch_bounds__(256)
+// bins hold ~130 samples on average (1024 at most): 128 threads per CTA keep
+// most threads busy on every bin
+constexpr int kInterpThreads = 128;
+
+__global__ void __launch_bounds__(kInterpThreads)
     k_fwd_interp(const __grid_constant__ CUtensorMap tmap, const FwdInterpArgs a, int n_items) {
   __shared__ __align__(128) float2 win[2][kWinStride];
   __shared__ __align__(8) uint64_t bar[2];
@@ -666,11 +670,11 @@ int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_
       int dev = 0, sms = 1, per_sm = 1;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_interp, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_interp, kInterpThreads, 0);
       p->fwd_interp_grid = std::max(1, sms * std::max(1, per_sm));
     }
     const int grid = std::min(p->n_fwd_items, p->fwd_interp_grid);
-    k_fwd_interp<<<grid, 256, 0, s>>>(p->tmap_Hx, a, p->n_fwd_items);
+    k_fwd_interp<<<grid, kInterpThreads, 0, s>>>(p->tmap_Hx, a, p->n_fwd_items);
     cpct_prof_end(p, KID_FWD_INTERP, s);
   }
 #define FN(L) launch_fwd_Ns<L>(p, d_sino, s)
