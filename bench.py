@@ -261,6 +261,46 @@ def paper_workload(torch, cpct, synth, steps=200):
                                     "note": "FFTs 3 ms + gridding 6 ms on a Tesla C1060 (another machine)"}}
 
 
+def batch_bench(args, torch, cpct, synth, runs=10):
+    """The operator pair over many slices as one CUDA graph (row a11): 1024^2
+    slices with view counts drawn from {64, 128, 256, 512}, one autotuned plan
+    per view count and clones of it per slice; Msamples/s over the batch."""
+    c = synth.CONFIGS["c3_batch1024"]
+    n = c["n"]
+    views = synth.views_for_batch("c3_batch1024")[:args.batch_slices]
+    base, caps = {}, {}
+    for m in sorted(set(int(v) for v in views)):
+        base[m] = cpct.Plan(n, n, m)
+        caps[m] = cpct.tune(base[m])
+    plans, used = [], {m: 0 for m in base}
+    for v in views:
+        m = int(v)
+        plans.append(base[m] if used[m] == 0 else cpct.clone(base[m]))
+        used[m] += 1
+    distinct = [torch.from_numpy(synth.phantom("c3_batch1024", slice_index=i)).cuda() for i in range(16)]
+    ins = [distinct[i % 16].clone() for i in range(len(plans))]
+    outs = [torch.empty((n, n), device="cuda") for _ in plans]
+    bt = cpct.Batch(plans, ins, outs, mode=cpct.BATCH_PAIR)
+    info = bt.info()
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        bt.run()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(runs)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        bt.run()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / runs
+    bt.close()
+    return {"metric": "batched Radon fwd+adj Msamples/s", "value": info["samples"] / (ms / 1000.0) / 1e6,
+            "unit": "Msamples/s", "ms_per_batch": ms, "slices": info["slices"], "samples_per_batch": info["samples"],
+            "branches": info["branches"], "tuned_caps": {str(m): list(v) for m, v in caps.items()},
+            "workload": f"{len(plans)} slices {n}x{n}, views from {sorted(base)} x {n} bins, one graph launch"}
+
+
 def spgl1_bench(args, torch, cpct, synth):
     """Batched SPGL1 on the 1024^2 / 128-view workload with noise (1% of max)
     and 8 stuck detector columns: slices that reach the root
@@ -427,6 +467,8 @@ def run_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = cpu_baseline(args.workload)
     if world == 1:
         out["paper_workload"] = paper_workload(torch, cpct, synth)
+    if world == 1 and args.batch_slices > 0:
+        out["batch"] = batch_bench(args, torch, cpct, synth)
     if world == 1 and args.spgl1_batch > 0:
         out["spgl1"] = spgl1_bench(args, torch, cpct, synth)
     print(json.dumps(out), flush=True)
@@ -443,21 +485,25 @@ def main():
     ap.add_argument("--workload", default="c2_2048", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spgl1-batch", type=int, default=64, help="slices of the SPGL1 workload (0: skip)")
+    ap.add_argument("--batch-slices", type=int, default=256, help="slices of the batched-operator workload (0: skip)")
     ap.add_argument("--spgl1-iters", type=int, default=0, help="override the SPGL1 iteration cap (0: 300)")
-    ap.add_argument("--only", default="", choices=["", "spgl1"], help="run one secondary workload alone")
+    ap.add_argument("--only", default="", choices=["", "spgl1", "batch"], help="run one secondary workload alone")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.only == "spgl1":
+    elif args.only in ("spgl1", "batch"):
         import torch
         from paper_1009_1380_gb300 import build as b
         b.build()
         from paper_1009_1380_gb300 import cpct, synth
         torch.cuda.set_device(local_rank)
-        print(json.dumps(spgl1_bench(args, torch, cpct, synth)), flush=True)
+        if args.only == "spgl1":
+            print(json.dumps(spgl1_bench(args, torch, cpct, synth)), flush=True)
+        else:
+            print(json.dumps(batch_bench(args, torch, cpct, synth)), flush=True)
     else:
         run_ours(args, rank, world, local_rank)
 
