@@ -9,7 +9,7 @@
 // radix-R DFTs (R = 16, last pass 2..16) and writes the Stockham
 // self-sorting output back.  Twiddles come from a per-pass table laid out
 // [m-1][j] so that consecutive threads read consecutive entries (built in FP64
-// by the plan).  Several FFTs run side by side in one CTA; every thread of the
+// by the plan); a DFT reads three entries and forms the other powers.  Several FFTs run side by side in one CTA; every thread of the
 // CTA must call run() (it contains __syncthreads()).
 #pragma once
 
@@ -94,6 +94,20 @@ struct SmemFFT {
     constexpr int L = 1 << fft_ll(P);
     constexpr int NB = E / R;
     static_assert(E % R == 0, "radix must divide E");
+    // inter-pass twiddles w^m = exp(DIR 2 pi i m j / (R L)), m = 1..R-1: the
+    // table entries for m = 1, 4, 8 (built in FP64) are loaded before the
+    // barrier, the other powers are products of at most four of them
+    float2 w1[NB], w4[NB], w8[NB];
+    if (L > 1) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int j = (t + b * T) & (L - 1);
+        const float2* twp = tw + fft_tw_offset(LOGN, P) + j;
+        w1[b] = __ldg(&twp[0]);
+        if (R > 4) w4[b] = __ldg(&twp[3 * L]);
+        if (R > 8) w8[b] = __ldg(&twp[7 * L]);
+      }
+    }
     float2 v[E];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -111,13 +125,25 @@ struct SmemFFT {
       const int j = i & (L - 1);
       float2* x = &v[b * R];
       if (L > 1) {
-        const float2* twp = tw + fft_tw_offset(LOGN, P) + j;
+        float2 w[R];
+        w[1] = w1[b];
+        if (DIR > 0) w[1].y = -w[1].y;
+        if (R > 2) w[2] = cmul(w[1], w[1]);
+        if (R > 3) w[3] = cmul(w[2], w[1]);
+        if (R > 4) {
+          w[4] = w4[b];
+          if (DIR > 0) w[4].y = -w[4].y;
 #pragma unroll
-        for (int m = 1; m < R; ++m) {
-          float2 w = __ldg(&twp[(m - 1) * L]);
-          if (DIR > 0) w.y = -w.y;
-          x[m] = cmul(x[m], w);
+          for (int m = 5; m < 8 && m < R; ++m) w[m] = cmul(w[4], w[m - 4]);
         }
+        if (R > 8) {
+          w[8] = w8[b];
+          if (DIR > 0) w[8].y = -w[8].y;
+#pragma unroll
+          for (int m = 9; m < R; ++m) w[m] = cmul(w[8], w[m - 8]);
+        }
+#pragma unroll
+        for (int m = 1; m < R; ++m) x[m] = cmul(x[m], w[m]);
       }
       dft_reg<LR, DIR>(x);
       const int base = (i - j) * R + j;
