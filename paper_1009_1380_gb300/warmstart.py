@@ -209,6 +209,11 @@ def evaluate(net, plans, b, sigma, fbp, opts, batch, kappa):
                 inf[i] = dict(inf_fb[j], fallback=True)
         r = _summary(inf, t + t_fb + t_net, t_net)
         r["fallbacks"] = len(bad)
+        # quality of the start: relative L2 distance to the cold solution
+        d0 = (x0 - x_cold).flatten(1).norm(dim=1) / x_cold.flatten(1).norm(dim=1).clamp_min(1e-30)
+        dh = (x_hat - x_cold).flatten(1).norm(dim=1) / x_cold.flatten(1).norm(dim=1).clamp_min(1e-30)
+        r["start_rel_err_mean"] = float(d0.mean().item())
+        r["prediction_rel_err_mean"] = float(dh.mean().item())
         # the warm and the cold solution of each slice: l1 norms
         l1w = np.array([f["xnorm1"] for f in inf])
         l1c = np.array([f["xnorm1"] for f in inf_cold])
