@@ -20,7 +20,7 @@ extern "C" int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cud
 extern "C" int radon_fbp(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream) {
   if (!plan || !d_img || !d_sino || !aligned16(d_img) || !aligned16(d_sino)) return CPCT_EINVAL;
   const double ramp = 3.14159265358979323846 / ((double)plan->m * plan->ns);
-  return cpct_launch_adj_ramp(plan, d_sino, d_img, (float)ramp, stream);
+  return cpct_launch_adj_ramp(plan, d_sino, d_img, (float)ramp, nullptr, stream);
 }
 
 namespace {

@@ -241,5 +241,9 @@ __host__ __device__ constexpr int fft_tw_size(int logn) { return fft_tw_offset(l
 int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_t s);
 int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_t s);
 // the adjoint with the ray spectra weighted by ramp * |k| (ramp = 0: none)
-int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float ramp, cudaStream_t s);
+// and every kernel skipped while *skip != 0 (skip: device flag or null)
+int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float ramp, const int* skip,
+                         cudaStream_t s);
+// the forward with every kernel skipped while *skip != 0
+int cpct_launch_fwd_skip(cpct_plan* p, const float* d_img, float* d_sino, const int* skip, cudaStream_t s);
 int cpct_radon_setup_attributes(int logG, int logNs);

@@ -60,7 +60,8 @@ constexpr size_t fft_smem(int nfft) { return (size_t)nfft * SmemFFT<LOG, kErow, 
 template <int LOGG>
 __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
     k_fwd_col(const float* __restrict__ img, const float* __restrict__ dp, float2* __restrict__ H1,
-              const float2* __restrict__ tw) {
+              const float2* __restrict__ tw, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   // the padding half [N/2, G - N/2) is zero: the FFT skips it (PIN)
   using FFT = SmemFFT<LOGG, kEcol, -1, true, false>;
   constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kEcol;
@@ -95,7 +96,9 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
 // ---------------------------------------------------------------------------
 template <int LOGG>
 __global__ void __launch_bounds__(kThreads)
-    k_fwd_row(const float2* __restrict__ H1, float2* __restrict__ Hx, const float2* __restrict__ tw, int ldh) {
+    k_fwd_row(const float2* __restrict__ H1, float2* __restrict__ Hx, const float2* __restrict__ tw, int ldh,
+              const int* __restrict__ skip) {
+  if (skip && *skip) return;
   // the padding half [N/2, G - N/2) is zero: the FFT skips it (PIN)
   using FFT = SmemFFT<LOGG, kErow, -1, true, false>;
   constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = rows_per_cta<LOGG>();
@@ -134,6 +137,7 @@ struct FwdInterpArgs {
   const float2* Hx;
   float2* Q;
   int* err;
+  const int* skip;  // the launch does nothing while *skip != 0 (may be null)
   int G, ldq, ldh, tiles_x;
   KBPoly poly;
 };
@@ -200,6 +204,7 @@ constexpr int kInterpThreads = 128;
 
 __global__ void __launch_bounds__(kInterpThreads)
     k_fwd_interp(const __grid_constant__ CUtensorMap tmap, const FwdInterpArgs a, int n_items) {
+  if (a.skip && *a.skip) return;
   __shared__ __align__(128) float2 win[2][kWinStride];
   __shared__ __align__(8) uint64_t bar[2];
   const int tid = threadIdx.x;
@@ -272,7 +277,9 @@ __global__ void __launch_bounds__(kInterpThreads)
 // ---------------------------------------------------------------------------
 template <int LOGNS>
 __global__ void __launch_bounds__(kThreads)
-    k_fwd_ray(const float2* __restrict__ Q, float* __restrict__ sino, const float2* __restrict__ tw, int M, int ldq) {
+    k_fwd_ray(const float2* __restrict__ Q, float* __restrict__ sino, const float2* __restrict__ tw, int M, int ldq,
+              const int* __restrict__ skip) {
+  if (skip && *skip) return;
   using FFT = SmemFFT<LOGNS, kErow, +1>;
   constexpr int NS = 1 << LOGNS, T = FFT::T, PPC = rows_per_cta<LOGNS>(), K = NS / 2;
   extern __shared__ float2 sm[];
@@ -308,7 +315,8 @@ __global__ void __launch_bounds__(kThreads)
 template <int LOGNS>
 __global__ void __launch_bounds__(kThreads)
     k_adj_ray(const float* __restrict__ sino, float2* __restrict__ Q, const float2* __restrict__ tw, int M, int ldq,
-              float ramp) {
+              float ramp, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   using FFT = SmemFFT<LOGNS, kErow, -1>;
   constexpr int NS = 1 << LOGNS, T = FFT::T, PPC = rows_per_cta<LOGNS>(), K = NS / 2;
   extern __shared__ float2 sm[];
@@ -348,6 +356,7 @@ struct AdjSpreadArgs {
   float2* Ax;
   float2* partials;
   int* err;
+  const int* skip;  // the launch does nothing while *skip != 0 (may be null)
   int G, ldq, ldh, tiles_x, ext_rows;
   KBPoly poly;
 };
@@ -363,6 +372,7 @@ constexpr int kRLd = kRRows + 2;                    // 44 complex per row (bank 
 // Rounds are applied in their fixed plan order, hence every output element
 // receives its contributions in the same order on every run.
 __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
+  if (a.skip && *a.skip) return;
   __shared__ __align__(16) float2 acc[kRRows * kRLd];
   const int lane = threadIdx.x;
   const int4 it = a.items[blockIdx.x];
@@ -444,7 +454,8 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
 // 7. fixed-order sum of the partial tiles of split tiles (slot order q = 0, 1, ...)
 __global__ void __launch_bounds__(CPCT_TILE * CPCT_TILE)
     k_adj_reduce(const int4* __restrict__ split, const float2* __restrict__ partials, float2* __restrict__ Ax,
-                 int tiles_x, int ldh, int ext_rows) {
+                 int tiles_x, int ldh, int ext_rows, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int4 sp = split[blockIdx.x];
   const int TC = (sp.x % tiles_x) * CPCT_TILE, TR = (sp.x / tiles_x) * CPCT_TILE;
   const int i = threadIdx.x;
@@ -472,7 +483,9 @@ __device__ __forceinline__ float2 wrapped(const float2* __restrict__ row, int a,
 
 template <int LOGG>
 __global__ void __launch_bounds__(kThreads)
-    k_adj_row(const float2* __restrict__ Ax, float2* __restrict__ H1, const float2* __restrict__ tw, int ldh) {
+    k_adj_row(const float2* __restrict__ Ax, float2* __restrict__ H1, const float2* __restrict__ tw, int ldh,
+              const int* __restrict__ skip) {
+  if (skip && *skip) return;
   // only X = -N/2 .. N/2-1 is kept: the FFT skips the other outputs (POUT)
   using FFT = SmemFFT<LOGG, kErow, +1, false, true>;
   constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = rows_per_cta<LOGG>();
@@ -507,7 +520,8 @@ __global__ void __launch_bounds__(kThreads)
 template <int LOGG>
 __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
     k_adj_col(const float2* __restrict__ H1, const float* __restrict__ dp, float* __restrict__ img,
-              const float2* __restrict__ tw) {
+              const float2* __restrict__ tw, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   // only Y = -N/2 .. N/2-1 is kept: the FFT skips the other outputs (POUT)
   using FFT = SmemFFT<LOGG, kEcol, +1, false, true>;
   constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kEcol;
@@ -570,42 +584,42 @@ int set_attr_Ns() {
 }
 
 template <int LOGG>
-void launch_fwd_G(cpct_plan* p, const float* img, cudaStream_t s) {
+void launch_fwd_G(cpct_plan* p, const float* img, const int* skip, cudaStream_t s) {
   constexpr int G = 1 << LOGG;
   cpct_prof_begin(p, KID_FWD_COL, s);
-  k_fwd_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kEcol, fft_smem<LOGG>(kColFFTs), s>>>(img, p->d_deapod, p->d_H1, p->d_twG);
+  k_fwd_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kEcol, fft_smem<LOGG>(kColFFTs), s>>>(img, p->d_deapod, p->d_H1, p->d_twG, skip);
   cpct_prof_end(p, KID_FWD_COL, s);
   constexpr int RPC = rows_per_cta<LOGG>();
   cpct_prof_begin(p, KID_FWD_ROW, s);
-  k_fwd_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kErow), fft_smem<LOGG>(RPC), s>>>(p->d_H1, p->d_Hx, p->d_twG, p->ldh);
+  k_fwd_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kErow), fft_smem<LOGG>(RPC), s>>>(p->d_H1, p->d_Hx, p->d_twG, p->ldh, skip);
   cpct_prof_end(p, KID_FWD_ROW, s);
 }
 template <int LOGNS>
-void launch_fwd_Ns(cpct_plan* p, float* sino, cudaStream_t s) {
+void launch_fwd_Ns(cpct_plan* p, float* sino, const int* skip, cudaStream_t s) {
   constexpr int NS = 1 << LOGNS, PPC = rows_per_cta<LOGNS>();
   const int pairs = (p->m + 1) / 2;
   cpct_prof_begin(p, KID_FWD_RAY, s);
-  k_fwd_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kErow), fft_smem<LOGNS>(PPC), s>>>(p->d_Q, sino, p->d_twNs, p->m, p->ldq);
+  k_fwd_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kErow), fft_smem<LOGNS>(PPC), s>>>(p->d_Q, sino, p->d_twNs, p->m, p->ldq, skip);
   cpct_prof_end(p, KID_FWD_RAY, s);
 }
 template <int LOGNS>
-void launch_adj_Ns(cpct_plan* p, const float* sino, float ramp, cudaStream_t s) {
+void launch_adj_Ns(cpct_plan* p, const float* sino, float ramp, const int* skip, cudaStream_t s) {
   constexpr int NS = 1 << LOGNS, PPC = rows_per_cta<LOGNS>();
   const int pairs = (p->m + 1) / 2;
   cpct_prof_begin(p, KID_ADJ_RAY, s);
   k_adj_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kErow), fft_smem<LOGNS>(PPC), s>>>(sino, p->d_Q, p->d_twNs, p->m,
-                                                                                           p->ldq, ramp);
+                                                                                           p->ldq, ramp, skip);
   cpct_prof_end(p, KID_ADJ_RAY, s);
 }
 template <int LOGG>
-void launch_adj_G(cpct_plan* p, float* img, cudaStream_t s) {
+void launch_adj_G(cpct_plan* p, float* img, const int* skip, cudaStream_t s) {
   constexpr int G = 1 << LOGG;
   constexpr int RPC = rows_per_cta<LOGG>();
   cpct_prof_begin(p, KID_ADJ_ROW, s);
-  k_adj_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kErow), fft_smem<LOGG>(RPC), s>>>(p->d_Ax, p->d_H1, p->d_twG, p->ldh);
+  k_adj_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kErow), fft_smem<LOGG>(RPC), s>>>(p->d_Ax, p->d_H1, p->d_twG, p->ldh, skip);
   cpct_prof_end(p, KID_ADJ_ROW, s);
   cpct_prof_begin(p, KID_ADJ_COL, s);
-  k_adj_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kEcol, fft_smem<LOGG>(kColFFTs), s>>>(p->d_H1, p->d_deapod, img, p->d_twG);
+  k_adj_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kEcol, fft_smem<LOGG>(kColFFTs), s>>>(p->d_H1, p->d_deapod, img, p->d_twG, skip);
   cpct_prof_end(p, KID_ADJ_COL, s);
 }
 
@@ -648,7 +662,11 @@ int cpct_radon_setup_attributes(int logG, int logNs) {
 }
 
 int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_t s) {
-#define FG(L) launch_fwd_G<L>(p, d_img, s)
+  return cpct_launch_fwd_skip(p, d_img, d_sino, nullptr, s);
+}
+
+int cpct_launch_fwd_skip(cpct_plan* p, const float* d_img, float* d_sino, const int* skip, cudaStream_t s) {
+#define FG(L) launch_fwd_G<L>(p, d_img, skip, s)
   CPCT_DISPATCH_G(p->logG, FG);
 #undef FG
   FwdInterpArgs a;
@@ -663,6 +681,7 @@ int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_
   a.ldh = p->ldh;
   a.tiles_x = p->tiles_x_fwd;
   a.poly = p->poly;
+  a.skip = skip;
   if (p->n_fwd_items > 0) {
     cpct_prof_begin(p, KID_FWD_INTERP, s);
     if (p->fwd_interp_grid <= 0) {
@@ -677,18 +696,19 @@ int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_
     k_fwd_interp<<<grid, kInterpThreads, 0, s>>>(p->tmap_Hx, a, p->n_fwd_items);
     cpct_prof_end(p, KID_FWD_INTERP, s);
   }
-#define FN(L) launch_fwd_Ns<L>(p, d_sino, s)
+#define FN(L) launch_fwd_Ns<L>(p, d_sino, skip, s)
   CPCT_DISPATCH_NS(p->logNs, FN);
 #undef FN
   return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
 }
 
 int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_t s) {
-  return cpct_launch_adj_ramp(p, d_sino, d_img, 0.f, s);
+  return cpct_launch_adj_ramp(p, d_sino, d_img, 0.f, nullptr, s);
 }
 
-int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float ramp, cudaStream_t s) {
-#define AN(L) launch_adj_Ns<L>(p, d_sino, ramp, s)
+int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float ramp, const int* skip,
+                         cudaStream_t s) {
+#define AN(L) launch_adj_Ns<L>(p, d_sino, ramp, skip, s)
   CPCT_DISPATCH_NS(p->logNs, AN);
 #undef AN
   AdjSpreadArgs a;
@@ -705,6 +725,7 @@ int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float 
   a.tiles_x = p->tiles_x_adj;
   a.ext_rows = p->ext_rows;
   a.poly = p->poly;
+  a.skip = skip;
   if (p->n_adj_items > 0) {
     cpct_prof_begin(p, KID_ADJ_SPREAD, s);
     k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
@@ -713,11 +734,11 @@ int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float 
   if (p->n_split > 0) {
     cpct_prof_begin(p, KID_ADJ_REDUCE, s);
     k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, p->d_partials, p->d_Ax, p->tiles_x_adj,
-                                                             p->ldh, p->ext_rows);
+                                                             p->ldh, p->ext_rows, skip);
     cpct_prof_end(p, KID_ADJ_REDUCE, s);
   }
 
-#define AG(L) launch_adj_G<L>(p, d_img, s)
+#define AG(L) launch_adj_G<L>(p, d_img, skip, s)
   CPCT_DISPATCH_G(p->logG, AG);
 #undef AG
   return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
@@ -771,7 +792,7 @@ extern "C" int radon_adj_noalloc(cpct_plan* p, const float* d_sino, float* d_img
   int status = CPCT_OK;
   float2* partials = noalloc_scratch(&status);
   if (!partials) return status;
-#define AN(L) launch_adj_Ns<L>(p, d_sino, 0.f, s)
+#define AN(L) launch_adj_Ns<L>(p, d_sino, 0.f, nullptr, s)
   CPCT_DISPATCH_NS(p->logNs, AN);
 #undef AN
   AdjSpreadArgs a;
@@ -788,13 +809,14 @@ extern "C" int radon_adj_noalloc(cpct_plan* p, const float* d_sino, float* d_img
   a.tiles_x = p->tiles_x_adj;
   a.ext_rows = p->ext_rows;
   a.poly = p->poly;
+  a.skip = nullptr;
   // every partial tile is written in full by its work item before the reduce
   // reads it, so the array needs no clearing between calls
   if (p->n_adj_items > 0) k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
   if (p->n_split > 0)
     k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, partials, p->d_Ax, p->tiles_x_adj, p->ldh,
-                                                             p->ext_rows);
-#define AG(L) launch_adj_G<L>(p, d_img, s)
+                                                             p->ext_rows, nullptr);
+#define AG(L) launch_adj_G<L>(p, d_img, nullptr, s)
   CPCT_DISPATCH_G(p->logG, AG);
 #undef AG
   return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;

@@ -239,6 +239,9 @@ struct SpgState {
   double ft, gtd, dn2, dinf, rtb_t;
   // counters / status
   int iter, n_line, status, done, ticks, n_trials, stationary, n_stationary;
+  // the tick's adjoint operator is skipped (its output unused) while set:
+  // no gradient update, or the slice is done
+  int skip_adj, pad2;
 };
 
 // SPGL1 status codes (spgl1_info.status)
@@ -656,6 +659,7 @@ __global__ void __launch_bounds__(kRB) k_spg_mid(SpgVec V) {
     if (!isfinite(st->ft) || !isfinite(st->gtd)) {
       st->status = S_NONFINITE;
       st->done = 1;
+      st->skip_adj = 1;
       return;
     }
   }
@@ -676,6 +680,7 @@ __global__ void __launch_bounds__(kRB) k_spg_mid(SpgVec V) {
     }
     if (acc) st->accept_x = st->accept_r = st->update_g = 1;
   }
+  st->skip_adj = st->update_g ? 0 : 1;
 }
 
 // end-of-tick controller: Barzilai-Borwein step, history, next tick
@@ -721,6 +726,7 @@ __global__ void __launch_bounds__(kRB) k_spg_end(SpgVec V) {
       if (st->line_fail) {
         st->status = S_LINE;
         st->done = 1;
+        st->skip_adj = 1;
         break;
       }
       if (st->stationary) {
@@ -730,6 +736,7 @@ __global__ void __launch_bounds__(kRB) k_spg_end(SpgVec V) {
         if (++st->n_stationary > 3) {
           st->status = S_LINE;
           st->done = 1;
+        st->skip_adj = 1;
           break;
         }
         spg_check(st);
@@ -822,7 +829,7 @@ void enqueue_tick(SliceWork& w, int filter) {
     k_spg_radix_select<<<1, kRB, 0, s>>>(V, pass);
   }
   k_spg_proj_apply<<<kRG, kRB, 0, s>>>(V);
-  cpct_launch_fwd(w.plan, V.xt, V.y, s);
+  cpct_launch_fwd_skip(w.plan, V.xt, V.y, &V.st->done, s);
   if (filter) {
     k_ring_colmean<<<(w.plan->ns + 31) / 32, kRB, 0, s>>>(V.y, w.ring.m, w.plan->m, w.plan->ns);
     k_ring_offset<<<1, kRB, 0, s>>>(w.ring.Q, w.ring.m, w.ring.d, w.plan->ns);
@@ -830,7 +837,7 @@ void enqueue_tick(SliceWork& w, int filter) {
   k_spg_resid<<<kRG, kRB, 0, s>>>(V, w.ring.d, w.plan->ns, filter);
   k_spg_mid<<<1, kRB, 0, s>>>(V);
   k_spg_accept<<<kRG, kRB, 0, s>>>(V);
-  cpct_launch_adj(w.plan, V.r, V.gtmp, s);
+  cpct_launch_adj_ramp(w.plan, V.r, V.gtmp, 0.f, &V.st->skip_adj, s);
   k_spg_grad<<<kRG, kRB, 0, s>>>(V);
   k_spg_end<<<1, kRB, 0, s>>>(V);
 }
