@@ -310,8 +310,11 @@ int cpct_unet_backward(cpct_unet* net, const float* d_in, const float* d_target,
                        cudaStream_t stream);
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the
- * gradients of the last backward pass; refreshes the BF16 weights. */
-int cpct_unet_adam_step(cpct_unet* net, float lr, cudaStream_t stream);
+ * gradients of the last backward pass, scaled by min(1, max_grad_norm /
+ * ||g||_2) when max_grad_norm > 0 (no clipping when 0); refreshes the BF16
+ * weights.  grad_norm (host, may be NULL) receives ||g||_2 before clipping,
+ * and then the call synchronizes `stream`. */
+int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm, double* grad_norm, cudaStream_t stream);
 
 /* One denoiser operation on caller tensors, for tests (B images, channels
  * fastest, device float32; H x W is the size of a for ops 0, 1, 2, 5 and

@@ -458,7 +458,7 @@ def _unet_setup():
         getattr(L, name).argtypes = [vp, vp, vp]
     L.cpct_unet_forward.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     L.cpct_unet_backward.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
-    L.cpct_unet_adam_step.argtypes = [vp, ctypes.c_float, vp]
+    L.cpct_unet_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_double), vp]
     return L
 
 
@@ -533,9 +533,14 @@ class UNet:
                                                B, ctypes.byref(loss), _stream(torch, stream)), "cpct_unet_backward")
         return loss.value
 
-    def adam_step(self, lr, stream=None):
-        check(_unet_setup().cpct_unet_adam_step(self.handle, float(lr), _stream(self._torch, stream)),
-              "cpct_unet_adam_step")
+    def adam_step(self, lr, max_grad_norm=0.0, return_norm=False, stream=None):
+        """One Adam step; gradients clipped to max_grad_norm (0: none).
+        Returns the gradient norm before clipping when return_norm is set."""
+        nrm = ctypes.c_double()
+        check(_unet_setup().cpct_unet_adam_step(self.handle, float(lr), float(max_grad_norm),
+                                                ctypes.byref(nrm) if return_norm else None,
+                                                _stream(self._torch, stream)), "cpct_unet_adam_step")
+        return nrm.value if return_norm else None
 
 
 def unet_debug_op(op, a, b, out_shape, w=None, C1=None, C2=0, Cout=0, stream=None):

@@ -617,12 +617,42 @@ __global__ void __launch_bounds__(kEW) k_head_wgrad(const float* __restrict__ g,
   }
 }
 
-// Adam on the FP32 master parameters (bias-corrected step size lr_t)
+// squared L2 norm of the gradient: FP32 per thread and warp, FP64 per block
+__global__ void __launch_bounds__(kEW) k_sumsq(const float* __restrict__ g, long long n, double* __restrict__ part) {
+  __shared__ double sh[kEW / 32];
+  float s = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fmaf(g[i], g[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kEW / 32; ++i) t += sh[i];
+    part[blockIdx.x] = t;
+  }
+}
+
+// gradient scale min(1, max_norm / ||g||) (max_norm <= 0: 1) from the block
+// partials in a fixed order; also stores ||g||
+__global__ void k_clip_scale(const double* __restrict__ part, int nb, float max_norm, float* __restrict__ scale,
+                             double* __restrict__ norm) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0.0;
+  for (int i = 0; i < nb; ++i) t += part[i];
+  const double nrm = sqrt(t);
+  *norm = nrm;
+  *scale = (max_norm > 0.f && nrm > (double)max_norm) ? (float)((double)max_norm / nrm) : 1.f;
+}
+
+// Adam on the FP32 master parameters (bias-corrected step size lr_t), the
+// gradient multiplied by *gscale
 __global__ void __launch_bounds__(kEW) k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                                               float* __restrict__ v, long long n, float lr_t, float b1, float b2,
-                                              float eps) {
+                                              float eps, const float* __restrict__ gscale) {
+  const float sc = *gscale;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float gi = g[i];
+    const float gi = g[i] * sc;
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
@@ -679,6 +709,9 @@ struct Net {
   float* part = nullptr;        // split partials
   size_t part_floats = 0;
   double* loss_part = nullptr;
+  double* norm_part = nullptr;   // gradient-norm block partials
+  double* d_gnorm = nullptr;     // ||g|| of the last Adam step
+  float* d_gscale = nullptr;     // clipping factor of the last Adam step
   int last_batch = 0;
 };
 
@@ -1016,7 +1049,8 @@ extern "C" int cpct_unet_create(cpct_unet** out, int levels, int base, int max_b
   n->g_skip.assign(L, nullptr);
   const size_t P0 = (size_t)max_batch * height * width;
   ok = ok && dalloc(*n, &n->X0, P0 * 32) && dalloc(*n, &n->out, P0) && dalloc(*n, &n->g_out, P0) &&
-       dalloc(*n, &n->loss_part, 1024);
+       dalloc(*n, &n->loss_part, 1024) && dalloc(*n, &n->norm_part, 152 * 16) && dalloc(*n, &n->d_gnorm, 1) &&
+       dalloc(*n, &n->d_gscale, 1);
   for (int l = 0; l < L && ok; ++l) {
     const size_t Pl = P0 >> (2 * l), cl = n->c[l];
     ok = dalloc(*n, &n->ea[l], Pl * cl) && dalloc(*n, &n->eb[l], Pl * cl) && dalloc(*n, &n->g_ea[l], Pl * cl) &&
@@ -1166,16 +1200,26 @@ extern "C" int cpct_unet_backward(cpct_unet* net, const float* d_in, const float
   return CPCT_OK;
 }
 
-extern "C" int cpct_unet_adam_step(cpct_unet* net, float lr, cudaStream_t stream) {
-  if (!net || !(lr > 0.f)) return CPCT_EINVAL;
+extern "C" int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm, double* grad_norm,
+                                   cudaStream_t stream) {
+  if (!net || !(lr > 0.f) || !(max_grad_norm >= 0.f)) return CPCT_EINVAL;
   Net& n = *net->net;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   n.adam_t++;
   const double lr_t = lr * std::sqrt(1.0 - std::pow((double)b2, n.adam_t)) / (1.0 - std::pow((double)b1, n.adam_t));
-  k_adam<<<grid_for((long long)n.n_param), kEW, 0, stream>>>(n.param, n.grad, n.adam_m, n.adam_v, (long long)n.n_param,
-                                                             (float)lr_t, b1, b2, eps);
+  const int nb = grid_for((long long)n.n_param);
+  k_sumsq<<<nb, kEW, 0, stream>>>(n.grad, (long long)n.n_param, n.norm_part);
+  k_clip_scale<<<1, 32, 0, stream>>>(n.norm_part, nb, max_grad_norm, n.d_gscale, n.d_gnorm);
+  k_adam<<<nb, kEW, 0, stream>>>(n.param, n.grad, n.adam_m, n.adam_v, (long long)n.n_param, (float)lr_t, b1, b2,
+                                 eps, n.d_gscale);
   refresh_bf16(n, stream);
-  return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return CPCT_ECUDA;
+  if (grad_norm) {
+    if (cudaMemcpyAsync(grad_norm, n.d_gnorm, sizeof(double), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      return CPCT_ECUDA;
+  }
+  return CPCT_OK;
 }
 
 // One network operation on caller tensors (NHWC, device float32), for tests:

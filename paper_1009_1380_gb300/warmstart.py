@@ -109,14 +109,30 @@ def scales(fbp):
     return fbp.flatten(1).std(dim=1).clamp_min(1e-12)
 
 
+CLIP_FACTOR = 2.0      # clip at twice the median of the recent gradient norms
+CLIP_WINDOW = 50
+DIVERGE_FACTOR = 1.5   # an epoch loss this far above the best restores the best weights
+
+
 def train(net, fbp, target, epochs, batch, lr, seed=0, log=None):
-    """Adam on (FBP / s, x / s) pairs; returns the per-epoch mean losses."""
+    """Adam on (FBP / s, x / s) pairs; returns the per-epoch mean losses.
+
+    Safeguards for a network without normalisation layers: cosine decay of
+    the learning rate to 5% over all steps; gradients clipped to twice the
+    median norm of the last 50 steps (after 20 steps); the weights of the best
+    epoch are kept, and an epoch whose loss exceeds 1.5x the best restores
+    them and halves the learning rate."""
     torch = net._torch
     s = scales(fbp)[:, None, None]
     inp, tgt = (fbp / s).contiguous(), (target / s).contiguous()
     rng = np.random.default_rng(seed)
     count = fbp.shape[0]
-    losses = []
+    steps_per_epoch = max(1, count // batch)
+    total = epochs * steps_per_epoch
+    losses, norms = [], []
+    best_loss, best_params = float("inf"), None
+    scale_lr = 1.0
+    step = 0
     for ep in range(epochs):
         perm = rng.permutation(count)
         tot, nb = 0.0, 0
@@ -124,11 +140,23 @@ def train(net, fbp, target, epochs, batch, lr, seed=0, log=None):
             idx = torch.from_numpy(perm[g:g + batch]).cuda()
             xb, tb = inp.index_select(0, idx).contiguous(), tgt.index_select(0, idx).contiguous()
             tot += net.backward(xb, tb)
-            net.adam_step(lr)
+            lr_t = scale_lr * lr * (0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * step / total)))
+            clip = CLIP_FACTOR * float(np.median(norms[-CLIP_WINDOW:])) if len(norms) >= 20 else 0.0
+            norms.append(net.adam_step(lr_t, max_grad_norm=clip, return_norm=True))
             nb += 1
+            step += 1
         losses.append(tot / max(nb, 1))
         if log:
             log(f"epoch {ep}: loss {losses[-1]:.4e}")
+        if losses[-1] < best_loss:
+            best_loss, best_params = losses[-1], net.get_params()
+        elif losses[-1] > DIVERGE_FACTOR * best_loss and best_params is not None:
+            net.set_params(best_params)
+            scale_lr *= 0.5
+            if log:
+                log(f"epoch {ep}: loss above {DIVERGE_FACTOR}x the best, weights restored, learning rate halved")
+    if best_params is not None and losses[-1] > best_loss:
+        net.set_params(best_params)
     return losses
 
 

@@ -112,9 +112,13 @@ def test_unet_training_reduces_loss(torch_cuda):
     x = (t + 0.5 * rng.standard_normal((B, H, W))).astype(np.float32)
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     l0 = net.backward(xd, td)
+    # the reported norm is the 2-norm of the gradients of the last backward
+    g = net.get_grads()
+    nrm = net.adam_step(1e-3, return_norm=True)
+    assert abs(nrm - np.linalg.norm(g.astype(np.float64))) <= 1e-5 * nrm
     for _ in range(30):
         net.backward(xd, td)
-        net.adam_step(1e-3)
+        net.adam_step(1e-3, max_grad_norm=0.5 * nrm)
     l1 = net.backward(xd, td)
     print("loss", l0, "->", l1)
     assert l1 < 0.5 * l0
