@@ -258,6 +258,12 @@ int spgl1_solve_batched(cpct_plan* const* plans, int batch, const float* const* 
  * the call and synchronizes `stream`. */
 int cpct_project_l1(const float* d_v, long long n, double tau, float* d_out, double* theta, cudaStream_t stream);
 
+/* The same for `batch` vectors of n values each (host arrays of device
+ * pointers d_v / d_out, radii tau, thresholds theta (may be NULL)), one
+ * workspace and one synchronization for all of them. */
+int cpct_project_l1_batched(const float* const* d_v, int batch, long long n, const double* tau,
+                            float* const* d_out, double* theta, cudaStream_t stream);
+
 /* ---- learned warm start: convolutional denoiser (no counterpart in the
  * paper; the network maps a filtered back-projection to a starting point of
  * spgl1_solve) ------------------------------------------------------------ */

@@ -288,7 +288,30 @@ def _spgl1_setup():
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vp),
                                       ctypes.POINTER(Spgl1Opts), ctypes.POINTER(Spgl1Info), vp]
     L.cpct_project_l1.argtypes = [vp, ctypes.c_longlong, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.cpct_project_l1_batched.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_longlong,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vp),
+                                          ctypes.POINTER(ctypes.c_double), vp]
     return L
+
+
+def project_l1_batched(vs, taus, outs=None, stream=None):
+    """Projections of equally sized float32 CUDA tensors onto l1 balls of the
+    given radii; returns (outs, thetas)."""
+    import torch
+    L = _spgl1_setup()
+    B = len(vs)
+    if outs is None:
+        outs = [torch.empty_like(v) for v in vs]
+    n = vs[0].numel()
+    for v, o in zip(vs, outs):
+        _dev_ptr(v, tuple(vs[0].shape), torch)
+        _dev_ptr(o, tuple(vs[0].shape), torch)
+    V = (ctypes.c_void_p * B)(*[v.data_ptr() for v in vs])
+    O = (ctypes.c_void_p * B)(*[o.data_ptr() for o in outs])
+    T = (ctypes.c_double * B)(*[float(t) for t in taus])
+    th = (ctypes.c_double * B)()
+    check(L.cpct_project_l1_batched(V, B, n, T, O, th, _stream(torch, stream)), "cpct_project_l1_batched")
+    return outs, list(th)
 
 
 def project_l1(v, tau, out=None, stream=None):

@@ -461,8 +461,16 @@ __global__ void __launch_bounds__(CPCT_TILE * CPCT_TILE)
   const int i = threadIdx.x;
   const float2* src = partials + (size_t)sp.y * CPCT_TILE * CPCT_TILE + i;
   constexpr size_t S = CPCT_TILE * CPCT_TILE;
+  // 16 independent loads in flight, summed in slot order
   float2 sum = make_float2(0.f, 0.f);
   int q = 0;
+  for (; q + 16 <= sp.z; q += 16) {
+    float2 v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = src[(size_t)(q + k) * S];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sum = cadd(sum, v[k]);
+  }
   for (; q + 4 <= sp.z; q += 4) {
     const float2 v0 = src[(q + 0) * S], v1 = src[(q + 1) * S], v2 = src[(q + 2) * S], v3 = src[(q + 3) * S];
     sum = cadd(cadd(cadd(cadd(sum, v0), v1), v2), v3);

@@ -1056,44 +1056,60 @@ extern "C" int spgl1_solve(cpct_plan* plan, const float* d_b, double sigma, floa
   return spgl1_solve_batched(&plan, 1, &d_b, &sigma, &d_x, opts, info, stream);
 }
 
-extern "C" int cpct_project_l1(const float* d_v, long long n, double tau, float* d_out, double* theta,
-                               cudaStream_t stream) {
-  if (!d_v || !d_out || n < 1 || n > (1LL << 30) || !std::isfinite(tau)) return CPCT_EINVAL;
-  // workspace: state, partials of the apply kernel, histogram
+extern "C" int cpct_project_l1_batched(const float* const* d_v, int batch, long long n, const double* tau,
+                                       float* const* d_out, double* theta, cudaStream_t stream) {
+  if (!d_v || !d_out || !tau || batch < 1 || n < 1 || n > (1LL << 30)) return CPCT_EINVAL;
+  for (int i = 0; i < batch; ++i)
+    if (!d_v[i] || !d_out[i] || !std::isfinite(tau[i])) return CPCT_EINVAL;
+  // workspace per vector: state, partials of the apply kernel, histogram
   const size_t b_state = (sizeof(SpgState) + 255) / 256 * 256;
   const size_t b_part = sizeof(double) * P_TOTAL * kRG;
-  const size_t b_cnt = sizeof(unsigned) * kBins;
+  const size_t b_hist = (sizeof(unsigned) + sizeof(unsigned long long)) * kBins;
+  const size_t b_one = b_state + b_part + b_hist;
   unsigned char* mem = nullptr;
-  if (cudaMalloc(&mem, b_state + b_part + b_cnt + sizeof(unsigned long long) * kBins) != cudaSuccess)
-    return CPCT_ENOMEM;
-  SpgState st;
-  std::memset(&st, 0, sizeof(st));
-  st.tau = tau;  // ps = 0: v = x - 0 * g = x
-  SpgVec V{};
-  V.x = const_cast<float*>(d_v);
-  V.g = const_cast<float*>(d_v);
-  V.xt = d_out;
-  V.n = n;
-  V.st = reinterpret_cast<SpgState*>(mem);
-  V.part = reinterpret_cast<double*>(mem + b_state);
-  V.hcnt = reinterpret_cast<unsigned*>(mem + b_state + b_part);
-  V.hsum = reinterpret_cast<unsigned long long*>(mem + b_state + b_part + b_cnt);
+  if (cudaMalloc(&mem, b_one * batch) != cudaSuccess) return CPCT_ENOMEM;
+  std::vector<SpgState> st(batch);
   int rc = CPCT_OK;
-  if (cudaMemcpyAsync(V.st, &st, sizeof(st), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemsetAsync(V.hcnt, 0, b_cnt + sizeof(unsigned long long) * kBins, stream) != cudaSuccess)
-    rc = CPCT_ECUDA;
-  if (rc == CPCT_OK) {
+  for (int i = 0; i < batch && rc == CPCT_OK; ++i) {
+    std::memset(&st[i], 0, sizeof(SpgState));
+    st[i].tau = tau[i];  // ps = 0: v = x - 0 * g = x
+  }
+  // the states, then zeroed histograms, in two copies
+  std::vector<unsigned char> init(b_one * batch, 0);
+  for (int i = 0; i < batch; ++i) std::memcpy(init.data() + b_one * i, &st[i], sizeof(SpgState));
+  if (cudaMemcpyAsync(mem, init.data(), init.size(), cudaMemcpyHostToDevice, stream) != cudaSuccess) rc = CPCT_ECUDA;
+  for (int i = 0; i < batch && rc == CPCT_OK; ++i) {
+    unsigned char* w = mem + b_one * i;
+    SpgVec V{};
+    V.x = const_cast<float*>(d_v[i]);
+    V.g = const_cast<float*>(d_v[i]);
+    V.xt = d_out[i];
+    V.n = n;
+    V.st = reinterpret_cast<SpgState*>(w);
+    V.part = reinterpret_cast<double*>(w + b_state);
+    V.hcnt = reinterpret_cast<unsigned*>(w + b_state + b_part);
+    V.hsum = reinterpret_cast<unsigned long long*>(w + b_state + b_part + sizeof(unsigned) * kBins);
     for (int pass = 0; pass < kRadixPasses; ++pass) {
       k_spg_radix_hist<<<kRG, kRB, 0, stream>>>(V, pass);
       k_spg_radix_select<<<1, kRB, 0, stream>>>(V, pass);
     }
     k_spg_proj_apply<<<kRG, kRB, 0, stream>>>(V);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(&st, V.st, sizeof(st), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-        cudaStreamSynchronize(stream) != cudaSuccess)
-      rc = CPCT_ECUDA;
   }
+  if (rc == CPCT_OK && cudaGetLastError() != cudaSuccess) rc = CPCT_ECUDA;
+  if (rc == CPCT_OK && theta) {
+    for (int i = 0; i < batch && rc == CPCT_OK; ++i)
+      if (cudaMemcpyAsync(&st[i], mem + b_one * i, sizeof(SpgState), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        rc = CPCT_ECUDA;
+  }
+  if (cudaStreamSynchronize(stream) != cudaSuccess && rc == CPCT_OK) rc = CPCT_ECUDA;
   cudaFree(mem);
-  if (rc == CPCT_OK && theta) *theta = st.proj_zero ? 0.0 : st.theta;
+  if (rc == CPCT_OK && theta)
+    for (int i = 0; i < batch; ++i) theta[i] = st[i].proj_zero ? 0.0 : st[i].theta;
   return rc;
+}
+
+extern "C" int cpct_project_l1(const float* d_v, long long n, double tau, float* d_out, double* theta,
+                               cudaStream_t stream) {
+  if (!d_v || !d_out) return CPCT_EINVAL;
+  return cpct_project_l1_batched(&d_v, 1, n, &tau, &d_out, theta, stream);
 }

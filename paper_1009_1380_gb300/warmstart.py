@@ -201,8 +201,8 @@ def project_start(x_hat, cal):
     projection per slice)."""
     x0 = torch_empty_like(x_hat)
     tau0 = cal["kappa"] * _soft_l1(x_hat, cal["theta"])
-    for i in range(x_hat.shape[0]):
-        cpct.project_l1(x_hat[i].reshape(-1), float(tau0[i]), out=x0[i].reshape(-1))
+    cpct.project_l1_batched([x_hat[i] for i in range(x_hat.shape[0])], tau0,
+                            outs=[x0[i] for i in range(x_hat.shape[0])])
     return x0
 
 
@@ -224,6 +224,8 @@ def evaluate(net, plans, b, sigma, fbp, opts, batch, kappa):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         x_hat = fbp if name == "fbp" else predict(net, fbp, batch)
+        torch.cuda.synchronize()
+        t_pred = time.perf_counter() - t0
         x0 = project_start(x_hat, kappa[name])
         torch.cuda.synchronize()
         t_net = time.perf_counter() - t0
@@ -236,6 +238,7 @@ def evaluate(net, plans, b, sigma, fbp, opts, batch, kappa):
             for j, i in enumerate(bad):
                 inf[i] = dict(inf_fb[j], fallback=True)
         r = _summary(inf, t + t_fb + t_net, t_net)
+        r["predict_s"] = t_pred
         r["fallbacks"] = len(bad)
         # quality of the start: relative L2 distance to the cold solution
         d0 = (x0 - x_cold).flatten(1).norm(dim=1) / x_cold.flatten(1).norm(dim=1).clamp_min(1e-30)

@@ -186,3 +186,15 @@ def test_project_l1_matches_oracle(torch_cuda, case):
     assert np.all(np.sign(o[o != 0]) == np.sign(v64[o != 0]))
     # ||out||_1 = tau to FP32 rounding of the outputs
     assert abs(np.abs(o).sum() - tau) <= 1e-6 * tau
+
+
+def test_project_l1_batched_equals_single(torch_cuda):
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    rng = np.random.default_rng(77)
+    vs = [torch.from_numpy(rng.standard_normal(5000).astype(np.float32)).cuda() for _ in range(5)]
+    taus = [0.0, 10.0, 100.0, 1e6, 3.5]
+    outs, th = cpct.project_l1_batched(vs, taus)
+    for v, t, o, h in zip(vs, taus, outs, th):
+        o1, h1 = cpct.project_l1(v, t)
+        assert torch.equal(o, o1) and h == h1
