@@ -100,9 +100,14 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+// FP32 staging rows of 32 channels padded to 36 floats (144 B): rows start 4
+// banks apart, so the conversion's 16-byte reads of 8 threads (4 rows x 2
+// halves) fall in 32 distinct banks
+constexpr int kAfLd = kBK + 4;
+
 template <int BN>
 constexpr size_t conv_smem() {
-  return (size_t)kStages * (kBM * kBK * 4 + BN * kBK * 2) + kBM * kBK * 2;
+  return (size_t)kStages * (kBM * kAfLd * 4 + BN * kBK * 2) + kBM * kBK * 2;
 }
 
 // Implicit-GEMM 3x3 convolution (zero padding 1): M = B*H*W pixels, N = Cout,
@@ -116,8 +121,8 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
   constexpr int WN = BN / 2;        // warp tile N (32 or 16)
   constexpr int NT = WN / 8;        // n8 tiles per warp
   extern __shared__ __align__(128) unsigned char smraw[];
-  float* Af = reinterpret_cast<float*>(smraw);                                   // [kStages][kBM * kBK]
-  uint32_t* sB = reinterpret_cast<uint32_t*>(smraw + (size_t)kStages * kBM * kBK * 4);  // [kStages][BN * kBK / 2]
+  float* Af = reinterpret_cast<float*>(smraw);                                     // [kStages][kBM][kAfLd]
+  uint32_t* sB = reinterpret_cast<uint32_t*>(smraw + (size_t)kStages * kBM * kAfLd * 4);  // [kStages][BN * kBK / 2]
   uint32_t* sA = sB + kStages * BN * kBK / 2;                                   // [kBM * kBK / 2]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 3, wn = warp >> 2;
@@ -144,13 +149,13 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
     const float* base = ci0 < a.C1 ? a.x1 : a.x2;
     const int cs = ci0 < a.C1 ? a.C1 : a.C2, co = (ci0 < a.C1 ? ci0 : ci0 - a.C1) + 4 * c16;
-    float* dst = Af + (size_t)st * kBM * kBK;
+    float* dst = Af + (size_t)st * kBM * kAfLd;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int sy = py[i] + dy, sx = px[i] + dx;
       const bool ok = pb[i] >= 0 && sy >= 0 && sy < a.H && sx >= 0 && sx < a.Wd;
       const float* src = ok ? base + (((size_t)pb[i] * a.H + sy) * a.Wd + sx) * cs + co : base;
-      cp_async16_zfill(smem_u32(dst + (r0 + 32 * i) * kBK + 4 * c16), src, ok);
+      cp_async16_zfill(smem_u32(dst + (r0 + 32 * i) * kAfLd + 4 * c16), src, ok);
     }
     if (tid < BN * 4) {
       const int r = tid >> 2, c = tid & 3;
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
   // FP32 chunk -> swizzled BF16 tile: thread -> (row, 16-channel half)
   auto convert = [&](int st) {
     const int row = tid >> 1, half = tid & 1;
-    const float4* src = reinterpret_cast<const float4*>(Af + (size_t)st * kBM * kBK + row * kBK + half * 16);
+    const float4* src = reinterpret_cast<const float4*>(Af + (size_t)st * kBM * kAfLd + row * kAfLd + half * 16);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const float4 u = src[2 * c], v = src[2 * c + 1];
