@@ -87,7 +87,8 @@ def conv(x: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
     for dy in range(k):
         for dx in range(k):
             patch = xp[:, :, dy:dy + H, dx:dx + Wd]              # (B, Ci, H, W)
-            y += np.einsum("oc,bchw->bohw", W[:, dy, dx, :], patch)
+            # sum over ci of W[co, dy, dx, ci] patch[b, ci]  -> (Co, B, H, W)
+            y += np.tensordot(W[:, dy, dx, :], patch, axes=([1], [1])).transpose(1, 0, 2, 3)
     return y + b[None, :, None, None]
 
 
@@ -102,8 +103,9 @@ def conv_backward(x: np.ndarray, W: np.ndarray, gy: np.ndarray):
     for dy in range(k):
         for dx in range(k):
             patch = xp[:, :, dy:dy + H, dx:dx + Wd]
-            gW[:, dy, dx, :] = np.einsum("bohw,bchw->oc", gy, patch)
-            gxp[:, :, dy:dy + H, dx:dx + Wd] += np.einsum("oc,bohw->bchw", W[:, dy, dx, :], gy)
+            # sum over b, p, q of gy[b, co] patch[b, ci]; sum over co of W[co, ci] gy[b, co]
+            gW[:, dy, dx, :] = np.tensordot(gy, patch, axes=([0, 2, 3], [0, 2, 3]))
+            gxp[:, :, dy:dy + H, dx:dx + Wd] += np.tensordot(W[:, dy, dx, :], gy, axes=([0], [1])).transpose(1, 0, 2, 3)
     gx = gxp[:, :, r:r + H, r:r + Wd]
     gb = gy.sum(axis=(0, 2, 3))
     return gx, gW, gb
