@@ -1,0 +1,110 @@
+"""Parity at the full sizes of the benchmark configurations (beyond the
+2048^2 operator test in test_gpu_radon.py), in the launch configurations the
+benchmark and the warm-start pipeline use:
+
+* batched operators (256 x 1024^2 slices, views 64..512): sampled rays of a
+  few slices of one graph launch against the FP64 gridding oracle;
+* SPGL1 on one 1024^2 / 128-view slice with noise and stuck columns: the
+  root condition and ||x||_1 of the device solution re-evaluated with the
+  FP64 oracle operator and filter;
+* the warm-start denoiser at its full shape (5 levels, 32 base channels) on
+  one 512^2 image against the FP64 oracle with the device's operand rounding.
+"""
+import numpy as np
+import pytest
+
+from oracle import nufft, ring, unet
+from paper_1009_1380_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_1380_gb300 import build
+    build.build()
+    return torch
+
+
+def test_batched_operator_full_size_sampled(torch_cuda):
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    n = 1024
+    views = [64, 512, 128, 256]
+    base = {m: cpct.Plan(n, n, m) for m in sorted(set(views))}
+    plans = [base[m] for m in views]
+    imgs = [synth.phantom("c3_batch1024", slice_index=i) for i in range(len(views))]
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [torch.empty((m, n), device="cuda") for m in views]
+    bt = cpct.Batch(plans, ins, outs, mode=cpct.BATCH_FWD)
+    bt.run()
+    torch.cuda.synchronize()
+    for i, m in enumerate(views):
+        geo = nufft.GridGeometry(n, n, nufft.default_angles(m))
+        rays = np.array([0, 1, m // 3, m // 2, m - 1])
+        ref = nufft.radon_grid(imgs[i].astype(np.float64), geo, rays)
+        e = _rel(outs[i].cpu().numpy().astype(np.float64)[rays], ref)
+        print(f"slice {i} ({m} views): sampled rays rel {e:.2e}")
+        assert e < 1e-5
+    bt.close()
+
+
+def test_spgl1_full_size_root_by_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    c = synth.CONFIGS["c4_spgl1_1024"]
+    n, m = c["n"], c["n_views"]
+    p = cpct.Plan(n, n, m)
+    x_true = synth.phantom("c4_spgl1_1024", slice_index=0)
+    y = p.fwd(torch.from_numpy(x_true).cuda()).cpu().numpy()
+    b, std, _ = synth.corrupt_sinogram(y, synth.rng_for(c["index"], 0))
+    b32 = b.astype(np.float32)
+    sigma = std * np.sqrt(m * n - n + 4)
+    x, info = cpct.spgl1(p, torch.from_numpy(b32).cuda(), sigma, opts=cpct.make_opts(max_iter=600))
+    print(info)
+    assert info["status"] == 1
+    xd = x.cpu().numpy().astype(np.float64)
+    geo = nufft.GridGeometry(n, n, nufft.default_angles(m))
+    bf = ring.ring_filter(b32.astype(np.float64))
+    r = ring.ring_filter(nufft.radon_grid(xd, geo)) - bf
+    rn = float(np.linalg.norm(r))
+    print("oracle ||F(Rx) - F b||", rn, "sigma", sigma, "device", info["rnorm"])
+    # the device's root test (opt_tol 1e-4 of ||F b||) re-evaluated in FP64
+    assert abs(rn - sigma) <= 2e-4 * np.linalg.norm(bf)
+    assert abs(np.abs(xd).sum() - info["xnorm1"]) <= 1e-5 * info["xnorm1"]
+
+
+def test_denoiser_full_shape_512(torch_cuda):
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct, warmstart
+    levels, base, H = 5, 32, 512
+    vec = warmstart.he_init(levels, base, seed=3)
+    rng = np.random.default_rng(4)
+    vec[-1 - 1:-1] = 0.0
+    # a non-zero head so that the output depends on every layer
+    specs = unet.layer_specs(levels, base)
+    nhead = specs[-1][2]
+    vec[-(nhead + 1):-1] = (0.1 * rng.standard_normal(nhead)).astype(np.float32)
+    x = rng.standard_normal((1, H, H)).astype(np.float32)
+    net = cpct.UNet(levels, base, 1, H, H)
+    net.set_params(vec)
+    out = net.forward(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    params, o = {}, 0
+    for name, co, ci, k in specs:
+        nw = co * k * k * ci
+        params[name + ".W"] = vec[o:o + nw].astype(np.float64).reshape(co, k, k, ci)
+        params[name + ".b"] = vec[o + nw:o + nw + co].astype(np.float64)
+        if k == 3:
+            params[name + ".W"] = unet.bf16_round(params[name + ".W"])
+        o += nw + co
+    ref, _ = unet.forward(params, x.astype(np.float64), levels, base, q=unet.bf16_round)
+    e = _rel(out - x, ref - x)
+    print("512^2 5-level denoiser: correction rel", e)
+    assert e < 1e-2
