@@ -340,8 +340,10 @@ int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm, double* g
  *   op 6: weight and bias gradients of op 0's convolution at input a (C1
  *         channels, C2 = 0) and output gradient b (Cout channels, used as
  *         is): y = (Cout, 3, 3, C1) weights then Cout biases (flat)
- * C1, C2 multiples of 32 (C1 > 0), Cout a multiple of 32 for ops 0, 5, 6.
- * Synchronous; allocates a workspace for ops 0, 5 and 6. */
+ *   op 7: op 0 computed by the forward kernel that reads BF16 copies of its
+ *         inputs (the network's forward pass); equals op 0
+ * C1, C2 multiples of 32 (C1 > 0), Cout a multiple of 32 for ops 0, 5, 6, 7.
+ * Synchronous; allocates a workspace for ops 0, 5, 6 and 7. */
 int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, float* d_y, const float* h_w, int B, int H, int W,
                        int C1, int C2, int Cout, cudaStream_t stream);
 

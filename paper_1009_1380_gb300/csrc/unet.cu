@@ -85,6 +85,11 @@ struct ConvArgs {
   // on ReLU outputs as pre-activation gradients)
   const float* om1;
   const float* om2;
+  // forward pass: BF16 copies of the inputs (read instead of x1 / x2 by the
+  // BF16-input kernel) and of the output (written beside y1 if given)
+  const __nv_bfloat16* xb1;
+  const __nv_bfloat16* xb2;
+  __nv_bfloat16* yb1;
   int O1, Cout;
   int relu;                // apply max(., 0) in the epilogue
   int B, H, Wd;            // batch, height, width
@@ -257,6 +262,137 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
           v1 = mv.y > 0.f ? v1 : 0.f;
         }
         *reinterpret_cast<float2*>((first ? a.y1 : a.y2) + off) = make_float2(v0, v1);
+        if (a.yb1 && first) *reinterpret_cast<uint32_t*>(a.yb1 + off) = pack_bf16(v0, v1);
+      }
+    }
+}
+
+constexpr int kStagesB = 4;  // pipeline depth of the BF16-input forward GEMM
+
+template <int BN>
+constexpr size_t conv_smem_b16() {
+  return (size_t)kStagesB * (kBM * kBK * 2 + BN * kBK * 2);
+}
+
+// The forward convolution reading the BF16 copies of its inputs: a 4-stage
+// cp.async pipeline copies the operand tiles (zero-filled outside the image)
+// straight into the swizzled layout that ldmatrix reads; no conversion, one
+// barrier per chunk.  Results equal k_conv3x3's (the same round-to-nearest
+// BF16 operands, the same accumulation order).
+template <int BN>
+__global__ void __launch_bounds__(kCT) k_conv3x3_b16(const ConvArgs a) {
+  constexpr int WN = BN / 2;
+  constexpr int NT = WN / 8;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint32_t* sA = reinterpret_cast<uint32_t*>(smraw);      // [kStagesB][kBM * kBK / 2]
+  uint32_t* sB = sA + kStagesB * kBM * kBK / 2;           // [kStagesB][BN * kBK / 2]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp & 3, wn = warp >> 2;
+  const int HW = a.H * a.Wd, P = a.B * HW;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int Cin = a.C1 + a.C2, cchunks = Cin / kBK, nk = 9 * cchunks;
+  // A copies: 16-byte chunk c (0..3) of rows r0 and r0 + 64
+  const int c = tid & 3, r0 = tid >> 2;
+  int py[2], px[2], pb[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int pm = m0 + r0 + 64 * i;
+    pb[i] = -1;
+    if (pm < P) {
+      pb[i] = pm / HW;
+      const int r = pm - pb[i] * HW;
+      py[i] = r / a.Wd;
+      px[i] = r - py[i] * a.Wd;
+    }
+  }
+  auto load_stage = [&](int kc, int st) {
+    const int tap = kc / cchunks, ci0 = (kc - tap * cchunks) * kBK;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const __nv_bfloat16* base = ci0 < a.C1 ? a.xb1 : a.xb2;
+    const int cs = ci0 < a.C1 ? a.C1 : a.C2, co = (ci0 < a.C1 ? ci0 : ci0 - a.C1) + 8 * c;
+    uint32_t* dA = sA + (size_t)st * kBM * kBK / 2;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int sy = py[i] + dy, sx = px[i] + dx;
+      const bool ok = pb[i] >= 0 && sy >= 0 && sy < a.H && sx >= 0 && sx < a.Wd;
+      const __nv_bfloat16* src = ok ? base + (((size_t)pb[i] * a.H + sy) * a.Wd + sx) * cs + co : base;
+      cp_async16_zfill(smem_u32(dA + 4 * sw64(r0 + 64 * i, c)), src, ok);
+    }
+    if (tid < BN * 4) {
+      const int r = tid >> 2, cc = tid & 3;
+      const __nv_bfloat16* src = a.W + ((size_t)(n0 + r) * 9 + tap) * Cin + ci0 + cc * 8;
+      cp_async16(smem_u32(sB + (size_t)st * BN * kBK / 2 + 4 * sw64(r, cc)), src);
+    }
+  };
+
+  float acc[2][NT][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+#pragma unroll
+  for (int st = 0; st < kStagesB - 1; ++st) {
+    if (st < nk) load_stage(st, st);
+    cp_async_commit();
+  }
+  for (int kc = 0; kc < nk; ++kc) {
+    const int cur = kc % kStagesB;
+    cp_async_wait<kStagesB - 2>();
+    __syncthreads();  // chunk kc landed for every thread; chunk kc-1 fully consumed
+    {
+      const int nx = kc + kStagesB - 1;
+      if (nx < nk) load_stage(nx, nx % kStagesB);
+      cp_async_commit();
+    }
+    const uint32_t* sAc = sA + (size_t)cur * kBM * kBK / 2;
+    const uint32_t* sBc = sB + (size_t)cur * BN * kBK / 2;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      uint32_t af[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm * 32 + i * 16 + (lane & 15);
+        const int cc = ks * 2 + (lane >> 4);
+        ldsm_x4(smem_u32(sAc + 4 * sw64(r, cc)), af[i][0], af[i][1], af[i][2], af[i][3]);
+      }
+#pragma unroll
+      for (int j = 0; j < NT; j += 2) {
+        const int r = wn * WN + j * 8 + (lane & 7) + ((lane >> 4) << 3);
+        const int cc = ks * 2 + ((lane >> 3) & 1);
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4(smem_u32(sBc + 4 * sw64(r, cc)), b0, b1, b2, b3);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          mma_bf16(acc[i][j], af[i], b0, b1);
+          mma_bf16(acc[i][j + 1], af[i], b2, b3);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = m0 + wm * 32 + i * 16 + (lane >> 2) + h * 8;
+      if (m >= P) continue;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int n = n0 + wn * WN + j * 8 + 2 * (lane & 3);
+        float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
+        if (a.bias) {
+          v0 += a.bias[n];
+          v1 += a.bias[n + 1];
+        }
+        if (a.relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        const size_t off = (size_t)m * a.Cout + n;
+        *reinterpret_cast<float2*>(a.y1 + off) = make_float2(v0, v1);
+        if (a.yb1) *reinterpret_cast<uint32_t*>(a.yb1 + off) = pack_bf16(v0, v1);
       }
     }
 }
@@ -436,19 +572,26 @@ __global__ void __launch_bounds__(kEW) k_colsum(const float* __restrict__ dy, co
   }
 }
 
-// level-0 input: X0[p][0] = x[p], channels 1..31 zero
-__global__ void __launch_bounds__(kEW) k_pack_input(const float* __restrict__ x, float* __restrict__ X0, int P) {
+// level-0 input: X0[p][0] = x[p], channels 1..31 zero (and its BF16 copy)
+__global__ void __launch_bounds__(kEW) k_pack_input(const float* __restrict__ x, float* __restrict__ X0,
+                                                    __nv_bfloat16* __restrict__ Xb, int P) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     float4* d = reinterpret_cast<float4*>(X0 + (size_t)p * 32);
     d[0] = make_float4(x[p], 0.f, 0.f, 0.f);
 #pragma unroll
     for (int i = 1; i < 8; ++i) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (Xb) {
+      uint4* db = reinterpret_cast<uint4*>(Xb + (size_t)p * 32);
+      db[0] = make_uint4(pack_bf16(x[p], 0.f), 0u, 0u, 0u);
+#pragma unroll
+      for (int i = 1; i < 4; ++i) db[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
 }
 
 // 2x2 average pooling: (B, H, W, C) -> (B, H/2, W/2, C), float4 over channels
-__global__ void __launch_bounds__(kEW) k_avgpool(const float* __restrict__ x, float* __restrict__ y, int B, int H, int W,
-                                                 int C) {
+__global__ void __launch_bounds__(kEW) k_avgpool(const float* __restrict__ x, float* __restrict__ y,
+                                                 __nv_bfloat16* __restrict__ yb, int B, int H, int W, int C) {
   const int H2 = H / 2, W2 = W / 2, C4 = C / 4;
   const long long n = (long long)B * H2 * W2 * C4;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -461,8 +604,10 @@ __global__ void __launch_bounds__(kEW) k_avgpool(const float* __restrict__ x, fl
     const float4* s = reinterpret_cast<const float4*>(x);
     const size_t r0 = (((size_t)b * H + 2 * oy) * W + 2 * ox) * C4 + c4, r1 = r0 + (size_t)W * C4;
     const float4 a0 = s[r0], a1 = s[r0 + C4], a2 = s[r1], a3 = s[r1 + C4];
-    reinterpret_cast<float4*>(y)[i] = make_float4(0.25f * (a0.x + a1.x + a2.x + a3.x), 0.25f * (a0.y + a1.y + a2.y + a3.y),
-                                                  0.25f * (a0.z + a1.z + a2.z + a3.z), 0.25f * (a0.w + a1.w + a2.w + a3.w));
+    const float4 o = make_float4(0.25f * (a0.x + a1.x + a2.x + a3.x), 0.25f * (a0.y + a1.y + a2.y + a3.y),
+                                 0.25f * (a0.z + a1.z + a2.z + a3.z), 0.25f * (a0.w + a1.w + a2.w + a3.w));
+    reinterpret_cast<float4*>(y)[i] = o;
+    if (yb) reinterpret_cast<uint2*>(yb)[i] = make_uint2(pack_bf16(o.x, o.y), pack_bf16(o.z, o.w));
   }
 }
 
@@ -501,8 +646,8 @@ __global__ void __launch_bounds__(kEW) k_avgpool_bwd(const float* __restrict__ g
 }
 
 // nearest 2x upsampling: (B, H, W, C) -> (B, 2H, 2W, C)
-__global__ void __launch_bounds__(kEW) k_upsample(const float* __restrict__ x, float* __restrict__ y, int B, int H, int W,
-                                                  int C) {
+__global__ void __launch_bounds__(kEW) k_upsample(const float* __restrict__ x, float* __restrict__ y,
+                                                  __nv_bfloat16* __restrict__ yb, int B, int H, int W, int C) {
   const int C4 = C / 4, H2 = 2 * H, W2 = 2 * W;
   const long long n = (long long)B * H2 * W2 * C4;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -512,7 +657,9 @@ __global__ void __launch_bounds__(kEW) k_upsample(const float* __restrict__ x, f
     q /= W2;
     const int oy = (int)(q % H2);
     const int b = (int)(q / H2);
-    reinterpret_cast<float4*>(y)[i] = reinterpret_cast<const float4*>(x)[(((size_t)b * H + oy / 2) * W + ox / 2) * C4 + c4];
+    const float4 o = reinterpret_cast<const float4*>(x)[(((size_t)b * H + oy / 2) * W + ox / 2) * C4 + c4];
+    reinterpret_cast<float4*>(y)[i] = o;
+    if (yb) reinterpret_cast<uint2*>(yb)[i] = make_uint2(pack_bf16(o.x, o.y), pack_bf16(o.z, o.w));
   }
 }
 
@@ -590,6 +737,13 @@ __global__ void __launch_bounds__(kEW) k_head_bwd(const float* __restrict__ g, c
   const long long n = (long long)P * C;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     gh[i] = h[i] > 0.f ? g[i / C] * wh[i % C] : 0.f;
+}
+
+// BF16 copy (round to nearest even) of n floats
+__global__ void __launch_bounds__(kEW) k_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ y,
+                                                 long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
 }
 
 // dz = dy where y > 0, else 0
@@ -709,6 +863,9 @@ struct Net {
   // activations and gradients (indexed by level)
   float* X0 = nullptr;
   std::vector<float*> ea, eb, pool, upin, upout, da, db;
+  // BF16 copies of every convolution input of the forward pass
+  __nv_bfloat16* X0b = nullptr;
+  std::vector<__nv_bfloat16*> eab, ebb, poolb, upinb, upoutb, dab;
   std::vector<float*> g_ea, g_eb, g_pool, g_upin, g_upout, g_da, g_db, g_skip;
   float *out = nullptr, *g_out = nullptr, *g_in = nullptr;
   float* part = nullptr;        // split partials
@@ -808,6 +965,10 @@ bool smem_attrs_set() {
          cudaSuccess;
     r &= cudaFuncSetAttribute(k_conv3x3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<32>()) ==
          cudaSuccess;
+    r &= cudaFuncSetAttribute(k_conv3x3_b16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)conv_smem_b16<64>()) == cudaSuccess;
+    r &= cudaFuncSetAttribute(k_conv3x3_b16<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)conv_smem_b16<32>()) == cudaSuccess;
     r &= cudaFuncSetAttribute(k_conv3x3_wgrad<64, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)wgrad_smem<64, 64>()) == cudaSuccess;
     r &= cudaFuncSetAttribute(k_conv3x3_wgrad<64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -824,6 +985,16 @@ bool smem_attrs_set() {
 void launch_conv(const Net& n, const ConvArgs& a, cudaStream_t s) {
   const int P = a.B * a.H * a.Wd;
   smem_attrs_set();  // if this failed, the launch below reports the error
+  if (a.xb1) {  // forward pass with BF16 input copies (single output tensor)
+    if (a.Cout % 64 == 0) {
+      dim3 grid((P + kBM - 1) / kBM, a.Cout / 64);
+      k_conv3x3_b16<64><<<grid, kCT, conv_smem_b16<64>(), s>>>(a);
+    } else {
+      dim3 grid((P + kBM - 1) / kBM, a.Cout / 32);
+      k_conv3x3_b16<32><<<grid, kCT, conv_smem_b16<32>(), s>>>(a);
+    }
+    return;
+  }
   if (a.Cout % 64 == 0) {
     dim3 grid((P + kBM - 1) / kBM, a.Cout / 64);
     k_conv3x3<64><<<grid, kCT, conv_smem<64>(), s>>>(a);
@@ -845,12 +1016,15 @@ void launch_wgrad(const WgradArgs& a, int bm, int bn, int splits, cudaStream_t s
 }
 
 // forward of one 3x3 layer: y = relu(conv(x1 | x2) + b)
-void conv_fwd(Net& n, int li, const float* x1, int C1, const float* x2, int C2, float* y, int B, int lv,
-              cudaStream_t s) {
+void conv_fwd(Net& n, int li, const float* x1, const __nv_bfloat16* xb1, int C1, const float* x2,
+              const __nv_bfloat16* xb2, int C2, float* y, __nv_bfloat16* yb, int B, int lv, cudaStream_t s) {
   const Layer& L = n.layers[li];
   ConvArgs a{};
   a.x1 = x1;
   a.x2 = x2;
+  a.xb1 = xb1;
+  a.xb2 = xb2;
+  a.yb1 = yb;
   a.C1 = C1;
   a.C2 = C2;
   a.W = n.wf + L.bf_off;
@@ -931,26 +1105,29 @@ void refresh_bf16(Net& n, cudaStream_t s) {
 
 void forward_pass(Net& n, const float* x, int B, cudaStream_t s) {
   const int P0 = B * n.H * n.W;
-  k_pack_input<<<grid_for(P0), kEW, 0, s>>>(x, n.X0, P0);
+  k_pack_input<<<grid_for(P0), kEW, 0, s>>>(x, n.X0, n.X0b, P0);
   const float* h = n.X0;
+  const __nv_bfloat16* hb = n.X0b;
   int hc = 32;
   for (int l = 0; l < n.L; ++l) {
-    conv_fwd(n, enc_a(l), h, hc, nullptr, 0, n.ea[l], B, l, s);
-    conv_fwd(n, enc_b(l), n.ea[l], n.c[l], nullptr, 0, n.eb[l], B, l, s);
+    conv_fwd(n, enc_a(l), h, hb, hc, nullptr, nullptr, 0, n.ea[l], n.eab[l], B, l, s);
+    conv_fwd(n, enc_b(l), n.ea[l], n.eab[l], n.c[l], nullptr, nullptr, 0, n.eb[l], n.ebb[l], B, l, s);
     if (l < n.L - 1) {
       const long long cnt = (long long)B * (n.H >> (l + 1)) * (n.W >> (l + 1)) * n.c[l] / 4;
-      k_avgpool<<<grid_for(cnt), kEW, 0, s>>>(n.eb[l], n.pool[l], B, n.H >> l, n.W >> l, n.c[l]);
+      k_avgpool<<<grid_for(cnt), kEW, 0, s>>>(n.eb[l], n.pool[l], n.poolb[l], B, n.H >> l, n.W >> l, n.c[l]);
       h = n.pool[l];
+      hb = n.poolb[l];
       hc = n.c[l];
     }
   }
   h = n.eb[n.L - 1];
   for (int l = n.L - 2; l >= 0; --l) {
     const long long cnt = (long long)B * (n.H >> l) * (n.W >> l) * n.c[l + 1] / 4;
-    k_upsample<<<grid_for(cnt), kEW, 0, s>>>(h, n.upin[l], B, n.H >> (l + 1), n.W >> (l + 1), n.c[l + 1]);
-    conv_fwd(n, dec_up(n, l), n.upin[l], n.c[l + 1], nullptr, 0, n.upout[l], B, l, s);
-    conv_fwd(n, dec_a(n, l), n.eb[l], n.c[l], n.upout[l], n.c[l], n.da[l], B, l, s);
-    conv_fwd(n, dec_b(n, l), n.da[l], n.c[l], nullptr, 0, n.db[l], B, l, s);
+    k_upsample<<<grid_for(cnt), kEW, 0, s>>>(h, n.upin[l], n.upinb[l], B, n.H >> (l + 1), n.W >> (l + 1), n.c[l + 1]);
+    conv_fwd(n, dec_up(n, l), n.upin[l], n.upinb[l], n.c[l + 1], nullptr, nullptr, 0, n.upout[l], n.upoutb[l], B, l,
+             s);
+    conv_fwd(n, dec_a(n, l), n.eb[l], n.ebb[l], n.c[l], n.upout[l], n.upoutb[l], n.c[l], n.da[l], n.dab[l], B, l, s);
+    conv_fwd(n, dec_b(n, l), n.da[l], n.dab[l], n.c[l], nullptr, nullptr, 0, n.db[l], nullptr, B, l, s);
     h = n.db[l];
   }
   const Layer& Hd = n.layers[head_idx(n)];
@@ -1052,7 +1229,21 @@ extern "C" int cpct_unet_create(cpct_unet** out, int levels, int base, int max_b
   n->g_da.assign(L, nullptr);
   n->g_db.assign(L, nullptr);
   n->g_skip.assign(L, nullptr);
+  n->eab.assign(L, nullptr);
+  n->ebb.assign(L, nullptr);
+  n->poolb.assign(L, nullptr);
+  n->upinb.assign(L, nullptr);
+  n->upoutb.assign(L, nullptr);
+  n->dab.assign(L, nullptr);
   const size_t P0 = (size_t)max_batch * height * width;
+  ok = ok && dalloc(*n, &n->X0b, P0 * 32);
+  for (int l = 0; l < L && ok; ++l) {
+    const size_t Pl = P0 >> (2 * l), cl = n->c[l];
+    ok = dalloc(*n, &n->eab[l], Pl * cl) && dalloc(*n, &n->ebb[l], Pl * cl);
+    if (ok && l < L - 1)
+      ok = dalloc(*n, &n->poolb[l], (Pl / 4) * cl) && dalloc(*n, &n->upinb[l], Pl * (size_t)n->c[l + 1]) &&
+           dalloc(*n, &n->upoutb[l], Pl * cl) && dalloc(*n, &n->dab[l], Pl * cl);
+  }
   ok = ok && dalloc(*n, &n->X0, P0 * 32) && dalloc(*n, &n->out, P0) && dalloc(*n, &n->g_out, P0) &&
        dalloc(*n, &n->loss_part, 1024) && dalloc(*n, &n->norm_part, 152 * 16) && dalloc(*n, &n->d_gnorm, 1) &&
        dalloc(*n, &n->d_gscale, 1);
@@ -1236,6 +1427,7 @@ extern "C" int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm
 //   op 4: y = adjoint of the upsampling applied to a (double-size)
 //   op 5: y = data gradient of op 0 at output gradient a with ReLU mask b
 //         (a, b: Cout channels; y: C1 + C2 channels, one tensor)
+//   op 7: op 0 through the forward kernel that reads BF16 copies of a, b
 //   op 6: y = weight and bias gradients of op 0's convolution (no mask) at
 //         input a (C1 channels) and output gradient b (Cout channels):
 //         [Cout][3][3][C1] weights, then Cout biases
@@ -1273,7 +1465,7 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
     cudaFree(part);
     return rc;
   }
-  if (op == 0 || op == 5) {
+  if (op == 0 || op == 5 || op == 7) {
     if (!h_w || Cout < 32 || Cout % 32 || (op == 5 && !d_b)) return CPCT_EINVAL;
     const int Cin = C1 + C2;
     const size_t nw = (size_t)Cout * 9 * Cin;
@@ -1293,7 +1485,8 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
       a.B = B;
       a.H = H;
       a.Wd = W;
-      if (op == 0) {
+      __nv_bfloat16* xb = nullptr;
+      if (op == 0 || op == 7) {
         a.x1 = d_a;
         a.x2 = d_b;
         a.C1 = C1;
@@ -1304,6 +1497,18 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
         a.O1 = Cout;
         a.Cout = Cout;
         a.relu = 1;
+        if (op == 7) {
+          const long long n1 = (long long)B * H * W * C1, n2 = (long long)B * H * W * C2;
+          if (cudaMalloc(&xb, sizeof(__nv_bfloat16) * (n1 + n2 + 8)) != cudaSuccess) rc = CPCT_ENOMEM;
+          if (rc == CPCT_OK) {
+            k_to_bf16<<<grid_for(n1), kEW, 0, stream>>>(d_a, xb, n1);
+            a.xb1 = xb;
+            if (C2) {
+              k_to_bf16<<<grid_for(n2), kEW, 0, stream>>>(d_b, xb + n1, n2);
+              a.xb2 = xb + n1;
+            }
+          }
+        }
       } else {
         // pre-activation gradient dz = a * (b > 0), then the data gradient
         float* dz = nullptr;
@@ -1323,8 +1528,9 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
           cudaFree(dz);
         }
       }
-      if (rc == CPCT_OK && op == 0) launch_conv(Net(), a, stream);
+      if (rc == CPCT_OK && (op == 0 || op == 7)) launch_conv(Net(), a, stream);
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
+      if (xb) cudaFree(xb);
     }
     cudaFree(bf);
     cudaFree(dw);
@@ -1333,10 +1539,10 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
   const long long n4 = (long long)B * H * W * C1 / 4;
   switch (op) {
     case 1:
-      k_avgpool<<<grid_for(n4 / 4), kEW, 0, stream>>>(d_a, d_y, B, H, W, C1);
+      k_avgpool<<<grid_for(n4 / 4), kEW, 0, stream>>>(d_a, d_y, nullptr, B, H, W, C1);
       break;
     case 2:
-      k_upsample<<<grid_for(n4 * 4), kEW, 0, stream>>>(d_a, d_y, B, H, W, C1);
+      k_upsample<<<grid_for(n4 * 4), kEW, 0, stream>>>(d_a, d_y, nullptr, B, H, W, C1);
       break;
     case 3:
       k_avgpool_bwd<<<grid_for(n4), kEW, 0, stream>>>(d_a, d_b, nullptr, d_y, B, H, W, C1);

@@ -153,6 +153,9 @@ def test_conv_op_parity(torch_cuda, C1, C2, Cout, H, W):
     ad = torch.from_numpy(_nhwc(x32[:, :C1])).cuda()
     bd = torch.from_numpy(_nhwc(x32[:, C1:])).cuda() if C2 else None
     y = cpct.unet_debug_op(0, ad, bd, (B, H, W, Cout), w=hw, C1=C1, C2=C2, Cout=Cout).cpu().numpy()
+    # the forward pass's kernel (BF16 input copies) computes the same values
+    y7 = cpct.unet_debug_op(7, ad, bd, (B, H, W, Cout), w=hw, C1=C1, C2=C2, Cout=Cout).cpu().numpy()
+    assert np.array_equal(y, y7)
     yo = unet.relu(unet.conv(q(x32.astype(np.float64)), Wq, bias.astype(np.float32).astype(np.float64)))
     e = _rel(_nchw(y), yo)
     print("conv", e)
