@@ -269,9 +269,14 @@ __global__ void __launch_bounds__(kCT) k_conv3x3(const ConvArgs a) {
 
 constexpr int kStagesB = 4;  // pipeline depth of the BF16-input forward GEMM
 
+// pixels per tile of the BF16-input kernel: every warp computes 32 x 32
+// (4 x 2 warps of 128 x 64, or 8 x 1 warps of 256 x 32 for 32 channels)
+template <int BN>
+constexpr int bm_b16() { return 8192 / BN; }
+
 template <int BN>
 constexpr size_t conv_smem_b16() {
-  return (size_t)kStagesB * (kBM * kBK * 2 + BN * kBK * 2);
+  return (size_t)kStagesB * (bm_b16<BN>() * kBK * 2 + BN * kBK * 2);
 }
 
 // The forward convolution reading the BF16 copies of its inputs: a 4-stage
@@ -281,21 +286,24 @@ constexpr size_t conv_smem_b16() {
 // BF16 operands, the same accumulation order).
 template <int BN>
 __global__ void __launch_bounds__(kCT) k_conv3x3_b16(const ConvArgs a) {
-  constexpr int WN = BN / 2;
+  constexpr int BM = bm_b16<BN>();
+  constexpr int WARPS_M = BM / 32;  // 4 or 8
+  constexpr int WN = 32;
   constexpr int NT = WN / 8;
+  constexpr int RPT = BM / 64;      // A rows per thread
   extern __shared__ __align__(128) unsigned char smraw[];
-  uint32_t* sA = reinterpret_cast<uint32_t*>(smraw);      // [kStagesB][kBM * kBK / 2]
-  uint32_t* sB = sA + kStagesB * kBM * kBK / 2;           // [kStagesB][BN * kBK / 2]
+  uint32_t* sA = reinterpret_cast<uint32_t*>(smraw);      // [kStagesB][BM * kBK / 2]
+  uint32_t* sB = sA + kStagesB * BM * kBK / 2;            // [kStagesB][BN * kBK / 2]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 3, wn = warp >> 2;
+  const int wm = warp % WARPS_M, wn = warp / WARPS_M;
   const int HW = a.H * a.Wd, P = a.B * HW;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int Cin = a.C1 + a.C2, cchunks = Cin / kBK, nk = 9 * cchunks;
-  // A copies: 16-byte chunk c (0..3) of rows r0 and r0 + 64
+  // A copies: 16-byte chunk c (0..3) of rows r0 + 64 i
   const int c = tid & 3, r0 = tid >> 2;
-  int py[2], px[2], pb[2];
+  int py[RPT], px[RPT], pb[RPT];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < RPT; ++i) {
     const int pm = m0 + r0 + 64 * i;
     pb[i] = -1;
     if (pm < P) {
@@ -310,9 +318,9 @@ __global__ void __launch_bounds__(kCT) k_conv3x3_b16(const ConvArgs a) {
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
     const __nv_bfloat16* base = ci0 < a.C1 ? a.xb1 : a.xb2;
     const int cs = ci0 < a.C1 ? a.C1 : a.C2, co = (ci0 < a.C1 ? ci0 : ci0 - a.C1) + 8 * c;
-    uint32_t* dA = sA + (size_t)st * kBM * kBK / 2;
+    uint32_t* dA = sA + (size_t)st * BM * kBK / 2;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < RPT; ++i) {
       const int sy = py[i] + dy, sx = px[i] + dx;
       const bool ok = pb[i] >= 0 && sy >= 0 && sy < a.H && sx >= 0 && sx < a.Wd;
       const __nv_bfloat16* src = ok ? base + (((size_t)pb[i] * a.H + sy) * a.Wd + sx) * cs + co : base;
@@ -346,7 +354,7 @@ __global__ void __launch_bounds__(kCT) k_conv3x3_b16(const ConvArgs a) {
       if (nx < nk) load_stage(nx, nx % kStagesB);
       cp_async_commit();
     }
-    const uint32_t* sAc = sA + (size_t)cur * kBM * kBK / 2;
+    const uint32_t* sAc = sA + (size_t)cur * BM * kBK / 2;
     const uint32_t* sBc = sB + (size_t)cur * BN * kBK / 2;
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
@@ -987,10 +995,10 @@ void launch_conv(const Net& n, const ConvArgs& a, cudaStream_t s) {
   smem_attrs_set();  // if this failed, the launch below reports the error
   if (a.xb1) {  // forward pass with BF16 input copies (single output tensor)
     if (a.Cout % 64 == 0) {
-      dim3 grid((P + kBM - 1) / kBM, a.Cout / 64);
+      dim3 grid((P + bm_b16<64>() - 1) / bm_b16<64>(), a.Cout / 64);
       k_conv3x3_b16<64><<<grid, kCT, conv_smem_b16<64>(), s>>>(a);
     } else {
-      dim3 grid((P + kBM - 1) / kBM, a.Cout / 32);
+      dim3 grid((P + bm_b16<32>() - 1) / bm_b16<32>(), a.Cout / 32);
       k_conv3x3_b16<32><<<grid, kCT, conv_smem_b16<32>(), s>>>(a);
     }
     return;
