@@ -990,7 +990,7 @@ bool smem_attrs_set() {
   return ok;
 }
 
-void launch_conv(const Net& n, const ConvArgs& a, cudaStream_t s) {
+void launch_conv(const ConvArgs& a, cudaStream_t s) {
   const int P = a.B * a.H * a.Wd;
   smem_attrs_set();  // if this failed, the launch below reports the error
   if (a.xb1) {  // forward pass with BF16 input copies (single output tensor)
@@ -1010,7 +1010,6 @@ void launch_conv(const Net& n, const ConvArgs& a, cudaStream_t s) {
     dim3 grid((P + kBM - 1) / kBM, a.Cout / 32);
     k_conv3x3<32><<<grid, kCT, conv_smem<32>(), s>>>(a);
   }
-  (void)n;
 }
 
 void launch_wgrad(const WgradArgs& a, int bm, int bn, int splits, cudaStream_t s) {
@@ -1045,7 +1044,7 @@ void conv_fwd(Net& n, int li, const float* x1, const __nv_bfloat16* xb1, int C1,
   a.B = B;
   a.H = n.H >> lv;
   a.Wd = n.W >> lv;
-  launch_conv(n, a, s);
+  launch_conv(a, s);
 }
 
 // backward of one 3x3 layer at dz = dL/dz, z its pre-activation: data
@@ -1076,7 +1075,7 @@ void conv_bwd(Net& n, int li, const float* dz, const float* x1, int C1, const fl
     a.B = B;
     a.H = H;
     a.Wd = W;
-    launch_conv(n, a, s);
+    launch_conv(a, s);
   }
   int bm, bn, splits, cps;
   wgrad_splits(L.cout, C1, C2, P, &bm, &bn, &splits, &cps);
@@ -1531,12 +1530,12 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
           a.y1 = d_y;
           a.O1 = Cin;
           a.Cout = Cin;
-          launch_conv(Net(), a, stream);
+          launch_conv(a, stream);
           if (cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
           cudaFree(dz);
         }
       }
-      if (rc == CPCT_OK && (op == 0 || op == 7)) launch_conv(Net(), a, stream);
+      if (rc == CPCT_OK && (op == 0 || op == 7)) launch_conv(a, stream);
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
       if (xb) cudaFree(xb);
     }
