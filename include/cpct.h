@@ -347,6 +347,13 @@ int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm, double* g
 int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, float* d_y, const float* h_w, int B, int H, int W,
                        int C1, int C2, int Cout, cudaStream_t stream);
 
+/* Test introspection of the tensor-core (tcgen05) path: D = A * B^T with one
+ * CTA and the accumulator in tensor memory.  A: 128 x k, B: n x k (bfloat16,
+ * row-major, device, 16-byte aligned), D: 128 x n (float32, device); k a
+ * multiple of 32, n in {32, 64, 128}.  Synchronous; CPCT_ETIMEOUT if a
+ * bounded wait for the MMA gave up. */
+int cpct_debug_tc_gemm(const void* d_a, const void* d_b, float* d_d, int n, int k, cudaStream_t stream);
+
 /* Allocation-free adjoint.  Some callers cannot allocate device memory at
  * the point where they apply the operator: code running under an allocator
  * that has reserved the whole device pool (a framework's caching allocator),

@@ -586,3 +586,17 @@ def unet_debug_op(op, a, b, out_shape, w=None, C1=None, C2=0, Cout=0, stream=Non
                                vp(y.data_ptr()), hw.ctypes.data_as(vp) if hw is not None else None,
                                B, H, W, C1, C2, Cout, _stream(torch, stream)), "cpct_unet_debug_op")
     return y
+
+
+def debug_tc_gemm(a_bf16, b_bf16):
+    """D = A * B^T on the tensor cores (tcgen05), A 128 x K, B N x K (bfloat16
+    CUDA tensors); returns D (float32)."""
+    import torch
+    L = lib()
+    vp = ctypes.c_void_p
+    L.cpct_debug_tc_gemm.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    n, k = b_bf16.shape
+    d = torch.empty((128, n), device=a_bf16.device, dtype=torch.float32)
+    check(L.cpct_debug_tc_gemm(vp(a_bf16.data_ptr()), vp(b_bf16.data_ptr()), vp(d.data_ptr()), n, k,
+                               _stream(torch, None)), "cpct_debug_tc_gemm")
+    return d

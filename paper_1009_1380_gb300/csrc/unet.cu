@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace {
 
@@ -1561,4 +1562,111 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
       return CPCT_EINVAL;
   }
   return cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(stream) == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 check: D (128 x N, FP32) = A (128 x K, BF16) * B (N x K, BF16)^T with
+// one CTA, the accumulator in tensor memory (for tests of the descriptors and
+// of the MMA / commit / load sequence)
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long long kTcWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+
+template <int N>
+__global__ void __launch_bounds__(128) k_tc_gemm_check(const __nv_bfloat16* __restrict__ A,
+                                                       const __nv_bfloat16* __restrict__ B, float* __restrict__ D,
+                                                       int K, int* __restrict__ err) {
+  __shared__ __align__(1024) unsigned char sA[128 * 32 * 2];
+  __shared__ __align__(1024) unsigned char sB[N * 32 * 2];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    cpct::tc_alloc(smem_u32(&tslot), N);
+    cpct::tc_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  cpct::tc_fence_before();
+  __syncthreads();
+  cpct::tc_fence_after();
+  const uint32_t tbase = tslot;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < K && ok; k0 += 32) {
+    // K-major core-matrix layout: (row / 8) * 512 + (k / 8) * 128 + (row % 8) * 16
+    for (int q = tid; q < 128 * 4; q += 128) {
+      const int r = q >> 2, c = q & 3;
+      cp_async16(smem_u32(sA + (r >> 3) * 512 + c * 128 + (r & 7) * 16), A + (size_t)r * K + k0 + 8 * c);
+    }
+    for (int q = tid; q < N * 4; q += 128) {
+      const int r = q >> 2, c = q & 3;
+      cp_async16(smem_u32(sB + (r >> 3) * 512 + c * 128 + (r & 7) * 16), B + (size_t)r * K + k0 + 8 * c);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    cpct::fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      cpct::tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const uint64_t ad = cpct::tc_smem_desc(smem_u32(sA) + kk * 256, 128, 512);
+        const uint64_t bd = cpct::tc_smem_desc(smem_u32(sB) + kk * 256, 128, 512);
+        cpct::tc_mma_bf16(tbase, ad, bd, cpct::tc_idesc_bf16(128, N), k0 > 0 || kk > 0);
+      }
+      cpct::tc_commit(&bar);
+    }
+    const bool w = mbar_wait_bounded(&bar, phase, kTcWaitCycles);
+    phase ^= 1u;
+    ok = __syncthreads_and(w);
+    cpct::tc_fence_after();
+  }
+  if (ok) {
+#pragma unroll
+    for (int j = 0; j < N / 8; ++j) {
+      float v[8];
+      cpct::tc_ld8(tbase + ((uint32_t)(warp * 32) << 16) + j * 8, v);
+      cpct::tc_wait_ld();
+      const int row = warp * 32 + lane;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) D[(size_t)row * N + j * 8 + i] = v[i];
+    }
+  } else if (tid == 0) {
+    atomicOr(err, 1);
+  }
+  cpct::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) cpct::tc_dealloc(tbase, N);
+}
+
+}  // namespace
+
+// D = A * B^T on the tensor cores (tcgen05); A 128 x K, B N x K (BF16,
+// row-major, device), D 128 x N (FP32, device); K a multiple of 32, N in
+// {32, 64, 128}.  Test introspection only.
+extern "C" int cpct_debug_tc_gemm(const void* d_a, const void* d_b, float* d_d, int n, int k, cudaStream_t stream) {
+  if (!d_a || !d_b || !d_d || k < 32 || k % 32 || (n != 32 && n != 64 && n != 128)) return CPCT_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_a) & 15u) || (reinterpret_cast<uintptr_t>(d_b) & 15u)) return CPCT_EINVAL;
+  int* err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return CPCT_ENOMEM;
+  int rc = cudaMemsetAsync(err, 0, sizeof(int), stream) == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+  const __nv_bfloat16* A = static_cast<const __nv_bfloat16*>(d_a);
+  const __nv_bfloat16* B = static_cast<const __nv_bfloat16*>(d_b);
+  if (rc == CPCT_OK) {
+    if (n == 32) k_tc_gemm_check<32><<<1, 128, 0, stream>>>(A, B, d_d, k, err);
+    else if (n == 64) k_tc_gemm_check<64><<<1, 128, 0, stream>>>(A, B, d_d, k, err);
+    else k_tc_gemm_check<128><<<1, 128, 0, stream>>>(A, B, d_d, k, err);
+  }
+  int h_err = 0;
+  if (rc == CPCT_OK && (cudaGetLastError() != cudaSuccess ||
+                        cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+                        cudaStreamSynchronize(stream) != cudaSuccess))
+    rc = CPCT_ECUDA;
+  cudaFree(err);
+  if (rc == CPCT_OK && h_err) rc = CPCT_ETIMEOUT;
+  return rc;
 }
