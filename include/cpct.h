@@ -305,8 +305,16 @@ int cpct_unet_get_params(cpct_unet* net, float* h_params, cudaStream_t stream);
 int cpct_unet_get_grads(cpct_unet* net, float* h_grads, cudaStream_t stream);
 
 /* out = net(in) for `batch` images; d_in, d_out device float32 batch x H x W
- * (16-byte aligned).  Stream-ordered, asynchronous. */
+ * (16-byte aligned).  Stream-ordered, asynchronous.  The 3x3 convolutions
+ * of the forward pass run on the tensor-memory (tcgen05) kernel, whose
+ * waits are bounded: an expired wait sets the net's device error flag
+ * (reported by cpct_unet_sync) and leaves that layer's output undefined. */
 int cpct_unet_forward(cpct_unet* net, const float* d_in, float* d_out, int batch, cudaStream_t stream);
+
+/* Synchronizes `stream` and reads and clears the net's device error flag:
+ * CPCT_OK, or CPCT_ETIMEOUT if a bounded device wait of a forward pass
+ * (cpct_unet_forward or cpct_unet_backward) expired since the last call. */
+int cpct_unet_sync(cpct_unet* net, cudaStream_t stream);
 
 /* Forward pass, loss against d_target and the gradients of every parameter
  * (kept on the device for cpct_unet_adam_step / cpct_unet_get_grads);
@@ -340,10 +348,19 @@ int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm, double* g
  *   op 6: weight and bias gradients of op 0's convolution at input a (C1
  *         channels, C2 = 0) and output gradient b (Cout channels, used as
  *         is): y = (Cout, 3, 3, C1) weights then Cout biases (flat)
- *   op 7: op 0 computed by the forward kernel that reads BF16 copies of its
- *         inputs (the network's forward pass); equals op 0
- * C1, C2 multiples of 32 (C1 > 0), Cout a multiple of 32 for ops 0, 5, 6, 7.
- * Synchronous; allocates a workspace for ops 0, 5, 6 and 7. */
+ *   op 7: op 0 computed by the mma.sync kernel that reads BF16 copies of its
+ *         inputs; equals op 0
+ *   op 8: op 0 computed by the tensor-memory (tcgen05) kernel that reads
+ *         BF16 copies of its inputs, as in the network's forward pass (Cout
+ *         in {32, 64, 128} or a multiple of 256; other Cout: CPCT_EINVAL):
+ *         operand tiles loaded by TMA where the image tiles into 128-pixel
+ *         boxes (W a multiple of 128, or a power of two below 128 dividing
+ *         H x W into 128-pixel blocks), else by cp.async gathers; the same
+ *         BF16 operands as op 0.  CPCT_ETIMEOUT if a bounded wait of the
+ *         kernel expired.
+ *   op 9: op 8 with the cp.async gathers whatever the shape.
+ * C1, C2 multiples of 32 (C1 > 0), Cout a multiple of 32 for ops 0 and 5-9.
+ * Synchronous; allocates a workspace for ops 0 and 5-9. */
 int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, float* d_y, const float* h_w, int B, int H, int W,
                        int C1, int C2, int Cout, cudaStream_t stream);
 

@@ -480,6 +480,7 @@ def _unet_setup():
     for name in ("cpct_unet_set_params", "cpct_unet_get_params", "cpct_unet_get_grads"):
         getattr(L, name).argtypes = [vp, vp, vp]
     L.cpct_unet_forward.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    L.cpct_unet_sync.argtypes = [vp, vp]
     L.cpct_unet_backward.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     L.cpct_unet_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.POINTER(ctypes.c_double), vp]
     return L
@@ -545,6 +546,11 @@ class UNet:
         check(_unet_setup().cpct_unet_forward(self.handle, _dev_ptr(x, shape, torch), _dev_ptr(out, shape, torch), B,
                                               _stream(torch, stream)), "cpct_unet_forward")
         return out
+
+    def sync(self, stream=None):
+        """Synchronize and raise if a bounded device wait of a forward pass
+        expired since the last call."""
+        check(_unet_setup().cpct_unet_sync(self.handle, _stream(self._torch, stream)), "cpct_unet_sync")
 
     def backward(self, x, target, stream=None):
         """Forward + loss + parameter gradients; returns the loss."""

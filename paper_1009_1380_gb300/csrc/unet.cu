@@ -94,6 +94,7 @@ struct ConvArgs {
   int O1, Cout;
   int relu;                // apply max(., 0) in the epilogue
   int B, H, Wd;            // batch, height, width
+  int* err;                // device error flag (bounded waits of the tensor-memory kernel)
 };
 
 constexpr int kStages = 3;  // cp.async pipeline depth of the convolution GEMMs
@@ -404,6 +405,302 @@ __global__ void __launch_bounds__(kCT) k_conv3x3_b16(const ConvArgs a) {
         if (a.yb1) *reinterpret_cast<uint32_t*>(a.yb1 + off) = pack_bf16(v0, v1);
       }
     }
+}
+
+// Persistent warp-specialized forward convolution on the tensor cores.
+constexpr int kTcLag = 2;         // chunks a cp.async producer keeps in flight before signalling one
+constexpr long long kTcWait = 2000000000LL;  // bounded waits (~1 s at 2 GHz)
+
+// threads: warps 0-3 epilogue, then the producers (4 warps of cp.async
+// copies, or one warp whose lane 0 issues TMA loads), then one MMA warp
+template <bool TMA>
+constexpr int tc_threads() {
+  return TMA ? 6 * 32 : 9 * 32;
+}
+
+// shared-memory budget of the stage ring: two CTAs per SM for N tiles up to
+// 128 columns, one for 256
+// (at least 3 stages for TMA, kTcLag + 2 for cp.async producers)
+template <int BN, int KC, bool TMA>
+constexpr int tc_stages() {
+  constexpr int budget = (BN >= 256 ? 192 : 100) * 1024, per = (128 + BN) * KC * 2, lo = TMA ? 3 : kTcLag + 2;
+  return budget / per > 12 ? 12 : budget / per < lo ? lo : budget / per;
+}
+template <int BN, int KC, bool TMA>
+constexpr size_t conv_smem_tc() {
+  return (size_t)tc_stages<BN, KC, TMA>() * (128 + BN) * KC * 2 + 1024;  // + alignment slack
+}
+
+// wait on an mbarrier phase; gives up (and raises the CTA's abort flag) after
+// kTcWait cycles, or as soon as another role has raised it
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kTcWait) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Tiles of the TMA path: Wb x Hb pixels of one image (Wb Hb = 128).  The
+// operand boxes come from 4-D tensor maps {C, W, H, B} of the BF16 input
+// copies (box {KC, Wb, Hb, 1}: zero fill outside the image is the
+// convolution's padding) and a 2-D map {9 Cin, Cout} of the weights (box
+// {KC, BN}), with the 128-byte (KC = 64) or 64-byte (KC = 32) swizzle: each
+// pixel / output channel is one row of KC channels, the K-major swizzled
+// layout the MMA descriptors name.
+struct TcMaps {
+  CUtensorMap a1, a2, w;
+  int Wb, Hb;
+};
+
+// Implicit GEMM: M = 128 pixels per tile, N = BN output channels, K = 9 Cin
+// in chunks of KC (32 or 64) channels of one tap (tap-major, then channel).
+// Each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... (N tile
+// fastest); the chunks of all its tiles flow through one ring of S stages:
+// * producers fill a stage with a chunk's BF16 operand tiles in a K-major
+//   layout and signal its "full" barrier: TMA (one thread, swizzled rows,
+//   the barrier completes on the transaction bytes), or cp.async copies by 128
+//   threads (zero-filled outside the image; element (row, k) at byte
+//   (row / 8) * 16 KC + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2, eight
+//   consecutive threads on eight consecutive rows), each thread arriving
+//   once its copies of the chunk have landed (kTcLag chunks later) and were
+//   fenced for the async proxy;
+// * one MMA thread waits for "full", issues KC / 16 MMAs (K = 16) into one
+//   of two FP32 accumulators in tensor memory and commits them to the
+//   stage's "empty" barrier (the producers refill the stage after it), and
+//   after a tile's last chunk to the accumulator's "tfull" barrier;
+// * the epilogue (warps 0-3, warp w on tile rows 32 w .. 32 w + 31) waits for
+//   "tfull", reads the accumulator with tcgen05.ld, adds the bias, applies
+//   the ReLU, writes FP32 and BF16 outputs and releases the accumulator
+//   ("tempty"), so that a tile's epilogue overlaps the next tile's MMAs.
+// Every wait is bounded; on expiry the CTA's abort flag stops all roles, the
+// MMA thread waits (bounded) for its MMAs in flight, and the error flag is
+// raised before the tensor memory is freed.
+template <int BN, int KC, bool TMA>
+__global__ void __launch_bounds__(tc_threads<TMA>(), BN >= 256 ? 1 : 2)
+    k_conv3x3_tc(const ConvArgs a, const __grid_constant__ TcMaps maps) {
+  constexpr int S = tc_stages<BN, KC, TMA>();
+  constexpr int NCH = KC / 8;                  // 16-byte pieces per row
+  constexpr int APT = NCH;                     // A pieces per cp.async producer thread
+  constexpr int RSTEP = 128 / (8 * NCH);       // 8-row groups between a thread's pieces
+  constexpr uint32_t A_BYTES = 128 * KC * 2, B_BYTES = BN * KC * 2;
+  // descriptors: swizzled rows of KC channels (TMA) or core matrices (cp.async)
+  constexpr uint32_t LAYOUT = TMA ? (KC == 64 ? cpct::kTcSwizzle128 : cpct::kTcSwizzle64) : cpct::kTcNoSwizzle;
+  constexpr uint32_t LBO = TMA ? 16 : 128, SBO = 16 * KC;     // SBO: 8 rows of KC channels either way
+  constexpr uint32_t KSTEP = TMA ? 32 : 256;                  // start advance per K = 16
+  constexpr int MMA_WARP = TMA ? 5 : 8;
+  extern __shared__ unsigned char smtc_raw[];
+  // 1024-byte aligned stage ring
+  unsigned char* smtc = smtc_raw + ((1024 - (smem_u32(smtc_raw) & 1023)) & 1023);
+  unsigned char* sA = smtc;                           // [S][A_BYTES]
+  unsigned char* sB = smtc + (size_t)S * A_BYTES;     // [S][B_BYTES]
+  __shared__ __align__(8) uint64_t full[S], empty[S], tfull[2], tempty[2];
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int HW = a.H * a.Wd, P = a.B * HW;
+  const int ntn = a.Cout / BN, ntiles = ((P + 127) / 128) * ntn;
+  const int Cin = a.C1 + a.C2, cchunks = Cin / KC, nk = 9 * cchunks;
+  const int txn = TMA ? a.Wd / maps.Wb : 1, tyn = TMA ? a.H / maps.Hb : 1;  // TMA tiles per image row / column
+  if (warp == MMA_WARP) {
+    cpct::tc_alloc(smem_u32(&tslot), 2 * BN);
+    cpct::tc_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], TMA ? 1 : 128);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 128);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  cpct::tc_fence_before();
+  __syncthreads();
+  cpct::tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (TMA && warp == 4) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      int g = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int mt = t / ntn, n0 = (t % ntn) * BN;
+        const int b = mt / (txn * tyn), rem = mt - b * (txn * tyn);
+        const int y0 = (rem / txn) * maps.Hb, x0 = (rem % txn) * maps.Wb;
+        bool ok = true;
+        for (int kc = 0; kc < nk; ++kc, ++g) {
+          const int st = g % S;
+          if (g >= S && !tc_wait(&empty[st], (uint32_t)(((g / S) - 1) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          const int tap = kc / cchunks, ci0 = (kc - tap * cchunks) * KC;
+          const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+          mbar_arrive_expect_tx(&full[st], A_BYTES + B_BYTES);
+          const bool first = ci0 < a.C1;
+          cpct::tma_load_4d(smem_u32(sA + (size_t)st * A_BYTES), first ? &maps.a1 : &maps.a2,
+                            first ? ci0 : ci0 - a.C1, x0 + dx, y0 + dy, b, &full[st]);
+          cpct::tma_load_2d_u32(smem_u32(sB + (size_t)st * B_BYTES), &maps.w, tap * Cin + ci0, n0, &full[st]);
+        }
+        if (!ok) break;
+      }
+      // on abort: loads still in flight land before the CTA exits
+      if (*abort)
+        for (int q = g - S < 0 ? 0 : g - S; q < g; ++q) mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kTcWait);
+    }
+    __syncwarp();
+  } else if (!TMA && warp >= 4 && warp < 8) {
+    // ---------------- cp.async producers ----------------
+    const int pt = tid - 128, c = (pt >> 3) % NCH;
+    int g = 0;  // chunks issued by this CTA
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int m0 = (t / ntn) * 128, n0 = (t % ntn) * BN;
+      int py[APT], px[APT], pb[APT];
+#pragma unroll
+      for (int i = 0; i < APT; ++i) {
+        const int pm = m0 + 8 * (i * RSTEP + pt / (8 * NCH)) + (pt & 7);
+        pb[i] = -1;
+        if (pm < P) {
+          pb[i] = pm / HW;
+          const int q = pm - pb[i] * HW;
+          py[i] = q / a.Wd;
+          px[i] = q - py[i] * a.Wd;
+        }
+      }
+      for (int kc = 0; kc < nk; ++kc, ++g) {
+        const int st = g % S;
+        if (g >= S && !tc_wait(&empty[st], (uint32_t)(((g / S) - 1) & 1), abort)) break;
+        const int tap = kc / cchunks, ci0 = (kc - tap * cchunks) * KC;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const __nv_bfloat16* base = ci0 < a.C1 ? a.xb1 : a.xb2;
+        const int cs = ci0 < a.C1 ? a.C1 : a.C2, co = (ci0 < a.C1 ? ci0 : ci0 - a.C1) + 8 * c;
+        unsigned char* dA = sA + (size_t)st * A_BYTES;
+#pragma unroll
+        for (int i = 0; i < APT; ++i) {
+          const int r = 8 * (i * RSTEP + pt / (8 * NCH)) + (pt & 7);
+          const int sy = py[i] + dy, sx = px[i] + dx;
+          const bool ok = pb[i] >= 0 && sy >= 0 && sy < a.H && sx >= 0 && sx < a.Wd;
+          const __nv_bfloat16* src = ok ? base + (((size_t)pb[i] * a.H + sy) * a.Wd + sx) * cs + co : base;
+          cp_async16_zfill(smem_u32(dA + (r >> 3) * SBO + c * 128 + (r & 7) * 16), src, ok);
+        }
+        unsigned char* dB = sB + (size_t)st * B_BYTES;
+#pragma unroll
+        for (int q = pt; q < BN * NCH; q += 128) {
+          const int r = 8 * ((q >> 3) / NCH) + (q & 7), cc = (q >> 3) % NCH;
+          const __nv_bfloat16* src = a.W + ((size_t)(n0 + r) * 9 + tap) * Cin + ci0 + cc * 8;
+          cp_async16(smem_u32(dB + (r >> 3) * SBO + cc * 128 + (r & 7) * 16), src);
+        }
+        cp_async_commit();
+        if (g >= kTcLag) {
+          cp_async_wait<kTcLag>();  // chunk g - kTcLag landed
+          cpct::fence_proxy_async_smem();
+          cpct::mbar_arrive(&full[(g - kTcLag) % S]);
+        }
+      }
+      if (*abort) break;
+    }
+    cp_async_wait<0>();
+    cpct::fence_proxy_async_smem();
+    for (int q = g - kTcLag < 0 ? 0 : g - kTcLag; q < g; ++q) cpct::mbar_arrive(&full[q % S]);
+  } else if (warp == MMA_WARP) {
+    // ---------------- MMA issue ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = cpct::tc_idesc_bf16(128, BN);
+      int g = 0, it = 0;
+      uint64_t* last = nullptr;  // barrier of the last commit, and its phase
+      uint32_t last_par = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+        const int acc = it & 1;
+        if (it >= 2 && !tc_wait(&tempty[acc], (uint32_t)(((it >> 1) - 1) & 1), abort)) break;
+        cpct::tc_fence_after();
+        const uint32_t d = tbase + acc * BN;
+        for (int kc = 0; kc < nk; ++kc, ++g) {
+          const int st = g % S;
+          if (!tc_wait(&full[st], (uint32_t)((g / S) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          cpct::tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + (size_t)st * A_BYTES);
+          const uint32_t b0 = smem_u32(sB + (size_t)st * B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < KC / 16; ++kk)
+            cpct::tc_mma_bf16(d, cpct::tc_smem_desc(a0 + kk * KSTEP, LBO, SBO, LAYOUT),
+                              cpct::tc_smem_desc(b0 + kk * KSTEP, LBO, SBO, LAYOUT), idesc, kc > 0 || kk > 0);
+          cpct::tc_commit(&empty[st]);
+          last = &empty[st];
+          last_par = (uint32_t)((g / S) & 1);
+        }
+        if (!ok) break;
+        cpct::tc_commit(&tfull[acc]);
+        last = &tfull[acc];
+        last_par = (uint32_t)((it >> 1) & 1);
+      }
+      // MMAs still in flight must finish before the tensor memory is freed
+      if (*abort && last) mbar_wait_bounded(last, last_par, kTcWait);
+    }
+    __syncwarp();
+  } else if (warp < 4) {
+    // ---------------- epilogue ----------------
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int acc = it & 1;
+      if (!tc_wait(&tfull[acc], (uint32_t)((it >> 1) & 1), abort)) break;
+      cpct::tc_fence_after();
+      const int mt = t / ntn, n0 = (t % ntn) * BN, p = warp * 32 + lane;
+      int m;
+      if (TMA) {
+        const int b = mt / (txn * tyn), rem = mt - b * (txn * tyn);
+        const int y = (rem / txn) * maps.Hb + p / maps.Wb, x = (rem % txn) * maps.Wb + p % maps.Wb;
+        m = (b * a.H + y) * a.Wd + x;
+      } else {
+        m = mt * 128 + p;
+      }
+#pragma unroll 1
+      for (int j = 0; j < BN / 16; ++j) {
+        float v[16];
+        cpct::tc_ld16(tbase + ((uint32_t)(warp * 32) << 16) + acc * BN + j * 16, v);
+        cpct::tc_wait_ld();
+        if (m < P) {
+          const int n = n0 + j * 16;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float x = v[i] + (a.bias ? a.bias[n + i] : 0.f);
+            v[i] = a.relu ? fmaxf(x, 0.f) : x;
+          }
+          float4* dst = reinterpret_cast<float4*>(a.y1 + (size_t)m * a.Cout + n);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          if (a.yb1) {
+            uint4* db = reinterpret_cast<uint4*>(a.yb1 + (size_t)m * a.Cout + n);
+            db[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                               pack_bf16(v[6], v[7]));
+            db[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
+                               pack_bf16(v[14], v[15]));
+          }
+        }
+      }
+      cpct::tc_fence_before();
+      cpct::mbar_arrive(&tempty[acc]);
+    }
+  }
+  cpct::tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && abort_flag) atomicOr(a.err, 1);
+  if (warp == MMA_WARP) {
+    cpct::tc_fence_after();
+    cpct::tc_dealloc(tbase, 2 * BN);
+  }
 }
 
 // swizzled 16-byte chunk index of a row of CPR chunks (CPR = 4 or 8)
@@ -883,6 +1180,7 @@ struct Net {
   double* norm_part = nullptr;   // gradient-norm block partials
   double* d_gnorm = nullptr;     // ||g|| of the last Adam step
   float* d_gscale = nullptr;     // clipping factor of the last Adam step
+  int* d_err = nullptr;          // device error flag (CPCT_ERR_* bits)
   int last_batch = 0;
 };
 
@@ -967,6 +1265,61 @@ size_t wgrad_splits(int cout, int c1, int c2, long long P, int* bm, int* bn, int
 
 // the pipelined kernels need more than the default 48 KB of dynamic shared
 // memory: raise the limit once per process (per kernel)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static const EncodeTiledFn fn = [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                   cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess
+               ? reinterpret_cast<EncodeTiledFn>(ptr)
+               : nullptr;
+  }();
+  return fn;
+}
+
+// 4-D map {C, W, H, B} of a BF16 NHWC activation, box {KC, Wb, Hb, 1},
+// 128-byte (KC = 64) or 64-byte (KC = 32) swizzle
+bool encode_act_map(CUtensorMap* m, const __nv_bfloat16* x, int C, int B, int H, int W, int Wb, int Hb, int KC) {
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)KC, (cuuint32_t)Wb, (cuuint32_t)Hb, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(x), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, KC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// tensor maps of the TMA forward convolution; false where the image does
+// not tile into 128-pixel boxes (or no encoder is available)
+bool encode_conv_maps(const ConvArgs& a, int bn, int kc, TcMaps* maps) {
+  if (!encode_fn()) return false;
+  const int Wb = a.Wd >= 128 ? 128 : a.Wd;
+  if (Wb < 1 || a.Wd % Wb || 128 % Wb) return false;
+  const int Hb = 128 / Wb;
+  if (a.H % Hb) return false;
+  maps->Wb = Wb;
+  maps->Hb = Hb;
+  const int Cin = a.C1 + a.C2;
+  if (!encode_act_map(&maps->a1, a.xb1, a.C1, a.B, a.H, a.Wd, Wb, Hb, kc)) return false;
+  if (a.C2 == 0)
+    maps->a2 = maps->a1;  // unused
+  else if (!encode_act_map(&maps->a2, a.xb2, a.C2, a.B, a.H, a.Wd, Wb, Hb, kc))
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)9 * Cin, (cuuint64_t)a.Cout};
+  const cuuint64_t strides[1] = {(cuuint64_t)9 * Cin * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kc, (cuuint32_t)bn};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode_fn()(&maps->w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(a.W), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     kc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool smem_attrs_set() {
   static const bool ok = [] {
     bool r = true;
@@ -978,6 +1331,20 @@ bool smem_attrs_set() {
                               (int)conv_smem_b16<64>()) == cudaSuccess;
     r &= cudaFuncSetAttribute(k_conv3x3_b16<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)conv_smem_b16<32>()) == cudaSuccess;
+#define CPCT_TC_ATTR(BN, KC)                                                                       \
+  r &= cudaFuncSetAttribute(k_conv3x3_tc<BN, KC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                            (int)conv_smem_tc<BN, KC, true>()) == cudaSuccess;                           \
+  r &= cudaFuncSetAttribute(k_conv3x3_tc<BN, KC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                            (int)conv_smem_tc<BN, KC, false>()) == cudaSuccess;
+    CPCT_TC_ATTR(256, 32)
+    CPCT_TC_ATTR(128, 32)
+    CPCT_TC_ATTR(64, 32)
+    CPCT_TC_ATTR(32, 32)
+    CPCT_TC_ATTR(256, 64)
+    CPCT_TC_ATTR(128, 64)
+    CPCT_TC_ATTR(64, 64)
+    CPCT_TC_ATTR(32, 64)
+#undef CPCT_TC_ATTR
     r &= cudaFuncSetAttribute(k_conv3x3_wgrad<64, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)wgrad_smem<64, 64>()) == cudaSuccess;
     r &= cudaFuncSetAttribute(k_conv3x3_wgrad<64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -991,9 +1358,40 @@ bool smem_attrs_set() {
   return ok;
 }
 
-void launch_conv(const ConvArgs& a, cudaStream_t s) {
+void launch_conv(const ConvArgs& a, cudaStream_t s, bool force_cp_async = false) {
   const int P = a.B * a.H * a.Wd;
   smem_attrs_set();  // if this failed, the launch below reports the error
+  // forward pass on the tensor-memory kernel: N tiles of 32, 64, 128 or 256
+  // channels (a power of two: the tensor memory allocation's granularity)
+  const int bn = a.Cout % 256 == 0 ? 256 : (a.Cout == 128 || a.Cout == 64 || a.Cout == 32) ? a.Cout : 0;
+  if (a.xb1 && a.err && bn) {
+    // persistent: one CTA (N tile of 256) or two per SM over all tiles;
+    // 64-channel chunks where both inputs split into them
+    static const int sms = [] {
+      int dev = 0, n = 0;
+      cudaGetDevice(&dev);
+      return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 1;
+    }();
+    const bool k64 = a.C1 % 64 == 0 && a.C2 % 64 == 0;
+    const long long ntiles = (long long)((P + 127) / 128) * (a.Cout / bn);
+    const int grid = (int)std::min<long long>(ntiles, (long long)sms * (bn >= 256 ? 1 : 2));
+    TcMaps maps;
+    const bool tma = !force_cp_async && encode_conv_maps(a, bn, k64 ? 64 : 32, &maps);
+    if (!tma) memset(&maps, 0, sizeof(maps));
+#define CPCT_TC_LAUNCH(BN, KC)                                                                           \
+  do {                                                                                                  \
+    if (tma)                                                                                            \
+      k_conv3x3_tc<BN, KC, true><<<grid, tc_threads<true>(), conv_smem_tc<BN, KC, true>(), s>>>(a, maps);   \
+    else                                                                                                    \
+      k_conv3x3_tc<BN, KC, false><<<grid, tc_threads<false>(), conv_smem_tc<BN, KC, false>(), s>>>(a, maps); \
+  } while (0)
+    if (bn == 256) { if (k64) CPCT_TC_LAUNCH(256, 64); else CPCT_TC_LAUNCH(256, 32); }
+    else if (bn == 128) { if (k64) CPCT_TC_LAUNCH(128, 64); else CPCT_TC_LAUNCH(128, 32); }
+    else if (bn == 64) { if (k64) CPCT_TC_LAUNCH(64, 64); else CPCT_TC_LAUNCH(64, 32); }
+    else { if (k64) CPCT_TC_LAUNCH(32, 64); else CPCT_TC_LAUNCH(32, 32); }
+#undef CPCT_TC_LAUNCH
+    return;
+  }
   if (a.xb1) {  // forward pass with BF16 input copies (single output tensor)
     if (a.Cout % 64 == 0) {
       dim3 grid((P + bm_b16<64>() - 1) / bm_b16<64>(), a.Cout / 64);
@@ -1045,6 +1443,7 @@ void conv_fwd(Net& n, int li, const float* x1, const __nv_bfloat16* xb1, int C1,
   a.B = B;
   a.H = n.H >> lv;
   a.Wd = n.W >> lv;
+  a.err = n.d_err;
   launch_conv(a, s);
 }
 
@@ -1254,7 +1653,7 @@ extern "C" int cpct_unet_create(cpct_unet** out, int levels, int base, int max_b
   }
   ok = ok && dalloc(*n, &n->X0, P0 * 32) && dalloc(*n, &n->out, P0) && dalloc(*n, &n->g_out, P0) &&
        dalloc(*n, &n->loss_part, 1024) && dalloc(*n, &n->norm_part, 152 * 16) && dalloc(*n, &n->d_gnorm, 1) &&
-       dalloc(*n, &n->d_gscale, 1);
+       dalloc(*n, &n->d_gscale, 1) && dalloc(*n, &n->d_err, 1);
   for (int l = 0; l < L && ok; ++l) {
     const size_t Pl = P0 >> (2 * l), cl = n->c[l];
     ok = dalloc(*n, &n->ea[l], Pl * cl) && dalloc(*n, &n->eb[l], Pl * cl) && dalloc(*n, &n->g_ea[l], Pl * cl) &&
@@ -1286,7 +1685,8 @@ extern "C" int cpct_unet_create(cpct_unet** out, int levels, int base, int max_b
     ok = cudaMemsetAsync(n->param, 0, sizeof(float) * n->n_param, stream) == cudaSuccess &&
          cudaMemsetAsync(n->grad, 0, sizeof(float) * n->n_param, stream) == cudaSuccess &&
          cudaMemsetAsync(n->adam_m, 0, sizeof(float) * n->n_param, stream) == cudaSuccess &&
-         cudaMemsetAsync(n->adam_v, 0, sizeof(float) * n->n_param, stream) == cudaSuccess;
+         cudaMemsetAsync(n->adam_v, 0, sizeof(float) * n->n_param, stream) == cudaSuccess &&
+         cudaMemsetAsync(n->d_err, 0, sizeof(int), stream) == cudaSuccess;
     refresh_bf16(*n, stream);
     ok = ok && cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(stream) == cudaSuccess;
   }
@@ -1382,6 +1782,22 @@ extern "C" int cpct_unet_forward(cpct_unet* net, const float* d_in, float* d_out
   return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
 }
 
+extern "C" int cpct_unet_sync(cpct_unet* net, cudaStream_t stream) {
+  if (!net) return CPCT_EINVAL;
+  Net& n = *net->net;
+  int err = 0;
+  if (cudaMemcpyAsync(&err, n.d_err, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+      cudaStreamSynchronize(stream) != cudaSuccess)
+    return CPCT_ECUDA;
+  if (err) {
+    if (cudaMemsetAsync(n.d_err, 0, sizeof(int), stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      return CPCT_ECUDA;
+    return CPCT_ETIMEOUT;
+  }
+  return CPCT_OK;
+}
+
 extern "C" int cpct_unet_backward(cpct_unet* net, const float* d_in, const float* d_target, int batch, double* loss,
                                   cudaStream_t stream) {
   if (!net || !unet_ptr_ok(d_in) || !unet_ptr_ok(d_target)) return CPCT_EINVAL;
@@ -1473,8 +1889,9 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
     cudaFree(part);
     return rc;
   }
-  if (op == 0 || op == 5 || op == 7) {
+  if (op == 0 || op == 5 || op == 7 || op == 8 || op == 9) {
     if (!h_w || Cout < 32 || Cout % 32 || (op == 5 && !d_b)) return CPCT_EINVAL;
+    if (op >= 8 && !(Cout % 256 == 0 || Cout == 128 || Cout == 64 || Cout == 32)) return CPCT_EINVAL;
     const int Cin = C1 + C2;
     const size_t nw = (size_t)Cout * 9 * Cin;
     float* dw = nullptr;
@@ -1494,7 +1911,8 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
       a.H = H;
       a.Wd = W;
       __nv_bfloat16* xb = nullptr;
-      if (op == 0 || op == 7) {
+      int* derr = nullptr;
+      if (op == 0 || op == 7 || op == 8 || op == 9) {
         a.x1 = d_a;
         a.x2 = d_b;
         a.C1 = C1;
@@ -1505,7 +1923,13 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
         a.O1 = Cout;
         a.Cout = Cout;
         a.relu = 1;
-        if (op == 7) {
+        if (op >= 8) {
+          if (cudaMalloc(&derr, sizeof(int)) != cudaSuccess ||
+              cudaMemsetAsync(derr, 0, sizeof(int), stream) != cudaSuccess)
+            rc = CPCT_ENOMEM;
+          a.err = derr;
+        }
+        if (op >= 7) {
           const long long n1 = (long long)B * H * W * C1, n2 = (long long)B * H * W * C2;
           if (cudaMalloc(&xb, sizeof(__nv_bfloat16) * (n1 + n2 + 8)) != cudaSuccess) rc = CPCT_ENOMEM;
           if (rc == CPCT_OK) {
@@ -1536,8 +1960,14 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
           cudaFree(dz);
         }
       }
-      if (rc == CPCT_OK && (op == 0 || op == 7)) launch_conv(a, stream);
+      if (rc == CPCT_OK && (op == 0 || op >= 7)) launch_conv(a, stream, op == 9);
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
+      if (derr) {
+        int e = 0;
+        if (rc == CPCT_OK && cudaMemcpy(&e, derr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = CPCT_ECUDA;
+        if (rc == CPCT_OK && e) rc = CPCT_ETIMEOUT;
+        cudaFree(derr);
+      }
       if (xb) cudaFree(xb);
     }
     cudaFree(bf);

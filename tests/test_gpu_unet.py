@@ -156,6 +156,9 @@ def test_conv_op_parity(torch_cuda, C1, C2, Cout, H, W):
     # the forward pass's kernel (BF16 input copies) computes the same values
     y7 = cpct.unet_debug_op(7, ad, bd, (B, H, W, Cout), w=hw, C1=C1, C2=C2, Cout=Cout).cpu().numpy()
     assert np.array_equal(y, y7)
+    # ... and so does the tensor-memory kernel, up to FP32 accumulation order
+    y8 = cpct.unet_debug_op(8, ad, bd, (B, H, W, Cout), w=hw, C1=C1, C2=C2, Cout=Cout).cpu().numpy()
+    assert np.max(np.abs(y8 - y)) <= 1e-5 * np.max(np.abs(y))
     yo = unet.relu(unet.conv(q(x32.astype(np.float64)), Wq, bias.astype(np.float32).astype(np.float64)))
     e = _rel(_nchw(y), yo)
     print("conv", e)
@@ -168,6 +171,51 @@ def test_conv_op_parity(torch_cuda, C1, C2, Cout, H, W):
     e = _rel(_nchw(gd), gx)
     print("dgrad", e)
     assert e < 1e-5
+
+
+@pytest.mark.parametrize("C1,C2,Cout,B,H,W", [
+    (32, 0, 32, 3, 21, 19),      # 1197 pixels: 9 full M tiles and a ragged tail
+    (32, 32, 64, 2, 16, 24),     # concatenated inputs
+    (128, 0, 128, 1, 30, 17),    # 64-channel chunks
+    (64, 64, 64, 2, 16, 33),     # 64-channel chunks from both inputs
+    (256, 0, 256, 2, 12, 11),    # N tile of 256 tensor-memory columns
+    (128, 128, 512, 1, 10, 13),  # two N tiles, 8 channel chunks per tap
+    # images that tile into 128-pixel TMA boxes (Wb x Hb)
+    (32, 0, 32, 2, 6, 128),      # 128 x 1
+    (32, 32, 64, 1, 8, 256),     # two boxes per row, concatenated inputs
+    (64, 64, 64, 2, 16, 64),     # 64 x 2, 64-channel chunks from both inputs
+    (128, 0, 128, 1, 32, 32),    # 32 x 4
+    (256, 0, 256, 2, 16, 16),    # 16 x 8
+    (128, 128, 512, 1, 8, 16),   # two N tiles of 256
+])
+def test_conv_tc_parity(torch_cuda, C1, C2, Cout, B, H, W):
+    """The tensor-memory (tcgen05) forward convolution against the oracle
+    with the same bfloat16 operand rounding (FP32 against FP64 accumulation),
+    at shapes spanning several 128-pixel tiles, a ragged tail and every N tile
+    width; with the operand tiles loaded by TMA where the image tiles into
+    128-pixel boxes (op 8) and by cp.async gathers (op 9)."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    rng = np.random.default_rng(1000 + C1 + 3 * C2 + Cout + H)
+    a = rng.standard_normal((B, C1, H, W))
+    b = rng.standard_normal((B, C2, H, W)) if C2 else None
+    Wt = rng.standard_normal((Cout, 3, 3, C1 + C2)) * np.sqrt(2.0 / (9 * (C1 + C2)))
+    bias = 0.1 * rng.standard_normal(Cout)
+    hw = np.concatenate([Wt.ravel(), bias]).astype(np.float32)
+    q = unet.bf16_round
+    x32 = (np.concatenate([a, b], axis=1) if C2 else a).astype(np.float32)
+    ad = torch.from_numpy(_nhwc(x32[:, :C1])).cuda()
+    bd = torch.from_numpy(_nhwc(x32[:, C1:])).cuda() if C2 else None
+    yo = unet.relu(unet.conv(q(x32.astype(np.float64)), q(Wt.astype(np.float32)),
+                             bias.astype(np.float32).astype(np.float64)))
+    tol = 1e-5 * np.max(np.abs(yo))
+    for op in (8, 9):
+        y = cpct.unet_debug_op(op, ad, bd, (B, H, W, Cout), w=hw, C1=C1, C2=C2, Cout=Cout).cpu().numpy()
+        e = _rel(_nchw(y), yo)
+        print("tcgen05 conv op", op, e)
+        assert e < 1e-5
+        # element-wise: FP32 accumulation of 9 (C1 + C2) products
+        assert np.max(np.abs(_nchw(y) - yo)) <= tol
 
 
 @pytest.mark.parametrize("C1,Cout,H,W", [(32, 32, 9, 13), (64, 128, 8, 8), (128, 64, 4, 4), (32, 64, 40, 24)])
