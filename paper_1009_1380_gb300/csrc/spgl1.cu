@@ -241,7 +241,11 @@ struct SpgState {
   int iter, n_line, status, done, ticks, n_trials, stationary, n_stationary;
   // the tick's adjoint operator is skipped (its output unused) while set:
   // no gradient update, or the slice is done
-  int skip_adj, pad2;
+  int skip_adj;
+  // the tick's forward operator is skipped while set: the slice is done, or
+  // the tick is a projected-gradient step-length tick (T_PG), which reads
+  // only x and g and accepts nothing
+  int skip_fwd;
 };
 
 // SPGL1 status codes (spgl1_info.status)
@@ -660,6 +664,7 @@ __global__ void __launch_bounds__(kRB) k_spg_mid(SpgVec V) {
       st->status = S_NONFINITE;
       st->done = 1;
       st->skip_adj = 1;
+      st->skip_fwd = 1;
       return;
     }
   }
@@ -763,6 +768,7 @@ __global__ void __launch_bounds__(kRB) k_spg_end(SpgVec V) {
       break;
     }
   }
+  st->skip_fwd = (st->done || st->type == T_PG) ? 1 : 0;
 }
 
 // ||b||^2 and ||x0||_1 for the set-up
@@ -788,6 +794,7 @@ __global__ void __launch_bounds__(kRB) k_spg_setup(SpgVec V, double tau0) {
   st->tau = tau0 >= 0.0 ? tau0 : q[1];
   st->type = T_INIT;
   st->ps = 0.0;
+  st->skip_fwd = 0;
 }
 
 // final ||x||_1 and ||r||_2 (ignores the done flag)
@@ -829,7 +836,7 @@ void enqueue_tick(SliceWork& w, int filter) {
     k_spg_radix_select<<<1, kRB, 0, s>>>(V, pass);
   }
   k_spg_proj_apply<<<kRG, kRB, 0, s>>>(V);
-  cpct_launch_fwd_skip(w.plan, V.xt, V.y, &V.st->done, s);
+  cpct_launch_fwd_skip(w.plan, V.xt, V.y, &V.st->skip_fwd, s);
   if (filter) {
     k_ring_colmean<<<(w.plan->ns + 31) / 32, kRB, 0, s>>>(V.y, w.ring.m, w.plan->m, w.plan->ns);
     k_ring_offset<<<1, kRB, 0, s>>>(w.ring.Q, w.ring.m, w.ring.d, w.plan->ns);

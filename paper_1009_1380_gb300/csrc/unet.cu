@@ -95,6 +95,13 @@ struct ConvArgs {
   int relu;                // apply max(., 0) in the epilogue
   int B, H, Wd;            // batch, height, width
   int* err;                // device error flag (bounded waits of the tensor-memory kernel)
+  // fused 1x1 head (tensor-memory kernel, one N tile covering Cout): if
+  // head_out is set, head_out[p] = head_x[p] + head_b[0] + sum_c head_w[c] y[p, c]
+  // (FP32, channel order)
+  const float* head_w;
+  const float* head_b;
+  const float* head_x;
+  float* head_out;
 };
 
 constexpr int kStages = 3;  // cp.async pipeline depth of the convolution GEMMs
@@ -401,7 +408,7 @@ __global__ void __launch_bounds__(kCT) k_conv3x3_b16(const ConvArgs a) {
           v1 = fmaxf(v1, 0.f);
         }
         const size_t off = (size_t)m * a.Cout + n;
-        *reinterpret_cast<float2*>(a.y1 + off) = make_float2(v0, v1);
+        if (a.y1) *reinterpret_cast<float2*>(a.y1 + off) = make_float2(v0, v1);
         if (a.yb1) *reinterpret_cast<uint32_t*>(a.yb1 + off) = pack_bf16(v0, v1);
       }
     }
@@ -658,6 +665,7 @@ __global__ void __launch_bounds__(tc_threads<TMA>(), BN >= 256 ? 1 : 2)
       if (!tc_wait(&tfull[acc], (uint32_t)((it >> 1) & 1), abort)) break;
       cpct::tc_fence_after();
       const int mt = t / ntn, n0 = (t % ntn) * BN, p = warp * 32 + lane;
+      float hs = a.head_out ? a.head_b[0] : 0.f;  // fused head: FP32, channel order
       int m;
       if (TMA) {
         const int b = mt / (txn * tyn), rem = mt - b * (txn * tyn);
@@ -678,9 +686,15 @@ __global__ void __launch_bounds__(tc_threads<TMA>(), BN >= 256 ? 1 : 2)
             const float x = v[i] + (a.bias ? a.bias[n + i] : 0.f);
             v[i] = a.relu ? fmaxf(x, 0.f) : x;
           }
-          float4* dst = reinterpret_cast<float4*>(a.y1 + (size_t)m * a.Cout + n);
+          if (a.head_out) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            for (int i = 0; i < 16; ++i) hs = fmaf(a.head_w[n + i], v[i], hs);
+          }
+          if (a.y1) {
+            float4* dst = reinterpret_cast<float4*>(a.y1 + (size_t)m * a.Cout + n);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          }
           if (a.yb1) {
             uint4* db = reinterpret_cast<uint4*>(a.yb1 + (size_t)m * a.Cout + n);
             db[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
@@ -690,6 +704,7 @@ __global__ void __launch_bounds__(tc_threads<TMA>(), BN >= 256 ? 1 : 2)
           }
         }
       }
+      if (a.head_out && m < P) a.head_out[m] = a.head_x[m] + hs;
       cpct::tc_fence_before();
       cpct::mbar_arrive(&tempty[acc]);
     }
@@ -895,42 +910,95 @@ __global__ void __launch_bounds__(kEW) k_pack_input(const float* __restrict__ x,
   }
 }
 
-// 2x2 average pooling: (B, H, W, C) -> (B, H/2, W/2, C), float4 over channels
+// The first 3x3 convolution (one input channel): z[p, co] = b[co] +
+// sum_tap bf16(x[p + tap]) w[co, tap] with the BF16 weights of the layer
+// (channel 0 of its [Cout][3][3][32] copy), FP32 accumulation in tap order,
+// ReLU; outputs FP32 (if y is set) and BF16.  Grid: x over the pixels of an
+// image row, y over the rows (b, row) of the batch; one thread per pixel,
+// all output channels (weights broadcast from shared memory).
+constexpr int kFirstMaxC = 1024;
+__global__ void __launch_bounds__(kEW) k_conv_first(const float* __restrict__ x, const __nv_bfloat16* __restrict__ wf,
+                                                    const float* __restrict__ bias, float* __restrict__ y,
+                                                    __nv_bfloat16* __restrict__ yb, int B, int H, int W, int C) {
+  __shared__ float sw[9 * kFirstMaxC];
+  __shared__ float sb[kFirstMaxC];
+  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) sw[i] = __bfloat162float(wf[(size_t)i * 32]);
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = bias[i];
+  __syncthreads();
+  const int px = blockIdx.x * blockDim.x + threadIdx.x;
+  if (px >= W) return;
+  for (int row = blockIdx.y; row < B * H; row += gridDim.y) {
+    const int py = row % H;
+    const size_t img = (size_t)(row - py) * W;  // first pixel of the image
+    float xv[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int sy = py + t / 3 - 1, sx = px + t % 3 - 1;
+      const bool ok = sy >= 0 && sy < H && sx >= 0 && sx < W;
+      xv[t] = ok ? __bfloat162float(__float2bfloat16_rn(x[img + (size_t)sy * W + sx])) : 0.f;
+    }
+    const size_t p = (size_t)row * W + px;
+    for (int g = 0; g < C / 8; ++g) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int co = g * 8 + j;
+        float acc = 0.f;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) acc = fmaf(xv[t], sw[co * 9 + t], acc);
+        v[j] = fmaxf(acc + sb[co], 0.f);
+      }
+      const size_t off = p * C + g * 8;
+      if (y) {
+        float4* d = reinterpret_cast<float4*>(y + off);
+        d[0] = make_float4(v[0], v[1], v[2], v[3]);
+        d[1] = make_float4(v[4], v[5], v[6], v[7]);
+      }
+      *reinterpret_cast<uint4*>(yb + off) =
+          make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    }
+  }
+}
+
+// launch shape of the row kernels: x over `per_row` items, y over rows
+inline dim3 row_grid(int per_row, int rows) {
+  return dim3((per_row + kEW - 1) / kEW, std::min(rows, 65535));
+}
+
+// 2x2 average pooling: (B, H, W, C) -> (B, H/2, W/2, C), float4 over
+// channels; FP32 output if y is set, BF16 copy if yb is set.  Grid:
+// row_grid(W/2 * C/4, B * H/2).
 __global__ void __launch_bounds__(kEW) k_avgpool(const float* __restrict__ x, float* __restrict__ y,
                                                  __nv_bfloat16* __restrict__ yb, int B, int H, int W, int C) {
   const int H2 = H / 2, W2 = W / 2, C4 = C / 4;
-  const long long n = (long long)B * H2 * W2 * C4;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int c4 = (int)(i % C4);
-    long long q = i / C4;
-    const int ox = (int)(q % W2);
-    q /= W2;
-    const int oy = (int)(q % H2);
-    const int b = (int)(q / H2);
-    const float4* s = reinterpret_cast<const float4*>(x);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= W2 * C4) return;
+  const int ox = e / C4, c4 = e - ox * C4;
+  const float4* s = reinterpret_cast<const float4*>(x);
+  for (int orow = blockIdx.y; orow < B * H2; orow += gridDim.y) {
+    const int oy = orow % H2, b = orow / H2;
     const size_t r0 = (((size_t)b * H + 2 * oy) * W + 2 * ox) * C4 + c4, r1 = r0 + (size_t)W * C4;
     const float4 a0 = s[r0], a1 = s[r0 + C4], a2 = s[r1], a3 = s[r1 + C4];
     const float4 o = make_float4(0.25f * (a0.x + a1.x + a2.x + a3.x), 0.25f * (a0.y + a1.y + a2.y + a3.y),
                                  0.25f * (a0.z + a1.z + a2.z + a3.z), 0.25f * (a0.w + a1.w + a2.w + a3.w));
-    reinterpret_cast<float4*>(y)[i] = o;
+    const size_t i = (size_t)orow * W2 * C4 + e;
+    if (y) reinterpret_cast<float4*>(y)[i] = o;
     if (yb) reinterpret_cast<uint2*>(yb)[i] = make_uint2(pack_bf16(o.x, o.y), pack_bf16(o.z, o.w));
   }
 }
-
 // adjoint of the pooling plus the skip gradient: g[p] = gp[p/2] / 4 + gs[p],
-// zeroed where the ReLU mask mk (if given) is not positive
+// zeroed where the ReLU mask mk (if given) is not positive.  Grid:
+// row_grid(W * C/4, B * H) over g.
 __global__ void __launch_bounds__(kEW) k_avgpool_bwd(const float* __restrict__ gp, const float* __restrict__ gs,
                                                      const float* __restrict__ mk, float* __restrict__ g, int B, int H,
                                                      int W, int C) {
   const int C4 = C / 4;
-  const long long n = (long long)B * H * W * C4;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int c4 = (int)(i % C4);
-    long long q = i / C4;
-    const int x = (int)(q % W);
-    q /= W;
-    const int yy = (int)(q % H);
-    const int b = (int)(q / H);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= W * C4) return;
+  const int x = e / C4, c4 = e - x * C4;
+  for (int row = blockIdx.y; row < B * H; row += gridDim.y) {
+    const int yy = row % H, b = row / H;
+    const size_t i = (size_t)row * W * C4 + e;
     const float4 v = reinterpret_cast<const float4*>(gp)[(((size_t)b * (H / 2) + yy / 2) * (W / 2) + x / 2) * C4 + c4];
     float4 o = make_float4(0.25f * v.x, 0.25f * v.y, 0.25f * v.z, 0.25f * v.w);
     if (gs) {
@@ -951,21 +1019,25 @@ __global__ void __launch_bounds__(kEW) k_avgpool_bwd(const float* __restrict__ g
   }
 }
 
-// nearest 2x upsampling: (B, H, W, C) -> (B, 2H, 2W, C)
+// nearest 2x upsampling: (B, H, W, C) -> (B, 2H, 2W, C); each thread reads
+// one float4 of the input and writes its 2x2 block (FP32 if y is set, BF16
+// if yb is set).  Grid: row_grid(W * C/4, B * H) over the input.
 __global__ void __launch_bounds__(kEW) k_upsample(const float* __restrict__ x, float* __restrict__ y,
                                                   __nv_bfloat16* __restrict__ yb, int B, int H, int W, int C) {
-  const int C4 = C / 4, H2 = 2 * H, W2 = 2 * W;
-  const long long n = (long long)B * H2 * W2 * C4;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int c4 = (int)(i % C4);
-    long long q = i / C4;
-    const int ox = (int)(q % W2);
-    q /= W2;
-    const int oy = (int)(q % H2);
-    const int b = (int)(q / H2);
-    const float4 o = reinterpret_cast<const float4*>(x)[(((size_t)b * H + oy / 2) * W + ox / 2) * C4 + c4];
-    reinterpret_cast<float4*>(y)[i] = o;
-    if (yb) reinterpret_cast<uint2*>(yb)[i] = make_uint2(pack_bf16(o.x, o.y), pack_bf16(o.z, o.w));
+  const int C4 = C / 4;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= W * C4) return;
+  const int ix = e / C4, c4 = e - ix * C4;
+  for (int irow = blockIdx.y; irow < B * H; irow += gridDim.y) {
+    const float4 o = reinterpret_cast<const float4*>(x)[(size_t)irow * W * C4 + e];
+    const uint2 ob = make_uint2(pack_bf16(o.x, o.y), pack_bf16(o.z, o.w));
+    const int iy = irow % H, b = irow / H;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const size_t i = (((size_t)b * 2 * H + 2 * iy + (d >> 1)) * 2 * W + 2 * ix + (d & 1)) * C4 + c4;
+      if (y) reinterpret_cast<float4*>(y)[i] = o;
+      if (yb) reinterpret_cast<uint2*>(yb)[i] = ob;
+    }
   }
 }
 
@@ -1170,7 +1242,6 @@ struct Net {
   float* X0 = nullptr;
   std::vector<float*> ea, eb, pool, upin, upout, da, db;
   // BF16 copies of every convolution input of the forward pass
-  __nv_bfloat16* X0b = nullptr;
   std::vector<__nv_bfloat16*> eab, ebb, poolb, upinb, upoutb, dab;
   std::vector<float*> g_ea, g_eb, g_pool, g_upin, g_upout, g_da, g_db, g_skip;
   float *out = nullptr, *g_out = nullptr, *g_in = nullptr;
@@ -1358,12 +1429,17 @@ bool smem_attrs_set() {
   return ok;
 }
 
+// N tile of the tensor-memory kernel for Cout (0: not eligible)
+int tc_bn(int Cout) {
+  return Cout % 256 == 0 ? 256 : (Cout == 128 || Cout == 64 || Cout == 32) ? Cout : 0;
+}
+
 void launch_conv(const ConvArgs& a, cudaStream_t s, bool force_cp_async = false) {
   const int P = a.B * a.H * a.Wd;
   smem_attrs_set();  // if this failed, the launch below reports the error
   // forward pass on the tensor-memory kernel: N tiles of 32, 64, 128 or 256
   // channels (a power of two: the tensor memory allocation's granularity)
-  const int bn = a.Cout % 256 == 0 ? 256 : (a.Cout == 128 || a.Cout == 64 || a.Cout == 32) ? a.Cout : 0;
+  const int bn = tc_bn(a.Cout);
   if (a.xb1 && a.err && bn) {
     // persistent: one CTA (N tile of 256) or two per SM over all tiles;
     // 64-channel chunks where both inputs split into them
@@ -1423,7 +1499,8 @@ void launch_wgrad(const WgradArgs& a, int bm, int bn, int splits, cudaStream_t s
 
 // forward of one 3x3 layer: y = relu(conv(x1 | x2) + b)
 void conv_fwd(Net& n, int li, const float* x1, const __nv_bfloat16* xb1, int C1, const float* x2,
-              const __nv_bfloat16* xb2, int C2, float* y, __nv_bfloat16* yb, int B, int lv, cudaStream_t s) {
+              const __nv_bfloat16* xb2, int C2, float* y, __nv_bfloat16* yb, int B, int lv, cudaStream_t s,
+              const float* head_x = nullptr, float* head_out = nullptr) {
   const Layer& L = n.layers[li];
   ConvArgs a{};
   a.x1 = x1;
@@ -1444,6 +1521,13 @@ void conv_fwd(Net& n, int li, const float* x1, const __nv_bfloat16* xb1, int C1,
   a.H = n.H >> lv;
   a.Wd = n.W >> lv;
   a.err = n.d_err;
+  if (head_out) {
+    const Layer& Hd = n.layers[head_idx(n)];
+    a.head_w = n.param + Hd.w_off;
+    a.head_b = n.param + Hd.b_off;
+    a.head_x = head_x;
+    a.head_out = head_out;
+  }
   launch_conv(a, s);
 }
 
@@ -1510,18 +1594,26 @@ void refresh_bf16(Net& n, cudaStream_t s) {
     }
 }
 
-void forward_pass(Net& n, const float* x, int B, cudaStream_t s) {
+// forward pass; `train` keeps the FP32 copies that only the backward pass
+// reads (outputs whose forward consumers read their BF16 copies: enc a, the
+// pooled and upsampled maps, dec up and dec a) and the padded FP32 input
+void forward_pass(Net& n, const float* x, int B, cudaStream_t s, bool train) {
   const int P0 = B * n.H * n.W;
-  k_pack_input<<<grid_for(P0), kEW, 0, s>>>(x, n.X0, n.X0b, P0);
-  const float* h = n.X0;
-  const __nv_bfloat16* hb = n.X0b;
-  int hc = 32;
+  if (train) k_pack_input<<<grid_for(P0), kEW, 0, s>>>(x, n.X0, nullptr, P0);
+  {
+    const Layer& L0 = n.layers[enc_a(0)];
+    k_conv_first<<<row_grid(n.W, B * n.H), kEW, 0, s>>>(x, n.wf + L0.bf_off, n.param + L0.b_off,
+                                                        train ? n.ea[0] : nullptr, n.eab[0], B, n.H, n.W, n.c[0]);
+  }
+  const float* h = nullptr;
+  const __nv_bfloat16* hb = nullptr;
+  int hc = 0;
   for (int l = 0; l < n.L; ++l) {
-    conv_fwd(n, enc_a(l), h, hb, hc, nullptr, nullptr, 0, n.ea[l], n.eab[l], B, l, s);
+    if (l > 0) conv_fwd(n, enc_a(l), h, hb, hc, nullptr, nullptr, 0, train ? n.ea[l] : nullptr, n.eab[l], B, l, s);
     conv_fwd(n, enc_b(l), n.ea[l], n.eab[l], n.c[l], nullptr, nullptr, 0, n.eb[l], n.ebb[l], B, l, s);
     if (l < n.L - 1) {
-      const long long cnt = (long long)B * (n.H >> (l + 1)) * (n.W >> (l + 1)) * n.c[l] / 4;
-      k_avgpool<<<grid_for(cnt), kEW, 0, s>>>(n.eb[l], n.pool[l], n.poolb[l], B, n.H >> l, n.W >> l, n.c[l]);
+      k_avgpool<<<row_grid((n.W >> (l + 1)) * n.c[l] / 4, B * (n.H >> (l + 1))), kEW, 0, s>>>(
+          n.eb[l], train ? n.pool[l] : nullptr, n.poolb[l], B, n.H >> l, n.W >> l, n.c[l]);
       h = n.pool[l];
       hb = n.poolb[l];
       hc = n.c[l];
@@ -1529,12 +1621,19 @@ void forward_pass(Net& n, const float* x, int B, cudaStream_t s) {
   }
   h = n.eb[n.L - 1];
   for (int l = n.L - 2; l >= 0; --l) {
-    const long long cnt = (long long)B * (n.H >> l) * (n.W >> l) * n.c[l + 1] / 4;
-    k_upsample<<<grid_for(cnt), kEW, 0, s>>>(h, n.upin[l], n.upinb[l], B, n.H >> (l + 1), n.W >> (l + 1), n.c[l + 1]);
-    conv_fwd(n, dec_up(n, l), n.upin[l], n.upinb[l], n.c[l + 1], nullptr, nullptr, 0, n.upout[l], n.upoutb[l], B, l,
-             s);
-    conv_fwd(n, dec_a(n, l), n.eb[l], n.ebb[l], n.c[l], n.upout[l], n.upoutb[l], n.c[l], n.da[l], n.dab[l], B, l, s);
-    conv_fwd(n, dec_b(n, l), n.da[l], n.dab[l], n.c[l], nullptr, nullptr, 0, n.db[l], nullptr, B, l, s);
+    k_upsample<<<row_grid((n.W >> (l + 1)) * n.c[l + 1] / 4, B * (n.H >> (l + 1))), kEW, 0, s>>>(
+        h, train ? n.upin[l] : nullptr, n.upinb[l], B, n.H >> (l + 1), n.W >> (l + 1), n.c[l + 1]);
+    conv_fwd(n, dec_up(n, l), n.upin[l], n.upinb[l], n.c[l + 1], nullptr, nullptr, 0, train ? n.upout[l] : nullptr,
+             n.upoutb[l], B, l, s);
+    conv_fwd(n, dec_a(n, l), n.eb[l], n.ebb[l], n.c[l], n.upout[l], n.upoutb[l], n.c[l], train ? n.da[l] : nullptr,
+             n.dab[l], B, l, s);
+    // the last layer carries the head in its epilogue where the tensor-memory
+    // kernel takes all c0 channels in one N tile; its output is then read
+    // only by the backward pass
+    const bool fuse = l == 0 && tc_bn(n.c[0]) == n.c[0];
+    conv_fwd(n, dec_b(n, l), n.da[l], n.dab[l], n.c[l], nullptr, nullptr, 0, fuse && !train ? nullptr : n.db[l],
+             nullptr, B, l, s, fuse ? x : nullptr, fuse ? n.out : nullptr);
+    if (fuse) return;
     h = n.db[l];
   }
   const Layer& Hd = n.layers[head_idx(n)];
@@ -1572,9 +1671,8 @@ void backward_pass(Net& n, const float* x, const float* t, int B, cudaStream_t s
   }
   for (int l = n.L - 1; l >= 0; --l) {
     if (l < n.L - 1) {
-      const long long cnt = (long long)B * (n.H >> l) * (n.W >> l) * n.c[l] / 4;
-      k_avgpool_bwd<<<grid_for(cnt), kEW, 0, s>>>(n.g_pool[l], n.g_skip[l], n.eb[l], n.g_eb[l], B, n.H >> l,
-                                                  n.W >> l, n.c[l]);
+      k_avgpool_bwd<<<row_grid((n.W >> l) * n.c[l] / 4, B * (n.H >> l)), kEW, 0, s>>>(
+          n.g_pool[l], n.g_skip[l], n.eb[l], n.g_eb[l], B, n.H >> l, n.W >> l, n.c[l]);
     }
     conv_bwd(n, enc_b(l), n.g_eb[l], n.ea[l], n.c[l], nullptr, 0, n.g_ea[l], nullptr, n.ea[l], nullptr, B, l, s);
     if (l > 0)
@@ -1643,7 +1741,6 @@ extern "C" int cpct_unet_create(cpct_unet** out, int levels, int base, int max_b
   n->upoutb.assign(L, nullptr);
   n->dab.assign(L, nullptr);
   const size_t P0 = (size_t)max_batch * height * width;
-  ok = ok && dalloc(*n, &n->X0b, P0 * 32);
   for (int l = 0; l < L && ok; ++l) {
     const size_t Pl = P0 >> (2 * l), cl = n->c[l];
     ok = dalloc(*n, &n->eab[l], Pl * cl) && dalloc(*n, &n->ebb[l], Pl * cl);
@@ -1775,7 +1872,7 @@ extern "C" int cpct_unet_forward(cpct_unet* net, const float* d_in, float* d_out
   if (!net || !unet_ptr_ok(d_in) || !unet_ptr_ok(d_out)) return CPCT_EINVAL;
   Net& n = *net->net;
   if (batch < 1 || batch > n.maxB) return CPCT_EINVAL;
-  forward_pass(n, d_in, batch, stream);
+  forward_pass(n, d_in, batch, stream, false);
   const size_t P0 = (size_t)batch * n.H * n.W;
   if (cudaMemcpyAsync(d_out, n.out, sizeof(float) * P0, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
     return CPCT_ECUDA;
@@ -1803,7 +1900,7 @@ extern "C" int cpct_unet_backward(cpct_unet* net, const float* d_in, const float
   if (!net || !unet_ptr_ok(d_in) || !unet_ptr_ok(d_target)) return CPCT_EINVAL;
   Net& n = *net->net;
   if (batch < 1 || batch > n.maxB) return CPCT_EINVAL;
-  forward_pass(n, d_in, batch, stream);
+  forward_pass(n, d_in, batch, stream, true);
   backward_pass(n, d_in, d_target, batch, stream);
   if (cudaGetLastError() != cudaSuccess) return CPCT_ECUDA;
   if (loss) {
@@ -1857,6 +1954,39 @@ extern "C" int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm
 //         [Cout][3][3][C1] weights, then Cout biases
 extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, float* d_y, const float* h_w, int B,
                                   int H, int W, int C1, int C2, int Cout, cudaStream_t stream) {
+  if (op == 10) {
+    // first layer: one input channel, weights [Cout][3][3][1] + bias
+    if (!d_a || !d_y || !h_w || B < 1 || H < 1 || W < 1 || C1 != 1 || C2 != 0 || Cout < 8 || Cout % 8 ||
+        Cout > kFirstMaxC)
+      return CPCT_EINVAL;
+    const size_t nw = (size_t)Cout * 9 * 32;
+    std::vector<float> hp(nw + Cout, 0.f);
+    for (int co = 0; co < Cout; ++co)
+      for (int t = 0; t < 9; ++t) hp[((size_t)co * 9 + t) * 32] = h_w[co * 9 + t];
+    for (int co = 0; co < Cout; ++co) hp[nw + co] = h_w[(size_t)Cout * 9 + co];
+    float* dw = nullptr;
+    __nv_bfloat16* bf = nullptr;
+    if (cudaMalloc(&dw, sizeof(float) * (nw + Cout)) != cudaSuccess) return CPCT_ENOMEM;
+    if (cudaMalloc(&bf, sizeof(__nv_bfloat16) * 2 * nw) != cudaSuccess) {
+      cudaFree(dw);
+      return CPCT_ENOMEM;
+    }
+    int rc = cudaMemcpyAsync(dw, hp.data(), sizeof(float) * hp.size(), cudaMemcpyHostToDevice, stream) == cudaSuccess
+                 ? CPCT_OK
+                 : CPCT_ECUDA;
+    if (rc == CPCT_OK) {
+      k_weights_bf16<<<grid_for((long long)nw), kEW, 0, stream>>>(dw, bf, bf + nw, Cout, 32);
+      __nv_bfloat16* yb = nullptr;
+      if (cudaMalloc(&yb, sizeof(__nv_bfloat16) * B * H * W * Cout) != cudaSuccess) rc = CPCT_ENOMEM;
+      if (rc == CPCT_OK)
+        k_conv_first<<<row_grid(W, B * H), kEW, 0, stream>>>(d_a, bf, dw + nw, d_y, yb, B, H, W, Cout);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
+      if (yb) cudaFree(yb);
+    }
+    cudaFree(bf);
+    cudaFree(dw);
+    return rc;
+  }
   if (!d_a || !d_y || B < 1 || H < 1 || W < 1 || C1 < 1 || C1 % 32 || C2 < 0 || C2 % 32) return CPCT_EINVAL;
   if (op == 6) {
     if (!d_b || C2 != 0 || Cout < 32 || Cout % 32) return CPCT_EINVAL;
@@ -1977,13 +2107,13 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
   const long long n4 = (long long)B * H * W * C1 / 4;
   switch (op) {
     case 1:
-      k_avgpool<<<grid_for(n4 / 4), kEW, 0, stream>>>(d_a, d_y, nullptr, B, H, W, C1);
+      k_avgpool<<<row_grid((W / 2) * C1 / 4, B * (H / 2)), kEW, 0, stream>>>(d_a, d_y, nullptr, B, H, W, C1);
       break;
     case 2:
-      k_upsample<<<grid_for(n4 * 4), kEW, 0, stream>>>(d_a, d_y, nullptr, B, H, W, C1);
+      k_upsample<<<row_grid(W * C1 / 4, B * H), kEW, 0, stream>>>(d_a, d_y, nullptr, B, H, W, C1);
       break;
     case 3:
-      k_avgpool_bwd<<<grid_for(n4), kEW, 0, stream>>>(d_a, d_b, nullptr, d_y, B, H, W, C1);
+      k_avgpool_bwd<<<row_grid(W * C1 / 4, B * H), kEW, 0, stream>>>(d_a, d_b, nullptr, d_y, B, H, W, C1);
       break;
     case 4:
       k_upsample_bwd<<<grid_for(n4), kEW, 0, stream>>>(d_a, nullptr, d_y, B, H, W, C1);

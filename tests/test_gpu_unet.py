@@ -218,6 +218,25 @@ def test_conv_tc_parity(torch_cuda, C1, C2, Cout, B, H, W):
         assert np.max(np.abs(_nchw(y) - yo)) <= tol
 
 
+@pytest.mark.parametrize("Cout,B,H,W", [(32, 2, 9, 13), (64, 1, 32, 32), (8, 3, 5, 7)])
+def test_first_conv_op_parity(torch_cuda, Cout, B, H, W):
+    """The network's first layer (one input channel, direct kernel) against
+    the oracle with the same bfloat16 operand rounding."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    rng = np.random.default_rng(500 + Cout + H)
+    x = rng.standard_normal((B, H, W)).astype(np.float32)
+    Wt = rng.standard_normal((Cout, 3, 3, 1)) * np.sqrt(2.0 / 9)
+    bias = 0.1 * rng.standard_normal(Cout)
+    hw = np.concatenate([Wt.ravel(), bias]).astype(np.float32)
+    y = cpct.unet_debug_op(10, torch.from_numpy(x).cuda(), None, (B, H, W, Cout), w=hw, C1=1, C2=0,
+                           Cout=Cout).cpu().numpy()
+    q = unet.bf16_round
+    yo = unet.relu(unet.conv(q(x.astype(np.float64))[:, None], q(Wt.astype(np.float32)),
+                             bias.astype(np.float32).astype(np.float64)))
+    assert np.max(np.abs(_nchw(y) - yo)) <= 1e-6 * np.max(np.abs(yo))
+
+
 @pytest.mark.parametrize("C1,Cout,H,W", [(32, 32, 9, 13), (64, 128, 8, 8), (128, 64, 4, 4), (32, 64, 40, 24)])
 def test_wgrad_op_parity(torch_cuda, C1, Cout, H, W):
     torch = torch_cuda
