@@ -331,6 +331,55 @@ def spgl1_bench(args, torch, cpct, synth):
                       f"<= {c['iterations']} iterations, opt_tol 1e-4, ring filter"}
 
 
+def denoiser_flops(levels, base, n):
+    """Multiply-add FLOPs of one forward pass of the denoiser on an n x n
+    image: every 3x3 layer at its level's resolution, and the 1x1 head."""
+    from paper_1009_1380_gb300 import warmstart as ws
+    shapes = ws.layer_shapes(levels, base)
+    f = 0.0
+    for i, (co, ci, k) in enumerate(shapes):
+        if i < 2 * levels:
+            lv = i // 2
+        elif i < len(shapes) - 1:
+            lv = levels - 2 - (i - 2 * levels) // 3
+        else:
+            lv = 0
+        f += 2.0 * k * k * ci * co * (n >> lv) ** 2
+    return f
+
+
+def denoiser_bench(args, torch, cpct, runs=10):
+    """Inference of the learned warm start's denoiser (row a12): 5 levels, 32
+    base channels, 512^2 images, a batch of args.unet_batch; images/s of the
+    forward pass (tcgen05 convolutions) with the L2 flushed between runs, and
+    the FLOP rate it implies."""
+    from paper_1009_1380_gb300 import warmstart as ws
+    levels, base, n, B = 5, 32, 512, args.unet_batch
+    net = cpct.UNet(levels, base, B, n, n)
+    net.set_params(ws.he_init(levels, base, seed=7))
+    x = torch.from_numpy(np.random.default_rng(0).standard_normal((B, n, n)).astype(np.float32)).cuda()
+    out = torch.empty_like(x)
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")
+    for _ in range(3):
+        net.forward(x, out)
+    net.sync()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(runs)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        net.forward(x, out)
+        b.record(stream)
+    torch.cuda.synchronize()
+    net.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / runs
+    net.close()
+    flops = denoiser_flops(levels, base, n) * B
+    return {"metric": "denoiser inference images/s", "value": B / (ms / 1000.0), "unit": "images/s",
+            "ms_per_batch": ms, "batch": B, "tflops": flops / (ms / 1000.0) / 1e12, "dtype": "bf16 x bf16 -> f32",
+            "workload": f"U-Net {levels} levels, {base} base channels, {B} x {n}x{n} images, random weights"}
+
+
 def max_over_ranks(x, dist=None, device="cpu"):
     """The maximum of a per-rank float over all ranks (x itself for one rank)."""
     if dist is None:
@@ -471,6 +520,8 @@ def run_ours(args, rank, world, local_rank):
         out["batch"] = batch_bench(args, torch, cpct, synth)
     if world == 1 and args.spgl1_batch > 0:
         out["spgl1"] = spgl1_bench(args, torch, cpct, synth)
+    if world == 1 and args.unet_batch > 0:
+        out["denoiser"] = denoiser_bench(args, torch, cpct)
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -487,14 +538,16 @@ def main():
     ap.add_argument("--spgl1-batch", type=int, default=64, help="slices of the SPGL1 workload (0: skip)")
     ap.add_argument("--batch-slices", type=int, default=256, help="slices of the batched-operator workload (0: skip)")
     ap.add_argument("--spgl1-iters", type=int, default=0, help="override the SPGL1 iteration cap (0: 300)")
-    ap.add_argument("--only", default="", choices=["", "spgl1", "batch"], help="run one secondary workload alone")
+    ap.add_argument("--unet-batch", type=int, default=32, help="images of the denoiser workload (0: skip)")
+    ap.add_argument("--only", default="", choices=["", "spgl1", "batch", "unet"],
+                    help="run one secondary workload alone")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.only in ("spgl1", "batch"):
+    elif args.only in ("spgl1", "batch", "unet"):
         import torch
         from paper_1009_1380_gb300 import build as b
         b.build()
@@ -502,6 +555,8 @@ def main():
         torch.cuda.set_device(local_rank)
         if args.only == "spgl1":
             print(json.dumps(spgl1_bench(args, torch, cpct, synth)), flush=True)
+        elif args.only == "unet":
+            print(json.dumps(denoiser_bench(args, torch, cpct)), flush=True)
         else:
             print(json.dumps(batch_bench(args, torch, cpct, synth)), flush=True)
     else:
