@@ -690,13 +690,31 @@ __global__ void __launch_bounds__(tc_threads<TMA>(), BN >= 256 ? 1 : 2)
 #pragma unroll
             for (int i = 0; i < 16; ++i) hs = fmaf(a.head_w[n + i], v[i], hs);
           }
-          if (a.y1) {
-            float4* dst = reinterpret_cast<float4*>(a.y1 + (size_t)m * a.Cout + n);
+          // channels [0, O1) go to y1 (row stride O1), [O1, Cout) to y2
+          // (stride Cout - O1); an optional ReLU mask of the same layout
+          // zeroes an output where it is not positive
+          const bool first = n < a.O1;
+          const size_t off = first ? (size_t)m * a.O1 + n : (size_t)m * (a.Cout - a.O1) + (n - a.O1);
+          const float* mk = first ? a.om1 : a.om2;
+          if (mk) {
+            const float4* mv = reinterpret_cast<const float4*>(mk + off);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float4 q = mv[i];
+              v[4 * i] = q.x > 0.f ? v[4 * i] : 0.f;
+              v[4 * i + 1] = q.y > 0.f ? v[4 * i + 1] : 0.f;
+              v[4 * i + 2] = q.z > 0.f ? v[4 * i + 2] : 0.f;
+              v[4 * i + 3] = q.w > 0.f ? v[4 * i + 3] : 0.f;
+            }
+          }
+          float* yo = first ? a.y1 : a.y2;
+          if (yo) {
+            float4* dst = reinterpret_cast<float4*>(yo + off);
 #pragma unroll
             for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
           }
-          if (a.yb1) {
-            uint4* db = reinterpret_cast<uint4*>(a.yb1 + (size_t)m * a.Cout + n);
+          if (a.yb1 && first) {
+            uint4* db = reinterpret_cast<uint4*>(a.yb1 + off);
             db[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
                                pack_bf16(v[6], v[7]));
             db[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
@@ -1124,6 +1142,15 @@ __global__ void __launch_bounds__(kEW) k_to_bf16(const float* __restrict__ x, __
     y[i] = __float2bfloat16_rn(x[i]);
 }
 
+// the same conversion, four elements per thread (n a multiple of 4)
+__global__ void __launch_bounds__(kEW) k_to_bf16x4(const float4* __restrict__ x, uint2* __restrict__ y,
+                                                   long long n4) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = x[i];
+    y[i] = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+  }
+}
+
 // dz = dy where y > 0, else 0
 __global__ void __launch_bounds__(kEW) k_relu_mask(const float* __restrict__ dy, const float* __restrict__ y,
                                                    float* __restrict__ dz, long long n) {
@@ -1252,6 +1279,7 @@ struct Net {
   double* d_gnorm = nullptr;     // ||g|| of the last Adam step
   float* d_gscale = nullptr;     // clipping factor of the last Adam step
   int* d_err = nullptr;          // device error flag (CPCT_ERR_* bits)
+  __nv_bfloat16* gradb = nullptr;  // BF16 copy of the gradient entering a data-gradient convolution
   int last_batch = 0;
 };
 
@@ -1545,6 +1573,15 @@ void conv_bwd(Net& n, int li, const float* dz, const float* x1, int C1, const fl
     ConvArgs a{};
     a.x1 = dz;
     a.x2 = nullptr;
+    if (tc_bn(C1 + C2)) {
+      // tensor-memory kernel on a BF16 copy of dz (the rounding the FP32
+      // kernel applies while staging); the largest dz is level 0's P0 x c0
+      const long long nz4 = P * L.cout / 4;
+      k_to_bf16x4<<<grid_for(nz4), kEW, 0, s>>>(reinterpret_cast<const float4*>(dz), reinterpret_cast<uint2*>(n.gradb),
+                                                 nz4);
+      a.xb1 = n.gradb;
+      a.err = n.d_err;
+    }
     a.C1 = L.cout;
     a.C2 = 0;
     a.W = n.wt + L.bf_off;
@@ -1750,7 +1787,7 @@ extern "C" int cpct_unet_create(cpct_unet** out, int levels, int base, int max_b
   }
   ok = ok && dalloc(*n, &n->X0, P0 * 32) && dalloc(*n, &n->out, P0) && dalloc(*n, &n->g_out, P0) &&
        dalloc(*n, &n->loss_part, 1024) && dalloc(*n, &n->norm_part, 152 * 16) && dalloc(*n, &n->d_gnorm, 1) &&
-       dalloc(*n, &n->d_gscale, 1) && dalloc(*n, &n->d_err, 1);
+       dalloc(*n, &n->d_gscale, 1) && dalloc(*n, &n->d_err, 1) && dalloc(*n, &n->gradb, P0 * n->c[0]);
   for (int l = 0; l < L && ok; ++l) {
     const size_t Pl = P0 >> (2 * l), cl = n->c[l];
     ok = dalloc(*n, &n->ea[l], Pl * cl) && dalloc(*n, &n->eb[l], Pl * cl) && dalloc(*n, &n->g_ea[l], Pl * cl) &&
@@ -2019,9 +2056,10 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
     cudaFree(part);
     return rc;
   }
-  if (op == 0 || op == 5 || op == 7 || op == 8 || op == 9) {
-    if (!h_w || Cout < 32 || Cout % 32 || (op == 5 && !d_b)) return CPCT_EINVAL;
-    if (op >= 8 && !(Cout % 256 == 0 || Cout == 128 || Cout == 64 || Cout == 32)) return CPCT_EINVAL;
+  if (op == 0 || op == 5 || op == 7 || op == 8 || op == 9 || op == 11) {
+    if (!h_w || Cout < 32 || Cout % 32 || ((op == 5 || op == 11) && !d_b)) return CPCT_EINVAL;
+    if ((op == 8 || op == 9) && !tc_bn(Cout)) return CPCT_EINVAL;
+    if (op == 11 && (C2 != 0 || !tc_bn(C1))) return CPCT_EINVAL;
     const int Cin = C1 + C2;
     const size_t nw = (size_t)Cout * 9 * Cin;
     float* dw = nullptr;
@@ -2078,6 +2116,17 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
         if (cudaMalloc(&dz, sizeof(float) * nz) != cudaSuccess) rc = CPCT_ENOMEM;
         if (rc == CPCT_OK) {
           k_relu_mask<<<grid_for(nz), kEW, 0, stream>>>(d_a, d_b, dz, nz);
+          if (op == 11) {
+            // tensor-memory kernel on the BF16 copy of dz
+            if (cudaMalloc(&xb, sizeof(__nv_bfloat16) * nz) != cudaSuccess ||
+                cudaMalloc(&derr, sizeof(int)) != cudaSuccess || cudaMemsetAsync(derr, 0, sizeof(int), stream) != cudaSuccess)
+              rc = CPCT_ENOMEM;
+            if (rc == CPCT_OK)
+              k_to_bf16x4<<<grid_for(nz / 4), kEW, 0, stream>>>(reinterpret_cast<const float4*>(dz),
+                                                                reinterpret_cast<uint2*>(xb), nz / 4);
+            a.xb1 = xb;
+            a.err = derr;
+          }
           a.x1 = dz;
           a.C1 = Cout;
           a.C2 = 0;
@@ -2085,12 +2134,12 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
           a.y1 = d_y;
           a.O1 = Cin;
           a.Cout = Cin;
-          launch_conv(a, stream);
+          if (rc == CPCT_OK) launch_conv(a, stream);
           if (cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
           cudaFree(dz);
         }
       }
-      if (rc == CPCT_OK && (op == 0 || op >= 7)) launch_conv(a, stream, op == 9);
+      if (rc == CPCT_OK && (op == 0 || op == 7 || op == 8 || op == 9)) launch_conv(a, stream, op == 9);
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(stream) != cudaSuccess) rc = CPCT_ECUDA;
       if (derr) {
         int e = 0;

@@ -133,7 +133,7 @@ def _nchw(a):
 
 
 @pytest.mark.parametrize("C1,C2,Cout,H,W", [(32, 0, 32, 9, 13), (64, 0, 128, 8, 8), (32, 32, 32, 16, 16),
-                                            (64, 64, 64, 8, 8)])
+                                            (64, 64, 64, 8, 8), (32, 0, 64, 16, 32)])
 def test_conv_op_parity(torch_cuda, C1, C2, Cout, H, W):
     """One convolution (and its data gradient) against the oracle with the
     same bfloat16 operand rounding: FP32 against FP64 accumulation."""
@@ -171,6 +171,15 @@ def test_conv_op_parity(torch_cuda, C1, C2, Cout, H, W):
     e = _rel(_nchw(gd), gx)
     print("dgrad", e)
     assert e < 1e-5
+    if C2 == 0:
+        # the tensor-memory kernel on the BF16 copy of the masked gradient
+        g11 = cpct.unet_debug_op(11, torch.from_numpy(_nhwc(gy)).cuda(),
+                                 torch.from_numpy(_nhwc(yo.astype(np.float32))).cuda(), (B, H, W, C1), w=hw, C1=C1,
+                                 C2=0, Cout=Cout).cpu().numpy()
+        e = _rel(_nchw(g11), gx)
+        print("dgrad tcgen05", e)
+        assert e < 1e-5
+        assert np.max(np.abs(g11 - gd)) <= 1e-5 * np.max(np.abs(gd))
 
 
 @pytest.mark.parametrize("C1,C2,Cout,B,H,W", [
