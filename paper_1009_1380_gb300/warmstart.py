@@ -322,7 +322,10 @@ def _summary(infos, wall, t_net):
             "slices_per_s": roots / wall if wall > 0 else None, "iterations_mean": float(its.mean()),
             "iterations_median": float(np.median(its)), "iterations_max": int(its.max()),
             "ticks_mean": float(np.mean([f["ticks"] for f in infos])),
-            "ticks_max": int(max(f["ticks"] for f in infos))}
+            "ticks_max": int(max(f["ticks"] for f in infos)),
+            # line-search trials (accepted or not); ticks - trials are the
+            # bookkeeping ticks (the first, and one or two per Newton update)
+            "trials_mean": float(np.mean([f["trials"] for f in infos]))}
 
 
 INFER_BATCH = 32  # images per forward call at inference (deep levels fill the GPU)

@@ -56,3 +56,17 @@ def test_single_rank_is_identity():
     b = _bench()
     assert b.max_over_ranks(3.0) == 3.0
     assert b.aggregate_rate(1, 10.0, 2.0) == 5.0
+
+
+def test_denoiser_flops_against_the_oracle_layer_list():
+    """The FLOP count behind the denoiser line, recounted from the oracle's
+    layer list: each layer's level from its name (encoder 'enc{l}', decoder
+    'dec{l}'), 2 k^2 Cin Cout multiply-adds per pixel of that level."""
+    from oracle import unet
+    b = _bench()
+    for levels, base, n in [(5, 32, 512), (3, 64, 128), (1, 32, 64)]:
+        ref = 0.0
+        for name, co, ci, k in unet.layer_specs(levels, base):
+            lv = int(name[3:].split(".")[0]) if name != "head" else 0
+            ref += 2.0 * k * k * ci * co * (n >> lv) ** 2
+        assert b.denoiser_flops(levels, base, n) == ref
