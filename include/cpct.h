@@ -359,6 +359,8 @@ int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm, double* g
  *         BF16 operands as op 0.  CPCT_ETIMEOUT if a bounded wait of the
  *         kernel expired.
  *   op 9: op 8 with the cp.async gathers whatever the shape.
+ *   op 12: op 6 computed by the weight-gradient kernel that reads BF16 copies
+ *         of a and b (the network's backward pass).
  *   op 11: op 5 computed by the tensor-memory kernel on a BF16 copy of the
  *         masked gradient (the network's backward pass; C2 = 0, C1 in {32,
  *         64, 128} or a multiple of 256).
@@ -366,8 +368,8 @@ int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm, double* g
  *         single-channel a (B x H x W, C1 = 1, C2 = 0), w = [Cout][3][3][1]
  *         then the Cout biases, Cout a multiple of 8 up to 1024: the direct
  *         kernel (BF16 operands, FP32 accumulation in tap order).
- * C1, C2 multiples of 32 (C1 > 0), Cout a multiple of 32 for ops 0, 5-9, 11.
- * Synchronous; allocates a workspace for ops 0 and 5-11. */
+ * C1, C2 multiples of 32 (C1 > 0), Cout a multiple of 32 for ops 0, 5-9, 11, 12.
+ * Synchronous; allocates a workspace for ops 0 and 5-12. */
 int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, float* d_y, const float* h_w, int B, int H, int W,
                        int C1, int C2, int Cout, cudaStream_t stream);
 

@@ -746,6 +746,10 @@ struct WgradArgs {
   const float* dz;   // [P][Cout] gradient of the layer's pre-activation
   const float* x1;   // layer input channels [0, C1)
   const float* x2;   // channels [C1, C1 + C2)
+  // BF16 copies (read by the BF16 kernel instead of dz, x1, x2)
+  const __nv_bfloat16* dzb;
+  const __nv_bfloat16* xb1;
+  const __nv_bfloat16* xb2;
   int C1, C2, Cout;
   int B, H, Wd;
   int chunks_per_split;  // 32-pixel chunks per split
@@ -877,6 +881,120 @@ __global__ void __launch_bounds__((BM / 16) * (BN / 16) * 32) k_conv3x3_wgrad(co
           make_float2(acc[j][2 * h], acc[j][2 * h + 1]);
     }
   }
+}
+
+// The weight gradient from BF16 copies of dZ and of the layer input: cp.async
+// copies the 16-byte chunks straight into the XOR-swizzled [pixel][channel]
+// tiles that ldmatrix.trans reads (a 4-stage pipeline, one barrier per
+// chunk of 32 pixels), every warp a 32 x 32 block of (co, ci).  The same
+// BF16 operands and the same K order per split as the FP32-input kernel.
+constexpr int kStagesW = 4;
+template <int BM, int BN>
+constexpr size_t wgrad_smem_b16() {
+  return (size_t)kStagesW * kBK * (BM + BN) * 2;
+}
+template <int BM, int BN>
+__global__ void __launch_bounds__((BM / 32) * (BN / 32) * 32) k_conv3x3_wgrad_b16(const WgradArgs a) {
+  constexpr int WN = BN / 32, NTH = (BM / 32) * WN * 32;
+  constexpr int CA = BM / 8, CB = BN / 8;  // 16-byte chunks per row
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint32_t* sA = reinterpret_cast<uint32_t*>(smraw);  // [kStagesW][kBK][BM] bf16
+  uint32_t* sB = sA + kStagesW * kBK * BM / 2;        // [kStagesW][kBK][BN] bf16
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp / WN, wn = warp % WN;
+  const int Cin = a.C1 + a.C2, ctiles = Cin / BN;
+  const int m0 = blockIdx.x * BM;
+  const int tap = blockIdx.y / ctiles, ci0 = (blockIdx.y % ctiles) * BN;
+  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int HW = a.H * a.Wd, P = a.B * HW;
+  const int c_begin = blockIdx.z * a.chunks_per_split;
+  const int c_end = min(c_begin + a.chunks_per_split, (P + kBK - 1) / kBK);
+  const __nv_bfloat16* xs = ci0 < a.C1 ? a.xb1 : a.xb2;
+  const int xc = ci0 < a.C1 ? a.C1 : a.C2, xo = ci0 < a.C1 ? ci0 : ci0 - a.C1;
+  auto load_stage = [&](int ch, int st) {
+    const int p0 = ch * kBK;
+    uint32_t* da = sA + (size_t)st * kBK * BM / 2;
+    uint32_t* db = sB + (size_t)st * kBK * BN / 2;
+    for (int idx = tid; idx < kBK * CA; idx += NTH) {
+      const int r = idx / CA, c = idx % CA, p = p0 + r;
+      const bool ok = p < P;
+      const __nv_bfloat16* src = ok ? a.dzb + (size_t)p * a.Cout + m0 + 8 * c : a.dzb;
+      cp_async16_zfill(smem_u32(da + 4 * swz<CA>(r, c)), src, ok);
+    }
+    for (int idx = tid; idx < kBK * CB; idx += NTH) {
+      const int r = idx / CB, c = idx % CB, p = p0 + r;
+      bool ok = p < P;
+      const __nv_bfloat16* src = xs;
+      if (ok) {
+        const int b = p / HW, rem = p - b * HW;
+        const int py = rem / a.Wd + dy, px = rem % a.Wd + dx;
+        ok = py >= 0 && py < a.H && px >= 0 && px < a.Wd;
+        if (ok) src = xs + (((size_t)b * a.H + py) * a.Wd + px) * xc + xo + 8 * c;
+      }
+      cp_async16_zfill(smem_u32(db + 4 * swz<CB>(r, c)), src, ok);
+    }
+  };
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  const int nch = max(0, c_end - c_begin);
+#pragma unroll
+  for (int st = 0; st < kStagesW - 1; ++st) {
+    if (st < nch) load_stage(c_begin + st, st);
+    cp_async_commit();
+  }
+  for (int k = 0; k < nch; ++k) {
+    cp_async_wait<kStagesW - 2>();
+    __syncthreads();  // chunk k landed for every thread; chunk k - 1 fully consumed
+    {
+      const int nx = k + kStagesW - 1;
+      if (nx < nch) load_stage(c_begin + nx, nx % kStagesW);
+      cp_async_commit();
+    }
+    const uint32_t* sAc = sA + (size_t)(k % kStagesW) * kBK * BM / 2;
+    const uint32_t* sBc = sB + (size_t)(k % kStagesW) * kBK * BN / 2;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int q = lane >> 3;
+      uint32_t af[2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int kk = ks * 16 + (lane & 7) + ((q >> 1) << 3);
+        const int c = wm * 4 + i * 2 + (q & 1);
+        ldsm_x4_t(smem_u32(sAc + 4 * swz<CA>(kk, c)), af[i][0], af[i][1], af[i][2], af[i][3]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        const int kk = ks * 16 + (lane & 7) + ((q & 1) << 3);
+        const int c = wn * 4 + jj * 2 + (q >> 1);
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4_t(smem_u32(sBc + 4 * swz<CB>(kk, c)), b0, b1, b2, b3);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          mma_bf16(acc[i][2 * jj], af[i], b0, b1);
+          mma_bf16(acc[i][2 * jj + 1], af[i], b2, b3);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  float* dst = a.part + (size_t)blockIdx.z * a.Cout * 9 * Cin;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int co = m0 + wm * 32 + i * 16 + (lane >> 2) + h * 8;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int ci = ci0 + wn * 32 + j * 8 + 2 * (lane & 3);
+        *reinterpret_cast<float2*>(dst + ((size_t)co * 9 + tap) * Cin + ci) =
+            make_float2(acc[i][j][2 * h], acc[i][j][2 * h + 1]);
+      }
+    }
 }
 
 // out[i] (+)= sum_s part[s][i], s in order (deterministic split reduction)
@@ -1348,13 +1466,18 @@ void free_net(Net* n) {
 // the largest split-partial buffer any layer needs (floats)
 // tiles of the weight gradient (an N tile must not straddle the two input
 // tensors of a concatenation) and the split of the pixel reduction
-size_t wgrad_splits(int cout, int c1, int c2, long long P, int* bm, int* bn, int* splits, int* cps) {
+// tiles and pixel splits of a weight gradient: enough CTAs for about 32
+// warps per SM (warps per CTA: (BM/16)(BN/16) for the FP32-input kernel,
+// (BM/32)(BN/32) for the BF16 one)
+size_t wgrad_splits(int cout, int c1, int c2, long long P, int* bm, int* bn, int* splits, int* cps, bool b16 = true) {
   const int cin = c1 + c2;
   *bm = cout % 64 == 0 ? 64 : 32;
   *bn = (c1 % 64 == 0 && c2 % 64 == 0) ? 64 : 32;
   const long long tiles = (long long)(cout / *bm) * 9 * (cin / *bn);
+  const long long warps = b16 ? (*bm / 32) * (*bn / 32) : (*bm / 16) * (*bn / 16);
   const long long chunks = (P + kBK - 1) / kBK;
-  long long s = std::max<long long>(1, std::min<long long>((4LL * 152 + tiles - 1) / tiles, chunks));
+  const long long want = (32LL * 152 + tiles * warps - 1) / (tiles * warps);
+  long long s = std::max<long long>(1, std::min<long long>(want, chunks));
   const long long per = (chunks + s - 1) / s;
   s = (chunks + per - 1) / per;
   *splits = (int)s;
@@ -1515,6 +1638,15 @@ void launch_conv(const ConvArgs& a, cudaStream_t s, bool force_cp_async = false)
   }
 }
 
+void launch_wgrad_b16(const WgradArgs& a, int bm, int bn, int splits, cudaStream_t s) {
+  const int Cin = a.C1 + a.C2;
+  dim3 grid(a.Cout / bm, 9 * (Cin / bn), splits);
+  if (bm == 64 && bn == 64) k_conv3x3_wgrad_b16<64, 64><<<grid, 4 * 32, wgrad_smem_b16<64, 64>(), s>>>(a);
+  else if (bm == 64) k_conv3x3_wgrad_b16<64, 32><<<grid, 2 * 32, wgrad_smem_b16<64, 32>(), s>>>(a);
+  else if (bn == 64) k_conv3x3_wgrad_b16<32, 64><<<grid, 2 * 32, wgrad_smem_b16<32, 64>(), s>>>(a);
+  else k_conv3x3_wgrad_b16<32, 32><<<grid, 32, wgrad_smem_b16<32, 32>(), s>>>(a);
+}
+
 void launch_wgrad(const WgradArgs& a, int bm, int bn, int splits, cudaStream_t s) {
   const int Cin = a.C1 + a.C2;
   smem_attrs_set();
@@ -1564,21 +1696,29 @@ void conv_fwd(Net& n, int li, const float* x1, const __nv_bfloat16* xb1, int C1,
 // mask (om1 / om2, the ReLU output it lands on) is not positive, so it is
 // again a pre-activation gradient -- and the weight and bias gradients into
 // n.grad
-void conv_bwd(Net& n, int li, const float* dz, const float* x1, int C1, const float* x2, int C2, float* dx1,
-              float* dx2, const float* om1, const float* om2, int B, int lv, cudaStream_t s) {
+// backward of one 3x3 layer: data gradient (if dx1) and weight / bias
+// gradients; xb1 / xb2 are the BF16 copies of the layer's inputs (null: the
+// FP32-input weight-gradient kernel)
+void conv_bwd(Net& n, int li, const float* dz, const float* x1, const __nv_bfloat16* xb1, int C1, const float* x2,
+              const __nv_bfloat16* xb2, int C2, float* dx1, float* dx2, const float* om1, const float* om2, int B,
+              int lv, cudaStream_t s) {
   const Layer& L = n.layers[li];
   const int H = n.H >> lv, W = n.W >> lv;
   const long long P = (long long)B * H * W;
+  const bool tc_dgrad = dx1 && tc_bn(C1 + C2);
+  const bool b16_wgrad = xb1 && (C2 == 0 || xb2);
+  if (tc_dgrad || b16_wgrad) {
+    // a BF16 copy of dz (the rounding the FP32 kernels apply while
+    // staging); the largest dz is level 0's P0 x c0
+    const long long nz4 = P * L.cout / 4;
+    k_to_bf16x4<<<grid_for(nz4), kEW, 0, s>>>(reinterpret_cast<const float4*>(dz), reinterpret_cast<uint2*>(n.gradb),
+                                               nz4);
+  }
   if (dx1) {
     ConvArgs a{};
     a.x1 = dz;
     a.x2 = nullptr;
-    if (tc_bn(C1 + C2)) {
-      // tensor-memory kernel on a BF16 copy of dz (the rounding the FP32
-      // kernel applies while staging); the largest dz is level 0's P0 x c0
-      const long long nz4 = P * L.cout / 4;
-      k_to_bf16x4<<<grid_for(nz4), kEW, 0, s>>>(reinterpret_cast<const float4*>(dz), reinterpret_cast<uint2*>(n.gradb),
-                                                 nz4);
+    if (tc_dgrad) {
       a.xb1 = n.gradb;
       a.err = n.d_err;
     }
@@ -1599,11 +1739,14 @@ void conv_bwd(Net& n, int li, const float* dz, const float* x1, int C1, const fl
     launch_conv(a, s);
   }
   int bm, bn, splits, cps;
-  wgrad_splits(L.cout, C1, C2, P, &bm, &bn, &splits, &cps);
+  wgrad_splits(L.cout, C1, C2, P, &bm, &bn, &splits, &cps, b16_wgrad);
   WgradArgs w{};
   w.dz = dz;
   w.x1 = x1;
   w.x2 = x2;
+  w.dzb = n.gradb;
+  w.xb1 = xb1;
+  w.xb2 = xb2;
   w.C1 = C1;
   w.C2 = C2;
   w.Cout = L.cout;
@@ -1612,7 +1755,10 @@ void conv_bwd(Net& n, int li, const float* dz, const float* x1, int C1, const fl
   w.Wd = W;
   w.chunks_per_split = cps;
   w.part = n.part;
-  launch_wgrad(w, bm, bn, splits, s);
+  if (b16_wgrad)
+    launch_wgrad_b16(w, bm, bn, splits, s);
+  else
+    launch_wgrad(w, bm, bn, splits, s);
   const long long nw = (long long)L.cout * 9 * (C1 + C2);
   k_split_sum<<<grid_for(nw), kEW, 0, s>>>(n.part, splits, nw, n.grad + L.w_off, 0);
   // bias: per-channel sums of dz over pixel ranges, then the fixed-order sum
@@ -1694,12 +1840,13 @@ void backward_pass(Net& n, const float* x, const float* t, int B, cudaStream_t s
     k_split_sum<<<grid_for(n.c[0] + 1), kEW, 0, s>>>(n.part, sp, n.c[0] + 1, n.grad + Hd.w_off, 0);
   }
   for (int l = 0; l <= n.L - 2; ++l) {
-    conv_bwd(n, dec_b(n, l), n.g_db[l], n.da[l], n.c[l], nullptr, 0, n.g_da[l], nullptr, n.da[l], nullptr, B, l, s);
+    conv_bwd(n, dec_b(n, l), n.g_db[l], n.da[l], n.dab[l], n.c[l], nullptr, nullptr, 0, n.g_da[l], nullptr, n.da[l],
+             nullptr, B, l, s);
     // the skip part is summed with the pooled path before its mask applies
-    conv_bwd(n, dec_a(n, l), n.g_da[l], n.eb[l], n.c[l], n.upout[l], n.c[l], n.g_skip[l], n.g_upout[l], nullptr,
-             n.upout[l], B, l, s);
-    conv_bwd(n, dec_up(n, l), n.g_upout[l], n.upin[l], n.c[l + 1], nullptr, 0, n.g_upin[l], nullptr, nullptr, nullptr,
-             B, l, s);
+    conv_bwd(n, dec_a(n, l), n.g_da[l], n.eb[l], n.ebb[l], n.c[l], n.upout[l], n.upoutb[l], n.c[l], n.g_skip[l],
+             n.g_upout[l], nullptr, n.upout[l], B, l, s);
+    conv_bwd(n, dec_up(n, l), n.g_upout[l], n.upin[l], n.upinb[l], n.c[l + 1], nullptr, nullptr, 0, n.g_upin[l],
+             nullptr, nullptr, nullptr, B, l, s);
     float* gnext = l + 1 <= n.L - 2 ? n.g_db[l + 1] : n.g_eb[n.L - 1];
     const float* mnext = l + 1 <= n.L - 2 ? n.db[l + 1] : n.eb[n.L - 1];
     const long long cnt = (long long)B * (n.H >> (l + 1)) * (n.W >> (l + 1)) * n.c[l + 1] / 4;
@@ -1711,12 +1858,14 @@ void backward_pass(Net& n, const float* x, const float* t, int B, cudaStream_t s
       k_avgpool_bwd<<<row_grid((n.W >> l) * n.c[l] / 4, B * (n.H >> l)), kEW, 0, s>>>(
           n.g_pool[l], n.g_skip[l], n.eb[l], n.g_eb[l], B, n.H >> l, n.W >> l, n.c[l]);
     }
-    conv_bwd(n, enc_b(l), n.g_eb[l], n.ea[l], n.c[l], nullptr, 0, n.g_ea[l], nullptr, n.ea[l], nullptr, B, l, s);
+    conv_bwd(n, enc_b(l), n.g_eb[l], n.ea[l], n.eab[l], n.c[l], nullptr, nullptr, 0, n.g_ea[l], nullptr, n.ea[l],
+             nullptr, B, l, s);
     if (l > 0)
-      conv_bwd(n, enc_a(l), n.g_ea[l], n.pool[l - 1], n.c[l - 1], nullptr, 0, n.g_pool[l - 1], nullptr, nullptr,
-               nullptr, B, l, s);
+      conv_bwd(n, enc_a(l), n.g_ea[l], n.pool[l - 1], n.poolb[l - 1], n.c[l - 1], nullptr, nullptr, 0,
+               n.g_pool[l - 1], nullptr, nullptr, nullptr, B, l, s);
     else
-      conv_bwd(n, enc_a(0), n.g_ea[0], n.X0, 32, nullptr, 0, nullptr, nullptr, nullptr, nullptr, B, 0, s);
+      conv_bwd(n, enc_a(0), n.g_ea[0], n.X0, nullptr, 32, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, B,
+               0, s);
   }
 }
 
@@ -1808,7 +1957,9 @@ extern "C" int cpct_unet_create(cpct_unet** out, int levels, int base, int max_b
     const Layer& Ly = n->layers[li];
     if (Ly.k != 3) continue;
     int bm, bn, sp, cps;
-    part = std::max(part, wgrad_splits(Ly.cout, Ly.c1, Ly.c2, (long long)(P0 >> (2 * Ly.lv)), &bm, &bn, &sp, &cps));
+    for (const bool b16 : {false, true})
+      part = std::max(part,
+                      wgrad_splits(Ly.cout, Ly.c1, Ly.c2, (long long)(P0 >> (2 * Ly.lv)), &bm, &bn, &sp, &cps, b16));
     const long long Pl = (long long)(P0 >> (2 * Ly.lv));
     part = std::max(part, (size_t)((Pl + colsum_rows(Pl) - 1) / colsum_rows(Pl)) * (size_t)Ly.cout);
   }
@@ -2025,15 +2176,27 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
     return rc;
   }
   if (!d_a || !d_y || B < 1 || H < 1 || W < 1 || C1 < 1 || C1 % 32 || C2 < 0 || C2 % 32) return CPCT_EINVAL;
-  if (op == 6) {
+  if (op == 6 || op == 12) {
     if (!d_b || C2 != 0 || Cout < 32 || Cout % 32) return CPCT_EINVAL;
     const long long P = (long long)B * H * W;
+    const bool b16 = op == 12;
     int bm, bn, sp, cps;
-    size_t need = wgrad_splits(Cout, C1, 0, P, &bm, &bn, &sp, &cps);
+    size_t need = wgrad_splits(Cout, C1, 0, P, &bm, &bn, &sp, &cps, b16);
     const int rows = (int)colsum_rows(P), csp = (int)((P + rows - 1) / rows);
     need = std::max(need, (size_t)csp * Cout);
     float* part = nullptr;
     if (cudaMalloc(&part, sizeof(float) * need) != cudaSuccess) return CPCT_ENOMEM;
+    __nv_bfloat16* cb = nullptr;  // op 12: BF16 copies of x (P x C1) and dz (P x Cout)
+    if (b16) {
+      if (cudaMalloc(&cb, sizeof(__nv_bfloat16) * P * (C1 + Cout)) != cudaSuccess) {
+        cudaFree(part);
+        return CPCT_ENOMEM;
+      }
+      k_to_bf16x4<<<grid_for(P * C1 / 4), kEW, 0, stream>>>(reinterpret_cast<const float4*>(d_a),
+                                                             reinterpret_cast<uint2*>(cb), P * C1 / 4);
+      k_to_bf16x4<<<grid_for(P * Cout / 4), kEW, 0, stream>>>(reinterpret_cast<const float4*>(d_b),
+                                                               reinterpret_cast<uint2*>(cb + P * C1), P * Cout / 4);
+    }
     WgradArgs w{};
     w.dz = d_b;
     w.x1 = d_a;
@@ -2046,13 +2209,19 @@ extern "C" int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, fl
     w.Wd = W;
     w.chunks_per_split = cps;
     w.part = part;
-    launch_wgrad(w, bm, bn, sp, stream);
+    w.xb1 = cb;
+    w.dzb = cb ? cb + P * C1 : nullptr;
+    if (b16)
+      launch_wgrad_b16(w, bm, bn, sp, stream);
+    else
+      launch_wgrad(w, bm, bn, sp, stream);
     const long long nw = (long long)Cout * 9 * C1;
     k_split_sum<<<grid_for(nw), kEW, 0, stream>>>(part, sp, nw, d_y, 0);
     dim3 cg((Cout + 31) / 32, csp);
     k_colsum<<<cg, kEW, 0, stream>>>(d_b, nullptr, (int)P, Cout, rows, part);
     k_split_sum<<<grid_for(Cout), kEW, 0, stream>>>(part, csp, Cout, d_y + nw, 0);
     const int rc = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(stream) == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+    if (cb) cudaFree(cb);
     cudaFree(part);
     return rc;
   }

@@ -264,6 +264,13 @@ def test_wgrad_op_parity(torch_cuda, C1, Cout, H, W):
     e_b = _rel(y[Cout * 9 * C1:], gb)
     print("wgrad", e_w, "bias", e_b)
     assert e_w < 1e-5 and e_b < 1e-5
+    # the kernel that reads BF16 copies of both operands (32 x 32 warp tiles)
+    y12 = cpct.unet_debug_op(12, torch.from_numpy(_nhwc(x)).cuda(), torch.from_numpy(_nhwc(gy)).cuda(),
+                             (Cout * 9 * C1 + Cout,), C1=C1, Cout=Cout).cpu().numpy()
+    e_w = _rel(y12[:Cout * 9 * C1], gW.ravel())
+    print("wgrad bf16", e_w)
+    assert e_w < 1e-5
+    assert np.array_equal(y12[Cout * 9 * C1:], y[Cout * 9 * C1:])
 
 
 def test_pool_upsample_ops(torch_cuda):
