@@ -46,7 +46,9 @@ def _hash_files(files) -> str:
         h.update(os.path.basename(f).encode())  # names, not paths: equal on every machine
         with open(f, "rb") as fh:
             h.update(fh.read())
-    h.update(" ".join(NVCC_FLAGS).encode())
+    # flags with the include directories by name: the repository's location
+    # differs between machines
+    h.update(" ".join(os.path.basename(f) if os.path.isabs(f) else f for f in NVCC_FLAGS).encode())
     return h.hexdigest()
 
 

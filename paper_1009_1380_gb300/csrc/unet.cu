@@ -7,12 +7,21 @@
 //   * activations and their gradients: FP32, NHWC (channel fastest);
 //   * weights: FP32 master copy (Adam), BF16 copies in [Cout][3][3][Cin]
 //     (forward) and [Cin][3][3][Cout] with flipped taps (data gradient);
-//   * every 3x3 convolution is an implicit GEMM on the tensor cores
-//     (BF16 x BF16 -> FP32, mma.sync m16n8k16): activation tiles are
-//     converted to BF16 while they are staged in shared memory, and the
-//     accumulation stays FP32;
-//   * the level-0 input is stored with 32 channels (channel 0 = image), so
-//     every GEMM reduction chunk is 32 channels of one tap.
+//   * every 3x3 convolution is an implicit GEMM with BF16 operands and FP32
+//     accumulation.  Forward and data-gradient convolutions run on the
+//     fifth-generation tensor cores (k_conv3x3_tc: TMA operand boxes,
+//     tcgen05.mma into tensor memory, persistent and warp-specialized);
+//     they read BF16 copies that the producers of their inputs write beside
+//     the FP32 tensors.  Weight gradients run on mma.sync m16n8k16 from the
+//     same BF16 copies.  The FP32-staging mma.sync kernels remain for shapes
+//     the others do not take;
+//   * the first layer (one input channel) is a direct kernel; for its weight
+//     gradient the training pass stores the input with 32 channels
+//     (channel 0 = image), so every GEMM reduction chunk is 32 channels of
+//     one tap;
+//   * inference (cpct_unet_forward) skips the FP32 copies that only the
+//     backward pass reads, and computes the 1x1 head in the last
+//     convolution's epilogue.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
