@@ -132,6 +132,22 @@ int radon_fbp(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t s
 int radon_fwd_host(cpct_plan* plan, const float* h_img, float* h_sino, cudaStream_t stream);
 int radon_adj_host(cpct_plan* plan, const float* h_sino, float* h_img, cudaStream_t stream);
 
+/* The operator pair over `count` slices in host memory, pipelined (the
+ * operators of sections "Gridding" and "Inverse gridding" applied slice by
+ * slice):
+ *   h_sinos[i] = R h_imgs[i]   (radon_fwd: N x N in, M x Ns out)
+ *   h_outs[i]  = R^H h_sinos[i] (radon_adj of the device-resident sinogram)
+ * Two device buffer sets alternate: slice i + 1's image is copied in and
+ * slice i - 1's results are copied out (on two streams of the call's own)
+ * while slice i's operators run on `stream`.  Host buffers are the
+ * caller's; with pinned memory the copies overlap the kernels (pageable
+ * memory works, without overlap).  Output buffers of different slices may
+ * coincide (the copies into them are ordered).  Synchronous: returns once
+ * every result is in host memory.  CPCT_EINVAL for null arguments or
+ * count < 1, CPCT_ENOMEM if the two buffer sets cannot be allocated. */
+int radon_pair_host_stream(cpct_plan* plan, const float* const* h_imgs, float* const* h_sinos,
+                           float* const* h_outs, int count, cudaStream_t stream);
+
 /* ---- many slices: clones, autotuner, batches ----------------------------- */
 
 /* A new plan for the same geometry as `src` that shares src's read-only

@@ -64,6 +64,7 @@ def lib():
                                      ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t)]
         for name in ("radon_fwd", "radon_adj", "radon_fbp", "radon_fwd_host", "radon_adj_host", "radon_adj_noalloc"):
             getattr(L, name).argtypes = [vp, vp, vp, vp]
+        L.radon_pair_host_stream.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
         L.cpct_strerror.restype = ctypes.c_char_p
         L.cpct_strerror.argtypes = [i]
         L.cpct_debug_bins.argtypes = [ctypes.POINTER(Geom), i, ctypes.POINTER(i), ctypes.POINTER(i),
@@ -197,6 +198,31 @@ class Plan:
         check(lib().radon_adj_host(self._h, sino.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
                                    _stream(self._torch, stream)), "radon_adj_host")
         return out
+
+    def pair_host_stream(self, imgs, sinos=None, outs=None, stream=None):
+        """Forward and adjoint of every image in `imgs` (host float32 arrays,
+        N x N), pipelined with the host<->device copies (radon_pair_host_stream);
+        returns (sinos, outs), host arrays (given or new).  Pinned buffers let
+        the copies overlap the kernels."""
+        count = len(imgs)
+        imgs = [np.ascontiguousarray(a, dtype=np.float32) for a in imgs]
+        for a in imgs:
+            if a.shape != (self.n, self.n):
+                raise ValueError(f"image shape {a.shape}, expected {(self.n, self.n)}")
+        if sinos is None:
+            sinos = [np.empty((self.n_views, self.n_det), dtype=np.float32) for _ in range(count)]
+        if outs is None:
+            outs = [np.empty((self.n, self.n), dtype=np.float32) for _ in range(count)]
+        for a, shape in [(x, (self.n_views, self.n_det)) for x in sinos] + [(x, (self.n, self.n)) for x in outs]:
+            if a.shape != shape or a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("output arrays must be C-contiguous float32 of the operator's shapes")
+        vp = ctypes.c_void_p
+        P = (vp * count)(*[a.ctypes.data for a in imgs])
+        S = (vp * count)(*[a.ctypes.data for a in sinos])
+        O = (vp * count)(*[a.ctypes.data for a in outs])
+        check(lib().radon_pair_host_stream(self._h, P, S, O, count, _stream(self._torch, stream)),
+              "radon_pair_host_stream")
+        return sinos, outs
 
     def profile_enable(self, mask=0x1FF):
         check(lib().cpct_profile_enable(self._h, ctypes.c_uint(mask)), "cpct_profile_enable")

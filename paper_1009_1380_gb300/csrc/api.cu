@@ -67,6 +67,67 @@ extern "C" int radon_adj_host(cpct_plan* p, const float* h_sino, float* h_img, c
   return CPCT_OK;
 }
 
+extern "C" int radon_pair_host_stream(cpct_plan* p, const float* const* h_imgs, float* const* h_sinos,
+                                      float* const* h_outs, int count, cudaStream_t s) {
+  if (!p || !h_imgs || !h_sinos || !h_outs || count < 1) return CPCT_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (!h_imgs[i] || !h_sinos[i] || !h_outs[i]) return CPCT_EINVAL;
+  const size_t ni = (size_t)p->n * p->n, ns = (size_t)p->m * p->ns;
+  const size_t bi = sizeof(float) * ni, bs = sizeof(float) * ns;
+  // two buffer sets (image, sinogram, adjoint) of sizes multiple of 16 bytes
+  float* buf = nullptr;
+  cudaStream_t up = nullptr, down = nullptr;
+  cudaEvent_t ev[4][2] = {};  // uploaded, forward done, adjoint done, downloaded
+  int rc = CPCT_OK;
+  auto ok = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == CPCT_OK) rc = CPCT_ECUDA;
+    return rc == CPCT_OK;
+  };
+  if (cudaMalloc(&buf, 2 * (2 * bi + bs)) != cudaSuccess) return CPCT_ENOMEM;
+  if (ok(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking)) &&
+      ok(cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking))) {
+    for (auto& e2 : ev)
+      for (auto& e : e2)
+        if (!ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) break;
+  }
+  enum { IN = 0, FWD = 1, ADJ = 2, OUT = 3 };
+  for (int i = 0; i < count && rc == CPCT_OK; ++i) {
+    const int k = i & 1;
+    float* img = buf + k * (2 * ni + ns);
+    float* sino = img + ni;
+    float* out = sino + ns;
+    // upload: the image buffer is free once slice i - 2's forward has read it
+    if (i >= 2 && !ok(cudaStreamWaitEvent(up, ev[FWD][k], 0))) break;
+    if (!ok(cudaMemcpyAsync(img, h_imgs[i], bi, cudaMemcpyHostToDevice, up))) break;
+    if (!ok(cudaEventRecord(ev[IN][k], up))) break;
+    // operators: after the upload, and once slice i - 2's downloads have
+    // read this set's sinogram and adjoint buffers
+    if (!ok(cudaStreamWaitEvent(s, ev[IN][k], 0))) break;
+    if (i >= 2 && !ok(cudaStreamWaitEvent(s, ev[OUT][k], 0))) break;
+    if ((rc = cpct_launch_fwd(p, img, sino, s)) != CPCT_OK) break;
+    if (!ok(cudaEventRecord(ev[FWD][k], s))) break;
+    if ((rc = cpct_launch_adj(p, sino, out, s)) != CPCT_OK) break;
+    if (!ok(cudaEventRecord(ev[ADJ][k], s))) break;
+    // downloads: the sinogram while the adjoint runs, then the adjoint
+    if (!ok(cudaStreamWaitEvent(down, ev[FWD][k], 0))) break;
+    if (!ok(cudaMemcpyAsync(h_sinos[i], sino, bs, cudaMemcpyDeviceToHost, down))) break;
+    if (!ok(cudaStreamWaitEvent(down, ev[ADJ][k], 0))) break;
+    if (!ok(cudaMemcpyAsync(h_outs[i], out, bi, cudaMemcpyDeviceToHost, down))) break;
+    if (!ok(cudaEventRecord(ev[OUT][k], down))) break;
+  }
+  // everything issued has finished before the buffers are released
+  if (down) ok(cudaStreamSynchronize(down));
+  if (up) ok(cudaStreamSynchronize(up));
+  ok(cudaStreamSynchronize(s));
+  for (auto& e2 : ev)
+    for (auto& e : e2)
+      if (e) cudaEventDestroy(e);
+  if (up) cudaStreamDestroy(up);
+  if (down) cudaStreamDestroy(down);
+  cudaFree(buf);
+  return rc;
+}
+
 extern "C" const char* cpct_strerror(int status) {
   switch (status) {
     case CPCT_OK: return "ok";

@@ -179,6 +179,32 @@ def test_host_variants_match_device(torch_cuda):
     np.testing.assert_array_equal(z_h, z_d.astype(np.float32))
 
 
+def test_pair_host_stream_matches_device(torch_cuda):
+    """The pipelined host-buffer pair (two device buffer sets, copies on
+    their own streams) equals the device operators slice by slice, bit for
+    bit, with distinct and with shared output buffers."""
+    torch = torch_cuda
+    n, m, count = 128, 90, 5
+    p = _plan(n, n, m)
+    rng = np.random.default_rng(21)
+    imgs = [rng.standard_normal((n, n)).astype(np.float32) for _ in range(count)]
+    sinos, outs = p.pair_host_stream(imgs)
+    for i in range(count):
+        y_d = p.fwd(torch.from_numpy(imgs[i]).cuda())
+        z_d = p.adj(y_d)
+        np.testing.assert_array_equal(sinos[i], y_d.cpu().numpy())
+        np.testing.assert_array_equal(outs[i], z_d.cpu().numpy())
+    # one output buffer pair for every slice: the last slice's results remain
+    s1 = np.empty((m, n), dtype=np.float32)
+    o1 = np.empty((n, n), dtype=np.float32)
+    p.pair_host_stream(imgs, [s1] * count, [o1] * count)
+    np.testing.assert_array_equal(s1, sinos[-1])
+    np.testing.assert_array_equal(o1, outs[-1])
+    # a single slice
+    s2, o2 = p.pair_host_stream(imgs[:1])
+    np.testing.assert_array_equal(o2[0], outs[0])
+
+
 def test_errors(torch_cuda):
     torch = torch_cuda
     from paper_1009_1380_gb300 import cpct
