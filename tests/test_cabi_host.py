@@ -106,3 +106,23 @@ def test_unet_param_count_matches_oracle(cpct):
         assert cpct.unet_param_count(levels, base) == want
     assert cpct.unet_param_count(0, 32) == -1
     assert cpct.unet_param_count(3, 16) == -1
+
+
+def test_host_stream_rejects_bad_arguments_before_any_device_work(cpct):
+    """radon_pair_host_stream validates its arguments on the host: a null
+    plan, null pointer arrays, a null slice pointer or count < 1 return
+    CPCT_EINVAL (-1) before any CUDA call."""
+    import ctypes
+    L = cpct.lib()
+    vp = ctypes.c_void_p
+    L.radon_pair_host_stream.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.c_int, vp]
+    buf = np.zeros(16, dtype=np.float32)
+    one = (vp * 1)(buf.ctypes.data)
+    nul = (vp * 1)(None)
+    fake_plan = vp(1)  # never dereferenced: the checks below fail first
+    assert L.radon_pair_host_stream(None, one, one, one, 1, None) == -1
+    assert L.radon_pair_host_stream(fake_plan, None, one, one, 1, None) == -1
+    assert L.radon_pair_host_stream(fake_plan, one, one, one, 0, None) == -1
+    assert L.radon_pair_host_stream(fake_plan, nul, one, one, 1, None) == -1
+    assert L.radon_pair_host_stream(fake_plan, one, one, nul, 1, None) == -1
