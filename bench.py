@@ -187,6 +187,7 @@ class OracleTimer:
         y = nf.ray_idft(P).real
         nf.grid_spread(nf.ray_idft_adj(y), self.geo, rays)
         t = time.perf_counter() - t0
+        self.last = (rays, y)  # the oracle's forward rays of this step
         return t + self.t_fft * rays_per_step / self.m, rays_per_step * self.ns
 
     def time_per_ray(self):
@@ -194,16 +195,25 @@ class OracleTimer:
         return (t - self.t_fft * 4 / self.m) / 4
 
 
-def cpu_baseline(workload, budget_s=20.0):
+def cpu_baseline(workload, budget_s=20.0, gpu_sino=None):
+    """The FP64 oracle timed on a bounded sample of rays; with the GPU's
+    sinogram of the same image (gpu_sino, host array), also the relative L2
+    error of the GPU forward over the sampled rays against the oracle's."""
     ot = OracleTimer(workload)
     per_ray = ot.time_per_ray()
     rays = int(max(1, min(ot.m, budget_s / max(per_ray, 1e-6))))
     t, samples = ot.step(rays)
-    return {"value": samples / t / 1e6, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 oracle (NumPy, single-threaded): fwd+adj gridding of {rays} of {ot.m} rays of "
-                       f"the {ot.n}x{ot.n} workload, plus {rays}/{ot.m} of the measured oversampled 2D FFT + "
-                       f"inverse FFT time ({ot.t_fft:.2f} s per full pair)"),
-            "seconds": t}
+    out = {"value": samples / t / 1e6, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
+           "sample": (f"FP64 oracle (NumPy, single-threaded): fwd+adj gridding of {rays} of {ot.m} rays of "
+                      f"the {ot.n}x{ot.n} workload, plus {rays}/{ot.m} of the measured oversampled 2D FFT + "
+                      f"inverse FFT time ({ot.t_fft:.2f} s per full pair)"),
+           "seconds": t}
+    if gpu_sino is not None:
+        idx, y_ref = ot.last
+        d = np.asarray(gpu_sino, dtype=np.float64)[idx] - y_ref
+        out["parity"] = {"fwd_rel_l2": float(np.linalg.norm(d) / np.linalg.norm(y_ref)), "rays": int(len(idx)),
+                         "against": "FP64 gridding oracle (same W, sigma, beta), the timed sample's rays"}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -515,7 +525,7 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed": t_wall,
     }
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.workload)
+        out["cpu_baseline"] = cpu_baseline(args.workload, gpu_sino=y.cpu().numpy())
     if world == 1:
         out["paper_workload"] = paper_workload(torch, cpct, synth)
     if world == 1 and args.batch_slices > 0:
