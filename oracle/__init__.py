@@ -21,6 +21,8 @@ Modules
 ``unet``      the convolutional denoiser of the learned warm start (no
               counterpart in the paper): forward pass and hand-written
               backward pass in FP64.
+``synthesis`` the horizontal finite-difference synthesis operator of the
+              analysis-l1 variant (u = C z, its adjoint and its inverse).
 
 Parity status of every function is listed in its module header.
 """
