@@ -125,6 +125,19 @@ int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t s
  * start.  Same arguments, layout and errors as radon_adj. */
 int radon_fbp(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream);
 
+/* The finite-difference synthesis operator of the analysis-l1 variant.  The
+ * paper puts the l1 norm on the phase-contrast image itself (a Laplacian of
+ * the object, sections "Introduction" and "Phase contrast"); the variant
+ * puts it on the horizontal differences z of a piecewise-constant image u
+ * through u = C z (prefix sums along every row: C inverts z[p, 0] = u[p, 0],
+ * z[p, q] = u[p, q] - u[p, q - 1]).
+ *   adjoint = 0: d_out = C d_in     (u[p, q] = sum_{q' <= q} z[p, q'])
+ *   adjoint = 1: d_out = C^T d_in   (sum_{q' >= q} of every row)
+ * d_in, d_out: device, n x n float32 row-major (row = y); in place allowed;
+ * FP32 sums.  n <= 4096.  Stream-ordered, asynchronous.  CPCT_EINVAL for
+ * null pointers, n out of range or adjoint not 0 / 1. */
+int cpct_synth_dh(const float* d_in, float* d_out, int n, int adjoint, cudaStream_t stream);
+
 /* Host-buffer variants: copy h_in (pinned or pageable host memory) to a
  * plan-owned device staging buffer, run the operator, copy the result back
  * to h_out and synchronize `stream`.  For end-to-end timing and for callers
@@ -211,6 +224,10 @@ typedef struct spgl1_opts {
 
 #define CPCT_SPGL1_TAU0 0x1       /* start from opts->tau0 instead of ||x0||_1  */
 #define CPCT_SPGL1_NO_FILTER 0x2  /* solve with A = R (no ring filter)          */
+#define CPCT_SPGL1_SYNTH_DH 0x4   /* analysis-l1 variant: x is z, the operator  */
+                                  /* acts on u = C z (cpct_synth_dh), so the    */
+                                  /* solve is min ||z||_1 s.t.                  */
+                                  /* ||F(R C z) - F b|| <= sigma; u = C x after */
 
 /* Result record of one solve. status: 1 root found (| ||r|| - sigma | <=
  * opt_tol max(1, ||F b||) at a solved or stagnant LASSO subproblem),

@@ -285,6 +285,7 @@ def debug_rounds(n, n_det, n_views, angles=None):
 # ---------------------------------------------------------------------------
 SPGL1_TAU0 = 0x1
 SPGL1_NO_FILTER = 0x2
+SPGL1_SYNTH_DH = 0x4
 SPGL1_STATUS = {1: "root found", 2: "basis pursuit solution", 3: "iteration cap", 4: "line search failure",
                 5: "non-finite"}
 
@@ -356,12 +357,30 @@ def project_l1(v, tau, out=None, stream=None):
     return out, th.value
 
 
-def make_opts(max_iter=0, opt_tol=0.0, bp_tol=0.0, memory=0, max_line=0, tau0=None, ring_filter=True):
+def make_opts(max_iter=0, opt_tol=0.0, bp_tol=0.0, memory=0, max_line=0, tau0=None, ring_filter=True,
+              synth_dh=False):
+    """SPGL1 options (0 = default).  synth_dh: the analysis-l1 variant, the
+    solution is z with the image u = synth_dh(z)."""
     o = Spgl1Opts()
     o.max_iter, o.opt_tol, o.bp_tol, o.memory, o.max_line = max_iter, opt_tol, bp_tol, memory, max_line
-    o.flags = (0 if ring_filter else SPGL1_NO_FILTER) | (SPGL1_TAU0 if tau0 is not None else 0)
+    o.flags = ((0 if ring_filter else SPGL1_NO_FILTER) | (SPGL1_TAU0 if tau0 is not None else 0)
+               | (SPGL1_SYNTH_DH if synth_dh else 0))
     o.tau0 = 0.0 if tau0 is None else float(tau0)
     return o
+
+
+def synth_dh(x, adjoint=False, out=None, stream=None):
+    """u = C x (row prefix sums) or C^T x (row suffix sums) of an N x N float32
+    CUDA tensor (cpct_synth_dh)."""
+    import torch
+    L = lib()
+    L.cpct_synth_dh.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty_like(x)
+    check(L.cpct_synth_dh(_dev_ptr(x, (n, n), torch), _dev_ptr(out, (n, n), torch), n, 1 if adjoint else 0,
+                          _stream(torch, stream)), "cpct_synth_dh")
+    return out
 
 
 def ring_filter(plan, sino, out=None, stream=None):

@@ -812,6 +812,81 @@ __global__ void __launch_bounds__(kRB) k_spg_final(SpgVec V) {
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// finite-difference synthesis operator of the analysis-l1 variant
+// ---------------------------------------------------------------------------
+// u = C z: prefix sums along every image row (C inverts the horizontal
+// difference z[p, 0] = u[p, 0], z[p, q] = u[p, q] - u[p, q - 1]); its adjoint
+// C^T w: suffix sums along every row.  One CTA per row (grid-stride over
+// rows), thread t owns `per` consecutive positions in scan order (from the
+// row's end for the adjoint); FP32 sums: the thread's run, then a warp and a
+// block scan of the run totals.  In place allowed: every thread writes only
+// the positions it has read, after the block's scan barrier.
+constexpr int kScanT = 256;
+constexpr int kScanMaxPer = 16;  // rows of up to 4096 values
+__global__ void __launch_bounds__(kScanT) k_synth_rows(const float* __restrict__ in, float* __restrict__ out, int n,
+                                                      int rows, int adjoint, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ float wsum[kScanT / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int per = (n + kScanT - 1) / kScanT;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const float* src = in + (size_t)row * n;
+    float* dst = out + (size_t)row * n;
+    float v[kScanMaxPer];
+    float run = 0.f;
+#pragma unroll
+    for (int i = 0; i < kScanMaxPer; ++i) {
+      const int q = t * per + i;
+      v[i] = 0.f;
+      if (i < per && q < n) v[i] = src[adjoint ? n - 1 - q : q];
+      run += v[i];
+    }
+    float x = run;  // inclusive scan of the run totals within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      float y = lane < kScanT / 32 ? wsum[lane] : 0.f;
+#pragma unroll
+      for (int o = 1; o < kScanT / 32; o <<= 1) {
+        const float u = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += u;
+      }
+      if (lane < kScanT / 32) wsum[lane] = y;
+    }
+    __syncthreads();
+    float acc = (x - run) + (w > 0 ? wsum[w - 1] : 0.f);  // exclusive prefix of this thread's run
+#pragma unroll
+    for (int i = 0; i < kScanMaxPer; ++i) {
+      const int q = t * per + i;
+      if (i < per && q < n) {
+        acc += v[i];
+        dst[adjoint ? n - 1 - q : q] = acc;
+      }
+    }
+    __syncthreads();  // wsum is reused by the next row
+  }
+}
+
+void launch_synth(const float* in, float* out, int n, int adjoint, const int* skip, cudaStream_t s) {
+  k_synth_rows<<<n < 4096 ? n : 4096, kScanT, 0, s>>>(in, out, n, n, adjoint, skip);
+}
+
+}  // namespace
+
+extern "C" int cpct_synth_dh(const float* d_in, float* d_out, int n, int adjoint, cudaStream_t stream) {
+  if (!d_in || !d_out || n < 1 || n > kScanT * kScanMaxPer || (adjoint != 0 && adjoint != 1)) return CPCT_EINVAL;
+  launch_synth(d_in, d_out, n, adjoint, nullptr, stream);
+  return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -826,6 +901,7 @@ struct SliceWork {
   RingWork ring;
   cudaStream_t stream = nullptr;
   float* mem = nullptr;
+  float* ubuf = nullptr;  // u = C xt of the analysis-l1 variant (within mem)
 };
 
 void enqueue_tick(SliceWork& w, int filter) {
@@ -836,7 +912,13 @@ void enqueue_tick(SliceWork& w, int filter) {
     k_spg_radix_select<<<1, kRB, 0, s>>>(V, pass);
   }
   k_spg_proj_apply<<<kRG, kRB, 0, s>>>(V);
-  cpct_launch_fwd_skip(w.plan, V.xt, V.y, &V.st->skip_fwd, s);
+  if (w.ubuf) {
+    // analysis-l1 variant: the operator acts on u = C xt
+    launch_synth(V.xt, w.ubuf, w.plan->n, 0, &V.st->skip_fwd, s);
+    cpct_launch_fwd_skip(w.plan, w.ubuf, V.y, &V.st->skip_fwd, s);
+  } else {
+    cpct_launch_fwd_skip(w.plan, V.xt, V.y, &V.st->skip_fwd, s);
+  }
   if (filter) {
     k_ring_colmean<<<(w.plan->ns + 31) / 32, kRB, 0, s>>>(V.y, w.ring.m, w.plan->m, w.plan->ns);
     k_ring_offset<<<1, kRB, 0, s>>>(w.ring.Q, w.ring.m, w.ring.d, w.plan->ns);
@@ -845,11 +927,12 @@ void enqueue_tick(SliceWork& w, int filter) {
   k_spg_mid<<<1, kRB, 0, s>>>(V);
   k_spg_accept<<<kRG, kRB, 0, s>>>(V);
   cpct_launch_adj_ramp(w.plan, V.r, V.gtmp, 0.f, &V.st->skip_adj, s);
+  if (w.ubuf) launch_synth(V.gtmp, V.gtmp, w.plan->n, 1, &V.st->skip_adj, s);  // C^T R^T F r
   k_spg_grad<<<kRG, kRB, 0, s>>>(V);
   k_spg_end<<<1, kRB, 0, s>>>(V);
 }
 
-int fill_opts(const spgl1_opts* o, SpgState& st, double* tau0, int* filter) {
+int fill_opts(const spgl1_opts* o, SpgState& st, double* tau0, int* filter, int* synth) {
   st.max_iter = (o && o->max_iter > 0) ? o->max_iter : 300;
   st.opt_tol = (o && o->opt_tol > 0) ? o->opt_tol : 1e-4;
   st.bp_tol = (o && o->bp_tol > 0) ? o->bp_tol : 1e-6;
@@ -861,6 +944,7 @@ int fill_opts(const spgl1_opts* o, SpgState& st, double* tau0, int* filter) {
   if (st.memory > kHist) return CPCT_EINVAL;
   *tau0 = (o && (o->flags & CPCT_SPGL1_TAU0)) ? o->tau0 : -1.0;
   *filter = (o && (o->flags & CPCT_SPGL1_NO_FILTER)) ? 0 : 1;
+  *synth = (o && (o->flags & CPCT_SPGL1_SYNTH_DH)) ? 1 : 0;
   return CPCT_OK;
 }
 
@@ -872,8 +956,8 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
   SpgState proto;
   std::memset(&proto, 0, sizeof(proto));
   double tau0 = -1.0;
-  int filter = 1;
-  int rc = fill_opts(opts, proto, &tau0, &filter);
+  int filter = 1, synth = 0;
+  int rc = fill_opts(opts, proto, &tau0, &filter, &synth);
   if (rc) return rc;
   for (int i = 0; i < batch; ++i) {
     if (!plans[i] || !d_b[i] || !d_x[i] || !(sigma[i] >= 0.0)) return CPCT_EINVAL;
@@ -909,7 +993,11 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
     w.b = d_b[i];
     w.sigma = sigma[i];
     const long long n = (long long)w.plan->n * w.plan->n, m = (long long)w.plan->m * w.plan->ns;
-    if (!cuda(cudaMalloc(&w.mem, sizeof(float) * (5 * n + 4 * m)))) goto done;
+    if (synth && w.plan->n > kScanT * kScanMaxPer) {
+      rc = CPCT_EINVAL;
+      goto done;
+    }
+    if (!cuda(cudaMalloc(&w.mem, sizeof(float) * ((synth ? 6 : 5) * n + 4 * m)))) goto done;
     SpgVec& V = w.V;
     V.n = n;
     V.m = m;
@@ -923,6 +1011,7 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
     V.rt = V.y + m;
     V.r = V.rt + m;
     V.bf = V.r + m;
+    w.ubuf = synth ? V.bf + m : nullptr;
     V.part = d_part + (size_t)i * P_TOTAL * kRG;
     V.hcnt = reinterpret_cast<unsigned*>(d_hist) + (size_t)i * kBins;
     V.hsum = reinterpret_cast<unsigned long long*>(d_hist + sizeof(unsigned) * kBins * batch) + (size_t)i * kBins;
