@@ -145,6 +145,7 @@ def train(net, fbp, target, epochs, batch, lr, seed=0, log=None):
             norms.append(net.adam_step(lr_t, max_grad_norm=clip, return_norm=True))
             nb += 1
             step += 1
+        net.sync()  # raises if a bounded device wait of the epoch's passes expired
         losses.append(tot / max(nb, 1))
         if log:
             log(f"epoch {ep}: loss {losses[-1]:.4e}")
@@ -168,6 +169,7 @@ def predict(net, fbp, batch):
     for g in range(0, fbp.shape[0], batch):
         k = min(batch, fbp.shape[0] - g)
         net.forward(inp[g:g + k], out=out[g:g + k])
+    net.sync()  # raises if a bounded device wait of a forward pass expired
     return out * s
 
 
