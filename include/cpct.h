@@ -152,7 +152,10 @@ int radon_adj_host(cpct_plan* plan, const float* h_sino, float* h_img, cudaStrea
  *   h_outs[i]  = R^H h_sinos[i] (radon_adj of the device-resident sinogram)
  * Two device buffer sets alternate: slice i + 1's image is copied in and
  * slice i - 1's results are copied out (on two streams of the call's own)
- * while slice i's operators run on `stream`.  Host buffers are the
+ * while slice i's operators run; the sets' operators run on `stream` with
+ * `plan` and on a stream of the call's own with a clone of `plan` (the same
+ * tables, its own workspaces, made and freed by the call; if the clone
+ * cannot be made, both sets use `plan` on `stream`).  Host buffers are the
  * caller's; with pinned memory the copies overlap the kernels (pageable
  * memory works, without overlap).  Output buffers of different slices may
  * coincide (the copies into them are ordered).  Synchronous: returns once

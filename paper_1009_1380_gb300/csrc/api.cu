@@ -74,9 +74,12 @@ extern "C" int radon_pair_host_stream(cpct_plan* p, const float* const* h_imgs, 
     if (!h_imgs[i] || !h_sinos[i] || !h_outs[i]) return CPCT_EINVAL;
   const size_t ni = (size_t)p->n * p->n, ns = (size_t)p->m * p->ns;
   const size_t bi = sizeof(float) * ni, bs = sizeof(float) * ns;
-  // two buffer sets (image, sinogram, adjoint) of sizes multiple of 16 bytes
+  // two buffer sets (image, sinogram, adjoint); set k runs on plan k (a
+  // clone of p: the same tables, its own workspaces) and compute stream k,
+  // so that two slices' kernels can run concurrently
   float* buf = nullptr;
-  cudaStream_t up = nullptr, down = nullptr;
+  cpct_plan* clone = nullptr;
+  cudaStream_t up = nullptr, down = nullptr, comp1 = nullptr;
   cudaEvent_t ev[4][2] = {};  // uploaded, forward done, adjoint done, downloaded
   int rc = CPCT_OK;
   auto ok = [&](cudaError_t e) {
@@ -85,29 +88,35 @@ extern "C" int radon_pair_host_stream(cpct_plan* p, const float* const* h_imgs, 
   };
   if (cudaMalloc(&buf, 2 * (2 * bi + bs)) != cudaSuccess) return CPCT_ENOMEM;
   if (ok(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking)) &&
-      ok(cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking))) {
+      ok(cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking)) &&
+      ok(cudaStreamCreateWithFlags(&comp1, cudaStreamNonBlocking))) {
     for (auto& e2 : ev)
       for (auto& e : e2)
         if (!ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) break;
   }
+  if (rc == CPCT_OK && count > 1 && cpct_plan_clone(p, &clone, s) != CPCT_OK) clone = nullptr;  // one plan then
+  cpct_plan* const plan_of[2] = {p, clone ? clone : p};
+  cudaStream_t const comp[2] = {s, clone ? comp1 : s};
   enum { IN = 0, FWD = 1, ADJ = 2, OUT = 3 };
   for (int i = 0; i < count && rc == CPCT_OK; ++i) {
     const int k = i & 1;
     float* img = buf + k * (2 * ni + ns);
     float* sino = img + ni;
     float* out = sino + ns;
+    cudaStream_t cs = comp[k];
     // upload: the image buffer is free once slice i - 2's forward has read it
     if (i >= 2 && !ok(cudaStreamWaitEvent(up, ev[FWD][k], 0))) break;
     if (!ok(cudaMemcpyAsync(img, h_imgs[i], bi, cudaMemcpyHostToDevice, up))) break;
     if (!ok(cudaEventRecord(ev[IN][k], up))) break;
     // operators: after the upload, and once slice i - 2's downloads have
-    // read this set's sinogram and adjoint buffers
-    if (!ok(cudaStreamWaitEvent(s, ev[IN][k], 0))) break;
-    if (i >= 2 && !ok(cudaStreamWaitEvent(s, ev[OUT][k], 0))) break;
-    if ((rc = cpct_launch_fwd(p, img, sino, s)) != CPCT_OK) break;
-    if (!ok(cudaEventRecord(ev[FWD][k], s))) break;
-    if ((rc = cpct_launch_adj(p, sino, out, s)) != CPCT_OK) break;
-    if (!ok(cudaEventRecord(ev[ADJ][k], s))) break;
+    // read this set's sinogram and adjoint buffers (slice i - 2 ran on the
+    // same plan and stream; with one plan both sets share stream s)
+    if (!ok(cudaStreamWaitEvent(cs, ev[IN][k], 0))) break;
+    if (i >= 2 && !ok(cudaStreamWaitEvent(cs, ev[OUT][k], 0))) break;
+    if ((rc = cpct_launch_fwd(plan_of[k], img, sino, cs)) != CPCT_OK) break;
+    if (!ok(cudaEventRecord(ev[FWD][k], cs))) break;
+    if ((rc = cpct_launch_adj(plan_of[k], sino, out, cs)) != CPCT_OK) break;
+    if (!ok(cudaEventRecord(ev[ADJ][k], cs))) break;
     // downloads: the sinogram while the adjoint runs, then the adjoint
     if (!ok(cudaStreamWaitEvent(down, ev[FWD][k], 0))) break;
     if (!ok(cudaMemcpyAsync(h_sinos[i], sino, bs, cudaMemcpyDeviceToHost, down))) break;
@@ -118,12 +127,15 @@ extern "C" int radon_pair_host_stream(cpct_plan* p, const float* const* h_imgs, 
   // everything issued has finished before the buffers are released
   if (down) ok(cudaStreamSynchronize(down));
   if (up) ok(cudaStreamSynchronize(up));
+  if (comp1) ok(cudaStreamSynchronize(comp1));
   ok(cudaStreamSynchronize(s));
+  if (clone) cpct_plan_destroy(clone);
   for (auto& e2 : ev)
     for (auto& e : e2)
       if (e) cudaEventDestroy(e);
   if (up) cudaStreamDestroy(up);
   if (down) cudaStreamDestroy(down);
+  if (comp1) cudaStreamDestroy(comp1);
   cudaFree(buf);
   return rc;
 }
