@@ -76,24 +76,44 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kname, workload):
-    """DRAM bytes per launch of `kname` from the committed ncu summary, if the
-    summary's source hash matches the current kernel sources (else None)."""
+def profile_value(kname, workload, key):
+    """A per-launch figure (`key: value` line) of `kname` from the committed
+    ncu summary, if the summary's source hash matches the current kernel
+    sources (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kname}_{workload}.md")
     if not os.path.exists(path):
         return None
     want = None
-    traffic = None
+    value = None
     with open(path) as fh:
         for line in fh:
             if line.startswith("source_sha256:"):
                 want = line.split(":", 1)[1].strip()
-            if line.startswith("traffic_bytes_per_launch:"):
-                traffic = float(line.split(":", 1)[1].strip())
-    if want is None or traffic is None:
+            if line.startswith(key + ":"):
+                value = float(line.split(":", 1)[1].strip())
+    if want is None or value is None:
         return None
     from paper_1009_1380_gb300 import build as b
-    return traffic if b.radon_digest() == want else None
+    return value if b.radon_digest() == want else None
+
+
+def profile_traffic(kname, workload):
+    """DRAM bytes per launch of `kname` from the committed ncu summary."""
+    return profile_value(kname, workload, "traffic_bytes_per_launch")
+
+
+def onchip_roofline(kname, workload, avg_launch_s, sm_mhz, sms=152):
+    """The kernel against its on-chip bound: shared-memory wavefronts per
+    launch (committed ncu count) / launch time, against one 128-byte
+    wavefront per SM per clock at the sampled SM clock."""
+    wf = profile_value(kname, workload, "smem_wavefronts_per_launch")
+    if wf is None or not avg_launch_s or not sm_mhz:
+        return None
+    achieved = wf / avg_launch_s
+    peak = sms * sm_mhz * 1e6
+    return {"bound": "shared-memory wavefronts", "achieved": achieved, "peak": peak, "unit": "wavefronts/s",
+            "frac": achieved / peak, "wavefronts_per_launch": wf,
+            "peak_basis": f"{sms} SMs x 1 wavefront (128 B) per clock at the sampled {sm_mhz:.0f} MHz"}
 
 
 class ClockSampler:
@@ -519,7 +539,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "alg_bytes_per_launch": ab, "avg_launch_us": dom_avg_s * 1e6,
-                     "traffic": profile_traffic(dominant, args.workload)},
+                     "traffic": profile_traffic(dominant, args.workload),
+                     "onchip": onchip_roofline(dominant, args.workload, dom_avg_s, (clk or {}).get("sm_mhz"))},
         "kernels_us": {k: round(v[0] / max(1, v[1]) * 1000.0, 2) for k, v in breakdown.items()},
         "clocks": clk,
         "wall_s_timed": t_wall,
