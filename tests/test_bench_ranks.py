@@ -70,3 +70,19 @@ def test_denoiser_flops_against_the_oracle_layer_list():
             lv = int(name[3:].split(".")[0]) if name != "head" else 0
             ref += 2.0 * k * k * ci * co * (n >> lv) ** 2
         assert b.denoiser_flops(levels, base, n) == ref
+
+
+def test_onchip_roofline_arithmetic(monkeypatch):
+    """roofline.onchip = committed wavefronts per launch / launch time against
+    one 128-byte wavefront per SM per clock; None without a committed count,
+    a launch time or a clock."""
+    b = _bench()
+    monkeypatch.setattr(b, "profile_value", lambda k, w, key: 1.0e7 if key == "smem_wavefronts_per_launch" else None)
+    r = b.onchip_roofline("k", "w", 50e-6, 2000.0, sms=100)
+    assert r["achieved"] == 1.0e7 / 50e-6
+    assert r["peak"] == 100 * 2000.0 * 1e6
+    assert abs(r["frac"] - (1.0e7 / 50e-6) / (100 * 2.0e9)) < 1e-12
+    assert b.onchip_roofline("k", "w", 0.0, 2000.0) is None
+    assert b.onchip_roofline("k", "w", 50e-6, None) is None
+    monkeypatch.setattr(b, "profile_value", lambda k, w, key: None)
+    assert b.onchip_roofline("k", "w", 50e-6, 2000.0) is None
