@@ -17,7 +17,7 @@ reverse.  This module states that operator twice:
   step in the paper's order: deapodize and zero-pad, oversampled 2D FFT,
   Kaiser-Bessel interpolation onto the polar samples, ray inverse FFT.
 
-Conventions (the paper states none; these are the readings this build uses):
+Conventions (the paper states none; these are the readings used here and on the GPU):
 
 * image ``x[p, q]``: row ``p`` is the y axis, column ``q`` the x axis; pixel
   coordinates ``X = q - N/2``, ``Y = p - N/2``;

@@ -12,9 +12,10 @@ SPGL1 iterations from a good x0 grows quickly with the error of tau0 (on a
 64^2 problem: 4 iterations from x* itself, 33-40 from x* plus noise with
 tau0 within 5% of tau*, 56-82 at 10-20% off, 137 cold).  So
 tau0 = kappa ||soft(net(FBP), theta s)||_1, with the noise floor theta and the
-factor kappa calibrated on training slices (``calibrate``).  The plain cold-started solver is the fallback for any
-slice whose warm solve does not reach the root, and the judge of the result
-(its residual criterion is unchanged).  The same calibrated projection of
+factor kappa calibrated on training slices (``calibrate``).  The plain
+cold-started solver is the fallback for any slice whose warm solve does not
+reach the root, and its root test decides whether a warm solve succeeded
+(the residual criterion is unchanged).  The same calibrated projection of
 the FBP image itself is the non-learned warm start it is compared with.
 
 Inputs are scaled per slice by s = the standard deviation of the FBP image:
