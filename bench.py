@@ -412,6 +412,35 @@ def denoiser_bench(args, torch, cpct, runs=10):
             "workload": f"U-Net {levels} levels, {base} base channels, {B} x {n}x{n} images, random weights"}
 
 
+def cufft_comparison(torch, n, breakdown, runs=20):
+    """cuFFT (through torch.fft) on the oversampled G x G grid of the
+    workload, timed with CUDA events, next to this library's forward 2D FFT
+    stage (k_fwd_col + k_fwd_row of the same run: real input, the zero half
+    of the padded columns skipped, half-plane output)."""
+    G = 2 * n
+    z = torch.randn(G, G, dtype=torch.complex64, device="cuda")
+    xr = torch.zeros(G, G, dtype=torch.float32, device="cuda")
+    xr[:n, :n] = torch.rand(n, n, device="cuda")
+    out = {}
+    for name, fn in (("cufft_c2c_us", lambda: torch.fft.fft2(z)), ("cufft_r2c_padded_us", lambda: torch.fft.rfft2(xr))):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(runs)]
+        for a, b in ev:
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        out[name] = 1000.0 * sum(a.elapsed_time(b) for a, b in ev) / runs
+    ours = [breakdown[k] for k in ("k_fwd_col", "k_fwd_row") if k in breakdown]
+    if len(ours) == 2:
+        out["ours_fwd_col_row_us"] = 1000.0 * sum(ms / max(1, c) for ms, c in ours)
+    out["grid"] = f"{G}x{G}"
+    out["note"] = ("cuFFT as a timed comparison only; ours includes deapodization and zero padding, "
+                   "skips the zero half of every column FFT and writes the half plane with its extension")
+    return out
+
+
 def max_over_ranks(x, dist=None, device="cpu"):
     """The maximum of a per-rank float over all ranks (x itself for one rank)."""
     if dist is None:
@@ -549,6 +578,8 @@ def run_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = cpu_baseline(args.workload, gpu_sino=y.cpu().numpy())
     if world == 1:
         out["paper_workload"] = paper_workload(torch, cpct, synth)
+    if world == 1:
+        out["fft_comparison"] = cufft_comparison(torch, n, breakdown)
     if world == 1 and args.batch_slices > 0:
         out["batch"] = batch_bench(args, torch, cpct, synth)
     if world == 1 and args.spgl1_batch > 0:
