@@ -126,3 +126,17 @@ def test_host_stream_rejects_bad_arguments_before_any_device_work(cpct):
     assert L.radon_pair_host_stream(fake_plan, one, one, one, 0, None) == -1
     assert L.radon_pair_host_stream(fake_plan, nul, one, one, 1, None) == -1
     assert L.radon_pair_host_stream(fake_plan, one, one, nul, 1, None) == -1
+
+
+def test_source_digest_is_independent_of_the_checkout_location(monkeypatch):
+    """The Radon source digest (which gates the committed ncu traffic in the
+    bench line) names include directories by basename, so a checkout at
+    another path gives the same digest; a changed flag gives another."""
+    from paper_1009_1380_gb300 import build
+    d0 = build.radon_digest()
+    moved = [("/elsewhere/repo/" + f.split("/")[-2] + "/" + f.split("/")[-1]) if f.startswith("/") else f
+             for f in build.NVCC_FLAGS]
+    monkeypatch.setattr(build, "NVCC_FLAGS", moved)
+    assert build.radon_digest() == d0
+    monkeypatch.setattr(build, "NVCC_FLAGS", moved + ["-DDIGEST_PROBE"])
+    assert build.radon_digest() != d0
