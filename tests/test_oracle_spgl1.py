@@ -104,3 +104,61 @@ def test_bpdn_certificate_with_ring_filter():
                    constraints=[cons], method="SLSQP", options=dict(maxiter=3000, ftol=1e-12))
     assert np.sum((M @ res.x - bf) ** 2) ** 0.5 <= sigma * (1 + 1e-6)
     assert abs(np.abs(x).sum() - res.fun) <= 1e-3 * res.fun, (np.abs(x).sum(), res.fun)
+
+
+def _bpdn_problem(seed=4):
+    n, ns, m = 16, 16, 12
+    R = _dense_radon(n, ns, m)
+    F = ring.ring_filter_matrix(m, ns)
+    A = F @ R
+    rng = np.random.default_rng(seed)
+    x_true = np.zeros(n * n)
+    x_true[rng.choice(n * n, size=10, replace=False)] = 1.0
+    y = R @ x_true
+    noise = 0.01 * np.abs(y).max()
+    b = (y + rng.normal(0, noise, y.shape)).reshape(m, ns)
+    b[:, 3] += 0.5
+    bf = F @ b.ravel()
+    sigma = noise * np.sqrt(m * ns - ns + 4)
+    return A, bf, sigma
+
+
+def test_warm_start_at_the_solution_stays_there():
+    """Started at its own solution (tau0 = its l1 norm), the solver finds the
+    root at once and does not move the point."""
+    A, bf, sigma = _bpdn_problem()
+    op, opT = (lambda v: A @ v), (lambda r: A.T @ r)
+    x, info = spgl1.spgl1(op, opT, bf, sigma)
+    assert info.status == spgl1.EXIT_ROOT_FOUND
+    x2, info2 = spgl1.spgl1(op, opT, bf, sigma, x0=x)
+    assert info2.status == spgl1.EXIT_ROOT_FOUND
+    assert info2.iterations <= 3
+    assert np.linalg.norm(x2 - x) <= 1e-3 * np.linalg.norm(x)
+
+
+def test_step_restart_readings_reach_the_same_root():
+    """Both step-length readings (restart from the projected gradient after a
+    Newton update of tau, or keep the Barzilai-Borwein step) satisfy the root
+    certificate and agree on ||x||_1 to the inexactness of the Newton method
+    (opt_tol 1e-6 here)."""
+    A, bf, sigma = _bpdn_problem()
+    op, opT = (lambda v: A @ v), (lambda r: A.T @ r)
+    res = []
+    for restart in (True, False):
+        x, info = spgl1.spgl1(op, opT, bf, sigma, opts=spgl1.Options(opt_tol=1e-6, restart_step=restart))
+        assert info.status == spgl1.EXIT_ROOT_FOUND
+        assert abs(info.rnorm - sigma) <= 1e-6 * max(1.0, np.linalg.norm(bf))
+        res.append(np.abs(x).sum())
+    assert abs(res[0] - res[1]) <= 1e-3 * res[0]
+
+
+def test_tau0_at_the_root_saves_iterations():
+    """Starting from x = 0 with tau0 = the final radius skips the Newton
+    steps of the cold start: fewer iterations, the same root."""
+    A, bf, sigma = _bpdn_problem()
+    op, opT = (lambda v: A @ v), (lambda r: A.T @ r)
+    x, info = spgl1.spgl1(op, opT, bf, sigma)
+    x2, info2 = spgl1.spgl1(op, opT, bf, sigma, tau0=info.tau)
+    assert info2.status == spgl1.EXIT_ROOT_FOUND
+    assert info2.iterations < info.iterations
+    assert abs(info2.xnorm1 - info.xnorm1) <= 1e-3 * info.xnorm1
