@@ -215,6 +215,30 @@ class OracleTimer:
         return (t - self.t_fft * 4 / self.m) / 4
 
 
+def host_info():
+    """The host's core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model}
+
+
 def cpu_baseline(workload, budget_s=20.0, gpu_sino=None):
     """The FP64 oracle timed on a bounded sample of rays; with the GPU's
     sinogram of the same image (gpu_sino, host array), also the relative L2
@@ -227,7 +251,7 @@ def cpu_baseline(workload, budget_s=20.0, gpu_sino=None):
            "sample": (f"FP64 oracle (NumPy, single-threaded): fwd+adj gridding of {rays} of {ot.m} rays of "
                       f"the {ot.n}x{ot.n} workload, plus {rays}/{ot.m} of the measured oversampled 2D FFT + "
                       f"inverse FFT time ({ot.t_fft:.2f} s per full pair)"),
-           "seconds": t}
+           "seconds": t, **host_info()}
     if gpu_sino is not None:
         idx, y_ref = ot.last
         d = np.asarray(gpu_sino, dtype=np.float64)[idx] - y_ref
@@ -258,7 +282,8 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": config_dict(args),
-           "cpu_baseline": {"value": value, "unit": "Msamples/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "Msamples/s", "cores": 1, "kind": "oracle", "sample": sample,
+                            **host_info()},
            "e2e": {"value": value, "unit": "Msamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
