@@ -116,8 +116,56 @@ def onchip_roofline(kname, workload, avg_launch_s, sm_mhz, sms=152):
             "peak_basis": f"{sms} SMs x 1 wavefront (128 B) per clock at the sampled {sm_mhz:.0f} MHz"}
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes (SM clock, its maximum and the
+    active clock-event reasons of one GPU); nothing is set."""
+
+    SM = 1  # NVML_CLOCK_SM
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(cuda_index).uuid)
+        except Exception:
+            uuid = None
+        ok = False
+        if uuid:
+            u = uuid if uuid.startswith(("GPU-", "MIG-")) else "GPU-" + uuid
+            ok = self.lib.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(self.h)) == 0
+        if not ok and self.lib.nvmlDeviceGetHandleByIndex_v2(int(cuda_index), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.get_reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint()
+        self.max_mhz = float(v.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(v)) == 0 \
+            else None
+
+    def sample(self):
+        v = self.ct.c_uint()
+        r = self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, self.ct.byref(v)) != 0:
+            return None
+        mask = int(r.value) if self.get_reasons(self.h, self.ct.byref(r)) == 0 else 0
+        return float(v.value), mask
+
+
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+    """SM clock and throttle reasons sampled during the timed region.
+
+    An NVML polling thread (about 1 ms period) records every sample with its
+    time; begin() / end() mark the timed region and stop() reduces the
+    samples that fall inside it (the timed region of a short run lasts a few
+    milliseconds, less than nvidia-smi's sampling period).  Without NVML,
+    nvidia-smi is sampled every 100 ms instead and every sample is kept."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -127,17 +175,64 @@ class ClockSampler:
         self.idx = gpu_index
         self.proc = None
         self.tmp = None
+        self.nvml = None
+        self.thread = None
+        self.samples = []
+        self.window = [None, None]
+        self.running = False
 
     def start(self):
+        try:
+            self.nvml = _Nvml(self.idx)
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            import threading
+            self.running = True
+
+            def poll():
+                while self.running:
+                    smp = self.nvml.sample()
+                    if smp is not None:
+                        self.samples.append((time.perf_counter(), smp[0], smp[1]))
+                    time.sleep(0.001)
+
+            self.thread = threading.Thread(target=poll, daemon=True)
+            self.thread.start()
+            return
         try:
             self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+            t0 = time.perf_counter()
+            while time.perf_counter() - t0 < 5.0 and os.path.getsize(self.tmp.name) == 0:
+                time.sleep(0.05)
         except (OSError, FileNotFoundError):
             self.proc = None
 
+    def begin(self):
+        self.window[0] = time.perf_counter()
+
+    def end(self):
+        self.window[1] = time.perf_counter()
+
     def stop(self):
+        if self.nvml is not None:
+            self.running = False
+            self.thread.join(timeout=5)
+            t0, t1 = self.window
+            inside = [x for x in self.samples if t0 is not None and t1 is not None and t0 <= x[0] <= t1]
+            if not inside:
+                return None
+            reasons = set()
+            for _, _, mask in inside:
+                for bit, nm in _Nvml.REASONS.items():
+                    if mask & bit:
+                        reasons.add(nm)
+            return {"sm_mhz": statistics.median(x[1] for x in inside), "sm_max_mhz": self.nvml.max_mhz,
+                    "reasons": sorted(reasons), "samples": len(inside), "source": "NVML, ~1 ms polling",
+                    "window_ms": 1000.0 * (t1 - t0)}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -164,20 +259,22 @@ class ClockSampler:
                     reasons.add(nm)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "source": "nvidia-smi, 100 ms"}
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 class OracleTimer:
-    """Times the FP64 oracle's fwd + adj on the workload.
+    """Times the FP64 oracle's forward + adjoint on the workload.
 
-    The 2D FFT and inverse FFT of the oversampled grid are timed once; a step
-    grids a block of rays forward and back (interpolation, ray inverse DFT,
-    ray DFT, spread) and is charged its share rays/M of the measured FFT time,
-    so that a cycle over all M rays costs exactly one full oracle pair.
-    """
+    full_pair(): one whole forward (deapodize/pad, 2D FFT, interpolation of
+    every ray, ray inverse DFT) and one whole adjoint of its output (ray DFT,
+    spread of every ray, inverse 2D FFT, crop/deapodize), timed end to end.
+    step(rays): the bounded sample of the reference arm: a block of rays
+    gridded forward and back, charged its share rays/M of the measured 2D FFT
+    pair, so that a cycle over all M rays costs one oracle pair."""
 
     def __init__(self, workload):
         from oracle import nufft
@@ -187,17 +284,32 @@ class OracleTimer:
         self.n, self.ns, self.m = n, ns, m
         self.img = synth.phantom(cfg).astype(np.float64)
         self.geo = nufft.GridGeometry(n, ns, nufft.default_angles(m))
-        t0 = time.perf_counter()
-        self.F = np.fft.fft2(nufft.grid_deapod_pad(self.img, self.geo))
-        t1 = time.perf_counter()
-        G = self.geo.grid
-        z = np.fft.ifft2(self.F) * (G * G)
-        nufft.grid_crop_deapod(z, self.geo)
-        t2 = time.perf_counter()
-        self.t_fft = (t1 - t0) + (t2 - t1)
+        self.F = None
         self.cursor = 0
 
+    def _fft_pair(self):
+        nf = self.nufft
+        t0 = time.perf_counter()
+        self.F = nf.fft2(nf.grid_deapod_pad(self.img, self.geo))
+        t1 = time.perf_counter()
+        G = self.geo.grid
+        nf.grid_crop_deapod(nf.ifft2(self.F) * (G * G), self.geo)
+        self.t_fft = time.perf_counter() - t0
+        return t1 - t0
+
+    def full_pair(self):
+        nf, geo = self.nufft, self.geo
+        G = geo.grid
+        t0 = time.perf_counter()
+        F = nf.fft2(nf.grid_deapod_pad(self.img, geo))
+        y = nf.ray_idft(nf.grid_interp(F, geo)).real
+        z = nf.grid_crop_deapod(nf.ifft2(nf.grid_spread(nf.ray_idft_adj(y), geo)) * (G * G), geo).real
+        t = time.perf_counter() - t0
+        return t, self.m * self.ns, y, z
+
     def step(self, rays_per_step):
+        if self.F is None:
+            self._fft_pair()
         nf = self.nufft
         r0 = self.cursor
         rays = (np.arange(rays_per_step) + r0) % self.m
@@ -239,24 +351,23 @@ def host_info():
     return {"host_cores": os.cpu_count(), "cpu_model": model}
 
 
-def cpu_baseline(workload, budget_s=20.0, gpu_sino=None):
-    """The FP64 oracle timed on a bounded sample of rays; with the GPU's
-    sinogram of the same image (gpu_sino, host array), also the relative L2
-    error of the GPU forward over the sampled rays against the oracle's."""
+def cpu_baseline(workload, gpu_sino=None):
+    """The FP64 oracle timed on one whole forward + adjoint pair of the
+    workload (no extrapolation); with the GPU's sinogram of the same image
+    (gpu_sino, host array), also the relative L2 error of the GPU forward over
+    every ray against the oracle's."""
     ot = OracleTimer(workload)
-    per_ray = ot.time_per_ray()
-    rays = int(max(1, min(ot.m, budget_s / max(per_ray, 1e-6))))
-    t, samples = ot.step(rays)
-    out = {"value": samples / t / 1e6, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
-           "sample": (f"FP64 oracle (NumPy, single-threaded): fwd+adj gridding of {rays} of {ot.m} rays of "
-                      f"the {ot.n}x{ot.n} workload, plus {rays}/{ot.m} of the measured oversampled 2D FFT + "
-                      f"inverse FFT time ({ot.t_fft:.2f} s per full pair)"),
+    t, samples, y_ref, _ = ot.full_pair()
+    cores = ot.nufft.FFT_WORKERS
+    out = {"value": samples / t / 1e6, "unit": "Msamples/s", "cores": cores, "kind": "oracle",
+           "sample": (f"one whole FP64 oracle forward + adjoint pair of the {ot.n}x{ot.n} workload "
+                      f"({ot.m} rays x {ot.ns} bins), timed once end to end: 2D FFTs by scipy.fft on "
+                      f"{cores} threads, gridding loops in single-threaded NumPy"),
            "seconds": t, **host_info()}
     if gpu_sino is not None:
-        idx, y_ref = ot.last
-        d = np.asarray(gpu_sino, dtype=np.float64)[idx] - y_ref
-        out["parity"] = {"fwd_rel_l2": float(np.linalg.norm(d) / np.linalg.norm(y_ref)), "rays": int(len(idx)),
-                         "against": "FP64 gridding oracle (same W, sigma, beta), the timed sample's rays"}
+        d = np.asarray(gpu_sino, dtype=np.float64) - y_ref
+        out["parity"] = {"fwd_rel_l2": float(np.linalg.norm(d) / np.linalg.norm(y_ref)), "rays": int(ot.m),
+                         "against": "FP64 gridding oracle (same W, sigma, beta), every ray"}
     return out
 
 
@@ -277,12 +388,14 @@ def run_reference(args, rank, world):
         tot_s += s
     value = tot_s / tot_t / 1e6
     sample = (f"per step: FP64 oracle fwd+adj gridding of {rays} of {ot.m} rays of the {ot.n}x{ot.n} workload "
-              f"plus {rays}/{ot.m} of the measured 2D FFT + inverse FFT time")
+              f"(single-threaded NumPy) plus {rays}/{ot.m} of the measured 2D FFT + inverse FFT time (scipy.fft, "
+              f"{ot.nufft.FFT_WORKERS} threads)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": config_dict(args),
-           "cpu_baseline": {"value": value, "unit": "Msamples/s", "cores": 1, "kind": "oracle", "sample": sample,
+           "cpu_baseline": {"value": value, "unit": "Msamples/s", "cores": ot.nufft.FFT_WORKERS, "kind": "oracle",
+                            "sample": sample,
                             **host_info()},
            "e2e": {"value": value, "unit": "Msamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -541,12 +654,14 @@ def run_ours(args, rank, world, local_rank):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     plan.launch_count(reset=True)
     t_wall0 = time.perf_counter()
+    clocks.begin()
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
         pair()
         ends[k].record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     t_wall = time.perf_counter() - t_wall0
     launches = plan.launch_count()
     if dist:

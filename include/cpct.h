@@ -116,6 +116,25 @@ int radon_fwd(cpct_plan* plan, const float* d_img, float* d_sino, cudaStream_t s
  *   d_img   device, N*N float32 (written)                                   */
 int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream);
 
+/* Complex operator pair.  Section "fast radon transform" builds the
+ * projections from the polar samples of the image's Fourier transform; the
+ * inverse FFT along each ray gives a complex sinogram y = A x, whose real
+ * part is what radon_fwd returns.  For a real image the polar spectrum is
+ * Hermitian in k, so y is real except for the Nyquist frequency k = -Ns/2,
+ * which has no partner: Im y[j, s] = (1/Ns) Im(P[j, -Ns/2]) (-1)^(s - Ns/2).
+ *   radon_fwd_c: y = A x,  d_img N*N float32 (read), d_sino_c M*Ns complex64
+ *                (interleaved re, im; written);
+ *   radon_adj_c: x = Re(A^H w),  d_sino_c M*Ns complex64 (read), d_img N*N
+ *                float32 (written): the exact adjoint of radon_fwd_c for the
+ *                real inner product Re<u, v> on complex sinograms (the image
+ *                is real).  Re(w) takes radon_adj's path; Im(w) only reaches
+ *                the Nyquist samples.
+ * A complex image x = a + i b maps to A a + i A b (two radon_fwd_c calls),
+ * and A^H w = Re(A^H w) + i Re(A^H (-i w)) (two radon_adj_c calls).  Same
+ * alignment, stream and error rules as radon_fwd / radon_adj. */
+int radon_fwd_c(cpct_plan* plan, const float* d_img, void* d_sino_c, cudaStream_t stream);
+int radon_adj_c(cpct_plan* plan, const void* d_sino_c, float* d_img, cudaStream_t stream);
+
 /* Filtered back-projection x = R^T(h * y): the ray spectra of the sinogram
  * are weighted by the ramp h[k] = (pi / M) |k| / Ns (the DC bin by (pi / M)
  * 0.25 / Ns, the mean of |k| over its width) before the adjoint, which
@@ -127,7 +146,8 @@ int radon_fbp(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t s
 
 /* The finite-difference synthesis operator of the analysis-l1 variant.  The
  * paper puts the l1 norm on the phase-contrast image itself (a Laplacian of
- * the object, sections "Introduction" and "Phase contrast"); the variant
+ * the object, section "Introduction"); its Conclusions point to total
+ * variation instead, i.e. l1 of the object's gradient.  The variant
  * puts it on the horizontal differences z of a piecewise-constant image u
  * through u = C z (prefix sums along every row: C inverts z[p, 0] = u[p, 0],
  * z[p, q] = u[p, q] - u[p, q - 1]).
@@ -146,8 +166,8 @@ int radon_fwd_host(cpct_plan* plan, const float* h_img, float* h_sino, cudaStrea
 int radon_adj_host(cpct_plan* plan, const float* h_sino, float* h_img, cudaStream_t stream);
 
 /* The operator pair over `count` slices in host memory, pipelined (the
- * operators of sections "Gridding" and "Inverse gridding" applied slice by
- * slice):
+ * forward operator and its adjoint of section "fast radon transform",
+ * applied slice by slice):
  *   h_sinos[i] = R h_imgs[i]   (radon_fwd: N x N in, M x Ns out)
  *   h_outs[i]  = R^H h_sinos[i] (radon_adj of the device-resident sinogram)
  * Two device buffer sets alternate: slice i + 1's image is copied in and
@@ -171,6 +191,17 @@ int radon_pair_host_stream(cpct_plan* plan, const float* const* h_imgs, float* c
  * workspaces, so that it can run concurrently with src on another slice.
  * Synchronous on `stream`.  Cheap: no bin building. */
 int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream_t stream);
+
+/* Install the work items of a plan with the given caps: fwd_cap samples per
+ * forward gather item, adj_cap conflict-free rounds per adjoint spread item
+ * (0 keeps the current cap; defaults 1024 and 64).  The plan must not have
+ * clones yet.  Allocates the new item lists; synchronous. */
+int cpct_plan_set_caps(cpct_plan* plan, int fwd_cap, int adj_cap, cudaStream_t stream);
+
+/* Work items of a plan: forward gather items, adjoint spread items, heavy
+ * tiles split over several spread items, and their partial tiles (slots).
+ * Host only; any output pointer may be NULL. */
+int cpct_plan_work(const cpct_plan* plan, int* n_fwd_items, int* n_adj_items, int* n_split, int* n_slots);
 
 /* Autotuner of the work-item sizes (the bins' split caps): times radon_fwd
  * for 256..4096 samples per gather item and radon_adj for 16..256 rounds per
@@ -466,6 +497,12 @@ int cpct_debug_bin_tile(const cpct_geom* g, int which, int tile, uint32_t* ids, 
  * valid = 1 if every invariant holds (each bin entry exactly once, no two
  * footprints of a round overlap, lane = bank class). */
 int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packed, int* valid);
+
+/* The adjoint work items that a plan of geometry g gets with `cap` rounds
+ * per spread item (0: the default cap), built on the host exactly as
+ * cpct_plan_create / cpct_plan_set_caps build them: items, split heavy
+ * tiles, partial tiles (slots).  No GPU needed. */
+int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, int* n_split, int* n_slots);
 
 /* The split of a sample coordinate u = k (hi + lo) into floor and fraction,
  * with the same float32 operations as the kernels. */

@@ -5,9 +5,10 @@ Test infrastructure only (like the rest of ``oracle/``): the product path
 never imports it.
 
 The paper minimises the l1 norm of the phase-contrast image itself, which is
-sparse because it is a Laplacian of the object (sections "Introduction" and
-"Phase contrast"); the l1 problem is solved by SPGL1 with the Radon operator
-and its adjoint.  The variant here puts the l1 norm on the horizontal finite
+sparse because it is a Laplacian of the object (section "Introduction"); the
+l1 problem is solved by SPGL1 with the Radon operator and its adjoint.  Its
+Conclusions point to total-variation regularisation, l1 of the object's
+gradient.  The variant here puts the l1 norm on the horizontal finite
 differences of a piecewise-constant image u instead, through an invertible
 synthesis operator:
 

@@ -64,6 +64,12 @@ def lib():
                                      ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t)]
         for name in ("radon_fwd", "radon_adj", "radon_fbp", "radon_fwd_host", "radon_adj_host", "radon_adj_noalloc"):
             getattr(L, name).argtypes = [vp, vp, vp, vp]
+        for name in ("radon_fwd_c", "radon_adj_c"):
+            getattr(L, name).argtypes = [vp, vp, vp, vp]
+        L.cpct_plan_set_caps.argtypes = [vp, i, i, vp]
+        L.cpct_plan_work.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.cpct_debug_adj_items.argtypes = [ctypes.POINTER(Geom), i, ctypes.POINTER(i), ctypes.POINTER(i),
+                                           ctypes.POINTER(i)]
         L.radon_pair_host_stream.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
         L.cpct_strerror.restype = ctypes.c_char_p
         L.cpct_strerror.argtypes = [i]
@@ -115,6 +121,14 @@ def _stream(torch, stream):
 def _dev_ptr(t, shape, torch):
     if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
         raise ValueError("expected a contiguous float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_ptr_c(t, shape, torch):
+    if not (t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous complex64 CUDA tensor")
     if tuple(t.shape) != tuple(shape):
         raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
     return ctypes.c_void_p(t.data_ptr())
@@ -173,6 +187,44 @@ class Plan:
         check(lib().radon_adj(self._h, _dev_ptr(sino, (self.n_views, self.n_det), torch),
                               _dev_ptr(out, (self.n, self.n), torch), _stream(torch, stream)), "radon_adj")
         return out
+
+    def fwd_c(self, img, out=None, stream=None):
+        """Complex sinogram A x (complex64, M x Ns) of a real image."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.n_views, self.n_det), device=img.device, dtype=torch.complex64)
+        check(lib().radon_fwd_c(self._h, _dev_ptr(img, (self.n, self.n), torch),
+                                _dev_ptr_c(out, (self.n_views, self.n_det), torch), _stream(torch, stream)),
+              "radon_fwd_c")
+        return out
+
+    def adj_c(self, sino_c, out=None, stream=None):
+        """Re(A^H w) of a complex sinogram (complex64, M x Ns)."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.n, self.n), device=sino_c.device, dtype=torch.float32)
+        check(lib().radon_adj_c(self._h, _dev_ptr_c(sino_c, (self.n_views, self.n_det), torch),
+                                _dev_ptr(out, (self.n, self.n), torch), _stream(torch, stream)), "radon_adj_c")
+        return out
+
+    def adj_noalloc(self, sino, out=None, stream=None):
+        """radon_adj_noalloc: the adjoint with the library's static scratch."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.n, self.n), device=sino.device, dtype=torch.float32)
+        check(lib().radon_adj_noalloc(self._h, _dev_ptr(sino, (self.n_views, self.n_det), torch),
+                                      _dev_ptr(out, (self.n, self.n), torch), _stream(torch, stream)),
+              "radon_adj_noalloc")
+        return out
+
+    def set_caps(self, fwd_cap=0, adj_cap=0, stream=None):
+        check(lib().cpct_plan_set_caps(self._h, int(fwd_cap), int(adj_cap), _stream(self._torch, stream)),
+              "cpct_plan_set_caps")
+
+    def work(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        check(lib().cpct_plan_work(self._h, *[ctypes.byref(x) for x in v]), "cpct_plan_work")
+        return dict(fwd_items=v[0].value, adj_items=v[1].value, n_split=v[2].value, n_slots=v[3].value)
 
     def fbp(self, sino, out=None, stream=None):
         """Filtered back-projection R^T(ramp * sino)."""
@@ -252,6 +304,16 @@ def debug_bins(n, n_det, n_views, which, angles=None):
     check(lib().cpct_debug_bins(ctypes.byref(g), int(which), ctypes.byref(t), ctypes.byref(e), ctypes.byref(c)),
           "cpct_debug_bins")
     return t.value, e.value, c.value
+
+
+def debug_adj_items(n, n_det, n_views, cap=0, angles=None):
+    """Host-side adjoint work items of a geometry with `cap` rounds per item
+    (no GPU needed): dict(items, n_split, n_slots)."""
+    g, _keep = make_geom(n, n_det, n_views, angles)
+    v = [ctypes.c_int() for _ in range(3)]
+    check(lib().cpct_debug_adj_items(ctypes.byref(g), int(cap), *[ctypes.byref(x) for x in v]),
+          "cpct_debug_adj_items")
+    return dict(items=v[0].value, n_split=v[1].value, n_slots=v[2].value)
 
 
 def debug_bin_tile(n, n_det, n_views, which, tile, cap=1 << 20, angles=None):

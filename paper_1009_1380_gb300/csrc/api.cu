@@ -17,6 +17,16 @@ extern "C" int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cud
   return cpct_launch_adj(plan, d_sino, d_img, stream);
 }
 
+extern "C" int radon_fwd_c(cpct_plan* plan, const float* d_img, void* d_sino_c, cudaStream_t stream) {
+  if (!plan || !d_img || !d_sino_c || !aligned16(d_img) || !aligned16(d_sino_c)) return CPCT_EINVAL;
+  return cpct_launch_fwd_c(plan, d_img, static_cast<float2*>(d_sino_c), stream);
+}
+
+extern "C" int radon_adj_c(cpct_plan* plan, const void* d_sino_c, float* d_img, cudaStream_t stream) {
+  if (!plan || !d_img || !d_sino_c || !aligned16(d_img) || !aligned16(d_sino_c)) return CPCT_EINVAL;
+  return cpct_launch_adj_c(plan, static_cast<const float2*>(d_sino_c), d_img, stream);
+}
+
 extern "C" int radon_fbp(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream) {
   if (!plan || !d_img || !d_sino || !aligned16(d_img) || !aligned16(d_sino)) return CPCT_EINVAL;
   const double ramp = 3.14159265358979323846 / ((double)plan->m * plan->ns);

@@ -246,4 +246,6 @@ int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float 
                          cudaStream_t s);
 // the forward with every kernel skipped while *skip != 0
 int cpct_launch_fwd_skip(cpct_plan* p, const float* d_img, float* d_sino, const int* skip, cudaStream_t s);
+int cpct_launch_fwd_c(cpct_plan* p, const float* d_img, float2* d_sino_c, cudaStream_t s);
+int cpct_launch_adj_c(cpct_plan* p, const float2* d_sino_c, float* d_img, cudaStream_t s);
 int cpct_radon_setup_attributes(int logG, int logNs);

@@ -873,3 +873,48 @@ extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap
   if (adj_cap) *adj_cap = p->adj_cap;
   return rc;
 }
+
+// Install work items with the given caps (0 keeps the current one); the
+// plan must not have clones.  Synchronous.
+extern "C" int cpct_plan_set_caps(cpct_plan* p, int fwd_cap, int adj_cap, cudaStream_t stream) {
+  if (!p || !p->shared || fwd_cap < 0 || adj_cap < 0) return CPCT_EINVAL;
+  if (p->shared->refs != 1) return CPCT_EINVAL;
+  int rc = CPCT_OK;
+  if (fwd_cap > 0) rc = install_fwd_items(p, fwd_cap, stream);
+  if (rc == CPCT_OK && adj_cap > 0) rc = install_adj_items(p, adj_cap, stream);
+  return rc;
+}
+
+// Work-item counts of a plan: forward gather items, adjoint spread items,
+// split heavy tiles and their partial tiles (slots).
+extern "C" int cpct_plan_work(const cpct_plan* p, int* n_fwd_items, int* n_adj_items, int* n_split, int* n_slots) {
+  if (!p) return CPCT_EINVAL;
+  if (n_fwd_items) *n_fwd_items = p->n_fwd_items;
+  if (n_adj_items) *n_adj_items = p->n_adj_items;
+  if (n_split) *n_split = p->n_split;
+  if (n_slots) *n_slots = p->n_slots;
+  return CPCT_OK;
+}
+
+// The adjoint work items a plan of geometry g would get with `cap` rounds per
+// item (0: the default cap), built on the host exactly as cpct_plan_create
+// and cpct_plan_set_caps build them.  No GPU needed.
+extern "C" int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, int* n_split, int* n_slots) {
+  if (!geom_ok(g) || cap < 0) return CPCT_EINVAL;
+  const int G = 2 * g->n, K = g->n_det / 2;
+  std::vector<float4> ray;
+  cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
+  cpct_detail::Bins f, a;
+  std::vector<int> fa0, frb;
+  cpct_detail::build_bins(g->n, g->n_det, g->n_views, G, ray, f, a, &fa0, &frb);
+  cpct_detail::Rounds rd;
+  cpct_detail::pack_rounds(a, G, fa0, frb, K, rd);
+  std::vector<int4> items, split;
+  std::vector<int> item_split;
+  int slots = 0;
+  cpct_detail::make_round_items(rd, cap > 0 ? cap : kAdjItemRounds, items, split, &slots, item_split);
+  if (n_items) *n_items = (int)items.size();
+  if (n_split) *n_split = (int)split.size();
+  if (n_slots) *n_slots = slots;
+  return CPCT_OK;
+}

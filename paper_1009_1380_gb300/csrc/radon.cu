@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kInterpThreads)
 // ---------------------------------------------------------------------------
 // 4. forward ray transform (c2r of the Hermitian-completed rays)
 // ---------------------------------------------------------------------------
-template <int LOGNS>
+template <int LOGNS, bool CPLX>
 __global__ void __launch_bounds__(kThreads)
     k_fwd_ray(const float2* __restrict__ Q, float* __restrict__ sino, const float2* __restrict__ tw, int M, int ldq,
               const int* __restrict__ skip) {
@@ -302,17 +302,33 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   FFT::run(buf, tw, t);
   const float inv = 1.f / (float)NS;
-  for (int s = t; s < NS; s += T) {
-    const float2 w = buf[fpad(s)];
-    if (v1) sino[(size_t)j1 * NS + s] = w.x * inv;
-    if (v2) sino[(size_t)j2 * NS + s] = w.y * inv;
+  if constexpr (CPLX) {
+    // complex sinogram y = A x (interleaved re, im).  Its real part is the
+    // real kernel's output; its imaginary part comes only from the Nyquist
+    // frequency k = -Ns/2, whose sample P[j, -K] = conj(Q[j, K]) has no
+    // Hermitian partner:  Im y[j, s] = -Im(Q[j, K]) (-1)^(s - K) / Ns.
+    const float i1 = v1 ? -Q[(size_t)j1 * ldq + K].y * inv : 0.f;
+    const float i2 = v2 ? -Q[(size_t)j2 * ldq + K].y * inv : 0.f;
+    float2* out = reinterpret_cast<float2*>(sino);
+    for (int s = t; s < NS; s += T) {
+      const float2 w = buf[fpad(s)];
+      const float sg = ((s + K) & 1) ? -1.f : 1.f;
+      if (v1) out[(size_t)j1 * NS + s] = make_float2(w.x * inv, sg * i1);
+      if (v2) out[(size_t)j2 * NS + s] = make_float2(w.y * inv, sg * i2);
+    }
+  } else {
+    for (int s = t; s < NS; s += T) {
+      const float2 w = buf[fpad(s)];
+      if (v1) sino[(size_t)j1 * NS + s] = w.x * inv;
+      if (v2) sino[(size_t)j2 * NS + s] = w.y * inv;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // 5. adjoint ray transform (transpose of step 4)
 // ---------------------------------------------------------------------------
-template <int LOGNS>
+template <int LOGNS, bool CPLX>
 __global__ void __launch_bounds__(kThreads)
     k_adj_ray(const float* __restrict__ sino, float2* __restrict__ Q, const float2* __restrict__ tw, int M, int ldq,
               float ramp, const int* __restrict__ skip) {
@@ -320,13 +336,32 @@ __global__ void __launch_bounds__(kThreads)
   using FFT = SmemFFT<LOGNS, kErow, -1>;
   constexpr int NS = 1 << LOGNS, T = FFT::T, PPC = rows_per_cta<LOGNS>(), K = NS / 2;
   extern __shared__ float2 sm[];
+  // complex input: per-thread partial sums of Im(w[s]) (-1)^s of both rays
+  __shared__ float nyq[2][CPLX ? kThreads : 1];
   const int f = threadIdx.x / T, t = threadIdx.x % T;
   float2* buf = sm + f * FFT::PADN;
   const int j1 = 2 * (blockIdx.x * PPC + f), j2 = j1 + 1;
   const bool v1 = j1 < M, v2 = j2 < M;
+  if constexpr (CPLX) {
+    // the real parts go through the packed FFT as in the real kernel; the
+    // imaginary parts only reach the Nyquist sample (see below)
+    const float2* in = reinterpret_cast<const float2*>(sino);
+    float a1 = 0.f, a2 = 0.f;
+    for (int s = t; s < NS; s += T) {
+      const float2 w1 = v1 ? in[(size_t)j1 * NS + s] : make_float2(0.f, 0.f);
+      const float2 w2 = v2 ? in[(size_t)j2 * NS + s] : make_float2(0.f, 0.f);
+      buf[fpad(s)] = make_float2(w1.x, w2.x);
+      const float sg = (s & 1) ? -1.f : 1.f;
+      a1 = fmaf(sg, w1.y, a1);
+      a2 = fmaf(sg, w2.y, a2);
+    }
+    nyq[0][threadIdx.x] = a1;
+    nyq[1][threadIdx.x] = a2;
+  } else {
 #pragma unroll
-  for (int s = t; s < NS; s += T)
-    buf[fpad(s)] = make_float2(v1 ? sino[(size_t)j1 * NS + s] : 0.f, v2 ? sino[(size_t)j2 * NS + s] : 0.f);
+    for (int s = t; s < NS; s += T)
+      buf[fpad(s)] = make_float2(v1 ? sino[(size_t)j1 * NS + s] : 0.f, v2 ? sino[(size_t)j2 * NS + s] : 0.f);
+  }
   __syncthreads();
   FFT::run(buf, tw, t);
   const float inv = 1.f / (float)NS;
@@ -337,6 +372,21 @@ __global__ void __launch_bounds__(kThreads)
     float2 d2 = make_float2(0.5f * (W.y + Wm.y), -0.5f * (W.x - Wm.x));
     float sc = ((k & 1) ? -inv : inv);
     if (k == 0 || k == K) { d1.y = 0.f; d2.y = 0.f; } else { sc *= 2.f; }
+    if constexpr (CPLX) {
+      // adjoint of the forward's Nyquist term conj(Q[j, K]) (-1)^(s-K) / Ns
+      // under the real inner product: Im Q~[j, K] = -(1/Ns) sum_s Im(w[j, s])
+      // (-1)^(s-K), i.e. sc * (-sum_s Im(w[j, s]) (-1)^s) with sc = (-1)^K / Ns;
+      // the thread's partials are summed in thread order (deterministic)
+      if (k == K) {
+        float s1 = 0.f, s2 = 0.f;
+        for (int i = 0; i < T; ++i) {
+          s1 += nyq[0][f * T + i];
+          s2 += nyq[1][f * T + i];
+        }
+        d1.y = -s1;
+        d2.y = -s2;
+      }
+    }
     // filtered back-projection: ramp weight (pi / M) |k| / Ns, the DC bin
     // weighted by the mean of |k| over its width (1/4)
     if (ramp > 0.f) sc *= ramp * (k == 0 ? 0.25f : (float)k);
@@ -582,13 +632,18 @@ int set_attr_G() {
   if (cudaFuncSetAttribute(k_adj_row<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(rows_per_cta<LOGG>())) != cudaSuccess) return CPCT_ECUDA;
   return CPCT_OK;
 }
+template <int LOGNS, bool CPLX>
+int set_attr_Ns_one() {
+  max_carveout(k_fwd_ray<LOGNS, CPLX>);
+  max_carveout(k_adj_ray<LOGNS, CPLX>);
+  if (cudaFuncSetAttribute(k_fwd_ray<LOGNS, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGNS>(rows_per_cta<LOGNS>())) != cudaSuccess) return CPCT_ECUDA;
+  if (cudaFuncSetAttribute(k_adj_ray<LOGNS, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGNS>(rows_per_cta<LOGNS>())) != cudaSuccess) return CPCT_ECUDA;
+  return CPCT_OK;
+}
 template <int LOGNS>
 int set_attr_Ns() {
-  max_carveout(k_fwd_ray<LOGNS>);
-  max_carveout(k_adj_ray<LOGNS>);
-  if (cudaFuncSetAttribute(k_fwd_ray<LOGNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGNS>(rows_per_cta<LOGNS>())) != cudaSuccess) return CPCT_ECUDA;
-  if (cudaFuncSetAttribute(k_adj_ray<LOGNS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGNS>(rows_per_cta<LOGNS>())) != cudaSuccess) return CPCT_ECUDA;
-  return CPCT_OK;
+  const int rc = set_attr_Ns_one<LOGNS, false>();
+  return rc ? rc : set_attr_Ns_one<LOGNS, true>();
 }
 
 template <int LOGG>
@@ -603,20 +658,27 @@ void launch_fwd_G(cpct_plan* p, const float* img, const int* skip, cudaStream_t 
   cpct_prof_end(p, KID_FWD_ROW, s);
 }
 template <int LOGNS>
-void launch_fwd_Ns(cpct_plan* p, float* sino, const int* skip, cudaStream_t s) {
+void launch_fwd_Ns(cpct_plan* p, float* sino, bool cplx, const int* skip, cudaStream_t s) {
   constexpr int NS = 1 << LOGNS, PPC = rows_per_cta<LOGNS>();
   const int pairs = (p->m + 1) / 2;
+  const dim3 grid((pairs + PPC - 1) / PPC), block(PPC * (NS / kErow));
   cpct_prof_begin(p, KID_FWD_RAY, s);
-  k_fwd_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kErow), fft_smem<LOGNS>(PPC), s>>>(p->d_Q, sino, p->d_twNs, p->m, p->ldq, skip);
+  if (cplx)
+    k_fwd_ray<LOGNS, true><<<grid, block, fft_smem<LOGNS>(PPC), s>>>(p->d_Q, sino, p->d_twNs, p->m, p->ldq, skip);
+  else
+    k_fwd_ray<LOGNS, false><<<grid, block, fft_smem<LOGNS>(PPC), s>>>(p->d_Q, sino, p->d_twNs, p->m, p->ldq, skip);
   cpct_prof_end(p, KID_FWD_RAY, s);
 }
 template <int LOGNS>
-void launch_adj_Ns(cpct_plan* p, const float* sino, float ramp, const int* skip, cudaStream_t s) {
+void launch_adj_Ns(cpct_plan* p, const float* sino, bool cplx, float ramp, const int* skip, cudaStream_t s) {
   constexpr int NS = 1 << LOGNS, PPC = rows_per_cta<LOGNS>();
   const int pairs = (p->m + 1) / 2;
+  const dim3 grid((pairs + PPC - 1) / PPC), block(PPC * (NS / kErow));
   cpct_prof_begin(p, KID_ADJ_RAY, s);
-  k_adj_ray<LOGNS><<<(pairs + PPC - 1) / PPC, PPC * (NS / kErow), fft_smem<LOGNS>(PPC), s>>>(sino, p->d_Q, p->d_twNs, p->m,
-                                                                                           p->ldq, ramp, skip);
+  if (cplx)
+    k_adj_ray<LOGNS, true><<<grid, block, fft_smem<LOGNS>(PPC), s>>>(sino, p->d_Q, p->d_twNs, p->m, p->ldq, ramp, skip);
+  else
+    k_adj_ray<LOGNS, false><<<grid, block, fft_smem<LOGNS>(PPC), s>>>(sino, p->d_Q, p->d_twNs, p->m, p->ldq, ramp, skip);
   cpct_prof_end(p, KID_ADJ_RAY, s);
 }
 template <int LOGG>
@@ -669,11 +731,11 @@ int cpct_radon_setup_attributes(int logG, int logNs) {
   return rc;
 }
 
-int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_t s) {
-  return cpct_launch_fwd_skip(p, d_img, d_sino, nullptr, s);
-}
+namespace {
 
-int cpct_launch_fwd_skip(cpct_plan* p, const float* d_img, float* d_sino, const int* skip, cudaStream_t s) {
+// forward operator; `sino` is M x Ns float32 (cplx = false) or M x Ns
+// interleaved complex64 (cplx = true)
+int launch_fwd_impl(cpct_plan* p, const float* d_img, float* d_sino, bool cplx, const int* skip, cudaStream_t s) {
 #define FG(L) launch_fwd_G<L>(p, d_img, skip, s)
   CPCT_DISPATCH_G(p->logG, FG);
 #undef FG
@@ -704,19 +766,17 @@ int cpct_launch_fwd_skip(cpct_plan* p, const float* d_img, float* d_sino, const 
     k_fwd_interp<<<grid, kInterpThreads, 0, s>>>(p->tmap_Hx, a, p->n_fwd_items);
     cpct_prof_end(p, KID_FWD_INTERP, s);
   }
-#define FN(L) launch_fwd_Ns<L>(p, d_sino, skip, s)
+#define FN(L) launch_fwd_Ns<L>(p, d_sino, cplx, skip, s)
   CPCT_DISPATCH_NS(p->logNs, FN);
 #undef FN
   return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
 }
 
-int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_t s) {
-  return cpct_launch_adj_ramp(p, d_sino, d_img, 0.f, nullptr, s);
-}
-
-int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float ramp, const int* skip,
-                         cudaStream_t s) {
-#define AN(L) launch_adj_Ns<L>(p, d_sino, ramp, skip, s)
+// adjoint operator; `partials` holds the partial tiles of the split heavy
+// tiles (the plan's own buffer, or the allocation-free entry point's array)
+int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, float ramp, const int* skip,
+                    float2* partials, cudaStream_t s) {
+#define AN(L) launch_adj_Ns<L>(p, d_sino, cplx, ramp, skip, s)
   CPCT_DISPATCH_NS(p->logNs, AN);
 #undef AN
   AdjSpreadArgs a;
@@ -725,7 +785,7 @@ int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float 
   a.ray = p->d_ray;
   a.Qt = p->d_Q;
   a.Ax = p->d_Ax;
-  a.partials = p->d_partials;
+  a.partials = partials;
   a.err = p->d_err;
   a.G = p->G;
   a.ldq = p->ldq;
@@ -734,6 +794,8 @@ int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float 
   a.ext_rows = p->ext_rows;
   a.poly = p->poly;
   a.skip = skip;
+  // every partial tile is written in full by its work item before the
+  // reduce reads it, so the partial tiles need no clearing between calls
   if (p->n_adj_items > 0) {
     cpct_prof_begin(p, KID_ADJ_SPREAD, s);
     k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
@@ -741,15 +803,41 @@ int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float 
   }
   if (p->n_split > 0) {
     cpct_prof_begin(p, KID_ADJ_REDUCE, s);
-    k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, p->d_partials, p->d_Ax, p->tiles_x_adj,
-                                                             p->ldh, p->ext_rows, skip);
+    k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, partials, p->d_Ax, p->tiles_x_adj, p->ldh,
+                                                             p->ext_rows, skip);
     cpct_prof_end(p, KID_ADJ_REDUCE, s);
   }
-
 #define AG(L) launch_adj_G<L>(p, d_img, skip, s)
   CPCT_DISPATCH_G(p->logG, AG);
 #undef AG
   return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+}
+
+}  // namespace
+
+int cpct_launch_fwd(cpct_plan* p, const float* d_img, float* d_sino, cudaStream_t s) {
+  return launch_fwd_impl(p, d_img, d_sino, false, nullptr, s);
+}
+
+int cpct_launch_fwd_skip(cpct_plan* p, const float* d_img, float* d_sino, const int* skip, cudaStream_t s) {
+  return launch_fwd_impl(p, d_img, d_sino, false, skip, s);
+}
+
+int cpct_launch_fwd_c(cpct_plan* p, const float* d_img, float2* d_sino_c, cudaStream_t s) {
+  return launch_fwd_impl(p, d_img, reinterpret_cast<float*>(d_sino_c), true, nullptr, s);
+}
+
+int cpct_launch_adj(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_t s) {
+  return launch_adj_impl(p, d_sino, d_img, false, 0.f, nullptr, p->d_partials, s);
+}
+
+int cpct_launch_adj_ramp(cpct_plan* p, const float* d_sino, float* d_img, float ramp, const int* skip,
+                         cudaStream_t s) {
+  return launch_adj_impl(p, d_sino, d_img, false, ramp, skip, p->d_partials, s);
+}
+
+int cpct_launch_adj_c(cpct_plan* p, const float2* d_sino_c, float* d_img, cudaStream_t s) {
+  return launch_adj_impl(p, reinterpret_cast<const float*>(d_sino_c), d_img, true, 0.f, nullptr, p->d_partials, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -800,32 +888,7 @@ extern "C" int radon_adj_noalloc(cpct_plan* p, const float* d_sino, float* d_img
   int status = CPCT_OK;
   float2* partials = noalloc_scratch(&status);
   if (!partials) return status;
-#define AN(L) launch_adj_Ns<L>(p, d_sino, 0.f, nullptr, s)
-  CPCT_DISPATCH_NS(p->logNs, AN);
-#undef AN
-  AdjSpreadArgs a;
-  a.items = p->d_adj_items;
-  a.ids = p->d_adj_ids;
-  a.ray = p->d_ray;
-  a.Qt = p->d_Q;
-  a.Ax = p->d_Ax;
-  a.partials = partials;
-  a.err = p->d_err;
-  a.G = p->G;
-  a.ldq = p->ldq;
-  a.ldh = p->ldh;
-  a.tiles_x = p->tiles_x_adj;
-  a.ext_rows = p->ext_rows;
-  a.poly = p->poly;
-  a.skip = nullptr;
-  // every partial tile is written in full by its work item before the reduce
-  // reads it, so the array needs no clearing between calls
-  if (p->n_adj_items > 0) k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
-  if (p->n_split > 0)
-    k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, partials, p->d_Ax, p->tiles_x_adj, p->ldh,
-                                                             p->ext_rows, nullptr);
-#define AG(L) launch_adj_G<L>(p, d_img, nullptr, s)
-  CPCT_DISPATCH_G(p->logG, AG);
-#undef AG
-  return cudaGetLastError() == cudaSuccess ? CPCT_OK : CPCT_ECUDA;
+  // the same kernels, in the same order and with the same profiling
+  // brackets, as radon_adj; only the partial tiles live elsewhere
+  return launch_adj_impl(p, d_sino, d_img, false, 0.f, nullptr, partials, s);
 }

@@ -795,6 +795,13 @@ __global__ void __launch_bounds__(kRB) k_spg_setup(SpgVec V, double tau0) {
   st->type = T_INIT;
   st->ps = 0.0;
   st->skip_fwd = 0;
+  if (!isfinite(st->bnorm) || !isfinite(st->tau)) {
+    // NaN / Inf in the data or the warm start: stop before the first tick
+    st->status = S_NONFINITE;
+    st->done = 1;
+    st->skip_fwd = 1;
+    st->skip_adj = 1;
+  }
 }
 
 // final ||x||_1 and ||r||_2 (ignores the done flag)

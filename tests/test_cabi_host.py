@@ -140,3 +140,17 @@ def test_source_digest_is_independent_of_the_checkout_location(monkeypatch):
     assert build.radon_digest() == d0
     monkeypatch.setattr(build, "NVCC_FLAGS", moved + ["-DDIGEST_PROBE"])
     assert build.radon_digest() != d0
+
+
+def test_adjoint_work_items_and_noalloc_bound(cpct):
+    """The default plan of the 2048^2 / 1024-view benchmark splits a few heavy
+    origin tiles into partial tiles that fit the allocation-free entry point's
+    512-slot array; smaller caps split more tiles (more slots), and the slot
+    count is the same function of the geometry on every call."""
+    d = cpct.debug_adj_items(2048, 2048, 1024)
+    assert d["n_split"] > 0 and 0 < d["n_slots"] <= 512, d
+    d16 = cpct.debug_adj_items(2048, 2048, 1024, 16)
+    assert d16["n_slots"] > d["n_slots"] and d16["items"] > d["items"]
+    assert cpct.debug_adj_items(2048, 2048, 1024) == d
+    small = cpct.debug_adj_items(64, 64, 10)
+    assert small["n_split"] == 0 and small["n_slots"] == 0

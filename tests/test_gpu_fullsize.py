@@ -56,6 +56,34 @@ def test_batched_operator_full_size_sampled(torch_cuda):
     bt.close()
 
 
+def test_adjoint_full_size_2048_against_oracle(torch_cuda):
+    """The 2048^2 / 1024-view adjoint element by element: a sinogram that is
+    non-zero on 256 rays (ray 0, ray M/2 and 254 others) is gridded back by
+    the FP64 oracle (ray DFT, spread of those rays' samples, inverse 2D FFT,
+    crop and deapodize) and by the device, in the benchmark's plan."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    n, m = 2048, 1024
+    rng = np.random.default_rng(2048)
+    rays = np.unique(np.concatenate([[0, m // 2], rng.choice(m, 254, replace=False)]))
+    w = np.zeros((m, n), dtype=np.float32)
+    w[rays] = rng.standard_normal((len(rays), n)).astype(np.float32)
+    p = cpct.Plan(n, n, m)
+    z = p.adj(torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    p.sync()
+    geo = nufft.GridGeometry(n, n, nufft.default_angles(m))
+    G = geo.grid
+    Pt = nufft.ray_idft_adj(w[rays].astype(np.float64))
+    Yh = nufft.grid_spread(Pt, geo, rays)
+    ref = nufft.grid_crop_deapod(nufft.ifft2(Yh) * (G * G), geo).real
+    zd = z.cpu().numpy().astype(np.float64)
+    e = _rel(zd, ref)
+    emax = float(np.abs(zd - ref).max() / np.abs(ref).max())
+    print(f"2048 adjoint vs oracle on {len(rays)} rays: rel L2 {e:.2e}, max {emax:.2e}")
+    assert e < 1e-5
+
+
 def test_spgl1_full_size_root_by_oracle(torch_cuda):
     torch = torch_cuda
     from paper_1009_1380_gb300 import cpct

@@ -123,6 +123,26 @@ def test_spgl1_warm_start_and_basis_pursuit_flag(torch_cuda):
     assert i3["status"] in (1, 3)
 
 
+@pytest.mark.parametrize("where", ["b", "x0"])
+def test_spgl1_nonfinite_input(torch_cuda, where):
+    """A NaN in the data or in the warm start ends the solve with
+    CPCT_ENONFINITE (status 5) instead of iterating on NaNs."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    n, m = 32, 16
+    geo, x_true, b, sigma = _problem(n, m, seed=9)
+    b32 = b.astype(np.float32)
+    x0 = np.zeros((n, n), dtype=np.float32)
+    if where == "b":
+        b32[3, 5] = np.nan
+    else:
+        x0[7, 7] = np.nan
+    p = cpct.Plan(n, n, m)
+    with pytest.raises(cpct.CpctError) as ei:
+        cpct.spgl1(p, torch.from_numpy(b32).cuda(), sigma, x0=torch.from_numpy(x0).cuda())
+    assert ei.value.status == -5
+
+
 def _proj_case(case, rng):
     if case == "gauss":
         v = rng.standard_normal(1 << 20)
