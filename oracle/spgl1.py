@@ -11,43 +11,91 @@ solved with SPGL1 (van den Berg and Friedlander, SIAM J. Sci. Comput. 31(2),
 is an orthogonal projector, filter(Radon{x} - data) = (F R) x - F data, so the
 solver is applied to A = F R with right-hand side F data and sigma = eps.
 
-The published method, restated:
+The published method, restated (paper and its public reference code):
 
-* the Pareto curve phi(tau) = ||b - A x_tau||_2, where x_tau solves the LASSO
-  problem  min ||A x - b||_2  s.t. ||x||_1 <= tau, is convex, decreasing and
-  differentiable with phi'(tau) = -||A^T r_tau||_inf / ||r_tau||_2;
+* Pareto curve phi(tau) = ||b - A x_tau||_2, x_tau a solution of the LASSO
+  problem  min ||A x - b||_2  s.t. ||x||_1 <= tau; phi is convex, decreasing
+  and differentiable, phi'(tau) = -||A^T r_tau||_inf / ||r_tau||_2;
 * the root phi(tau) = sigma is found by Newton's method,
-  tau <- tau + (||r|| - sigma) ||r|| / ||A^T r||_inf, each LASSO problem being
-  solved only as accurately as the current root error requires (duality gap);
-* each LASSO problem is solved by the spectral projected gradient method:
-  x <- P_tau(x - alpha g) with g = -A^T r, Barzilai-Borwein step lengths
-  alpha = s^T s / s^T y, and a non-monotone backtracking search along the
-  projection arc against the maximum of the last few objective values;
+  tau <- tau + (||r|| - sigma) ||r|| / ||A^T r||_inf, each LASSO problem
+  solved only roughly: tau is updated when the objective f = ||r||^2 / 2
+  stops decreasing (relative change <= dec_tol while ||r|| > 2 sigma, and
+  below a tenth of the root error once ||r|| <= 2 sigma), never two
+  iterations in a row; the Barzilai-Borwein step is kept across updates;
+  when tau decreases, x is projected onto the smaller ball;
+* exit tests at the top of every iteration, in this order: least-squares
+  solution (||g||_inf <= ls_tol ||r||); and, when the duality gap is small
+  (|r^T (r - b) + tau ||g||_inf| / max(1, f) <= max(opt_tol, |f - sigma^2/2|
+  / max(1, f))) or the root error is <= opt_tol: suboptimal BP (||r|| <=
+  sigma), overridden by root found (root error <= opt_tol), overridden by
+  BP solution (||r|| <= bp_tol ||b||); with
+  a single fixed tau (the LASSO problem alone): optimal when the gap is <=
+  opt_tol or ||r|| < opt_tol ||b||;
+* each iteration is a spectral projected-gradient step: a non-monotone
+  search along the projection arc x(s) = P_tau(x - s g), starting at the
+  Barzilai-Borwein step s = gstep (s^T s / s^T y of the last step, clamped
+  to [step_min, step_max]), halving it, against the largest of the last
+  `memory` objective values (values with f <= sigma^2/2 are not recorded);
+  if two consecutive rejected trials move x by displacements of the same
+  norm (to 1e-6), the arc is flat and the gradient is rescaled so that the
+  next displacement is a fraction 2^-k of the last one (k = 0, 1, ... per
+  rescaling within the search);
+* if the arc search fails (no sufficient decrease within max_line halvings,
+  or a trial with no descent), a backtracking search along the fixed
+  feasible direction d = P_tau(x - gstep g) - x follows (safeguarded
+  quadratic interpolation of the step, else halving); if that fails too, x
+  is kept, step_max is divided by 10 (at most max_line_errors times, then
+  the solve stops with a line-search error) and gstep = min(step_max,
+  gstep);
 * P_tau is the Euclidean projection onto the l1 ball of radius tau.
 
-Inexact Newton and termination (readings): the LASSO problem for the current
-tau counts as solved when its relative duality gap is <= max(opt_tol,
-relative error in f) or when it stagnates (relative decrease of f in the last
-step <= dec_tol = 1e-4 while ||r|| > 2 sigma, <= 0.1 |(||r|| - sigma)| /
-||r|| otherwise); the tau Newton step is then taken, and the root is accepted
-when | ||r|| - sigma | <= opt_tol max(1, ||b||) at such a point (root error
-measured relative to the data).
+Readings where the published method leaves a choice:
 
-Constants (the paper gives none; readings): memory of 3 objective values,
-sufficient-decrease gamma = 1e-4, step lengths clamped to [1e-16, 1e5],
-a flat projection arc is detected when two consecutive trial displacements
-have the same norm to 1e-6 (the step then jumps to half the displacement's
-scale), after every Newton update of tau the step restarts from the projected
-gradient,
-opt_tol = 1e-4, bp_tol = 1e-6, at most 30 halvings per line search.
+* root error |(||r|| - sigma)| / max(1, ||b||): the root certificate
+  |(||r|| - sigma)| <= opt_tol max(1, ||b||) of the L1 problem's solution
+  (the published code divides by max(1, ||r||), which is 10-30x stricter on
+  the tomography problems here, where ||b|| >> sigma);
+* the stagnation threshold near the root is 0.1 |(||r|| - sigma)| / ||r||,
+  a relative root error: the published 0.1 |(||r|| - sigma)| compares a
+  relative change of f with an absolute residual difference, so it depends
+  on the scale of the data (scaling A and b by c leaves the relative change
+  of f unchanged and multiplies |(||r|| - sigma)| by c); for data with
+  ||r|| ~ 1 the two agree;
+
+* sufficient decrease as in the paper's Algorithm 1: f(x_trial) <
+  f_max + gamma g^T (x_trial - x) on the arc, and f_max + gamma t g^T d at
+  step t along the feasible direction;
+* a first arc trial without descent (g^T (P(x - gstep g) - x) >= 0, i.e.
+  the projected-gradient step does not move x) means x is optimal for the
+  current tau: the iteration ends with x unchanged, without a fallback
+  search or step-max damping (the fallback direction would be the same
+  zero displacement); the unchanged f then counts as stagnation;
+* the fallback search starts at t = 1/2 (interpolated from the first arc
+  trial): its t = 1 point is the first arc trial, already rejected by the
+  same test;
+* after a failed fallback search x, f and r are all restored;
+* after the projection onto a smaller ball, r, f and g are recomputed at
+  the projected x and the non-monotone history restarts from its f: values
+  recorded on the larger ball can lie below every objective value the
+  smaller ball attains, and a search against them cannot succeed (with a
+  superoptimal warm start every search then failed until the line-error
+  limit stopped the solve);
+* a cold start has tau = 0 and x = 0; a warm start x0 has tau =
+  ||x0||_1 unless tau0 is given.
+
+Constants: memory 3, gamma 1e-4, step lengths clamped to [1e-16, 1e5],
+opt_tol 1e-4, bp_tol = ls_tol = 1e-6, dec_tol 1e-4, max_line 10 (at most 11
+trials per search), max_line_errors 10.
 
 Parity pins (tests/test_oracle_spgl1.py): the l1 projection is pinned by its
 optimality conditions and by an independent bisection; the solver with
-sigma = 0 is pinned against a linear-programming solve of basis pursuit and
-with sigma > 0 by the optimality certificate (root error and duality gap).
-Exact iterate-by-iterate parity with the GPU solver is NOT pinned: FP32
-operator rounding can flip line-search branches ("parity unpinned" for the
-iterate sequence; final-point parity is pinned by the certificate).
+sigma = 0 is pinned against a linear-programming solve of basis pursuit,
+with sigma > 0 by the optimality certificate and an independent SLSQP
+solve, and the fixed-tau LASSO solution by its duality gap and an
+independent projected-gradient solve.  Exact iterate-by-iterate parity with
+the GPU solver is NOT pinned: FP32 operator rounding can flip line-search
+branches ("parity unpinned" for the iterate sequence; final-point parity is
+pinned by the certificate).
 """
 from __future__ import annotations
 
@@ -107,6 +155,9 @@ EXIT_ROOT_FOUND = 1
 EXIT_BP_FOUND = 2
 EXIT_ITERATIONS = 3
 EXIT_LINE_ERROR = 4
+EXIT_LEAST_SQUARES = 6
+EXIT_SUBOPTIMAL_BP = 7
+EXIT_OPTIMAL = 8
 
 
 @dataclass
@@ -114,13 +165,14 @@ class Options:
     max_iter: int = 300
     opt_tol: float = 1e-4
     bp_tol: float = 1e-6
+    ls_tol: float = 1e-6
+    dec_tol: float = 1e-4
     memory: int = 3
     gamma: float = 1e-4
     step_min: float = 1e-16
     step_max: float = 1e5
-    max_line: int = 30
-    dec_tol: float = 1e-4
-    restart_step: bool = True
+    max_line: int = 10
+    max_line_errors: int = 10
 
 
 @dataclass
@@ -129,6 +181,9 @@ class Info:
     iterations: int = 0
     n_prod_A: int = 0
     n_prod_At: int = 0
+    n_newton: int = 0
+    n_line_errors: int = 0
+    n_safeguard: int = 0
     tau: float = 0.0
     rnorm: float = 0.0
     xnorm1: float = 0.0
@@ -136,8 +191,14 @@ class Info:
     history: list = field(default_factory=list)
 
 
-def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
-    """Solve min ||x||_1 s.t. ||A x - b||_2 <= sigma.
+def _clamp_step(v, o, step_max):
+    return min(step_max, max(o.step_min, v))
+
+
+def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None, single_tau=False):
+    """Solve min ||x||_1 s.t. ||A x - b||_2 <= sigma (Pareto root finding), or,
+    with ``single_tau``, the LASSO problem min ||A x - b||_2 s.t. ||x||_1 <=
+    tau0 alone (sigma ignored).
 
     ``A`` and ``At`` are callables (real arrays in, real arrays out).  Returns
     (x, Info).  ``x0`` warm-starts the iterate; ``tau0`` defaults to 0 for a
@@ -147,6 +208,10 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
     info = Info()
     b = np.asarray(b, dtype=np.float64)
     bnorm = float(np.linalg.norm(b))
+    if single_tau:
+        if tau0 is None:
+            raise ValueError("a single-tau (LASSO) solve needs tau0")
+        sigma = 0.0
 
     def Ax(x):
         info.n_prod_A += 1
@@ -156,135 +221,153 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
         info.n_prod_At += 1
         return At(r)
 
+    def f_of(r):
+        return 0.5 * float(r.ravel() @ r.ravel())
+
     if x0 is None:
-        x = None
+        x = np.zeros(Atr(b).shape)
+        info.n_prod_At -= 1  # shape query only
         tau = 0.0 if tau0 is None else float(tau0)
     else:
         x = np.asarray(x0, dtype=np.float64)
         tau = float(np.abs(x).sum()) if tau0 is None else float(tau0)
-    if x is None:
-        xshape = Atr(b).shape
-        x = np.zeros(xshape)
+    step_max = o.step_max
+    line_errors_left = o.max_line_errors
+
     x = project_l1(x, tau)
     r = b - Ax(x)
     g = -Atr(r)
-    f = 0.5 * float(r.ravel() @ r.ravel())
+    f = f_of(r)
+    fhist = [-np.inf] * o.memory
+    fhist[0] = f
+    f_old = f
+    dx = project_l1(x - g, tau) - x
+    dxn = float(np.abs(dx).max()) if dx.size else 0.0
+    gstep = step_max if dxn < 1.0 / step_max else _clamp_step(1.0 / dxn, o, step_max)
 
-    def pg_step(x, g, tau):
-        # step length 1 / ||P_tau(x - g) - x||_inf from the projected gradient
-        dx = project_l1(x - g, tau) - x
-        dxn = float(np.abs(dx).max()) if dx.size else 0.0
-        return o.step_max if dxn < 1.0 / o.step_max else min(o.step_max, max(o.step_min, 1.0 / dxn))
-
-    alpha = pg_step(x, g, tau)
-
-    fhist = [f]
     it = 0
-    f_old = None
-    n_stationary = 0
+    upd_last = False
+    status = 0
     while True:
-        rnorm = float(np.linalg.norm(r))
+        # ---- exit tests and Newton update of tau (top of the iteration) ----
         gnorm = float(np.abs(g).max())
-        # duality gap of the current LASSO problem, in the scale of f
+        rnorm = float(np.linalg.norm(r))
         gap = float(r.ravel() @ (r - b).ravel()) + tau * gnorm
         rel_gap = abs(gap) / max(1.0, f)
-        err_root = abs(rnorm - sigma) / max(1.0, bnorm)
-        err_f = abs(f - 0.5 * sigma ** 2) / max(1.0, f)
+        aerr1 = rnorm - sigma
+        rerr1 = abs(aerr1) / max(1.0, bnorm)
+        rerr2 = abs(f - 0.5 * sigma ** 2) / max(1.0, f)
         info.history.append((it, tau, rnorm, rel_gap))
-
-        status = 0
-        # the current LASSO problem is solved as accurately as the distance
-        # to the root requires: certified by its duality gap, or stagnant
-        # (objective decrease below 1e-4 relative far from the root, below a
-        # tenth of the relative root error near it)
-        solved_sub = rel_gap <= max(o.opt_tol, err_f)
-        if f_old is not None and f > 0:
-            dec = abs(f - f_old) / f
-            if rnorm > 2 * sigma:
-                solved_sub = solved_sub or dec <= o.dec_tol
-            else:
-                solved_sub = solved_sub or dec <= 0.1 * abs(rnorm - sigma) / max(rnorm, 1e-300)
-        if solved_sub:
-            if err_root <= o.opt_tol:
-                status = EXIT_ROOT_FOUND
-            elif gnorm <= o.bp_tol * rnorm or rnorm <= o.bp_tol * bnorm:
-                status = EXIT_BP_FOUND
-        if status == 0 and it >= o.max_iter:
+        if single_tau:
+            if rel_gap <= o.opt_tol or rnorm < o.opt_tol * bnorm:
+                status = EXIT_OPTIMAL
+        else:
+            if gnorm <= o.ls_tol * rnorm:
+                status = EXIT_LEAST_SQUARES
+            if rel_gap <= max(o.opt_tol, rerr2) or rerr1 <= o.opt_tol:
+                if rnorm <= sigma:
+                    status = EXIT_SUBOPTIMAL_BP
+                if rerr1 <= o.opt_tol:
+                    status = EXIT_ROOT_FOUND
+                if rnorm <= o.bp_tol * bnorm:
+                    status = EXIT_BP_FOUND
+            change = abs(f - f_old)
+            near = 0.1 * abs(rnorm - sigma) / max(rnorm, 1e-300)
+            stagnant = (change <= o.dec_tol * f and rnorm > 2 * sigma) or (change <= near * f and rnorm <= 2 * sigma)
+            upd = stagnant and not status and not upd_last
+            upd_last = upd
+            if upd:
+                tau_old = tau
+                tau = max(0.0, tau + rnorm * aerr1 / gnorm)
+                info.n_newton += 1
+                shrink = tau < tau_old
+                if shrink:
+                    # the ball shrank: x is projected onto it, and the
+                    # residual, objective, gradient and the non-monotone
+                    # history restart at the projected point (objective
+                    # values recorded on the larger ball are below what the
+                    # smaller one can attain)
+                    x = project_l1(x, tau)
+                    r = b - Ax(x)
+                    g = -Atr(r)
+                    f = f_of(r)
+                    fhist = [-np.inf] * o.memory
+                    fhist[0] = f
+        if not status and it >= o.max_iter:
             status = EXIT_ITERATIONS
         if status:
             break
 
-        if solved_sub and gnorm > 0:
-            # Newton step on the Pareto curve
-            tau_new = max(0.0, tau + (rnorm - sigma) * rnorm / gnorm)
-            if tau_new < tau:
-                # the ball shrank: project x onto it and bring the residual,
-                # objective and gradient up to date with the projected x
-                x = project_l1(x, tau_new)
-                r = b - Ax(x)
-                g = -Atr(r)
-                f = 0.5 * float(r.ravel() @ r.ravel())
-            tau_was_zero = tau == 0.0
-            tau = tau_new
-            if tau_was_zero or o.restart_step:
-                # leaving tau = 0 (x = 0, no step history yet): restart the
-                # step length from the projected gradient on the new ball
-                alpha = pg_step(x, g, tau)
-
-        # spectral projected gradient step, non-monotone arc search
+        # ---- one spectral projected-gradient iteration ----
         it += 1
-        x_old, g_old, f_old = x, g, f
-        fmax = max(fhist[-o.memory:])
-        step = alpha
-        accepted = False
-        dn_prev = None
-        gn = float(np.linalg.norm(g_old))
-        for _ in range(o.max_line + 1):
-            xt = project_l1(x_old - step * g_old, tau)
+        x_old, f_old, g_old, r_old = x, f, g, r
+        fmax = max(fhist)
+        # non-monotone search along the projection arc
+        step, scale, n_safe, sn = 1.0, 1.0, 0, 0.0
+        gn = float(np.linalg.norm(g))
+        accepted = stationary = False
+        d1 = f1 = gtd1 = None
+        for trial in range(o.max_line + 1):
+            xt = project_l1(x - step * scale * gstep * g, tau)
             rt = b - Ax(xt)
-            ft = 0.5 * float(rt.ravel() @ rt.ravel())
-            d = (xt - x_old).ravel()
-            gtd = float(g_old.ravel() @ d)
-            if gtd >= 0:
-                break  # no descent along the arc: x is stationary for this tau
-            if ft < fmax + o.gamma * gtd:
+            ft = f_of(rt)
+            s = (xt - x).ravel()
+            gts = float(g.ravel() @ s)
+            if trial == 0:
+                d1, f1, gtd1 = s.reshape(x.shape), ft, gts
+            if gts >= 0:
+                stationary = trial == 0
+                break
+            if ft < fmax + o.gamma * gts:
                 accepted = True
                 break
-            dn = float(np.linalg.norm(d))
-            if dn_prev is not None and abs(dn - dn_prev) <= 1e-6 * dn and gn > 0:
-                # the arc is flat here (the projection saturates for long
-                # steps): jump to the step whose gradient move is half the
-                # current displacement
-                step = min(0.5 * step, 0.5 * dn / gn)
-            else:
-                step *= 0.5
-            dn_prev = dn
-        if not accepted and gtd < 0 and ft < f_old:
-            accepted = True  # halvings exhausted, but f decreased
-        if not accepted:
-            # no descent along the arc, or no measurable decrease after every
-            # halving: x is stationary for the current LASSO problem to the
-            # working precision, which is then solved (f unchanged registers
-            # as stagnation at the next check); only repeated stationarity
-            # without progress is a failure
-            n_stationary += 1
-            if n_stationary > 3:
-                info.status = EXIT_LINE_ERROR
+            step *= 0.5
+            sn_old, sn = sn, float(np.linalg.norm(s))
+            if abs(sn - sn_old) <= 1e-6 * sn and gn > 0:
+                # flat arc: rescale so that the next displacement is
+                # step * |s| / 2^n_safe
+                scale = sn / (gstep * gn) / 2.0 ** n_safe
+                n_safe += 1
+                info.n_safeguard += 1
+        if not accepted and not stationary:
+            # feasible-direction search along d1 (its t = 1 point is the
+            # first arc trial, already rejected)
+            t, fnew = 1.0, f1
+            for _ in range(o.max_line):
+                if t <= 0.1:
+                    t *= 0.5
+                else:
+                    den = 2.0 * (fnew - f - t * gtd1)
+                    tmp = (-gtd1 * t * t) / den if den != 0 else np.nan
+                    t = tmp if (np.isfinite(tmp) and 0.1 <= tmp <= 0.9 * t) else 0.5 * t
+                xt = x + t * d1
+                rt = b - Ax(xt)
+                fnew = ft = f_of(rt)
+                if ft < fmax + o.gamma * t * gtd1:
+                    accepted = True
+                    break
+        if accepted:
+            x, r, f = xt, rt, ft
+            g = -Atr(r)
+            s = (x - x_old).ravel()
+            yv = (g - g_old).ravel()
+            sts, sty = float(s @ s), float(s @ yv)
+            gstep = step_max if sty <= 0 else _clamp_step(sts / sty, o, step_max)
+        elif stationary:
+            pass  # x optimal for this tau: unchanged f registers as stagnation
+        else:
+            x, f, g, r = x_old, f_old, g_old, r_old
+            info.n_line_errors += 1
+            if line_errors_left <= 0:
+                status = EXIT_LINE_ERROR
                 break
-            continue
-        n_stationary = 0
-        x, r, f = xt, rt, ft
-        g = -Atr(r)
-        s = (x - x_old).ravel()
-        yv = (g - g_old).ravel()
-        sts = float(s @ s)
-        sty = float(s @ yv)
-        alpha = o.step_max if sty <= 0 else min(o.step_max, max(o.step_min, sts / sty))
-        if f > 0.5 * sigma ** 2:
-            fhist.append(f)
+            step_max /= 10.0
+            line_errors_left -= 1
+            gstep = min(step_max, gstep)
+        if single_tau or f > 0.5 * sigma ** 2:
+            fhist[it % o.memory] = f
 
-    if info.status == 0:
-        info.status = status
+    info.status = status
     info.iterations = it
     info.tau = tau
     info.rnorm = float(np.linalg.norm(r))
@@ -293,3 +376,9 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None):
     gap = float(r.ravel() @ (r - b).ravel()) + tau * gnorm
     info.rel_gap = abs(gap) / max(1.0, 0.5 * info.rnorm ** 2)
     return x, info
+
+
+def lasso(A, At, b, tau, x0=None, opts: Options | None = None):
+    """The LASSO problem min ||A x - b||_2 s.t. ||x||_1 <= tau by the same
+    spectral projected gradient (SPGL1 with a single fixed tau)."""
+    return spgl1(A, At, b, 0.0, x0=x0, tau0=tau, opts=opts, single_tau=True)

@@ -136,29 +136,66 @@ def test_warm_start_at_the_solution_stays_there():
     assert np.linalg.norm(x2 - x) <= 1e-3 * np.linalg.norm(x)
 
 
-def test_step_restart_readings_reach_the_same_root():
-    """Both step-length readings (restart from the projected gradient after a
-    Newton update of tau, or keep the Barzilai-Borwein step) satisfy the root
-    certificate and agree on ||x||_1 to the inexactness of the Newton method
-    (opt_tol 1e-6 here)."""
+def test_lasso_fixed_tau_matches_independent_qp():
+    """With a single fixed tau the solver returns the LASSO solution
+    min ||A x - b|| s.t. ||x||_1 <= tau: checked against the same problem as a
+    smooth program in (x+, x-) >= 0 solved by SLSQP, and by its duality gap."""
     A, bf, sigma = _bpdn_problem()
     op, opT = (lambda v: A @ v), (lambda r: A.T @ r)
-    res = []
-    for restart in (True, False):
-        x, info = spgl1.spgl1(op, opT, bf, sigma, opts=spgl1.Options(opt_tol=1e-6, restart_step=restart))
-        assert info.status == spgl1.EXIT_ROOT_FOUND
-        assert abs(info.rnorm - sigma) <= 1e-6 * max(1.0, np.linalg.norm(bf))
-        res.append(np.abs(x).sum())
-    assert abs(res[0] - res[1]) <= 1e-3 * res[0]
+    x_bp, info_bp = spgl1.spgl1(op, opT, bf, sigma)
+    tau = 0.8 * info_bp.tau  # strictly inside the Pareto curve's root
+    # the gap certifies x to first order while f is resolved to FP64 rounding
+    # (second order): a relative gap of 1e-7 is within reach, 1e-10 is not
+    x, info = spgl1.lasso(op, opT, bf, tau, opts=spgl1.Options(opt_tol=1e-7, max_iter=20000))
+    assert info.status == spgl1.EXIT_OPTIMAL, info.status
+    assert abs(np.abs(x).sum() - tau) <= 1e-9 * tau
+    N = A.shape[1]
+    M = np.hstack([A, -A])
+    res = minimize(lambda z: 0.5 * np.sum((M @ z - bf) ** 2), np.full(2 * N, tau / (2 * N)),
+                   jac=lambda z: M.T @ (M @ z - bf), bounds=[(0, None)] * (2 * N),
+                   constraints=[{"type": "ineq", "fun": lambda z: tau - z.sum(), "jac": lambda z: -np.ones_like(z)}],
+                   method="SLSQP", options=dict(maxiter=5000, ftol=1e-14))
+    x_qp = res.x[:N] - res.x[N:]
+    f_sp = 0.5 * np.sum((A @ x - bf) ** 2)
+    f_qp = 0.5 * np.sum((A @ x_qp - bf) ** 2)
+    assert f_sp <= f_qp * (1 + 1e-9)
+    assert np.linalg.norm(x - x_qp) <= 1e-3 * np.linalg.norm(x_qp), np.linalg.norm(x - x_qp) / np.linalg.norm(x_qp)
+    # duality gap of the returned point
+    r = bf - A @ x
+    gap = r @ (r - bf) + tau * np.abs(A.T @ r).max()
+    assert abs(gap) <= 1e-7 * max(1.0, 0.5 * r @ r)
 
 
-def test_tau0_at_the_root_saves_iterations():
-    """Starting from x = 0 with tau0 = the final radius skips the Newton
-    steps of the cold start: fewer iterations, the same root."""
-    A, bf, sigma = _bpdn_problem()
+def test_flat_arc_safeguard_rescales_the_step():
+    """A Barzilai-Borwein step far too long for the ball makes consecutive
+    arc trials project to the same point; the safeguard then shrinks the
+    displacement geometrically, and the search still finds a decrease."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((30, 60))
+    b = rng.standard_normal(30)
     op, opT = (lambda v: A @ v), (lambda r: A.T @ r)
-    x, info = spgl1.spgl1(op, opT, bf, sigma)
-    x2, info2 = spgl1.spgl1(op, opT, bf, sigma, tau0=info.tau)
-    assert info2.status == spgl1.EXIT_ROOT_FOUND
-    assert info2.iterations < info.iterations
-    assert abs(info2.xnorm1 - info.xnorm1) <= 1e-3 * info.xnorm1
+    x, info = spgl1.lasso(op, opT, b, 0.5, opts=spgl1.Options(opt_tol=1e-7, max_iter=5000, step_min=1e5))
+    # step_min = step_max: every iteration starts at a step of 1e5
+    assert info.status == spgl1.EXIT_OPTIMAL, info.status
+    assert info.n_safeguard > 0
+    x_ref, _ = spgl1.lasso(op, opT, b, 0.5, opts=spgl1.Options(opt_tol=1e-7, max_iter=5000))
+    assert np.linalg.norm(x - x_ref) <= 1e-4 * np.linalg.norm(x_ref)
+
+
+def test_warm_start_near_the_solution_saves_iterations():
+    """A warm start close to the solution (x* plus 1% noise, projected onto the
+    ball of the final radius, tau = its l1 norm) reaches the same root in
+    fewer iterations than the cold start; so does the superoptimal start x*
+    plus noise without the projection (tau above the root)."""
+    for seed in (4, 5, 6):
+        A, bf, sigma = _bpdn_problem(seed)
+        op, opT = (lambda v: A @ v), (lambda r: A.T @ r)
+        x, info = spgl1.spgl1(op, opT, bf, sigma)
+        rng = np.random.default_rng(12)
+        xn = x + 0.01 * np.linalg.norm(x) / np.sqrt(x.size) * rng.standard_normal(x.size)
+        for x0 in (spgl1.project_l1(xn, info.tau), xn):
+            x2, info2 = spgl1.spgl1(op, opT, bf, sigma, x0=x0)
+            assert info2.status == spgl1.EXIT_ROOT_FOUND
+            assert info2.n_line_errors == 0
+            assert info2.iterations < info.iterations
+            assert abs(info2.xnorm1 - info.xnorm1) <= 1e-3 * info.xnorm1
