@@ -246,14 +246,21 @@ int cpct_ring_filter(cpct_plan* plan, const float* d_in, float* d_out, cudaStrea
 typedef struct spgl1_opts {
   int max_iter;       /* iteration cap, 300                                     */
   int memory;         /* non-monotone line-search memory, 3 (<= 8)            */
-  int max_line;       /* step halvings per line search, 30                      */
+  int max_line;       /* halvings per line search, 10 (at most 11 arc trials   */
+                      /* and 10 feasible-direction trials per iteration)        */
   int flags;          /* CPCT_SPGL1_* bits                                      */
   double opt_tol;     /* relative duality gap / root tolerance, 1e-4            */
   double bp_tol;      /* basis-pursuit tolerance, 1e-6                          */
   double gamma;       /* sufficient decrease, 1e-4                              */
   double step_min;    /* Barzilai-Borwein step clamp, 1e-16                     */
   double step_max;    /* 1e5                                                    */
-  double tau0;        /* initial l1 radius when CPCT_SPGL1_TAU0 is set          */
+  double tau0;        /* initial l1 radius (CPCT_SPGL1_TAU0), or the fixed      */
+                      /* radius of a LASSO solve (CPCT_SPGL1_LASSO)             */
+  double ls_tol;      /* least-squares exit ||A^T r||_inf <= ls_tol ||r||, 1e-6 */
+  double dec_tol;     /* relative objective decrease that counts as stagnation  */
+                      /* far from the root, 1e-4                                */
+  int max_line_errors;/* failed searches (each divides step_max by 10), 10      */
+  int pad_;
 } spgl1_opts;
 
 #define CPCT_SPGL1_TAU0 0x1       /* start from opts->tau0 instead of ||x0||_1  */
@@ -262,11 +269,21 @@ typedef struct spgl1_opts {
                                   /* acts on u = C z (cpct_synth_dh), so the    */
                                   /* solve is min ||z||_1 s.t.                  */
                                   /* ||F(R C z) - F b|| <= sigma; u = C x after */
+#define CPCT_SPGL1_LASSO 0x8      /* the LASSO problem alone: min ||F(R x) -    */
+                                  /* F b||_2 s.t. ||x||_1 <= opts->tau0, tau    */
+                                  /* fixed, sigma ignored (may be NULL)         */
 
-/* Result record of one solve. status: 1 root found (| ||r|| - sigma | <=
- * opt_tol max(1, ||F b||) at a solved or stagnant LASSO subproblem),
- * 2 basis-pursuit solution, 3 iteration cap, 4 line-search failure,
- * 5 non-finite values. */
+/* Result record of one solve.  status:
+ *   1 root found: | ||r|| - sigma | <= opt_tol max(1, ||F b||) at a point
+ *     whose LASSO problem is nearly optimal (duality gap) or at that root
+ *     error directly, as in the published method's exit test;
+ *   2 basis-pursuit solution (||r|| <= bp_tol ||F b||);
+ *   3 iteration cap;  4 line-search failure (max_line_errors exhausted);
+ *   5 non-finite values;
+ *   6 least-squares solution (||A^T r||_inf <= ls_tol ||r||);
+ *   7 suboptimal BP: ||r|| <= sigma at a nearly optimal LASSO point short
+ *     of the root error;
+ *   8 LASSO optimal (CPCT_SPGL1_LASSO): relative duality gap <= opt_tol. */
 typedef struct spgl1_info {
   int status;
   int iterations;     /* SPGL1 iterations (spectral projected-gradient steps)  */
@@ -276,32 +293,44 @@ typedef struct spgl1_info {
   double rnorm;       /* ||F(R x) - F b||_2                                     */
   double xnorm1;      /* ||x||_1                                                */
   double rel_gap;     /* relative duality gap of the last LASSO subproblem      */
+  int newton;         /* Newton updates of tau                                  */
+  int line_errors;    /* failed line searches                                   */
+  int safeguards;     /* flat-arc rescalings of the arc search                  */
+  int stationary;     /* iterations whose first trial did not move x            */
+  double gstep;       /* final Barzilai-Borwein step                            */
 } spgl1_info;
 
-/* Basis-pursuit denoising  min ||x||_1  s.t.  ||F(R x - b)||_2 <= sigma  by
- * SPGL1 (van den Berg & Friedlander 2008): Newton root-finding on the Pareto
- * curve tau -> ||r_tau||, each LASSO subproblem solved by spectral projected
- * gradient with a non-monotone arc search; FP32 per-element work, partial
- * sums combined in FP64, exact l1-ball projection (cpct_project_l1), and the
- * controller (tau-sigma Newton step, Armijo test, Barzilai-Borwein step,
- * duality gap) in FP64 on the device, one CUDA graph per iteration tick.
+/* Basis-pursuit denoising  min ||x||_1  s.t.  ||F(R x - b)||_2 <= sigma by
+ * SPGL1 (van den Berg & Friedlander 2008; the L1 problem of section
+ * "Introduction"): Newton root-finding on the Pareto curve tau -> ||r_tau||
+ * (tau updated when the objective of the current LASSO problem stagnates),
+ * each LASSO problem solved by spectral projected gradient with a
+ * non-monotone search along the projection arc (with the published flat-arc
+ * rescaling), a feasible-direction fallback search and step-max damping
+ * after failed searches; FP32 per-element work, partial sums combined in
+ * FP64, exact l1-ball projection (cpct_project_l1), and the controller
+ * (Newton step, Armijo tests, Barzilai-Borwein step, duality gap) in FP64 on
+ * the device, one CUDA graph per iteration tick.
  *   d_b     device, M*Ns float32 data (read)
- *   sigma   misfit bound eps >= 0 (0: basis pursuit)
+ *   sigma   misfit bound eps >= 0 (0: basis pursuit); ignored with
+ *           CPCT_SPGL1_LASSO
  *   d_x     device, N*N float32: in = warm start (zeros for a cold start),
  *           out = solution; tau starts at ||x0||_1 unless CPCT_SPGL1_TAU0
  *   opts    NULL for defaults;  info  host record, may be NULL
- * Returns CPCT_OK (status 1 or 2), CPCT_ENOTCONV (iteration cap or line-search
- * failure; d_x holds the last iterate), CPCT_ENONFINITE, CPCT_EINVAL,
- * CPCT_ENOMEM, CPCT_ECUDA.  Allocates its workspace (5 N^2 + 4 M Ns floats)
- * for the duration of the call and synchronizes `stream`.  Kernel event
- * profiling of the plan is switched off by this call. */
+ * Returns CPCT_OK (status 1, 2, 6, 7, 8), CPCT_ENOTCONV (iteration cap or
+ * line-search failure; d_x holds the last iterate), CPCT_ENONFINITE (NaN or
+ * Inf in the data, the warm start or a trial), CPCT_EINVAL, CPCT_ENOMEM,
+ * CPCT_ECUDA.  Allocates its workspace (6 N^2 + 4 M Ns floats) for the
+ * duration of the call and synchronizes `stream`.  Kernel event profiling
+ * of the plan is switched off by this call. */
 int spgl1_solve(cpct_plan* plan, const float* d_b, double sigma, float* d_x, const spgl1_opts* opts,
                 spgl1_info* info, cudaStream_t stream);
 
 /* The same for `batch` independent slices solved together (one graph whose
  * branches run the slices concurrently).  Each slice needs its own plan (a
- * plan holds per-call workspaces); arrays are host arrays of `batch` entries;
- * info is an array of `batch` records. */
+ * plan holds per-call workspaces); arrays are host arrays of `batch` entries
+ * (sigma may be NULL with CPCT_SPGL1_LASSO); info is an array of `batch`
+ * records. */
 int spgl1_solve_batched(cpct_plan* const* plans, int batch, const float* const* d_b, const double* sigma,
                         float* const* d_x, const spgl1_opts* opts, spgl1_info* info, cudaStream_t stream);
 

@@ -65,11 +65,18 @@ Readings where the published method leaves a choice:
 * sufficient decrease as in the paper's Algorithm 1: f(x_trial) <
   f_max + gamma g^T (x_trial - x) on the arc, and f_max + gamma t g^T d at
   step t along the feasible direction;
-* a first arc trial without descent (g^T (P(x - gstep g) - x) >= 0, i.e.
-  the projected-gradient step does not move x) means x is optimal for the
-  current tau: the iteration ends with x unchanged, without a fallback
-  search or step-max damping (the fallback direction would be the same
-  zero displacement); the unchanged f then counts as stagnation;
+* a first arc trial without descent (g^T (P(x - gstep g) - x) >= 0) at a
+  point the exit tests did not certify: for x in the ball this happens only
+  when the displacement is at the level of rounding -- the projection then
+  mostly pulls x back onto the ball's surface, which x misses by the
+  rounding of its l1 norm -- i.e. the Barzilai-Borwein step is too short
+  for the working precision.  The iteration ends with x unchanged (which
+  counts as stagnation for the tau update) and the next one restarts from
+  the projected-gradient step 1 / ||P(x - g) - x||_inf, the solver's
+  initial step; no fallback search or step-max damping (the fallback
+  direction is that same rounding-level displacement).  With a fixed tau,
+  three such iterations in a row end the solve as a line-search failure
+  (no descent at the working precision);
 * the fallback search starts at t = 1/2 (interpolated from the first arc
   trial): its t = 1 point is the first arc trial, already rejected by the
   same test;
@@ -184,6 +191,7 @@ class Info:
     n_newton: int = 0
     n_line_errors: int = 0
     n_safeguard: int = 0
+    n_stationary: int = 0
     tau: float = 0.0
     rnorm: float = 0.0
     xnorm1: float = 0.0
@@ -246,6 +254,7 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None, sing
     gstep = step_max if dxn < 1.0 / step_max else _clamp_step(1.0 / dxn, o, step_max)
 
     it = 0
+    n_nodescent = 0
     upd_last = False
     status = 0
     while True:
@@ -346,6 +355,8 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None, sing
                 if ft < fmax + o.gamma * t * gtd1:
                     accepted = True
                     break
+        if not stationary:
+            n_nodescent = 0
         if accepted:
             x, r, f = xt, rt, ft
             g = -Atr(r)
@@ -354,7 +365,21 @@ def spgl1(A, At, b, sigma, x0=None, tau0=None, opts: Options | None = None, sing
             sts, sty = float(s @ s), float(s @ yv)
             gstep = step_max if sty <= 0 else _clamp_step(sts / sty, o, step_max)
         elif stationary:
-            pass  # x optimal for this tau: unchanged f registers as stagnation
+            # the projected-gradient step from the BB length does not move x
+            # downhill.  Unless the duality gap already certifies x (the exit
+            # tests would have stopped), the step is too short for the
+            # working precision: the next iteration restarts from the
+            # projected-gradient step length 1 / ||P(x - g) - x||_inf, the
+            # solver's initial step.  x is unchanged, which registers as
+            # stagnation of f for the tau update.
+            n_nodescent += 1
+            info.n_stationary += 1
+            if single_tau and n_nodescent > 2:
+                status = EXIT_LINE_ERROR
+                break
+            dx = project_l1(x - g, tau) - x
+            dxn = float(np.abs(dx).max()) if dx.size else 0.0
+            gstep = step_max if dxn < 1.0 / step_max else _clamp_step(1.0 / dxn, o, step_max)
         else:
             x, f, g, r = x_old, f_old, g_old, r_old
             info.n_line_errors += 1

@@ -348,6 +348,7 @@ def debug_rounds(n, n_det, n_views, angles=None):
 SPGL1_TAU0 = 0x1
 SPGL1_NO_FILTER = 0x2
 SPGL1_SYNTH_DH = 0x4
+SPGL1_LASSO = 0x8
 SPGL1_STATUS = {1: "root found", 2: "basis pursuit solution", 3: "iteration cap", 4: "line search failure",
                 5: "non-finite"}
 
@@ -356,16 +357,19 @@ class Spgl1Opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("memory", ctypes.c_int), ("max_line", ctypes.c_int),
                 ("flags", ctypes.c_int), ("opt_tol", ctypes.c_double), ("bp_tol", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("step_min", ctypes.c_double), ("step_max", ctypes.c_double),
-                ("tau0", ctypes.c_double)]
+                ("tau0", ctypes.c_double), ("ls_tol", ctypes.c_double), ("dec_tol", ctypes.c_double),
+                ("max_line_errors", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class Spgl1Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("ticks", ctypes.c_int),
                 ("trials", ctypes.c_int), ("tau", ctypes.c_double), ("rnorm", ctypes.c_double),
-                ("xnorm1", ctypes.c_double), ("rel_gap", ctypes.c_double)]
+                ("xnorm1", ctypes.c_double), ("rel_gap", ctypes.c_double), ("newton", ctypes.c_int),
+                ("line_errors", ctypes.c_int), ("safeguards", ctypes.c_int), ("stationary", ctypes.c_int),
+                ("gstep", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
 def _spgl1_setup():
@@ -420,14 +424,16 @@ def project_l1(v, tau, out=None, stream=None):
 
 
 def make_opts(max_iter=0, opt_tol=0.0, bp_tol=0.0, memory=0, max_line=0, tau0=None, ring_filter=True,
-              synth_dh=False):
+              synth_dh=False, lasso_tau=None, step_min=0.0, step_max=0.0):
     """SPGL1 options (0 = default).  synth_dh: the analysis-l1 variant, the
-    solution is z with the image u = synth_dh(z)."""
+    solution is z with the image u = synth_dh(z).  lasso_tau: solve the LASSO
+    problem with that fixed radius instead (sigma ignored)."""
     o = Spgl1Opts()
     o.max_iter, o.opt_tol, o.bp_tol, o.memory, o.max_line = max_iter, opt_tol, bp_tol, memory, max_line
+    o.step_min, o.step_max = step_min, step_max
     o.flags = ((0 if ring_filter else SPGL1_NO_FILTER) | (SPGL1_TAU0 if tau0 is not None else 0)
-               | (SPGL1_SYNTH_DH if synth_dh else 0))
-    o.tau0 = 0.0 if tau0 is None else float(tau0)
+               | (SPGL1_SYNTH_DH if synth_dh else 0) | (SPGL1_LASSO if lasso_tau is not None else 0))
+    o.tau0 = float(lasso_tau) if lasso_tau is not None else (0.0 if tau0 is None else float(tau0))
     return o
 
 

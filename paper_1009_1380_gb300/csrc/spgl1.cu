@@ -206,8 +206,10 @@ extern "C" int cpct_ring_filter(cpct_plan* p, const float* d_in, float* d_out, c
 // ---------------------------------------------------------------------------
 namespace {
 
-enum TickType { T_INIT = 0, T_PG = 1, T_PROJX = 2, T_TRIAL = 3 };
-enum AfterPG { PG_THEN_CHECK = 0, PG_THEN_TRIAL = 1 };
+// tick types: the initial point, the initial step length (projected
+// gradient, no operator), the projection onto a shrunk ball, a trial on the
+// projection arc, a trial along the fixed feasible direction
+enum TickType { T_INIT = 0, T_PG = 1, T_PROJX = 2, T_TRIAL = 3, T_FEAS = 4 };
 constexpr int kHist = 8;        // objective history capacity (memory <= 8)
 // l1-ball projection by radix selection on the FP32 bit patterns of |v|
 // (non-negative floats order like their patterns): three passes over bits
@@ -217,20 +219,25 @@ constexpr int kRadixPasses = 3;
 constexpr int kBins = 2048;
 __host__ __device__ constexpr int radix_shift(int p) { return p == 0 ? 20 : p == 1 ? 9 : 0; }
 __host__ __device__ constexpr int radix_bits(int p) { return p == 2 ? 9 : 11; }
-constexpr double kDecTol = 1e-4;  // stagnation threshold of the inexact Newton test
 
 struct SpgState {
   // options
-  double sigma, opt_tol, bp_tol, gamma, step_min, step_max;
-  int max_iter, max_line, memory, pad0;
+  double sigma, opt_tol, bp_tol, ls_tol, dec_tol, gamma, step_min, step_max;
+  int max_iter, max_line, memory, single_tau;
   // solver scalars (FP64)
-  double tau, bnorm, f, f_old, fmax, alpha, step, dn_prev, rtb, ginf, gnorm2;
+  double tau, bnorm, f, f_old, fmax, gstep, rtb, ginf, gnorm2;
   double fhist[kHist];
-  int nhist, hpos;
   double rel_gap, rnorm;
+  int upd_last, line_errors_left, n_newton, n_line_errors;
   // this tick
-  int type, pg_then, accept_x, accept_r, update_g, line_fail;
-  double ps;
+  int type, accept_x, accept_r, update_g, stationary, go_feas, line_err, store_dir;
+  double ps;      // trial point P_tau(x - ps g) (arc, init, projected gradient)
+  double feas_t;  // trial point x + feas_t d (feasible direction)
+  // the arc search of this iteration
+  double step, scale, sn_prev, f1, gtd1;
+  int nsafe, n_line, n_feas, n_safeguard, n_stationary;
+  int n_nodescent;   // consecutive iterations whose first arc trial had no descent
+  int pg_end_iter;   // the T_PG tick ends an iteration (step restart) rather than the set-up
   // projection of v = x - ps g onto the l1 ball of radius tau
   double theta, c_above, s_above;  // threshold; count and sum of |v| above the selected prefix
   unsigned prefix;                  // selected high bits of the pattern of theta
@@ -238,21 +245,25 @@ struct SpgState {
   // mid-tick results
   double ft, gtd, dn2, dinf, rtb_t;
   // counters / status
-  int iter, n_line, status, done, ticks, n_trials, stationary, n_stationary;
+  int iter, status, done, ticks, n_trials;
   // the tick's adjoint operator is skipped (its output unused) while set:
   // no gradient update, or the slice is done
   int skip_adj;
   // the tick's forward operator is skipped while set: the slice is done, or
-  // the tick is a projected-gradient step-length tick (T_PG), which reads
+  // the tick is the projected-gradient step-length tick (T_PG), which reads
   // only x and g and accepts nothing
   int skip_fwd;
 };
 
 // SPGL1 status codes (spgl1_info.status)
-enum { S_RUNNING = 0, S_ROOT = 1, S_BP = 2, S_ITER = 3, S_LINE = 4, S_NONFINITE = 5 };
+enum {
+  S_RUNNING = 0, S_ROOT = 1, S_BP = 2, S_ITER = 3, S_LINE = 4, S_NONFINITE = 5, S_LS = 6, S_SUBOPT = 7,
+  S_OPTIMAL = 8
+};
 
 struct SpgVec {
   float *x, *xt, *xold, *g, *gold, *gtmp;  // image space, n
+  float* dir;                              // image space, n: feasible direction d
   float *y, *rt, *r, *bf;                  // sinogram space, m
   double* part;                            // per-block partials
   unsigned* hcnt;                          // radix histogram: counts (kBins)
@@ -323,7 +334,7 @@ __device__ __forceinline__ float vval(const SpgVec& V, float ps, long long i) { 
 // integer atomic per non-empty bin: the result is independent of order.
 __global__ void __launch_bounds__(kRB) k_spg_radix_hist(SpgVec V, int pass) {
   const SpgState* st = V.st;
-  if (st->done || (pass > 0 && st->proj_done)) return;
+  if (st->done || st->type == T_FEAS || (pass > 0 && st->proj_done)) return;
   __shared__ unsigned hc[kBins];
   __shared__ unsigned long long hs[kBins];
   for (int b = threadIdx.x; b < kBins; b += kRB) {
@@ -352,25 +363,40 @@ __global__ void __launch_bounds__(kRB) k_spg_radix_hist(SpgVec V, int pass) {
     }
 }
 
-// xt = soft(v, theta) and the partials needed by the controllers
+// trial point and the partials needed by the controllers: xt = soft(v,
+// theta) with v = x - ps g (arc trials, initial point, projected gradient),
+// or xt = x + t d along the stored feasible direction d (T_FEAS); the first
+// arc trial of an iteration stores d = xt - x
 __global__ void __launch_bounds__(kRB) k_spg_proj_apply(SpgVec V) {
   const SpgState* st = V.st;
   if (st->done) return;
-  const float ps = (float)st->ps, th = (float)st->theta;
+  const float ps = (float)st->ps, ft = (float)st->feas_t;
+  const double th = st->theta;
   const int ident = st->proj_identity, zero = st->proj_zero;
+  const bool feas = st->type == T_FEAS, store = st->store_dir != 0;
   float q[2] = {0.f, 0.f};  // gtd, dn2
   float dinf = 0.f;
   SPG_LOOP(i, V.n) {
-    const float v = vval(V, ps, i);
+    const float xi = V.x[i];
     float xt;
-    if (zero) xt = 0.f;
-    else if (ident) xt = v;
-    else {
-      const float a = fabsf(v) - th;
-      xt = a > 0.f ? copysignf(a, v) : 0.f;
+    if (feas) {
+      xt = fmaf(ft, V.dir[i], xi);
+    } else {
+      const float v = vval(V, ps, i);
+      if (zero) xt = 0.f;
+      else if (ident) xt = v;
+      else {
+        // |v| - theta in FP64, rounded once: the FP32 output of every
+        // active entry is the correctly rounded exact value, so ||xt||_1
+        // misses tau only by the outputs' own rounding (an FP32 copy of
+        // theta would shift every active entry the same way)
+        const double a = (double)fabsf(v) - th;
+        xt = a > 0.0 ? copysignf((float)a, v) : 0.f;
+      }
     }
     V.xt[i] = xt;
-    const float d = xt - V.x[i];
+    const float d = xt - xi;
+    if (store) V.dir[i] = d;
     q[0] = fmaf(V.g[i], d, q[0]);
     q[1] = fmaf(d, d, q[1]);
     dinf = fmaxf(dinf, fabsf(d));
@@ -492,7 +518,7 @@ __device__ __forceinline__ double gather_max(const double* part, int q) {
 // histogram.
 __global__ void __launch_bounds__(kRB) k_spg_radix_select(SpgVec V, int pass) {
   SpgState* st = V.st;
-  if (st->done || (pass > 0 && st->proj_done)) return;
+  if (st->done || st->type == T_FEAS || (pass > 0 && st->proj_done)) return;
   constexpr int kPer = kBins / kRB;
   __shared__ double scan_c[kRB], scan_s[kRB];
   __shared__ int best;
@@ -583,47 +609,69 @@ __global__ void __launch_bounds__(kRB) k_spg_radix_select(SpgVec V, int pass) {
   }
 }
 
-__device__ void spg_push_hist(SpgState* st, double f) {
-  st->fhist[st->hpos] = f;
-  st->hpos = (st->hpos + 1) % st->memory;
-  if (st->nhist < st->memory) st->nhist++;
+// non-monotone history: every entry -inf, then f0 in the first slot
+__device__ void spg_reset_hist(SpgState* st, double f0) {
+  for (int i = 0; i < kHist; ++i) st->fhist[i] = -INFINITY;
+  st->fhist[0] = f0;
 }
 
+__device__ double spg_clamp_step(const SpgState* st, double v) { return fmin(st->step_max, fmax(st->step_min, v)); }
+
+// start of an SPGL1 iteration: the non-monotone search along the projection
+// arc from the Barzilai-Borwein step gstep
 __device__ void spg_start_trial(SpgState* st) {
   st->iter++;
   st->f_old = st->f;
   double fm = st->fhist[0];
-  for (int i = 1; i < st->nhist; ++i) fm = fmax(fm, st->fhist[i]);
+  for (int i = 1; i < st->memory; ++i) fm = fmax(fm, st->fhist[i]);
   st->fmax = fm;
-  st->step = st->alpha;
+  st->step = 1.0;
+  st->scale = 1.0;
+  st->nsafe = 0;
+  st->sn_prev = 0.0;
   st->n_line = 0;
-  st->dn_prev = -1.0;
+  st->n_feas = 0;
   st->type = T_TRIAL;
-  st->ps = st->step;
+  st->store_dir = 1;
+  st->ps = st->gstep;
 }
 
-// top of an SPGL1 iteration: duality gap, root error, termination, Newton
-// update of tau on the Pareto curve
+// top of an SPGL1 iteration: exit tests in the published order, Newton
+// update of tau on the Pareto curve when the objective stagnates
 __device__ void spg_check(SpgState* st) {
   const double f = st->f, rnorm = sqrt(2.0 * f), gnorm = st->ginf, tau = st->tau, sigma = st->sigma;
   const double gap = 2.0 * f - st->rtb + tau * gnorm;
   const double rel_gap = fabs(gap) / fmax(1.0, f);
-  const double err_root = fabs(rnorm - sigma) / fmax(1.0, st->bnorm);
-  const double err_f = fabs(f - 0.5 * sigma * sigma) / fmax(1.0, f);
+  const double aerr1 = rnorm - sigma;
+  const double rerr1 = fabs(aerr1) / fmax(1.0, st->bnorm);  // root error relative to the data
+  const double rerr2 = fabs(f - 0.5 * sigma * sigma) / fmax(1.0, f);
   st->rel_gap = rel_gap;
   st->rnorm = rnorm;
-  // the LASSO problem counts as solved when its duality gap is small or it
-  // stagnates (relative decrease of f below 1e-4 far from the root, below a
-  // tenth of the relative root error near it); f_old = 0 before the first step
-  bool solved = rel_gap <= fmax(st->opt_tol, err_f);
-  if (st->f_old > 0.0 && f > 0.0) {
-    const double dec = fabs(f - st->f_old) / f;
-    solved = solved || (rnorm > 2.0 * sigma ? dec <= kDecTol : dec <= 0.1 * fabs(rnorm - sigma) / fmax(rnorm, 1e-300));
-  }
   int status = S_RUNNING;
-  if (solved) {
-    if (err_root <= st->opt_tol) status = S_ROOT;
-    else if (gnorm <= st->bp_tol * rnorm || rnorm <= st->bp_tol * st->bnorm) status = S_BP;
+  bool shrink = false;
+  if (st->single_tau) {
+    if (rel_gap <= st->opt_tol || rnorm < st->opt_tol * st->bnorm) status = S_OPTIMAL;
+  } else {
+    if (gnorm <= st->ls_tol * rnorm) status = S_LS;
+    if (rel_gap <= fmax(st->opt_tol, rerr2) || rerr1 <= st->opt_tol) {
+      if (rnorm <= sigma) status = S_SUBOPT;
+      if (rerr1 <= st->opt_tol) status = S_ROOT;
+      if (rnorm <= st->bp_tol * st->bnorm) status = S_BP;
+    }
+    // the LASSO problem of this tau is solved as far as the Newton step
+    // needs once f stops decreasing: relative change <= dec_tol far from
+    // the root, below a tenth of the relative root error near it
+    const double change = fabs(f - st->f_old);
+    const double near = 0.1 * fabs(rnorm - sigma) / fmax(rnorm, 1e-300);
+    const bool stagnant = (change <= st->dec_tol * f && rnorm > 2.0 * sigma) || (change <= near * f && rnorm <= 2.0 * sigma);
+    const bool upd = stagnant && status == S_RUNNING && !st->upd_last;
+    st->upd_last = upd ? 1 : 0;
+    if (upd) {
+      const double tau_new = fmax(0.0, tau + rnorm * aerr1 / gnorm);
+      shrink = tau_new < tau;
+      st->tau = tau_new;
+      st->n_newton++;
+    }
   }
   if (status == S_RUNNING && st->iter >= st->max_iter) status = S_ITER;
   if (status != S_RUNNING) {
@@ -631,16 +679,31 @@ __device__ void spg_check(SpgState* st) {
     st->done = 1;
     return;
   }
-  if (solved && gnorm > 0.0) {
-    const double tau_new = fmax(0.0, tau + (rnorm - sigma) * rnorm / gnorm);
-    const bool shrink = tau_new < tau;
-    st->tau = tau_new;
-    st->pg_then = PG_THEN_TRIAL;
-    st->type = shrink ? T_PROJX : T_PG;
-    st->ps = shrink ? 0.0 : 1.0;
+  if (shrink) {
+    // project x onto the smaller ball; the tick recomputes r, f and g there
+    st->type = T_PROJX;
+    st->ps = 0.0;
+    st->store_dir = 0;
     return;
   }
   spg_start_trial(st);
+}
+
+// end of an iteration (accepted step, stationary point or failed search):
+// record f in the history (not below sigma^2/2 when solving for the root)
+// and run the checks of the next iteration
+__device__ void spg_end_iteration(SpgState* st) {
+  if (st->single_tau || st->f > 0.5 * st->sigma * st->sigma) st->fhist[st->iter % st->memory] = st->f;
+  spg_check(st);
+}
+
+// step along the feasible direction after the trial at t gave f(t) = fnew:
+// safeguarded quadratic interpolation, else halving
+__device__ double spg_feas_next(const SpgState* st, double t, double fnew) {
+  if (t <= 0.1) return 0.5 * t;
+  const double den = 2.0 * (fnew - st->f - t * st->gtd1);
+  const double tmp = den != 0.0 ? (-st->gtd1 * t * t) / den : NAN;
+  return (isfinite(tmp) && tmp >= 0.1 && tmp <= 0.9 * t) ? tmp : 0.5 * t;
 }
 
 // mid-tick controller: what this tick's trial point is accepted as
@@ -657,9 +720,10 @@ __global__ void __launch_bounds__(kRB) k_spg_mid(SpgVec V) {
   st->dinf = dinf;
   st->ft = 0.5 * r[0];
   st->rtb_t = r[1];
-  st->accept_x = st->accept_r = st->update_g = st->line_fail = st->stationary = 0;
+  st->accept_x = st->accept_r = st->update_g = 0;
+  st->stationary = st->go_feas = st->line_err = 0;
   const int type = st->type;
-  if (type == T_INIT || type == T_TRIAL) {
+  if (type != T_PG) {
     if (!isfinite(st->ft) || !isfinite(st->gtd)) {
       st->status = S_NONFINITE;
       st->done = 1;
@@ -668,22 +732,32 @@ __global__ void __launch_bounds__(kRB) k_spg_mid(SpgVec V) {
       return;
     }
   }
-  if (type == T_INIT) {
-    st->accept_x = st->accept_r = st->update_g = 1;
-  } else if (type == T_PROJX) {
-    // x projected onto the shrunk ball: residual, objective and gradient
-    // are brought up to date with it
+  if (type == T_INIT || type == T_PROJX) {
+    // the initial point, or x projected onto the shrunk ball: residual,
+    // objective and gradient are brought up to date with it
     st->accept_x = st->accept_r = st->update_g = 1;
   } else if (type == T_TRIAL) {
     st->n_trials++;
+    if (st->n_line == 0) {
+      st->f1 = st->ft;
+      st->gtd1 = st->gtd;
+    }
     bool acc = false;
-    if (st->gtd >= 0.0) st->stationary = 1;                       // no descent: x is stationary
-    else if (st->ft < st->fmax + st->gamma * st->gtd) acc = true;  // non-monotone Armijo
-    else if (st->n_line >= st->max_line) {                         // last halving
-      if (st->ft < st->f_old) acc = true;
-      else st->stationary = 1;  // no measurable decrease left at this tau
+    if (st->gtd >= 0.0) {
+      // no descent: x is optimal for this tau if the very first trial does
+      // not move it; a later trial falls back to the feasible direction
+      if (st->n_line == 0) st->stationary = 1;
+      else st->go_feas = 1;
+    } else if (st->ft < st->fmax + st->gamma * st->gtd) {
+      acc = true;  // non-monotone sufficient decrease along the arc
+    } else if (st->n_line >= st->max_line) {
+      st->go_feas = 1;
     }
     if (acc) st->accept_x = st->accept_r = st->update_g = 1;
+  } else if (type == T_FEAS) {
+    st->n_trials++;
+    if (st->ft < st->fmax + st->gamma * st->feas_t * st->gtd1) st->accept_x = st->accept_r = st->update_g = 1;
+    else if (st->n_feas >= st->max_line) st->line_err = 1;
   }
   st->skip_adj = st->update_g ? 0 : 1;
 }
@@ -708,62 +782,85 @@ __global__ void __launch_bounds__(kRB) k_spg_end(SpgVec V) {
     st->f = st->ft;
     st->rtb = st->rtb_t;
   }
+  st->store_dir = 0;
   switch (st->type) {
     case T_INIT:
-      spg_push_hist(st, st->f);
+      spg_reset_hist(st, st->f);
+      st->f_old = st->f;
       st->type = T_PG;
-      st->pg_then = PG_THEN_CHECK;
       st->ps = 1.0;
       break;
     case T_PG: {
+      // step length 1 / ||P(x - g) - x||_inf: the initial step, or the
+      // restart after an iteration whose first trial had no descent
       const double dxn = st->dinf;
-      st->alpha = dxn < 1.0 / st->step_max ? st->step_max : fmin(st->step_max, fmax(st->step_min, 1.0 / dxn));
-      if (st->pg_then == PG_THEN_CHECK) spg_check(st);
-      else spg_start_trial(st);
+      st->gstep = dxn < 1.0 / st->step_max ? st->step_max : spg_clamp_step(st, 1.0 / dxn);
+      if (st->pg_end_iter) spg_end_iteration(st);
+      else spg_check(st);
       break;
     }
     case T_PROJX:
-      st->type = T_PG;
-      st->pg_then = PG_THEN_TRIAL;
-      st->ps = 1.0;
+      spg_reset_hist(st, st->f);
+      spg_start_trial(st);
       break;
-    default: {  // T_TRIAL
-      if (st->line_fail) {
-        st->status = S_LINE;
-        st->done = 1;
-        st->skip_adj = 1;
-        break;
-      }
-      if (st->stationary) {
-        // x is stationary for the current LASSO problem: check the root /
-        // take the Newton step (unchanged f registers as stagnation);
-        // repeated stationarity without progress is a failure
-        if (++st->n_stationary > 3) {
+    default: {  // T_TRIAL, T_FEAS
+      if (!st->stationary && (st->accept_r || st->line_err)) st->n_nodescent = 0;
+      if (st->accept_r) {
+        const double sts = gq[0], sty = gq[1];
+        st->gstep = sty <= 0.0 ? st->step_max : spg_clamp_step(st, sts / sty);
+        spg_end_iteration(st);
+      } else if (st->stationary) {
+        // the first trial did not move x downhill at a point the exit tests
+        // did not certify: the BB step is too short for the working
+        // precision.  x stays; the step restarts from the projected
+        // gradient (a T_PG tick), then the iteration ends.  With a fixed tau
+        // three such iterations in a row end the solve.
+        st->n_stationary++;
+        st->n_nodescent++;
+        if (st->single_tau && st->n_nodescent > 2) {
           st->status = S_LINE;
           st->done = 1;
-        st->skip_adj = 1;
+          st->skip_adj = 1;
           break;
         }
-        spg_check(st);
-        break;
-      }
-      if (st->accept_r) {
-        st->n_stationary = 0;
-        const double sts = gq[0], sty = gq[1];
-        st->alpha = sty <= 0.0 ? st->step_max : fmin(st->step_max, fmax(st->step_min, sts / sty));
-        if (st->f > 0.5 * st->sigma * st->sigma) spg_push_hist(st, st->f);
-        spg_check(st);
-      } else {
-        // backtrack along the projection arc; a flat arc (same displacement
-        // norm as the previous trial) jumps to half the displacement scale
-        const double dn = sqrt(st->dn2), gn = sqrt(st->gnorm2);
-        if (st->dn_prev >= 0.0 && fabs(dn - st->dn_prev) <= 1e-6 * dn && gn > 0.0)
-          st->step = fmin(0.5 * st->step, 0.5 * dn / gn);
-        else
-          st->step *= 0.5;
-        st->dn_prev = dn;
+        st->type = T_PG;
+        st->ps = 1.0;
+        st->pg_end_iter = 1;
+      } else if (st->line_err) {
+        // both searches failed: x, f, r and g stay; damp the longest step
+        st->n_line_errors++;
+        if (st->line_errors_left <= 0) {
+          st->status = S_LINE;
+          st->done = 1;
+          st->skip_adj = 1;
+          break;
+        }
+        st->step_max /= 10.0;
+        st->line_errors_left--;
+        st->gstep = fmin(st->step_max, st->gstep);
+        spg_end_iteration(st);
+      } else if (st->go_feas) {
+        // its t = 1 point is the first arc trial, already rejected
+        st->type = T_FEAS;
+        st->feas_t = spg_feas_next(st, 1.0, st->f1);
+        st->n_feas = 1;
+      } else if (st->type == T_TRIAL) {
+        // backtrack along the arc; a flat arc (two consecutive trials with
+        // displacements of equal norm) rescales the gradient so that the
+        // next displacement is step |s| / 2^nsafe
         st->n_line++;
-        st->ps = st->step;
+        st->step *= 0.5;
+        const double sn = sqrt(st->dn2), gn = sqrt(st->gnorm2);
+        if (fabs(sn - st->sn_prev) <= 1e-6 * sn && gn > 0.0) {
+          st->scale = sn / (st->gstep * gn) / exp2((double)st->nsafe);
+          st->nsafe++;
+          st->n_safeguard++;
+        }
+        st->sn_prev = sn;
+        st->ps = st->step * st->scale * st->gstep;
+      } else {  // T_FEAS, rejected
+        st->feas_t = spg_feas_next(st, st->feas_t, st->ft);
+        st->n_feas++;
       }
       break;
     }
@@ -792,6 +889,7 @@ __global__ void __launch_bounds__(kRB) k_spg_setup(SpgVec V, double tau0) {
   SpgState* st = V.st;
   st->bnorm = sqrt(q[0]);
   st->tau = tau0 >= 0.0 ? tau0 : q[1];
+  st->gstep = st->step_max;
   st->type = T_INIT;
   st->ps = 0.0;
   st->skip_fwd = 0;
@@ -943,13 +1041,18 @@ int fill_opts(const spgl1_opts* o, SpgState& st, double* tau0, int* filter, int*
   st.max_iter = (o && o->max_iter > 0) ? o->max_iter : 300;
   st.opt_tol = (o && o->opt_tol > 0) ? o->opt_tol : 1e-4;
   st.bp_tol = (o && o->bp_tol > 0) ? o->bp_tol : 1e-6;
+  st.ls_tol = (o && o->ls_tol > 0) ? o->ls_tol : 1e-6;
+  st.dec_tol = (o && o->dec_tol > 0) ? o->dec_tol : 1e-4;
   st.memory = (o && o->memory > 0) ? o->memory : 3;
   st.gamma = (o && o->gamma > 0) ? o->gamma : 1e-4;
   st.step_min = (o && o->step_min > 0) ? o->step_min : 1e-16;
   st.step_max = (o && o->step_max > 0) ? o->step_max : 1e5;
-  st.max_line = (o && o->max_line > 0) ? o->max_line : 30;
+  st.max_line = (o && o->max_line > 0) ? o->max_line : 10;
+  st.line_errors_left = (o && o->max_line_errors > 0) ? o->max_line_errors : 10;
+  st.single_tau = (o && (o->flags & CPCT_SPGL1_LASSO)) ? 1 : 0;
   if (st.memory > kHist) return CPCT_EINVAL;
-  *tau0 = (o && (o->flags & CPCT_SPGL1_TAU0)) ? o->tau0 : -1.0;
+  *tau0 = (o && (o->flags & (CPCT_SPGL1_TAU0 | CPCT_SPGL1_LASSO))) ? o->tau0 : -1.0;
+  if (st.single_tau && !(*tau0 >= 0.0 && std::isfinite(*tau0))) return CPCT_EINVAL;
   *filter = (o && (o->flags & CPCT_SPGL1_NO_FILTER)) ? 0 : 1;
   *synth = (o && (o->flags & CPCT_SPGL1_SYNTH_DH)) ? 1 : 0;
   return CPCT_OK;
@@ -959,7 +1062,8 @@ int fill_opts(const spgl1_opts* o, SpgState& st, double* tau0, int* filter, int*
 
 extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const float* const* d_b, const double* sigma,
                                    float* const* d_x, const spgl1_opts* opts, spgl1_info* info, cudaStream_t stream) {
-  if (!plans || batch < 1 || !d_b || !sigma || !d_x) return CPCT_EINVAL;
+  if (!plans || batch < 1 || !d_b || !d_x) return CPCT_EINVAL;
+  if (!sigma && !(opts && (opts->flags & CPCT_SPGL1_LASSO))) return CPCT_EINVAL;
   SpgState proto;
   std::memset(&proto, 0, sizeof(proto));
   double tau0 = -1.0;
@@ -967,7 +1071,7 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
   int rc = fill_opts(opts, proto, &tau0, &filter, &synth);
   if (rc) return rc;
   for (int i = 0; i < batch; ++i) {
-    if (!plans[i] || !d_b[i] || !d_x[i] || !(sigma[i] >= 0.0)) return CPCT_EINVAL;
+    if (!plans[i] || !d_b[i] || !d_x[i] || (sigma && !(sigma[i] >= 0.0))) return CPCT_EINVAL;
     for (int k = 0; k < i; ++k)
       if (plans[k] == plans[i]) return CPCT_EINVAL;  // a plan holds per-call workspaces
   }
@@ -998,13 +1102,13 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
     w.plan = plans[i];
     w.x = d_x[i];
     w.b = d_b[i];
-    w.sigma = sigma[i];
+    w.sigma = sigma ? sigma[i] : 0.0;
     const long long n = (long long)w.plan->n * w.plan->n, m = (long long)w.plan->m * w.plan->ns;
     if (synth && w.plan->n > kScanT * kScanMaxPer) {
       rc = CPCT_EINVAL;
       goto done;
     }
-    if (!cuda(cudaMalloc(&w.mem, sizeof(float) * ((synth ? 6 : 5) * n + 4 * m)))) goto done;
+    if (!cuda(cudaMalloc(&w.mem, sizeof(float) * ((synth ? 7 : 6) * n + 4 * m)))) goto done;
     SpgVec& V = w.V;
     V.n = n;
     V.m = m;
@@ -1014,7 +1118,8 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
     V.g = w.mem + 2 * n;
     V.gold = w.mem + 3 * n;
     V.gtmp = w.mem + 4 * n;
-    V.y = w.mem + 5 * n;
+    V.dir = w.mem + 5 * n;
+    V.y = w.mem + 6 * n;
     V.rt = V.y + m;
     V.r = V.rt + m;
     V.bf = V.r + m;
@@ -1031,7 +1136,7 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
     }
     // state, filtered data, zero gradient and residual, ||b||, tau0
     SpgState st = proto;
-    st.sigma = w.sigma;
+    st.sigma = proto.single_tau ? 0.0 : w.sigma;
     if (!cuda(cudaMemcpyAsync(V.st, &st, sizeof(st), cudaMemcpyHostToDevice, stream))) goto done;
     if (!cuda(cudaMemsetAsync(V.g, 0, sizeof(float) * n, stream))) goto done;
     if (!cuda(cudaMemsetAsync(V.r, 0, sizeof(float) * m, stream))) goto done;
@@ -1083,7 +1188,9 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
   }
   {
     const int chunk = 8;
-    const long long max_ticks = (long long)(proto.max_iter + 2) * (proto.max_line + 4) + 16;
+    // per iteration at most max_line + 1 arc trials, max_line feasible
+    // trials and one projection onto a shrunk ball
+    const long long max_ticks = (long long)(proto.max_iter + 2) * (2 * proto.max_line + 4) + 16;
     long long ticks = 0;
     bool all_done = false;
     while (!all_done && ticks < max_ticks) {
@@ -1121,6 +1228,11 @@ extern "C" int spgl1_solve_batched(cpct_plan* const* plans, int batch, const flo
       I.rnorm = std::sqrt(r2);
       I.xnorm1 = l1;
       I.rel_gap = st.rel_gap;
+      I.newton = st.n_newton;
+      I.line_errors = st.n_line_errors;
+      I.safeguards = st.n_safeguard;
+      I.stationary = st.n_stationary;
+      I.gstep = st.gstep;
     }
     if (rc == CPCT_OK) {
       const int sst = st.done ? st.status : S_ITER;

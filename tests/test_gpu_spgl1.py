@@ -1,15 +1,16 @@
 """GPU ring filter and SPGL1 against the FP64 oracle (through the C ABI).
 
 Pins: the filter matches the oracle projector to FP32 rounding and is
-idempotent on the device; the device SPGL1 reaches the root (| ||r|| - sigma |
-<= opt_tol ||F b||) and its solution matches the oracle's in misfit (relative
-1e-3), in l1 norm (relative 2e-3) and in x (relative L2 5e-2).  SPGL1 is an
-inexact Newton method on the Pareto curve: its LASSO subproblems end when the
-objective stagnates, with a duality gap that is still large, so ||x||_1 at
-exit is fixed only to about the subproblem accuracy.  Rounding alone moves it:
-the FP64 oracle on two CPU platforms ends 5e-4 apart on this problem, and
-FP32 operators change line-search branches, so iterate-by-iterate parity is
-not expected and the comparison is between near-optimal points.
+idempotent on the device.  With a single fixed tau (the LASSO problem, whose
+solution the mathematics fixes) the device solution matches the oracle's
+element by element (relative L2 1e-3) once both duality gaps are small.  The
+basis-pursuit denoising solve reaches the root on both sides, and the
+solutions agree in misfit and in l1 norm to 1e-3 (survey pin P8).  Its x is
+compared at 5e-2 only: SPGL1 is an inexact Newton method whose exit test is
+the root error alone, with the last LASSO problem's duality gap still O(1),
+so x at exit is fixed by the method only to a few percent -- the FP64 oracle
+itself ends 2.9% apart (relative L2) between opt_tol 1e-6 and 1e-7 on this
+problem, and FP32 operators change line-search branches.
 """
 import numpy as np
 import pytest
@@ -63,6 +64,12 @@ def _problem(n, m, seed=5):
     return geo, x_true, b, sigma
 
 
+def _ops(n, m, geo):
+    A = lambda v: ring.ring_filter(nufft.radon_grid(v.reshape(n, n), geo))
+    At = lambda r: nufft.radon_grid_adj(ring.ring_filter(r.reshape(m, n)), geo)
+    return A, At
+
+
 def test_spgl1_matches_oracle(torch_cuda):
     torch = torch_cuda
     from paper_1009_1380_gb300 import cpct
@@ -70,26 +77,56 @@ def test_spgl1_matches_oracle(torch_cuda):
     geo, x_true, b, sigma = _problem(n, m)
     b32 = b.astype(np.float32)
     bf = ring.ring_filter(b32.astype(np.float64))
-    A = lambda v: ring.ring_filter(nufft.radon_grid(v.reshape(n, n), geo))
-    At = lambda r: nufft.radon_grid_adj(ring.ring_filter(r.reshape(m, n)), geo)
-    # a root tolerance 10x tighter than the default: both solvers stop within
-    # opt_tol ||F b|| of sigma, which moves ||x||_1 along the Pareto curve by
-    # about that relative amount
-    tol = 1e-5
-    xo, io = spgl1.spgl1(A, At, bf, sigma, opts=spgl1.Options(opt_tol=tol, max_iter=600))
+    A, At = _ops(n, m, geo)
+    tol = 1e-6
+    xo, io = spgl1.spgl1(A, At, bf, sigma, opts=spgl1.Options(opt_tol=tol, max_iter=3000))
     p = cpct.Plan(n, n, m)
-    xg, ig = cpct.spgl1(p, torch.from_numpy(b32).cuda(), sigma, opts=cpct.make_opts(opt_tol=tol, max_iter=600))
+    xg, ig = cpct.spgl1(p, torch.from_numpy(b32).cuda(), sigma, opts=cpct.make_opts(opt_tol=tol, max_iter=3000))
     xg = xg.cpu().numpy().astype(np.float64)
     rg = np.linalg.norm(A(xg) - bf)
-    print("oracle", io.status, io.iterations, io.rnorm, io.xnorm1)
+    print("oracle", io.status, io.iterations, io.n_newton, io.rnorm, io.xnorm1, io.rel_gap)
     print("gpu   ", ig)
     print("x rel", _rel(xg, xo), "l1 rel", abs(ig["xnorm1"] - io.xnorm1) / io.xnorm1, "r (oracle op)", rg, sigma)
     assert io.status == spgl1.EXIT_ROOT_FOUND
     assert ig["status"] == 1
     assert abs(ig["rnorm"] - sigma) <= 2 * tol * np.linalg.norm(bf)
-    assert abs(rg - sigma) <= 1e-3 * np.linalg.norm(bf)
-    assert abs(ig["xnorm1"] - io.xnorm1) <= 2e-3 * io.xnorm1
-    assert _rel(xg, xo) < 5e-2
+    assert abs(rg - io.rnorm) <= 1e-3 * io.rnorm
+    assert abs(ig["xnorm1"] - io.xnorm1) <= 1e-3 * io.xnorm1
+    # measured 0.8-1.0%; the oracle's own x moves 2.9% between opt_tol 1e-6
+    # and 1e-7, so 1e-2 is at the method's own determinacy
+    assert _rel(xg, xo) < 2e-2
+
+
+@pytest.mark.parametrize("n,m,tol", [(64, 64, 1e-3), (128, 90, 2e-3)])
+def test_lasso_matches_oracle(torch_cuda, n, m, tol):
+    """The LASSO problem min ||F(R x) - F b|| s.t. ||x||_1 <= tau at a fixed
+    tau (half the l1 norm of the true image): device and FP64 oracle solutions
+    agree element by element.  The device solve runs until its objective
+    stops resolving descent (FP32 operators: the rounding of F(R x) makes f
+    noisy at ~1e-7 ||r|| ||b||, and the duality gap ends near 1e-3, where the
+    oracle's is 1e-5); x agrees with the oracle to about that gap (measured
+    4.9e-4 at 64^2, 1.25e-3 at 128^2)."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    geo, x_true, b, sigma = _problem(n, m)
+    b32 = b.astype(np.float32)
+    bf = ring.ring_filter(b32.astype(np.float64))
+    A, At = _ops(n, m, geo)
+    tau = 0.5 * float(np.abs(x_true).sum())
+    xo, io = spgl1.lasso(A, At, bf, tau, opts=spgl1.Options(opt_tol=1e-5, max_iter=20000))
+    p = cpct.Plan(n, n, m)
+    xg, ig = cpct.spgl1(p, torch.from_numpy(b32).cuda(), 0.0,
+                        opts=cpct.make_opts(opt_tol=1e-5, max_iter=5000, lasso_tau=tau))
+    xg = xg.cpu().numpy().astype(np.float64)
+    e = _rel(xg, xo)
+    print(f"n={n} m={m} tau={tau:.3f}: oracle status {io.status} it {io.iterations} gap {io.rel_gap:.2e}; "
+          f"gpu {ig}; x rel {e:.2e}")
+    assert io.status == spgl1.EXIT_OPTIMAL
+    # 8: gap <= opt_tol; 4: no descent at the working precision
+    assert ig["status"] in (8, 4)
+    assert ig["rel_gap"] <= 5e-3
+    assert abs(np.abs(xg).sum() - tau) <= 1e-5 * tau
+    assert e <= tol
 
 
 def test_spgl1_batched_equals_single(torch_cuda):
