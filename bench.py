@@ -493,12 +493,50 @@ def spgl1_bench(args, torch, cpct, synth):
     wall = time.perf_counter() - t0
     roots = sum(1 for i in infos if i["status"] == 1)
     its = [i["iterations"] for i in infos]
+    status_counts = {}
+    for i in infos:
+        status_counts[str(i["status"])] = status_counts.get(str(i["status"]), 0) + 1
     return {"metric": "SPGL1 slices/s to the root", "value": roots / wall, "unit": "slices/s",
             "slices": B, "slices_at_root": roots, "wall_s": wall,
             "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
             "ticks_mean": float(np.mean([i["ticks"] for i in infos])),
+            "status_counts": status_counts,
+            "newton_mean": float(np.mean([i["newton"] for i in infos])),
+            "line_errors": int(sum(i["line_errors"] for i in infos)),
+            "nodescent_iterations": int(sum(i["stationary"] for i in infos)),
+            "not_at_root": [{"slice": k, "status": i["status"], "iterations": i["iterations"],
+                             "root_error": abs(i["rnorm"] - sig[k]) / sig[k], "newton": i["newton"]}
+                            for k, i in enumerate(infos) if i["status"] != 1],
             "config": f"{B} slices {n}x{n} Laplacian phantoms, {m} views x {n} bins, noise 1% + 8 stuck columns, "
                       f"<= {c['iterations']} iterations, opt_tol 1e-4, ring filter"}
+
+
+def warm_bench(args, torch, cpct, synth):
+    """The learned warm start, bounded (C5 shape: 512^2 slices, 90 views):
+    generate training pairs (FBP input, cold SPGL1 target), train the U-Net
+    with the library's kernels, then solve fresh slices cold and from the
+    network's calibrated prediction to the same root tolerance (1e-3 of
+    ||F b||); wall time includes the network and the fallback cold solves."""
+    from paper_1009_1380_gb300 import warmstart
+    t0 = time.perf_counter()
+    res = warmstart.run(pairs=args.warm_pairs, eval_slices=args.warm_eval, epochs=args.warm_epochs, batch=8,
+                        lr=1e-3, levels=5, base=32, plans_per_group=64, target_iters=500, eval_tol=1e-3,
+                        log=lambda *a: None)
+    ev = res["eval"]
+    cold, learned, lp, fbp = ev["cold"], ev["learned"], ev["learned_pipelined"], ev["fbp"]
+    return {"metric": "SPGL1 slices/s to residual 1e-3, learned vs cold start", "unit": "slices/s",
+            "value": lp["slices_per_s"], "cold": cold["slices_per_s"],
+            "speedup_wall": cold["wall_s"] / lp["wall_s"],
+            "cold_wall_s": cold["wall_s"], "learned_wall_s": lp["wall_s"], "learned_net_s": lp["net_s"],
+            "learned_unpipelined_wall_s": learned["wall_s"], "fbp_start_wall_s": fbp["wall_s"],
+            "cold_iterations_mean": cold["iterations_mean"], "learned_iterations_mean": learned["iterations_mean"],
+            "fbp_start_iterations_mean": fbp["iterations_mean"],
+            "cold_at_root": cold["at_root"], "learned_at_root": lp["at_root"], "fallbacks": lp["fallbacks"],
+            "prediction_rel_err_mean": learned["prediction_rel_err_mean"],
+            "train_pairs": args.warm_pairs, "eval_slices": args.warm_eval, "epochs": args.warm_epochs,
+            "train_s": res["train_s"], "total_s": time.perf_counter() - t0,
+            "config": "512x512 Laplacian phantoms, 90 views, noise 1% + 8 stuck columns; U-Net 5 levels / 32 base "
+                      "channels trained on generated (FBP, cold SPGL1) pairs; root tolerance 1e-3 ||F b||"}
 
 
 def denoiser_flops(levels, base, n):
@@ -726,6 +764,8 @@ def run_ours(args, rank, world, local_rank):
         out["spgl1"] = spgl1_bench(args, torch, cpct, synth)
     if world == 1 and args.unet_batch > 0:
         out["denoiser"] = denoiser_bench(args, torch, cpct)
+    if world == 1 and args.warm_pairs > 0:
+        out["warm"] = warm_bench(args, torch, cpct, synth)
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -743,7 +783,10 @@ def main():
     ap.add_argument("--batch-slices", type=int, default=256, help="slices of the batched-operator workload (0: skip)")
     ap.add_argument("--spgl1-iters", type=int, default=0, help="override the SPGL1 iteration cap (0: 300)")
     ap.add_argument("--unet-batch", type=int, default=32, help="images of the denoiser workload (0: skip)")
-    ap.add_argument("--only", default="", choices=["", "spgl1", "batch", "unet"],
+    ap.add_argument("--warm-pairs", type=int, default=1024, help="training pairs of the warm-start run (0: skip)")
+    ap.add_argument("--warm-eval", type=int, default=256, help="fresh slices of the warm-start run")
+    ap.add_argument("--warm-epochs", type=int, default=8, help="training epochs of the warm-start run")
+    ap.add_argument("--only", default="", choices=["", "spgl1", "batch", "unet", "warm"],
                     help="run one secondary workload alone")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -751,7 +794,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.only in ("spgl1", "batch", "unet"):
+    elif args.only in ("spgl1", "batch", "unet", "warm"):
         import torch
         from paper_1009_1380_gb300 import build as b
         b.build()
@@ -761,6 +804,8 @@ def main():
             print(json.dumps(spgl1_bench(args, torch, cpct, synth)), flush=True)
         elif args.only == "unet":
             print(json.dumps(denoiser_bench(args, torch, cpct)), flush=True)
+        elif args.only == "warm":
+            print(json.dumps(warm_bench(args, torch, cpct, synth)), flush=True)
         else:
             print(json.dumps(batch_bench(args, torch, cpct, synth)), flush=True)
     else:

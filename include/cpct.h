@@ -469,6 +469,27 @@ int cpct_unet_adam_step(cpct_unet* net, float lr, float max_grad_norm, double* g
 int cpct_unet_debug_op(int op, const float* d_a, const float* d_b, float* d_y, const float* h_w, int B, int H, int W,
                        int C1, int C2, int Cout, cudaStream_t stream);
 
+/* Per-slice statistics and scaling of the learned warm start (no
+ * counterpart in the paper).  A batch is `batch` (1..65535) slices of n >= 1
+ * contiguous float32 values each (device, caller-owned); h_* arrays are host
+ * arrays of `batch` entries.  Reductions are deterministic (fixed grids,
+ * FP64 sums in a fixed order).  Each call allocates a small stream-ordered
+ * workspace and synchronizes `stream`; CPCT_EINVAL for null pointers, sizes
+ * out of range or non-finite per-slice parameters.
+ *   cpct_slice_moments: mean and sample standard deviation (divisor n - 1;
+ *                       0 for n = 1) of every slice, two passes (the second
+ *                       about the mean); either output may be NULL;
+ *   cpct_slice_soft_l1: h_out[i] = sum_j max(|x_ij| - h_thresh[i], 0), the
+ *                       l1 norm of the soft-thresholded slice (thresholds
+ *                       finite, >= 0);
+ *   cpct_slice_scale:   d_out slice i = h_factor[i] * d_in slice i (FP32
+ *                       product; d_out may alias d_in). */
+int cpct_slice_moments(const float* d_x, int batch, long long n, double* h_mean, double* h_std, cudaStream_t stream);
+int cpct_slice_soft_l1(const float* d_x, int batch, long long n, const double* h_thresh, double* h_out,
+                       cudaStream_t stream);
+int cpct_slice_scale(const float* d_in, float* d_out, int batch, long long n, const double* h_factor,
+                     cudaStream_t stream);
+
 /* Test introspection of the tensor-core (tcgen05) path: D = A * B^T with one
  * CTA and the accumulator in tensor memory.  A: 128 x k, B: n x k (bfloat16,
  * row-major, device, 16-byte aligned), D: 128 x n (float32, device); k a

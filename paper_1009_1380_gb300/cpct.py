@@ -306,6 +306,63 @@ def debug_bins(n, n_det, n_views, which, angles=None):
     return t.value, e.value, c.value
 
 
+# ---------------------------------------------------------------------------
+# per-slice statistics and scaling (learned warm start)
+# ---------------------------------------------------------------------------
+def _slices_setup():
+    L = lib()
+    vp, ll = ctypes.c_void_p, ctypes.c_longlong
+    L.cpct_slice_moments.argtypes = [vp, ctypes.c_int, ll, vp, vp, vp]
+    L.cpct_slice_soft_l1.argtypes = [vp, ctypes.c_int, ll, vp, vp, vp]
+    L.cpct_slice_scale.argtypes = [vp, vp, ctypes.c_int, ll, vp, vp]
+    return L
+
+
+def _slices_ptr(x):
+    import torch
+    if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.dim() >= 2):
+        raise ValueError("expected a contiguous float32 CUDA tensor of slices (batch, ...)")
+    return ctypes.c_void_p(x.data_ptr()), x.shape[0], x[0].numel()
+
+
+def slice_moments(x, stream=None):
+    """Per-slice (mean, sample standard deviation) of a batch of slices,
+    host float64 arrays (cpct_slice_moments)."""
+    import torch
+    p, b, n = _slices_ptr(x)
+    mean, std = np.zeros(b), np.zeros(b)
+    check(_slices_setup().cpct_slice_moments(p, b, n, mean.ctypes.data_as(ctypes.c_void_p),
+                                             std.ctypes.data_as(ctypes.c_void_p), _stream(torch, stream)),
+          "cpct_slice_moments")
+    return mean, std
+
+
+def slice_soft_l1(x, thresh, stream=None):
+    """Per-slice sum max(|x| - thresh_i, 0) (cpct_slice_soft_l1)."""
+    import torch
+    p, b, n = _slices_ptr(x)
+    th = np.ascontiguousarray(np.broadcast_to(np.asarray(thresh, dtype=np.float64), (b,)))
+    out = np.zeros(b)
+    check(_slices_setup().cpct_slice_soft_l1(p, b, n, th.ctypes.data_as(ctypes.c_void_p),
+                                             out.ctypes.data_as(ctypes.c_void_p), _stream(torch, stream)),
+          "cpct_slice_soft_l1")
+    return out
+
+
+def slice_scale(x, factor, out=None, stream=None):
+    """out slice i = factor_i * x slice i (cpct_slice_scale); new tensor
+    unless `out` is given (may be x itself)."""
+    import torch
+    p, b, n = _slices_ptr(x)
+    if out is None:
+        out = torch.empty_like(x)
+    q, _, _ = _slices_ptr(out)
+    f = np.ascontiguousarray(np.broadcast_to(np.asarray(factor, dtype=np.float64), (b,)))
+    check(_slices_setup().cpct_slice_scale(p, q, b, n, f.ctypes.data_as(ctypes.c_void_p), _stream(torch, stream)),
+          "cpct_slice_scale")
+    return out
+
+
 def debug_adj_items(n, n_det, n_views, cap=0, angles=None):
     """Host-side adjoint work items of a geometry with `cap` rounds per item
     (no GPU needed): dict(items, n_split, n_slots)."""

@@ -107,7 +107,8 @@ def solve(plans, b, sigma, opts, x0=None):
 
 
 def scales(fbp):
-    return fbp.flatten(1).std(dim=1).clamp_min(1e-12)
+    """Per-slice standard deviations (host float64), kept away from zero."""
+    return np.maximum(cpct.slice_moments(fbp)[1], 1e-12)
 
 
 CLIP_FACTOR = 2.0      # clip at twice the median of the recent gradient norms
@@ -124,8 +125,8 @@ def train(net, fbp, target, epochs, batch, lr, seed=0, log=None):
     epoch are kept, and an epoch whose loss exceeds 1.5x the best restores
     them and halves the learning rate."""
     torch = net._torch
-    s = scales(fbp)[:, None, None]
-    inp, tgt = (fbp / s).contiguous(), (target / s).contiguous()
+    inv = 1.0 / scales(fbp)
+    inp, tgt = cpct.slice_scale(fbp, inv), cpct.slice_scale(target, inv)
     rng = np.random.default_rng(seed)
     count = fbp.shape[0]
     steps_per_epoch = max(1, count // batch)
@@ -164,14 +165,14 @@ def train(net, fbp, target, epochs, batch, lr, seed=0, log=None):
 
 def predict(net, fbp, batch):
     torch = net._torch
-    s = scales(fbp)[:, None, None]
-    inp = (fbp / s).contiguous()
+    s = scales(fbp)
+    inp = cpct.slice_scale(fbp, 1.0 / s)
     out = torch.empty_like(inp)
     for g in range(0, fbp.shape[0], batch):
         k = min(batch, fbp.shape[0] - g)
         net.forward(inp[g:g + k], out=out[g:g + k])
     net.sync()  # raises if a bounded device wait of a forward pass expired
-    return out * s
+    return cpct.slice_scale(out, s, out=out)
 
 
 # candidate noise floors (in units of the prediction's per-slice standard
@@ -179,24 +180,32 @@ def predict(net, fbp, batch):
 THETAS = (0.0, 0.02, 0.05, 0.1, 0.2, 0.3, 0.5, 0.75, 1.0)
 
 
-def _soft_l1(x_hat, theta):
-    """Per slice ||soft(x_hat, theta s)||_1, s the slice's standard deviation."""
-    s = x_hat.flatten(1).std(dim=1)
-    return (x_hat.abs().flatten(1) - theta * s[:, None]).clamp_min(0.0).sum(dim=1).double().cpu().numpy()
+def _soft_l1(x_hat, theta, s=None):
+    """Per slice ||soft(x_hat, theta s)||_1, s the slice's standard deviation
+    (cpct_slice_moments and cpct_slice_soft_l1)."""
+    s = cpct.slice_moments(x_hat)[1] if s is None else s
+    return cpct.slice_soft_l1(x_hat, theta * s)
 
 
-def calibrate(x_hat, tau_star):
-    """Starting-radius estimate tau0 = kappa ||soft(x_hat, theta s)||_1: theta
-    minimises the spread of log(tau* / ||soft||_1) over the given slices,
+def calibrate_table(soft, tau_star):
+    """The calibration from soft[t][i] = ||soft(x_hat_i, THETAS[t] s_i)||_1:
+    theta minimises the spread of log(tau* / ||soft||_1) over the slices,
     kappa is the median ratio at that theta."""
     tau_star = np.asarray(tau_star, dtype=np.float64)
     best = None
-    for th in THETAS:
-        r = tau_star / np.maximum(_soft_l1(x_hat, th), 1e-30)
+    for th, col in zip(THETAS, soft):
+        r = tau_star / np.maximum(np.asarray(col, dtype=np.float64), 1e-30)
         spread = float(np.std(np.log(r)))
         if best is None or spread < best["spread"]:
             best = {"theta": th, "kappa": float(np.median(r)), "spread": spread}
     return best
+
+
+def calibrate(x_hat, tau_star):
+    """Starting-radius estimate tau0 = kappa ||soft(x_hat, theta s)||_1 with
+    theta and kappa fitted on the given slices (calibrate_table)."""
+    s = cpct.slice_moments(x_hat)[1]
+    return calibrate_table([_soft_l1(x_hat, th, s) for th in THETAS], tau_star)
 
 
 def project_start(x_hat, cal):
