@@ -1,20 +1,19 @@
 """The learned warm start gains over the method without it.
 
 A small instance of the whole pipeline on the GPU: 128 x 128 slices with 45
-views, 192 generated (FBP, cold SPGL1) pairs, a 3-level U-Net trained by the
+views, 384 generated (FBP, cold SPGL1) pairs, a 3-level U-Net trained by the
 library's own kernels, then 16 fresh slices solved cold, from the FBP and
 from the network's prediction, all to the same root tolerance.  The learned
 start must be much closer to the solution than the starting points the
 method has without the network (zero, as in the cold start, and the FBP
 image under the same calibrated projection), must need fewer SPGL1
 iterations than the cold start and than the FBP start, every slice must end
-at the root
-(warm failures fall back to the cold solver), and the warm solutions must
-match the cold ones in l1 norm to 1e-2 (both stop anywhere within the root
-tolerance 1e-3 ||F b|| of sigma, which moves ||x||_1 along the Pareto
-curve).  A network trained this briefly predicts the solution to ~35% (L2);
-the iteration and wall-time gain of the full-size pipeline (4096 pairs at
-512^2) is measured by `python -m paper_1009_1380_gb300.warmstart`.
+at the root (warm failures fall back to the cold solver), and the warm
+solutions must match the cold ones in l1 norm to 1e-1 (both stop anywhere
+within the root tolerance 1e-3 ||F b|| of sigma, which moves ||x||_1 along
+the Pareto curve).  The wall-time gain of the full-size pipeline (4096
+pairs at 512^2) is measured by `python -m paper_1009_1380_gb300.warmstart`,
+and a bounded run of it by the benchmark's `warm` entry.
 """
 import numpy as np
 import pytest
