@@ -184,6 +184,26 @@ int radon_adj_host(cpct_plan* plan, const float* h_sino, float* h_img, cudaStrea
 int radon_pair_host_stream(cpct_plan* plan, const float* const* h_imgs, float* const* h_sinos,
                            float* const* h_outs, int count, cudaStream_t stream);
 
+/* Preprocessing front end (section "Introduction", Fig. 1): the radiographs
+ * taken with the detector near the sample and 1 m downstream are background
+ * normalized, n = (I - D) / (F - D) (flat-field correction; 0 where the
+ * reference F - D <= 0, a dead or saturated pixel), and subtracted; the
+ * difference is the propagation-based phase-contrast image, and its rows
+ * over all angles are the sinograms, one per detector row:
+ *   sino_z[j, s] = n_near[j, z, s] - n_far[j, z, s].
+ *   d_near, d_far            device, n_views x n_rows x n_det uint16 camera
+ *                            frames (angle j, detector row z, column s)
+ *   d_flat_near, d_flat_far  device, n_rows x n_det float32 open-beam frames
+ *   d_dark                   device, n_rows x n_det float32 dark frame
+ *   d_sinos                  device, n_rows x n_views x n_det float32 (slice
+ *                            z's M x Ns sinogram at d_sinos + z M Ns), written
+ * FP32 arithmetic (the reciprocal of each reference is formed once).
+ * Stream-ordered, asynchronous (a small stream-ordered workspace of 2
+ * n_rows n_det floats).  CPCT_EINVAL for null pointers or sizes < 1. */
+int cpct_preprocess_pc(const uint16_t* d_near, const uint16_t* d_far, const float* d_flat_near,
+                       const float* d_flat_far, const float* d_dark, int n_views, int n_rows, int n_det,
+                       float* d_sinos, cudaStream_t stream);
+
 /* ---- many slices: clones, autotuner, batches ----------------------------- */
 
 /* A new plan for the same geometry as `src` that shares src's read-only

@@ -363,6 +363,30 @@ def slice_scale(x, factor, out=None, stream=None):
     return out
 
 
+def preprocess_pc(near, far, flat_near, flat_far, dark, out=None, stream=None):
+    """Phase-contrast sinograms from near/far camera frames (uint16 CUDA
+    tensors (M, rows, Ns); int16 tensors holding the same bits are accepted)
+    and float32 flats and dark (rows, Ns): (rows, M, Ns) float32
+    (cpct_preprocess_pc)."""
+    import torch
+    L = lib()
+    vp = ctypes.c_void_p
+    L.cpct_preprocess_pc.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+    M, rows, ns = near.shape
+    raw = (getattr(torch, "uint16", torch.int16), torch.int16)
+    for t, dt, shape in ((near, raw, (M, rows, ns)), (far, raw, (M, rows, ns)),
+                         (flat_near, (torch.float32,), (rows, ns)), (flat_far, (torch.float32,), (rows, ns)),
+                         (dark, (torch.float32,), (rows, ns))):
+        if not (t.is_cuda and t.dtype in dt and t.is_contiguous() and tuple(t.shape) == shape):
+            raise ValueError(f"expected a contiguous {dt} CUDA tensor of shape {shape}")
+    if out is None:
+        out = torch.empty((rows, M, ns), device=near.device, dtype=torch.float32)
+    check(L.cpct_preprocess_pc(vp(near.data_ptr()), vp(far.data_ptr()), vp(flat_near.data_ptr()),
+                               vp(flat_far.data_ptr()), vp(dark.data_ptr()), M, rows, ns,
+                               _dev_ptr(out, (rows, M, ns), torch), _stream(torch, stream)), "cpct_preprocess_pc")
+    return out
+
+
 def debug_adj_items(n, n_det, n_views, cap=0, angles=None):
     """Host-side adjoint work items of a geometry with `cap` rounds per item
     (no GPU needed): dict(items, n_split, n_slots)."""

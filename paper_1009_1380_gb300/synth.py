@@ -181,3 +181,67 @@ def corrupt_sinogram(y_clean: np.ndarray, rng: np.random.Generator,
 def random_sinogram(n_views: int, n_det: int, rng: np.random.Generator, dtype=np.float32):
     """Dense random test vector in sinogram space (for adjoint tests)."""
     return rng.standard_normal((n_views, n_det)).astype(dtype)
+
+
+def pc_radiographs(n_views: int, n_rows: int, n_det: int, rng: np.random.Generator, n_spheres: int = 6,
+                   noise: bool = True, counts: bool = True, contrast: float = 0.05, i0: float = 20000.0):
+    """Synthetic near/far radiographs of a stack of spheres (input generation
+    for the preprocessing front end; the paper's Fig. 1 shows such frames of
+    two glass balls).
+
+    Spheres (radius R, centre (cx, cy, cz) in pixels, x/y about the rotation
+    axis at detector column n_det/2) project to chords
+    t = 2 sqrt(R^2 - (u - cx cos th - cy sin th)^2 - (z - cz)^2).  With the
+    projected phase phi = -sum a_phi t and absorption A = sum a_mu t
+    (a_mu << a_phi), the near (contact) frame is F T with transmission
+    T = exp(-A) and the far frame F' T (1 - c lap(phi)), the first-order
+    transport-of-intensity term of a propagation distance c = dz / k;
+    lap is the 5-point detector Laplacian over (row, column).  Flats F, F'
+    carry a per-pixel gain, dark D an offset; with ``noise`` the frames get
+    beam fluctuations per frame (0.3%), shot noise and 3 dead columns (gain
+    0 in both flats); with ``counts`` they are rounded to uint16.
+
+    Returns dict(near, far (M, rows, Ns), flat_near, flat_far, dark
+    (rows, Ns), pc_term (M, rows, Ns) = T c lap(phi) (noise-free value of
+    the normalized near - far difference), spheres)."""
+    th = np.pi * np.arange(n_views) / n_views
+    u = np.arange(-1, n_det + 1, dtype=np.float64) - n_det / 2.0
+    z = np.arange(-1, n_rows + 1, dtype=np.float64)
+    sph = []
+    for _ in range(n_spheres):
+        R = rng.uniform(0.08, 0.2) * n_det
+        rho = rng.uniform(0.0, 0.45 * n_det - R)
+        ang = rng.uniform(0.0, 2 * np.pi)
+        sph.append((R, rho * np.cos(ang), rho * np.sin(ang), rng.uniform(-0.3, 1.3) * n_rows,
+                    rng.uniform(0.5, 1.0), rng.uniform(0.002, 0.01)))
+    phi = np.zeros((n_views, n_rows + 2, n_det + 2))
+    A = np.zeros_like(phi)
+    for R, cx, cy, cz, a_phi, a_mu in sph:
+        sc = cx * np.cos(th) + cy * np.sin(th)
+        q = R * R - (u[None, None, :] - sc[:, None, None]) ** 2 - (z[None, :, None] - cz) ** 2
+        t = 2.0 * np.sqrt(np.maximum(q, 0.0))
+        phi -= a_phi * t
+        A += a_mu * t
+    lap = (phi[:, :-2, 1:-1] + phi[:, 2:, 1:-1] + phi[:, 1:-1, :-2] + phi[:, 1:-1, 2:] - 4 * phi[:, 1:-1, 1:-1])
+    T = np.exp(-A[:, 1:-1, 1:-1])
+    c = contrast / max(float(np.abs(lap).max()), 1e-30)
+    dark = rng.uniform(95.0, 105.0, (n_rows, n_det))
+    gain_n = rng.uniform(0.8, 1.2, (n_rows, n_det))
+    gain_f = rng.uniform(0.8, 1.2, (n_rows, n_det))
+    if noise:
+        dead = rng.choice(n_det, size=3, replace=False)
+        gain_n[:, dead] = 0.0
+        gain_f[:, dead] = 0.0
+    flat_n = dark + i0 * gain_n
+    flat_f = dark + i0 * gain_f
+    beam = 1.0 + (0.003 * rng.standard_normal(n_views) if noise else 0.0)
+    near = dark[None] + i0 * gain_n[None] * T * np.reshape(beam, (-1, 1, 1))
+    far = dark[None] + i0 * gain_f[None] * T * (1.0 - c * lap) * np.reshape(beam, (-1, 1, 1))
+    if noise:
+        near = near + np.sqrt(np.maximum(near, 0.0)) * rng.standard_normal(near.shape)
+        far = far + np.sqrt(np.maximum(far, 0.0)) * rng.standard_normal(far.shape)
+    if counts:
+        near = np.clip(np.rint(near), 0, 65535).astype(np.uint16)
+        far = np.clip(np.rint(far), 0, 65535).astype(np.uint16)
+    return {"near": near, "far": far, "flat_near": flat_n, "flat_far": flat_f, "dark": dark,
+            "pc_term": T * c * lap, "spheres": sph}
