@@ -468,6 +468,7 @@ def batch_bench(args, torch, cpct, synth, runs=10):
     return {"metric": "batched Radon fwd+adj Msamples/s", "value": info["samples"] / (ms / 1000.0) / 1e6,
             "unit": "Msamples/s", "ms_per_batch": ms, "slices": info["slices"], "samples_per_batch": info["samples"],
             "branches": info["branches"], "tuned_caps": {str(m): list(v) for m, v in caps.items()},
+            "tuned_bins": {str(m): {op: list(v[:2]) for op, v in base[m].bins().items()} for m in base},
             "workload": f"{len(plans)} slices {n}x{n}, views from {sorted(base)} x {n} bins, one graph launch"}
 
 
@@ -509,6 +510,49 @@ def spgl1_bench(args, torch, cpct, synth):
                             for k, i in enumerate(infos) if i["status"] != 1],
             "config": f"{B} slices {n}x{n} Laplacian phantoms, {m} views x {n} bins, noise 1% + 8 stuck columns, "
                       f"<= {c['iterations']} iterations, opt_tol 1e-4, ring filter"}
+
+
+def bins_bench(torch, cpct, synth, runs=10):
+    """Bin plans of the gridding kernels compared (the paper's quadtree
+    against uniform tiles of 16, 32 and 64 points, each with heavy bins split
+    into work items): gather and spread (+ reduce) device time per launch,
+    CUDA events around each kernel, L2 flushed before every pair, at the
+    2048^2 / 1024-view workload and at the largest and smallest view counts
+    of the batched 1024^2 workload."""
+    out = {"note": "us per launch, median of %d pairs; spread includes the reduce of split bins" % runs}
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")
+    for name, n, m, cfg in [("2048x1024", 2048, 1024, "c2_2048"), ("1024x512", 1024, 512, "paper_1024"),
+                            ("1024x64", 1024, 64, "paper_1024")]:
+        plan = cpct.Plan(n, n, m)
+        img = torch.from_numpy(synth.phantom(cfg)).cuda()
+        y = torch.empty((m, n), device="cuda")
+        z = torch.empty((n, n), device="cuda")
+        res = {}
+        for kind, tile in [("uniform", 16), ("uniform", 32), ("uniform", 64), ("quadtree", 0)]:
+            plan.set_bins("fwd", kind, tile)
+            plan.set_bins("adj", kind, tile)
+            for _ in range(3):
+                plan.fwd(img, y)
+                plan.adj(y, z)
+            g, sp, pair = [], [], []
+            for _ in range(runs):
+                flush.zero_()
+                plan.profile_enable(0x1FF)
+                plan.fwd(img, y)
+                plan.adj(y, z)
+                torch.cuda.synchronize()
+                pr = plan.profile_read()
+                g.append(pr["k_fwd_interp"][0] * 1e3)
+                sp.append((pr["k_adj_spread"][0] + pr.get("k_adj_reduce", (0.0, 0))[0]) * 1e3)
+                pair.append(sum(v[0] for v in pr.values()) * 1e3)
+            plan.profile_enable(0)
+            b = plan.bins()
+            res[kind if kind == "quadtree" else f"uniform{tile}"] = {
+                "gather_us": float(np.median(g)), "spread_us": float(np.median(sp)), "pair_us": float(np.median(pair)),
+                "adj_bins_16_32_64": b["adj"][2], "work": plan.work()}
+        out[name] = res
+        plan.close()
+    return out
 
 
 def warm_bench(args, torch, cpct, synth):
@@ -760,6 +804,8 @@ def run_ours(args, rank, world, local_rank):
         out["fft_comparison"] = cufft_comparison(torch, n, breakdown)
     if world == 1 and args.batch_slices > 0:
         out["batch"] = batch_bench(args, torch, cpct, synth)
+    if world == 1 and not args.no_bins:
+        out["bins"] = bins_bench(torch, cpct, synth)
     if world == 1 and args.spgl1_batch > 0:
         out["spgl1"] = spgl1_bench(args, torch, cpct, synth)
     if world == 1 and args.unet_batch > 0:
@@ -783,10 +829,11 @@ def main():
     ap.add_argument("--batch-slices", type=int, default=256, help="slices of the batched-operator workload (0: skip)")
     ap.add_argument("--spgl1-iters", type=int, default=0, help="override the SPGL1 iteration cap (0: 300)")
     ap.add_argument("--unet-batch", type=int, default=32, help="images of the denoiser workload (0: skip)")
+    ap.add_argument("--no-bins", action="store_true", help="skip the bin-plan comparison")
     ap.add_argument("--warm-pairs", type=int, default=1024, help="training pairs of the warm-start run (0: skip)")
     ap.add_argument("--warm-eval", type=int, default=256, help="fresh slices of the warm-start run")
     ap.add_argument("--warm-epochs", type=int, default=8, help="training epochs of the warm-start run")
-    ap.add_argument("--only", default="", choices=["", "spgl1", "batch", "unet", "warm"],
+    ap.add_argument("--only", default="", choices=["", "spgl1", "batch", "unet", "warm", "bins"],
                     help="run one secondary workload alone")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -794,7 +841,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.only in ("spgl1", "batch", "unet", "warm"):
+    elif args.only in ("spgl1", "batch", "unet", "warm", "bins"):
         import torch
         from paper_1009_1380_gb300 import build as b
         b.build()
@@ -806,6 +853,8 @@ def main():
             print(json.dumps(denoiser_bench(args, torch, cpct)), flush=True)
         elif args.only == "warm":
             print(json.dumps(warm_bench(args, torch, cpct, synth)), flush=True)
+        elif args.only == "bins":
+            print(json.dumps(bins_bench(torch, cpct, synth)), flush=True)
         else:
             print(json.dumps(batch_bench(args, torch, cpct, synth)), flush=True)
     else:

@@ -218,15 +218,41 @@ int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream_t stream);
  * clones yet.  Allocates the new item lists; synchronous. */
 int cpct_plan_set_caps(cpct_plan* plan, int fwd_cap, int adj_cap, cudaStream_t stream);
 
+/* Bin plans (section "fast radon transform": the sample plane is divided
+ * into bins, one thread block per bin, chosen by a quadtree that repeatedly
+ * divides the bin of largest samples x grid points into four).  A bin is a
+ * square of T x T points of the oversampled half spectrum, T = 16, 32 or 64;
+ * a plan is a uniform tiling with one T (kind CPCT_BINS_UNIFORM, `tile` = T)
+ * or that quadtree (kind CPCT_BINS_QUADTREE, leaves of 16..64 points; a bin
+ * is split while its cost exceeds twice the mean cost of the non-empty
+ * leaves).  which = 0: the forward gather (a sample belongs to the bin of
+ * its footprint's first point), 1: the adjoint spread (a sample belongs to
+ * every bin its 6x6 footprint touches).  cpct_plan_set_bins installs a plan
+ * for one operator (keeping its cap); the plan must not have clones;
+ * synchronous.  The default is uniform 32 for both.  Results do not depend
+ * on the bin plan beyond FP32 rounding (each bin sums its samples in its
+ * own order); for a given plan they are bitwise reproducible.
+ * cpct_plan_bins reports the installed plans (kind, tile, 0 for a quadtree)
+ * and, per operator, the number of bins of each size (16, 32, 64; host
+ * arrays of 3, may be NULL). */
+#define CPCT_BINS_UNIFORM 0
+#define CPCT_BINS_QUADTREE 1
+int cpct_plan_set_bins(cpct_plan* plan, int which, int kind, int tile, cudaStream_t stream);
+int cpct_plan_bins(const cpct_plan* plan, int* fwd_kind, int* fwd_tile, int* adj_kind, int* adj_tile,
+                   int* fwd_class_bins, int* adj_class_bins);
+
 /* Work items of a plan: forward gather items, adjoint spread items, heavy
- * tiles split over several spread items, and their partial tiles (slots).
- * Host only; any output pointer may be NULL. */
+ * bins split over several spread items, and their partial-tile space in
+ * units of 32 x 32 tiles (slots).  Host only; any output pointer may be
+ * NULL. */
 int cpct_plan_work(const cpct_plan* plan, int* n_fwd_items, int* n_adj_items, int* n_split, int* n_slots);
 
-/* Autotuner of the work-item sizes (the bins' split caps): times radon_fwd
- * for 256..4096 samples per gather item and radon_adj for 16..256 rounds per
- * spread item (median of `reps` launches each, CUDA events on `stream`) and
- * keeps the fastest; reports the chosen caps.  The plan must not have clones
+/* Autotuner of the bin plans and work-item sizes: for each operator times
+ * the bin plans uniform 16, 32, 64 and the quadtree at the default cap, keeps
+ * the fastest, then times its caps (256..4096 samples per gather item,
+ * 16..256 rounds per spread item) and keeps the fastest (median of `reps`
+ * launches each, CUDA events on `stream`); reports the chosen caps
+ * (cpct_plan_bins reports the bin plans).  The plan must not have clones
  * yet.  Allocates temporary buffers; synchronous. */
 int cpct_plan_tune(cpct_plan* plan, int reps, int* fwd_cap, int* adj_cap, cudaStream_t stream);
 
@@ -568,11 +594,21 @@ int cpct_debug_bin_tile(const cpct_geom* g, int which, int tile, uint32_t* ids, 
  * footprints of a round overlap, lane = bank class). */
 int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packed, int* valid);
 
-/* The adjoint work items that a plan of geometry g gets with `cap` rounds
- * per spread item (0: the default cap), built on the host exactly as
- * cpct_plan_create / cpct_plan_set_caps build them: items, split heavy
- * tiles, partial tiles (slots).  No GPU needed. */
+/* The adjoint work items that a plan of geometry g gets with its default
+ * bin plan and `cap` rounds per spread item (0: the default cap), built on
+ * the host exactly as cpct_plan_create / cpct_plan_set_caps build them:
+ * items, split heavy bins, partial-tile slots of 32 x 32.  No GPU needed. */
 int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, int* n_split, int* n_slots);
+
+/* A bin plan of a geometry built on the host exactly as cpct_plan_set_bins
+ * builds it (kind, tile as there): forward and adjoint bin counts, the
+ * adjoint bins of each size (16, 32, 64; host array of 3, may be NULL), the
+ * adjoint rounds, and valid = 1 if every invariant holds (disjoint aligned
+ * bins; forward lists partition the samples by first point; adjoint lists
+ * hold exactly the samples whose footprint touches the bin; rounds hold
+ * each entry once, footprints disjoint, lane = bank class).  No GPU needed. */
+int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int* n_fwd_bins, int* n_adj_bins,
+                       int* adj_class_bins, int* n_rounds, int* valid);
 
 /* The split of a sample coordinate u = k (hi + lo) into floor and fraction,
  * with the same float32 operations as the kernels. */

@@ -67,6 +67,10 @@ def lib():
         for name in ("radon_fwd_c", "radon_adj_c"):
             getattr(L, name).argtypes = [vp, vp, vp, vp]
         L.cpct_plan_set_caps.argtypes = [vp, i, i, vp]
+        L.cpct_plan_set_bins.argtypes = [vp, i, i, i, vp]
+        L.cpct_plan_bins.argtypes = [vp] + [ctypes.POINTER(i)] * 4 + [vp, vp]
+        L.cpct_debug_binplan.argtypes = [ctypes.POINTER(Geom), i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp,
+                                         ctypes.POINTER(i), ctypes.POINTER(i)]
         L.cpct_plan_work.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
         L.cpct_debug_adj_items.argtypes = [ctypes.POINTER(Geom), i, ctypes.POINTER(i), ctypes.POINTER(i),
                                            ctypes.POINTER(i)]
@@ -220,6 +224,23 @@ class Plan:
     def set_caps(self, fwd_cap=0, adj_cap=0, stream=None):
         check(lib().cpct_plan_set_caps(self._h, int(fwd_cap), int(adj_cap), _stream(self._torch, stream)),
               "cpct_plan_set_caps")
+
+    def set_bins(self, which, kind, tile=0, stream=None):
+        """Bin plan of one operator (which 'fwd' or 'adj'): kind 'uniform'
+        with tile 16 / 32 / 64, or 'quadtree' (cpct_plan_set_bins)."""
+        w = {"fwd": 0, "adj": 1}[which]
+        k = {"uniform": BINS_UNIFORM, "quadtree": BINS_QUADTREE}[kind]
+        check(lib().cpct_plan_set_bins(self._h, w, k, int(tile), _stream(self._torch, stream)), "cpct_plan_set_bins")
+
+    def bins(self):
+        """Installed bin plans: {'fwd': (kind, tile, bins per class), 'adj': ...}."""
+        v = [ctypes.c_int() for _ in range(4)]
+        fc = np.zeros(3, dtype=np.int32)
+        ac = np.zeros(3, dtype=np.int32)
+        check(lib().cpct_plan_bins(self._h, *[ctypes.byref(x) for x in v], fc.ctypes.data_as(ctypes.c_void_p),
+                                   ac.ctypes.data_as(ctypes.c_void_p)), "cpct_plan_bins")
+        name = {BINS_UNIFORM: "uniform", BINS_QUADTREE: "quadtree"}
+        return {"fwd": (name[v[0].value], v[1].value, fc.tolist()), "adj": (name[v[2].value], v[3].value, ac.tolist())}
 
     def work(self):
         v = [ctypes.c_int() for _ in range(4)]
@@ -385,6 +406,24 @@ def preprocess_pc(near, far, flat_near, flat_far, dark, out=None, stream=None):
                                vp(flat_far.data_ptr()), vp(dark.data_ptr()), M, rows, ns,
                                _dev_ptr(out, (rows, M, ns), torch), _stream(torch, stream)), "cpct_preprocess_pc")
     return out
+
+
+BINS_UNIFORM = 0
+BINS_QUADTREE = 1
+
+
+def debug_binplan(n, n_det, n_views, kind, tile=0, angles=None):
+    """Host-side bin plan of a geometry (no GPU needed): kind 'uniform' (tile
+    16/32/64) or 'quadtree'; dict(fwd_bins, adj_bins, adj_class_bins, rounds,
+    valid)."""
+    g, _keep = make_geom(n, n_det, n_views, angles)
+    k = {"uniform": BINS_UNIFORM, "quadtree": BINS_QUADTREE}[kind]
+    nf, na, nr, ok = (ctypes.c_int() for _ in range(4))
+    cls = np.zeros(3, dtype=np.int32)
+    check(lib().cpct_debug_binplan(ctypes.byref(g), k, int(tile), ctypes.byref(nf), ctypes.byref(na),
+                                   cls.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nr), ctypes.byref(ok)),
+          "cpct_debug_binplan")
+    return dict(fwd_bins=nf.value, adj_bins=na.value, adj_class_bins=cls.tolist(), rounds=nr.value, valid=ok.value)
 
 
 def debug_adj_items(n, n_det, n_views, cap=0, angles=None):

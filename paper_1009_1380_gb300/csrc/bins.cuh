@@ -1,0 +1,93 @@
+// Bin plans of the gridding kernels (host side; no device code).
+//
+// Section "fast radon transform": the sample plane is divided into bins
+// with one thread block per bin; the paper chooses them with a quadtree that
+// starts from one bin holding every sample and repeatedly divides the most
+// computationally intensive bin into four equal bins, the intensity being
+// the number of samples times the number of grid points of the bin.
+//
+// Here a bin is a square of T x T grid points (T = 16, 32 or 64, aligned to
+// T) of the extended half spectrum.  A bin plan is either a uniform tiling
+// with one T, or the paper's quadtree (leaves of 16..64 points).  The
+// forward gather puts every polar sample in the bin holding the first grid
+// point of its 6x6 footprint; the adjoint spread puts it in every bin its
+// footprint touches, packed into conflict-free rounds.  Bins whose lists are
+// longer than a cap are split into several work items (the adjoint's write
+// partial tiles, summed afterwards in a fixed order).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cpct_detail {
+
+constexpr int kNumTileClasses = 3;  // T = 16, 32, 64
+inline int tile_class(int T) { return T <= 16 ? 0 : T <= 32 ? 1 : 2; }
+inline int class_tile(int c) { return 16 << c; }
+inline int pack_xy(int x0, int y0) { return (y0 << 16) | x0; }
+
+enum BinKind { BIN_UNIFORM = 0, BIN_QUADTREE = 1 };
+
+// host mirror of the kernels' split of u = k (hi + lo) into floor and
+// fraction (identical IEEE single-precision operations)
+void host_split(float k, float hi, float lo, int* fl_out, float* z);
+
+// first grid point of every polar sample's 6x6 footprint: column
+// a0 = floor(u) - 2 mod G and buffer row rb0 = floor(v) of the extended
+// spectrum, for sample (j, k), k = 0..K, at index j (K + 1) + k
+struct Samples {
+  int m = 0, K = 0;
+  std::vector<int> a0, rb0;
+};
+
+void make_rays(int n, int ns, int m, const double* angles, double scale, std::vector<float4>& ray);
+void make_samples(int ns, int m, int G, const std::vector<float4>& ray, Samples& s);
+
+struct BinLayout {
+  int kind = BIN_UNIFORM;
+  int tile = 32;             // uniform tile size (0 for a quadtree)
+  std::vector<int4> bins;    // (x0, y0, T, 0)
+};
+
+// uniform tiling of the domain [0, W) x [0, H) with T x T bins
+void uniform_layout(int T, int W, int H, BinLayout& L);
+// the paper's quadtree over [0, W) x [0, H): split the bin of largest
+// samples x points (first points counted) into four while that cost exceeds
+// alpha times the mean cost of the non-empty leaves and the bin is larger
+// than 16; leaves larger than 64 are then tiled with 64 x 64 bins
+void quadtree_layout(const Samples& s, int W, int H, double alpha, BinLayout& L);
+
+struct BinLists {
+  std::vector<int> ptr;        // bins + 1
+  std::vector<uint32_t> ids;   // sample ids (j << 16 | k), grouped by bin, increasing inside a bin
+};
+void assign_fwd(const Samples& s, int W, int H, const BinLayout& L, BinLists& out);
+void assign_adj(const Samples& s, int W, int H, const BinLayout& L, BinLists& out);
+
+// forward: order every bin's samples so that within each group of 16 the
+// first cells fall in distinct 64-bit bank pairs of the staged window
+void order_fwd(const Samples& s, const BinLayout& L, BinLists& b);
+
+// adjoint: rounds of <= 32 samples with pairwise disjoint footprints in the
+// bin's (T + 10) x (T + 12) accumulator, lane = bank class of the first cell
+struct Rounds {
+  std::vector<int> ptr;         // bins + 1, in rounds
+  std::vector<uint32_t> ids;    // 32 per round, 0xffffffff = empty lane
+};
+inline int round_pitch(int T) { return T + 2 * CPCT_HALO + 2; }
+void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, Rounds& out);
+
+// work items, grouped by tile class and longest first within a class
+struct Items {
+  std::vector<int4> items;   // forward (xy, begin, end, 0); adjoint (xy, begin, end, partial offset or -1)
+  int cls[kNumTileClasses + 1] = {0, 0, 0, 0};
+  std::vector<int4> split;   // adjoint: (xy, partial offset, pieces, T), grouped by class
+  int split_cls[kNumTileClasses + 1] = {0, 0, 0, 0};
+  long long partial_elems = 0;  // complex values of all partial tiles
+};
+void fwd_items(const BinLayout& L, const std::vector<int>& ptr, int cap, Items& out);
+void adj_items(const BinLayout& L, const std::vector<int>& rptr, int cap, Items& out);
+
+}  // namespace cpct_detail

@@ -58,7 +58,6 @@ struct cpct_plan {
   int n, ns, m, G, K;       // K = Ns/2
   int logn, logG, logNs;
   int ldh, ext_rows, ldq;
-  int tiles_x_fwd, tiles_y_fwd, tiles_x_adj, tiles_y_adj;
   int flags;
   double scale;             // G / Ns
 
@@ -72,25 +71,32 @@ struct cpct_plan {
   float2* d_Ax;             // adjoint accumulator (same shape)
   float2* d_H1;             // (N+1) x N
   float2* d_Q;              // M x LDQ
-  // forward gather bins
+  // bins: squares of T x T grid points (T = 16, 32, 64; class c = 0, 1, 2);
+  // work items are grouped by class, a bin's origin packed as y0 << 16 | x0
+  // forward gather work items (origin, first sample, end sample, 0)
   int n_fwd_items;
-  int4* d_fwd_items;        // (tile, begin, end, 0)
-  uint32_t* d_fwd_ids;      // sample ids (j << 16 | k), grouped by tile
-  // adjoint spread bins
+  int fwd_cls[4];           // items of class c: [fwd_cls[c], fwd_cls[c + 1])
+  int4* d_fwd_items;
+  uint32_t* d_fwd_ids;      // sample ids (j << 16 | k), grouped by bin
+  // adjoint spread work items (origin, first round, end round, partial offset or -1)
   int n_adj_items;
-  int4* d_adj_items;        // (tile, begin, end, slot or -1)
-  uint32_t* d_adj_ids;
-  int n_slots;
-  float2* d_partials;       // n_slots x 32 x 32 partial tiles (split heavy tiles)
+  int adj_cls[4];
+  int4* d_adj_items;
+  uint32_t* d_adj_ids;      // rounds of 32 lanes
+  int n_slots;              // partial-tile space in units of 32 x 32 tiles (rounded up)
+  long long partial_elems;  // complex values of the partial tiles of split bins
+  float2* d_partials;
   int n_split;
-  int4* d_split;            // (tile, first slot, n slots, 0)
+  int split_cls[4];
+  int4* d_split;            // (origin, partial offset, pieces, T), grouped by class
+  int fwd_kind, fwd_tile, adj_kind, adj_tile;  // bin plans (kind 0 uniform, 1 quadtree)
   // staging for the host-buffer entry points
   float* d_stage_img;
   float* d_stage_sino;
   int* d_err;
-  CUtensorMap tmap_Hx;
+  CUtensorMap tmap_Hx[3];   // TMA windows of 16, 32 and 64 point bins
   size_t device_bytes;
-  int fwd_interp_grid;      // persistent grid of the forward gather (0 = not yet sized)
+  int fwd_interp_grid[3];   // persistent grids of the forward gather per class (0 = not yet sized)
   int fwd_cap, adj_cap;     // work-item caps (samples / rounds per item), tunable
   struct PlanShared* shared;  // read-only geometry shared with clones (refcounted)
   long long launches;       // kernels launched by this plan's operators
@@ -104,8 +110,11 @@ struct cpct_plan {
 #include <vector>
 struct PlanShared {
   std::atomic<int> refs{1};
-  std::vector<int> fwd_tile_ptr;    // forward bins: tiles + 1
-  std::vector<int> round_tile_ptr;  // adjoint rounds per tile: tiles + 1
+  std::vector<float4> ray;          // per-ray geometry (host copy)
+  std::vector<int4> fwd_bins;       // forward bins (x0, y0, T, 0)
+  std::vector<int> fwd_ptr;         // forward bins: samples, bins + 1
+  std::vector<int4> adj_bins;       // adjoint bins
+  std::vector<int> round_ptr;       // adjoint rounds per bin: bins + 1
 };
 
 // bracket a kernel launch: counts it and, if its id is profiled, records a

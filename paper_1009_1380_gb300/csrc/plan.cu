@@ -1,14 +1,15 @@
 // Plan construction: geometry, Kaiser-Bessel kernel approximation and
 // deapodization (built on the device in FP64), FFT twiddle tables, and the
-// tile bin lists of the polar samples.
+// bin plans of the polar samples.
 //
 // Gridding (section "fast radon transform") convolves the irregular polar
 // samples with a kernel on the regular grid.  The paper divides the sample
 // plane into bins (one thread block per bin) chosen by a quadtree on the cost
-// samples x grid points; here the bins are fixed 32x32 grid tiles and every
-// bin whose sample list is longer than a cap is split into several work items
-// (ordered longest first), which balances the load around the origin where all
-// rays meet.
+// samples x grid points.  A plan's bins are either a uniform tiling (16, 32
+// or 64 grid points; 32 by default) or that quadtree (bins.cu), chosen per
+// operator by cpct_plan_set_bins or the autotuner; every bin whose list is
+// longer than a cap is split into several work items (ordered longest
+// first), which balances the load around the origin where all rays meet.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -17,6 +18,7 @@
 #include <cstring>
 #include <vector>
 
+#include "bins.cuh"
 #include "common.cuh"
 
 namespace {
@@ -126,24 +128,6 @@ bool geom_ok(const cpct_geom* g) {
   return true;
 }
 
-// host mirror of split_coord (identical IEEE single-precision operations)
-void host_split(float k, float hi, float lo, int* fl_out, float* z) {
-  float p = k * hi;
-  float e = std::fmaf(k, hi, -p);
-  float corr = std::fmaf(k, lo, e);
-  float fl = std::floor(p);
-  float zz = (p - fl) + corr;
-  if (zz < 0.f) {
-    float t = zz + 1.f;
-    if (t < 1.f) { zz = t; fl = fl - 1.f; } else { zz = 0.f; }
-  } else if (zz >= 1.f) {
-    zz = zz - 1.f;
-    fl = fl + 1.f;
-  }
-  *fl_out = (int)fl;
-  *z = zz;
-}
-
 struct Alloc {
   cpct_plan* p;
   bool fail_next;
@@ -203,17 +187,49 @@ void free_plan(cpct_plan* p) {
   delete p;
 }
 
+// TMA descriptors of the forward extended spectrum (viewed as float32 pairs),
+// one per bin size: boxes of T + 5 rows of T + 6 complex values
 int encode_hx_map(cpct_plan* p) {
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) return CPCT_EUNSUPPORTED;
-  cuuint64_t dims[2] = {(cuuint64_t)2 * p->ldh, (cuuint64_t)p->ext_rows};
-  cuuint64_t strides[1] = {(cuuint64_t)p->ldh * sizeof(float2)};
-  cuuint32_t box[2] = {2 * (CPCT_TILE + CPCT_HALO + 1), CPCT_TILE + CPCT_HALO};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult cr = enc(&p->tmap_Hx, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->d_Hx, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return cr == CUDA_SUCCESS ? CPCT_OK : CPCT_ECUDA;
+  for (int c = 0; c < cpct_detail::kNumTileClasses; ++c) {
+    const int T = cpct_detail::class_tile(c);
+    cuuint64_t dims[2] = {(cuuint64_t)2 * p->ldh, (cuuint64_t)p->ext_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)p->ldh * sizeof(float2)};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * (T + CPCT_HALO + 1)), (cuuint32_t)(T + CPCT_HALO)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = enc(&p->tmap_Hx[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->d_Hx, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return CPCT_ECUDA;
+  }
+  return CPCT_OK;
+}
+
+// domains of the bins: forward, the first points (columns 0..G-1, rows up to
+// the largest first row); adjoint, every cell a footprint touches
+void fwd_domain(const cpct_detail::Samples& s, int G, int* W, int* H) {
+  int mr = 0;
+  for (int r : s.rb0) mr = std::max(mr, r);
+  *W = G;
+  *H = mr + 1;
+}
+void adj_domain(const cpct_detail::Samples& s, int G, int* W, int* H) {
+  int mr = 0;
+  for (int r : s.rb0) mr = std::max(mr, r);
+  *W = G + CPCT_HALO;
+  *H = mr + CPCT_HALO + 1;
+}
+
+constexpr double kQuadAlpha = 2.0;  // quadtree: split while cost > alpha x mean leaf cost
+
+void make_layout(const cpct_detail::Samples& s, int W, int H, int kind, int tile, cpct_detail::BinLayout& L) {
+  if (kind == cpct_detail::BIN_QUADTREE) cpct_detail::quadtree_layout(s, W, H, kQuadAlpha, L);
+  else cpct_detail::uniform_layout(tile, W, H, L);
+}
+
+bool bins_args_ok(int kind, int tile) {
+  return kind == cpct_detail::BIN_QUADTREE || (kind == cpct_detail::BIN_UNIFORM && (tile == 16 || tile == 32 || tile == 64));
 }
 
 }  // namespace
@@ -221,293 +237,168 @@ int encode_hx_map(cpct_plan* p) {
 // ---------------------------------------------------------------------------
 // bin lists (exported for host-side tests: no GPU needed)
 // ---------------------------------------------------------------------------
-extern "C" int cpct_debug_bins(const cpct_geom* g, int which, int* n_tiles, int* n_entries, int64_t* checksum);
+namespace {
 
-namespace cpct_detail {
-
-struct Bins {
-  int tiles_x, tiles_y;
-  std::vector<int> ptr;          // tiles + 1
-  std::vector<uint32_t> ids;     // grouped by tile, increasing id inside a tile
+struct HostBins {
+  cpct_detail::Samples s;
+  cpct_detail::BinLayout fl, al;
+  cpct_detail::BinLists fwd, adj;
+  int fW, fH, aW, aH;
 };
 
-struct RayTab {
-  std::vector<float4> ray;
-};
-
-void make_rays(int n, int ns, int m, const double* angles, double scale, std::vector<float4>& ray) {
-  ray.resize(m);
-  for (int j = 0; j < m; ++j) {
-    const double th = angles ? angles[j] : M_PI * (double)j / (double)m;
-    const double c = scale * std::cos(th), s = scale * std::sin(th);
-    const float ch = (float)c, sh = (float)s;
-    ray[j] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
-  }
-}
-
-// forward bins: every sample (j, k >= 0) lands in the tile of its footprint's
-// first grid point (a0 = floor(u)-2 mod G, buffer row floor(v)); adjoint bins:
-// every tile of the extended spectrum that its 6x6 footprint touches.
-void build_bins(int n, int ns, int m, int G, const std::vector<float4>& ray, Bins& fwd, Bins& adj,
-                std::vector<int>* a0_out = nullptr, std::vector<int>* rb0_out = nullptr) {
-  const int K = ns / 2;
-  const int T = CPCT_TILE;
-  fwd.tiles_x = G / T;
-  fwd.tiles_y = n / T + 1;
-  adj.tiles_x = G / T + 1;
-  adj.tiles_y = (n + 5) / T + 1;
-  const int nf = fwd.tiles_x * fwd.tiles_y, na = adj.tiles_x * adj.tiles_y;
-  std::vector<int> cf(nf + 1, 0), ca(na + 1, 0);
-  std::vector<int> fa0((size_t)m * (K + 1)), frb((size_t)m * (K + 1));
-  for (int j = 0; j < m; ++j) {
-    for (int k = 0; k <= K; ++k) {
-      int fu, fv;
-      float zu, zv;
-      host_split((float)k, ray[j].x, ray[j].y, &fu, &zu);
-      host_split((float)k, ray[j].z, ray[j].w, &fv, &zv);
-      const int a0 = (fu - 2) & (G - 1);
-      const int rb0 = fv;  // buffer row of the first tap: (floor(v) - 2) + 2
-      const size_t sidx = (size_t)j * (K + 1) + k;
-      fa0[sidx] = a0;
-      frb[sidx] = rb0;
-      cf[(rb0 / T) * fwd.tiles_x + a0 / T + 1]++;
-      for (int ty = rb0 / T; ty <= (rb0 + CPCT_HALO) / T; ++ty)
-        for (int tx = a0 / T; tx <= (a0 + CPCT_HALO) / T; ++tx) ca[ty * adj.tiles_x + tx + 1]++;
-    }
-  }
-  for (int i = 0; i < nf; ++i) cf[i + 1] += cf[i];
-  for (int i = 0; i < na; ++i) ca[i + 1] += ca[i];
-  fwd.ptr = cf;
-  adj.ptr = ca;
-  fwd.ids.resize(cf[nf]);
-  adj.ids.resize(ca[na]);
-  std::vector<int> pf(cf.begin(), cf.end() - 1), pa(ca.begin(), ca.end() - 1);
-  for (int j = 0; j < m; ++j) {
-    for (int k = 0; k <= K; ++k) {
-      const size_t sidx = (size_t)j * (K + 1) + k;
-      const int a0 = fa0[sidx], rb0 = frb[sidx];
-      const uint32_t id = ((uint32_t)j << 16) | (uint32_t)k;
-      fwd.ids[pf[(rb0 / T) * fwd.tiles_x + a0 / T]++] = id;
-      for (int ty = rb0 / T; ty <= (rb0 + CPCT_HALO) / T; ++ty)
-        for (int tx = a0 / T; tx <= (a0 + CPCT_HALO) / T; ++tx) adj.ids[pa[ty * adj.tiles_x + tx]++] = id;
-    }
-  }
-  if (a0_out) a0_out->swap(fa0);
-  if (rb0_out) rb0_out->swap(frb);
-}
-
-// Pack the samples of every adjoint tile into rounds of at most 32 samples
-// whose 6x6 footprints (clipped to the tile plus a 5-cell halo) are pairwise
-// disjoint, so that one warp can add a whole round with one lane per sample
-// and no two lanes touching the same accumulator.  The lane of a sample is
-// fixed by the 64-bit shared-memory bank pair of its footprint's first cell
-// (lanes c and c+16 for bank pair c), which makes every accumulator access of
-// a round bank-conflict free.  Greedy first fit in bin order (deterministic).
-struct Rounds {
-  std::vector<int> tile_ptr;      // tiles + 1, in rounds
-  std::vector<uint32_t> ids;      // 32 per round, 0xffffffff = empty lane
-};
-
-constexpr int kRoundLd = CPCT_TILE + 2 * CPCT_HALO + 2;  // 44 complex per accumulator row
-
-void pack_rounds(const Bins& adj, int G, const std::vector<int>& fa0, const std::vector<int>& frb, int K,
-                 Rounds& out) {
-  const int nt = (int)adj.ptr.size() - 1;
-  out.tile_ptr.assign(nt + 1, 0);
-  out.ids.clear();
-  struct R {
-    uint64_t occ[CPCT_TILE + 2 * CPCT_HALO];
-    uint32_t lanes;
-    int count;
-  };
-  std::vector<R> rounds;
-  for (int t = 0; t < nt; ++t) {
-    const int TC = (t % adj.tiles_x) * CPCT_TILE, TR = (t / adj.tiles_x) * CPCT_TILE;
-    rounds.clear();
-    size_t first_open = 0;
-    std::vector<std::array<uint32_t, 32>> lanes_of;
-    for (int e = adj.ptr[t]; e < adj.ptr[t + 1]; ++e) {
-      const uint32_t id = adj.ids[e];
-      const size_t sidx = (size_t)(id >> 16) * (K + 1) + (id & 0xffffu);
-      const int ar = fa0[sidx] - TC + CPCT_HALO, br = frb[sidx] - TR + CPCT_HALO;  // 0..36
-      const int cls = ((br * kRoundLd + ar) & 15);
-      const uint64_t fm = 0x3Full << ar;
-      size_t r = first_open;
-      for (; r < rounds.size(); ++r) {
-        R& rd = rounds[r];
-        if (rd.count == 32) continue;
-        if ((rd.lanes >> cls) & (rd.lanes >> (cls + 16)) & 1u) continue;
-        bool clash = false;
-        for (int q = 0; q < CPCT_W && !clash; ++q) clash = (rd.occ[br + q] & fm) != 0;
-        if (!clash) break;
-      }
-      if (r == rounds.size()) {
-        rounds.push_back(R{});
-        std::memset(&rounds.back(), 0, sizeof(R));
-        std::array<uint32_t, 32> empty;
-        empty.fill(0xffffffffu);
-        lanes_of.push_back(empty);
-      }
-      R& rd = rounds[r];
-      const int lane = ((rd.lanes >> cls) & 1u) ? cls + 16 : cls;
-      rd.lanes |= 1u << lane;
-      rd.count++;
-      for (int q = 0; q < CPCT_W; ++q) rd.occ[br + q] |= fm;
-      lanes_of[r][lane] = id;
-      while (first_open < rounds.size() && rounds[first_open].count == 32) ++first_open;
-    }
-    for (auto& l : lanes_of) out.ids.insert(out.ids.end(), l.begin(), l.end());
-    out.tile_ptr[t + 1] = out.tile_ptr[t] + (int)rounds.size();
-  }
-}
-
-// Order the samples of every forward bin so that within each group of 16
-// consecutive samples (one half-warp) the first cells of their 6x6 windows
-// fall in distinct 64-bit bank pairs of the staged 37 x 38 window: every tap
-// load of the gather is then bank-conflict free.  Round-robin over the bank
-// classes, each class in bin order (deterministic).
-void order_fwd_bins(Bins& fwd, int K, const std::vector<int>& fa0, const std::vector<int>& frb, int win_ld) {
-  const int nt = (int)fwd.ptr.size() - 1;
-  std::vector<uint32_t> cls[16];
-  for (int t = 0; t < nt; ++t) {
-    const int C0 = (t % fwd.tiles_x) * CPCT_TILE, R0 = (t / fwd.tiles_x) * CPCT_TILE;
-    for (auto& c : cls) c.clear();
-    for (int e = fwd.ptr[t]; e < fwd.ptr[t + 1]; ++e) {
-      const uint32_t id = fwd.ids[e];
-      const size_t sidx = (size_t)(id >> 16) * (K + 1) + (id & 0xffffu);
-      const int ar = fa0[sidx] - C0, br = frb[sidx] - R0;
-      cls[(br * win_ld + ar) & 15].push_back(id);
-    }
-    size_t pos[16] = {0};
-    int e = fwd.ptr[t];
-    while (e < fwd.ptr[t + 1]) {
-      for (int c = 0; c < 16; ++c)
-        if (pos[c] < cls[c].size()) fwd.ids[e++] = cls[c][pos[c]++];
-    }
-  }
-}
-
-// split bins into work items of at most `cap` entries, longest first
-void make_items(const Bins& b, int cap, bool slots, std::vector<int4>& items, std::vector<int4>& split,
-                int* n_slots) {
-  const int nt = (int)b.ptr.size() - 1;
-  items.clear();
-  split.clear();
-  int slot = 0;
-  for (int t = 0; t < nt; ++t) {
-    const int beg = b.ptr[t], end = b.ptr[t + 1];
-    if (end == beg) continue;
-    const int pieces = (end - beg + cap - 1) / cap;
-    if (pieces == 1 || !slots) {
-      for (int q = 0; q < pieces; ++q)
-        items.push_back(make_int4(t, beg + q * cap, std::min(end, beg + (q + 1) * cap), -1));
-    } else {
-      split.push_back(make_int4(t, slot, pieces, 0));
-      for (int q = 0; q < pieces; ++q)
-        items.push_back(make_int4(t, beg + q * cap, std::min(end, beg + (q + 1) * cap), slot + q));
-      slot += pieces;
-    }
-  }
-  std::stable_sort(items.begin(), items.end(),
-                   [](const int4& a, const int4& c) { return (a.z - a.y) > (c.z - c.y); });
-  if (n_slots) *n_slots = slot;
-}
-
-// work items over rounds: at most `cap` rounds per item, longest first; tiles
-// split over several items accumulate into partial-tile slots
-void make_round_items(const Rounds& rd, int cap, std::vector<int4>& items, std::vector<int4>& split, int* n_slots,
-                      std::vector<int>& item_split) {
-  const int nt = (int)rd.tile_ptr.size() - 1;
-  items.clear();
-  split.clear();
-  int slot = 0;
-  for (int t = 0; t < nt; ++t) {
-    const int beg = rd.tile_ptr[t], end = rd.tile_ptr[t + 1];
-    if (end == beg) continue;
-    const int pieces = (end - beg + cap - 1) / cap;
-    if (pieces == 1) {
-      items.push_back(make_int4(t, beg, end, -1));
-    } else {
-      split.push_back(make_int4(t, slot, pieces, 0));
-      for (int q = 0; q < pieces; ++q)
-        items.push_back(make_int4(t, beg + q * cap, std::min(end, beg + (q + 1) * cap), slot + q));
-      slot += pieces;
-    }
-  }
-  std::stable_sort(items.begin(), items.end(),
-                   [](const int4& a, const int4& c) { return (a.z - a.y) > (c.z - c.y); });
-  *n_slots = slot;
-  // split index of every item (slots of split k are contiguous from split[k].y)
-  item_split.assign(items.size(), -1);
-  for (size_t i = 0; i < items.size(); ++i) {
-    if (items[i].w < 0) continue;
-    int lo = 0, hi = (int)split.size() - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (split[mid].y <= items[i].w) lo = mid; else hi = mid - 1;
-    }
-    item_split[i] = lo;
-  }
-}
-
-}  // namespace cpct_detail
-
-// Round packing of the adjoint bins of a geometry (host only): number of
-// rounds, number of packed samples, and 1 if every round is footprint- and
-// bank-conflict free and every bin entry appears exactly once, else 0.
-extern "C" int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packed, int* valid) {
-  if (!geom_ok(g)) return CPCT_EINVAL;
-  const int G = 2 * g->n, K = g->n_det / 2;
+int host_bins(const cpct_geom* g, int kind, int tile, HostBins& h, bool rounds_order = true) {
+  if (!geom_ok(g) || !bins_args_ok(kind, tile)) return CPCT_EINVAL;
+  const int G = 2 * g->n;
   std::vector<float4> ray;
   cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
-  cpct_detail::Bins f, a;
-  std::vector<int> fa0, frb;
-  cpct_detail::build_bins(g->n, g->n_det, g->n_views, G, ray, f, a, &fa0, &frb);
-  cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(a, G, fa0, frb, K, rd);
-  const int nt = (int)a.ptr.size() - 1;
-  int ok = 1, packed = 0;
-  for (int t = 0; t < nt && ok; ++t) {
-    const int TC = (t % a.tiles_x) * CPCT_TILE, TR = (t / a.tiles_x) * CPCT_TILE;
-    std::vector<uint32_t> seen;
-    for (int r = rd.tile_ptr[t]; r < rd.tile_ptr[t + 1] && ok; ++r) {
+  cpct_detail::make_samples(g->n_det, g->n_views, G, ray, h.s);
+  fwd_domain(h.s, G, &h.fW, &h.fH);
+  adj_domain(h.s, G, &h.aW, &h.aH);
+  make_layout(h.s, h.fW, h.fH, kind, tile, h.fl);
+  make_layout(h.s, h.aW, h.aH, kind, tile, h.al);
+  cpct_detail::assign_fwd(h.s, h.fW, h.fH, h.fl, h.fwd);
+  cpct_detail::assign_adj(h.s, h.aW, h.aH, h.al, h.adj);
+  (void)rounds_order;
+  return CPCT_OK;
+}
+
+// every invariant of a bin plan: bins are disjoint squares of 16/32/64
+// aligned to their size; forward lists partition the samples by first point;
+// adjoint lists hold each sample once in every bin its footprint touches;
+// rounds hold every adjoint entry once, footprints of a round disjoint,
+// lane = bank class
+int check_plan(const HostBins& h, const cpct_detail::Rounds& rd, int* n_packed) {
+  int ok = 1;
+  const auto& s = h.s;
+  auto disjoint = [&](const cpct_detail::BinLayout& L) {
+    std::vector<std::pair<int, int>> cells;
+    for (const int4& b : L.bins) {
+      if (!(b.z == 16 || b.z == 32 || b.z == 64) || b.x % b.z || b.y % b.z) return false;
+      for (int y = b.y; y < b.y + b.z; y += 16)
+        for (int x = b.x; x < b.x + b.z; x += 16) cells.push_back({y, x});
+    }
+    std::sort(cells.begin(), cells.end());
+    return std::adjacent_find(cells.begin(), cells.end()) == cells.end();
+  };
+  if (!disjoint(h.fl) || !disjoint(h.al)) ok = 0;
+  const size_t ns = s.a0.size();
+  std::vector<int> seen(ns, 0);
+  for (size_t t = 0; t + 1 < h.fwd.ptr.size() && ok; ++t) {
+    const int4 b = h.fl.bins[t];
+    for (int e = h.fwd.ptr[t]; e < h.fwd.ptr[t + 1]; ++e) {
+      const uint32_t id = h.fwd.ids[e];
+      const size_t i = (size_t)(id >> 16) * (s.K + 1) + (id & 0xffffu);
+      seen[i]++;
+      if (s.a0[i] < b.x || s.a0[i] >= b.x + b.z || s.rb0[i] < b.y || s.rb0[i] >= b.y + b.z) ok = 0;
+    }
+  }
+  for (size_t i = 0; i < ns && ok; ++i)
+    if (seen[i] != 1) ok = 0;
+  // adjoint: a footprint touches bin [x0, x0 + T) x [y0, y0 + T) iff its
+  // first point lies in [x0 - 5, x0 + T - 1] x [y0 - 5, y0 + T - 1]; the
+  // number of such samples per bin from 2D prefix sums of the first points
+  {
+    const int PW = h.aW + 1, PH = h.aH + 1;
+    std::vector<int> pre((size_t)(PH + 1) * (PW + 1), 0);
+    for (size_t i = 0; i < ns; ++i) pre[(size_t)(s.rb0[i] + 1) * (PW + 1) + s.a0[i] + 1]++;
+    for (int y = 1; y <= PH; ++y)
+      for (int x = 1; x <= PW; ++x)
+        pre[(size_t)y * (PW + 1) + x] += pre[(size_t)(y - 1) * (PW + 1) + x] + pre[(size_t)y * (PW + 1) + x - 1] -
+                                         pre[(size_t)(y - 1) * (PW + 1) + x - 1];
+    auto count = [&](int x0, int y0, int x1, int y1) {  // first points in [x0, x1) x [y0, y1)
+      x0 = std::max(0, std::min(x0, PW));
+      x1 = std::max(0, std::min(x1, PW));
+      y0 = std::max(0, std::min(y0, PH));
+      y1 = std::max(0, std::min(y1, PH));
+      if (x1 <= x0 || y1 <= y0) return 0;
+      const int w = PW + 1;
+      return pre[(size_t)y1 * w + x1] - pre[(size_t)y0 * w + x1] - pre[(size_t)y1 * w + x0] + pre[(size_t)y0 * w + x0];
+    };
+    for (size_t t = 0; t + 1 < h.adj.ptr.size() && ok; ++t) {
+      const int4 b = h.al.bins[t];
+      const int want = count(b.x - CPCT_HALO, b.y - CPCT_HALO, b.x + b.z, b.y + b.z);
+      if (h.adj.ptr[t + 1] - h.adj.ptr[t] != want) ok = 0;
+    }
+  }
+  int packed = 0;
+  for (size_t t = 0; t + 1 < rd.ptr.size() && ok; ++t) {
+    const int4 b = h.al.bins[t];
+    const int ld = cpct_detail::round_pitch(b.z);
+    std::vector<uint32_t> got;
+    for (int r = rd.ptr[t]; r < rd.ptr[t + 1] && ok; ++r) {
       std::vector<int> cells;
       for (int l = 0; l < 32; ++l) {
         const uint32_t id = rd.ids[(size_t)r * 32 + l];
         if (id == 0xffffffffu) continue;
-        seen.push_back(id);
-        const size_t sidx = (size_t)(id >> 16) * (K + 1) + (id & 0xffffu);
-        const int ar = fa0[sidx] - TC + CPCT_HALO, br = frb[sidx] - TR + CPCT_HALO;
-        if (ar < 0 || br < 0 || ar > CPCT_TILE + CPCT_HALO - 1 || br > CPCT_TILE + CPCT_HALO - 1) ok = 0;
-        if (((br * cpct_detail::kRoundLd + ar) & 15) != (l & 15)) ok = 0;
+        got.push_back(id);
+        const size_t i = (size_t)(id >> 16) * (s.K + 1) + (id & 0xffffu);
+        const int ar = s.a0[i] - b.x + CPCT_HALO, br = s.rb0[i] - b.y + CPCT_HALO;
+        if (ar < 0 || br < 0 || ar > b.z + CPCT_HALO - 1 || br > b.z + CPCT_HALO - 1) ok = 0;
+        if (((br * ld + ar) & 15) != (l & 15)) ok = 0;
         for (int q = 0; q < CPCT_W; ++q)
-          for (int c = 0; c < CPCT_W; ++c) cells.push_back((br + q) * cpct_detail::kRoundLd + ar + c);
+          for (int c = 0; c < CPCT_W; ++c) cells.push_back((br + q) * ld + ar + c);
       }
       std::sort(cells.begin(), cells.end());
       if (std::adjacent_find(cells.begin(), cells.end()) != cells.end()) ok = 0;
     }
-    std::vector<uint32_t> want(a.ids.begin() + a.ptr[t], a.ids.begin() + a.ptr[t + 1]);
-    std::sort(seen.begin(), seen.end());
-    std::sort(want.begin(), want.end());
-    if (seen != want) ok = 0;
-    packed += (int)seen.size();
+    std::vector<uint32_t> want_ids(h.adj.ids.begin() + h.adj.ptr[t], h.adj.ids.begin() + h.adj.ptr[t + 1]);
+    std::sort(got.begin(), got.end());
+    std::sort(want_ids.begin(), want_ids.end());
+    if (got != want_ids) ok = 0;
+    packed += (int)got.size();
   }
-  if (n_rounds) *n_rounds = (int)(rd.ids.size() / 32);
   if (n_packed) *n_packed = packed;
+  return ok;
+}
+
+}  // namespace
+
+// Round packing of the adjoint bins of a geometry (default bin plan, host
+// only): number of rounds, number of packed samples, and 1 if every round
+// is footprint- and bank-conflict free and every bin entry appears exactly
+// once, else 0.
+extern "C" int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packed, int* valid) {
+  HostBins h;
+  int rc = host_bins(g, cpct_detail::BIN_UNIFORM, CPCT_TILE, h);
+  if (rc) return rc;
+  cpct_detail::Rounds rd;
+  cpct_detail::pack_rounds(h.s, h.al, h.adj, rd);
+  const int ok = check_plan(h, rd, n_packed);
+  if (n_rounds) *n_rounds = (int)(rd.ids.size() / 32);
   if (valid) *valid = ok;
   return CPCT_OK;
 }
 
-// which = 0: forward bins, 1: adjoint bins.  Reports the number of tiles, the
-// number of entries and a checksum sum(id * (position + 1)) of the id list.
+// A bin plan of a geometry (host only): kind 0 uniform tiles of `tile`
+// points, kind 1 the quadtree.  Reports the forward and adjoint bin counts,
+// the bins of each size class (T = 16, 32, 64) of the adjoint plan, the
+// rounds and 1 if every invariant holds (check_plan).
+extern "C" int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int* n_fwd_bins, int* n_adj_bins,
+                                  int* adj_class_bins, int* n_rounds, int* valid) {
+  HostBins h;
+  int rc = host_bins(g, kind, tile, h);
+  if (rc) return rc;
+  cpct_detail::Rounds rd;
+  cpct_detail::pack_rounds(h.s, h.al, h.adj, rd);
+  if (valid) *valid = check_plan(h, rd, nullptr);
+  if (n_fwd_bins) *n_fwd_bins = (int)h.fl.bins.size();
+  if (n_adj_bins) *n_adj_bins = (int)h.al.bins.size();
+  if (adj_class_bins) {
+    for (int c = 0; c < cpct_detail::kNumTileClasses; ++c) adj_class_bins[c] = 0;
+    for (const int4& b : h.al.bins) adj_class_bins[cpct_detail::tile_class(b.z)]++;
+  }
+  if (n_rounds) *n_rounds = (int)(rd.ids.size() / 32);
+  return CPCT_OK;
+}
+
+// which = 0: forward bins, 1: adjoint bins (default bin plan).  Reports the
+// number of bins, the number of entries and a checksum sum(id * (position +
+// 1)) of the id list.
 extern "C" int cpct_debug_bins(const cpct_geom* g, int which, int* n_tiles, int* n_entries, int64_t* checksum) {
-  if (!geom_ok(g)) return CPCT_EINVAL;
-  const int G = 2 * g->n;
-  std::vector<float4> ray;
-  cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
-  cpct_detail::Bins f, a;
-  cpct_detail::build_bins(g->n, g->n_det, g->n_views, G, ray, f, a);
-  const cpct_detail::Bins& b = which ? a : f;
+  HostBins h;
+  int rc = host_bins(g, cpct_detail::BIN_UNIFORM, CPCT_TILE, h);
+  if (rc) return rc;
+  const cpct_detail::BinLists& b = which ? h.adj : h.fwd;
   if (n_tiles) *n_tiles = (int)b.ptr.size() - 1;
   if (n_entries) *n_entries = (int)b.ids.size();
   if (checksum) {
@@ -518,16 +409,14 @@ extern "C" int cpct_debug_bins(const cpct_geom* g, int which, int* n_tiles, int*
   return CPCT_OK;
 }
 
-// Copy the bin list of tile `tile` (which = 0 forward, 1 adjoint) into ids
-// (capacity cap); returns the number of entries or a negative status.
+// Copy the bin list of bin `tile` (which = 0 forward, 1 adjoint; default bin
+// plan) into ids (capacity cap); returns the number of entries or a negative
+// status.
 extern "C" int cpct_debug_bin_tile(const cpct_geom* g, int which, int tile, uint32_t* ids, int cap) {
-  if (!geom_ok(g)) return CPCT_EINVAL;
-  const int G = 2 * g->n;
-  std::vector<float4> ray;
-  cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
-  cpct_detail::Bins f, a;
-  cpct_detail::build_bins(g->n, g->n_det, g->n_views, G, ray, f, a);
-  const cpct_detail::Bins& b = which ? a : f;
+  HostBins h;
+  int rc = host_bins(g, cpct_detail::BIN_UNIFORM, CPCT_TILE, h);
+  if (rc) return rc;
+  const cpct_detail::BinLists& b = which ? h.adj : h.fwd;
   if (tile < 0 || tile >= (int)b.ptr.size() - 1) return CPCT_EINVAL;
   const int cnt = b.ptr[tile + 1] - b.ptr[tile];
   for (int i = 0; i < cnt && i < cap; ++i) ids[i] = b.ids[b.ptr[tile] + i];
@@ -536,9 +425,115 @@ extern "C" int cpct_debug_bin_tile(const cpct_geom* g, int which, int tile, uint
 
 // Sample coordinate split exactly as the kernels do it (host mirror).
 extern "C" int cpct_debug_split(float k, float hi, float lo, int* fl, float* z) {
-  host_split(k, hi, lo, fl, z);
+  cpct_detail::host_split(k, hi, lo, fl, z);
   return CPCT_OK;
 }
+
+namespace {
+
+// replace a device array by a new upload of `src` (at least one element)
+template <class T>
+int replace_upload(cpct_plan* p, T** dst, const std::vector<T>& src, cudaStream_t s) {
+  T* d = nullptr;
+  const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+  if (cudaMalloc((void**)&d, bytes) != cudaSuccess) return CPCT_ENOMEM;
+  if (!src.empty() && cudaMemcpyAsync(d, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaFree(d);
+    return CPCT_ECUDA;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaFree(d);
+    return CPCT_ECUDA;
+  }
+  if (*dst) cudaFree(*dst);
+  *dst = d;
+  p->device_bytes += bytes;
+  return CPCT_OK;
+}
+
+// forward work items of the installed bin plan with `cap` samples per item
+int install_fwd_items(cpct_plan* p, int cap, cudaStream_t s) {
+  cpct_detail::BinLayout L;
+  L.bins = p->shared->fwd_bins;
+  cpct_detail::Items it;
+  cpct_detail::fwd_items(L, p->shared->fwd_ptr, cap, it);
+  int rc = replace_upload(p, &p->d_fwd_items, it.items, s);
+  if (rc) return rc;
+  p->n_fwd_items = (int)it.items.size();
+  for (int c = 0; c <= cpct_detail::kNumTileClasses; ++c) p->fwd_cls[c] = it.cls[c];
+  p->fwd_cap = cap;
+  return CPCT_OK;
+}
+
+// adjoint work items (and split list, partial tiles) with `cap` rounds per item
+int install_adj_items(cpct_plan* p, int cap, cudaStream_t s) {
+  cpct_detail::BinLayout L;
+  L.bins = p->shared->adj_bins;
+  cpct_detail::Items it;
+  cpct_detail::adj_items(L, p->shared->round_ptr, cap, it);
+  int rc = replace_upload(p, &p->d_adj_items, it.items, s);
+  if (!rc) rc = replace_upload(p, &p->d_split, it.split, s);
+  if (rc) return rc;
+  if (it.partial_elems > p->partial_elems || !p->d_partials) {
+    float2* dp = nullptr;
+    if (cudaMalloc(&dp, sizeof(float2) * (size_t)std::max(1LL, it.partial_elems)) != cudaSuccess) return CPCT_ENOMEM;
+    if (p->d_partials) cudaFree(p->d_partials);
+    p->d_partials = dp;
+  }
+  p->n_adj_items = (int)it.items.size();
+  for (int c = 0; c <= cpct_detail::kNumTileClasses; ++c) {
+    p->adj_cls[c] = it.cls[c];
+    p->split_cls[c] = it.split_cls[c];
+  }
+  p->n_split = (int)it.split.size();
+  p->partial_elems = it.partial_elems;
+  p->n_slots = (int)((it.partial_elems + 1023) / 1024);
+  p->adj_cap = cap;
+  return CPCT_OK;
+}
+
+// build and upload a bin plan for the forward gather
+int install_fwd_plan(cpct_plan* p, int kind, int tile, int cap, cudaStream_t s) {
+  cpct_detail::Samples smp;
+  cpct_detail::make_samples(p->ns, p->m, p->G, p->shared->ray, smp);
+  int W, H;
+  fwd_domain(smp, p->G, &W, &H);
+  cpct_detail::BinLayout L;
+  make_layout(smp, W, H, kind, tile, L);
+  cpct_detail::BinLists b;
+  cpct_detail::assign_fwd(smp, W, H, L, b);
+  cpct_detail::order_fwd(smp, L, b);
+  int rc = replace_upload(p, &p->d_fwd_ids, b.ids, s);
+  if (rc) return rc;
+  p->shared->fwd_bins = L.bins;
+  p->shared->fwd_ptr = b.ptr;
+  p->fwd_kind = kind;
+  p->fwd_tile = kind == cpct_detail::BIN_UNIFORM ? tile : 0;
+  return install_fwd_items(p, cap, s);
+}
+
+// build and upload a bin plan for the adjoint spread (bins, rounds)
+int install_adj_plan(cpct_plan* p, int kind, int tile, int cap, cudaStream_t s) {
+  cpct_detail::Samples smp;
+  cpct_detail::make_samples(p->ns, p->m, p->G, p->shared->ray, smp);
+  int W, H;
+  adj_domain(smp, p->G, &W, &H);
+  cpct_detail::BinLayout L;
+  make_layout(smp, W, H, kind, tile, L);
+  cpct_detail::BinLists b;
+  cpct_detail::assign_adj(smp, W, H, L, b);
+  cpct_detail::Rounds rd;
+  cpct_detail::pack_rounds(smp, L, b, rd);
+  int rc = replace_upload(p, &p->d_adj_ids, rd.ids, s);
+  if (rc) return rc;
+  p->shared->adj_bins = L.bins;
+  p->shared->round_ptr = rd.ptr;
+  p->adj_kind = kind;
+  p->adj_tile = kind == cpct_detail::BIN_UNIFORM ? tile : 0;
+  return install_adj_items(p, cap, s);
+}
+
+}  // namespace
 
 extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_t stream) {
   if (!out) return CPCT_EINVAL;
@@ -615,36 +610,13 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
     TRYC(cudaMemsetAsync(p->d_Ax, 0, hx_bytes, stream));
     TRYC(cudaMemsetAsync(p->d_Q, 0, sizeof(float2) * (size_t)m * p->ldq, stream));
     TRYC(cudaMemsetAsync(p->d_err, 0, sizeof(int), stream));
-    // bins
-    cpct_detail::Bins fb, ab;
-    std::vector<int> fa0, frb;
-    cpct_detail::build_bins(n, ns, m, p->G, ray, fb, ab, &fa0, &frb);
-    cpct_detail::Rounds rounds;
-    cpct_detail::pack_rounds(ab, p->G, fa0, frb, p->K, rounds);
-    cpct_detail::order_fwd_bins(fb, p->K, fa0, frb, CPCT_TILE + CPCT_HALO + 1);
-    p->tiles_x_fwd = fb.tiles_x;
-    p->tiles_y_fwd = fb.tiles_y;
-    p->tiles_x_adj = ab.tiles_x;
-    p->tiles_y_adj = ab.tiles_y;
-    std::vector<int4> fitems, aitems, fsplit, asplit;
-    cpct_detail::make_items(fb, kFwdItemMax, false, fitems, fsplit, nullptr);
-    std::vector<int> item_split;
-    p->fwd_cap = kFwdItemMax;
-    p->adj_cap = kAdjItemRounds;
-    cpct_detail::make_round_items(rounds, kAdjItemRounds, aitems, asplit, &p->n_slots, item_split);
+    // bins: uniform 32 x 32 tiles for both operators (cpct_plan_set_bins and
+    // the autotuner choose others)
     p->shared = new (std::nothrow) PlanShared;
     if (!p->shared) { rc = CPCT_ENOMEM; goto fail; }
-    p->shared->fwd_tile_ptr = fb.ptr;
-    p->shared->round_tile_ptr = rounds.tile_ptr;
-    p->n_fwd_items = (int)fitems.size();
-    p->n_adj_items = (int)aitems.size();
-    p->n_split = (int)asplit.size();
-    TRY(upload(al, &p->d_fwd_items, fitems, stream));
-    TRY(upload(al, &p->d_fwd_ids, fb.ids, stream));
-    TRY(upload(al, &p->d_adj_items, aitems, stream));
-    TRY(upload(al, &p->d_adj_ids, rounds.ids, stream));
-    TRY(upload(al, &p->d_split, asplit, stream));
-    TRY(al((void**)&p->d_partials, sizeof(float2) * (size_t)std::max(1, p->n_slots) * CPCT_TILE * CPCT_TILE));
+    p->shared->ray = ray;
+    TRY(install_fwd_plan(p, cpct_detail::BIN_UNIFORM, CPCT_TILE, kFwdItemMax, stream));
+    TRY(install_adj_plan(p, cpct_detail::BIN_UNIFORM, CPCT_TILE, kAdjItemRounds, stream));
     // TMA descriptor of the forward extended spectrum (viewed as float32 pairs)
     TRY(encode_hx_map(p));
     // FP32 copy of the even/odd polynomial parts
@@ -731,7 +703,7 @@ extern "C" int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream
   if ((rc = al((void**)&p->d_Hx, hx_bytes)) || (rc = al((void**)&p->d_Ax, hx_bytes)) ||
       (rc = al((void**)&p->d_H1, sizeof(float2) * (size_t)(p->n + 1) * p->n)) ||
       (rc = al((void**)&p->d_Q, sizeof(float2) * (size_t)p->m * p->ldq)) || (rc = al((void**)&p->d_err, sizeof(int))) ||
-      (rc = al((void**)&p->d_partials, sizeof(float2) * (size_t)std::max(1, p->n_slots) * CPCT_TILE * CPCT_TILE))) {
+      (rc = al((void**)&p->d_partials, sizeof(float2) * (size_t)std::max(1LL, p->partial_elems)))) {
     free_plan(p);
     return rc;
   }
@@ -750,73 +722,11 @@ extern "C" int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream
   return CPCT_OK;
 }
 
-namespace {
-
-// install forward items built with `cap` samples per item
-int install_fwd_items(cpct_plan* p, int cap, cudaStream_t s) {
-  cpct_detail::Bins b;
-  b.ptr = p->shared->fwd_tile_ptr;
-  b.tiles_x = p->tiles_x_fwd;
-  b.tiles_y = p->tiles_y_fwd;
-  std::vector<int4> items, split;
-  cpct_detail::make_items(b, cap, false, items, split, nullptr);
-  int4* d = nullptr;
-  if (cudaMalloc(&d, sizeof(int4) * std::max<size_t>(1, items.size())) != cudaSuccess) return CPCT_ENOMEM;
-  if (cudaMemcpyAsync(d, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaFree(d);
-    return CPCT_ECUDA;
-  }
-  cudaFree(p->d_fwd_items);
-  p->d_fwd_items = d;
-  p->n_fwd_items = (int)items.size();
-  p->fwd_cap = cap;
-  return CPCT_OK;
-}
-
-// install adjoint items (and split list, partial tiles) with `cap` rounds per item
-int install_adj_items(cpct_plan* p, int cap, cudaStream_t s) {
-  cpct_detail::Rounds r;
-  r.tile_ptr = p->shared->round_tile_ptr;
-  std::vector<int4> items, split;
-  std::vector<int> item_split;
-  int n_slots = 0;
-  cpct_detail::make_round_items(r, cap, items, split, &n_slots, item_split);
-  int4 *di = nullptr, *ds = nullptr;
-  float2* dp = nullptr;
-  if (cudaMalloc(&di, sizeof(int4) * std::max<size_t>(1, items.size())) != cudaSuccess ||
-      cudaMalloc(&ds, sizeof(int4) * std::max<size_t>(1, split.size())) != cudaSuccess ||
-      cudaMalloc(&dp, sizeof(float2) * (size_t)std::max(1, n_slots) * CPCT_TILE * CPCT_TILE) != cudaSuccess) {
-    if (di) cudaFree(di);
-    if (ds) cudaFree(ds);
-    return CPCT_ENOMEM;
-  }
-  cudaMemcpyAsync(di, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, s);
-  if (!split.empty()) cudaMemcpyAsync(ds, split.data(), sizeof(int4) * split.size(), cudaMemcpyHostToDevice, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaFree(di);
-    cudaFree(ds);
-    cudaFree(dp);
-    return CPCT_ECUDA;
-  }
-  cudaFree(p->d_adj_items);
-  cudaFree(p->d_split);
-  cudaFree(p->d_partials);
-  p->d_adj_items = di;
-  p->d_split = ds;
-  p->d_partials = dp;
-  p->n_adj_items = (int)items.size();
-  p->n_split = (int)split.size();
-  p->n_slots = n_slots;
-  p->adj_cap = cap;
-  return CPCT_OK;
-}
-
-}  // namespace
-
-// Autotuner of the work-item caps (how many samples a forward gather item and
-// how many rounds an adjoint spread item may hold): every candidate is timed
-// (median of `reps` launches, CUDA events on `stream`) and the fastest kept.
+// Autotuner of the bin plans and work-item sizes: for each operator the bin
+// plans (uniform 16, 32, 64 and the quadtree) are timed at the default cap,
+// then the caps of the fastest plan (gather: 256..4096 samples per item;
+// spread: 16..256 rounds per item); every candidate is the median of `reps`
+// launches (CUDA events on `stream`) and the fastest is kept.
 extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap, cudaStream_t stream) {
   if (!p || !p->shared) return CPCT_EINVAL;
   if (p->shared->refs != 1) return CPCT_EINVAL;  // tune before cloning
@@ -847,24 +757,44 @@ extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap
     std::sort(t.begin(), t.end());
     return t[t.size() / 2];
   };
+  struct Cand {
+    int kind, tile;
+  };
+  const Cand plans[] = {{cpct_detail::BIN_UNIFORM, 16}, {cpct_detail::BIN_UNIFORM, 32}, {cpct_detail::BIN_UNIFORM, 64},
+                        {cpct_detail::BIN_QUADTREE, 0}};
   int rc = CPCT_OK;
-  const int fcands[] = {256, 512, 1024, 2048, 4096};
-  const int acands[] = {16, 32, 64, 128, 256};
-  int best_f = p->fwd_cap, best_a = p->adj_cap;
-  float tf = 1e30f, ta = 1e30f;
-  for (int c : fcands) {
-    if ((rc = install_fwd_items(p, c, stream)) != CPCT_OK) break;
-    const float t = time_op(true);
-    if (t < tf) { tf = t; best_f = c; }
+  for (int op = 0; op < 2 && rc == CPCT_OK; ++op) {
+    const bool fwd = op == 0;
+    const int cap0 = fwd ? kFwdItemMax : kAdjItemRounds;
+    Cand best = plans[1];
+    float tb = 1e30f;
+    for (const Cand& c : plans) {
+      rc = fwd ? install_fwd_plan(p, c.kind, c.tile, cap0, stream) : install_adj_plan(p, c.kind, c.tile, cap0, stream);
+      if (rc != CPCT_OK) break;
+      const float t = time_op(fwd);
+      if (t < tb) {
+        tb = t;
+        best = c;
+      }
+    }
+    if (rc == CPCT_OK)
+      rc = fwd ? install_fwd_plan(p, best.kind, best.tile, cap0, stream)
+               : install_adj_plan(p, best.kind, best.tile, cap0, stream);
+    const int fc[] = {256, 512, 1024, 2048, 4096};
+    const int ac[] = {16, 32, 64, 128, 256};
+    int best_cap = cap0;
+    tb = 1e30f;
+    for (int i = 0; i < 5 && rc == CPCT_OK; ++i) {
+      const int cap = fwd ? fc[i] : ac[i];
+      if ((rc = fwd ? install_fwd_items(p, cap, stream) : install_adj_items(p, cap, stream)) != CPCT_OK) break;
+      const float t = time_op(fwd);
+      if (t < tb) {
+        tb = t;
+        best_cap = cap;
+      }
+    }
+    if (rc == CPCT_OK) rc = fwd ? install_fwd_items(p, best_cap, stream) : install_adj_items(p, best_cap, stream);
   }
-  if (rc == CPCT_OK) rc = install_fwd_items(p, best_f, stream);
-  for (int c : acands) {
-    if (rc != CPCT_OK) break;
-    if ((rc = install_adj_items(p, c, stream)) != CPCT_OK) break;
-    const float t = time_op(false);
-    if (t < ta) { ta = t; best_a = c; }
-  }
-  if (rc == CPCT_OK) rc = install_adj_items(p, best_a, stream);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(img);
@@ -885,8 +815,37 @@ extern "C" int cpct_plan_set_caps(cpct_plan* p, int fwd_cap, int adj_cap, cudaSt
   return rc;
 }
 
+// Install a bin plan for one operator (which 0 forward, 1 adjoint): kind 0
+// uniform tiles of `tile` points (16, 32, 64), kind 1 the quadtree; keeps the
+// operator's current cap.  The plan must not have clones.  Synchronous.
+extern "C" int cpct_plan_set_bins(cpct_plan* p, int which, int kind, int tile, cudaStream_t stream) {
+  if (!p || !p->shared || (which != 0 && which != 1) || !bins_args_ok(kind, tile)) return CPCT_EINVAL;
+  if (p->shared->refs != 1) return CPCT_EINVAL;
+  return which == 0 ? install_fwd_plan(p, kind, tile, p->fwd_cap, stream)
+                    : install_adj_plan(p, kind, tile, p->adj_cap, stream);
+}
+
+// The bin plans of a plan: kind (0 uniform, 1 quadtree) and tile (uniform
+// size, 0 for a quadtree) of each operator, and per operator the bins of
+// each size class (T = 16, 32, 64; arrays of 3, may be NULL).
+extern "C" int cpct_plan_bins(const cpct_plan* p, int* fwd_kind, int* fwd_tile, int* adj_kind, int* adj_tile,
+                              int* fwd_class_bins, int* adj_class_bins) {
+  if (!p || !p->shared) return CPCT_EINVAL;
+  if (fwd_kind) *fwd_kind = p->fwd_kind;
+  if (fwd_tile) *fwd_tile = p->fwd_tile;
+  if (adj_kind) *adj_kind = p->adj_kind;
+  if (adj_tile) *adj_tile = p->adj_tile;
+  for (int which = 0; which < 2; ++which) {
+    int* out = which ? adj_class_bins : fwd_class_bins;
+    if (!out) continue;
+    for (int c = 0; c < cpct_detail::kNumTileClasses; ++c) out[c] = 0;
+    for (const int4& b : which ? p->shared->adj_bins : p->shared->fwd_bins) out[cpct_detail::tile_class(b.z)]++;
+  }
+  return CPCT_OK;
+}
+
 // Work-item counts of a plan: forward gather items, adjoint spread items,
-// split heavy tiles and their partial tiles (slots).
+// split heavy bins and their partial-tile space in 32 x 32 tiles (slots).
 extern "C" int cpct_plan_work(const cpct_plan* p, int* n_fwd_items, int* n_adj_items, int* n_split, int* n_slots) {
   if (!p) return CPCT_EINVAL;
   if (n_fwd_items) *n_fwd_items = p->n_fwd_items;
@@ -896,25 +855,20 @@ extern "C" int cpct_plan_work(const cpct_plan* p, int* n_fwd_items, int* n_adj_i
   return CPCT_OK;
 }
 
-// The adjoint work items a plan of geometry g would get with `cap` rounds per
-// item (0: the default cap), built on the host exactly as cpct_plan_create
-// and cpct_plan_set_caps build them.  No GPU needed.
+// The adjoint work items a plan of geometry g gets with its default bin plan
+// and `cap` rounds per item (0: the default cap), built on the host exactly
+// as cpct_plan_create / cpct_plan_set_caps build them.  No GPU needed.
 extern "C" int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, int* n_split, int* n_slots) {
-  if (!geom_ok(g) || cap < 0) return CPCT_EINVAL;
-  const int G = 2 * g->n, K = g->n_det / 2;
-  std::vector<float4> ray;
-  cpct_detail::make_rays(g->n, g->n_det, g->n_views, g->angles, (double)G / g->n_det, ray);
-  cpct_detail::Bins f, a;
-  std::vector<int> fa0, frb;
-  cpct_detail::build_bins(g->n, g->n_det, g->n_views, G, ray, f, a, &fa0, &frb);
+  if (cap < 0) return CPCT_EINVAL;
+  HostBins h;
+  int rc = host_bins(g, cpct_detail::BIN_UNIFORM, CPCT_TILE, h);
+  if (rc) return rc;
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(a, G, fa0, frb, K, rd);
-  std::vector<int4> items, split;
-  std::vector<int> item_split;
-  int slots = 0;
-  cpct_detail::make_round_items(rd, cap > 0 ? cap : kAdjItemRounds, items, split, &slots, item_split);
-  if (n_items) *n_items = (int)items.size();
-  if (n_split) *n_split = (int)split.size();
-  if (n_slots) *n_slots = slots;
+  cpct_detail::pack_rounds(h.s, h.al, h.adj, rd);
+  cpct_detail::Items it;
+  cpct_detail::adj_items(h.al, rd.ptr, cap > 0 ? cap : kAdjItemRounds, it);
+  if (n_items) *n_items = (int)it.items.size();
+  if (n_split) *n_split = (int)it.split.size();
+  if (n_slots) *n_slots = (int)((it.partial_elems + 1023) / 1024);
   return CPCT_OK;
 }

@@ -138,21 +138,28 @@ struct FwdInterpArgs {
   float2* Q;
   int* err;
   const int* skip;  // the launch does nothing while *skip != 0 (may be null)
-  int G, ldq, ldh, tiles_x;
+  int G, ldq, ldh;
   KBPoly poly;
 };
 
-constexpr int kWinR = CPCT_TILE + CPCT_HALO;      // 37 rows
-constexpr int kWinC = CPCT_TILE + CPCT_HALO + 1;  // 38 complex columns (304 B rows)
-// buffer stride: a TMA tensor copy into shared memory must start on a 128-byte
-// boundary, so each window buffer is padded to a multiple of 128 bytes
-constexpr int kWinStride = ((kWinR * kWinC * (int)sizeof(float2) + 127) / 128) * 128 / (int)sizeof(float2);
-static_assert((kWinStride * sizeof(float2)) % 128 == 0, "window buffers must be 128-byte aligned");
+// window of a T x T bin: T + 5 rows of T + 6 complex values (the 6x6
+// footprints of every sample whose first point lies in the bin)
+template <int T>
+struct Win {
+  static constexpr int R = T + CPCT_HALO;
+  static constexpr int C = T + CPCT_HALO + 1;
+  // buffer stride: a TMA tensor copy into shared memory must start on a
+  // 128-byte boundary, so each window buffer is padded to a multiple of 128 bytes
+  static constexpr int stride = ((R * C * (int)sizeof(float2) + 127) / 128) * 128 / (int)sizeof(float2);
+  static constexpr size_t smem = 2 * (size_t)stride * sizeof(float2);
+};
 
 // interpolate one polar sample from the staged window (or, if the bin does not
 // hold it -- never expected -- from global memory, recording the mismatch)
+template <int T>
 __device__ __forceinline__ void interp_sample(const FwdInterpArgs& a, const float2* win, int C0, int R0, uint32_t id,
                                               float4 r) {
+  constexpr int kWinC = Win<T>::C;
   const int j = (int)(id >> 16), k = (int)(id & 0xffffu);
   int fu, fv;
   float zu, zv;
@@ -164,7 +171,7 @@ __device__ __forceinline__ void interp_sample(const FwdInterpArgs& a, const floa
   kb_weights(a.poly, zv, wv);
   const int ar = a0 - C0, br = fv - R0;
   float2 acc = make_float2(0.f, 0.f);
-  if ((unsigned)ar < (unsigned)CPCT_TILE && (unsigned)br < (unsigned)CPCT_TILE) {
+  if ((unsigned)ar < (unsigned)T && (unsigned)br < (unsigned)T) {
 #pragma unroll
     for (int rr = 0; rr < CPCT_W; ++rr) {
       const float2* row = win + (br + rr) * kWinC + ar;
@@ -194,18 +201,22 @@ __device__ __forceinline__ void interp_sample(const FwdInterpArgs& a, const floa
   a.Q[(size_t)j * a.ldq + k] = acc;
 }
 
-// Persistent CTAs walk the work items (tile, sample range) round robin; the
-// 37x38 grid window of the next item is copied by TMA into the second buffer
-// while the current one is interpolated, and the next item's first sample id
-// and ray are prefetched into registers.
-// bins hold ~130 samples on average (1024 at most): 128 threads per CTA keep
-// most threads busy on every bin
+// Persistent CTAs walk the work items (bin, sample range) of one bin size T
+// round robin; the (T + 5) x (T + 6) grid window of the next item is copied
+// by TMA into the second buffer while the current one is interpolated, and
+// the next item's first sample id and ray are prefetched into registers.
+// 32 x 32 bins hold ~130 samples on average (1024 at most): 128 threads per
+// CTA keep most threads busy on every bin
 constexpr int kInterpThreads = 128;
 
+template <int T>
 __global__ void __launch_bounds__(kInterpThreads)
     k_fwd_interp(const __grid_constant__ CUtensorMap tmap, const FwdInterpArgs a, int n_items) {
   if (a.skip && *a.skip) return;
-  __shared__ __align__(128) float2 win[2][kWinStride];
+  constexpr int kWinStride = Win<T>::stride;
+  extern __shared__ __align__(128) unsigned char win_raw[];
+  // TMA destinations start on a 128-byte boundary (the launch adds 128 bytes)
+  float2* win0 = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(win_raw) + 127) & ~(uintptr_t)127);
   __shared__ __align__(8) uint64_t bar[2];
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -216,9 +227,9 @@ __global__ void __launch_bounds__(kInterpThreads)
   __syncthreads();
   auto issue = [&](int item, int buf) {
     const int4 itn = a.items[item];
-    const int c0 = (itn.x % a.tiles_x) * CPCT_TILE, r0 = (itn.x / a.tiles_x) * CPCT_TILE;
-    mbar_arrive_expect_tx(&bar[buf], (uint32_t)(kWinR * kWinC * sizeof(float2)));
-    tma_load_2d(win[buf], &tmap, 2 * c0, r0, &bar[buf]);
+    const int c0 = itn.x & 0xffff, r0 = itn.x >> 16;
+    mbar_arrive_expect_tx(&bar[buf], (uint32_t)(Win<T>::R * Win<T>::C * sizeof(float2)));
+    tma_load_2d(win0 + buf * kWinStride, &tmap, 2 * c0, r0, &bar[buf]);
   };
   int item = blockIdx.x;
   if (tid == 0 && item < n_items) issue(item, 0);
@@ -260,11 +271,12 @@ __global__ void __launch_bounds__(kInterpThreads)
       }
       return;
     }
-    const int C0 = (it.x % a.tiles_x) * CPCT_TILE, R0 = (it.x / a.tiles_x) * CPCT_TILE;
-    if (pid != 0xffffffffu) interp_sample(a, win[cur], C0, R0, pid, pray);
+    const int C0 = it.x & 0xffff, R0 = it.x >> 16;
+    const float2* wcur = win0 + cur * kWinStride;
+    if (pid != 0xffffffffu) interp_sample<T>(a, wcur, C0, R0, pid, pray);
     for (int idx = it.y + tid + (int)blockDim.x; idx < it.z; idx += blockDim.x) {
       const uint32_t id = a.ids[idx];
-      interp_sample(a, win[cur], C0, R0, id, a.ray[id >> 16]);
+      interp_sample<T>(a, wcur, C0, R0, id, a.ray[id >> 16]);
     }
     pid = nid;
     pray = nray;
@@ -407,12 +419,18 @@ struct AdjSpreadArgs {
   float2* partials;
   int* err;
   const int* skip;  // the launch does nothing while *skip != 0 (may be null)
-  int G, ldq, ldh, tiles_x, ext_rows;
+  int G, ldq, ldh, ext_rows;
   KBPoly poly;
 };
 
-constexpr int kRRows = CPCT_TILE + 2 * CPCT_HALO;  // 42: tile rows plus a 5-cell halo on both sides
-constexpr int kRLd = kRRows + 2;                    // 44 complex per row (bank classes use this stride)
+// accumulator of a T x T bin: T + 10 rows (a 5-cell halo on both sides) of
+// T + 12 complex values (the row pitch the bank classes of the rounds use;
+// 44 for T = 32)
+template <int T>
+struct Acc {
+  static constexpr int rows = T + 2 * CPCT_HALO;
+  static constexpr int ld = rows + 2;
+};
 
 // One warp per work item (a run of conflict-free rounds of one tile).  In a
 // round, lane l holds one sample (or none); the 6x6 footprints of the round's
@@ -421,12 +439,14 @@ constexpr int kRLd = kRRows + 2;                    // 44 complex per row (bank 
 // cells with plain shared-memory loads and stores: no atomics, no conflicts.
 // Rounds are applied in their fixed plan order, hence every output element
 // receives its contributions in the same order on every run.
+template <int T>
 __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
   if (a.skip && *a.skip) return;
+  constexpr int kRRows = Acc<T>::rows, kRLd = Acc<T>::ld;
   __shared__ __align__(16) float2 acc[kRRows * kRLd];
   const int lane = threadIdx.x;
   const int4 it = a.items[blockIdx.x];
-  const int TC = (it.x % a.tiles_x) * CPCT_TILE, TR = (it.x / a.tiles_x) * CPCT_TILE;
+  const int TC = it.x & 0xffff, TR = it.x >> 16;
   for (int i = lane; i < kRRows * kRLd; i += 32) acc[i] = make_float2(0.f, 0.f);
   // software pipeline: ids two rounds ahead, sample data one round ahead
   uint32_t id0 = it.y < it.z ? a.ids[(size_t)it.y * 32 + lane] : 0xffffffffu;
@@ -453,7 +473,7 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
       split_coord(k, ray0.x, ray0.y, fu, zu);
       split_coord(k, ray0.z, ray0.w, fv, zv);
       const int ar = ((fu - 2) & (a.G - 1)) - TC + CPCT_HALO, br = fv - TR + CPCT_HALO;
-      if ((unsigned)ar <= (unsigned)(CPCT_TILE + CPCT_HALO - 1) && (unsigned)br <= (unsigned)(CPCT_TILE + CPCT_HALO - 1)) {
+      if ((unsigned)ar <= (unsigned)(T + CPCT_HALO - 1) && (unsigned)br <= (unsigned)(T + CPCT_HALO - 1)) {
         float wu[CPCT_W], wv[CPCT_W];
         kb_weights(a.poly, zu, wu);
         kb_weights(a.poly, zv, wv);
@@ -488,46 +508,51 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
   }
   __syncwarp();
   if (it.w < 0) {
-    for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32) {
-      const int rr = i / CPCT_TILE, cc = i % CPCT_TILE;
+    for (int i = lane; i < T * T; i += 32) {
+      const int rr = i / T, cc = i % T;
       const int gr = TR + rr, gc = TC + cc;
       if (gr < a.ext_rows && gc < a.ldh)
         a.Ax[(size_t)gr * a.ldh + gc] = acc[(rr + CPCT_HALO) * kRLd + cc + CPCT_HALO];
     }
   } else {
-    float2* dst = a.partials + (size_t)it.w * CPCT_TILE * CPCT_TILE;
-    for (int i = lane; i < CPCT_TILE * CPCT_TILE; i += 32)
-      dst[i] = acc[(i / CPCT_TILE + CPCT_HALO) * kRLd + i % CPCT_TILE + CPCT_HALO];
+    float2* dst = a.partials + (size_t)it.w;
+    for (int i = lane; i < T * T; i += 32) dst[i] = acc[(i / T + CPCT_HALO) * kRLd + i % T + CPCT_HALO];
   }
 }
 
-// 7. fixed-order sum of the partial tiles of split tiles (slot order q = 0, 1, ...)
-__global__ void __launch_bounds__(CPCT_TILE * CPCT_TILE)
+// 7. fixed-order sum of the partial tiles of a split T x T bin (piece order
+// q = 0, 1, ...); one block per split bin
+template <int T>
+constexpr int reduce_threads() { return T * T < 1024 ? T * T : 1024; }
+
+template <int T>
+__global__ void __launch_bounds__(reduce_threads<T>())
     k_adj_reduce(const int4* __restrict__ split, const float2* __restrict__ partials, float2* __restrict__ Ax,
-                 int tiles_x, int ldh, int ext_rows, const int* __restrict__ skip) {
+                 int ldh, int ext_rows, const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int4 sp = split[blockIdx.x];
-  const int TC = (sp.x % tiles_x) * CPCT_TILE, TR = (sp.x / tiles_x) * CPCT_TILE;
-  const int i = threadIdx.x;
-  const float2* src = partials + (size_t)sp.y * CPCT_TILE * CPCT_TILE + i;
-  constexpr size_t S = CPCT_TILE * CPCT_TILE;
-  // 16 independent loads in flight, summed in slot order
-  float2 sum = make_float2(0.f, 0.f);
-  int q = 0;
-  for (; q + 16 <= sp.z; q += 16) {
-    float2 v[16];
+  const int TC = sp.x & 0xffff, TR = sp.x >> 16;
+  constexpr size_t S = (size_t)T * T;
+  for (int i = threadIdx.x; i < T * T; i += reduce_threads<T>()) {
+    const float2* src = partials + (size_t)sp.y + i;
+    // 16 independent loads in flight, summed in piece order
+    float2 sum = make_float2(0.f, 0.f);
+    int q = 0;
+    for (; q + 16 <= sp.z; q += 16) {
+      float2 v[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = src[(size_t)(q + k) * S];
+      for (int k = 0; k < 16; ++k) v[k] = src[(size_t)(q + k) * S];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) sum = cadd(sum, v[k]);
+      for (int k = 0; k < 16; ++k) sum = cadd(sum, v[k]);
+    }
+    for (; q + 4 <= sp.z; q += 4) {
+      const float2 v0 = src[(q + 0) * S], v1 = src[(q + 1) * S], v2 = src[(q + 2) * S], v3 = src[(q + 3) * S];
+      sum = cadd(cadd(cadd(cadd(sum, v0), v1), v2), v3);
+    }
+    for (; q < sp.z; ++q) sum = cadd(sum, src[q * S]);
+    const int gr = TR + i / T, gc = TC + i % T;
+    if (gr < ext_rows && gc < ldh) Ax[(size_t)gr * ldh + gc] = sum;
   }
-  for (; q + 4 <= sp.z; q += 4) {
-    const float2 v0 = src[(q + 0) * S], v1 = src[(q + 1) * S], v2 = src[(q + 2) * S], v3 = src[(q + 3) * S];
-    sum = cadd(cadd(cadd(cadd(sum, v0), v1), v2), v3);
-  }
-  for (; q < sp.z; ++q) sum = cadd(sum, src[q * S]);
-  const int gr = TR + i / CPCT_TILE, gc = TC + i % CPCT_TILE;
-  if (gr < ext_rows && gc < ldh) Ax[(size_t)gr * ldh + gc] = sum;
 }
 
 // ---------------------------------------------------------------------------
@@ -717,10 +742,38 @@ void launch_adj_G(cpct_plan* p, float* img, const int* skip, cudaStream_t s) {
     default: return CPCT_EINVAL;    \
   }
 
+constexpr int kBinClasses = 3;  // bins of 16, 32 and 64 grid points
+
+template <int T>
+int set_attr_interp() {
+  if (cudaFuncSetAttribute(k_fwd_interp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Win<T>::smem + 128) !=
+      cudaSuccess)
+    return CPCT_ECUDA;
+  return CPCT_OK;
+}
+
+template <int T>
+void launch_fwd_interp(cpct_plan* p, const FwdInterpArgs& a, int n_items, cudaStream_t s) {
+  const int c = T == 16 ? 0 : T == 32 ? 1 : 2;
+  if (p->fwd_interp_grid[c] <= 0) {
+    // persistent grid: every CTA resident at once
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_interp<T>, kInterpThreads, Win<T>::smem + 128);
+    p->fwd_interp_grid[c] = std::max(1, sms * std::max(1, per_sm));
+  }
+  const int grid = std::min(n_items, p->fwd_interp_grid[c]);
+  k_fwd_interp<T><<<grid, kInterpThreads, Win<T>::smem + 128, s>>>(p->tmap_Hx[c], a, n_items);
+}
+
 }  // namespace
 
 int cpct_radon_setup_attributes(int logG, int logNs) {
-  int rc = CPCT_OK;
+  int rc = set_attr_interp<16>();
+  if (!rc) rc = set_attr_interp<32>();
+  if (!rc) rc = set_attr_interp<64>();
+  if (rc) return rc;
 #define SETG(L) rc = set_attr_G<L>()
 #define SETN(L) rc = set_attr_Ns<L>()
   CPCT_DISPATCH_G(logG, SETG);
@@ -740,7 +793,6 @@ int launch_fwd_impl(cpct_plan* p, const float* d_img, float* d_sino, bool cplx, 
   CPCT_DISPATCH_G(p->logG, FG);
 #undef FG
   FwdInterpArgs a;
-  a.items = p->d_fwd_items;
   a.ids = p->d_fwd_ids;
   a.ray = p->d_ray;
   a.Hx = p->d_Hx;
@@ -749,21 +801,18 @@ int launch_fwd_impl(cpct_plan* p, const float* d_img, float* d_sino, bool cplx, 
   a.G = p->G;
   a.ldq = p->ldq;
   a.ldh = p->ldh;
-  a.tiles_x = p->tiles_x_fwd;
   a.poly = p->poly;
   a.skip = skip;
   if (p->n_fwd_items > 0) {
     cpct_prof_begin(p, KID_FWD_INTERP, s);
-    if (p->fwd_interp_grid <= 0) {
-      // persistent grid: every CTA resident at once
-      int dev = 0, sms = 1, per_sm = 1;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_interp, kInterpThreads, 0);
-      p->fwd_interp_grid = std::max(1, sms * std::max(1, per_sm));
+    for (int c = 0; c < kBinClasses; ++c) {
+      const int n_items = p->fwd_cls[c + 1] - p->fwd_cls[c];
+      if (n_items <= 0) continue;
+      a.items = p->d_fwd_items + p->fwd_cls[c];
+      if (c == 0) launch_fwd_interp<16>(p, a, n_items, s);
+      else if (c == 1) launch_fwd_interp<32>(p, a, n_items, s);
+      else launch_fwd_interp<64>(p, a, n_items, s);
     }
-    const int grid = std::min(p->n_fwd_items, p->fwd_interp_grid);
-    k_fwd_interp<<<grid, kInterpThreads, 0, s>>>(p->tmap_Hx, a, p->n_fwd_items);
     cpct_prof_end(p, KID_FWD_INTERP, s);
   }
 #define FN(L) launch_fwd_Ns<L>(p, d_sino, cplx, skip, s)
@@ -780,7 +829,6 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
   CPCT_DISPATCH_NS(p->logNs, AN);
 #undef AN
   AdjSpreadArgs a;
-  a.items = p->d_adj_items;
   a.ids = p->d_adj_ids;
   a.ray = p->d_ray;
   a.Qt = p->d_Q;
@@ -790,7 +838,6 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
   a.G = p->G;
   a.ldq = p->ldq;
   a.ldh = p->ldh;
-  a.tiles_x = p->tiles_x_adj;
   a.ext_rows = p->ext_rows;
   a.poly = p->poly;
   a.skip = skip;
@@ -798,13 +845,29 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
   // reduce reads it, so the partial tiles need no clearing between calls
   if (p->n_adj_items > 0) {
     cpct_prof_begin(p, KID_ADJ_SPREAD, s);
-    k_adj_spread<<<p->n_adj_items, 32, 0, s>>>(a);
+    for (int c = 0; c < kBinClasses; ++c) {
+      const int n_items = p->adj_cls[c + 1] - p->adj_cls[c];
+      if (n_items <= 0) continue;
+      a.items = p->d_adj_items + p->adj_cls[c];
+      if (c == 0) k_adj_spread<16><<<n_items, 32, 0, s>>>(a);
+      else if (c == 1) k_adj_spread<32><<<n_items, 32, 0, s>>>(a);
+      else k_adj_spread<64><<<n_items, 32, 0, s>>>(a);
+    }
     cpct_prof_end(p, KID_ADJ_SPREAD, s);
   }
   if (p->n_split > 0) {
     cpct_prof_begin(p, KID_ADJ_REDUCE, s);
-    k_adj_reduce<<<p->n_split, CPCT_TILE * CPCT_TILE, 0, s>>>(p->d_split, partials, p->d_Ax, p->tiles_x_adj, p->ldh,
-                                                             p->ext_rows, skip);
+    for (int c = 0; c < kBinClasses; ++c) {
+      const int n = p->split_cls[c + 1] - p->split_cls[c];
+      if (n <= 0) continue;
+      const int4* sp = p->d_split + p->split_cls[c];
+      if (c == 0)
+        k_adj_reduce<16><<<n, reduce_threads<16>(), 0, s>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+      else if (c == 1)
+        k_adj_reduce<32><<<n, reduce_threads<32>(), 0, s>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+      else
+        k_adj_reduce<64><<<n, reduce_threads<64>(), 0, s>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+    }
     cpct_prof_end(p, KID_ADJ_REDUCE, s);
   }
 #define AG(L) launch_adj_G<L>(p, d_img, skip, s)
@@ -853,7 +916,7 @@ constexpr int kNoAllocMaxDevices = 64;
 // Every device that loads this library holds this array until the process
 // exits.  Host code must not use its name as a device address: the device
 // address is looked up per device with cudaGetSymbolAddress below.
-static __device__ __align__(256) float2 g_noalloc_partials[(size_t)kNoAllocMaxSlots * CPCT_TILE * CPCT_TILE];
+static __device__ __align__(256) float2 g_noalloc_partials[(size_t)kNoAllocMaxSlots * 1024];
 
 std::mutex g_noalloc_mutex;
 float2* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
@@ -884,7 +947,8 @@ float2* noalloc_scratch(int* status) {
 extern "C" int radon_adj_noalloc(cpct_plan* p, const float* d_sino, float* d_img, cudaStream_t s) {
   if (!p || !d_sino || !d_img) return CPCT_EINVAL;
   if ((reinterpret_cast<uintptr_t>(d_sino) & 15u) || (reinterpret_cast<uintptr_t>(d_img) & 15u)) return CPCT_EINVAL;
-  if (p->n_slots > kNoAllocMaxSlots) return CPCT_EINVAL;  // geometry needs more partial tiles than the array holds
+  // the plan's split bins need more partial-tile space than the array holds
+  if (p->partial_elems > (long long)kNoAllocMaxSlots * 1024) return CPCT_EINVAL;
   int status = CPCT_OK;
   float2* partials = noalloc_scratch(&status);
   if (!partials) return status;

@@ -198,8 +198,9 @@ def pc_radiographs(n_views: int, n_rows: int, n_det: int, rng: np.random.Generat
     transport-of-intensity term of a propagation distance c = dz / k;
     lap is the 5-point detector Laplacian over (row, column).  Flats F, F'
     carry a per-pixel gain, dark D an offset; with ``noise`` the frames get
-    beam fluctuations per frame (0.3%), shot noise and 3 dead columns (gain
-    0 in both flats); with ``counts`` they are rounded to uint16.
+    beam fluctuations per frame (0.3%), shot noise and (detectors of 8 or
+    more columns) 3 dead columns (gain 0 in both flats); with ``counts``
+    they are rounded to uint16.
 
     Returns dict(near, far (M, rows, Ns), flat_near, flat_far, dark
     (rows, Ns), pc_term (M, rows, Ns) = T c lap(phi) (noise-free value of
@@ -228,7 +229,7 @@ def pc_radiographs(n_views: int, n_rows: int, n_det: int, rng: np.random.Generat
     dark = rng.uniform(95.0, 105.0, (n_rows, n_det))
     gain_n = rng.uniform(0.8, 1.2, (n_rows, n_det))
     gain_f = rng.uniform(0.8, 1.2, (n_rows, n_det))
-    if noise:
+    if noise and n_det >= 8:
         dead = rng.choice(n_det, size=3, replace=False)
         gain_n[:, dead] = 0.0
         gain_f[:, dead] = 0.0

@@ -154,3 +154,27 @@ def test_adjoint_work_items_and_noalloc_bound(cpct):
     assert cpct.debug_adj_items(2048, 2048, 1024) == d
     small = cpct.debug_adj_items(64, 64, 10)
     assert small["n_split"] == 0 and small["n_slots"] == 0
+
+
+@pytest.mark.parametrize("n,ns,m", [(64, 64, 10), (128, 128, 180), (256, 256, 64), (64, 128, 33), (1024, 1024, 128)])
+def test_bin_plans_valid(cpct, n, ns, m):
+    """Every bin plan (uniform 16 / 32 / 64 and the paper's quadtree) holds
+    its invariants: disjoint aligned bins, forward lists = the samples by
+    first point, adjoint lists = exactly the samples whose footprint touches
+    the bin (checked by 2D prefix sums), valid conflict-free rounds."""
+    for kind, tile in [("uniform", 16), ("uniform", 32), ("uniform", 64), ("quadtree", 0)]:
+        d = cpct.debug_binplan(n, ns, m, kind, tile)
+        assert d["valid"] == 1, (kind, tile, d)
+        if kind == "uniform":
+            assert d["adj_class_bins"][{16: 0, 32: 1, 64: 2}[tile]] == d["adj_bins"]
+
+
+def test_quadtree_splits_where_samples_are_dense(cpct):
+    """The quadtree divides the bins of largest samples x points: at 1024^2 /
+    128 views its leaves are 16 points wide around the origin (where every
+    ray passes) and 64 wide where few samples land, with every size present."""
+    d = cpct.debug_binplan(1024, 1024, 128, "quadtree")
+    assert all(c > 0 for c in d["adj_class_bins"]), d
+    u16 = cpct.debug_binplan(1024, 1024, 128, "uniform", 16)
+    u64 = cpct.debug_binplan(1024, 1024, 128, "uniform", 64)
+    assert u64["adj_bins"] < d["adj_bins"] < u16["adj_bins"]

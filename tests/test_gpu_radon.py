@@ -194,6 +194,64 @@ def test_complex_variants(torch_cuda, n, ns, m):
     assert rel < 3e-8
 
 
+@pytest.mark.parametrize("kind,tile", [("uniform", 16), ("uniform", 64), ("quadtree", 0)])
+@pytest.mark.parametrize("n,ns,m", [(128, 128, 180), (256, 256, 64), (64, 128, 33)])
+def test_bin_plans_parity(torch_cuda, kind, tile, n, ns, m):
+    """Every bin plan gives the operator pair of the FP64 oracle (1e-5), also
+    with caps small enough to split bins of every size into several work
+    items (partial tiles summed by the reduce kernel), bitwise reproducibly."""
+    torch = torch_cuda
+    rng = np.random.default_rng(500 + n + m)
+    img = rng.standard_normal((n, n))
+    sino = rng.standard_normal((m, ns))
+    geo = nufft.GridGeometry(n, ns, nufft.default_angles(m))
+    y_ref = nufft.radon_grid(img, geo)
+    z_ref = nufft.radon_grid_adj(sino, geo)
+    p = _plan(n, ns, m)
+    p.set_bins("fwd", kind, tile)
+    p.set_bins("adj", kind, tile)
+    b = p.bins()
+    assert b["fwd"][0] == kind and b["adj"][0] == kind
+    for caps in [(0, 0), (64, 4)]:
+        if caps != (0, 0):
+            p.set_caps(*caps)
+            assert p.work()["n_split"] > 0
+        y, z = _run(torch, p, img, sino)
+        y2, z2 = _run(torch, p, img, sino)
+        ef, ea = _rel(y, y_ref), _rel(z, z_ref)
+        print(f"{kind} {tile} n={n} ns={ns} m={m} caps={caps}: fwd {ef:.2e} adj {ea:.2e} bins {b}")
+        assert ef < TOL and ea < TOL
+        assert np.array_equal(y, y2) and np.array_equal(z, z2)
+
+
+def test_tuned_bin_plan_full_size(torch_cuda):
+    """The autotuner's choice (bin plan and caps per operator) at 1024^2 /
+    512 views: sampled rays of the forward against the FP64 oracle, the
+    adjoint against the default plan's (the same operator up to FP32
+    summation order)."""
+    torch = torch_cuda
+    n, m = 1024, 512
+    img = synth.phantom("paper_1024")
+    p = _plan(n, n, m)
+    q = _plan(n, n, m)
+    from paper_1009_1380_gb300 import cpct
+    caps = cpct.tune(p, reps=3)
+    print("tuned", caps, p.bins())
+    x = torch.from_numpy(img).cuda()
+    y = p.fwd(x).cpu().numpy().astype(np.float64)
+    geo = nufft.GridGeometry(n, n, nufft.default_angles(m))
+    rays = np.array([0, 1, 100, 255, 256, 400, 511])
+    e = _rel(y[rays], nufft.radon_grid(img.astype(np.float64), geo, rays))
+    w = torch.randn((m, n), device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    z = p.adj(w).cpu().numpy().astype(np.float64)
+    z0 = q.adj(w).cpu().numpy().astype(np.float64)
+    ea = _rel(z, z0)
+    torch.cuda.synchronize()
+    p.sync()
+    print(f"tuned plan: sampled rays {e:.2e}, adjoint vs default plan {ea:.2e}")
+    assert e < TOL and ea < 1e-6
+
+
 def test_edge_cases(torch_cuda):
     torch = torch_cuda
     p = _plan(64, 64, 10)
