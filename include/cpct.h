@@ -232,6 +232,9 @@ int cpct_plan_set_caps(cpct_plan* plan, int fwd_cap, int adj_cap, cudaStream_t s
  * synchronous.  The default is uniform 32 for both.  Results do not depend
  * on the bin plan beyond FP32 rounding (each bin sums its samples in its
  * own order); for a given plan they are bitwise reproducible.
+ * Changing the bins of a plan that a captured batch (cpct_batch_create)
+ * uses leaves that batch's graph with freed bin lists: install bin plans
+ * (and caps) before building batches.
  * cpct_plan_bins reports the installed plans (kind, tile, 0 for a quadtree)
  * and, per operator, the number of bins of each size (16, 32, 64; host
  * arrays of 3, may be NULL). */

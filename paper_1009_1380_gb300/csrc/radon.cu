@@ -804,10 +804,14 @@ int launch_fwd_impl(cpct_plan* p, const float* d_img, float* d_sino, bool cplx, 
   a.poly = p->poly;
   a.skip = skip;
   if (p->n_fwd_items > 0) {
+    // one profiling bracket around the launches of every bin size (the
+    // launch counter counts each of them)
     cpct_prof_begin(p, KID_FWD_INTERP, s);
+    int launched = 0;
     for (int c = 0; c < kBinClasses; ++c) {
       const int n_items = p->fwd_cls[c + 1] - p->fwd_cls[c];
       if (n_items <= 0) continue;
+      if (launched++) p->launches++;
       a.items = p->d_fwd_items + p->fwd_cls[c];
       if (c == 0) launch_fwd_interp<16>(p, a, n_items, s);
       else if (c == 1) launch_fwd_interp<32>(p, a, n_items, s);
@@ -845,9 +849,11 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
   // reduce reads it, so the partial tiles need no clearing between calls
   if (p->n_adj_items > 0) {
     cpct_prof_begin(p, KID_ADJ_SPREAD, s);
+    int launched = 0;
     for (int c = 0; c < kBinClasses; ++c) {
       const int n_items = p->adj_cls[c + 1] - p->adj_cls[c];
       if (n_items <= 0) continue;
+      if (launched++) p->launches++;
       a.items = p->d_adj_items + p->adj_cls[c];
       if (c == 0) k_adj_spread<16><<<n_items, 32, 0, s>>>(a);
       else if (c == 1) k_adj_spread<32><<<n_items, 32, 0, s>>>(a);
@@ -857,9 +863,11 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
   }
   if (p->n_split > 0) {
     cpct_prof_begin(p, KID_ADJ_REDUCE, s);
+    int launched = 0;
     for (int c = 0; c < kBinClasses; ++c) {
       const int n = p->split_cls[c + 1] - p->split_cls[c];
       if (n <= 0) continue;
+      if (launched++) p->launches++;
       const int4* sp = p->d_split + p->split_cls[c];
       if (c == 0)
         k_adj_reduce<16><<<n, reduce_threads<16>(), 0, s>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
