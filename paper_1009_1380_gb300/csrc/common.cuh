@@ -97,6 +97,10 @@ struct cpct_plan {
   CUtensorMap tmap_Hx[3];   // TMA windows of 16, 32 and 64 point bins
   size_t device_bytes;
   int fwd_interp_grid[3];   // persistent grids of the forward gather per class (0 = not yet sized)
+  // plans with bins of several sizes run the per-size launches concurrently:
+  // two side streams fork from the launch stream and join it again
+  cudaStream_t side[2];
+  cudaEvent_t ev_fork, ev_join[2];
   int fwd_cap, adj_cap;     // work-item caps (samples / rounds per item), tunable
   struct PlanShared* shared;  // read-only geometry shared with clones (refcounted)
   long long launches;       // kernels launched by this plan's operators
@@ -122,6 +126,10 @@ struct PlanShared {
 void cpct_prof_begin(cpct_plan* p, int kid, cudaStream_t s);
 void cpct_prof_end(cpct_plan* p, int kid, cudaStream_t s);
 void cpct_prof_free(cpct_plan* p);
+
+// side streams and events of a plan (created with the plan and each clone)
+int cpct_plan_streams_create(cpct_plan* p);
+void cpct_plan_streams_destroy(cpct_plan* p);
 
 // ---------------------------------------------------------------------------
 // small device helpers

@@ -171,6 +171,7 @@ EncodeTiledFn get_encode_fn() {
 void free_plan(cpct_plan* p) {
   if (!p) return;
   cpct_prof_free(p);
+  cpct_plan_streams_destroy(p);
   // per-plan workspaces
   void* own[] = {p->d_Hx, p->d_Ax, p->d_H1, p->d_Q, p->d_partials, p->d_stage_img, p->d_stage_sino, p->d_err};
   for (void* q : own)
@@ -577,6 +578,7 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
   {
     int rca = cpct_radon_setup_attributes(p->logG, p->logNs);
     if (rca != CPCT_OK) { rc = rca; goto fail; }
+    TRY(cpct_plan_streams_create(p));
     // geometry
     std::vector<float4> ray;
     cpct_detail::make_rays(n, ns, m, g->angles, p->scale, ray);
@@ -690,6 +692,13 @@ extern "C" int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream
   if (!p) return CPCT_ENOMEM;
   std::memcpy(p, src, sizeof(*p));
   // fresh per-plan state; the geometry pointers stay shared
+  p->side[0] = p->side[1] = nullptr;
+  p->ev_fork = p->ev_join[0] = p->ev_join[1] = nullptr;
+  if (cpct_plan_streams_create(p) != CPCT_OK) {
+    cpct_plan_streams_destroy(p);
+    delete p;
+    return CPCT_ECUDA;
+  }
   p->d_Hx = p->d_Ax = p->d_H1 = p->d_Q = p->d_partials = nullptr;
   p->d_stage_img = p->d_stage_sino = nullptr;
   p->d_err = nullptr;
@@ -871,4 +880,24 @@ extern "C" int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, i
   if (n_split) *n_split = (int)it.split.size();
   if (n_slots) *n_slots = (int)((it.partial_elems + 1023) / 1024);
   return CPCT_OK;
+}
+
+int cpct_plan_streams_create(cpct_plan* p) {
+  for (int i = 0; i < 2; ++i)
+    if (cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking) != cudaSuccess) return CPCT_ECUDA;
+  if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) return CPCT_ECUDA;
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming) != cudaSuccess) return CPCT_ECUDA;
+  return CPCT_OK;
+}
+
+void cpct_plan_streams_destroy(cpct_plan* p) {
+  for (int i = 0; i < 2; ++i) {
+    if (p->side[i]) cudaStreamDestroy(p->side[i]);
+    if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
+    p->side[i] = nullptr;
+    p->ev_join[i] = nullptr;
+  }
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  p->ev_fork = nullptr;
 }

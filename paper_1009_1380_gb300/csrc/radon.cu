@@ -804,19 +804,28 @@ int launch_fwd_impl(cpct_plan* p, const float* d_img, float* d_sino, bool cplx, 
   a.poly = p->poly;
   a.skip = skip;
   if (p->n_fwd_items > 0) {
-    // one profiling bracket around the launches of every bin size (the
-    // launch counter counts each of them)
+    // one profiling bracket around the launches of every bin size; with
+    // bins of several sizes the per-size launches run concurrently on side
+    // streams forked from `s` (they read disjoint item lists and write
+    // disjoint polar samples)
     cpct_prof_begin(p, KID_FWD_INTERP, s);
-    int launched = 0;
-    for (int c = 0; c < kBinClasses; ++c) {
-      const int n_items = p->fwd_cls[c + 1] - p->fwd_cls[c];
-      if (n_items <= 0) continue;
-      if (launched++) p->launches++;
+    int cls[kBinClasses], nc = 0;
+    for (int c = 0; c < kBinClasses; ++c)
+      if (p->fwd_cls[c + 1] > p->fwd_cls[c]) cls[nc++] = c;
+    p->launches += nc - 1;
+    if (nc > 1) cudaEventRecord(p->ev_fork, s);
+    for (int i = 0; i < nc; ++i) {
+      const int c = cls[i];
+      cudaStream_t si = i == 0 ? s : p->side[i - 1];
+      if (i > 0) cudaStreamWaitEvent(si, p->ev_fork, 0);
       a.items = p->d_fwd_items + p->fwd_cls[c];
-      if (c == 0) launch_fwd_interp<16>(p, a, n_items, s);
-      else if (c == 1) launch_fwd_interp<32>(p, a, n_items, s);
-      else launch_fwd_interp<64>(p, a, n_items, s);
+      const int n_items = p->fwd_cls[c + 1] - p->fwd_cls[c];
+      if (c == 0) launch_fwd_interp<16>(p, a, n_items, si);
+      else if (c == 1) launch_fwd_interp<32>(p, a, n_items, si);
+      else launch_fwd_interp<64>(p, a, n_items, si);
+      if (i > 0) cudaEventRecord(p->ev_join[i - 1], si);
     }
+    for (int i = 1; i < nc; ++i) cudaStreamWaitEvent(s, p->ev_join[i - 1], 0);
     cpct_prof_end(p, KID_FWD_INTERP, s);
   }
 #define FN(L) launch_fwd_Ns<L>(p, d_sino, cplx, skip, s)
@@ -847,36 +856,50 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
   a.skip = skip;
   // every partial tile is written in full by its work item before the
   // reduce reads it, so the partial tiles need no clearing between calls
-  if (p->n_adj_items > 0) {
+  int cls[kBinClasses], nc = 0;
+  for (int c = 0; c < kBinClasses; ++c)
+    if (p->adj_cls[c + 1] > p->adj_cls[c]) cls[nc++] = c;
+  auto spread = [&](int c, cudaStream_t si) {
+    a.items = p->d_adj_items + p->adj_cls[c];
+    const int n_items = p->adj_cls[c + 1] - p->adj_cls[c];
+    if (c == 0) k_adj_spread<16><<<n_items, 32, 0, si>>>(a);
+    else if (c == 1) k_adj_spread<32><<<n_items, 32, 0, si>>>(a);
+    else k_adj_spread<64><<<n_items, 32, 0, si>>>(a);
+  };
+  auto reduce = [&](int c, cudaStream_t si) {
+    const int n = p->split_cls[c + 1] - p->split_cls[c];
+    if (n <= 0) return false;
+    const int4* sp = p->d_split + p->split_cls[c];
+    if (c == 0) k_adj_reduce<16><<<n, reduce_threads<16>(), 0, si>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+    else if (c == 1) k_adj_reduce<32><<<n, reduce_threads<32>(), 0, si>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+    else k_adj_reduce<64><<<n, reduce_threads<64>(), 0, si>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+    return true;
+  };
+  if (nc == 1) {
     cpct_prof_begin(p, KID_ADJ_SPREAD, s);
-    int launched = 0;
-    for (int c = 0; c < kBinClasses; ++c) {
-      const int n_items = p->adj_cls[c + 1] - p->adj_cls[c];
-      if (n_items <= 0) continue;
-      if (launched++) p->launches++;
-      a.items = p->d_adj_items + p->adj_cls[c];
-      if (c == 0) k_adj_spread<16><<<n_items, 32, 0, s>>>(a);
-      else if (c == 1) k_adj_spread<32><<<n_items, 32, 0, s>>>(a);
-      else k_adj_spread<64><<<n_items, 32, 0, s>>>(a);
-    }
+    spread(cls[0], s);
     cpct_prof_end(p, KID_ADJ_SPREAD, s);
-  }
-  if (p->n_split > 0) {
-    cpct_prof_begin(p, KID_ADJ_REDUCE, s);
-    int launched = 0;
-    for (int c = 0; c < kBinClasses; ++c) {
-      const int n = p->split_cls[c + 1] - p->split_cls[c];
-      if (n <= 0) continue;
-      if (launched++) p->launches++;
-      const int4* sp = p->d_split + p->split_cls[c];
-      if (c == 0)
-        k_adj_reduce<16><<<n, reduce_threads<16>(), 0, s>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
-      else if (c == 1)
-        k_adj_reduce<32><<<n, reduce_threads<32>(), 0, s>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
-      else
-        k_adj_reduce<64><<<n, reduce_threads<64>(), 0, s>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+    if (p->n_split > 0) {
+      cpct_prof_begin(p, KID_ADJ_REDUCE, s);
+      reduce(cls[0], s);
+      cpct_prof_end(p, KID_ADJ_REDUCE, s);
     }
-    cpct_prof_end(p, KID_ADJ_REDUCE, s);
+  } else if (nc > 1) {
+    // bins of several sizes: each size's spread and reduce run as one chain
+    // on its own stream (disjoint output regions and partial tiles); the
+    // bracket of k_adj_spread covers the whole fork..join, reduce included
+    cpct_prof_begin(p, KID_ADJ_SPREAD, s);
+    cudaEventRecord(p->ev_fork, s);
+    for (int i = 0; i < nc; ++i) {
+      cudaStream_t si = i == 0 ? s : p->side[i - 1];
+      if (i > 0) cudaStreamWaitEvent(si, p->ev_fork, 0);
+      spread(cls[i], si);
+      if (i > 0) p->launches++;
+      if (reduce(cls[i], si)) p->launches++;
+      if (i > 0) cudaEventRecord(p->ev_join[i - 1], si);
+    }
+    for (int i = 1; i < nc; ++i) cudaStreamWaitEvent(s, p->ev_join[i - 1], 0);
+    cpct_prof_end(p, KID_ADJ_SPREAD, s);
   }
 #define AG(L) launch_adj_G<L>(p, d_img, skip, s)
   CPCT_DISPATCH_G(p->logG, AG);

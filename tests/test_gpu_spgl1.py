@@ -144,6 +144,35 @@ def test_spgl1_batched_equals_single(torch_cuda):
         assert torch.equal(x1, xs[i]), f"slice {i} differs between batched and single solves"
 
 
+def test_spgl1_with_quadtree_bins(torch_cuda):
+    """A solve whose plans use the quadtree bins (several bin sizes, their
+    launches forked onto side streams inside the captured tick graph)
+    reaches the root, and a batched solve equals the single ones bitwise."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    n, m = 128, 90
+    probs = [_problem(n, m, seed=s) for s in (31, 32)]
+    plans = []
+    for _ in probs:
+        p = cpct.Plan(n, n, m)
+        p.set_bins("fwd", "quadtree")
+        p.set_bins("adj", "quadtree")
+        assert sum(1 for c in p.bins()["adj"][2] if c > 0) > 1
+        plans.append(p)
+    bs = [torch.from_numpy(pb[2].astype(np.float32)).cuda() for pb in probs]
+    sig = [pb[3] for pb in probs]
+    xs, infos = cpct.spgl1_batched(plans, bs, sig)
+    for i, (geo, x_true, b, sigma) in enumerate(probs):
+        x1, i1 = cpct.spgl1(plans[i], bs[i], sig[i])
+        print("quadtree solve", i1)
+        assert i1["status"] == 1
+        assert torch.equal(x1, xs[i])
+        A, _ = _ops(n, m, geo)
+        bf = ring.ring_filter(b.astype(np.float32).astype(np.float64))
+        rg = np.linalg.norm(A(x1.cpu().numpy().astype(np.float64)) - bf)
+        assert abs(rg - sigma) <= 2e-4 * np.linalg.norm(bf)
+
+
 def test_spgl1_warm_start_and_basis_pursuit_flag(torch_cuda):
     torch = torch_cuda
     from paper_1009_1380_gb300 import cpct
