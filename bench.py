@@ -515,7 +515,8 @@ def spgl1_bench(args, torch, cpct, synth):
 def bins_bench(torch, cpct, synth, runs=10):
     """Bin plans of the gridding kernels compared (the paper's quadtree
     against uniform tiles of 16, 32 and 64 points, each with heavy bins split
-    into work items): gather and spread (+ reduce) device time per launch,
+    into work items; adjoint rounds of 16 lanes, and of 32 for uniform 32):
+    gather and spread (+ reduce) device time per launch,
     CUDA events around each kernel, L2 flushed before every pair, at the
     2048^2 / 1024-view workload and at the largest and smallest view counts
     of the batched 1024^2 workload."""
@@ -528,9 +529,11 @@ def bins_bench(torch, cpct, synth, runs=10):
         y = torch.empty((m, n), device="cuda")
         z = torch.empty((n, n), device="cuda")
         res = {}
-        for kind, tile in [("uniform", 16), ("uniform", 32), ("uniform", 64), ("quadtree", 0)]:
+        for kind, tile, lanes in [("uniform", 16, 16), ("uniform", 32, 16), ("uniform", 32, 32), ("uniform", 64, 16),
+                                  ("quadtree", 0, 16)]:
             plan.set_bins("fwd", kind, tile)
             plan.set_bins("adj", kind, tile)
+            plan.set_rounds(lanes)
             for _ in range(3):
                 plan.fwd(img, y)
                 plan.adj(y, z)
@@ -547,7 +550,7 @@ def bins_bench(torch, cpct, synth, runs=10):
                 pair.append(sum(v[0] for v in pr.values()) * 1e3)
             plan.profile_enable(0)
             b = plan.bins()
-            res[kind if kind == "quadtree" else f"uniform{tile}"] = {
+            res[(kind if kind == "quadtree" else f"uniform{tile}") + ("" if lanes == 16 else f"_rounds{lanes}")] = {
                 "gather_us": float(np.median(g)), "spread_us": float(np.median(sp)), "pair_us": float(np.median(pair)),
                 "adj_bins_16_32_64": b["adj"][2], "work": plan.work()}
         out[name] = res

@@ -241,6 +241,15 @@ int cpct_plan_set_caps(cpct_plan* plan, int fwd_cap, int adj_cap, cudaStream_t s
 #define CPCT_BINS_UNIFORM 0
 #define CPCT_BINS_QUADTREE 1
 int cpct_plan_set_bins(cpct_plan* plan, int which, int kind, int tile, cudaStream_t stream);
+
+/* Width of the adjoint spread's conflict-free rounds (default 32): 16 puts
+ * one sample per 64-bit shared-memory bank class in the lower half-warp, so
+ * each accumulator access is served in one pass; 32 puts up to two per class
+ * in both halves (two passes).  cpct_plan_set_rounds re-packs the installed
+ * adjoint bins (the plan must not have clones; synchronous);
+ * cpct_plan_rounds returns the width (or CPCT_EINVAL for a NULL plan). */
+int cpct_plan_set_rounds(cpct_plan* plan, int lanes, cudaStream_t stream);
+int cpct_plan_rounds(const cpct_plan* plan);
 int cpct_plan_bins(const cpct_plan* plan, int* fwd_kind, int* fwd_tile, int* adj_kind, int* adj_tile,
                    int* fwd_class_bins, int* adj_class_bins);
 
@@ -252,7 +261,8 @@ int cpct_plan_work(const cpct_plan* plan, int* n_fwd_items, int* n_adj_items, in
 
 /* Autotuner of the bin plans and work-item sizes: for each operator times
  * the bin plans uniform 16, 32, 64 and the quadtree at the default cap, keeps
- * the fastest, then times its caps (256..4096 samples per gather item,
+ * the fastest (for the adjoint then the faster round width, 16 or 32), then
+ * times its caps (256..4096 samples per gather item,
  * 16..256 rounds per spread item) and keeps the fastest (median of `reps`
  * launches each, CUDA events on `stream`); reports the chosen caps
  * (cpct_plan_bins reports the bin plans).  The plan must not have clones

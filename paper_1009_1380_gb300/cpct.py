@@ -68,6 +68,8 @@ def lib():
             getattr(L, name).argtypes = [vp, vp, vp, vp]
         L.cpct_plan_set_caps.argtypes = [vp, i, i, vp]
         L.cpct_plan_set_bins.argtypes = [vp, i, i, i, vp]
+        L.cpct_plan_set_rounds.argtypes = [vp, i, vp]
+        L.cpct_plan_rounds.argtypes = [vp]
         L.cpct_plan_bins.argtypes = [vp] + [ctypes.POINTER(i)] * 4 + [vp, vp]
         L.cpct_debug_binplan.argtypes = [ctypes.POINTER(Geom), i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp,
                                          ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -231,6 +233,13 @@ class Plan:
         w = {"fwd": 0, "adj": 1}[which]
         k = {"uniform": BINS_UNIFORM, "quadtree": BINS_QUADTREE}[kind]
         check(lib().cpct_plan_set_bins(self._h, w, k, int(tile), _stream(self._torch, stream)), "cpct_plan_set_bins")
+
+    def set_rounds(self, lanes, stream=None):
+        """Width of the adjoint's conflict-free rounds: 16 or 32."""
+        check(lib().cpct_plan_set_rounds(self._h, int(lanes), _stream(self._torch, stream)), "cpct_plan_set_rounds")
+
+    def rounds(self):
+        return int(lib().cpct_plan_rounds(self._h))
 
     def bins(self):
         """Installed bin plans: {'fwd': (kind, tile, bins per class), 'adj': ...}."""

@@ -282,8 +282,9 @@ void order_fwd(const Samples& s, const BinLayout& L, BinLists& b) {
   }
 }
 
-void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, Rounds& out) {
+void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, int lanes, Rounds& out) {
   const int nt = (int)adj.ptr.size() - 1;
+  out.lanes = lanes;
   out.ptr.assign(nt + 1, 0);
   out.ids.clear();
   constexpr int kMaxRows = 64 + 2 * CPCT_HALO;
@@ -312,8 +313,8 @@ void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, Roun
       size_t r = first_open;
       for (; r < rounds.size(); ++r) {
         R& rd = rounds[r];
-        if (rd.count == 32) continue;
-        if ((rd.lanes >> cls) & (rd.lanes >> (cls + 16)) & 1u) continue;
+        if (rd.count == lanes) continue;
+        if (lanes == 16 ? ((rd.lanes >> cls) & 1u) : ((rd.lanes >> cls) & (rd.lanes >> (cls + 16)) & 1u)) continue;
         bool clash = false;
         for (int q = 0; q < CPCT_W && !clash; ++q)
           clash = ((rd.occ[br + q][0] & fm[0]) | (rd.occ[br + q][1] & fm[1])) != 0;
@@ -335,9 +336,9 @@ void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, Roun
         rd.occ[br + q][1] |= fm[1];
       }
       lanes_of[r][lane] = id;
-      while (first_open < rounds.size() && rounds[first_open].count == 32) ++first_open;
+      while (first_open < rounds.size() && rounds[first_open].count == lanes) ++first_open;
     }
-    for (auto& l : lanes_of) out.ids.insert(out.ids.end(), l.begin(), l.end());
+    for (auto& l : lanes_of) out.ids.insert(out.ids.end(), l.begin(), l.begin() + lanes);
     out.ptr[t + 1] = out.ptr[t] + (int)rounds.size();
   }
 }

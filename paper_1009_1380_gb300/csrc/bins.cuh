@@ -70,14 +70,20 @@ void assign_adj(const Samples& s, int W, int H, const BinLayout& L, BinLists& ou
 // first cells fall in distinct 64-bit bank pairs of the staged window
 void order_fwd(const Samples& s, const BinLayout& L, BinLists& b);
 
-// adjoint: rounds of <= 32 samples with pairwise disjoint footprints in the
-// bin's (T + 10) x (T + 12) accumulator, lane = bank class of the first cell
+// adjoint: rounds of samples with pairwise disjoint footprints in the bin's
+// (T + 10) x (T + 13) accumulator; the 64-bit bank pair of a sample's first
+// cell is its class (the odd pitch shifts the classes of consecutive rows by
+// 13).  32-lane rounds hold at most two samples per class (lanes c and
+// c + 16: a 64-bit access of the warp is served in two half-warp passes);
+// 16-lane rounds hold at most one (lane c), so that only the lower half-warp
+// accesses shared memory and every access is served in one pass.
 struct Rounds {
+  int lanes = 32;               // samples per round (16 or 32)
   std::vector<int> ptr;         // bins + 1, in rounds
-  std::vector<uint32_t> ids;    // 32 per round, 0xffffffff = empty lane
+  std::vector<uint32_t> ids;    // `lanes` per round, 0xffffffff = empty lane
 };
-inline int round_pitch(int T) { return T + 2 * CPCT_HALO + 2; }
-void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, Rounds& out);
+inline int round_pitch(int T) { return T + 2 * CPCT_HALO + 3; }
+void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, int lanes, Rounds& out);
 
 // work items, grouped by tile class and longest first within a class
 struct Items {

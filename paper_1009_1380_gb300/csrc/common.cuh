@@ -90,6 +90,7 @@ struct cpct_plan {
   int split_cls[4];
   int4* d_split;            // (origin, partial offset, pieces, T), grouped by class
   int fwd_kind, fwd_tile, adj_kind, adj_tile;  // bin plans (kind 0 uniform, 1 quadtree)
+  int round_lanes;          // samples per adjoint round (16 or 32)
   // staging for the host-buffer entry points
   float* d_stage_img;
   float* d_stage_sino;

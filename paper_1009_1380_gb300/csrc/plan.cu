@@ -26,6 +26,7 @@ namespace {
 constexpr int kPolyDeg = 9;            // Chebyshev interpolation degree per tap
 constexpr int kFwdItemMax = 1024;      // samples per forward gather work item
 constexpr int kAdjItemRounds = 64;     // conflict-free rounds per adjoint spread work item
+constexpr int kRoundLanes = 32;        // samples per adjoint round (32; 16 is a tuner option)
 
 // ---------------------------------------------------------------------------
 // FP64 device builders (kernel table, deapodization, twiddles)
@@ -328,8 +329,8 @@ int check_plan(const HostBins& h, const cpct_detail::Rounds& rd, int* n_packed) 
     std::vector<uint32_t> got;
     for (int r = rd.ptr[t]; r < rd.ptr[t + 1] && ok; ++r) {
       std::vector<int> cells;
-      for (int l = 0; l < 32; ++l) {
-        const uint32_t id = rd.ids[(size_t)r * 32 + l];
+      for (int l = 0; l < rd.lanes; ++l) {
+        const uint32_t id = rd.ids[(size_t)r * rd.lanes + l];
         if (id == 0xffffffffu) continue;
         got.push_back(id);
         const size_t i = (size_t)(id >> 16) * (s.K + 1) + (id & 0xffffu);
@@ -363,9 +364,9 @@ extern "C" int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packe
   int rc = host_bins(g, cpct_detail::BIN_UNIFORM, CPCT_TILE, h);
   if (rc) return rc;
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(h.s, h.al, h.adj, rd);
+  cpct_detail::pack_rounds(h.s, h.al, h.adj, kRoundLanes, rd);
   const int ok = check_plan(h, rd, n_packed);
-  if (n_rounds) *n_rounds = (int)(rd.ids.size() / 32);
+  if (n_rounds) *n_rounds = (int)(rd.ids.size() / rd.lanes);
   if (valid) *valid = ok;
   return CPCT_OK;
 }
@@ -380,7 +381,7 @@ extern "C" int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int* n
   int rc = host_bins(g, kind, tile, h);
   if (rc) return rc;
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(h.s, h.al, h.adj, rd);
+  cpct_detail::pack_rounds(h.s, h.al, h.adj, kRoundLanes, rd);
   if (valid) *valid = check_plan(h, rd, nullptr);
   if (n_fwd_bins) *n_fwd_bins = (int)h.fl.bins.size();
   if (n_adj_bins) *n_adj_bins = (int)h.al.bins.size();
@@ -388,7 +389,7 @@ extern "C" int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int* n
     for (int c = 0; c < cpct_detail::kNumTileClasses; ++c) adj_class_bins[c] = 0;
     for (const int4& b : h.al.bins) adj_class_bins[cpct_detail::tile_class(b.z)]++;
   }
-  if (n_rounds) *n_rounds = (int)(rd.ids.size() / 32);
+  if (n_rounds) *n_rounds = (int)(rd.ids.size() / rd.lanes);
   return CPCT_OK;
 }
 
@@ -514,7 +515,8 @@ int install_fwd_plan(cpct_plan* p, int kind, int tile, int cap, cudaStream_t s) 
 }
 
 // build and upload a bin plan for the adjoint spread (bins, rounds)
-int install_adj_plan(cpct_plan* p, int kind, int tile, int cap, cudaStream_t s) {
+int install_adj_plan(cpct_plan* p, int kind, int tile, int cap, cudaStream_t s, int lanes = 0) {
+  if (lanes == 0) lanes = p->round_lanes ? p->round_lanes : kRoundLanes;
   cpct_detail::Samples smp;
   cpct_detail::make_samples(p->ns, p->m, p->G, p->shared->ray, smp);
   int W, H;
@@ -524,9 +526,10 @@ int install_adj_plan(cpct_plan* p, int kind, int tile, int cap, cudaStream_t s) 
   cpct_detail::BinLists b;
   cpct_detail::assign_adj(smp, W, H, L, b);
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(smp, L, b, rd);
+  cpct_detail::pack_rounds(smp, L, b, lanes, rd);
   int rc = replace_upload(p, &p->d_adj_ids, rd.ids, s);
   if (rc) return rc;
+  p->round_lanes = lanes;
   p->shared->adj_bins = L.bins;
   p->shared->round_ptr = rd.ptr;
   p->adj_kind = kind;
@@ -789,6 +792,13 @@ extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap
     if (rc == CPCT_OK)
       rc = fwd ? install_fwd_plan(p, best.kind, best.tile, cap0, stream)
                : install_adj_plan(p, best.kind, best.tile, cap0, stream);
+    if (!fwd && rc == CPCT_OK) {
+      // round width of the adjoint: the other width, kept if faster
+      const int other = p->round_lanes == 16 ? 32 : 16;
+      const float t_cur = time_op(false);
+      if ((rc = install_adj_plan(p, best.kind, best.tile, cap0, stream, other)) == CPCT_OK && time_op(false) >= t_cur)
+        rc = install_adj_plan(p, best.kind, best.tile, cap0, stream, other == 16 ? 32 : 16);
+    }
     const int fc[] = {256, 512, 1024, 2048, 4096};
     const int ac[] = {16, 32, 64, 128, 256};
     int best_cap = cap0;
@@ -834,6 +844,17 @@ extern "C" int cpct_plan_set_bins(cpct_plan* p, int which, int kind, int tile, c
                     : install_adj_plan(p, kind, tile, p->adj_cap, stream);
 }
 
+// Width of the adjoint's conflict-free rounds: 16 (one sample per bank
+// class, the lower half-warp only) or 32 (two per class); re-packs the
+// installed adjoint bins.  The plan must not have clones.  Synchronous.
+extern "C" int cpct_plan_set_rounds(cpct_plan* p, int lanes, cudaStream_t stream) {
+  if (!p || !p->shared || (lanes != 16 && lanes != 32)) return CPCT_EINVAL;
+  if (p->shared->refs != 1) return CPCT_EINVAL;
+  return install_adj_plan(p, p->adj_kind, p->adj_tile ? p->adj_tile : CPCT_TILE, p->adj_cap, stream, lanes);
+}
+
+extern "C" int cpct_plan_rounds(const cpct_plan* p) { return p ? p->round_lanes : CPCT_EINVAL; }
+
 // The bin plans of a plan: kind (0 uniform, 1 quadtree) and tile (uniform
 // size, 0 for a quadtree) of each operator, and per operator the bins of
 // each size class (T = 16, 32, 64; arrays of 3, may be NULL).
@@ -873,7 +894,7 @@ extern "C" int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, i
   int rc = host_bins(g, cpct_detail::BIN_UNIFORM, CPCT_TILE, h);
   if (rc) return rc;
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(h.s, h.al, h.adj, rd);
+  cpct_detail::pack_rounds(h.s, h.al, h.adj, kRoundLanes, rd);
   cpct_detail::Items it;
   cpct_detail::adj_items(h.al, rd.ptr, cap > 0 ? cap : kAdjItemRounds, it);
   if (n_items) *n_items = (int)it.items.size();

@@ -420,16 +420,17 @@ struct AdjSpreadArgs {
   int* err;
   const int* skip;  // the launch does nothing while *skip != 0 (may be null)
   int G, ldq, ldh, ext_rows;
+  int lanes;  // samples per round: 16 (lanes 0..15) or 32
   KBPoly poly;
 };
 
 // accumulator of a T x T bin: T + 10 rows (a 5-cell halo on both sides) of
-// T + 12 complex values (the row pitch the bank classes of the rounds use;
-// 44 for T = 32)
+// T + 13 complex values (the odd row pitch the bank classes of the rounds
+// use; 45 for T = 32)
 template <int T>
 struct Acc {
   static constexpr int rows = T + 2 * CPCT_HALO;
-  static constexpr int ld = rows + 2;
+  static constexpr int ld = rows + 3;
 };
 
 // One warp per work item (a run of conflict-free rounds of one tile).  In a
@@ -448,9 +449,12 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
   const int4 it = a.items[blockIdx.x];
   const int TC = it.x & 0xffff, TR = it.x >> 16;
   for (int i = lane; i < kRRows * kRLd; i += 32) acc[i] = make_float2(0.f, 0.f);
-  // software pipeline: ids two rounds ahead, sample data one round ahead
-  uint32_t id0 = it.y < it.z ? a.ids[(size_t)it.y * 32 + lane] : 0xffffffffu;
-  uint32_t id1 = it.y + 1 < it.z ? a.ids[(size_t)(it.y + 1) * 32 + lane] : 0xffffffffu;
+  // software pipeline: ids two rounds ahead, sample data one round ahead;
+  // with 16-lane rounds the upper half-warp holds no sample
+  const int L = a.lanes;
+  const bool act = lane < L;
+  uint32_t id0 = act && it.y < it.z ? a.ids[(size_t)it.y * L + lane] : 0xffffffffu;
+  uint32_t id1 = act && it.y + 1 < it.z ? a.ids[(size_t)(it.y + 1) * L + lane] : 0xffffffffu;
   float4 ray0 = make_float4(0.f, 0.f, 0.f, 0.f);
   float2 val0 = make_float2(0.f, 0.f);
   if (id0 != 0xffffffffu) {
@@ -459,7 +463,7 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
   }
   __syncwarp();
   for (int r = it.y; r < it.z; ++r) {
-    const uint32_t id2 = r + 2 < it.z ? a.ids[(size_t)(r + 2) * 32 + lane] : 0xffffffffu;
+    const uint32_t id2 = act && r + 2 < it.z ? a.ids[(size_t)(r + 2) * L + lane] : 0xffffffffu;
     float4 ray1 = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 val1 = make_float2(0.f, 0.f);
     if (id1 != 0xffffffffu) {
@@ -852,6 +856,7 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
   a.ldq = p->ldq;
   a.ldh = p->ldh;
   a.ext_rows = p->ext_rows;
+  a.lanes = p->round_lanes;
   a.poly = p->poly;
   a.skip = skip;
   // every partial tile is written in full by its work item before the

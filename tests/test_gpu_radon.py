@@ -194,9 +194,10 @@ def test_complex_variants(torch_cuda, n, ns, m):
     assert rel < 3e-8
 
 
-@pytest.mark.parametrize("kind,tile", [("uniform", 16), ("uniform", 64), ("quadtree", 0)])
+@pytest.mark.parametrize("kind,tile,lanes", [("uniform", 16, 16), ("uniform", 64, 16), ("quadtree", 0, 16),
+                                             ("uniform", 32, 32), ("quadtree", 0, 32)])
 @pytest.mark.parametrize("n,ns,m", [(128, 128, 180), (256, 256, 64), (64, 128, 33)])
-def test_bin_plans_parity(torch_cuda, kind, tile, n, ns, m):
+def test_bin_plans_parity(torch_cuda, kind, tile, lanes, n, ns, m):
     """Every bin plan gives the operator pair of the FP64 oracle (1e-5), also
     with caps small enough to split bins of every size into several work
     items (partial tiles summed by the reduce kernel), bitwise reproducibly."""
@@ -210,6 +211,8 @@ def test_bin_plans_parity(torch_cuda, kind, tile, n, ns, m):
     p = _plan(n, ns, m)
     p.set_bins("fwd", kind, tile)
     p.set_bins("adj", kind, tile)
+    p.set_rounds(lanes)
+    assert p.rounds() == lanes
     b = p.bins()
     assert b["fwd"][0] == kind and b["adj"][0] == kind
     for caps in [(0, 0), (64, 4)]:
