@@ -558,6 +558,19 @@ def bins_bench(torch, cpct, synth, runs=10):
     return out
 
 
+def sweep_bench():
+    """Few-view / low-dose sweep (the paper's Conclusions): relative L2
+    error against the true image of the filtered back-projection, SPGL1 and
+    its analysis-l1 variant on 256^2 slices for 32..256 views at 1% and 4%
+    noise (4 slices per point)."""
+    from paper_1009_1380_gb300 import sweep
+    t0 = time.perf_counter()
+    pts = sweep.run(n=256, views=(32, 64, 128, 256), noises=(0.01, 0.04), count=4)
+    return {"points": pts, "seconds": time.perf_counter() - t0,
+            "note": "noise = standard deviation / sinogram maximum (dose ~ 1 / noise^2); errors against the true "
+                    "phase-contrast image (FBP, SPGL1) and object (analysis-l1 variant)"}
+
+
 def warm_bench(args, torch, cpct, synth):
     """The learned warm start, bounded (C5 shape: 512^2 slices, 90 views):
     generate training pairs (FBP input, cold SPGL1 target), train the U-Net
@@ -815,6 +828,8 @@ def run_ours(args, rank, world, local_rank):
         out["denoiser"] = denoiser_bench(args, torch, cpct)
     if world == 1 and args.warm_pairs > 0:
         out["warm"] = warm_bench(args, torch, cpct, synth)
+    if world == 1 and not args.no_sweep:
+        out["sweep"] = sweep_bench()
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -833,10 +848,11 @@ def main():
     ap.add_argument("--spgl1-iters", type=int, default=0, help="override the SPGL1 iteration cap (0: 300)")
     ap.add_argument("--unet-batch", type=int, default=32, help="images of the denoiser workload (0: skip)")
     ap.add_argument("--no-bins", action="store_true", help="skip the bin-plan comparison")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the few-view / low-dose sweep")
     ap.add_argument("--warm-pairs", type=int, default=1024, help="training pairs of the warm-start run (0: skip)")
     ap.add_argument("--warm-eval", type=int, default=256, help="fresh slices of the warm-start run")
     ap.add_argument("--warm-epochs", type=int, default=8, help="training epochs of the warm-start run")
-    ap.add_argument("--only", default="", choices=["", "spgl1", "batch", "unet", "warm", "bins"],
+    ap.add_argument("--only", default="", choices=["", "spgl1", "batch", "unet", "warm", "bins", "sweep"],
                     help="run one secondary workload alone")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -844,7 +860,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.only in ("spgl1", "batch", "unet", "warm", "bins"):
+    elif args.only in ("spgl1", "batch", "unet", "warm", "bins", "sweep"):
         import torch
         from paper_1009_1380_gb300 import build as b
         b.build()
@@ -858,6 +874,8 @@ def main():
             print(json.dumps(warm_bench(args, torch, cpct, synth)), flush=True)
         elif args.only == "bins":
             print(json.dumps(bins_bench(torch, cpct, synth)), flush=True)
+        elif args.only == "sweep":
+            print(json.dumps(sweep_bench()), flush=True)
         else:
             print(json.dumps(batch_bench(args, torch, cpct, synth)), flush=True)
     else:
