@@ -567,8 +567,9 @@ def sweep_bench():
     t0 = time.perf_counter()
     pts = sweep.run(n=256, views=(32, 64, 128, 256), noises=(0.01, 0.04), count=4)
     return {"points": pts, "seconds": time.perf_counter() - t0,
-            "note": "noise = standard deviation / sinogram maximum (dose ~ 1 / noise^2); errors against the true "
-                    "phase-contrast image (FBP, SPGL1) and object (analysis-l1 variant)"}
+            "note": "noise = standard deviation / sinogram maximum (dose ~ 1 / noise^2); phase-contrast data: FBP and "
+                    "SPGL1 errors against the true phase-contrast image; absorption data of the same objects: FBP "
+                    "and the analysis-l1 variant against the object"}
 
 
 def warm_bench(args, torch, cpct, synth):
