@@ -64,8 +64,8 @@ def source_digest() -> str:
 
 
 # files that define the Radon operator kernels (kernels, their headers, and
-# the plan builder whose tables and bins they read)
-RADON_FILES = ("radon.cu", "plan.cu", "common.cuh", "fft.cuh")
+# the plan and bin-plan builders whose tables and bins they read)
+RADON_FILES = ("radon.cu", "plan.cu", "bins.cu", "bins.cuh", "common.cuh", "fft.cuh")
 
 
 def radon_digest() -> str:

@@ -3,9 +3,10 @@
 Pins: the synthesis operator C (row prefix sums) and its adjoint C^T match
 oracle/synthesis.py to FP32 summation accuracy, satisfy the adjoint identity
 and work in place.  SPGL1 with CPCT_SPGL1_SYNTH_DH (the operator F R C)
-follows the oracle's solve of the same problem over its first 30 iterations
-(misfit and ||z||_1 within 1e-2, z within 5e-2): the device composes C and
-C^T with the operators as the oracle does.  The variant itself converges
+follows the oracle's solve of the fixed-radius subproblem over 30
+iterations (misfit and ||z||_1 within 1e-3, z within 1e-2) and takes the
+oracle's first Newton update of the root-finding solve: the device composes
+C and C^T with the operators as the oracle does.  The variant itself converges
 slowly: on this 64^2 / 64-view problem the FP64 oracle is still at
 ||r|| = 77 for sigma = 65 after 4000 iterations (C scales the problem's
 conditioning with the image width), so no root parity is claimed.
@@ -62,7 +63,7 @@ def test_synthesis_operator_parity(torch_cuda, n):
 def test_synthesis_spgl1_follows_oracle(torch_cuda):
     torch = torch_cuda
     from paper_1009_1380_gb300 import cpct
-    n, m, iters = 64, 64, 30
+    n, m, iters, tau = 64, 64, 30, 35.0
     rng = np.random.default_rng(17)
     u_true, _ = synth.ellipse_phantom(n, 6, rng, axes_range=(200.0, 500.0))
     geo = nufft.GridGeometry(n, n, nufft.default_angles(m))
@@ -72,22 +73,28 @@ def test_synthesis_spgl1_follows_oracle(torch_cuda):
     bf = ring.ring_filter(b32.astype(np.float64))
     A = lambda zz: ring.ring_filter(nufft.radon_grid(synthesis.synth_dh(zz.reshape(n, n)), geo))
     At = lambda r: synthesis.synth_dh_adj(nufft.radon_grid_adj(ring.ring_filter(r.reshape(m, n)), geo))
-    zo, io = spgl1.spgl1(A, At, bf, sigma, opts=spgl1.Options(opt_tol=1e-5, max_iter=iters))
     p = cpct.Plan(n, n, m)
-    zg, ig = cpct.spgl1(p, torch.from_numpy(b32).cuda(), sigma,
-                        opts=cpct.make_opts(opt_tol=1e-5, max_iter=iters, synth_dh=True))
+    bd = torch.from_numpy(b32).cuda()
+    # (1) the fixed-radius subproblem, 30 iterations: no Newton decisions, so
+    # the trajectory is stable under FP32 operators (a relative perturbation
+    # of 1e-6 in b moves the oracle's 30th iterate by 3e-5)
+    zo, io = spgl1.lasso(A, At, bf, tau, opts=spgl1.Options(opt_tol=1e-5, max_iter=iters))
+    zg, ig = cpct.spgl1(p, bd, sigma, opts=cpct.make_opts(opt_tol=1e-5, max_iter=iters, synth_dh=True, lasso_tau=tau))
     zg = zg.cpu().numpy().astype(np.float64)
     print("oracle", io.status, io.iterations, io.rnorm, io.xnorm1)
     print("gpu   ", ig)
-    # both stop at the iteration cap, far from the root of this badly
-    # conditioned problem (C's conditioning grows with the image width), so
-    # the iterates are compared after the same number of steps: FP32
-    # operators flip some line-search and Newton-update decisions, which
-    # moves the iterate by a few percent (measured 1.8% in ||z||_1); a
-    # wiring error of C or C^T in the solve moves it far more
     assert io.iterations == iters and ig["iterations"] == iters
-    assert abs(ig["rnorm"] - io.rnorm) <= 1e-2 * io.rnorm
-    assert abs(ig["xnorm1"] - io.xnorm1) <= 5e-2 * io.xnorm1
-    # the device iterate under the oracle's operator
-    assert abs(np.linalg.norm(A(zg) - bf) - io.rnorm) <= 1e-2 * io.rnorm
-    assert _rel(zg, zo) < 1e-1
+    assert abs(ig["rnorm"] - io.rnorm) <= 1e-3 * io.rnorm
+    assert abs(ig["xnorm1"] - io.xnorm1) <= 1e-3 * io.xnorm1
+    assert abs(np.linalg.norm(A(zg) - bf) - io.rnorm) <= 1e-3 * io.rnorm
+    assert _rel(zg, zo) < 1e-2
+    # (2) the root-finding solve: its first Newton update of tau (from the
+    # zero iterate) is the oracle's.  Later updates fire when the objective's
+    # relative change crosses 1e-4, which on this slowly converging problem
+    # it approaches within 10% (oracle iteration 7), so the solves are not
+    # compared past the first update.
+    zo2, io2 = spgl1.spgl1(A, At, bf, sigma, opts=spgl1.Options(opt_tol=1e-5, max_iter=3))
+    _, ig2 = cpct.spgl1(p, bd, sigma, opts=cpct.make_opts(opt_tol=1e-5, max_iter=3, synth_dh=True))
+    assert io2.n_newton == 1 and ig2["newton"] == 1
+    assert abs(ig2["tau"] - io2.tau) <= 1e-5 * io2.tau
+    assert abs(ig2["rnorm"] - io2.rnorm) <= 1e-3 * io2.rnorm
