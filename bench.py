@@ -515,7 +515,7 @@ def spgl1_bench(args, torch, cpct, synth):
 def bins_bench(torch, cpct, synth, runs=10):
     """Bin plans of the gridding kernels compared (the paper's quadtree
     against uniform tiles of 16, 32 and 64 points, each with heavy bins split
-    into work items; adjoint rounds of 16 lanes, and of 32 for uniform 32):
+    into work items; adjoint rounds of 16, 32 and 64 lanes):
     gather and spread (+ reduce) device time per launch,
     CUDA events around each kernel, L2 flushed before every pair, at the
     2048^2 / 1024-view workload and at the largest and smallest view counts
@@ -529,8 +529,9 @@ def bins_bench(torch, cpct, synth, runs=10):
         y = torch.empty((m, n), device="cuda")
         z = torch.empty((n, n), device="cuda")
         res = {}
-        for kind, tile, lanes in [("uniform", 16, 16), ("uniform", 32, 16), ("uniform", 32, 32), ("uniform", 64, 16),
-                                  ("quadtree", 0, 16)]:
+        for kind, tile, lanes in [("uniform", 16, 16), ("uniform", 32, 16), ("uniform", 32, 32), ("uniform", 32, 64),
+                                  ("uniform", 64, 16), ("uniform", 64, 32), ("uniform", 64, 64), ("quadtree", 0, 16),
+                                  ("quadtree", 0, 32), ("quadtree", 0, 64)]:
             plan.set_bins("fwd", kind, tile)
             plan.set_bins("adj", kind, tile)
             plan.set_rounds(lanes)

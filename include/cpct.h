@@ -242,10 +242,12 @@ int cpct_plan_set_caps(cpct_plan* plan, int fwd_cap, int adj_cap, cudaStream_t s
 #define CPCT_BINS_QUADTREE 1
 int cpct_plan_set_bins(cpct_plan* plan, int which, int kind, int tile, cudaStream_t stream);
 
-/* Width of the adjoint spread's conflict-free rounds (default 32): 16 puts
- * one sample per 64-bit shared-memory bank class in the lower half-warp, so
- * each accumulator access is served in one pass; 32 puts up to two per class
- * in both halves (two passes).  cpct_plan_set_rounds re-packs the installed
+/* Width of the adjoint spread's conflict-free rounds (default 32): every
+ * half-warp holds at most one sample per 64-bit shared-memory bank class, so
+ * each of its accumulator accesses is served in one pass.  16 uses the lower
+ * half-warp only; 32 one warp (two samples per class); 64 two warps of one
+ * work item (four per class; rounds of the larger tiles have room for 64
+ * disjoint footprints).  cpct_plan_set_rounds re-packs the installed
  * adjoint bins (the plan must not have clones; synchronous);
  * cpct_plan_rounds returns the width (or CPCT_EINVAL for a NULL plan). */
 int cpct_plan_set_rounds(cpct_plan* plan, int lanes, cudaStream_t stream);
@@ -614,13 +616,15 @@ int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packed, int* val
 int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, int* n_split, int* n_slots);
 
 /* A bin plan of a geometry built on the host exactly as cpct_plan_set_bins
- * builds it (kind, tile as there): forward and adjoint bin counts, the
- * adjoint bins of each size (16, 32, 64; host array of 3, may be NULL), the
- * adjoint rounds, and valid = 1 if every invariant holds (disjoint aligned
- * bins; forward lists partition the samples by first point; adjoint lists
- * hold exactly the samples whose footprint touches the bin; rounds hold
- * each entry once, footprints disjoint, lane = bank class).  No GPU needed. */
-int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int* n_fwd_bins, int* n_adj_bins,
+ * builds it (kind, tile as there; adjoint rounds of `lanes` samples, 16, 32
+ * or 64, 0 for the default): forward and adjoint bin counts, the adjoint
+ * bins of each size (16, 32, 64; host array of 3, may be NULL), the adjoint
+ * rounds, and valid = 1 if every invariant holds (disjoint aligned bins;
+ * forward lists partition the samples by first point; adjoint lists hold
+ * exactly the samples whose footprint touches the bin; rounds hold each
+ * entry once, footprints disjoint, lane = bank class mod 16).  No GPU
+ * needed; CPCT_EINVAL for another width. */
+int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int lanes, int* n_fwd_bins, int* n_adj_bins,
                        int* adj_class_bins, int* n_rounds, int* valid);
 
 /* The split of a sample coordinate u = k (hi + lo) into floor and fraction,

@@ -71,7 +71,7 @@ def lib():
         L.cpct_plan_set_rounds.argtypes = [vp, i, vp]
         L.cpct_plan_rounds.argtypes = [vp]
         L.cpct_plan_bins.argtypes = [vp] + [ctypes.POINTER(i)] * 4 + [vp, vp]
-        L.cpct_debug_binplan.argtypes = [ctypes.POINTER(Geom), i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp,
+        L.cpct_debug_binplan.argtypes = [ctypes.POINTER(Geom), i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp,
                                          ctypes.POINTER(i), ctypes.POINTER(i)]
         L.cpct_plan_work.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
         L.cpct_debug_adj_items.argtypes = [ctypes.POINTER(Geom), i, ctypes.POINTER(i), ctypes.POINTER(i),
@@ -235,7 +235,8 @@ class Plan:
         check(lib().cpct_plan_set_bins(self._h, w, k, int(tile), _stream(self._torch, stream)), "cpct_plan_set_bins")
 
     def set_rounds(self, lanes, stream=None):
-        """Width of the adjoint's conflict-free rounds: 16 or 32."""
+        """Width of the adjoint's conflict-free rounds: 16, 32 or 64 (two
+        warps per work item)."""
         check(lib().cpct_plan_set_rounds(self._h, int(lanes), _stream(self._torch, stream)), "cpct_plan_set_rounds")
 
     def rounds(self):
@@ -421,15 +422,15 @@ BINS_UNIFORM = 0
 BINS_QUADTREE = 1
 
 
-def debug_binplan(n, n_det, n_views, kind, tile=0, angles=None):
+def debug_binplan(n, n_det, n_views, kind, tile=0, angles=None, lanes=0):
     """Host-side bin plan of a geometry (no GPU needed): kind 'uniform' (tile
-    16/32/64) or 'quadtree'; dict(fwd_bins, adj_bins, adj_class_bins, rounds,
-    valid)."""
+    16/32/64) or 'quadtree', adjoint rounds of `lanes` samples (16/32/64, 0:
+    default); dict(fwd_bins, adj_bins, adj_class_bins, rounds, valid)."""
     g, _keep = make_geom(n, n_det, n_views, angles)
     k = {"uniform": BINS_UNIFORM, "quadtree": BINS_QUADTREE}[kind]
     nf, na, nr, ok = (ctypes.c_int() for _ in range(4))
     cls = np.zeros(3, dtype=np.int32)
-    check(lib().cpct_debug_binplan(ctypes.byref(g), k, int(tile), ctypes.byref(nf), ctypes.byref(na),
+    check(lib().cpct_debug_binplan(ctypes.byref(g), k, int(tile), int(lanes), ctypes.byref(nf), ctypes.byref(na),
                                    cls.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nr), ctypes.byref(ok)),
           "cpct_debug_binplan")
     return dict(fwd_bins=nf.value, adj_bins=na.value, adj_class_bins=cls.tolist(), rounds=nr.value, valid=ok.value)

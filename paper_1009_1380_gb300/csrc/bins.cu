@@ -290,11 +290,12 @@ void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, int 
   constexpr int kMaxRows = 64 + 2 * CPCT_HALO;
   struct R {
     uint64_t occ[kMaxRows][2];  // accumulator columns 0..127 per row
-    uint32_t lanes;
+    uint64_t lanes;             // occupied lanes
     int count;
   };
+  const int per_class = lanes / 16;  // lanes c, c + 16, ... of bank class c
   std::vector<R> rounds;
-  std::vector<std::array<uint32_t, 32>> lanes_of;
+  std::vector<std::array<uint32_t, 64>> lanes_of;
   for (int t = 0; t < nt; ++t) {
     const int4 bn = L.bins[t];
     const int T = bn.z, ld = round_pitch(T);
@@ -314,7 +315,9 @@ void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, int 
       for (; r < rounds.size(); ++r) {
         R& rd = rounds[r];
         if (rd.count == lanes) continue;
-        if (lanes == 16 ? ((rd.lanes >> cls) & 1u) : ((rd.lanes >> cls) & (rd.lanes >> (cls + 16)) & 1u)) continue;
+        int used = 0;
+        for (int h = 0; h < per_class; ++h) used += (int)((rd.lanes >> (cls + 16 * h)) & 1ull);
+        if (used == per_class) continue;
         bool clash = false;
         for (int q = 0; q < CPCT_W && !clash; ++q)
           clash = ((rd.occ[br + q][0] & fm[0]) | (rd.occ[br + q][1] & fm[1])) != 0;
@@ -323,13 +326,14 @@ void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, int 
       if (r == rounds.size()) {
         rounds.emplace_back();
         std::memset(&rounds.back(), 0, sizeof(R));
-        std::array<uint32_t, 32> empty;
+        std::array<uint32_t, 64> empty;
         empty.fill(0xffffffffu);
         lanes_of.push_back(empty);
       }
       R& rd = rounds[r];
-      const int lane = ((rd.lanes >> cls) & 1u) ? cls + 16 : cls;
-      rd.lanes |= 1u << lane;
+      int lane = cls;
+      while ((rd.lanes >> lane) & 1ull) lane += 16;
+      rd.lanes |= 1ull << lane;
       rd.count++;
       for (int q = 0; q < CPCT_W; ++q) {
         rd.occ[br + q][0] |= fm[0];

@@ -73,12 +73,13 @@ void order_fwd(const Samples& s, const BinLayout& L, BinLists& b);
 // adjoint: rounds of samples with pairwise disjoint footprints in the bin's
 // (T + 10) x (T + 13) accumulator; the 64-bit bank pair of a sample's first
 // cell is its class (the odd pitch shifts the classes of consecutive rows by
-// 13).  32-lane rounds hold at most two samples per class (lanes c and
-// c + 16: a 64-bit access of the warp is served in two half-warp passes);
-// 16-lane rounds hold at most one (lane c), so that only the lower half-warp
-// accesses shared memory and every access is served in one pass.
+// 13).  A round of `lanes` samples holds at most lanes / 16 per class, in
+// lanes c, c + 16, ...: every half-warp's 64-bit access is then served in
+// one pass.  16-lane rounds use the lower half-warp only, 32-lane rounds one
+// warp, 64-lane rounds two warps (the larger tiles have room for 64
+// disjoint footprints).
 struct Rounds {
-  int lanes = 32;               // samples per round (16 or 32)
+  int lanes = 32;               // samples per round (16, 32 or 64)
   std::vector<int> ptr;         // bins + 1, in rounds
   std::vector<uint32_t> ids;    // `lanes` per round, 0xffffffff = empty lane
 };

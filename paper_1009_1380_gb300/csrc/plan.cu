@@ -26,7 +26,7 @@ namespace {
 constexpr int kPolyDeg = 9;            // Chebyshev interpolation degree per tap
 constexpr int kFwdItemMax = 1024;      // samples per forward gather work item
 constexpr int kAdjItemRounds = 64;     // conflict-free rounds per adjoint spread work item
-constexpr int kRoundLanes = 32;        // samples per adjoint round (32; 16 is a tuner option)
+constexpr int kRoundLanes = 32;        // samples per adjoint round (32; 16 and 64 are tuner options)
 
 // ---------------------------------------------------------------------------
 // FP64 device builders (kernel table, deapodization, twiddles)
@@ -372,16 +372,19 @@ extern "C" int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packe
 }
 
 // A bin plan of a geometry (host only): kind 0 uniform tiles of `tile`
-// points, kind 1 the quadtree.  Reports the forward and adjoint bin counts,
-// the bins of each size class (T = 16, 32, 64) of the adjoint plan, the
-// rounds and 1 if every invariant holds (check_plan).
-extern "C" int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int* n_fwd_bins, int* n_adj_bins,
-                                  int* adj_class_bins, int* n_rounds, int* valid) {
+// points, kind 1 the quadtree, adjoint rounds of `lanes` samples (0: the
+// default width).  Reports the forward and adjoint bin counts, the bins of
+// each size class (T = 16, 32, 64) of the adjoint plan, the rounds and 1 if
+// every invariant holds (check_plan).
+extern "C" int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int lanes, int* n_fwd_bins,
+                                  int* n_adj_bins, int* adj_class_bins, int* n_rounds, int* valid) {
+  if (lanes == 0) lanes = kRoundLanes;
+  if (lanes != 16 && lanes != 32 && lanes != 64) return CPCT_EINVAL;
   HostBins h;
   int rc = host_bins(g, kind, tile, h);
   if (rc) return rc;
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(h.s, h.al, h.adj, kRoundLanes, rd);
+  cpct_detail::pack_rounds(h.s, h.al, h.adj, lanes, rd);
   if (valid) *valid = check_plan(h, rd, nullptr);
   if (n_fwd_bins) *n_fwd_bins = (int)h.fl.bins.size();
   if (n_adj_bins) *n_adj_bins = (int)h.al.bins.size();
@@ -793,11 +796,20 @@ extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap
       rc = fwd ? install_fwd_plan(p, best.kind, best.tile, cap0, stream)
                : install_adj_plan(p, best.kind, best.tile, cap0, stream);
     if (!fwd && rc == CPCT_OK) {
-      // round width of the adjoint: the other width, kept if faster
-      const int other = p->round_lanes == 16 ? 32 : 16;
-      const float t_cur = time_op(false);
-      if ((rc = install_adj_plan(p, best.kind, best.tile, cap0, stream, other)) == CPCT_OK && time_op(false) >= t_cur)
-        rc = install_adj_plan(p, best.kind, best.tile, cap0, stream, other == 16 ? 32 : 16);
+      // round width of the adjoint: the fastest of 16, 32 and 64 lanes
+      const int widths[] = {16, 32, 64};
+      int best_w = p->round_lanes;
+      float tw = time_op(false);
+      for (int w : widths) {
+        if (w == best_w) continue;
+        if ((rc = install_adj_plan(p, best.kind, best.tile, cap0, stream, w)) != CPCT_OK) break;
+        const float t = time_op(false);
+        if (t < tw) {
+          tw = t;
+          best_w = w;
+        }
+      }
+      if (rc == CPCT_OK && p->round_lanes != best_w) rc = install_adj_plan(p, best.kind, best.tile, cap0, stream, best_w);
     }
     const int fc[] = {256, 512, 1024, 2048, 4096};
     const int ac[] = {16, 32, 64, 128, 256};
@@ -845,10 +857,11 @@ extern "C" int cpct_plan_set_bins(cpct_plan* p, int which, int kind, int tile, c
 }
 
 // Width of the adjoint's conflict-free rounds: 16 (one sample per bank
-// class, the lower half-warp only) or 32 (two per class); re-packs the
-// installed adjoint bins.  The plan must not have clones.  Synchronous.
+// class, the lower half-warp only), 32 (two per class, one warp) or 64 (four
+// per class, two warps); re-packs the installed adjoint bins.  The plan must
+// not have clones.  Synchronous.
 extern "C" int cpct_plan_set_rounds(cpct_plan* p, int lanes, cudaStream_t stream) {
-  if (!p || !p->shared || (lanes != 16 && lanes != 32)) return CPCT_EINVAL;
+  if (!p || !p->shared || (lanes != 16 && lanes != 32 && lanes != 64)) return CPCT_EINVAL;
   if (p->shared->refs != 1) return CPCT_EINVAL;
   return install_adj_plan(p, p->adj_kind, p->adj_tile ? p->adj_tile : CPCT_TILE, p->adj_cap, stream, lanes);
 }

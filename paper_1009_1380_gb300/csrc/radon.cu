@@ -420,7 +420,7 @@ struct AdjSpreadArgs {
   int* err;
   const int* skip;  // the launch does nothing while *skip != 0 (may be null)
   int G, ldq, ldh, ext_rows;
-  int lanes;  // samples per round: 16 (lanes 0..15) or 32
+  int lanes;  // samples per round: 16 (lanes 0..15), 32 (one warp) or 64 (two warps)
   KBPoly poly;
 };
 
@@ -433,22 +433,25 @@ struct Acc {
   static constexpr int ld = rows + 3;
 };
 
-// One warp per work item (a run of conflict-free rounds of one tile).  In a
-// round, lane l holds one sample (or none); the 6x6 footprints of the round's
-// samples are pairwise disjoint and their first cells fall in distinct 64-bit
-// bank pairs within each half-warp, so every lane updates its 36 accumulator
-// cells with plain shared-memory loads and stores: no atomics, no conflicts.
-// Rounds are applied in their fixed plan order, hence every output element
-// receives its contributions in the same order on every run.
+// One warp (two for 64-lane rounds) per work item: a run of conflict-free
+// rounds of one tile.  In a round, thread l holds one sample (or none); the
+// 6x6 footprints of the round's samples are pairwise disjoint and their
+// first cells fall in distinct 64-bit bank pairs within each half-warp, so
+// every thread updates its 36 accumulator cells with plain shared-memory
+// loads and stores: no atomics, no conflicts.  Rounds are applied in their
+// fixed plan order (a barrier of the item's threads between rounds), hence
+// every output element receives its contributions in the same order on
+// every run.
 template <int T>
-__global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
+__global__ void __launch_bounds__(64) k_adj_spread(const AdjSpreadArgs a) {
   if (a.skip && *a.skip) return;
   constexpr int kRRows = Acc<T>::rows, kRLd = Acc<T>::ld;
   __shared__ __align__(16) float2 acc[kRRows * kRLd];
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x, nt = blockDim.x;
+  const bool two_warps = nt > 32;
   const int4 it = a.items[blockIdx.x];
   const int TC = it.x & 0xffff, TR = it.x >> 16;
-  for (int i = lane; i < kRRows * kRLd; i += 32) acc[i] = make_float2(0.f, 0.f);
+  for (int i = lane; i < kRRows * kRLd; i += nt) acc[i] = make_float2(0.f, 0.f);
   // software pipeline: ids two rounds ahead, sample data one round ahead;
   // with 16-lane rounds the upper half-warp holds no sample
   const int L = a.lanes;
@@ -461,7 +464,8 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
     ray0 = a.ray[id0 >> 16];
     val0 = a.Qt[(size_t)(id0 >> 16) * a.ldq + (id0 & 0xffffu)];
   }
-  __syncwarp();
+  if (two_warps) __syncthreads();
+  else __syncwarp();
   for (int r = it.y; r < it.z; ++r) {
     const uint32_t id2 = act && r + 2 < it.z ? a.ids[(size_t)(r + 2) * L + lane] : 0xffffffffu;
     float4 ray1 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -504,15 +508,15 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
         atomicOr(a.err, CPCT_ERR_BIN);
       }
     }
-    __syncwarp();
+    if (two_warps) __syncthreads();
+    else __syncwarp();
     id0 = id1;
     ray0 = ray1;
     val0 = val1;
     id1 = id2;
   }
-  __syncwarp();
   if (it.w < 0) {
-    for (int i = lane; i < T * T; i += 32) {
+    for (int i = lane; i < T * T; i += nt) {
       const int rr = i / T, cc = i % T;
       const int gr = TR + rr, gc = TC + cc;
       if (gr < a.ext_rows && gc < a.ldh)
@@ -520,7 +524,7 @@ __global__ void __launch_bounds__(32) k_adj_spread(const AdjSpreadArgs a) {
     }
   } else {
     float2* dst = a.partials + (size_t)it.w;
-    for (int i = lane; i < T * T; i += 32) dst[i] = acc[(i / T + CPCT_HALO) * kRLd + i % T + CPCT_HALO];
+    for (int i = lane; i < T * T; i += nt) dst[i] = acc[(i / T + CPCT_HALO) * kRLd + i % T + CPCT_HALO];
   }
 }
 
@@ -867,9 +871,10 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
   auto spread = [&](int c, cudaStream_t si) {
     a.items = p->d_adj_items + p->adj_cls[c];
     const int n_items = p->adj_cls[c + 1] - p->adj_cls[c];
-    if (c == 0) k_adj_spread<16><<<n_items, 32, 0, si>>>(a);
-    else if (c == 1) k_adj_spread<32><<<n_items, 32, 0, si>>>(a);
-    else k_adj_spread<64><<<n_items, 32, 0, si>>>(a);
+    const int nt = a.lanes > 32 ? 64 : 32;
+    if (c == 0) k_adj_spread<16><<<n_items, nt, 0, si>>>(a);
+    else if (c == 1) k_adj_spread<32><<<n_items, nt, 0, si>>>(a);
+    else k_adj_spread<64><<<n_items, nt, 0, si>>>(a);
   };
   auto reduce = [&](int c, cudaStream_t si) {
     const int n = p->split_cls[c + 1] - p->split_cls[c];

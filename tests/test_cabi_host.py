@@ -161,12 +161,23 @@ def test_bin_plans_valid(cpct, n, ns, m):
     """Every bin plan (uniform 16 / 32 / 64 and the paper's quadtree) holds
     its invariants: disjoint aligned bins, forward lists = the samples by
     first point, adjoint lists = exactly the samples whose footprint touches
-    the bin (checked by 2D prefix sums), valid conflict-free rounds."""
+    the bin (checked by 2D prefix sums), valid conflict-free rounds of 16,
+    32 and 64 lanes; wider rounds never need more rounds."""
     for kind, tile in [("uniform", 16), ("uniform", 32), ("uniform", 64), ("quadtree", 0)]:
-        d = cpct.debug_binplan(n, ns, m, kind, tile)
-        assert d["valid"] == 1, (kind, tile, d)
+        rounds = []
+        for lanes in (16, 32, 64):
+            d = cpct.debug_binplan(n, ns, m, kind, tile, lanes=lanes)
+            assert d["valid"] == 1, (kind, tile, lanes, d)
+            rounds.append(d["rounds"])
+        assert rounds[0] >= rounds[1] >= rounds[2], (kind, tile, rounds)
         if kind == "uniform":
             assert d["adj_class_bins"][{16: 0, 32: 1, 64: 2}[tile]] == d["adj_bins"]
+
+
+def test_binplan_rejects_other_round_widths(cpct):
+    for lanes in (8, 48, 128):
+        with pytest.raises(RuntimeError):
+            cpct.debug_binplan(64, 64, 10, "uniform", 32, lanes=lanes)
 
 
 def test_quadtree_splits_where_samples_are_dense(cpct):
