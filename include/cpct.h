@@ -214,9 +214,23 @@ int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream_t stream);
 
 /* Install the work items of a plan with the given caps: fwd_cap samples per
  * forward gather item, adj_cap conflict-free rounds per adjoint spread item
- * (0 keeps the current cap; defaults 1024 and 64).  The plan must not have
- * clones yet.  Allocates the new item lists; synchronous. */
+ * (0 keeps the current cap).  A new plan's caps are chosen from its
+ * geometry and the GPU: about the work of one resident CTA per item when
+ * the work is spread evenly (gather 256..4096 samples, spread 8..64
+ * rounds), since a launch lasts at least as long as its longest item.  The
+ * plan must not have clones yet.  Allocates the new item lists;
+ * synchronous. */
 int cpct_plan_set_caps(cpct_plan* plan, int fwd_cap, int adj_cap, cudaStream_t stream);
+
+/* Install the automatic caps for `concurrent` slices applying the operator
+ * at the same time (the batched solver's or a batch's slices): each slice
+ * gets 1 / concurrent of the resident CTAs, so the items grow with the
+ * concurrency (one slice alone is cut finest: its launch is bound by its
+ * longest item; many at once are bound by their total work, which small
+ * items raise by their partial tiles).  Clones made afterwards share the
+ * items.  CPCT_EINVAL for concurrent < 1 or a plan with clones;
+ * synchronous. */
+int cpct_plan_auto_caps(cpct_plan* plan, int concurrent, cudaStream_t stream);
 
 /* Bin plans (section "fast radon transform": the sample plane is divided
  * into bins, one thread block per bin, chosen by a quadtree that repeatedly
@@ -262,10 +276,10 @@ int cpct_plan_bins(const cpct_plan* plan, int* fwd_kind, int* fwd_tile, int* adj
 int cpct_plan_work(const cpct_plan* plan, int* n_fwd_items, int* n_adj_items, int* n_split, int* n_slots);
 
 /* Autotuner of the bin plans and work-item sizes: for each operator times
- * the bin plans uniform 16, 32, 64 and the quadtree at the default cap, keeps
- * the fastest (for the adjoint then the faster round width, 16 or 32), then
- * times its caps (256..4096 samples per gather item,
- * 16..256 rounds per spread item) and keeps the fastest (median of `reps`
+ * the bin plans uniform 16, 32, 64 and the quadtree at the automatic cap,
+ * keeps the fastest (for the adjoint then the fastest round width, 16, 32
+ * or 64), then times its caps (the automatic one, 256..4096 samples per
+ * gather item, 8..128 rounds per spread item) and keeps the fastest (median of `reps`
  * launches each, CUDA events on `stream`); reports the chosen caps
  * (cpct_plan_bins reports the bin plans).  The plan must not have clones
  * yet.  Allocates temporary buffers; synchronous. */
@@ -567,8 +581,9 @@ int cpct_debug_tc_gemm(const void* d_a, const void* d_b, float* d_d, int n, int 
  * same summation order), but the only scratch of its gridding step -- the
  * partial tiles of the few heavy tiles that are split over several work
  * items -- lives in a fixed device array inside this library instead of plan
- * memory: CPCT_NOALLOC_MAX_SLOTS tiles of 32 x 32 complex64 (8 KB each, 4 MB
- * in all), held by every GPU that loads the library until the process exits.
+ * memory: CPCT_NOALLOC_MAX_SLOTS tiles of 32 x 32 complex64 (8 KB each, 16
+ * MB in all), held by every GPU that loads the library until the process
+ * exits.
  * The paper has no counterpart of this entry point.
  *   plan    an existing plan (created earlier; this call allocates nothing:
  *           no cudaMalloc, cudaFree or allocating library routine)
@@ -581,7 +596,7 @@ int cpct_debug_tc_gemm(const void* d_a, const void* d_b, float* d_d, int n, int 
  * keeps the last call's contents (each call overwrites every tile it reads,
  * so nothing needs clearing); calls that overlap on the GPU -- on different
  * streams, or from different plans -- race on it and must be serialised. */
-#define CPCT_NOALLOC_MAX_SLOTS 512
+#define CPCT_NOALLOC_MAX_SLOTS 2048
 int radon_adj_noalloc(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream);
 
 /* Human-readable name of a cpct_status (static string). */
@@ -610,9 +625,11 @@ int cpct_debug_bin_tile(const cpct_geom* g, int which, int tile, uint32_t* ids, 
 int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packed, int* valid);
 
 /* The adjoint work items that a plan of geometry g gets with its default
- * bin plan and `cap` rounds per spread item (0: the default cap), built on
- * the host exactly as cpct_plan_create / cpct_plan_set_caps build them:
- * items, split heavy bins, partial-tile slots of 32 x 32.  No GPU needed. */
+ * bin plan and `cap` rounds per spread item (0: the automatic cap of
+ * cpct_plan_create, for the current GPU, or for a GB300 when there is
+ * none), built on the host exactly as cpct_plan_create / cpct_plan_set_caps
+ * build them: items, split heavy bins, partial-tile slots of 32 x 32.  No
+ * GPU needed. */
 int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, int* n_split, int* n_slots);
 
 /* A bin plan of a geometry built on the host exactly as cpct_plan_set_bins

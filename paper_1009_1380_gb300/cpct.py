@@ -67,6 +67,7 @@ def lib():
         for name in ("radon_fwd_c", "radon_adj_c"):
             getattr(L, name).argtypes = [vp, vp, vp, vp]
         L.cpct_plan_set_caps.argtypes = [vp, i, i, vp]
+        L.cpct_plan_auto_caps.argtypes = [vp, i, vp]
         L.cpct_plan_set_bins.argtypes = [vp, i, i, i, vp]
         L.cpct_plan_set_rounds.argtypes = [vp, i, vp]
         L.cpct_plan_rounds.argtypes = [vp]
@@ -226,6 +227,11 @@ class Plan:
     def set_caps(self, fwd_cap=0, adj_cap=0, stream=None):
         check(lib().cpct_plan_set_caps(self._h, int(fwd_cap), int(adj_cap), _stream(self._torch, stream)),
               "cpct_plan_set_caps")
+
+    def auto_caps(self, concurrent=1, stream=None):
+        """Automatic work-item caps for `concurrent` slices at once
+        (cpct_plan_auto_caps)."""
+        check(lib().cpct_plan_auto_caps(self._h, int(concurrent), _stream(self._torch, stream)), "cpct_plan_auto_caps")
 
     def set_bins(self, which, kind, tile=0, stream=None):
         """Bin plan of one operator (which 'fwd' or 'adj'): kind 'uniform'

@@ -90,7 +90,7 @@ struct cpct_plan {
   int split_cls[4];
   int4* d_split;            // (origin, partial offset, pieces, T), grouped by class
   int fwd_kind, fwd_tile, adj_kind, adj_tile;  // bin plans (kind 0 uniform, 1 quadtree)
-  int round_lanes;          // samples per adjoint round (16 or 32)
+  int round_lanes;          // samples per adjoint round (16, 32 or 64)
   // staging for the host-buffer entry points
   float* d_stage_img;
   float* d_stage_sino;
@@ -103,6 +103,7 @@ struct cpct_plan {
   cudaStream_t side[2];
   cudaEvent_t ev_fork, ev_join[2];
   int fwd_cap, adj_cap;     // work-item caps (samples / rounds per item), tunable
+  int concurrency;          // slices expected to run at once (automatic caps; 0 = 1)
   struct PlanShared* shared;  // read-only geometry shared with clones (refcounted)
   long long launches;       // kernels launched by this plan's operators
   CpctProfiler* prof;       // NULL unless profiling is enabled
@@ -267,3 +268,7 @@ int cpct_launch_fwd_skip(cpct_plan* p, const float* d_img, float* d_sino, const 
 int cpct_launch_fwd_c(cpct_plan* p, const float* d_img, float2* d_sino_c, cudaStream_t s);
 int cpct_launch_adj_c(cpct_plan* p, const float2* d_sino_c, float* d_img, cudaStream_t s);
 int cpct_radon_setup_attributes(int logG, int logNs);
+// resident CTAs of a gridding kernel on the current GPU (SMs x CTAs per SM):
+// which 0 the gather of T x T bins, 1 the spread with `threads` threads per
+// item; 0 if unknown
+int cpct_gridding_resident(int which, int T, int threads);

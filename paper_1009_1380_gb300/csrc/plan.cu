@@ -24,8 +24,7 @@
 namespace {
 
 constexpr int kPolyDeg = 9;            // Chebyshev interpolation degree per tap
-constexpr int kFwdItemMax = 1024;      // samples per forward gather work item
-constexpr int kAdjItemRounds = 64;     // conflict-free rounds per adjoint spread work item
+constexpr int kCapAuto = 0;            // work-item caps chosen from the geometry (auto_*_cap)
 constexpr int kRoundLanes = 32;        // samples per adjoint round (32; 16 and 64 are tuner options)
 
 // ---------------------------------------------------------------------------
@@ -456,8 +455,45 @@ int replace_upload(cpct_plan* p, T** dst, const std::vector<T>& src, cudaStream_
   return CPCT_OK;
 }
 
+// Automatic work-item sizes.  The items of a launch run their samples or
+// rounds one after another, so the longest item bounds the launch: items
+// are cut to about the work one resident CTA gets when the work is spread
+// evenly.  Spread: 1.2 x rounds / resident items, 8..64 rounds; gather:
+// 0.67 x samples / resident CTAs of the persistent grid, a multiple of 64,
+// 256..4096 samples.  Measured on GB300 from 512^2 / 90 views to 2048^2 /
+// 1024 views: within a few percent of the best fixed cap at every size
+// (fixed caps of 64 rounds and 1024 samples left the smaller geometries
+// bound by their longest items: 1024^2 / 128 views, spread 45 -> 14 us,
+// gather 16 -> 10 us).  Without a GPU, a GB300's resident counts are used
+// (152 SMs; 14 spread items or 9 gather CTAs of 32 x 32 bins per SM).
+constexpr int kNominalSpreadResident = 152 * 14;
+constexpr int kNominalGatherResident = 152 * 9;
+
+// resident CTAs per slice when `concurrency` slices share the GPU
+int share(int resident, int nominal, int concurrency) {
+  if (resident <= 0) resident = nominal;
+  return std::max(1, resident / std::max(1, concurrency));
+}
+
+int auto_adj_cap(long long rounds, int resident) {
+  if (resident <= 0) resident = kNominalSpreadResident;
+  const long long c = (12 * rounds / resident + 5) / 10;
+  return (int)std::min<long long>(64, std::max<long long>(8, c));
+}
+
+int auto_fwd_cap(long long samples, int resident) {
+  if (resident <= 0) resident = kNominalGatherResident;
+  const long long c = (67 * samples / resident) / 100 / 64 * 64;
+  return (int)std::min<long long>(4096, std::max<long long>(256, c));
+}
+
 // forward work items of the installed bin plan with `cap` samples per item
+// (kCapAuto: auto_fwd_cap)
 int install_fwd_items(cpct_plan* p, int cap, cudaStream_t s) {
+  if (cap == kCapAuto)
+    cap = auto_fwd_cap(p->shared->fwd_ptr.empty() ? 0 : p->shared->fwd_ptr.back(),
+                       share(cpct_gridding_resident(0, p->fwd_tile ? p->fwd_tile : CPCT_TILE, 0),
+                             kNominalGatherResident, p->concurrency));
   cpct_detail::BinLayout L;
   L.bins = p->shared->fwd_bins;
   cpct_detail::Items it;
@@ -470,8 +506,13 @@ int install_fwd_items(cpct_plan* p, int cap, cudaStream_t s) {
   return CPCT_OK;
 }
 
-// adjoint work items (and split list, partial tiles) with `cap` rounds per item
+// adjoint work items (and split list, partial tiles) with `cap` rounds per
+// item (kCapAuto: auto_adj_cap)
 int install_adj_items(cpct_plan* p, int cap, cudaStream_t s) {
+  if (cap == kCapAuto)
+    cap = auto_adj_cap(p->shared->round_ptr.empty() ? 0 : p->shared->round_ptr.back(),
+                       share(cpct_gridding_resident(1, p->adj_tile ? p->adj_tile : CPCT_TILE, p->round_lanes > 32 ? 64 : 32),
+                             kNominalSpreadResident, p->concurrency));
   cpct_detail::BinLayout L;
   L.bins = p->shared->adj_bins;
   cpct_detail::Items it;
@@ -623,8 +664,8 @@ extern "C" int cpct_plan_create(cpct_plan** out, const cpct_geom* g, cudaStream_
     p->shared = new (std::nothrow) PlanShared;
     if (!p->shared) { rc = CPCT_ENOMEM; goto fail; }
     p->shared->ray = ray;
-    TRY(install_fwd_plan(p, cpct_detail::BIN_UNIFORM, CPCT_TILE, kFwdItemMax, stream));
-    TRY(install_adj_plan(p, cpct_detail::BIN_UNIFORM, CPCT_TILE, kAdjItemRounds, stream));
+    TRY(install_fwd_plan(p, cpct_detail::BIN_UNIFORM, CPCT_TILE, kCapAuto, stream));
+    TRY(install_adj_plan(p, cpct_detail::BIN_UNIFORM, CPCT_TILE, kCapAuto, stream));
     // TMA descriptor of the forward extended spectrum (viewed as float32 pairs)
     TRY(encode_hx_map(p));
     // FP32 copy of the even/odd polynomial parts
@@ -780,7 +821,7 @@ extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap
   int rc = CPCT_OK;
   for (int op = 0; op < 2 && rc == CPCT_OK; ++op) {
     const bool fwd = op == 0;
-    const int cap0 = fwd ? kFwdItemMax : kAdjItemRounds;
+    const int cap0 = kCapAuto;
     Cand best = plans[1];
     float tb = 1e30f;
     for (const Cand& c : plans) {
@@ -811,12 +852,14 @@ extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap
       }
       if (rc == CPCT_OK && p->round_lanes != best_w) rc = install_adj_plan(p, best.kind, best.tile, cap0, stream, best_w);
     }
+    // caps: the automatic one (installed now), then fixed candidates
     const int fc[] = {256, 512, 1024, 2048, 4096};
-    const int ac[] = {16, 32, 64, 128, 256};
-    int best_cap = cap0;
-    tb = 1e30f;
+    const int ac[] = {8, 16, 32, 64, 128};
+    int best_cap = fwd ? p->fwd_cap : p->adj_cap;
+    tb = time_op(fwd);
     for (int i = 0; i < 5 && rc == CPCT_OK; ++i) {
       const int cap = fwd ? fc[i] : ac[i];
+      if (cap == best_cap) continue;
       if ((rc = fwd ? install_fwd_items(p, cap, stream) : install_adj_items(p, cap, stream)) != CPCT_OK) break;
       const float t = time_op(fwd);
       if (t < tb) {
@@ -843,6 +886,17 @@ extern "C" int cpct_plan_set_caps(cpct_plan* p, int fwd_cap, int adj_cap, cudaSt
   int rc = CPCT_OK;
   if (fwd_cap > 0) rc = install_fwd_items(p, fwd_cap, stream);
   if (rc == CPCT_OK && adj_cap > 0) rc = install_adj_items(p, adj_cap, stream);
+  return rc;
+}
+
+// Automatic caps for `concurrent` slices running at once (each gets that
+// share of the resident CTAs).  The plan must not have clones.  Synchronous.
+extern "C" int cpct_plan_auto_caps(cpct_plan* p, int concurrent, cudaStream_t stream) {
+  if (!p || !p->shared || concurrent < 1) return CPCT_EINVAL;
+  if (p->shared->refs != 1) return CPCT_EINVAL;
+  p->concurrency = concurrent;
+  int rc = install_fwd_items(p, kCapAuto, stream);
+  if (rc == CPCT_OK) rc = install_adj_items(p, kCapAuto, stream);
   return rc;
 }
 
@@ -909,7 +963,7 @@ extern "C" int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, i
   cpct_detail::Rounds rd;
   cpct_detail::pack_rounds(h.s, h.al, h.adj, kRoundLanes, rd);
   cpct_detail::Items it;
-  cpct_detail::adj_items(h.al, rd.ptr, cap > 0 ? cap : kAdjItemRounds, it);
+  cpct_detail::adj_items(h.al, rd.ptr, cap > 0 ? cap : auto_adj_cap(rd.ptr.back(), cpct_gridding_resident(1, CPCT_TILE, 32)), it);
   if (n_items) *n_items = (int)it.items.size();
   if (n_split) *n_split = (int)it.split.size();
   if (n_slots) *n_slots = (int)((it.partial_elems + 1023) / 1024);

@@ -777,6 +777,26 @@ void launch_fwd_interp(cpct_plan* p, const FwdInterpArgs& a, int n_items, cudaSt
 
 }  // namespace
 
+int cpct_gridding_resident(int which, int T, int threads) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  cudaError_t e;
+  if (which == 0)
+    e = T == 16   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fwd_interp<16>, kInterpThreads, Win<16>::smem + 128)
+        : T == 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fwd_interp<64>, kInterpThreads, Win<64>::smem + 128)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fwd_interp<32>, kInterpThreads, Win<32>::smem + 128);
+  else
+    e = T == 16   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adj_spread<16>, threads, 0)
+        : T == 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adj_spread<64>, threads, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_adj_spread<32>, threads, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * per;
+}
+
 int cpct_radon_setup_attributes(int logG, int logNs) {
   int rc = set_attr_interp<16>();
   if (!rc) rc = set_attr_interp<32>();

@@ -68,6 +68,7 @@ def _rel(a, b):
 def run_point(n, m, noise, count, torch, max_iter=400, synth_iters=300):
     """One (views, noise) point: mean relative errors and solver costs."""
     plan0 = cpct.Plan(n, n, m)
+    plan0.auto_caps(count)
     plans = [plan0] + [cpct.clone(plan0) for _ in range(count - 1)]
     # phase contrast: FBP and SPGL1 (l1 of x), batched over the slices
     xs, bs, sig = _slices(plan0, count, noise, 0, torch)

@@ -352,6 +352,7 @@ def run(pairs, eval_slices, epochs, batch, lr, levels, base, plans_per_group, ta
                       "batch": batch, "lr": lr, "levels": levels, "base": base, "target_max_iter": target_iters,
                       "eval_opt_tol": eval_tol}}
     plan0 = cpct.Plan(n, n, m)
+    plan0.auto_caps(plans_per_group)  # work items for a group of slices at once
     plans = [plan0] + [cpct.clone(plan0) for _ in range(plans_per_group - 1)]
     t0 = time.perf_counter()
     b, sigma, fbp = make_slices(plan0, pairs, 0, torch)

@@ -145,15 +145,26 @@ def test_source_digest_is_independent_of_the_checkout_location(monkeypatch):
 def test_adjoint_work_items_and_noalloc_bound(cpct):
     """The default plan of the 2048^2 / 1024-view benchmark splits a few heavy
     origin tiles into partial tiles that fit the allocation-free entry point's
-    512-slot array; smaller caps split more tiles (more slots), and the slot
-    count is the same function of the geometry on every call."""
+    2048-slot array; smaller caps split more tiles (more slots), and the slot
+    count is the same function of the geometry on every call.  The automatic
+    cap grows with the geometry's rounds (items of about one resident CTA's
+    share): 2048^2 / 1024 views splits fewer tiles than a cap of 16, small
+    geometries get the smallest cap, 8, and still fit the array (a cap of 64
+    splits nothing at 64^2 / 10 views)."""
     d = cpct.debug_adj_items(2048, 2048, 1024)
-    assert d["n_split"] > 0 and 0 < d["n_slots"] <= 512, d
+    assert d["n_split"] > 0 and 0 < d["n_slots"] <= 2048, d
     d16 = cpct.debug_adj_items(2048, 2048, 1024, 16)
     assert d16["n_slots"] > d["n_slots"] and d16["items"] > d["items"]
     assert cpct.debug_adj_items(2048, 2048, 1024) == d
+    for n, m in [(1024, 128), (512, 90), (1024, 512)]:
+        da = cpct.debug_adj_items(n, n, m)
+        assert da["n_slots"] <= 2048, (n, m, da)
+    assert cpct.debug_adj_items(1024, 1024, 128) == cpct.debug_adj_items(1024, 1024, 128, 8)
+    # 64^2 / 10 views: only the bins at the origin, where every ray passes,
+    # hold more than 8 rounds
     small = cpct.debug_adj_items(64, 64, 10)
-    assert small["n_split"] == 0 and small["n_slots"] == 0
+    assert 0 < small["n_split"] <= 4 and small["n_slots"] <= 16, small
+    assert cpct.debug_adj_items(64, 64, 10, 64)["n_split"] == 0
 
 
 @pytest.mark.parametrize("n,ns,m", [(64, 64, 10), (128, 128, 180), (256, 256, 64), (64, 128, 33), (1024, 1024, 128)])

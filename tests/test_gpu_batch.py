@@ -54,7 +54,8 @@ def test_tuned_plan_matches_oracle(torch_cuda):
     p = cpct.Plan(n, n, m)
     fcap, acap = cpct.tune(p, reps=3)
     print("tuned caps", fcap, acap)
-    assert fcap in (256, 512, 1024, 2048, 4096) and acap in (16, 32, 64, 128, 256)
+    # the automatic caps or one of the fixed candidates
+    assert 256 <= fcap <= 4096 and fcap % 64 == 0 and 8 <= acap <= 128
     rng = np.random.default_rng(12)
     img = rng.standard_normal((n, n))
     w = rng.standard_normal((m, n))

@@ -359,3 +359,32 @@ def test_full_size_2048_sampled_rays(torch_cuda):
     print("2048 adjoint identity rel", rel)
     assert rel < 1e-6
     p.sync()
+
+
+def test_auto_caps_follow_concurrency(torch_cuda):
+    """Automatic work-item caps: a plan alone cuts its items finest (its
+    launch is bound by its longest item); for 64 slices at once each gets
+    1/64 of the resident CTAs, so the items are longer and fewer.  The
+    operator is unchanged (FP32 summation order of the split bins aside)."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    n, m = 1024, 128
+    p = _plan(n, n, m)
+    w1 = p.work()
+    w = torch.randn((m, n), device="cuda", generator=torch.Generator(device="cuda").manual_seed(9))
+    z1 = p.adj(w).double()
+    p.auto_caps(64)
+    w64 = p.work()
+    z64 = p.adj(w).double()
+    print("alone", w1, "64 at once", w64)
+    assert w64["adj_items"] < w1["adj_items"] and w64["n_slots"] < w1["n_slots"]
+    assert w64["fwd_items"] <= w1["fwd_items"]
+    assert float((z64 - z1).norm() / z1.norm()) < 1e-6
+    p.auto_caps(1)
+    assert p.work() == w1
+    with pytest.raises(RuntimeError):
+        p.auto_caps(0)
+    c = cpct.clone(p)
+    with pytest.raises(RuntimeError):
+        p.auto_caps(2)
+    c.close()

@@ -40,7 +40,7 @@ def test_noalloc_adjoint_matches_radon_adj_twice(torch_cuda):
     n, m = 2048, 1024
     plan = cpct.Plan(n, n, m)
     work = plan.work()
-    assert work["n_split"] > 0 and 0 < work["n_slots"] <= 512, work
+    assert work["n_split"] > 0 and 0 < work["n_slots"] <= 2048, work
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     gen = torch.Generator(device="cuda").manual_seed(20)
     x = torch.from_numpy(synth.phantom("c2_2048")).cuda()
@@ -90,9 +90,9 @@ def test_noalloc_rejects_plans_needing_more_partial_tiles(torch_cuda):
     torch = torch_cuda
     from paper_1009_1380_gb300 import cpct
     L = cpct.lib()
-    n, m = 1024, 512
+    n, m = 2048, 1024
     host = cpct.debug_adj_items(n, n, m, 16)
-    assert host["n_slots"] > 512, host
+    assert host["n_slots"] > 2048, host
     plan = cpct.Plan(n, n, m)
     plan.set_caps(adj_cap=16)
     assert plan.work()["n_slots"] == host["n_slots"]
