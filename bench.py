@@ -521,7 +521,8 @@ def spgl1_bench(args, torch, cpct, synth):
 def bins_bench(torch, cpct, synth, runs=10):
     """Bin plans of the gridding kernels compared (the paper's quadtree
     against uniform tiles of 16, 32 and 64 points, each with heavy bins split
-    into work items; adjoint rounds of 16, 32 and 64 lanes):
+    into work items; adjoint rounds of 16, 32 and 64 lanes, and column
+    groups):
     gather and spread (+ reduce) device time per launch,
     CUDA events around each kernel, L2 flushed before every pair, at the
     2048^2 / 1024-view workload and at the largest and smallest view counts
@@ -535,9 +536,10 @@ def bins_bench(torch, cpct, synth, runs=10):
         y = torch.empty((m, n), device="cuda")
         z = torch.empty((n, n), device="cuda")
         res = {}
-        for kind, tile, lanes in [("uniform", 16, 16), ("uniform", 32, 16), ("uniform", 32, 32), ("uniform", 32, 64),
-                                  ("uniform", 64, 16), ("uniform", 64, 32), ("uniform", 64, 64), ("quadtree", 0, 16),
-                                  ("quadtree", 0, 32), ("quadtree", 0, 64)]:
+        for kind, tile, lanes in [("uniform", 16, 16), ("uniform", 16, 5), ("uniform", 32, 16), ("uniform", 32, 32),
+                                  ("uniform", 32, 64), ("uniform", 32, 5), ("uniform", 64, 16), ("uniform", 64, 32),
+                                  ("uniform", 64, 64), ("uniform", 64, 5), ("quadtree", 0, 16), ("quadtree", 0, 32),
+                                  ("quadtree", 0, 64), ("quadtree", 0, 5)]:
             plan.set_bins("fwd", kind, tile)
             plan.set_bins("adj", kind, tile)
             plan.set_rounds(lanes)
@@ -557,7 +559,8 @@ def bins_bench(torch, cpct, synth, runs=10):
                 pair.append(sum(v[0] for v in pr.values()) * 1e3)
             plan.profile_enable(0)
             b = plan.bins()
-            res[(kind if kind == "quadtree" else f"uniform{tile}") + ("" if lanes == 16 else f"_rounds{lanes}")] = {
+            res[(kind if kind == "quadtree" else f"uniform{tile}")
+                + ("" if lanes == 16 else "_columns" if lanes == cpct.ROUNDS_COLUMNS else f"_rounds{lanes}")] = {
                 "gather_us": float(np.median(g)), "spread_us": float(np.median(sp)), "pair_us": float(np.median(pair)),
                 "adj_bins_16_32_64": b["adj"][2], "work": plan.work()}
         out[name] = res

@@ -217,9 +217,10 @@ int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream_t stream);
  * (0 keeps the current cap).  A new plan's caps are chosen from its
  * geometry and the GPU: about the work of one resident CTA per item when
  * the work is spread evenly (gather 256..4096 samples, spread 8..64
- * rounds), since a launch lasts at least as long as its longest item.  The
- * plan must not have clones yet.  Allocates the new item lists;
- * synchronous. */
+ * rounds), since a launch lasts at least as long as its longest item; a
+ * new bin plan or round width takes its own automatic cap unless a cap was
+ * fixed here.  The plan must not have clones yet.  Allocates the new item
+ * lists; synchronous. */
 int cpct_plan_set_caps(cpct_plan* plan, int fwd_cap, int adj_cap, cudaStream_t stream);
 
 /* Install the automatic caps for `concurrent` slices applying the operator
@@ -242,7 +243,8 @@ int cpct_plan_auto_caps(cpct_plan* plan, int concurrent, cudaStream_t stream);
  * leaves).  which = 0: the forward gather (a sample belongs to the bin of
  * its footprint's first point), 1: the adjoint spread (a sample belongs to
  * every bin its 6x6 footprint touches).  cpct_plan_set_bins installs a plan
- * for one operator (keeping its cap); the plan must not have clones;
+ * for one operator (keeping a cap fixed by cpct_plan_set_caps, else taking
+ * the automatic cap of the new bins); the plan must not have clones;
  * synchronous.  The default is uniform 32 for both.  Results do not depend
  * on the bin plan beyond FP32 rounding (each bin sums its samples in its
  * own order); for a given plan they are bitwise reproducible.
@@ -261,9 +263,17 @@ int cpct_plan_set_bins(cpct_plan* plan, int which, int kind, int tile, cudaStrea
  * each of its accumulator accesses is served in one pass.  16 uses the lower
  * half-warp only; 32 one warp (two samples per class); 64 two warps of one
  * work item (four per class; rounds of the larger tiles have room for 64
- * disjoint footprints).  cpct_plan_set_rounds re-packs the installed
- * adjoint bins (the plan must not have clones; synchronous);
+ * disjoint footprints).  CPCT_ROUNDS_COLUMNS selects column groups instead:
+ * five samples per warp, six lanes per sample, one per footprint column,
+ * each applying its column's six taps row after row; the five samples'
+ * first cells follow a fixed bank pattern, so every half-warp access is
+ * served in one pass, and each entry carries the sample's fractions and
+ * accumulator coordinates (16 bytes per entry instead of 4).
+ * cpct_plan_set_rounds re-packs the installed adjoint bins (with the
+ * automatic cap unless cpct_plan_set_caps fixed one; the plan must not have
+ * clones; synchronous);
  * cpct_plan_rounds returns the width (or CPCT_EINVAL for a NULL plan). */
+#define CPCT_ROUNDS_COLUMNS 5
 int cpct_plan_set_rounds(cpct_plan* plan, int lanes, cudaStream_t stream);
 int cpct_plan_rounds(const cpct_plan* plan);
 int cpct_plan_bins(const cpct_plan* plan, int* fwd_kind, int* fwd_tile, int* adj_kind, int* adj_tile,
@@ -634,12 +644,14 @@ int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, int* n_split
 
 /* A bin plan of a geometry built on the host exactly as cpct_plan_set_bins
  * builds it (kind, tile as there; adjoint rounds of `lanes` samples, 16, 32
- * or 64, 0 for the default): forward and adjoint bin counts, the adjoint
- * bins of each size (16, 32, 64; host array of 3, may be NULL), the adjoint
- * rounds, and valid = 1 if every invariant holds (disjoint aligned bins;
- * forward lists partition the samples by first point; adjoint lists hold
- * exactly the samples whose footprint touches the bin; rounds hold each
- * entry once, footprints disjoint, lane = bank class mod 16).  No GPU
+ * or 64, CPCT_ROUNDS_COLUMNS for column groups, 0 for the default): forward
+ * and adjoint bin counts, the adjoint bins of each size (16, 32, 64; host
+ * array of 3, may be NULL), the adjoint rounds (or groups), and valid = 1 if
+ * every invariant holds (disjoint aligned bins; forward lists partition the
+ * samples by first point; adjoint lists hold exactly the samples whose
+ * footprint touches the bin; rounds hold each entry once, footprints
+ * disjoint, lane = bank class mod 16, or for groups the slots' classes in
+ * the conflict-free pattern and each entry's payload that of its sample).  No GPU
  * needed; CPCT_EINVAL for another width. */
 int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int lanes, int* n_fwd_bins, int* n_adj_bins,
                        int* adj_class_bins, int* n_rounds, int* valid);

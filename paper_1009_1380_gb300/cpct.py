@@ -242,7 +242,8 @@ class Plan:
 
     def set_rounds(self, lanes, stream=None):
         """Width of the adjoint's conflict-free rounds: 16, 32 or 64 (two
-        warps per work item)."""
+        warps per work item), or ROUNDS_COLUMNS (column groups of five
+        samples)."""
         check(lib().cpct_plan_set_rounds(self._h, int(lanes), _stream(self._torch, stream)), "cpct_plan_set_rounds")
 
     def rounds(self):
@@ -426,6 +427,7 @@ def preprocess_pc(near, far, flat_near, flat_far, dark, out=None, stream=None):
 
 BINS_UNIFORM = 0
 BINS_QUADTREE = 1
+ROUNDS_COLUMNS = 5  # round width of column groups (CPCT_ROUNDS_COLUMNS)
 
 
 def debug_binplan(n, n_det, n_views, kind, tile=0, angles=None, lanes=0):

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <queue>
 
@@ -48,6 +49,8 @@ void make_samples(int ns, int m, int G, const std::vector<float4>& ray, Samples&
   s.K = K;
   s.a0.resize((size_t)m * (K + 1));
   s.rb0.resize((size_t)m * (K + 1));
+  s.zu.resize((size_t)m * (K + 1));
+  s.zv.resize((size_t)m * (K + 1));
   for (int j = 0; j < m; ++j)
     for (int k = 0; k <= K; ++k) {
       int fu, fv;
@@ -57,6 +60,8 @@ void make_samples(int ns, int m, int G, const std::vector<float4>& ray, Samples&
       const size_t i = (size_t)j * (K + 1) + k;
       s.a0[i] = (fu - 2) & (G - 1);
       s.rb0[i] = fv;  // buffer row of the first tap: (floor(v) - 2) + 2
+      s.zu[i] = zu;
+      s.zv[i] = zv;
     }
 }
 
@@ -344,6 +349,69 @@ void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, int 
     }
     for (auto& l : lanes_of) out.ids.insert(out.ids.end(), l.begin(), l.begin() + lanes);
     out.ptr[t + 1] = out.ptr[t] + (int)rounds.size();
+  }
+}
+
+void pack_groups(const Samples& s, const BinLayout& L, const BinLists& adj, Rounds& out) {
+  const int nt = (int)adj.ptr.size() - 1;
+  out.lanes = kGroupLanes;
+  out.ptr.assign(nt + 1, 0);
+  out.ids.clear();
+  struct Gp {
+    int base;                          // bank class of slot 0
+    int used;                          // occupied slots (bits)
+    int ar[kGroupSlots], br[kGroupSlots];
+    uint32_t w[kGroupWords];
+  };
+  std::vector<Gp> groups;
+  for (int t = 0; t < nt; ++t) {
+    const int4 bn = L.bins[t];
+    const int ld = round_pitch(bn.z);
+    groups.clear();
+    size_t first_open = 0;
+    for (int e = adj.ptr[t]; e < adj.ptr[t + 1]; ++e) {
+      const uint32_t id = adj.ids[e];
+      const size_t i = (size_t)(id >> 16) * (s.K + 1) + (id & 0xffffu);
+      const int ar = s.a0[i] - bn.x + CPCT_HALO, br = s.rb0[i] - bn.y + CPCT_HALO;  // 0 .. T + 4
+      const int cls = (br * ld + ar) & 15;
+      size_t g = first_open;
+      int slot = -1;
+      for (; g < groups.size() && slot < 0; ++g) {
+        const Gp& gp = groups[g];
+        if (gp.used == (1 << kGroupSlots) - 1) continue;
+        for (int j = 1; j < kGroupSlots && slot < 0; ++j) {
+          if (((gp.used >> j) & 1) || ((gp.base + kGroupPattern[j]) & 15) != cls) continue;
+          bool clash = false;
+          for (int q = 0; q < kGroupSlots && !clash; ++q)
+            clash = ((gp.used >> q) & 1) && std::abs(gp.ar[q] - ar) < CPCT_W && std::abs(gp.br[q] - br) < CPCT_W;
+          if (!clash) slot = j;
+        }
+        if (slot >= 0) break;
+      }
+      if (slot < 0) {  // a new group with this sample in slot 0
+        Gp gp;
+        gp.base = cls;
+        gp.used = 0;
+        for (int q = 0; q < kGroupWords; ++q) gp.w[q] = 0xffffffffu;
+        groups.push_back(gp);
+        g = groups.size() - 1;
+        slot = 0;
+      }
+      Gp& gp = groups[g];
+      gp.used |= 1 << slot;
+      gp.ar[slot] = ar;
+      gp.br[slot] = br;
+      uint32_t zu, zv;
+      std::memcpy(&zu, &s.zu[i], 4);
+      std::memcpy(&zv, &s.zv[i], 4);
+      gp.w[4 * slot + 0] = id;
+      gp.w[4 * slot + 1] = zu;
+      gp.w[4 * slot + 2] = zv;
+      gp.w[4 * slot + 3] = (uint32_t)ar | ((uint32_t)br << 16);
+      while (first_open < groups.size() && groups[first_open].used == (1 << kGroupSlots) - 1) ++first_open;
+    }
+    for (const Gp& gp : groups) out.ids.insert(out.ids.end(), gp.w, gp.w + kGroupWords);
+    out.ptr[t + 1] = out.ptr[t] + (int)groups.size();
   }
 }
 

@@ -40,6 +40,7 @@ void host_split(float k, float hi, float lo, int* fl_out, float* z);
 struct Samples {
   int m = 0, K = 0;
   std::vector<int> a0, rb0;
+  std::vector<float> zu, zv;  // fractions of u and v (the kernels' split)
 };
 
 void make_rays(int n, int ns, int m, const double* angles, double scale, std::vector<float4>& ray);
@@ -79,12 +80,32 @@ void order_fwd(const Samples& s, const BinLayout& L, BinLists& b);
 // warp, 64-lane rounds two warps (the larger tiles have room for 64
 // disjoint footprints).
 struct Rounds {
-  int lanes = 32;               // samples per round (16, 32 or 64)
+  int lanes = 32;               // samples per round (16, 32 or 64), or kGroupLanes
   std::vector<int> ptr;         // bins + 1, in rounds
-  std::vector<uint32_t> ids;    // `lanes` per round, 0xffffffff = empty lane
+  std::vector<uint32_t> ids;    // round_words(lanes) per round, 0xffffffff = empty lane
 };
 inline int round_pitch(int T) { return T + 2 * CPCT_HALO + 3; }
 void pack_rounds(const Samples& s, const BinLayout& L, const BinLists& adj, int lanes, Rounds& out);
+
+// Column groups (round width kGroupLanes): five samples per warp, lane
+// 6 s + c applies column c of sample s's footprint, rows 0..5 in turn, so a
+// sample's 36 taps take six accesses of six lanes.  A half-warp then holds
+// the columns of up to three samples; its accesses are conflict free when
+// the first cells' bank classes of slots 0..4 are b, b + 6, b + 12, b + 2,
+// b + 8 (mod 16) for the group's base class b (half-warp 0: slot 0 columns
+// on classes b..b+5, slot 1 on b+6..b+11, slot 2's first four on
+// b+12..b+15; half-warp 1: slot 2's last two on b, b+1, slot 3 on
+// b+2..b+7, slot 4 on b+8..b+13).  The footprints of a group are pairwise
+// disjoint.  Each entry carries what the kernel would otherwise recompute
+// per lane: (id, zu bits, zv bits, ar | br << 16), accumulator coordinates
+// relative to the bin's halo origin; an empty slot has id 0xffffffff.
+constexpr int kGroupLanes = 5;      // the round-width value of column groups
+constexpr int kGroupSlots = 5;
+constexpr int kGroupWords = 4 * kGroupSlots;  // uint32 words per group
+constexpr int kGroupPattern[kGroupSlots] = {0, 6, 12, 2, 8};
+void pack_groups(const Samples& s, const BinLayout& L, const BinLists& adj, Rounds& out);
+// uint32 words per round of a width (rounds: one id per lane)
+inline int round_words(int lanes) { return lanes == kGroupLanes ? kGroupWords : lanes; }
 
 // work items, grouped by tile class and longest first within a class
 struct Items {

@@ -104,6 +104,7 @@ struct cpct_plan {
   cudaEvent_t ev_fork, ev_join[2];
   int fwd_cap, adj_cap;     // work-item caps (samples / rounds per item), tunable
   int concurrency;          // slices expected to run at once (automatic caps; 0 = 1)
+  int fwd_cap_set, adj_cap_set;  // 1 once cpct_plan_set_caps fixed the cap (else automatic)
   struct PlanShared* shared;  // read-only geometry shared with clones (refcounted)
   long long launches;       // kernels launched by this plan's operators
   CpctProfiler* prof;       // NULL unless profiling is enabled

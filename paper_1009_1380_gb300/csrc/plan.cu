@@ -322,20 +322,39 @@ int check_plan(const HostBins& h, const cpct_detail::Rounds& rd, int* n_packed) 
     }
   }
   int packed = 0;
+  const bool grp = rd.lanes == cpct_detail::kGroupLanes;
+  const int words = cpct_detail::round_words(rd.lanes);
   for (size_t t = 0; t + 1 < rd.ptr.size() && ok; ++t) {
     const int4 b = h.al.bins[t];
     const int ld = cpct_detail::round_pitch(b.z);
     std::vector<uint32_t> got;
     for (int r = rd.ptr[t]; r < rd.ptr[t + 1] && ok; ++r) {
       std::vector<int> cells;
-      for (int l = 0; l < rd.lanes; ++l) {
-        const uint32_t id = rd.ids[(size_t)r * rd.lanes + l];
-        if (id == 0xffffffffu) continue;
+      const uint32_t* w = rd.ids.data() + (size_t)r * words;
+      int base = -1;
+      for (int l = 0; l < (grp ? cpct_detail::kGroupSlots : rd.lanes); ++l) {
+        const uint32_t id = grp ? w[4 * l] : w[l];
+        if (id == 0xffffffffu) {
+          if (grp && l == 0) ok = 0;  // slot 0 opens every group
+          continue;
+        }
         got.push_back(id);
         const size_t i = (size_t)(id >> 16) * (s.K + 1) + (id & 0xffffu);
         const int ar = s.a0[i] - b.x + CPCT_HALO, br = s.rb0[i] - b.y + CPCT_HALO;
         if (ar < 0 || br < 0 || ar > b.z + CPCT_HALO - 1 || br > b.z + CPCT_HALO - 1) ok = 0;
-        if (((br * ld + ar) & 15) != (l & 15)) ok = 0;
+        const int cls = (br * ld + ar) & 15;
+        if (grp) {
+          // slot classes follow the conflict-free pattern; the payload is the
+          // sample's fractions and accumulator coordinates
+          if (l == 0) base = cls;
+          if (cls != ((base + cpct_detail::kGroupPattern[l]) & 15)) ok = 0;
+          uint32_t zu, zv;
+          std::memcpy(&zu, &s.zu[i], 4);
+          std::memcpy(&zv, &s.zv[i], 4);
+          if (w[4 * l + 1] != zu || w[4 * l + 2] != zv || w[4 * l + 3] != ((uint32_t)ar | ((uint32_t)br << 16))) ok = 0;
+        } else if (cls != (l & 15)) {
+          ok = 0;
+        }
         for (int q = 0; q < CPCT_W; ++q)
           for (int c = 0; c < CPCT_W; ++c) cells.push_back((br + q) * ld + ar + c);
       }
@@ -354,6 +373,15 @@ int check_plan(const HostBins& h, const cpct_detail::Rounds& rd, int* n_packed) 
 
 }  // namespace
 
+// conflict-free rounds or column groups of the adjoint bins
+void pack_adj(const cpct_detail::Samples& s, const cpct_detail::BinLayout& L, const cpct_detail::BinLists& b,
+              int lanes, cpct_detail::Rounds& rd) {
+  if (lanes == cpct_detail::kGroupLanes) cpct_detail::pack_groups(s, L, b, rd);
+  else cpct_detail::pack_rounds(s, L, b, lanes, rd);
+}
+
+bool lanes_ok(int lanes) { return lanes == 16 || lanes == 32 || lanes == 64 || lanes == cpct_detail::kGroupLanes; }
+
 // Round packing of the adjoint bins of a geometry (default bin plan, host
 // only): number of rounds, number of packed samples, and 1 if every round
 // is footprint- and bank-conflict free and every bin entry appears exactly
@@ -363,9 +391,9 @@ extern "C" int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packe
   int rc = host_bins(g, cpct_detail::BIN_UNIFORM, CPCT_TILE, h);
   if (rc) return rc;
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(h.s, h.al, h.adj, kRoundLanes, rd);
+  pack_adj(h.s, h.al, h.adj, kRoundLanes, rd);
   const int ok = check_plan(h, rd, n_packed);
-  if (n_rounds) *n_rounds = (int)(rd.ids.size() / rd.lanes);
+  if (n_rounds) *n_rounds = (int)(rd.ids.size() / cpct_detail::round_words(rd.lanes));
   if (valid) *valid = ok;
   return CPCT_OK;
 }
@@ -378,12 +406,12 @@ extern "C" int cpct_debug_rounds(const cpct_geom* g, int* n_rounds, int* n_packe
 extern "C" int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int lanes, int* n_fwd_bins,
                                   int* n_adj_bins, int* adj_class_bins, int* n_rounds, int* valid) {
   if (lanes == 0) lanes = kRoundLanes;
-  if (lanes != 16 && lanes != 32 && lanes != 64) return CPCT_EINVAL;
+  if (!lanes_ok(lanes)) return CPCT_EINVAL;
   HostBins h;
   int rc = host_bins(g, kind, tile, h);
   if (rc) return rc;
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(h.s, h.al, h.adj, lanes, rd);
+  pack_adj(h.s, h.al, h.adj, lanes, rd);
   if (valid) *valid = check_plan(h, rd, nullptr);
   if (n_fwd_bins) *n_fwd_bins = (int)h.fl.bins.size();
   if (n_adj_bins) *n_adj_bins = (int)h.al.bins.size();
@@ -391,7 +419,7 @@ extern "C" int cpct_debug_binplan(const cpct_geom* g, int kind, int tile, int la
     for (int c = 0; c < cpct_detail::kNumTileClasses; ++c) adj_class_bins[c] = 0;
     for (const int4& b : h.al.bins) adj_class_bins[cpct_detail::tile_class(b.z)]++;
   }
-  if (n_rounds) *n_rounds = (int)(rd.ids.size() / rd.lanes);
+  if (n_rounds) *n_rounds = (int)(rd.ids.size() / cpct_detail::round_words(rd.lanes));
   return CPCT_OK;
 }
 
@@ -475,10 +503,13 @@ int share(int resident, int nominal, int concurrency) {
   return std::max(1, resident / std::max(1, concurrency));
 }
 
-int auto_adj_cap(long long rounds, int resident) {
+int auto_adj_cap(long long rounds, int resident, int lanes) {
   if (resident <= 0) resident = kNominalSpreadResident;
+  // a column group holds up to 5 samples, a round up to 16 .. 64: the same
+  // bounds in samples
+  const int lo = lanes == cpct_detail::kGroupLanes ? 24 : 8, hi = 8 * lo;
   const long long c = (12 * rounds / resident + 5) / 10;
-  return (int)std::min<long long>(64, std::max<long long>(8, c));
+  return (int)std::min<long long>(hi, std::max<long long>(lo, c));
 }
 
 int auto_fwd_cap(long long samples, int resident) {
@@ -511,8 +542,9 @@ int install_fwd_items(cpct_plan* p, int cap, cudaStream_t s) {
 int install_adj_items(cpct_plan* p, int cap, cudaStream_t s) {
   if (cap == kCapAuto)
     cap = auto_adj_cap(p->shared->round_ptr.empty() ? 0 : p->shared->round_ptr.back(),
-                       share(cpct_gridding_resident(1, p->adj_tile ? p->adj_tile : CPCT_TILE, p->round_lanes > 32 ? 64 : 32),
-                             kNominalSpreadResident, p->concurrency));
+                       share(cpct_gridding_resident(1, p->adj_tile ? p->adj_tile : CPCT_TILE, p->round_lanes == 64 ? 64 : 32),
+                             kNominalSpreadResident, p->concurrency),
+                       p->round_lanes);
   cpct_detail::BinLayout L;
   L.bins = p->shared->adj_bins;
   cpct_detail::Items it;
@@ -570,7 +602,7 @@ int install_adj_plan(cpct_plan* p, int kind, int tile, int cap, cudaStream_t s, 
   cpct_detail::BinLists b;
   cpct_detail::assign_adj(smp, W, H, L, b);
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(smp, L, b, lanes, rd);
+  pack_adj(smp, L, b, lanes, rd);
   int rc = replace_upload(p, &p->d_adj_ids, rd.ids, s);
   if (rc) return rc;
   p->round_lanes = lanes;
@@ -837,8 +869,9 @@ extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap
       rc = fwd ? install_fwd_plan(p, best.kind, best.tile, cap0, stream)
                : install_adj_plan(p, best.kind, best.tile, cap0, stream);
     if (!fwd && rc == CPCT_OK) {
-      // round width of the adjoint: the fastest of 16, 32 and 64 lanes
-      const int widths[] = {16, 32, 64};
+      // round width of the adjoint: the fastest of 16, 32 and 64 lanes and
+      // column groups
+      const int widths[] = {16, 32, 64, cpct_detail::kGroupLanes};
       int best_w = p->round_lanes;
       float tw = time_op(false);
       for (int w : widths) {
@@ -884,8 +917,14 @@ extern "C" int cpct_plan_set_caps(cpct_plan* p, int fwd_cap, int adj_cap, cudaSt
   if (!p || !p->shared || fwd_cap < 0 || adj_cap < 0) return CPCT_EINVAL;
   if (p->shared->refs != 1) return CPCT_EINVAL;
   int rc = CPCT_OK;
-  if (fwd_cap > 0) rc = install_fwd_items(p, fwd_cap, stream);
-  if (rc == CPCT_OK && adj_cap > 0) rc = install_adj_items(p, adj_cap, stream);
+  if (fwd_cap > 0) {
+    rc = install_fwd_items(p, fwd_cap, stream);
+    p->fwd_cap_set = 1;
+  }
+  if (rc == CPCT_OK && adj_cap > 0) {
+    rc = install_adj_items(p, adj_cap, stream);
+    p->adj_cap_set = 1;
+  }
   return rc;
 }
 
@@ -895,19 +934,21 @@ extern "C" int cpct_plan_auto_caps(cpct_plan* p, int concurrent, cudaStream_t st
   if (!p || !p->shared || concurrent < 1) return CPCT_EINVAL;
   if (p->shared->refs != 1) return CPCT_EINVAL;
   p->concurrency = concurrent;
+  p->fwd_cap_set = p->adj_cap_set = 0;
   int rc = install_fwd_items(p, kCapAuto, stream);
   if (rc == CPCT_OK) rc = install_adj_items(p, kCapAuto, stream);
   return rc;
 }
 
 // Install a bin plan for one operator (which 0 forward, 1 adjoint): kind 0
-// uniform tiles of `tile` points (16, 32, 64), kind 1 the quadtree; keeps the
-// operator's current cap.  The plan must not have clones.  Synchronous.
+// uniform tiles of `tile` points (16, 32, 64), kind 1 the quadtree; keeps a
+// cap fixed by cpct_plan_set_caps, else takes the automatic cap of the new
+// bins.  The plan must not have clones.  Synchronous.
 extern "C" int cpct_plan_set_bins(cpct_plan* p, int which, int kind, int tile, cudaStream_t stream) {
   if (!p || !p->shared || (which != 0 && which != 1) || !bins_args_ok(kind, tile)) return CPCT_EINVAL;
   if (p->shared->refs != 1) return CPCT_EINVAL;
-  return which == 0 ? install_fwd_plan(p, kind, tile, p->fwd_cap, stream)
-                    : install_adj_plan(p, kind, tile, p->adj_cap, stream);
+  return which == 0 ? install_fwd_plan(p, kind, tile, p->fwd_cap_set ? p->fwd_cap : kCapAuto, stream)
+                    : install_adj_plan(p, kind, tile, p->adj_cap_set ? p->adj_cap : kCapAuto, stream);
 }
 
 // Width of the adjoint's conflict-free rounds: 16 (one sample per bank
@@ -915,9 +956,10 @@ extern "C" int cpct_plan_set_bins(cpct_plan* p, int which, int kind, int tile, c
 // per class, two warps); re-packs the installed adjoint bins.  The plan must
 // not have clones.  Synchronous.
 extern "C" int cpct_plan_set_rounds(cpct_plan* p, int lanes, cudaStream_t stream) {
-  if (!p || !p->shared || (lanes != 16 && lanes != 32 && lanes != 64)) return CPCT_EINVAL;
+  if (!p || !p->shared || !lanes_ok(lanes)) return CPCT_EINVAL;
   if (p->shared->refs != 1) return CPCT_EINVAL;
-  return install_adj_plan(p, p->adj_kind, p->adj_tile ? p->adj_tile : CPCT_TILE, p->adj_cap, stream, lanes);
+  return install_adj_plan(p, p->adj_kind, p->adj_tile ? p->adj_tile : CPCT_TILE, p->adj_cap_set ? p->adj_cap : kCapAuto,
+                          stream, lanes);
 }
 
 extern "C" int cpct_plan_rounds(const cpct_plan* p) { return p ? p->round_lanes : CPCT_EINVAL; }
@@ -961,9 +1003,9 @@ extern "C" int cpct_debug_adj_items(const cpct_geom* g, int cap, int* n_items, i
   int rc = host_bins(g, cpct_detail::BIN_UNIFORM, CPCT_TILE, h);
   if (rc) return rc;
   cpct_detail::Rounds rd;
-  cpct_detail::pack_rounds(h.s, h.al, h.adj, kRoundLanes, rd);
+  pack_adj(h.s, h.al, h.adj, kRoundLanes, rd);
   cpct_detail::Items it;
-  cpct_detail::adj_items(h.al, rd.ptr, cap > 0 ? cap : auto_adj_cap(rd.ptr.back(), cpct_gridding_resident(1, CPCT_TILE, 32)), it);
+  cpct_detail::adj_items(h.al, rd.ptr, cap > 0 ? cap : auto_adj_cap(rd.ptr.back(), cpct_gridding_resident(1, CPCT_TILE, 32), rd.lanes), it);
   if (n_items) *n_items = (int)it.items.size();
   if (n_split) *n_split = (int)it.split.size();
   if (n_slots) *n_slots = (int)((it.partial_elems + 1023) / 1024);

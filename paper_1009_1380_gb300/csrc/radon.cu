@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "bins.cuh"
 #include "common.cuh"
 #include "fft.cuh"
 
@@ -420,7 +421,7 @@ struct AdjSpreadArgs {
   int* err;
   const int* skip;  // the launch does nothing while *skip != 0 (may be null)
   int G, ldq, ldh, ext_rows;
-  int lanes;  // samples per round: 16 (lanes 0..15), 32 (one warp) or 64 (two warps)
+  int lanes;  // samples per round: 16 (lanes 0..15), 32 (one warp), 64 (two warps), or column groups
   KBPoly poly;
 };
 
@@ -525,6 +526,108 @@ __global__ void __launch_bounds__(64) k_adj_spread(const AdjSpreadArgs a) {
   } else {
     float2* dst = a.partials + (size_t)it.w;
     for (int i = lane; i < T * T; i += nt) dst[i] = acc[(i / T + CPCT_HALO) * kRLd + i % T + CPCT_HALO];
+  }
+}
+
+// Column groups (round width cpct_detail::kGroupLanes): one warp per work
+// item, five samples per group; lane 6 s + c applies column c of slot s's
+// footprint, row after row, so a sample's 36 taps take six accesses of six
+// lanes and a group's 30 lanes cover five samples.  The slots' first cells
+// follow a bank pattern that keeps each half-warp's accesses conflict free
+// (the packer's invariant), and the footprints of a group are disjoint.  The
+// entries carry the sample's fractions and accumulator coordinates (the host
+// computed them with the kernels' own split), so a lane evaluates only its
+// column's weight and the six row weights.  Groups are applied in plan
+// order: the result is bitwise reproducible, with per-tap products equal to
+// the rounds' (only the order of the additions into a cell differs).
+template <int T>
+__global__ void __launch_bounds__(32) k_adj_spread_cols(const AdjSpreadArgs a) {
+  if (a.skip && *a.skip) return;
+  constexpr int kRRows = Acc<T>::rows, kRLd = Acc<T>::ld;
+  constexpr uint32_t kEmpty = 0xffffffffu;
+  __shared__ __align__(16) float2 acc[kRRows * kRLd];
+  const int lane = threadIdx.x;
+  const int slot = lane / CPCT_W, c = lane - CPCT_W * slot;
+  const bool act = slot < cpct_detail::kGroupSlots;
+  // this lane's column tap: pair min(c, 5 - c) of the even / odd split
+  const int pi = c < 3 ? c : CPCT_W - 1 - c;
+  float E[CPCT_NPOLY], O[CPCT_NPOLY];
+#pragma unroll
+  for (int d = 0; d < CPCT_NPOLY; ++d) {
+    E[d] = pi == 0 ? a.poly.e[0][d] : pi == 1 ? a.poly.e[1][d] : a.poly.e[2][d];
+    O[d] = pi == 0 ? a.poly.o[0][d] : pi == 1 ? a.poly.o[1][d] : a.poly.o[2][d];
+  }
+  const int4 it = a.items[blockIdx.x];
+  const int TC = it.x & 0xffff, TR = it.x >> 16;
+  for (int i = lane; i < kRRows * kRLd; i += 32) acc[i] = make_float2(0.f, 0.f);
+  const uint4* ent = reinterpret_cast<const uint4*>(a.ids);
+  const uint4 none = make_uint4(kEmpty, 0u, 0u, 0u);
+  // software pipeline over a register ring: a group is about a sixth of a
+  // round's work, so entries are fetched 2 kDepth groups ahead and the
+  // sample values (a gather from the polar samples) kDepth ahead
+  constexpr int kDepth = 4;
+  uint4 e[2 * kDepth];
+  float2 v[kDepth];
+  auto fetch_e = [&](int g) { return act && g < it.z ? ent[(size_t)g * cpct_detail::kGroupSlots + slot] : none; };
+  auto fetch_v = [&](const uint4& x) {
+    return x.x != kEmpty ? a.Qt[(size_t)(x.x >> 16) * a.ldq + (x.x & 0xffffu)] : make_float2(0.f, 0.f);
+  };
+#pragma unroll
+  for (int k = 0; k < 2 * kDepth; ++k) e[k] = fetch_e(it.y + k);
+#pragma unroll
+  for (int k = 0; k < kDepth; ++k) v[k] = fetch_v(e[k]);
+  __syncwarp();
+  for (int r = it.y; r < it.z; r += kDepth) {
+#pragma unroll
+    for (int k = 0; k < kDepth; ++k) {
+      const uint4 e0 = e[k];
+      const float2 v0 = v[k];
+      // refill: this slot's value for group r + k + kDepth (its entry was
+      // fetched kDepth groups ago), its entry for group r + k + 2 kDepth
+      v[k] = fetch_v(e[k + kDepth]);
+      e[k] = e[k + kDepth];
+      e[k + kDepth] = fetch_e(r + k + 2 * kDepth);
+      if (e0.x != kEmpty) {
+        const int ar = (int)(e0.w & 0xffffu), br = (int)(e0.w >> 16);
+        if (ar <= T + CPCT_HALO - 1 && br <= T + CPCT_HALO - 1) {
+          const float zu = __uint_as_float(e0.y), zv = __uint_as_float(e0.z);
+          float wv[CPCT_W];
+          kb_weights(a.poly, zv, wv);
+          const float su = fmaf(2.f, zu, -1.f), su2 = su * su;
+          float Eu = E[CPCT_NPOLY - 1], Ou = O[CPCT_NPOLY - 1];
+#pragma unroll
+          for (int d = CPCT_NPOLY - 2; d >= 0; --d) {
+            Eu = fmaf(Eu, su2, E[d]);
+            Ou = fmaf(Ou, su2, O[d]);
+          }
+          float wu = fmaf(c < 3 ? su : -su, Ou, Eu);
+          if (c == CPCT_W - 1 && zu == 0.f) wu = 0.f;  // open support, as kb_weights
+          float2* col = acc + br * kRLd + ar + c;
+#pragma unroll
+          for (int q = 0; q < CPCT_W; ++q) {
+            const float2 vq = cscale(v0, wv[q]);
+            float2 t = col[q * kRLd];
+            t.x = fmaf(wu, vq.x, t.x);
+            t.y = fmaf(wu, vq.y, t.y);
+            col[q * kRLd] = t;
+          }
+        } else {
+          atomicOr(a.err, CPCT_ERR_BIN);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (it.w < 0) {
+    for (int i = lane; i < T * T; i += 32) {
+      const int rr = i / T, cc = i % T;
+      const int gr = TR + rr, gc = TC + cc;
+      if (gr < a.ext_rows && gc < a.ldh)
+        a.Ax[(size_t)gr * a.ldh + gc] = acc[(rr + CPCT_HALO) * kRLd + cc + CPCT_HALO];
+    }
+  } else {
+    float2* dst = a.partials + (size_t)it.w;
+    for (int i = lane; i < T * T; i += 32) dst[i] = acc[(i / T + CPCT_HALO) * kRLd + i % T + CPCT_HALO];
   }
 }
 
@@ -891,6 +994,12 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
   auto spread = [&](int c, cudaStream_t si) {
     a.items = p->d_adj_items + p->adj_cls[c];
     const int n_items = p->adj_cls[c + 1] - p->adj_cls[c];
+    if (a.lanes == cpct_detail::kGroupLanes) {
+      if (c == 0) k_adj_spread_cols<16><<<n_items, 32, 0, si>>>(a);
+      else if (c == 1) k_adj_spread_cols<32><<<n_items, 32, 0, si>>>(a);
+      else k_adj_spread_cols<64><<<n_items, 32, 0, si>>>(a);
+      return;
+    }
     const int nt = a.lanes > 32 ? 64 : 32;
     if (c == 0) k_adj_spread<16><<<n_items, nt, 0, si>>>(a);
     else if (c == 1) k_adj_spread<32><<<n_items, nt, 0, si>>>(a);

@@ -173,14 +173,19 @@ def test_bin_plans_valid(cpct, n, ns, m):
     its invariants: disjoint aligned bins, forward lists = the samples by
     first point, adjoint lists = exactly the samples whose footprint touches
     the bin (checked by 2D prefix sums), valid conflict-free rounds of 16,
-    32 and 64 lanes; wider rounds never need more rounds."""
+    32 and 64 lanes and of column groups (slot classes in the conflict-free
+    pattern, the entries' fractions and coordinates those of the samples);
+    wider rounds never need more rounds."""
     for kind, tile in [("uniform", 16), ("uniform", 32), ("uniform", 64), ("quadtree", 0)]:
         rounds = []
-        for lanes in (16, 32, 64):
+        for lanes in (16, 32, 64, cpct.ROUNDS_COLUMNS):
             d = cpct.debug_binplan(n, ns, m, kind, tile, lanes=lanes)
             assert d["valid"] == 1, (kind, tile, lanes, d)
             rounds.append(d["rounds"])
         assert rounds[0] >= rounds[1] >= rounds[2], (kind, tile, rounds)
+        # column groups hold at most 5 samples: at least a fifth of the
+        # entries, and never more groups than entries
+        assert rounds[3] >= rounds[1] * 32 // 5 // 8
         if kind == "uniform":
             assert d["adj_class_bins"][{16: 0, 32: 1, 64: 2}[tile]] == d["adj_bins"]
 

@@ -196,7 +196,8 @@ def test_complex_variants(torch_cuda, n, ns, m):
 
 @pytest.mark.parametrize("kind,tile,lanes", [("uniform", 16, 16), ("uniform", 64, 16), ("quadtree", 0, 16),
                                              ("uniform", 32, 32), ("quadtree", 0, 32), ("uniform", 64, 64),
-                                             ("uniform", 32, 64), ("quadtree", 0, 64)])
+                                             ("uniform", 32, 64), ("quadtree", 0, 64), ("uniform", 16, 5),
+                                             ("uniform", 32, 5), ("uniform", 64, 5), ("quadtree", 0, 5)])
 @pytest.mark.parametrize("n,ns,m", [(128, 128, 180), (256, 256, 64), (64, 128, 33)])
 def test_bin_plans_parity(torch_cuda, kind, tile, lanes, n, ns, m):
     """Every bin plan gives the operator pair of the FP64 oracle (1e-5), also
