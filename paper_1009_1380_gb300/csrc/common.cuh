@@ -98,6 +98,7 @@ struct cpct_plan {
   CUtensorMap tmap_Hx[3];   // TMA windows of 16, 32 and 64 point bins
   size_t device_bytes;
   int fwd_interp_grid[3];   // persistent grids of the forward gather per class (0 = not yet sized)
+  int adj_row_grid;         // persistent grid of the adjoint row transform (0 = not yet sized)
   // plans with bins of several sizes run the per-size launches concurrently:
   // two side streams fork from the launch stream and join it again
   cudaStream_t side[2];
@@ -232,6 +233,21 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
       "[%4];" ::"r"(smem_u32(smem_dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
+}
+
+// plain bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to shared memory, completion on `bar`
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// order this thread's earlier shared-memory accesses (generic proxy) before
+// its later bulk copies into shared memory (async proxy)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------

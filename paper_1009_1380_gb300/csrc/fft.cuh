@@ -87,13 +87,23 @@ struct SmemFFT {
   static constexpr int NPASS = fft_npass(LOGN);
   static_assert(E >= 16 && (N % E) == 0, "E must be >= 16 and divide N");
 
-  template <int P>
-  __device__ static __forceinline__ void pass(float2* buf, const float2* __restrict__ tw, int t) {
+  // One Stockham pass P.  SRCG (first pass only): the R inputs of every DFT
+  // come from ld(q), q = i + m N/R, instead of the buffer -- consecutive
+  // threads read consecutive q, so a caller reading global memory reads it
+  // coalesced, and no barrier separates the reads from the buffer writes.
+  // DSTG (last pass only): output k = i + m N/R goes to st(k, value) instead
+  // of the buffer (natural order, consecutive threads at consecutive k), and
+  // no barrier follows.
+  template <int P, bool SRCG, bool DSTG, class LD, class ST>
+  __device__ static __forceinline__ void pass(float2* buf, const float2* __restrict__ tw, int t, const LD& ld,
+                                              const ST& st) {
     constexpr int LR = fft_lr(LOGN, P);
     constexpr int R = 1 << LR;
     constexpr int L = 1 << fft_ll(P);
     constexpr int NB = E / R;
     static_assert(E % R == 0, "radix must divide E");
+    static_assert(!SRCG || P == 0, "only the first pass reads through ld");
+    static_assert(!DSTG || P == NPASS - 1, "only the last pass writes through st");
     // inter-pass twiddles w^m = exp(DIR 2 pi i m j / (R L)), m = 1..R-1: the
     // table entries for m = 1, 4, 8 (built in FP64) are loaded before the
     // barrier, the other powers are products of at most four of them
@@ -115,10 +125,13 @@ struct SmemFFT {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         if (PIN && R >= 4 && P == 0 && m >= R / 4 && m < 3 * R / 4) v[b * R + m] = make_float2(0.f, 0.f);
+        else if constexpr (SRCG) v[b * R + m] = ld(i + m * (N / R));
         else v[b * R + m] = buf[fpad(i + m * (N / R))];
       }
     }
-    __syncthreads();
+    // in place: every read of the pass before any write (a pass that reads
+    // through ld or writes through st shares nothing with the buffer)
+    if constexpr (!SRCG && !DSTG) __syncthreads();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int i = t + b * T;
@@ -150,26 +163,74 @@ struct SmemFFT {
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         // (for R >= 4 the outputs i + m N/R, i < N/R, outside [-N/4, N/4)
-        // are exactly m = R/4 .. 3R/4-1; a radix-2 last pass stores all)
+        // are exactly m = R/4 .. 3R/4-1; a radix-2 last pass writes all of
+        // them to the buffer and hands only the kept ones to st)
         if (POUT && R >= 4 && P == NPASS - 1 && m >= R / 4 && m < 3 * R / 4) continue;
-        buf[fpad(base + m * L)] = x[m];
+        if constexpr (DSTG) {
+          // st() only ever sees kept outputs: a radix-2 last pass checks k
+          const int k = base + m * L;
+          if (POUT && R < 4 && k >= N / 4 && k < 3 * N / 4) continue;
+          st(k, x[m]);
+        } else {
+          buf[fpad(base + m * L)] = x[m];
+        }
       }
     }
-    __syncthreads();
+    if constexpr (!DSTG) __syncthreads();
   }
 
-  template <int P>
-  __device__ static __forceinline__ void passes(float2* buf, const float2* __restrict__ tw, int t) {
-    pass<P>(buf, tw, t);
-    if constexpr (P + 1 < NPASS) passes<P + 1>(buf, tw, t);
+  // after_first() runs once the first pass is complete in every thread (the
+  // first pass ends with a barrier when more passes follow): from then on
+  // the source that ld() read may be overwritten
+  template <int P, bool SRCG, bool DSTG, class LD, class ST, class AF>
+  __device__ static __forceinline__ void passes(float2* buf, const float2* __restrict__ tw, int t, const LD& ld,
+                                                const ST& st, const AF& after_first) {
+    constexpr bool last = P + 1 == NPASS;
+    pass<P, SRCG && P == 0, DSTG && last>(buf, tw, t, ld, st);
+    if constexpr (P == 0) after_first();
+    if constexpr (!last) passes<P + 1, SRCG, DSTG>(buf, tw, t, ld, st, after_first);
   }
+
+  struct NoLoad {
+    __device__ float2 operator()(int) const { return make_float2(0.f, 0.f); }
+  };
+  struct NoStore {
+    __device__ void operator()(int, float2) const {}
+  };
+  struct NoHook {
+    __device__ void operator()() const {}
+  };
 
   // In-place transform of buf[fpad(q)], q = 0..N-1 (unnormalised):
   // DIR = -1: X[k] = sum_q x[q] exp(-2 pi i k q / N); DIR = +1: conjugate kernel.
-  // Threads with t >= T must still call (pass t = -1 ... no: every thread of
-  // the CTA must reach the barriers), so callers give each thread a valid t.
+  // Every thread of the CTA must call it (it contains __syncthreads()), so
+  // callers give each thread a valid t.
   __device__ static __forceinline__ void run(float2* buf, const float2* __restrict__ tw, int t) {
-    passes<0>(buf, tw, t);
+    passes<0, false, false>(buf, tw, t, NoLoad(), NoStore(), NoHook());
+  }
+
+  // The same transform with the input read through ld(q) in the first pass
+  // (x[q] = ld(q); with PIN only q outside [N/4, 3N/4) are asked for) and,
+  // with DSTG, the output handed to st(k, X[k]) by the last pass (with POUT
+  // only k outside [N/4, 3N/4)); buf is then scratch of N + N/16 values.
+  // The input never visits shared memory, and with DSTG neither does the
+  // output: NPASS - 1 shared-memory round trips instead of NPASS + 1 for a
+  // staged input and output, and 2 NPASS - 3 barriers instead of 2 NPASS + 1
+  // (3 instead of 7 for three passes).  Every thread of the CTA must call
+  // it.  Without DSTG the output is in buf after the call, as with run(),
+  // and the call ends with a barrier.
+  template <bool DSTG, class LD, class ST>
+  __device__ static __forceinline__ void run_io(float2* buf, const float2* __restrict__ tw, int t, const LD& ld,
+                                                const ST& st) {
+    passes<0, true, DSTG>(buf, tw, t, ld, st, NoHook());
+  }
+  // run_io with after_first() called when every thread has finished the
+  // first pass, i.e. has read all of its input through ld() (needs NPASS >= 2)
+  template <bool DSTG, class LD, class ST, class AF>
+  __device__ static __forceinline__ void run_io(float2* buf, const float2* __restrict__ tw, int t, const LD& ld,
+                                                const ST& st, const AF& after_first) {
+    static_assert(NPASS >= 2, "the first pass must end with a barrier");
+    passes<0, true, DSTG>(buf, tw, t, ld, st, after_first);
   }
 };
 

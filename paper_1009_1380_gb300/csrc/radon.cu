@@ -44,7 +44,6 @@ namespace {
 constexpr int kEcol = 32;              // FFT values per thread, column kernels
 constexpr int kErow = 16;              // FFT values per thread, row and ray kernels
 constexpr int kColFFTs = 4;            // packed column FFTs per CTA (8 columns)
-constexpr int kColHalf = kColFFTs / 2; // float4 loads of 4 real columns per image row
 constexpr int kThreads = 256;          // threads of the row / ray FFT kernels
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
@@ -69,26 +68,27 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * (2 * kColFFTs);
-  // deapodized columns: FFT f packs columns q0+2f (real part), q0+2f+1 (imag)
-#pragma unroll
-  for (int idx = tid; idx < kColHalf * N; idx += nthr) {
-    const int p = idx / kColHalf, h = idx % kColHalf;
-    const float4 v = *reinterpret_cast<const float4*>(img + (size_t)p * N + q0 + 4 * h);
-    const float4 d = *reinterpret_cast<const float4*>(dp + q0 + 4 * h);
+  // FFT f packs the deapodized columns q0+2f (real part) and q0+2f+1
+  // (imaginary part); the FFTs interleave over the lanes (f = tid mod 4), so
+  // that the first pass, which reads the image straight from global memory,
+  // has every 4 lanes read 32 contiguous bytes of one image row.  Input
+  // x[pos] = image row (pos + N/2) mod G; the zero half is skipped.
+  const int f = tid % kColFFTs, t = tid / kColFFTs;
+  const float2 dq = *reinterpret_cast<const float2*>(dp + q0 + 2 * f);
+  const auto ld = [&](int pos) -> float2 {
+    const int p = (pos + N / 2) & (G - 1);
+    const float2 v = *reinterpret_cast<const float2*>(img + (size_t)p * N + q0 + 2 * f);
     const float cp = dp[p];
-    const int pos = (p - N / 2) & (G - 1);
-    sm[(2 * h) * FFT::PADN + fpad(pos)] = make_float2(v.x * cp * d.x, v.y * cp * d.y);
-    sm[(2 * h + 1) * FFT::PADN + fpad(pos)] = make_float2(v.z * cp * d.z, v.w * cp * d.w);
-  }
-  __syncthreads();
-  FFT::run(sm + (tid / FFT::T) * FFT::PADN, tw, tid % FFT::T);
+    return make_float2(v.x * cp * dq.x, v.y * cp * dq.y);
+  };
+  FFT::template run_io<false>(sm + f * FFT::PADN, tw, t, ld, typename FFT::NoStore());
   // unpack the two real columns: C1 = (Z[b] + conj Z[G-b])/2, C2 = (Z[b] - conj Z[G-b])/(2i)
   for (int idx = tid; idx < (N + 1) * kColFFTs; idx += nthr) {
-    const int b = idx / kColFFTs, f = idx % kColFFTs;
-    const float2 Z = sm[f * FFT::PADN + fpad(b)];
-    const float2 Zm = sm[f * FFT::PADN + fpad((G - b) & (G - 1))];
+    const int b = idx / kColFFTs, fo = idx % kColFFTs;
+    const float2 Z = sm[fo * FFT::PADN + fpad(b)];
+    const float2 Zm = sm[fo * FFT::PADN + fpad((G - b) & (G - 1))];
     const float4 o = make_float4(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y), 0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
-    *reinterpret_cast<float4*>(H1 + (size_t)b * N + q0 + 2 * f) = o;
+    *reinterpret_cast<float4*>(H1 + (size_t)b * N + q0 + 2 * fo) = o;
   }
 }
 
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
 // 2. forward row transform + extension
 // ---------------------------------------------------------------------------
 template <int LOGG>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
     k_fwd_row(const float2* __restrict__ H1, float2* __restrict__ Hx, const float2* __restrict__ tw, int ldh,
               const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -108,24 +108,32 @@ __global__ void __launch_bounds__(kThreads)
   float2* buf = sm + f * FFT::PADN;
   const int b = blockIdx.x * RPC + f;
   const bool valid = b <= N;
-#pragma unroll
-  for (int q = t; q < N; q += T) {
-    const int pos = (q - N / 2) & (G - 1);
-    buf[fpad(pos)] = valid ? H1[(size_t)b * N + q] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  FFT::run(buf, tw, t);
-  if (!valid) return;
-  float2* dst = Hx + (size_t)(b + 2) * ldh;
-  for (int a = t; a < G + 6; a += T) dst[a] = buf[fpad(a & (G - 1))];
   // Hermitian mirrors: ext row -b (b = 1, 2) and ext row G-b (b = N-3..N-1)
   int mrow = -1;
   if (b == 1 || b == 2) mrow = 2 - b;
   else if (b >= N - 3 && b <= N - 1) mrow = (2 * N - b) + 2;
-  if (mrow >= 0) {
-    float2* md = Hx + (size_t)mrow * ldh;
-    for (int a = t; a < G + 6; a += T) md[a] = cconj(buf[fpad((-a) & (G - 1))]);
-  }
+  const float2* src = H1 + (size_t)(valid ? b : 0) * N;
+  float2* dst = Hx + (size_t)(b + 2) * ldh;
+  float2* md = Hx + (size_t)(mrow < 0 ? 0 : mrow) * ldh;
+  // FFT input x[pos] = H1[b, (pos + N/2) mod G]: the first pass reads the row
+  // straight from global memory (the zero half [N/2, G - N/2) is skipped);
+  // the last pass writes the extended row (columns G..G+5 repeat 0..5) and
+  // the conjugated mirror row straight to global memory
+  const auto ld = [&](int pos) -> float2 {
+    return valid ? src[(pos + N / 2) & (G - 1)] : make_float2(0.f, 0.f);
+  };
+  const auto st = [&](int a, float2 v) {
+    if (!valid) return;
+    dst[a] = v;
+    if (a < 6) dst[a + G] = v;
+    if (mrow >= 0) {
+      const int am = (-a) & (G - 1);
+      const float2 c = cconj(v);
+      md[am] = c;
+      if (am < 6) md[am + G] = c;
+    }
+  };
+  FFT::template run_io<true>(buf, tw, t, ld, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -300,8 +308,9 @@ __global__ void __launch_bounds__(kThreads)
   float2* buf = sm + f * FFT::PADN;
   const int j1 = 2 * (blockIdx.x * PPC + f), j2 = j1 + 1;
   const bool v1 = j1 < M, v2 = j2 < M;
-#pragma unroll
-  for (int k = t; k < NS; k += T) {
+  // the first pass reads the two rays straight from Q: Hermitian completion
+  // (k > K from Q[Ns - k], conjugated), (-1)^k centring, packed as q1 + i q2
+  const auto ld = [&](int k) -> float2 {
     const int kk = k <= K ? k : NS - k;
     const float sg = (kk & 1) ? -1.f : 1.f;
     float2 q1 = v1 ? Q[(size_t)j1 * ldq + kk] : make_float2(0.f, 0.f);
@@ -310,11 +319,10 @@ __global__ void __launch_bounds__(kThreads)
     q2 = cscale(q2, sg);
     if (kk == 0 || kk == K) { q1.y = 0.f; q2.y = 0.f; }
     if (k > K) { q1.y = -q1.y; q2.y = -q2.y; }
-    buf[fpad(k)] = make_float2(q1.x - q2.y, q1.y + q2.x);
-  }
-  __syncthreads();
-  FFT::run(buf, tw, t);
+    return make_float2(q1.x - q2.y, q1.y + q2.x);
+  };
   const float inv = 1.f / (float)NS;
+  // the last pass writes the sinogram rows straight to global memory
   if constexpr (CPLX) {
     // complex sinogram y = A x (interleaved re, im).  Its real part is the
     // real kernel's output; its imaginary part comes only from the Nyquist
@@ -323,18 +331,18 @@ __global__ void __launch_bounds__(kThreads)
     const float i1 = v1 ? -Q[(size_t)j1 * ldq + K].y * inv : 0.f;
     const float i2 = v2 ? -Q[(size_t)j2 * ldq + K].y * inv : 0.f;
     float2* out = reinterpret_cast<float2*>(sino);
-    for (int s = t; s < NS; s += T) {
-      const float2 w = buf[fpad(s)];
-      const float sg = ((s + K) & 1) ? -1.f : 1.f;
-      if (v1) out[(size_t)j1 * NS + s] = make_float2(w.x * inv, sg * i1);
-      if (v2) out[(size_t)j2 * NS + s] = make_float2(w.y * inv, sg * i2);
-    }
+    const auto st = [&](int s_, float2 w) {
+      const float sg = ((s_ + K) & 1) ? -1.f : 1.f;
+      if (v1) out[(size_t)j1 * NS + s_] = make_float2(w.x * inv, sg * i1);
+      if (v2) out[(size_t)j2 * NS + s_] = make_float2(w.y * inv, sg * i2);
+    };
+    FFT::template run_io<true>(buf, tw, t, ld, st);
   } else {
-    for (int s = t; s < NS; s += T) {
-      const float2 w = buf[fpad(s)];
-      if (v1) sino[(size_t)j1 * NS + s] = w.x * inv;
-      if (v2) sino[(size_t)j2 * NS + s] = w.y * inv;
-    }
+    const auto st = [&](int s_, float2 w) {
+      if (v1) sino[(size_t)j1 * NS + s_] = w.x * inv;
+      if (v2) sino[(size_t)j2 * NS + s_] = w.y * inv;
+    };
+    FFT::template run_io<true>(buf, tw, t, ld, st);
   }
 }
 
@@ -370,13 +378,15 @@ __global__ void __launch_bounds__(kThreads)
     }
     nyq[0][threadIdx.x] = a1;
     nyq[1][threadIdx.x] = a2;
+    __syncthreads();
+    FFT::run(buf, tw, t);
   } else {
-#pragma unroll
-    for (int s = t; s < NS; s += T)
-      buf[fpad(s)] = make_float2(v1 ? sino[(size_t)j1 * NS + s] : 0.f, v2 ? sino[(size_t)j2 * NS + s] : 0.f);
+    // the first pass reads the two sinogram rows straight from global memory
+    const auto ld = [&](int s_) -> float2 {
+      return make_float2(v1 ? sino[(size_t)j1 * NS + s_] : 0.f, v2 ? sino[(size_t)j2 * NS + s_] : 0.f);
+    };
+    FFT::template run_io<false>(buf, tw, t, ld, typename FFT::NoStore());
   }
-  __syncthreads();
-  FFT::run(buf, tw, t);
   const float inv = 1.f / (float)NS;
   for (int k = t; k <= K; k += T) {
     const float2 W = buf[fpad(k)];
@@ -675,37 +685,94 @@ __device__ __forceinline__ float2 wrapped(const float2* __restrict__ row, int a,
   return v;
 }
 
+// Persistent: each CTA takes groups of RPC rows (b = g RPC + f) in turn.  The
+// raw rows (G + 6 values: the wrapped columns included) arrive in shared
+// memory by bulk copies; the copy of the CTA's next group is issued as soon
+// as the first FFT pass has read the current one, so it lands while the
+// remaining passes and the stores run.  Mirror rows (5 rows) are read from
+// global memory.  Every wait is bounded: on a timeout the CTA records
+// CPCT_ERR_TIMEOUT, lets its copy in flight land and returns.
 template <int LOGG>
-__global__ void __launch_bounds__(kThreads)
+struct AdjRowSmem {
+  static constexpr int G = 1 << LOGG;
+  static constexpr int RPC = rows_per_cta<LOGG>();
+  static constexpr int RAWS = (G + 6 + 15) / 16 * 16;  // raw row stride (128-byte multiple)
+  static constexpr uint32_t RAW_BYTES = (uint32_t)(G + 6) * sizeof(float2);  // a multiple of 16
+  static constexpr size_t bytes = (size_t)RPC * (RAWS + SmemFFT<LOGG, kErow, +1, false, true>::PADN) * sizeof(float2) + 128;
+};
+
+template <int LOGG>
+__global__ void __launch_bounds__(kThreads, 3)
     k_adj_row(const float2* __restrict__ Ax, float2* __restrict__ H1, const float2* __restrict__ tw, int ldh,
-              const int* __restrict__ skip) {
+              int* __restrict__ err, const int* __restrict__ skip) {
   if (skip && *skip) return;
   // only X = -N/2 .. N/2-1 is kept: the FFT skips the other outputs (POUT)
   using FFT = SmemFFT<LOGG, kErow, +1, false, true>;
-  constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = rows_per_cta<LOGG>();
-  extern __shared__ float2 sm[];
-  const int f = threadIdx.x / T, t = threadIdx.x % T;
-  float2* buf = sm + f * FFT::PADN;
-  const int b = blockIdx.x * RPC + f;
-  const bool valid = b <= N;
-  int mrow = -1;
-  if (b == 1 || b == 2) mrow = 2 - b;
-  else if (b >= N - 3 && b <= N - 1) mrow = (2 * N - b) + 2;
-  const float2* row = Ax + (size_t)(b + 2) * ldh;
-  const float2* mr = Ax + (size_t)(mrow < 0 ? 0 : mrow) * ldh;
-#pragma unroll
-  for (int a = t; a < G; a += T) buf[fpad(a)] = valid ? row[a] : make_float2(0.f, 0.f);
-  // fold the extension: wrapped columns G..G+5 and, for rows 1, 2, N-3..N-1,
-  // the conjugated mirror row (each thread only touches its own elements)
-  if (valid)
-    for (int a = t; a < 6; a += T) buf[fpad(a)] = cadd(buf[fpad(a)], row[a + G]);
-  if (valid && mrow >= 0) {
-    for (int a = t; a < G; a += T) buf[fpad(a)] = cadd(buf[fpad(a)], cconj(wrapped(mr, (-a) & (G - 1), G)));
+  using S = AdjRowSmem<LOGG>;
+  constexpr int G = 1 << LOGG, N = G / 2, T = FFT::T, RPC = S::RPC;
+  constexpr int ngroups = (N + 1 + RPC - 1) / RPC;
+  extern __shared__ __align__(128) unsigned char adj_row_raw[];
+  float2* raw0 = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(adj_row_raw) + 127) & ~(uintptr_t)127);
+  __shared__ __align__(8) uint64_t bar;
+  const int tid = threadIdx.x;
+  const int f = tid / T, t = tid % T;
+  float2* raw = raw0 + f * S::RAWS;
+  float2* buf = raw0 + RPC * S::RAWS + f * FFT::PADN;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
   }
   __syncthreads();
-  FFT::run(buf, tw, t);
-  if (!valid) return;
-  for (int q = t; q < N; q += T) H1[(size_t)b * N + q] = buf[fpad((q - N / 2) & (G - 1))];
+  // thread 0: copy the rows of group g into the raw buffers
+  const auto issue = [&](int g) {
+    const int nv = min(RPC, N + 1 - g * RPC);
+    mbar_arrive_expect_tx(&bar, (uint32_t)nv * S::RAW_BYTES);
+    for (int ff = 0; ff < nv; ++ff)
+      bulk_load(raw0 + ff * S::RAWS, Ax + (size_t)(g * RPC + ff + 2) * ldh, S::RAW_BYTES, &bar);
+  };
+  int g = blockIdx.x;
+  if (tid == 0 && g < ngroups) issue(g);
+  uint32_t phase = 0;
+  for (; g < ngroups; g += gridDim.x) {
+    const bool ok = mbar_wait_bounded(&bar, phase, kWaitCycles);
+    // (also orders the previous group's last-pass reads of buf before this
+    // group's first-pass writes)
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) {
+        atomicOr(err, CPCT_ERR_TIMEOUT);
+        mbar_wait_bounded(&bar, phase, kWaitCycles / 4);
+      }
+      return;
+    }
+    phase ^= 1u;
+    const int b = g * RPC + f;
+    const bool valid = b <= N;
+    int mrow = -1;
+    if (b == 1 || b == 2) mrow = 2 - b;
+    else if (b >= N - 3 && b <= N - 1) mrow = (2 * N - b) + 2;
+    const float2* mr = Ax + (size_t)(mrow < 0 ? 0 : mrow) * ldh;
+    // fold the extension into the first pass's input: wrapped columns
+    // G..G+5 and, for rows 1, 2, N-3..N-1, the conjugated mirror row
+    const auto ld = [&](int a) -> float2 {
+      if (!valid) return make_float2(0.f, 0.f);
+      float2 v = raw[a];
+      if (a < 6) v = cadd(v, raw[a + G]);
+      if (mrow >= 0) v = cadd(v, cconj(wrapped(mr, (-a) & (G - 1), G)));
+      return v;
+    };
+    float2* out = H1 + (size_t)b * N;
+    const auto st = [&](int k, float2 v) {
+      if (valid) out[(k + N / 2) & (G - 1)] = v;
+    };
+    const int gn = g + gridDim.x;
+    const auto prefetch = [&]() {
+      if (tid == 0 && gn < ngroups) {
+        fence_proxy_async_smem();
+        issue(gn);
+      }
+    };
+    FFT::template run_io<true>(buf, tw, t, ld, st, prefetch);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -718,34 +785,30 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
   if (skip && *skip) return;
   // only Y = -N/2 .. N/2-1 is kept: the FFT skips the other outputs (POUT)
   using FFT = SmemFFT<LOGG, kEcol, +1, false, true>;
-  constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kEcol;
+  constexpr int G = 1 << LOGG, N = G / 2;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   const int q0 = blockIdx.x * (2 * kColFFTs);
-#pragma unroll
-  for (int idx = tid; idx < (N + 1) * kColFFTs; idx += nthr) {
-    const int b = idx / kColFFTs, f = idx % kColFFTs;
-    const float4 z = *reinterpret_cast<const float4*>(H1 + (size_t)b * N + q0 + 2 * f);  // z1 = (x,y), z2 = (z,w)
-    float2* buf = sm + f * FFT::PADN;
-    if (b == 0 || b == N) {
-      buf[fpad(b)] = make_float2(z.x, z.z);
-    } else {
-      buf[fpad(b)] = make_float2(0.5f * (z.x - z.w), 0.5f * (z.y + z.z));
-      buf[fpad(G - b)] = make_float2(0.5f * (z.x + z.w), 0.5f * (z.z - z.y));
-    }
-  }
-  __syncthreads();
-  FFT::run(sm + (tid / FFT::T) * FFT::PADN, tw, tid % FFT::T);
-  for (int idx = tid; idx < kColHalf * N; idx += nthr) {
-    const int p = idx / kColHalf, h = idx % kColHalf;
-    const int pos = (p - N / 2) & (G - 1);
-    const float2 w0 = sm[(2 * h) * FFT::PADN + fpad(pos)];
-    const float2 w1 = sm[(2 * h + 1) * FFT::PADN + fpad(pos)];
-    const float4 d = *reinterpret_cast<const float4*>(dp + q0 + 4 * h);
+  // FFT f packs columns q0+2f and q0+2f+1; the FFTs interleave over the lanes
+  // (f = tid mod 4).  The first pass reads H1 straight from global memory and
+  // Hermitian-symmetrises it: x[b] and x[G-b] both come from row b of the
+  // two columns z1 = (z.x, z.y), z2 = (z.z, z.w)
+  const int f = tid % kColFFTs, t = tid / kColFFTs;
+  const auto ld = [&](int pos) -> float2 {
+    const int b = pos <= N ? pos : G - pos;
+    const float4 z = *reinterpret_cast<const float4*>(H1 + (size_t)b * N + q0 + 2 * f);
+    if (b == 0 || b == N) return make_float2(z.x, z.z);
+    if (pos < N) return make_float2(0.5f * (z.x - z.w), 0.5f * (z.y + z.z));
+    return make_float2(0.5f * (z.x + z.w), 0.5f * (z.z - z.y));
+  };
+  // the last pass writes the cropped, deapodized columns straight to the image
+  const float2 dq = *reinterpret_cast<const float2*>(dp + q0 + 2 * f);
+  const auto st = [&](int k, float2 w) {
+    const int p = (k + N / 2) & (G - 1);
     const float cp = dp[p];
-    *reinterpret_cast<float4*>(img + (size_t)p * N + q0 + 4 * h) =
-        make_float4(w0.x * cp * d.x, w0.y * cp * d.y, w1.x * cp * d.z, w1.y * cp * d.w);
-  }
+    *reinterpret_cast<float2*>(img + (size_t)p * N + q0 + 2 * f) = make_float2(w.x * cp * dq.x, w.y * cp * dq.y);
+  };
+  FFT::template run_io<true>(sm + f * FFT::PADN, tw, t, ld, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -765,7 +828,7 @@ int set_attr_G() {
   if (cudaFuncSetAttribute(k_fwd_col<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(kColFFTs)) != cudaSuccess) return CPCT_ECUDA;
   if (cudaFuncSetAttribute(k_adj_col<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(kColFFTs)) != cudaSuccess) return CPCT_ECUDA;
   if (cudaFuncSetAttribute(k_fwd_row<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(rows_per_cta<LOGG>())) != cudaSuccess) return CPCT_ECUDA;
-  if (cudaFuncSetAttribute(k_adj_row<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(rows_per_cta<LOGG>())) != cudaSuccess) return CPCT_ECUDA;
+  if (cudaFuncSetAttribute(k_adj_row<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjRowSmem<LOGG>::bytes) != cudaSuccess) return CPCT_ECUDA;
   return CPCT_OK;
 }
 template <int LOGNS, bool CPLX>
@@ -821,8 +884,18 @@ template <int LOGG>
 void launch_adj_G(cpct_plan* p, float* img, const int* skip, cudaStream_t s) {
   constexpr int G = 1 << LOGG;
   constexpr int RPC = rows_per_cta<LOGG>();
+  const int groups = (p->n + 1 + RPC - 1) / RPC;
+  if (p->adj_row_grid <= 0) {
+    // persistent grid: every CTA resident at once
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_row<LOGG>, RPC * (G / kErow), AdjRowSmem<LOGG>::bytes);
+    p->adj_row_grid = std::max(1, sms * std::max(1, per_sm));
+  }
   cpct_prof_begin(p, KID_ADJ_ROW, s);
-  k_adj_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kErow), fft_smem<LOGG>(RPC), s>>>(p->d_Ax, p->d_H1, p->d_twG, p->ldh, skip);
+  k_adj_row<LOGG><<<std::min(groups, p->adj_row_grid), RPC * (G / kErow), AdjRowSmem<LOGG>::bytes, s>>>(
+      p->d_Ax, p->d_H1, p->d_twG, p->ldh, p->d_err, skip);
   cpct_prof_end(p, KID_ADJ_ROW, s);
   cpct_prof_begin(p, KID_ADJ_COL, s);
   k_adj_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kEcol, fft_smem<LOGG>(kColFFTs), s>>>(p->d_H1, p->d_deapod, img, p->d_twG, skip);
