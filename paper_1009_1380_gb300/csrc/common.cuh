@@ -99,6 +99,9 @@ struct cpct_plan {
   size_t device_bytes;
   int fwd_interp_grid[3];   // persistent grids of the forward gather per class (0 = not yet sized)
   int adj_row_grid;         // persistent grid of the adjoint row transform (0 = not yet sized)
+  int fwd_col_grid;         // persistent grid of the forward column transform (0 = not yet sized)
+  CUtensorMap tmap_img;     // TMA descriptor of the last image given to the forward column transform
+  const float* tmap_img_ptr;  // the image tmap_img was encoded for (null: none)
   // plans with bins of several sizes run the per-size launches concurrently:
   // two side streams fork from the launch stream and join it again
   cudaStream_t side[2];
@@ -130,6 +133,10 @@ struct PlanShared {
 void cpct_prof_begin(cpct_plan* p, int kid, cudaStream_t s);
 void cpct_prof_end(cpct_plan* p, int kid, cudaStream_t s);
 void cpct_prof_free(cpct_plan* p);
+
+// TMA descriptor of a caller's image for the forward column transform
+// (boxes of 8 columns by min(N, 256) rows), cached in the plan by address
+int cpct_image_cols_map(cpct_plan* p, const float* img, const CUtensorMap** out);
 
 // side streams and events of a plan (created with the plan and each clone)
 int cpct_plan_streams_create(cpct_plan* p);

@@ -235,6 +235,32 @@ bool bins_args_ok(int kind, int tile) {
 
 }  // namespace
 
+// TMA descriptor of a caller's N x N float32 image for the forward column
+// transform: boxes of 8 columns (32 bytes) by min(N, 256) rows.  Kept in the
+// plan with the image address it was encoded for, so a repeated address
+// costs nothing.
+int cpct_image_cols_map(cpct_plan* p, const float* img, const CUtensorMap** out) {
+  if (p->tmap_img_ptr != img) {
+    EncodeTiledFn enc = get_encode_fn();
+    if (!enc) return CPCT_EUNSUPPORTED;
+    cuuint64_t dims[2] = {(cuuint64_t)p->n, (cuuint64_t)p->n};
+    cuuint64_t strides[1] = {(cuuint64_t)p->n * sizeof(float)};
+    cuuint32_t box[2] = {8u, (cuuint32_t)std::min(p->n, 256)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = enc(&p->tmap_img, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(img), dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+      p->tmap_img_ptr = nullptr;
+      return CPCT_ECUDA;
+    }
+    p->tmap_img_ptr = img;
+  }
+  *out = &p->tmap_img;
+  return CPCT_OK;
+}
+
+
 // ---------------------------------------------------------------------------
 // bin lists (exported for host-side tests: no GPU needed)
 // ---------------------------------------------------------------------------

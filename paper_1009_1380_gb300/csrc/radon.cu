@@ -57,38 +57,94 @@ constexpr size_t fft_smem(int nfft) { return (size_t)nfft * SmemFFT<LOG, kErow, 
 // ---------------------------------------------------------------------------
 // 1. forward column transform
 // ---------------------------------------------------------------------------
+// Persistent: each CTA takes blocks of 8 image columns in turn (FFT f packs
+// the deapodized columns q0+2f (real part) and q0+2f+1 (imaginary part)).  A
+// block arrives in shared memory by 2-D TMA tile copies (8 columns x min(N,
+// 256) rows each); the copy of the CTA's next block is issued as soon as the
+// first FFT pass has read the current one, so it lands while the other
+// passes, the unpack and the stores run.  The deapodization vector is staged
+// once per CTA.  Every wait is bounded: on a timeout the CTA records
+// CPCT_ERR_TIMEOUT, lets its copy in flight land and returns.
 template <int LOGG>
-__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol)
-    k_fwd_col(const float* __restrict__ img, const float* __restrict__ dp, float2* __restrict__ H1,
-              const float2* __restrict__ tw, const int* __restrict__ skip) {
+struct FwdColSmem {
+  static constexpr int G = 1 << LOGG, N = G / 2;
+  static constexpr int BR = N < 256 ? N : 256;  // rows per TMA box
+  static constexpr int FFTS = kColFFTs * SmemFFT<LOGG, kEcol, -1, true, false>::PADN;  // complex values
+  static constexpr size_t bytes = (size_t)N * 8 * sizeof(float)  // the block: N rows x 8 columns
+                                  + (size_t)FFTS * sizeof(float2) + (size_t)N * sizeof(float) + 128;
+};
+
+template <int LOGG>
+__global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol, LOGG >= 12 ? 1 : 2)
+    k_fwd_col(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ dp, float2* __restrict__ H1,
+              const float2* __restrict__ tw, int* __restrict__ err, const int* __restrict__ skip) {
   if (skip && *skip) return;
   // the padding half [N/2, G - N/2) is zero: the FFT skips it (PIN)
   using FFT = SmemFFT<LOGG, kEcol, -1, true, false>;
+  using S = FwdColSmem<LOGG>;
   constexpr int G = 1 << LOGG, N = G / 2, nthr = kColFFTs * G / kEcol;
-  extern __shared__ float2 sm[];
+  constexpr int nblocks = N / (2 * kColFFTs);
+  extern __shared__ __align__(128) unsigned char fwd_col_raw[];
+  float* blk = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(fwd_col_raw) + 127) & ~(uintptr_t)127);
+  float2* sm = reinterpret_cast<float2*>(blk + N * 8);
+  float* sdp = reinterpret_cast<float*>(sm + S::FFTS);
+  __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x;
-  const int q0 = blockIdx.x * (2 * kColFFTs);
-  // FFT f packs the deapodized columns q0+2f (real part) and q0+2f+1
-  // (imaginary part); the FFTs interleave over the lanes (f = tid mod 4), so
-  // that the first pass, which reads the image straight from global memory,
-  // has every 4 lanes read 32 contiguous bytes of one image row.  Input
-  // x[pos] = image row (pos + N/2) mod G; the zero half is skipped.
-  const int f = tid % kColFFTs, t = tid / kColFFTs;
-  const float2 dq = *reinterpret_cast<const float2*>(dp + q0 + 2 * f);
-  const auto ld = [&](int pos) -> float2 {
-    const int p = (pos + N / 2) & (G - 1);
-    const float2 v = *reinterpret_cast<const float2*>(img + (size_t)p * N + q0 + 2 * f);
-    const float cp = dp[p];
-    return make_float2(v.x * cp * dq.x, v.y * cp * dq.y);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  for (int i = tid; i < N; i += nthr) sdp[i] = dp[i];
+  __syncthreads();
+  // thread 0: copy the 8 columns of block q of every row into blk
+  const auto issue = [&](int q) {
+    mbar_arrive_expect_tx(&bar, (uint32_t)(N * 8 * sizeof(float)));
+    for (int r = 0; r < N; r += S::BR) tma_load_2d(blk + r * 8, &tmap, q * 2 * kColFFTs, r, &bar);
   };
-  FFT::template run_io<false>(sm + f * FFT::PADN, tw, t, ld, typename FFT::NoStore());
-  // unpack the two real columns: C1 = (Z[b] + conj Z[G-b])/2, C2 = (Z[b] - conj Z[G-b])/(2i)
-  for (int idx = tid; idx < (N + 1) * kColFFTs; idx += nthr) {
-    const int b = idx / kColFFTs, fo = idx % kColFFTs;
-    const float2 Z = sm[fo * FFT::PADN + fpad(b)];
-    const float2 Zm = sm[fo * FFT::PADN + fpad((G - b) & (G - 1))];
-    const float4 o = make_float4(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y), 0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
-    *reinterpret_cast<float4*>(H1 + (size_t)b * N + q0 + 2 * fo) = o;
+  int q = blockIdx.x;
+  if (tid == 0 && q < nblocks) issue(q);
+  // the FFTs interleave over the lanes (f = tid mod 4): the first pass's
+  // shared-memory reads of one row are 32 contiguous bytes per 4 lanes
+  const int f = tid % kColFFTs, t = tid / kColFFTs;
+  uint32_t phase = 0;
+  for (; q < nblocks; q += gridDim.x) {
+    const bool ok = mbar_wait_bounded(&bar, phase, kWaitCycles);
+    // (also orders the previous block's unpack reads of sm before this
+    // block's first-pass writes)
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) {
+        atomicOr(err, CPCT_ERR_TIMEOUT);
+        mbar_wait_bounded(&bar, phase, kWaitCycles / 4);
+      }
+      return;
+    }
+    phase ^= 1u;
+    const int q0 = q * (2 * kColFFTs);
+    const float dq0 = sdp[q0 + 2 * f], dq1 = sdp[q0 + 2 * f + 1];
+    // input x[pos] = image row (pos + N/2) mod G (the zero half is skipped)
+    const auto ld = [&](int pos) -> float2 {
+      const int p = (pos + N / 2) & (G - 1);
+      const float2 v = *reinterpret_cast<const float2*>(blk + p * 8 + 2 * f);
+      const float cp = sdp[p];
+      return make_float2(v.x * cp * dq0, v.y * cp * dq1);
+    };
+    const int qn = q + gridDim.x;
+    const auto prefetch = [&]() {
+      if (tid == 0 && qn < nblocks) {
+        fence_proxy_async_smem();
+        issue(qn);
+      }
+    };
+    FFT::template run_io<false>(sm + f * FFT::PADN, tw, t, ld, typename FFT::NoStore(), prefetch);
+    // unpack the two real columns: C1 = (Z[b] + conj Z[G-b])/2, C2 = (Z[b] - conj Z[G-b])/(2i)
+    for (int idx = tid; idx < (N + 1) * kColFFTs; idx += nthr) {
+      const int b = idx / kColFFTs, fo = idx % kColFFTs;
+      const float2 Z = sm[fo * FFT::PADN + fpad(b)];
+      const float2 Zm = sm[fo * FFT::PADN + fpad((G - b) & (G - 1))];
+      const float4 o =
+          make_float4(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y), 0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
+      *reinterpret_cast<float4*>(H1 + (size_t)b * N + q0 + 2 * fo) = o;
+    }
   }
 }
 
@@ -825,7 +881,7 @@ int set_attr_G() {
   max_carveout(k_adj_col<LOGG>);
   max_carveout(k_fwd_row<LOGG>);
   max_carveout(k_adj_row<LOGG>);
-  if (cudaFuncSetAttribute(k_fwd_col<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(kColFFTs)) != cudaSuccess) return CPCT_ECUDA;
+  if (cudaFuncSetAttribute(k_fwd_col<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FwdColSmem<LOGG>::bytes) != cudaSuccess) return CPCT_ECUDA;
   if (cudaFuncSetAttribute(k_adj_col<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(kColFFTs)) != cudaSuccess) return CPCT_ECUDA;
   if (cudaFuncSetAttribute(k_fwd_row<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem<LOGG>(rows_per_cta<LOGG>())) != cudaSuccess) return CPCT_ECUDA;
   if (cudaFuncSetAttribute(k_adj_row<LOGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AdjRowSmem<LOGG>::bytes) != cudaSuccess) return CPCT_ECUDA;
@@ -846,15 +902,28 @@ int set_attr_Ns() {
 }
 
 template <int LOGG>
-void launch_fwd_G(cpct_plan* p, const float* img, const int* skip, cudaStream_t s) {
+int launch_fwd_G(cpct_plan* p, const float* img, const int* skip, cudaStream_t s) {
   constexpr int G = 1 << LOGG;
+  const int nthr = kColFFTs * G / kEcol, nblocks = p->n / (2 * kColFFTs);
+  if (p->fwd_col_grid <= 0) {
+    // persistent grid: every CTA resident at once
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_col<LOGG>, nthr, FwdColSmem<LOGG>::bytes);
+    p->fwd_col_grid = std::max(1, sms * std::max(1, per_sm));
+  }
+  const CUtensorMap* tm = nullptr;
+  if (cpct_image_cols_map(p, img, &tm) != CPCT_OK) return CPCT_ECUDA;
   cpct_prof_begin(p, KID_FWD_COL, s);
-  k_fwd_col<LOGG><<<p->n / (2 * kColFFTs), kColFFTs * G / kEcol, fft_smem<LOGG>(kColFFTs), s>>>(img, p->d_deapod, p->d_H1, p->d_twG, skip);
+  k_fwd_col<LOGG><<<std::min(nblocks, p->fwd_col_grid), nthr, FwdColSmem<LOGG>::bytes, s>>>(
+      *tm, p->d_deapod, p->d_H1, p->d_twG, p->d_err, skip);
   cpct_prof_end(p, KID_FWD_COL, s);
   constexpr int RPC = rows_per_cta<LOGG>();
   cpct_prof_begin(p, KID_FWD_ROW, s);
   k_fwd_row<LOGG><<<(p->n + 1 + RPC - 1) / RPC, RPC * (G / kErow), fft_smem<LOGG>(RPC), s>>>(p->d_H1, p->d_Hx, p->d_twG, p->ldh, skip);
   cpct_prof_end(p, KID_FWD_ROW, s);
+  return CPCT_OK;
 }
 template <int LOGNS>
 void launch_fwd_Ns(cpct_plan* p, float* sino, bool cplx, const int* skip, cudaStream_t s) {
@@ -993,7 +1062,11 @@ namespace {
 // forward operator; `sino` is M x Ns float32 (cplx = false) or M x Ns
 // interleaved complex64 (cplx = true)
 int launch_fwd_impl(cpct_plan* p, const float* d_img, float* d_sino, bool cplx, const int* skip, cudaStream_t s) {
-#define FG(L) launch_fwd_G<L>(p, d_img, skip, s)
+#define FG(L)                                        \
+  {                                                  \
+    const int rc_ = launch_fwd_G<L>(p, d_img, skip, s); \
+    if (rc_ != CPCT_OK) return rc_;                  \
+  }
   CPCT_DISPATCH_G(p->logG, FG);
 #undef FG
   FwdInterpArgs a;
