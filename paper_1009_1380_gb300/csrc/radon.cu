@@ -698,38 +698,33 @@ __global__ void __launch_bounds__(32) k_adj_spread_cols(const AdjSpreadArgs a) {
 }
 
 // 7. fixed-order sum of the partial tiles of a split T x T bin (piece order
-// q = 0, 1, ...); one block per split bin
-template <int T>
-constexpr int reduce_threads() { return T * T < 1024 ? T * T : 1024; }
+// q = 0, 1, ...); kReduceThreads threads per part of a bin, blockIdx.y the
+// part.  Every thread issues the loads of up to 16 pieces at once (one
+// round trip for a bin of at most 16 pieces) and adds them in piece order.
+constexpr int kReduceThreads = 256;
 
 template <int T>
-__global__ void __launch_bounds__(reduce_threads<T>())
+__global__ void __launch_bounds__(kReduceThreads)
     k_adj_reduce(const int4* __restrict__ split, const float2* __restrict__ partials, float2* __restrict__ Ax,
                  int ldh, int ext_rows, const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int4 sp = split[blockIdx.x];
   const int TC = sp.x & 0xffff, TR = sp.x >> 16;
   constexpr size_t S = (size_t)T * T;
-  for (int i = threadIdx.x; i < T * T; i += reduce_threads<T>()) {
-    const float2* src = partials + (size_t)sp.y + i;
-    // 16 independent loads in flight, summed in piece order
-    float2 sum = make_float2(0.f, 0.f);
-    int q = 0;
-    for (; q + 16 <= sp.z; q += 16) {
-      float2 v[16];
+  const int i = blockIdx.y * kReduceThreads + threadIdx.x;
+  if (i >= T * T) return;
+  const float2* src = partials + (size_t)sp.y + i;
+  float2 sum = make_float2(0.f, 0.f);
+  for (int q0 = 0; q0 < sp.z; q0 += 16) {
+    float2 v[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = src[(size_t)(q + k) * S];
+    for (int k = 0; k < 16; ++k) v[k] = q0 + k < sp.z ? src[(size_t)(q0 + k) * S] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) sum = cadd(sum, v[k]);
-    }
-    for (; q + 4 <= sp.z; q += 4) {
-      const float2 v0 = src[(q + 0) * S], v1 = src[(q + 1) * S], v2 = src[(q + 2) * S], v3 = src[(q + 3) * S];
-      sum = cadd(cadd(cadd(cadd(sum, v0), v1), v2), v3);
-    }
-    for (; q < sp.z; ++q) sum = cadd(sum, src[q * S]);
-    const int gr = TR + i / T, gc = TC + i % T;
-    if (gr < ext_rows && gc < ldh) Ax[(size_t)gr * ldh + gc] = sum;
+    for (int k = 0; k < 16; ++k)
+      if (q0 + k < sp.z) sum = cadd(sum, v[k]);
   }
+  const int gr = TR + i / T, gc = TC + i % T;
+  if (gr < ext_rows && gc < ldh) Ax[(size_t)gr * ldh + gc] = sum;
 }
 
 // ---------------------------------------------------------------------------
@@ -1155,9 +1150,11 @@ int launch_adj_impl(cpct_plan* p, const float* d_sino, float* d_img, bool cplx, 
     const int n = p->split_cls[c + 1] - p->split_cls[c];
     if (n <= 0) return false;
     const int4* sp = p->d_split + p->split_cls[c];
-    if (c == 0) k_adj_reduce<16><<<n, reduce_threads<16>(), 0, si>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
-    else if (c == 1) k_adj_reduce<32><<<n, reduce_threads<32>(), 0, si>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
-    else k_adj_reduce<64><<<n, reduce_threads<64>(), 0, si>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+    const int T = c == 0 ? 16 : c == 1 ? 32 : 64;
+    const dim3 grid(n, (T * T + kReduceThreads - 1) / kReduceThreads);
+    if (c == 0) k_adj_reduce<16><<<grid, kReduceThreads, 0, si>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+    else if (c == 1) k_adj_reduce<32><<<grid, kReduceThreads, 0, si>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
+    else k_adj_reduce<64><<<grid, kReduceThreads, 0, si>>>(sp, partials, p->d_Ax, p->ldh, p->ext_rows, skip);
     return true;
   };
   if (nc == 1) {
