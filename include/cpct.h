@@ -276,6 +276,26 @@ int cpct_plan_set_bins(cpct_plan* plan, int which, int kind, int tile, cudaStrea
 #define CPCT_ROUNDS_COLUMNS 5
 int cpct_plan_set_rounds(cpct_plan* plan, int lanes, cudaStream_t stream);
 int cpct_plan_rounds(const cpct_plan* plan);
+
+/* Graph replay of the operators.  The paper has no counterpart: this is a
+ * launch mechanism of this library.  With enable = 1, radon_fwd, radon_adj,
+ * their host-buffer variants and radon_pair_host_stream capture the kernels
+ * of one application into a CUDA graph the first time they see a given
+ * (operator, input address, output address, profiling mask) and replay that
+ * graph on the caller's stream on later calls with the same addresses: the
+ * same kernels with the same arguments, so the results are bit for bit those
+ * of direct launches, without the per-kernel launch cost of the host.  At
+ * most 8 graphs are kept per plan (least recently used dropped); changing the
+ * bin plans, caps or round width drops them all.  A call made while the
+ * caller's stream is being captured launches directly (into the caller's
+ * graph).  The first call with new addresses captures and instantiates a
+ * graph (host work of the order of 100 us); callers that pass new buffers on
+ * every call should leave graph mode off (the default).  enable = 0 turns the
+ * mode off and frees the graphs.  Returns CPCT_EINVAL for a NULL plan or an
+ * enable other than 0 or 1.
+ * cpct_plan_graphs returns the number of graphs held (CPCT_EINVAL for NULL). */
+int cpct_plan_set_graphs(cpct_plan* plan, int enable);
+int cpct_plan_graphs(const cpct_plan* plan);
 int cpct_plan_bins(const cpct_plan* plan, int* fwd_kind, int* fwd_tile, int* adj_kind, int* adj_tile,
                    int* fwd_class_bins, int* adj_class_bins);
 

@@ -71,6 +71,8 @@ def lib():
         L.cpct_plan_set_bins.argtypes = [vp, i, i, i, vp]
         L.cpct_plan_set_rounds.argtypes = [vp, i, vp]
         L.cpct_plan_rounds.argtypes = [vp]
+        L.cpct_plan_set_graphs.argtypes = [vp, i]
+        L.cpct_plan_graphs.argtypes = [vp]
         L.cpct_plan_bins.argtypes = [vp] + [ctypes.POINTER(i)] * 4 + [vp, vp]
         L.cpct_debug_binplan.argtypes = [ctypes.POINTER(Geom), i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp,
                                          ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -248,6 +250,14 @@ class Plan:
 
     def rounds(self):
         return int(lib().cpct_plan_rounds(self._h))
+
+    def set_graphs(self, enable=True):
+        """Graph replay of the operators (cpct_plan_set_graphs)."""
+        check(lib().cpct_plan_set_graphs(self._h, 1 if enable else 0), "cpct_plan_set_graphs")
+
+    def graphs(self):
+        """Number of captured operator graphs held by the plan."""
+        return int(lib().cpct_plan_graphs(self._h))
 
     def bins(self):
         """Installed bin plans: {'fwd': (kind, tile, bins per class), 'adj': ...}."""

@@ -9,12 +9,12 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 extern "C" int radon_fwd(cpct_plan* plan, const float* d_img, float* d_sino, cudaStream_t stream) {
   if (!plan || !d_img || !d_sino || !aligned16(d_img) || !aligned16(d_sino)) return CPCT_EINVAL;
-  return cpct_launch_fwd(plan, d_img, d_sino, stream);
+  return cpct_graph_run(plan, 0, d_img, d_sino, stream);
 }
 
 extern "C" int radon_adj(cpct_plan* plan, const float* d_sino, float* d_img, cudaStream_t stream) {
   if (!plan || !d_img || !d_sino || !aligned16(d_img) || !aligned16(d_sino)) return CPCT_EINVAL;
-  return cpct_launch_adj(plan, d_sino, d_img, stream);
+  return cpct_graph_run(plan, 1, d_sino, d_img, stream);
 }
 
 extern "C" int radon_fwd_c(cpct_plan* plan, const float* d_img, void* d_sino_c, cudaStream_t stream) {
@@ -58,7 +58,7 @@ extern "C" int radon_fwd_host(cpct_plan* p, const float* h_img, float* h_sino, c
   int rc = ensure_staging(p);
   if (rc) return rc;
   CPCT_CUDA_TRY(cudaMemcpyAsync(p->d_stage_img, h_img, sizeof(float) * (size_t)p->n * p->n, cudaMemcpyHostToDevice, s));
-  rc = cpct_launch_fwd(p, p->d_stage_img, p->d_stage_sino, s);
+  rc = cpct_graph_run(p, 0, p->d_stage_img, p->d_stage_sino, s);
   if (rc) return rc;
   CPCT_CUDA_TRY(cudaMemcpyAsync(h_sino, p->d_stage_sino, sizeof(float) * (size_t)p->m * p->ns, cudaMemcpyDeviceToHost, s));
   CPCT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -70,7 +70,7 @@ extern "C" int radon_adj_host(cpct_plan* p, const float* h_sino, float* h_img, c
   int rc = ensure_staging(p);
   if (rc) return rc;
   CPCT_CUDA_TRY(cudaMemcpyAsync(p->d_stage_sino, h_sino, sizeof(float) * (size_t)p->m * p->ns, cudaMemcpyHostToDevice, s));
-  rc = cpct_launch_adj(p, p->d_stage_sino, p->d_stage_img, s);
+  rc = cpct_graph_run(p, 1, p->d_stage_sino, p->d_stage_img, s);
   if (rc) return rc;
   CPCT_CUDA_TRY(cudaMemcpyAsync(h_img, p->d_stage_img, sizeof(float) * (size_t)p->n * p->n, cudaMemcpyDeviceToHost, s));
   CPCT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -123,9 +123,9 @@ extern "C" int radon_pair_host_stream(cpct_plan* p, const float* const* h_imgs, 
     // same plan and stream; with one plan both sets share stream s)
     if (!ok(cudaStreamWaitEvent(cs, ev[IN][k], 0))) break;
     if (i >= 2 && !ok(cudaStreamWaitEvent(cs, ev[OUT][k], 0))) break;
-    if ((rc = cpct_launch_fwd(plan_of[k], img, sino, cs)) != CPCT_OK) break;
+    if ((rc = cpct_graph_run(plan_of[k], 0, img, sino, cs)) != CPCT_OK) break;
     if (!ok(cudaEventRecord(ev[FWD][k], cs))) break;
-    if ((rc = cpct_launch_adj(plan_of[k], sino, out, cs)) != CPCT_OK) break;
+    if ((rc = cpct_graph_run(plan_of[k], 1, sino, out, cs)) != CPCT_OK) break;
     if (!ok(cudaEventRecord(ev[ADJ][k], cs))) break;
     // downloads: the sinogram while the adjoint runs, then the adjoint
     if (!ok(cudaStreamWaitEvent(down, ev[FWD][k], 0))) break;

@@ -112,6 +112,10 @@ struct cpct_plan {
   struct PlanShared* shared;  // read-only geometry shared with clones (refcounted)
   long long launches;       // kernels launched by this plan's operators
   CpctProfiler* prof;       // NULL unless profiling is enabled
+  // graph replay of the operators (cpct_plan_set_graphs): 0 = direct launches
+  int graph_mode;
+  struct GraphCache* graphs;  // captured operator graphs (NULL: none yet)
+  struct GraphCapture* capturing;  // set while an operator is being captured
 };
 
 // Read-only data of one geometry, shared by a plan and its clones: the
@@ -137,6 +141,17 @@ void cpct_prof_free(cpct_plan* p);
 // TMA descriptor of a caller's image for the forward column transform
 // (boxes of 8 columns by min(N, 256) rows), cached in the plan by address
 int cpct_image_cols_map(cpct_plan* p, const float* img, const CUtensorMap** out);
+
+// graph replay of the operators (graphs.cu): run op 0 (forward, in = image,
+// out = sinogram) or 1 (adjoint, in = sinogram, out = image) through the
+// plan's graph cache when graph mode is on, else launch directly
+int cpct_graph_run(cpct_plan* p, int op, const void* in, void* out, cudaStream_t s);
+// drop every captured graph (the launch configuration changed)
+void cpct_graph_clear(cpct_plan* p);
+// free the graph cache (plan destruction)
+void cpct_graph_free(cpct_plan* p);
+// while capturing: record a profiling event as a graph node (profile.cu)
+void cpct_graph_prof_event(cpct_plan* p, int kid, bool begin, cudaEvent_t ev, cudaStream_t s);
 
 // side streams and events of a plan (created with the plan and each clone)
 int cpct_plan_streams_create(cpct_plan* p);

@@ -170,6 +170,7 @@ EncodeTiledFn get_encode_fn() {
 
 void free_plan(cpct_plan* p) {
   if (!p) return;
+  cpct_graph_free(p);
   cpct_prof_free(p);
   cpct_plan_streams_destroy(p);
   // per-plan workspaces
@@ -547,6 +548,7 @@ int auto_fwd_cap(long long samples, int resident) {
 // forward work items of the installed bin plan with `cap` samples per item
 // (kCapAuto: auto_fwd_cap)
 int install_fwd_items(cpct_plan* p, int cap, cudaStream_t s) {
+  cpct_graph_clear(p);  // captured graphs hold the old work items
   if (cap == kCapAuto)
     cap = auto_fwd_cap(p->shared->fwd_ptr.empty() ? 0 : p->shared->fwd_ptr.back(),
                        share(cpct_gridding_resident(0, p->fwd_tile ? p->fwd_tile : CPCT_TILE, 0),
@@ -566,6 +568,7 @@ int install_fwd_items(cpct_plan* p, int cap, cudaStream_t s) {
 // adjoint work items (and split list, partial tiles) with `cap` rounds per
 // item (kCapAuto: auto_adj_cap)
 int install_adj_items(cpct_plan* p, int cap, cudaStream_t s) {
+  cpct_graph_clear(p);  // captured graphs hold the old work items
   if (cap == kCapAuto)
     cap = auto_adj_cap(p->shared->round_ptr.empty() ? 0 : p->shared->round_ptr.back(),
                        share(cpct_gridding_resident(1, p->adj_tile ? p->adj_tile : CPCT_TILE, p->round_lanes == 64 ? 64 : 32),
@@ -808,6 +811,8 @@ extern "C" int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream
   p->d_stage_img = p->d_stage_sino = nullptr;
   p->d_err = nullptr;
   p->prof = nullptr;
+  p->graphs = nullptr;
+  p->capturing = nullptr;
   p->launches = 0;
   p->device_bytes = 0;
   p->shared->refs++;

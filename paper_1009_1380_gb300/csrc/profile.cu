@@ -35,6 +35,11 @@ void cpct_prof_begin(cpct_plan* p, int kid, cudaStream_t s) {
   p->launches++;
   CpctProfiler* pr = p->prof;
   if (!pr || !(pr->mask & (1u << kid))) return;
+  if (p->capturing) {
+    // inside a graph capture: an event-record node whose event the replay sets
+    cpct_graph_prof_event(p, kid, true, pr->get(), s);
+    return;
+  }
   pr->open_a = pr->get();
   pr->open_kid = kid;
   if (pr->open_a) cudaEventRecord(pr->open_a, s);
@@ -42,7 +47,12 @@ void cpct_prof_begin(cpct_plan* p, int kid, cudaStream_t s) {
 
 void cpct_prof_end(cpct_plan* p, int kid, cudaStream_t s) {
   CpctProfiler* pr = p->prof;
-  if (!pr || !(pr->mask & (1u << kid)) || pr->open_kid != kid || !pr->open_a) return;
+  if (!pr || !(pr->mask & (1u << kid))) return;
+  if (p->capturing) {
+    cpct_graph_prof_event(p, kid, false, pr->get(), s);
+    return;
+  }
+  if (pr->open_kid != kid || !pr->open_a) return;
   cudaEvent_t b = pr->get();
   if (!b) return;
   cudaEventRecord(b, s);
@@ -61,6 +71,16 @@ void cpct_prof_free(cpct_plan* p) {
   delete p->prof;
   p->prof = nullptr;
 }
+
+// events of the plan's profiler pool, for graph replays (graphs.cu)
+cudaEvent_t cpct_prof_event(cpct_plan* p) { return p->prof ? p->prof->get() : nullptr; }
+void cpct_prof_push(cpct_plan* p, int kid, cudaEvent_t a, cudaEvent_t b) {
+  if (p->prof) p->prof->recs.push_back({kid, a, b});
+}
+void cpct_prof_release(cpct_plan* p, cudaEvent_t e) {
+  if (p->prof && e) p->prof->pool.push_back(e);
+}
+unsigned cpct_prof_mask(const cpct_plan* p) { return p->prof ? p->prof->mask : 0u; }
 
 extern "C" int cpct_profile_enable(cpct_plan* p, unsigned mask) {
   if (!p) return CPCT_EINVAL;
