@@ -141,6 +141,8 @@ void cpct_prof_free(cpct_plan* p);
 // TMA descriptor of a caller's image for the forward column transform
 // (boxes of 8 columns by min(N, 256) rows), cached in the plan by address
 int cpct_image_cols_map(cpct_plan* p, const float* img, const CUtensorMap** out);
+// image columns per block of the forward column transform (radon.cu)
+int cpct_col_block_width();
 
 // graph replay of the operators (graphs.cu): run op 0 (forward, in = image,
 // out = sinogram) or 1 (adjoint, in = sinogram, out = image) through the

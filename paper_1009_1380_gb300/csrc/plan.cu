@@ -246,7 +246,7 @@ int cpct_image_cols_map(cpct_plan* p, const float* img, const CUtensorMap** out)
     if (!enc) return CPCT_EUNSUPPORTED;
     cuuint64_t dims[2] = {(cuuint64_t)p->n, (cuuint64_t)p->n};
     cuuint64_t strides[1] = {(cuuint64_t)p->n * sizeof(float)};
-    cuuint32_t box[2] = {8u, (cuuint32_t)std::min(p->n, 256)};
+    cuuint32_t box[2] = {(cuuint32_t)cpct_col_block_width(), (cuuint32_t)std::min(p->n, 256)};
     cuuint32_t estr[2] = {1, 1};
     CUresult cr = enc(&p->tmap_img, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(img), dims, strides, box,
                       estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -43,7 +43,7 @@ namespace {
 
 constexpr int kEcol = 32;              // FFT values per thread, column kernels
 constexpr int kErow = 16;              // FFT values per thread, row and ray kernels
-constexpr int kColFFTs = 4;            // packed column FFTs per CTA (8 columns)
+constexpr int kColFFTs = 4;            // packed column FFTs per CTA (2 kColFFTs image columns)
 constexpr int kThreads = 256;          // threads of the row / ray FFT kernels
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
@@ -57,9 +57,9 @@ constexpr size_t fft_smem(int nfft) { return (size_t)nfft * SmemFFT<LOG, kErow, 
 // ---------------------------------------------------------------------------
 // 1. forward column transform
 // ---------------------------------------------------------------------------
-// Persistent: each CTA takes blocks of 8 image columns in turn (FFT f packs
+// Persistent: each CTA takes blocks of 2 kColFFTs image columns in turn (FFT f packs
 // the deapodized columns q0+2f (real part) and q0+2f+1 (imaginary part)).  A
-// block arrives in shared memory by 2-D TMA tile copies (8 columns x min(N,
+// block arrives in shared memory by 2-D TMA tile copies (all its columns x min(N,
 // 256) rows each); the copy of the CTA's next block is issued as soon as the
 // first FFT pass has read the current one, so it lands while the other
 // passes, the unpack and the stores run.  The deapodization vector is staged
@@ -70,7 +70,8 @@ struct FwdColSmem {
   static constexpr int G = 1 << LOGG, N = G / 2;
   static constexpr int BR = N < 256 ? N : 256;  // rows per TMA box
   static constexpr int FFTS = kColFFTs * SmemFFT<LOGG, kEcol, -1, true, false>::PADN;  // complex values
-  static constexpr size_t bytes = (size_t)N * 8 * sizeof(float)  // the block: N rows x 8 columns
+  static constexpr int CW = 2 * kColFFTs;        // image columns per block
+  static constexpr size_t bytes = (size_t)N * CW * sizeof(float)  // the block: N rows x CW columns
                                   + (size_t)FFTS * sizeof(float2) + (size_t)N * sizeof(float) + 128;
 };
 
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol, LOGG >= 12 ? 1 :
   constexpr int nblocks = N / (2 * kColFFTs);
   extern __shared__ __align__(128) unsigned char fwd_col_raw[];
   float* blk = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(fwd_col_raw) + 127) & ~(uintptr_t)127);
-  float2* sm = reinterpret_cast<float2*>(blk + N * 8);
+  float2* sm = reinterpret_cast<float2*>(blk + N * S::CW);
   float* sdp = reinterpret_cast<float*>(sm + S::FFTS);
   __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x;
@@ -96,10 +97,10 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol, LOGG >= 12 ? 1 :
   }
   for (int i = tid; i < N; i += nthr) sdp[i] = dp[i];
   __syncthreads();
-  // thread 0: copy the 8 columns of block q of every row into blk
+  // thread 0: copy the columns of block q of every row into blk
   const auto issue = [&](int q) {
-    mbar_arrive_expect_tx(&bar, (uint32_t)(N * 8 * sizeof(float)));
-    for (int r = 0; r < N; r += S::BR) tma_load_2d(blk + r * 8, &tmap, q * 2 * kColFFTs, r, &bar);
+    mbar_arrive_expect_tx(&bar, (uint32_t)(N * S::CW * sizeof(float)));
+    for (int r = 0; r < N; r += S::BR) tma_load_2d(blk + r * S::CW, &tmap, q * S::CW, r, &bar);
   };
   int q = blockIdx.x;
   if (tid == 0 && q < nblocks) issue(q);
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kColFFTs*(1 << LOGG) / kEcol, LOGG >= 12 ? 1 :
     // input x[pos] = image row (pos + N/2) mod G (the zero half is skipped)
     const auto ld = [&](int pos) -> float2 {
       const int p = (pos + N / 2) & (G - 1);
-      const float2 v = *reinterpret_cast<const float2*>(blk + p * 8 + 2 * f);
+      const float2 v = *reinterpret_cast<const float2*>(blk + p * S::CW + 2 * f);
       const float cp = sdp[p];
       return make_float2(v.x * cp * dq0, v.y * cp * dq1);
     };
@@ -1016,6 +1017,8 @@ void launch_fwd_interp(cpct_plan* p, const FwdInterpArgs& a, int n_items, cudaSt
 }
 
 }  // namespace
+
+int cpct_col_block_width() { return 2 * kColFFTs; }
 
 int cpct_gridding_resident(int which, int T, int threads) {
   int dev = 0, sms = 0, per = 0;
