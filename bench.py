@@ -724,8 +724,7 @@ def config_dict(args):
     n, ns, m, _ = WORKLOADS[args.workload]
     return {"workload": f"{args.workload}: {n}x{n} float32 phantom, {m} views x {ns} bins, KB W=6 sigma=2",
             "n": n, "n_views": m, "n_det": ns, "samples_per_op": m * ns,
-            "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}",
-            "launch": "each operator replayed as one CUDA graph (cpct_plan_set_graphs)"}
+            "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{args.gpus}"}
 
 
 # ---------------------------------------------------------------------------
@@ -847,6 +846,7 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": 4 * n * n, "d2h_bytes_per_step": 4 * m * ns + 4 * n * n,
                 "call": f"radon_pair_host_stream over {e2e_steps} slices (pinned host buffers)"},
         "gpu_launches": launches,
+        "launch": "each operator replayed as one CUDA graph (cpct_plan_set_graphs)",
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "alg_bytes_per_launch": ab, "avg_launch_us": dom_avg_s * 1e6,
