@@ -171,16 +171,22 @@ int radon_adj_host(cpct_plan* plan, const float* h_sino, float* h_img, cudaStrea
  *   h_sinos[i] = R h_imgs[i]   (radon_fwd: N x N in, M x Ns out)
  *   h_outs[i]  = R^H h_sinos[i] (radon_adj of the device-resident sinogram)
  * Two device buffer sets alternate: slice i + 1's image is copied in and
- * slice i - 1's results are copied out (on two streams of the call's own)
- * while slice i's operators run; the sets' operators run on `stream` with
- * `plan` and on a stream of the call's own with a clone of `plan` (the same
- * tables, its own workspaces, made and freed by the call; if the clone
- * cannot be made, both sets use `plan` on `stream`).  Host buffers are the
+ * slice i - 1's results are copied out (on two copy streams) while slice
+ * i's operators run; the sets' operators run on `stream` with `plan` and on
+ * a second compute stream with a clone of `plan` (the same tables, its own
+ * workspaces; if the clone cannot be made, both sets use `plan` on
+ * `stream`).  The buffer sets (2 x (2 N^2 + M Ns) floats), the clone, the
+ * streams and their events are made by the first call and kept in the plan
+ * for later calls.  They are freed with the plan, or before a call that
+ * changes the plan's configuration (cpct_plan_set_caps, _auto_caps,
+ * _set_bins, _set_rounds, _tune).  The clone follows the plan's graph mode.
+ * Host buffers are the
  * caller's; with pinned memory the copies overlap the kernels (pageable
  * memory works, without overlap).  Output buffers of different slices may
  * coincide (the copies into them are ordered).  Synchronous: returns once
- * every result is in host memory.  CPCT_EINVAL for null arguments or
- * count < 1, CPCT_ENOMEM if the two buffer sets cannot be allocated. */
+ * every result is in host memory.  Calls on one plan must not overlap (they
+ * share the kept buffers).  CPCT_EINVAL for null arguments or count < 1,
+ * CPCT_ENOMEM if the two buffer sets cannot be allocated. */
 int radon_pair_host_stream(cpct_plan* plan, const float* const* h_imgs, float* const* h_sinos,
                            float* const* h_outs, int count, cudaStream_t stream);
 

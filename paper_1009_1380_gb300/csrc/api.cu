@@ -1,5 +1,6 @@
 // Exported operator entry points (C ABI, declared in include/cpct.h).
 #include <cstdint>
+#include <new>
 
 #include "common.cuh"
 
@@ -77,6 +78,71 @@ extern "C" int radon_adj_host(cpct_plan* p, const float* h_sino, float* h_img, c
   return CPCT_OK;
 }
 
+// What radon_pair_host_stream keeps in the plan between calls: two device
+// buffer sets (image, sinogram, adjoint), a clone of the plan (the same
+// tables, its own workspaces) so that two slices' kernels can run at once,
+// the copy streams, the second compute stream and the events.  Created by
+// the first call that needs them, freed with the plan or before the plan's
+// configuration changes.
+struct HostStream {
+  float* buf = nullptr;
+  size_t bytes = 0;
+  cpct_plan* clone = nullptr;
+  cudaStream_t up = nullptr, down = nullptr, comp1 = nullptr;
+  cudaEvent_t ev[4][2] = {};  // uploaded, forward done, adjoint done, downloaded
+};
+
+void cpct_host_stream_release(cpct_plan* p) {
+  if (!p || !p->hstream) return;
+  HostStream* h = p->hstream;
+  p->hstream = nullptr;
+  if (h->down) cudaStreamSynchronize(h->down);
+  if (h->up) cudaStreamSynchronize(h->up);
+  if (h->comp1) cudaStreamSynchronize(h->comp1);
+  if (h->clone) cpct_plan_destroy(h->clone);
+  for (auto& e2 : h->ev)
+    for (auto& e : e2)
+      if (e) cudaEventDestroy(e);
+  if (h->up) cudaStreamDestroy(h->up);
+  if (h->down) cudaStreamDestroy(h->down);
+  if (h->comp1) cudaStreamDestroy(h->comp1);
+  if (h->buf) cudaFree(h->buf);
+  delete h;
+}
+
+namespace {
+// the plan's host-stream resources, created on first use (a clone only
+// when two slices or more are streamed)
+int host_stream_setup(cpct_plan* p, bool want_clone, cudaStream_t s) {
+  const size_t ni = (size_t)p->n * p->n, ns = (size_t)p->m * p->ns;
+  const size_t bytes = 2 * sizeof(float) * (2 * ni + ns);
+  if (!p->hstream) {
+    HostStream* h = new (std::nothrow) HostStream;
+    if (!h) return CPCT_ENOMEM;
+    p->hstream = h;
+    bool ok = cudaMalloc(&h->buf, bytes) == cudaSuccess;
+    if (!ok) h->buf = nullptr;
+    h->bytes = bytes;
+    ok = ok && cudaStreamCreateWithFlags(&h->up, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&h->down, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&h->comp1, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto& e2 : h->ev)
+      for (auto& e : e2) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      const int status = h->buf ? CPCT_ECUDA : CPCT_ENOMEM;
+      cpct_host_stream_release(p);
+      return status;
+    }
+  }
+  if (want_clone && !p->hstream->clone && cpct_plan_clone(p, &p->hstream->clone, s) != CPCT_OK)
+    p->hstream->clone = nullptr;  // one plan then
+  // the clone follows the plan's launch mode
+  cpct_plan* c = p->hstream->clone;
+  if (c && c->graph_mode != p->graph_mode) cpct_plan_set_graphs(c, p->graph_mode);
+  return CPCT_OK;
+}
+}  // namespace
+
 extern "C" int radon_pair_host_stream(cpct_plan* p, const float* const* h_imgs, float* const* h_sinos,
                                       float* const* h_outs, int count, cudaStream_t s) {
   if (!p || !h_imgs || !h_sinos || !h_outs || count < 1) return CPCT_EINVAL;
@@ -84,33 +150,28 @@ extern "C" int radon_pair_host_stream(cpct_plan* p, const float* const* h_imgs, 
     if (!h_imgs[i] || !h_sinos[i] || !h_outs[i]) return CPCT_EINVAL;
   const size_t ni = (size_t)p->n * p->n, ns = (size_t)p->m * p->ns;
   const size_t bi = sizeof(float) * ni, bs = sizeof(float) * ns;
-  // two buffer sets (image, sinogram, adjoint); set k runs on plan k (a
-  // clone of p: the same tables, its own workspaces) and compute stream k,
-  // so that two slices' kernels can run concurrently
-  float* buf = nullptr;
-  cpct_plan* clone = nullptr;
-  cudaStream_t up = nullptr, down = nullptr, comp1 = nullptr;
-  cudaEvent_t ev[4][2] = {};  // uploaded, forward done, adjoint done, downloaded
-  int rc = CPCT_OK;
+  int rc = host_stream_setup(p, count > 1, s);
+  if (rc != CPCT_OK) return rc;
+  HostStream* h = p->hstream;
   auto ok = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == CPCT_OK) rc = CPCT_ECUDA;
     return rc == CPCT_OK;
   };
-  if (cudaMalloc(&buf, 2 * (2 * bi + bs)) != cudaSuccess) return CPCT_ENOMEM;
-  if (ok(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking)) &&
-      ok(cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking)) &&
-      ok(cudaStreamCreateWithFlags(&comp1, cudaStreamNonBlocking))) {
-    for (auto& e2 : ev)
-      for (auto& e : e2)
-        if (!ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming))) break;
-  }
-  if (rc == CPCT_OK && count > 1 && cpct_plan_clone(p, &clone, s) != CPCT_OK) clone = nullptr;  // one plan then
-  cpct_plan* const plan_of[2] = {p, clone ? clone : p};
-  cudaStream_t const comp[2] = {s, clone ? comp1 : s};
+  // set k runs on plan k and compute stream k (with one plan both sets
+  // share the caller's stream)
+  cpct_plan* const plan_of[2] = {p, h->clone ? h->clone : p};
+  cudaStream_t const comp[2] = {s, h->clone ? h->comp1 : s};
+  cudaStream_t const up = h->up, down = h->down;
+  auto& ev = h->ev;
   enum { IN = 0, FWD = 1, ADJ = 2, OUT = 3 };
+  // the buffers are free once the previous call's work on them is done
+  for (int k = 0; k < 2; ++k) {
+    ok(cudaStreamWaitEvent(up, ev[OUT][k], 0));
+    ok(cudaStreamWaitEvent(comp[k], ev[OUT][k], 0));
+  }
   for (int i = 0; i < count && rc == CPCT_OK; ++i) {
     const int k = i & 1;
-    float* img = buf + k * (2 * ni + ns);
+    float* img = h->buf + k * (2 * ni + ns);
     float* sino = img + ni;
     float* out = sino + ns;
     cudaStream_t cs = comp[k];
@@ -119,8 +180,7 @@ extern "C" int radon_pair_host_stream(cpct_plan* p, const float* const* h_imgs, 
     if (!ok(cudaMemcpyAsync(img, h_imgs[i], bi, cudaMemcpyHostToDevice, up))) break;
     if (!ok(cudaEventRecord(ev[IN][k], up))) break;
     // operators: after the upload, and once slice i - 2's downloads have
-    // read this set's sinogram and adjoint buffers (slice i - 2 ran on the
-    // same plan and stream; with one plan both sets share stream s)
+    // read this set's sinogram and adjoint buffers
     if (!ok(cudaStreamWaitEvent(cs, ev[IN][k], 0))) break;
     if (i >= 2 && !ok(cudaStreamWaitEvent(cs, ev[OUT][k], 0))) break;
     if ((rc = cpct_graph_run(plan_of[k], 0, img, sino, cs)) != CPCT_OK) break;
@@ -134,19 +194,11 @@ extern "C" int radon_pair_host_stream(cpct_plan* p, const float* const* h_imgs, 
     if (!ok(cudaMemcpyAsync(h_outs[i], out, bi, cudaMemcpyDeviceToHost, down))) break;
     if (!ok(cudaEventRecord(ev[OUT][k], down))) break;
   }
-  // everything issued has finished before the buffers are released
-  if (down) ok(cudaStreamSynchronize(down));
-  if (up) ok(cudaStreamSynchronize(up));
-  if (comp1) ok(cudaStreamSynchronize(comp1));
+  // every copy has landed in host memory before the call returns
+  ok(cudaStreamSynchronize(down));
+  ok(cudaStreamSynchronize(up));
+  if (h->clone) ok(cudaStreamSynchronize(h->comp1));
   ok(cudaStreamSynchronize(s));
-  if (clone) cpct_plan_destroy(clone);
-  for (auto& e2 : ev)
-    for (auto& e : e2)
-      if (e) cudaEventDestroy(e);
-  if (up) cudaStreamDestroy(up);
-  if (down) cudaStreamDestroy(down);
-  if (comp1) cudaStreamDestroy(comp1);
-  cudaFree(buf);
   return rc;
 }
 

@@ -116,6 +116,7 @@ struct cpct_plan {
   int graph_mode;
   struct GraphCache* graphs;  // captured operator graphs (NULL: none yet)
   struct GraphCapture* capturing;  // set while an operator is being captured
+  struct HostStream* hstream;  // buffers, clone and streams of radon_pair_host_stream (NULL: none yet)
 };
 
 // Read-only data of one geometry, shared by a plan and its clones: the
@@ -152,6 +153,8 @@ int cpct_graph_run(cpct_plan* p, int op, const void* in, void* out, cudaStream_t
 void cpct_graph_clear(cpct_plan* p);
 // free the graph cache (plan destruction)
 void cpct_graph_free(cpct_plan* p);
+// free what radon_pair_host_stream keeps between calls (api.cu)
+void cpct_host_stream_release(cpct_plan* p);
 // while capturing: record a profiling event as a graph node (profile.cu)
 void cpct_graph_prof_event(cpct_plan* p, int kid, bool begin, cudaEvent_t ev, cudaStream_t s);
 

@@ -170,6 +170,7 @@ EncodeTiledFn get_encode_fn() {
 
 void free_plan(cpct_plan* p) {
   if (!p) return;
+  cpct_host_stream_release(p);
   cpct_graph_free(p);
   cpct_prof_free(p);
   cpct_plan_streams_destroy(p);
@@ -813,6 +814,7 @@ extern "C" int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream
   p->prof = nullptr;
   p->graphs = nullptr;
   p->capturing = nullptr;
+  p->hstream = nullptr;
   p->launches = 0;
   p->device_bytes = 0;
   p->shared->refs++;
@@ -848,6 +850,7 @@ extern "C" int cpct_plan_clone(const cpct_plan* src, cpct_plan** out, cudaStream
 // launches (CUDA events on `stream`) and the fastest is kept.
 extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap, cudaStream_t stream) {
   if (!p || !p->shared) return CPCT_EINVAL;
+  cpct_host_stream_release(p);  // its cached clone shares this plan's tables
   if (p->shared->refs != 1) return CPCT_EINVAL;  // tune before cloning
   if (reps < 1) reps = 5;
   float *img = nullptr, *sino = nullptr;
@@ -946,6 +949,7 @@ extern "C" int cpct_plan_tune(cpct_plan* p, int reps, int* fwd_cap, int* adj_cap
 // plan must not have clones.  Synchronous.
 extern "C" int cpct_plan_set_caps(cpct_plan* p, int fwd_cap, int adj_cap, cudaStream_t stream) {
   if (!p || !p->shared || fwd_cap < 0 || adj_cap < 0) return CPCT_EINVAL;
+  cpct_host_stream_release(p);  // its cached clone shares this plan's tables
   if (p->shared->refs != 1) return CPCT_EINVAL;
   int rc = CPCT_OK;
   if (fwd_cap > 0) {
@@ -963,6 +967,7 @@ extern "C" int cpct_plan_set_caps(cpct_plan* p, int fwd_cap, int adj_cap, cudaSt
 // share of the resident CTAs).  The plan must not have clones.  Synchronous.
 extern "C" int cpct_plan_auto_caps(cpct_plan* p, int concurrent, cudaStream_t stream) {
   if (!p || !p->shared || concurrent < 1) return CPCT_EINVAL;
+  cpct_host_stream_release(p);  // its cached clone shares this plan's tables
   if (p->shared->refs != 1) return CPCT_EINVAL;
   p->concurrency = concurrent;
   p->fwd_cap_set = p->adj_cap_set = 0;
@@ -977,6 +982,7 @@ extern "C" int cpct_plan_auto_caps(cpct_plan* p, int concurrent, cudaStream_t st
 // bins.  The plan must not have clones.  Synchronous.
 extern "C" int cpct_plan_set_bins(cpct_plan* p, int which, int kind, int tile, cudaStream_t stream) {
   if (!p || !p->shared || (which != 0 && which != 1) || !bins_args_ok(kind, tile)) return CPCT_EINVAL;
+  cpct_host_stream_release(p);  // its cached clone shares this plan's tables
   if (p->shared->refs != 1) return CPCT_EINVAL;
   return which == 0 ? install_fwd_plan(p, kind, tile, p->fwd_cap_set ? p->fwd_cap : kCapAuto, stream)
                     : install_adj_plan(p, kind, tile, p->adj_cap_set ? p->adj_cap : kCapAuto, stream);
@@ -988,6 +994,7 @@ extern "C" int cpct_plan_set_bins(cpct_plan* p, int which, int kind, int tile, c
 // not have clones.  Synchronous.
 extern "C" int cpct_plan_set_rounds(cpct_plan* p, int lanes, cudaStream_t stream) {
   if (!p || !p->shared || !lanes_ok(lanes)) return CPCT_EINVAL;
+  cpct_host_stream_release(p);  // its cached clone shares this plan's tables
   if (p->shared->refs != 1) return CPCT_EINVAL;
   return install_adj_plan(p, p->adj_kind, p->adj_tile ? p->adj_tile : CPCT_TILE, p->adj_cap_set ? p->adj_cap : kCapAuto,
                           stream, lanes);

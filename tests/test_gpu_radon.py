@@ -317,6 +317,43 @@ def test_pair_host_stream_matches_device(torch_cuda):
     np.testing.assert_array_equal(o2[0], outs[0])
 
 
+def test_pair_host_stream_keeps_its_resources(torch_cuda):
+    """The buffers, plan clone and streams kept in the plan between calls:
+    repeated calls, graph mode switched on, and a configuration change
+    between calls (which frees them) all give the device operators' results
+    bit for bit."""
+    torch = torch_cuda
+    n, m, count = 128, 64, 4
+    p = _plan(n, n, m)
+    rng = np.random.default_rng(22)
+    imgs = [rng.standard_normal((n, n)).astype(np.float32) for _ in range(count)]
+
+    def device(plan):
+        ys, zs = [], []
+        for im in imgs:
+            y = plan.fwd(torch.from_numpy(im).cuda())
+            ys.append(y.cpu().numpy())
+            zs.append(plan.adj(y).cpu().numpy())
+        return ys, zs
+
+    ys, zs = device(p)
+    for call in range(3):
+        if call == 1:
+            p.set_graphs(True)
+        sinos, outs = p.pair_host_stream(imgs)
+        for i in range(count):
+            np.testing.assert_array_equal(sinos[i], ys[i])
+            np.testing.assert_array_equal(outs[i], zs[i])
+    # a new work-item cap frees the kept clone; the next call makes a new one
+    p.set_caps(fwd_cap=300, adj_cap=12)
+    ys2, zs2 = device(p)
+    sinos, outs = p.pair_host_stream(imgs)
+    for i in range(count):
+        np.testing.assert_array_equal(sinos[i], ys2[i])
+        np.testing.assert_array_equal(outs[i], zs2[i])
+    p.sync()
+
+
 def test_errors(torch_cuda):
     torch = torch_cuda
     from paper_1009_1380_gb300 import cpct
