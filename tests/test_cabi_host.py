@@ -128,6 +128,22 @@ def test_host_stream_rejects_bad_arguments_before_any_device_work(cpct):
     assert L.radon_pair_host_stream(fake_plan, one, one, nul, 1, None) == -1
 
 
+def test_graph_mode_rejects_bad_arguments(cpct):
+    """cpct_plan_set_graphs / cpct_plan_graphs check their arguments on the
+    host: a null plan or an enable other than 0 or 1 is CPCT_EINVAL (-1)."""
+    import ctypes
+    L = cpct.lib()
+    vp = ctypes.c_void_p
+    L.cpct_plan_set_graphs.argtypes = [vp, ctypes.c_int]
+    L.cpct_plan_graphs.argtypes = [vp]
+    assert L.cpct_plan_set_graphs(None, 1) == -1
+    assert L.cpct_plan_set_graphs(None, 0) == -1
+    assert L.cpct_plan_graphs(None) == -1
+    fake_plan = vp(1)  # never dereferenced: the value check fails first
+    assert L.cpct_plan_set_graphs(fake_plan, 2) == -1
+    assert L.cpct_plan_set_graphs(fake_plan, -1) == -1
+
+
 def test_source_digest_is_independent_of_the_checkout_location(monkeypatch):
     """The Radon source digest (which gates the committed ncu traffic in the
     bench line) names include directories by basename, so a checkout at
