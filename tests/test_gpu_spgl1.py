@@ -5,7 +5,7 @@ idempotent on the device.  With a single fixed tau (the LASSO problem, whose
 solution the mathematics fixes) the device solution matches the oracle's
 element by element (relative L2 1e-3) once both duality gaps are small.  The
 basis-pursuit denoising solve reaches the root on both sides, and the
-solutions agree in misfit and in l1 norm to 1e-3 (survey pin P8).  Its x is
+solutions agree in misfit and in l1 norm to 1e-3 (the certificate pin).  Its x is
 compared at 5e-2 only: SPGL1 is an inexact Newton method whose exit test is
 the root error alone, with the last LASSO problem's duality gap still O(1),
 so x at exit is fixed by the method only to a few percent -- the FP64 oracle
