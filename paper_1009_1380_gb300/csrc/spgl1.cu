@@ -67,21 +67,6 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ]) {
   __syncthreads();
 }
 
-__device__ __forceinline__ double block_max(double v) {
-  __shared__ double sh[kRB / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  v = warp_max(v);
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = sh[0];
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, sh[i]);
-    v = m;
-  }
-  __syncthreads();
-  return v;
-}
-
 // ---------------------------------------------------------------------------
 // ring filter
 // ---------------------------------------------------------------------------
@@ -277,8 +262,6 @@ constexpr int P_APPLY = 0;                  // 3: gtd, dn2, dinf
 constexpr int P_RES = P_APPLY + 3;          // 2: sum rt^2, sum rt*bf
 constexpr int P_GRAD = P_RES + 2;           // 4: sts, sty, ginf, gnorm2
 constexpr int P_TOTAL = P_GRAD + 4;
-
-__device__ __forceinline__ double pget(const double* part, int q, int b) { return part[(size_t)q * kRG + b]; }
 
 // FP64 throughput is a small fraction of FP32 on this GPU, so every
 // per-element operation and per-thread / per-warp partial is FP32 (counts are
