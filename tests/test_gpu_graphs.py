@@ -148,3 +148,26 @@ def test_calls_inside_a_caller_capture_launch_directly(torch_cuda):
     torch.cuda.synchronize()
     assert torch.equal(y, y0)
     p.sync()
+
+
+def test_host_buffer_operators_in_graph_mode(torch_cuda):
+    """radon_fwd_host / radon_adj_host replay their graphs (the plan's staging
+    buffers are the same on every call) and give the device operators'
+    results bit for bit, call after call."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300.cpct import Plan
+    n, m = 256, 90
+    rng = np.random.default_rng(5)
+    p = Plan(n, n, m)
+    imgs = [rng.standard_normal((n, n)).astype(np.float32) for _ in range(3)]
+    ref = [(p.fwd(torch.from_numpy(im).cuda()).cpu().numpy(),) for im in imgs]
+    ref = [(y, p.adj(torch.from_numpy(y).cuda()).cpu().numpy()) for (y,) in ref]
+    p.set_graphs(True)
+    for k in range(2):
+        for im, (y_ref, z_ref) in zip(imgs, ref):
+            y = p.fwd_host(im)
+            z = p.adj_host(y)
+            np.testing.assert_array_equal(y, y_ref)
+            np.testing.assert_array_equal(z, z_ref)
+    assert p.graphs() == 2
+    p.sync()
