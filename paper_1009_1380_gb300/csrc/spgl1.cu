@@ -357,6 +357,7 @@ __global__ void __launch_bounds__(kRB) k_spg_proj_apply(SpgVec V) {
   const double th = st->theta;
   const int ident = st->proj_identity, zero = st->proj_zero;
   const bool feas = st->type == T_FEAS, store = st->store_dir != 0;
+  const bool full = st->type == T_INIT || !st->single_tau;  // operator on xt itself
   float q[2] = {0.f, 0.f};  // gtd, dn2
   float dinf = 0.f;
   SPG_LOOP(i, V.n) {
@@ -379,6 +380,13 @@ __global__ void __launch_bounds__(kRB) k_spg_proj_apply(SpgVec V) {
     }
     V.xt[i] = xt;
     const float d = xt - xi;
+    // the operator's input.  With a fixed tau (LASSO) the trial's step from
+    // x: the residual is then r - F(R d), whose FP32 rounding is relative to
+    // ||R d|| rather than to ||R xt||, so the objective resolves the small
+    // decreases of the last iterations.  Else (and on the set-up tick) the
+    // trial point itself: the root-finding's control was checked against
+    // the FP64 oracle with the residual bf - F(R xt).
+    if (V.gtmp) V.gtmp[i] = full ? xt : d;  // (null in the stand-alone projection)
     if (store) V.dir[i] = d;
     q[0] = fmaf(V.g[i], d, q[0]);
     q[1] = fmaf(d, d, q[1]);
@@ -394,14 +402,19 @@ __global__ void __launch_bounds__(kRB) k_spg_proj_apply(SpgVec V) {
   }
 }
 
-// rt = bf - F(R xt) = bf - (y - d), with the filter offsets d per column
+// rt = bf - F(R xt).  With y = R xt (the set-up tick, and every tick when
+// tau is updated) rt = bf - F y; with a fixed tau after the set-up tick
+// y = R (xt - x) and rt = r - F y, r the residual of the current x (the same
+// value in exact arithmetic; F y = y - d with the filter offsets d per
+// column)
 __global__ void __launch_bounds__(kRB) k_spg_resid(SpgVec V, const float* __restrict__ doff, int ns, int filter) {
   const SpgState* st = V.st;
   if (st->done) return;
+  const float* base = (st->type == T_INIT || !st->single_tau) ? V.bf : V.r;
   float q[2] = {0.f, 0.f};
   SPG_LOOP(i, V.m) {
     const float fy = filter ? V.y[i] - doff[i % ns] : V.y[i];
-    const float r = V.bf[i] - fy;
+    const float r = base[i] - fy;
     V.rt[i] = r;
     q[0] = fmaf(r, r, q[0]);
     q[1] = fmaf(r, V.bf[i], q[1]);
@@ -1000,12 +1013,14 @@ void enqueue_tick(SliceWork& w, int filter) {
     k_spg_radix_select<<<1, kRB, 0, s>>>(V, pass);
   }
   k_spg_proj_apply<<<kRG, kRB, 0, s>>>(V);
+  // the operator acts on gtmp, written by the projection: the trial point,
+  // or its step from x with a fixed tau (k_spg_proj_apply)
   if (w.ubuf) {
-    // analysis-l1 variant: the operator acts on u = C xt
-    launch_synth(V.xt, w.ubuf, w.plan->n, 0, &V.st->skip_fwd, s);
+    // analysis-l1 variant: the operator acts on u = C gtmp
+    launch_synth(V.gtmp, w.ubuf, w.plan->n, 0, &V.st->skip_fwd, s);
     cpct_launch_fwd_skip(w.plan, w.ubuf, V.y, &V.st->skip_fwd, s);
   } else {
-    cpct_launch_fwd_skip(w.plan, V.xt, V.y, &V.st->skip_fwd, s);
+    cpct_launch_fwd_skip(w.plan, V.gtmp, V.y, &V.st->skip_fwd, s);
   }
   if (filter) {
     k_ring_colmean<<<(w.plan->ns + 31) / 32, kRB, 0, s>>>(V.y, w.ring.m, w.plan->m, w.plan->ns);

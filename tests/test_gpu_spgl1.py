@@ -97,15 +97,15 @@ def test_spgl1_matches_oracle(torch_cuda):
     assert _rel(xg, xo) < 2e-2
 
 
-@pytest.mark.parametrize("n,m,tol", [(64, 64, 1e-3), (128, 90, 2e-3)])
+@pytest.mark.parametrize("n,m,tol", [(64, 64, 1e-3), (128, 90, 1e-3)])
 def test_lasso_matches_oracle(torch_cuda, n, m, tol):
     """The LASSO problem min ||F(R x) - F b|| s.t. ||x||_1 <= tau at a fixed
     tau (half the l1 norm of the true image): device and FP64 oracle solutions
-    agree element by element.  The device solve runs until its objective
-    stops resolving descent (FP32 operators: the rounding of F(R x) makes f
-    noisy at ~1e-7 ||r|| ||b||, and the duality gap ends near 1e-3, where the
-    oracle's is 1e-5); x agrees with the oracle to about that gap (measured
-    4.9e-4 at 64^2, 1.25e-3 at 128^2)."""
+    agree element by element.  With a fixed tau the device keeps the residual
+    as r - F(R (xt - x)), so its FP32 rounding is relative to the step, not to
+    ||R xt||.  The solve runs until the objective stops resolving descent, at
+    a duality gap near 1e-3 (the oracle's is 1e-5).  Measured x against the
+    oracle: 7.8e-4 at 64^2, 2.1e-4 at 128^2."""
     torch = torch_cuda
     from paper_1009_1380_gb300 import cpct
     geo, x_true, b, sigma = _problem(n, m)
