@@ -5,12 +5,13 @@ idempotent on the device.  With a single fixed tau (the LASSO problem, whose
 solution the mathematics fixes) the device solution matches the oracle's
 element by element (relative L2 1e-3) once both duality gaps are small.  The
 basis-pursuit denoising solve reaches the root on both sides, and the
-solutions agree in misfit and in l1 norm to 1e-3 (the certificate pin).  Its x is
-compared at 5e-2 only: SPGL1 is an inexact Newton method whose exit test is
-the root error alone, with the last LASSO problem's duality gap still O(1),
-so x at exit is fixed by the method only to a few percent -- the FP64 oracle
-itself ends 2.9% apart (relative L2) between opt_tol 1e-6 and 1e-7 on this
-problem, and FP32 operators change line-search branches.
+solutions agree in misfit and in l1 norm to 1e-3 (the certificate pin).  Its
+x is compared at 2e-2 (measured 0.8-1.0%): SPGL1 is an inexact Newton method
+whose exit test is the root error alone, with the last LASSO problem's
+duality gap still O(1), so x at exit is fixed by the method only to a few
+percent -- the FP64 oracle itself ends 2.9% apart (relative L2) between
+opt_tol 1e-6 and 1e-7 on this problem, and FP32 operators change
+line-search branches.
 """
 import numpy as np
 import pytest
