@@ -8,7 +8,10 @@ benchmark and the warm-start pipeline use:
   root condition and ||x||_1 of the device solution re-evaluated with the
   FP64 oracle operator and filter;
 * the warm-start denoiser at its full shape (5 levels, 32 base channels) on
-  one 512^2 image against the FP64 oracle with the device's operand rounding.
+  one 512^2 image against the FP64 oracle with the device's operand rounding;
+* the largest geometries a plan accepts (32768 views; 2048^2 with 4096
+  detector bins): both operators against the FP64 oracle (measured 2.1e-7 ..
+  3.1e-7).
 """
 import numpy as np
 import pytest
@@ -201,3 +204,35 @@ def test_complex_pair_full_size_2048(torch_cuda):
     e_a = _rel(z.cpu().numpy().astype(np.float64), z_ref)
     print(f"2048 complex pair: fwd_c sampled rays rel {e_f:.2e}, adj_c on {len(rays)} rays rel {e_a:.2e}")
     assert e_f < 1e-5 and e_a < 1e-5
+
+
+@pytest.mark.parametrize("n,ns,m", [(64, 64, 32768), (2048, 4096, 256)])
+def test_largest_accepted_geometries(torch_cuda, n, ns, m):
+    """The limits a plan accepts: the most views (32768, every 16-bit ray
+    index of the bin lists in use) and the largest image with the widest
+    detector (2048^2, 4096 bins: the 4096-point ray transforms).  Forward and
+    adjoint against the FP64 oracle: every ray where the oracle is quick,
+    else eight rays including the first and the last (the adjoint of a
+    sinogram that is non-zero on those rays only)."""
+    torch = torch_cuda
+    from paper_1009_1380_gb300 import cpct
+    rng = np.random.default_rng(n + ns + m)
+    img = rng.standard_normal((n, n)).astype(np.float32)
+    geo = nufft.GridGeometry(n, ns, nufft.default_angles(m))
+    G = geo.grid
+    rays = np.arange(m) if n <= 64 else np.array([0, 1, 2, 63, 64, 128, 200, m - 1])
+    w = np.zeros((m, ns), dtype=np.float32)
+    w[rays] = rng.standard_normal((len(rays), ns)).astype(np.float32)
+    p = cpct.Plan(n, ns, m)
+    y = p.fwd(torch.from_numpy(img).cuda())
+    z = p.adj(torch.from_numpy(w).cuda())
+    torch.cuda.synchronize()
+    p.sync()
+    y_ref = nufft.radon_grid(img.astype(np.float64), geo, rays)
+    Pt = nufft.ray_idft_adj(w[rays].astype(np.float64))
+    Yh = nufft.grid_spread(Pt, geo, rays)
+    z_ref = nufft.grid_crop_deapod(nufft.ifft2(Yh) * (G * G), geo).real
+    ef = _rel(y.cpu().numpy()[rays].astype(np.float64), y_ref)
+    ea = _rel(z.cpu().numpy().astype(np.float64), z_ref)
+    print(f"{n}^2, {ns} bins, {m} views: fwd {ef:.2e} on {len(rays)} rays, adj {ea:.2e}")
+    assert ef < 1e-5 and ea < 1e-5
