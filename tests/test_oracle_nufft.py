@@ -11,6 +11,7 @@ dropped term, a wrong sign, a transposed operand, a wrong centre) fails one:
 * adjoint identity (1e-12)        -> every adjoint
 * quadrature of the kernel        -> the Kaiser-Bessel Fourier transform
 * exact vs gridding (1e-4)        -> deapodization, taps, oversampled FFT
+* planted mistakes                -> that pin fails for each of them
 """
 import math
 
@@ -187,3 +188,44 @@ def test_fbp_recovers_disk_value():
     for (cx, cy, r, v) in disks:
         mask = (X[None, :] - cx) ** 2 + (X[:, None] - cy) ** 2 < (r - 3) ** 2
         assert abs(rec[mask].mean() - v) / v < 0.05
+
+
+@pytest.mark.parametrize("mistake", ["no_deapod", "swapped_axes", "tap_shift", "fft_sign", "spread_one_axis"])
+def test_planted_mistakes_fail_the_gridding_pin(monkeypatch, mistake):
+    """A plausible mistake planted in the gridding oracle (on the CPU) makes
+    it miss the exact operator by far more than the 1e-4 the pin allows:
+    the deapodization left out, the u and v axes swapped, the taps shifted by
+    one grid point, the forward 2D FFT of the wrong sign, the spread weighting
+    by one axis only (adjoint)."""
+    n, m = 32, 45
+    th = nufft.default_angles(m)
+    img = np.random.default_rng(6).standard_normal((n, n))
+    w = np.random.default_rng(7).standard_normal((m, n))
+    geo = nufft.GridGeometry(n, n, th)
+    if mistake == "no_deapod":
+        geo.cx = np.ones_like(geo.cx)
+    elif mistake == "swapped_axes":
+        geo.u, geo.v = geo.v.copy(), geo.u.copy()
+    elif mistake == "tap_shift":
+        taps = geo.taps
+        monkeypatch.setattr(geo, "taps", lambda c: (lambda a, wt: (a + 1, wt))(*taps(c)))
+    elif mistake == "fft_sign":
+        G = geo.grid
+        monkeypatch.setattr(nufft, "fft2", lambda a: nufft.ifft2(a) * (G * G))
+    elif mistake == "spread_one_axis":
+        def spread(Pt, g, rays=None):
+            G = g.grid
+            a, wa = g.taps(g.u)
+            b, _ = g.taps(g.v)
+            out = np.zeros(G * G, dtype=np.complex128)
+            for ib in range(b.shape[-1]):
+                for ia in range(a.shape[-1]):
+                    np.add.at(out, ((b[..., ib] % G) * G + (a[..., ia] % G)).ravel(), (wa[..., ia] * Pt).ravel())
+            return out.reshape(G, G)
+        monkeypatch.setattr(nufft, "grid_spread", spread)
+    if mistake == "spread_one_axis":
+        err = _rel(nufft.radon_grid_adj(w, geo), nufft.radon_exact_adj(w, n, th))
+    else:
+        err = _rel(nufft.radon_grid_c(img, geo), nufft.radon_exact_c(img, n, th))
+    print(mistake, err)
+    assert err > 1e-2, (mistake, err)
