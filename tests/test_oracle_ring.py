@@ -51,3 +51,35 @@ def test_removes_stuck_column_offset_exactly():
     V = np.stack([s ** d for d in range(4)], axis=1)
     trend = V @ np.linalg.lstsq(V, spike, rcond=None)[0]
     np.testing.assert_allclose(out, z + trend[None, :], atol=1e-12)
+
+
+def _pins_hold():
+    """The checks of the tests above, as one predicate."""
+    try:
+        test_projector_properties()
+        test_annihilates_non_cubic_column_offsets()
+        test_keeps_sinograms_with_cubic_column_means()
+        test_removes_stuck_column_offset_exactly()
+    except AssertionError:
+        return False
+    return True
+
+
+def test_planted_mistakes_fail_the_pins(monkeypatch):
+    """Plausible mistakes planted in the filter (on the CPU) each fail at
+    least one pin: a quadratic instead of a cubic trend, column sums instead
+    of means, the trend removed instead of kept, means over the detector
+    instead of over the angles."""
+    assert _pins_hold()
+    basis, means = ring.cubic_basis, ring.column_means
+    mistakes = {
+        "quadratic": ("cubic_basis", lambda n: basis(n)[:, :3]),
+        "sums": ("column_means", lambda y: y.sum(axis=0)),
+        "trend_removed": ("cubic_fit", lambda m: m - basis(m.shape[0]) @ (basis(m.shape[0]).T @ m)),
+        "row_means": ("column_means", lambda y: np.resize(y.mean(axis=1), y.shape[1])),
+    }
+    for name, (attr, fn) in mistakes.items():
+        with monkeypatch.context() as mp:
+            mp.setattr(ring, attr, fn)
+            assert not _pins_hold(), name
+    assert ring.column_means is means and _pins_hold()

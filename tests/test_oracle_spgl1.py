@@ -199,3 +199,37 @@ def test_warm_start_near_the_solution_saves_iterations():
             assert info2.n_line_errors == 0
             assert info2.iterations < info.iterations
             assert abs(info2.xnorm1 - info.xnorm1) <= 1e-3 * info.xnorm1
+
+
+@pytest.mark.parametrize("mistake", ["theta_next_rho", "no_clip", "unsigned", "scaled"])
+def test_planted_projection_mistakes_fail_the_pin(monkeypatch, mistake):
+    """A plausible mistake planted in the l1-ball projection (on the CPU)
+    fails the optimality pin above: the threshold taken with one term too
+    many, soft thresholding without the clip at zero, the signs dropped,
+    and a rescaling of v onto the sphere instead of a projection."""
+    right = spgl1.project_l1
+
+    def wrong(v, tau):
+        v = np.asarray(v, dtype=np.float64)
+        if np.abs(v).sum() <= tau:
+            return v.copy()
+        u = np.sort(np.abs(v))[::-1]
+        cs = np.cumsum(u)
+        j = np.arange(1, u.size + 1)
+        rho = int(np.nonzero(u > (cs - tau) / j)[0][-1])
+        if mistake == "theta_next_rho":
+            rho = min(rho + 1, u.size - 1)
+        theta = (cs[rho] - tau) / (rho + 1)
+        if mistake == "no_clip":
+            return np.sign(v) * (np.abs(v) - theta)
+        if mistake == "unsigned":
+            return np.maximum(np.abs(v) - theta, 0.0)
+        if mistake == "scaled":
+            return v * tau / np.abs(v).sum()
+        return np.sign(v) * np.maximum(np.abs(v) - theta, 0.0)
+
+    monkeypatch.setattr(spgl1, "project_l1", wrong)
+    with pytest.raises(AssertionError):
+        test_project_l1_kkt_and_bisection()
+    monkeypatch.setattr(spgl1, "project_l1", right)
+    test_project_l1_kkt_and_bisection()
