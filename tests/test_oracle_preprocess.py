@@ -60,3 +60,46 @@ def test_noise_free_difference_is_the_phase_laplacian():
                              counts=False)
     s = pp.phase_contrast_sinograms(r["near"], r["far"], r["flat_near"], r["flat_far"], r["dark"])
     np.testing.assert_allclose(s, r["pc_term"].transpose(1, 0, 2), rtol=1e-10, atol=1e-12)
+
+
+def _pins_hold():
+    try:
+        test_normalization_identities()
+        test_dead_reference_pixels_give_zero()
+        test_equal_frames_and_transpose()
+        test_noise_free_difference_is_the_phase_laplacian()
+    except (AssertionError, FloatingPointError, ValueError):
+        return False
+    return True
+
+
+def test_planted_mistakes_fail_the_pins(monkeypatch):
+    """Plausible mistakes planted in the preprocessing oracle (on the CPU)
+    each fail at least one pin: the dark frame not subtracted from the flat,
+    the dark frame not subtracted from the image, far minus near, the
+    (angle, row) axes left untransposed."""
+    assert _pins_hold()
+    norm, pcs = pp.normalize, pp.phase_contrast_sinograms
+
+    def flat_raw(frame, flat, dark):
+        f = np.asarray(frame, np.float64)
+        return (f - dark) / np.asarray(flat, np.float64)
+
+    def frame_raw(frame, flat, dark):
+        den = np.asarray(flat, np.float64) - dark
+        return np.where(den > 0, np.asarray(frame, np.float64) / np.where(den > 0, den, 1.0), 0.0)
+
+    def swapped(near, far, flat_near, flat_far, dark):
+        return pcs(far, near, flat_far, flat_near, dark)
+
+    def untransposed(near, far, flat_near, flat_far, dark):
+        return np.ascontiguousarray(pcs(near, far, flat_near, flat_far, dark).transpose(1, 0, 2))
+
+    for name, attr, fn in [("flat_raw", "normalize", flat_raw), ("frame_raw", "normalize", frame_raw),
+                           ("swapped", "phase_contrast_sinograms", swapped),
+                           ("untransposed", "phase_contrast_sinograms", untransposed)]:
+        with monkeypatch.context() as mp:
+            mp.setattr(pp, attr, fn)
+            with np.errstate(all="ignore"):
+                assert not _pins_hold(), name
+    assert pp.normalize is norm and _pins_hold()
